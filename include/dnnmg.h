@@ -1,0 +1,171 @@
+/*
+ * dnnmg.h - C ABI of the GB300 (sm_103a) DNN-MG hot path.
+ *
+ * The library advances the 2D incompressible Navier-Stokes equations
+ * (Sec. 2.1, Eq. 1 with the boundary conditions of Eq. 2) in a channel
+ * [0,4] x [0,1] with a block obstacle, discretised by Q1/Q1 finite elements
+ * with local projection stabilisation (Eqs. 4-5) on a hierarchy of uniformly
+ * refined meshes.  Each time step solves A_n(x_n) = f_n (Eq. 6) by Newton's
+ * method (Eq. 7) whose linear systems are solved by flexible GMRES
+ * preconditioned with one geometric multigrid V-cycle (Sec. 2.2, Algorithm 1
+ * lines 2-4).  In DNN-MG mode a patch-wise recurrent network (stacked GRUs +
+ * dense layers, Sec. 2.2 and Sec. 3.1) predicts a velocity correction on the
+ * level(s) above the finest solved one, which enters the next step through
+ * the restricted right-hand side (Algorithm 1 lines 6-9); the network is
+ * trained with the loss of Eq. 8.
+ *
+ * Conventions
+ *  - Every function returns a status code (DNNMG_OK = 0).  On failure the
+ *    context keeps a message, read with dnnmg_last_error().  Nothing prints
+ *    and nothing aborts.
+ *  - The context owns all device memory it needs; it allocates it in
+ *    dnnmg_setup() and frees it in dnnmg_destroy().  Apart from the calls that
+ *    say otherwise, calls do not allocate.
+ *  - Pointer arguments marked "device" are device pointers of the current
+ *    CUDA device, borrowed for the duration of the call.  Work is issued on
+ *    the stream given to dnnmg_setup(); functions that return results to the
+ *    host synchronise that stream.
+ *  - A field on mesh level l is stored as [3][ny+1][nx+1] (u, v, p; x index
+ *    fastest) with nx = 16 * 2^l, ny = 4 * 2^l: node (i, j) of component c at
+ *    c * (nx+1)(ny+1) + j * (nx+1) + i.  Velocity-only fields are [2][..].
+ *  - A context is not thread-safe; use one per host thread.
+ */
+#ifndef DNNMG_H
+#define DNNMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define DNNMG_OK 0
+#define DNNMG_ERR_ARG 1            /* invalid argument or configuration */
+#define DNNMG_ERR_CUDA 2           /* a CUDA call failed */
+#define DNNMG_ERR_NOT_CONVERGED 3  /* Newton hit its iteration cap; the step is still taken */
+#define DNNMG_ERR_NUMERICAL 4      /* NaN/Inf or a singular local/coarse matrix */
+#define DNNMG_ERR_TIMEOUT 5        /* a device loop hit its iteration cap */
+#define DNNMG_ERR_STATE 6          /* call not valid in the context's current state */
+
+/* precision modes */
+#define DNNMG_FP64 0   /* everything in FP64 */
+#define DNNMG_MIXED 1  /* V-cycle and GMRES in FP32 inside FP64 Newton (defect correction) */
+
+/* time-step modes */
+#define DNNMG_PLAIN 0  /* classical Newton-Krylov-multigrid step (Algorithm 1 lines 2-4) */
+#define DNNMG_NET 1    /* DNN-MG step (Algorithm 1 lines 2-9) */
+
+typedef struct dnnmg_ctx dnnmg_ctx;
+
+/* Configuration (plain old data).  Start from dnnmg_default_config(). */
+typedef struct dnnmg_config {
+  double nu;          /* kinematic viscosity, 1/Re (Eq. 1) */
+  double dt;          /* time step k (Eq. 5) */
+  double theta;       /* time scheme weight: 1 = backward Euler, 0.5 = Crank-Nicolson (Eq. 5) */
+  double alpha0;      /* LPS parameter, alpha_T = alpha0 * Re * h_T^2 (Sec. 2.1) */
+  double newton_tol;  /* stop when the l2 norm of f_n - A_n(x) over free DOFs <= newton_tol */
+  double gmres_rtol;  /* relative residual reduction of FGMRES per Newton step */
+  double omega;       /* damping of the Vanka update */
+  double eps_damp;    /* Newton damping epsilon (Algorithm 1 line 4) */
+  int32_t obstacle_i0, obstacle_j0; /* lower-left level-0 cell of the 2x2 solid block, -1 = none */
+  int32_t level_solve;     /* finest level L solved by multigrid */
+  int32_t level_coarse;    /* coarsest multigrid level (direct solve), >= 1 */
+  int32_t replaced_levels; /* levels above L replaced by the network (1 or 2; 0 = none) */
+  int32_t precision;       /* DNNMG_FP64 or DNNMG_MIXED */
+  int32_t newton_max;      /* Newton iteration cap */
+  int32_t gmres_m;         /* FGMRES restart length (<= 40) */
+  int32_t gmres_maxit;     /* total FGMRES iteration cap per Newton step */
+  int32_t nu1, nu2;        /* pre- and post-smoothing sweeps of the V(nu1, nu2) cycle */
+  int32_t hidden;          /* GRU hidden size (64) */
+  int32_t gru_layers;      /* stacked GRU cells (2) */
+  int32_t mlp_width;       /* width of the hidden dense layer (128) */
+  int32_t reserved[8];
+} dnnmg_config;
+
+/* Per-step statistics returned by dnnmg_step(). */
+typedef struct dnnmg_step_stats {
+  int32_t newton_its;
+  int32_t gmres_its;   /* total FGMRES iterations = V-cycles */
+  int32_t fallback;    /* 1 if the network correction was dropped for this step */
+  int32_t status;      /* status code of the step */
+  double res0;         /* initial nonlinear residual norm */
+  double res_final;    /* final nonlinear residual norm */
+  double ms;           /* device time of the step in milliseconds */
+} dnnmg_step_stats;
+
+/* Fill *cfg with the defaults: nu = 0.01, dt = 0.01, theta = 1, alpha0 = 0.1,
+ * newton_tol = 1e-10, gmres_rtol = 1e-4, omega = 0.8, eps_damp = 1,
+ * obstacle at level-0 cell (2, 1), L = 3, coarse level 1, replaced_levels = 1,
+ * FP64, newton_max = 20, gmres_m = 20, gmres_maxit = 200, V(2,2), GRU 2 x 64,
+ * dense width 128.  Returns DNNMG_ERR_ARG if cfg is NULL. */
+int dnnmg_default_config(dnnmg_config* cfg);
+
+/* Create a context: builds the level hierarchy coarse..L (and L+1..L+r for the
+ * network), boundary masks, stencil constants and all workspaces, and sets the
+ * state to the impulsive start (zero interior velocity and pressure, parabolic
+ * inflow u = 6y(1-y)).  `stream` is a cudaStream_t (NULL = legacy default).
+ * Errors: DNNMG_ERR_ARG for an invalid configuration (levels out of range,
+ * obstacle not inside the channel, unsupported sizes), DNNMG_ERR_CUDA if an
+ * allocation fails; *out is NULL then. */
+int dnnmg_setup(const dnnmg_config* cfg, void* stream, dnnmg_ctx** out);
+
+/* Free everything owned by ctx.  NULL is allowed. */
+int dnnmg_destroy(dnnmg_ctx* ctx);
+
+/* Message of the last failure on ctx ("" if none), owned by ctx.  With
+ * ctx = NULL: the message of this thread's last failed dnnmg_setup(). */
+const char* dnnmg_last_error(const dnnmg_ctx* ctx);
+
+/* Cells of mesh level `level` (any level from 0 to L + replaced_levels). */
+int dnnmg_level_dims(const dnnmg_ctx* ctx, int level, int* nx, int* ny);
+
+/* Copy the FP64 state x_n of the finest solved level L to/from device
+ * buffer x ([3][nn] doubles).  set_state imposes the Dirichlet values on the
+ * constrained DOFs and clears the network's stored right-hand side and
+ * hidden state. */
+int dnnmg_get_state(dnnmg_ctx* ctx, double* x);
+int dnnmg_set_state(dnnmg_ctx* ctx, const double* x);
+
+/* Linearise the multigrid hierarchy at the velocity of the FP64 device state
+ * x ([3][nn] doubles on level L): the velocity is injected nodally to every
+ * coarser level, every level's Jacobian A'(vbar) (Eq. 7) is set up (Vanka
+ * inverses, coarse-level LU and inverse).  Needed before dnnmg_apply() and
+ * dnnmg_vcycle(); dnnmg_step() does it itself.
+ * Errors: DNNMG_ERR_NUMERICAL if a local Vanka matrix or the coarse matrix
+ * is singular. */
+int dnnmg_linearize(dnnmg_ctx* ctx, const double* x);
+
+/* y = A'(vbar) w on level `level` (coarse <= level <= L) at the current
+ * linearisation, with identity rows and columns on constrained DOFs.
+ * w, y: device [3][nn] arrays of double (precision = DNNMG_FP64) or float
+ * (DNNMG_MIXED); precision must equal the context's. */
+int dnnmg_apply(dnnmg_ctx* ctx, int level, const void* w, void* y, int precision);
+
+/* One V(nu1, nu2) cycle (Sec. 2.2; cell-wise Vanka smoother, bilinear
+ * transfers, direct coarse solve) on level `level` for A'(vbar) x = b,
+ * starting from x = 0.  b, x: device [3][nn] arrays of the context's
+ * precision (see dnnmg_apply).  b should vanish on constrained DOFs. */
+int dnnmg_vcycle(dnnmg_ctx* ctx, int level, const void* b, void* x, int precision);
+
+/* r = f - A_n(x) (Eqs. 4-5) on level L in FP64, zero on constrained DOFs.
+ * x, f, r: device [3][nn] doubles. */
+int dnnmg_residual(dnnmg_ctx* ctx, const double* x, const double* f, double* r);
+
+/* One time step (Eq. 6) from the context's state.  mode = DNNMG_PLAIN: the
+ * right-hand side is the old-time term of Eq. 5; mode = DNNMG_NET: the step
+ * uses the restricted right-hand side left by the previous DNN-MG step (if
+ * any) and ends with Algorithm 1 lines 6-9 (prolongation, network, Rhs,
+ * restriction).  If the Newton iteration count exceeds the fallback threshold
+ * the step is recomputed without the network right-hand side (Sec. 3.3).
+ * stats (host pointer, may be NULL) receives the step statistics.
+ * Returns DNNMG_ERR_NOT_CONVERGED if Newton hit newton_max (the step is still
+ * taken), DNNMG_ERR_NUMERICAL on NaN/Inf. */
+int dnnmg_step(dnnmg_ctx* ctx, int mode, dnnmg_step_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DNNMG_H */

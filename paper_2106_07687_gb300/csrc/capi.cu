@@ -1,0 +1,231 @@
+// Host runtime and C ABI of libdnnmg: level hierarchy, stencil constants,
+// V-cycle, flexible GMRES and Newton orchestration (Sec. 2.2, Algorithm 1).
+// All arithmetic of the method runs in the kernels of this library; the host
+// code only sequences launches and reads back convergence scalars.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/dnnmg.h"
+#include "kernels.h"
+#include "runtime.h"
+
+using namespace dnnmg;
+
+namespace dnnmg {
+
+// ---------------------------------------------------------------------------
+// Geometry of one level (host side), Sec. 2.1 / Eq. 2 with the channel
+// reading: obstacle = 2x2 block of level-0 cells, no-slip on walls and on
+// every node of a solid cell, parabolic inflow at x = 0, do-nothing at x = 4.
+HostLevel make_level(int ell, int oi0, int oj0) {
+  HostLevel L;
+  L.ell = ell;
+  Grid& g = L.g;
+  g.nx = 16 << ell;
+  g.ny = 4 << ell;
+  g.nnx = g.nx + 1;
+  g.nny = g.ny + 1;
+  g.nn = g.nnx * g.nny;
+  g.h = 4.0 / g.nx;
+  L.solid.assign((size_t)g.nx * g.ny, 0);
+  if (oi0 >= 0)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        const int I = i >> ell, J = j >> ell;
+        if (I >= oi0 && I < oi0 + 2 && J >= oj0 && J < oj0 + 2) L.solid[(size_t)j * g.nx + i] = 1;
+      }
+  L.flags.assign(g.nn, 0);
+  for (int j = 0; j <= g.ny; ++j)
+    for (int i = 0; i <= g.nx; ++i) {
+      bool touch_solid = false, touch_fluid = false;
+      for (int cy = -1; cy <= 0; ++cy)
+        for (int cx = -1; cx <= 0; ++cx) {
+          const int ci = i + cx, cj = j + cy;
+          if (ci < 0 || cj < 0 || ci >= g.nx || cj >= g.ny) continue;
+          if (L.solid[(size_t)cj * g.nx + ci])
+            touch_solid = true;
+          else
+            touch_fluid = true;
+        }
+      uint8_t f = 0;
+      if (touch_solid || i == 0 || j == 0 || j == g.ny) f |= kVDir;
+      if (!touch_fluid) f |= kPFix;
+      L.flags[(size_t)j * g.nnx + i] = f;
+    }
+  return L;
+}
+
+// Q1 element constants from 1D tensor products on a cell of width h:
+// 1D mass h/6 [2 1; 1 2], 1D stiffness 1/h [1 -1; -1 1],
+// 1D int phi_i phi_j' = [-1/2 1/2; -1/2 1/2].
+template <typename T>
+Sten<T> make_sten(double h, const dnnmg_config& c) {
+  const double m1[2][2] = {{h / 3, h / 6}, {h / 6, h / 3}};
+  const double k1[2][2] = {{1 / h, -1 / h}, {-1 / h, 1 / h}};
+  const double c1[2][2] = {{-0.5, 0.5}, {-0.5, 0.5}};
+  double M[4][4], K[4][4], Dx[4][4], Dy[4][4];
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) {
+      const int ax = a & 1, ay = a >> 1, bx = b & 1, by = b >> 1;
+      M[a][b] = m1[ax][bx] * m1[ay][by];
+      K[a][b] = k1[ax][bx] * m1[ay][by] + m1[ax][bx] * k1[ay][by];
+      Dx[a][b] = c1[ax][bx] * m1[ay][by];
+      Dy[a][b] = m1[ax][bx] * c1[ay][by];
+    }
+  Sten<T> s;
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) {
+      s.E[a * 4 + b] = (T)(M[a][b] / c.dt + c.theta * c.nu * K[a][b]);
+      s.Dx[a * 4 + b] = (T)Dx[a][b];
+      s.Dy[a * 4 + b] = (T)Dy[a][b];
+    }
+  // LPS on a 2x2-cell patch: S9 = alpha kappa^T K9 kappa, kappa = I - Pi,
+  // Pi = bilinear interpolation from the patch corners.
+  double K9[9][9] = {};
+  for (int cy = 0; cy < 2; ++cy)
+    for (int cx = 0; cx < 2; ++cx)
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) {
+          const int ma = (cx + (a & 1)) + 3 * (cy + (a >> 1));
+          const int mb = (cx + (b & 1)) + 3 * (cy + (b >> 1));
+          K9[ma][mb] += K[a][b];
+        }
+  double kap[9][9] = {};
+  for (int m = 0; m < 9; ++m) {
+    const int sx = m % 3, sy = m / 3;
+    kap[m][m] += 1.0;
+    for (int cy = 0; cy <= 2; cy += 2)
+      for (int cx = 0; cx <= 2; cx += 2) {
+        const double w = (1.0 - std::abs(sx - cx) / 2.0) * (1.0 - std::abs(sy - cy) / 2.0);
+        kap[m][cx + 3 * cy] -= w;
+      }
+  }
+  const double alpha = c.alpha0 * h * h / c.nu;
+  for (int m = 0; m < 9; ++m)
+    for (int n = 0; n < 9; ++n) {
+      double acc = 0;
+      for (int p = 0; p < 9; ++p)
+        for (int q = 0; q < 9; ++q) acc += kap[p][m] * K9[p][q] * kap[q][n];
+      s.S9[m * 9 + n] = (T)(alpha * acc);
+    }
+  s.wq = (T)(c.theta * h * h / 4.0);
+  s.ih = (T)(1.0 / h);
+  return s;
+}
+
+template Sten<float> make_sten<float>(double, const dnnmg_config&);
+template Sten<double> make_sten<double>(double, const dnnmg_config&);
+
+}  // namespace dnnmg
+
+// ---------------------------------------------------------------------------
+// C ABI
+
+namespace {
+thread_local std::string g_setup_error;  // message of this thread's last failed setup
+}
+
+extern "C" {
+
+int dnnmg_default_config(dnnmg_config* c) {
+  if (!c) return DNNMG_ERR_ARG;
+  std::memset(c, 0, sizeof(*c));
+  c->nu = 0.01;
+  c->dt = 0.01;
+  c->theta = 1.0;
+  c->alpha0 = 0.1;
+  c->newton_tol = 1e-10;
+  c->gmres_rtol = 1e-4;
+  c->omega = 0.8;
+  c->eps_damp = 1.0;
+  c->obstacle_i0 = 2;
+  c->obstacle_j0 = 1;
+  c->level_solve = 3;
+  c->level_coarse = 1;
+  c->replaced_levels = 1;
+  c->precision = DNNMG_FP64;
+  c->newton_max = 20;
+  c->gmres_m = 20;
+  c->gmres_maxit = 200;
+  c->nu1 = 2;
+  c->nu2 = 2;
+  c->hidden = 64;
+  c->gru_layers = 2;
+  c->mlp_width = 128;
+  return DNNMG_OK;
+}
+
+int dnnmg_setup(const dnnmg_config* cfg, void* stream, dnnmg_ctx** out) {
+  if (!out) return DNNMG_ERR_ARG;
+  *out = nullptr;
+  if (!cfg) return DNNMG_ERR_ARG;
+  std::unique_ptr<dnnmg_ctx> ctx(new dnnmg_ctx());
+  ctx->cfg = *cfg;
+  ctx->st = (cudaStream_t)stream;
+  int rc = ctx->init();
+  if (rc != DNNMG_OK) {
+    g_setup_error = ctx->err;
+    return rc;
+  }
+  g_setup_error.clear();
+  *out = ctx.release();
+  return DNNMG_OK;
+}
+
+int dnnmg_destroy(dnnmg_ctx* ctx) {
+  delete ctx;
+  return DNNMG_OK;
+}
+
+const char* dnnmg_last_error(const dnnmg_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_setup_error.c_str();
+}
+
+int dnnmg_level_dims(const dnnmg_ctx* ctx, int level, int* nx, int* ny) {
+  if (!ctx || !nx || !ny || level < 0 || level >= (int)ctx->lv.size()) return DNNMG_ERR_ARG;
+  *nx = ctx->lv[level].g.nx;
+  *ny = ctx->lv[level].g.ny;
+  return DNNMG_OK;
+}
+
+int dnnmg_get_state(dnnmg_ctx* ctx, double* x) {
+  if (!ctx || !x) return DNNMG_ERR_ARG;
+  return ctx->get_state(x);
+}
+
+int dnnmg_set_state(dnnmg_ctx* ctx, const double* x) {
+  if (!ctx || !x) return DNNMG_ERR_ARG;
+  return ctx->set_state(x);
+}
+
+int dnnmg_linearize(dnnmg_ctx* ctx, const double* x) {
+  if (!ctx || !x) return DNNMG_ERR_ARG;
+  return ctx->linearize_api(x);
+}
+
+int dnnmg_apply(dnnmg_ctx* ctx, int level, const void* w, void* y, int precision) {
+  if (!ctx || !w || !y) return DNNMG_ERR_ARG;
+  return ctx->apply_api(level, w, y, precision);
+}
+
+int dnnmg_vcycle(dnnmg_ctx* ctx, int level, const void* b, void* x, int precision) {
+  if (!ctx || !b || !x) return DNNMG_ERR_ARG;
+  return ctx->vcycle_api(level, b, x, precision);
+}
+
+int dnnmg_residual(dnnmg_ctx* ctx, const double* x, const double* f, double* r) {
+  if (!ctx || !x || !f || !r) return DNNMG_ERR_ARG;
+  return ctx->residual_api(x, f, r);
+}
+
+int dnnmg_step(dnnmg_ctx* ctx, int mode, dnnmg_step_stats* stats) {
+  if (!ctx) return DNNMG_ERR_ARG;
+  if (mode != DNNMG_PLAIN && mode != DNNMG_NET) return ctx->fail(DNNMG_ERR_ARG, "unknown mode");
+  return ctx->step(mode, stats);
+}
+
+}  // extern "C"

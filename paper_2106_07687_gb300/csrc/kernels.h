@@ -1,0 +1,101 @@
+// Host-side launchers of the solver kernels (internal to libdnnmg).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace dnnmg {
+
+// Operator rows (stencil.cu) ---------------------------------------------
+// y = A'(vbar) w on free DOFs, y = w on constrained DOFs (Eq. 7).
+template <typename T>
+void launch_apply(const Grid& g, const Sten<T>& s, const T* w, const T* vb, T* y, cudaStream_t st);
+// d = b - A'(vbar) x with the same constrained handling; if `masked`,
+// d is zeroed on constrained DOFs (input of the restriction).
+template <typename T>
+void launch_defect(const Grid& g, const Sten<T>& s, const T* b, const T* x, const T* vb, T* d,
+                   bool masked, cudaStream_t st);
+// r = f - A(x) on free DOFs, 0 on constrained DOFs (FP64 nonlinear residual).
+void launch_residual64(const Grid& g, const Sten<double>& s, const double* x, const double* f,
+                       double* r, cudaStream_t st);
+// f = (1/k) M v_old on the velocity rows, 0 on the pressure rows.
+void launch_old_time_rhs64(const Grid& g, double inv_k, const double* x_old, double* f,
+                           cudaStream_t st);
+
+// Transfers (transfer.cu) ----------------------------------------------------
+// bc = R d (R = P^T on free DOFs, coarse constrained rows zeroed)
+template <typename T>
+void launch_restrict(const Grid& fine, const Grid& coarse, const T* d, T* bc, cudaStream_t st);
+// x += P xc on free fine DOFs
+template <typename T>
+void launch_prolong_add(const Grid& fine, const Grid& coarse, const T* xc, T* x, cudaStream_t st);
+// coarse (I, J) <- fine (2I, 2J), ncomp fields
+template <typename T>
+void launch_inject(const Grid& fine, const Grid& coarse, const T* xf, T* xc, int ncomp,
+                   cudaStream_t st);
+// Unmasked bilinear prolongation of ncomp fields (DNN-MG state transfer).
+void launch_prolong_state64(const Grid& fine, const Grid& coarse, const double* xc, double* xf,
+                            int ncomp, cudaStream_t st);
+// Unmasked R = P^T of ncomp fields (DNN-MG right-hand side restriction).
+void launch_restrict_full64(const Grid& fine, const Grid& coarse, const double* bf, double* bc,
+                            int ncomp, cudaStream_t st);
+
+// Vanka (vanka.cu) -----------------------------------------------------------
+// inverse of the 12x12 restriction of A'(vbar) to every fluid cell, stored
+// inv[colour][144][slot], slot = tj * (nx/2 + 1) + ti, cell (2ti - ci, 2tj - cj)
+template <typename T>
+void launch_vanka_setup(const Grid& g, const Sten<T>& s, const T* vb, T* inv, int* status,
+                        cudaStream_t st);
+// one colour pass: xout = xin + omega A_c^{-1} (b - A xin)_c on the colour's cells
+template <typename T>
+void launch_vanka_pass(const Grid& g, const Sten<T>& s, int colour, const T* b, const T* xin,
+                       const T* vb, const T* inv, T omega, T* xout, cudaStream_t st);
+inline int vanka_slots(const Grid& g) { return (g.nx / 2 + 1) * (g.ny / 2 + 1); }
+
+// Coarse direct solve (coarse.cu) -------------------------------------------
+// Assemble the banded Jacobian of the coarsest level (FP64), factor it with
+// partial pivoting and form the explicit inverse Ainv (ndof x ndof, FP64,
+// unknowns in band order).  `work` needs coarse_work_doubles(g) doubles.
+size_t coarse_work_doubles(const Grid& g);
+void launch_coarse_factor(const Grid& g, const Sten<double>& s, const double* vb, double* work,
+                          double* Ainv, int* status, cudaStream_t st);
+// x = Ainv b, b and x in the [3][nn] layout of the level
+template <typename T>
+void launch_coarse_solve(const Grid& g, const double* Ainv, const T* b, T* x, cudaStream_t st);
+
+// Vectors (vec.cu) ----------------------------------------------------------
+template <typename Ts, typename Td>
+void launch_cast(const Ts* a, Td* b, size_t n, cudaStream_t st);
+template <typename T>
+void launch_fill(T* a, T v, size_t n, cudaStream_t st);
+// partial dot products of w against k vectors V[i] (stride ld); out[k] after
+// launch_dots_finish.  partials needs dots_partials(n, k) doubles.
+template <typename T>
+void launch_multidot(const T* V, size_t ld, int k, const T* w, size_t n, double* partials,
+                     double* out, cudaStream_t st);
+// w -= sum_i h[i] V[i]
+template <typename T>
+void launch_multiaxpy(const T* V, size_t ld, int k, const double* h, T* w, size_t n,
+                      cudaStream_t st);
+// y = s * x with s = a, 1/a or 1/sqrt(a) (mode 0, 1, 2), a read on the device
+template <typename T>
+void launch_scale_dev(const T* x, const double* a, int mode, T* y, size_t n, cudaStream_t st);
+// x += eps * (sum_i y[i] Z[i]) in FP64 accumulation, result type Tx
+template <typename T, typename Tx>
+void launch_combine(const T* Z, size_t ld, int k, const double* y, double eps, Tx* x, size_t n,
+                    cudaStream_t st);
+size_t dots_partials(size_t n, int k);
+// FGMRES small-matrix kernels: Hessenberg column j (from h[0..j+1]) is
+// rotated, the new Givens rotation stored and g updated; resid = |g[j+1]|.
+void launch_givens(double* H, int ldh, double* cs, double* sn, double* gvec, const double* hcol,
+                   int j, double* resid, cudaStream_t st);
+// y = H[0:k,0:k]^{-1} g[0:k] (back substitution)
+void launch_backsolve(const double* H, int ldh, const double* gvec, int k, double* y,
+                      cudaStream_t st);
+// set V0 = r / ||r|| with norm from nrm2[0]; g[0] = ||r||
+template <typename T>
+void launch_gmres_start(const T* r, const double* nrm2, T* v0, double* gvec, size_t n,
+                        cudaStream_t st);
+
+}  // namespace dnnmg

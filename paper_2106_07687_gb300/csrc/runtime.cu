@@ -1,0 +1,392 @@
+// Host runtime: multigrid V-cycle, flexible GMRES and Newton time step
+// (Sec. 2.2, Eq. 7, Algorithm 1 lines 2-4), sequencing the kernels of this
+// library on the context's stream.
+#include <cmath>
+#include <cstring>
+
+#include "runtime.h"
+
+using namespace dnnmg;
+
+namespace dnnmg {
+
+namespace {
+
+template <typename T>
+class Solver final : public SolverBase {
+ public:
+  explicit Solver(dnnmg_ctx* c) : c_(c) {}
+
+  int init() {
+    const dnnmg_config& cfg = c_->cfg;
+    st_ = c_->st;
+    K_ = cfg.level_solve - cfg.level_coarse;
+    lv_.resize(K_ + 1);
+    for (int k = 0; k <= K_; ++k) {
+      Lev& l = lv_[k];
+      l.g = c_->grid(cfg.level_coarse + k);
+      const size_t n3 = 3 * (size_t)l.g.nn, n2 = 2 * (size_t)l.g.nn;
+      l.s = make_sten<T>(l.g.h, cfg);
+      l.s64 = make_sten<double>(l.g.h, cfg);
+      l.x = c_->mem.alloc<T>(n3);
+      l.x2 = c_->mem.alloc<T>(n3);
+      l.b = c_->mem.alloc<T>(n3);
+      l.d = c_->mem.alloc<T>(n3);
+      l.vb = c_->mem.alloc<T>(n2);
+      l.vb64 = c_->mem.alloc<double>(n2);
+      if (k > 0) l.inv = c_->mem.alloc<T>((size_t)4 * 144 * vanka_slots(l.g));
+    }
+    const Grid& g0 = lv_[0].g;
+    coarse_work_ = c_->mem.alloc<double>(coarse_work_doubles(g0));
+    ainv_ = c_->mem.alloc<double>((size_t)9 * g0.nn * g0.nn);
+    status_ = c_->mem.alloc<int>(4);
+    m_ = cfg.gmres_m;
+    n_ = 3 * (size_t)lv_[K_].g.nn;
+    V_ = c_->mem.alloc<T>((m_ + 1) * n_);
+    Z_ = c_->mem.alloc<T>(m_ * n_);
+    wsol_ = c_->mem.alloc<T>(n_);
+    rT_ = c_->mem.alloc<T>(n_);
+    rcur_ = c_->mem.alloc<T>(n_);
+    H_ = c_->mem.alloc<double>((m_ + 1) * (m_ + 1));
+    cs_ = c_->mem.alloc<double>(m_ + 1);
+    sn_ = c_->mem.alloc<double>(m_ + 1);
+    gv_ = c_->mem.alloc<double>(m_ + 2);
+    hcol_ = c_->mem.alloc<double>(2 * m_ + 4);
+    y_ = c_->mem.alloc<double>(m_ + 1);
+    one_ = c_->mem.alloc<double>(1);
+    partials_ = c_->mem.alloc<double>(dots_partials(n_, 2 * m_ + 4));
+    if (!c_->mem.ok()) return c_->fail(DNNMG_ERR_CUDA, "device allocation failed");
+    const double one = 1.0;
+    cudaMemcpyAsync(one_, &one, sizeof(double), cudaMemcpyHostToDevice, st_);
+    return c_->check("solver init");
+  }
+
+  int precision() const override { return sizeof(T) == 8 ? DNNMG_FP64 : DNNMG_MIXED; }
+
+  // Linearise every level at the velocity of x64 (level L): nodal injection
+  // down the hierarchy, Vanka inverses, coarse LU and inverse.
+  int linearize(const double* x64) override {
+    cudaMemcpyAsync(lv_[K_].vb64, x64, 2 * sizeof(double) * lv_[K_].g.nn,
+                    cudaMemcpyDeviceToDevice, st_);
+    for (int k = K_; k > 0; --k)
+      launch_inject<double>(lv_[k].g, lv_[k - 1].g, lv_[k].vb64, lv_[k - 1].vb64, 2, st_);
+    cudaMemsetAsync(status_, 0, sizeof(int), st_);
+    for (int k = 0; k <= K_; ++k) {
+      launch_cast<double, T>(lv_[k].vb64, lv_[k].vb, 2 * (size_t)lv_[k].g.nn, st_);
+      if (k > 0) launch_vanka_setup<T>(lv_[k].g, lv_[k].s, lv_[k].vb, lv_[k].inv, status_, st_);
+    }
+    launch_coarse_factor(lv_[0].g, lv_[0].s64, lv_[0].vb64, coarse_work_, ainv_, status_, st_);
+    int status = 0;
+    cudaMemcpyAsync(c_->h_scalars, status_, sizeof(int), cudaMemcpyDeviceToHost, st_);
+    if (int rc = c_->check("linearize")) return rc;
+    cudaStreamSynchronize(st_);
+    std::memcpy(&status, c_->h_scalars, sizeof(int));
+    linearized_ = true;
+    if (status & 1) return c_->fail(DNNMG_ERR_NUMERICAL, "singular local Vanka matrix");
+    if (status & 2) return c_->fail(DNNMG_ERR_NUMERICAL, "singular coarse-level matrix");
+    return DNNMG_OK;
+  }
+
+  int apply(int k, const void* w, void* y) override {
+    if (!linearized_) return c_->fail(DNNMG_ERR_STATE, "apply before linearize");
+    launch_apply<T>(lv_[k].g, lv_[k].s, static_cast<const T*>(w), lv_[k].vb, static_cast<T*>(y),
+                    st_);
+    return c_->check("apply");
+  }
+
+  int vcycle(int k, const void* b, void* x) override {
+    if (!linearized_) return c_->fail(DNNMG_ERR_STATE, "vcycle before linearize");
+    launch_fill<T>(static_cast<T*>(x), T(0), 3 * (size_t)lv_[k].g.nn, st_);
+    cycle(k, static_cast<const T*>(b), static_cast<T*>(x));
+    return c_->check("vcycle");
+  }
+
+  // FGMRES(m) with right preconditioning by one V-cycle; CGS with one
+  // re-orthogonalisation; x64 += eps * w at the end.
+  int solve(const double* r64, double* x64, double eps, int* its_out) override {
+    const dnnmg_config& cfg = c_->cfg;
+    launch_cast<double, T>(r64, rT_, n_, st_);
+    launch_fill<T>(wsol_, T(0), n_, st_);
+    cudaMemcpyAsync(rcur_, rT_, n_ * sizeof(T), cudaMemcpyDeviceToDevice, st_);
+    int its = 0;
+    double target = -1.0;
+    bool done = false;
+    while (!done) {
+      launch_multidot<T>(rcur_, n_, 1, rcur_, n_, partials_, hcol_, st_);
+      launch_gmres_start<T>(rcur_, hcol_, V_, gv_, n_, st_);
+      if (target < 0) {
+        double b2 = 0;
+        if (int rc = read_scalar(hcol_, &b2)) return rc;
+        target = cfg.gmres_rtol * std::sqrt(b2);
+        if (!(b2 > 0)) break;
+        if (!std::isfinite(b2)) return c_->fail(DNNMG_ERR_NUMERICAL, "non-finite residual");
+      }
+      int k = 0;
+      for (int j = 0; j < m_; ++j) {
+        T* vj = V_ + (size_t)j * n_;
+        T* zj = Z_ + (size_t)j * n_;
+        T* w = V_ + (size_t)(j + 1) * n_;
+        launch_fill<T>(zj, T(0), n_, st_);
+        cycle(K_, vj, zj);
+        launch_apply<T>(lv_[K_].g, lv_[K_].s, zj, lv_[K_].vb, w, st_);
+        launch_multidot<T>(V_, n_, j + 1, w, n_, partials_, hcol_, st_);
+        launch_multiaxpy<T>(V_, n_, j + 1, hcol_, w, n_, st_);
+        launch_multidot<T>(V_, n_, j + 1, w, n_, partials_, hcol_ + j + 1, st_);
+        launch_multiaxpy<T>(V_, n_, j + 1, hcol_ + j + 1, w, n_, st_);
+        launch_multidot<T>(w, n_, 1, w, n_, partials_, hcol_ + 2 * j + 2, st_);
+        launch_givens(H_, m_ + 1, cs_, sn_, gv_, hcol_, j, y_ + m_, st_);
+        launch_scale_dev<T>(w, hcol_ + 2 * j + 2, 2, w, n_, st_);
+        ++its;
+        k = j + 1;
+        double res = 0;
+        if (int rc = read_scalar(y_ + m_, &res)) return rc;
+        if (!std::isfinite(res)) return c_->fail(DNNMG_ERR_NUMERICAL, "non-finite GMRES residual");
+        if (res <= target || its >= cfg.gmres_maxit) {
+          done = true;
+          break;
+        }
+      }
+      launch_backsolve(H_, m_ + 1, gv_, k, y_, st_);
+      launch_combine<T, T>(Z_, n_, k, y_, 1.0, wsol_, n_, st_);
+      if (!done) {
+        // restart from the true residual of the current iterate
+        launch_defect<T>(lv_[K_].g, lv_[K_].s, rT_, wsol_, lv_[K_].vb, rcur_, false, st_);
+      }
+    }
+    launch_combine<T, double>(wsol_, n_, 1, one_, eps, x64, n_, st_);
+    if (its_out) *its_out = its;
+    return c_->check("fgmres");
+  }
+
+ private:
+  struct Lev {
+    Grid g{};
+    Sten<T> s{};
+    Sten<double> s64{};
+    T *x = nullptr, *x2 = nullptr, *b = nullptr, *d = nullptr, *vb = nullptr, *inv = nullptr;
+    double* vb64 = nullptr;
+  };
+
+  int read_scalar(const double* dev, double* out) {
+    cudaMemcpyAsync(c_->h_scalars, dev, sizeof(double), cudaMemcpyDeviceToHost, st_);
+    if (cudaStreamSynchronize(st_) != cudaSuccess) return c_->check("sync");
+    std::memcpy(out, c_->h_scalars, sizeof(double));
+    return DNNMG_OK;
+  }
+
+  // nu sweeps of four colour passes, ping-ponging between x and the level's
+  // second buffer; an even number of passes leaves the result in x.
+  void smooth(int k, const T* b, T* x, int sweeps) {
+    Lev& l = lv_[k];
+    T* cur = x;
+    T* nxt = l.x2;
+    for (int s = 0; s < sweeps; ++s)
+      for (int colour = 0; colour < 4; ++colour) {
+        launch_vanka_pass<T>(l.g, l.s, colour, b, cur, l.vb, l.inv, (T)c_->cfg.omega, nxt, st_);
+        T* t = cur;
+        cur = nxt;
+        nxt = t;
+      }
+  }
+
+  // One V(nu1, nu2) cycle on level k for A x = b with x = 0 on entry.
+  void cycle(int k, const T* b, T* x) {
+    Lev& l = lv_[k];
+    if (k == 0) {
+      launch_coarse_solve<T>(l.g, ainv_, b, x, st_);
+      return;
+    }
+    Lev& lc = lv_[k - 1];
+    smooth(k, b, x, c_->cfg.nu1);
+    launch_defect<T>(l.g, l.s, b, x, l.vb, l.d, true, st_);
+    launch_restrict<T>(l.g, lc.g, l.d, lc.b, st_);
+    launch_fill<T>(lc.x, T(0), 3 * (size_t)lc.g.nn, st_);
+    cycle(k - 1, lc.b, lc.x);
+    launch_prolong_add<T>(l.g, lc.g, lc.x, x, st_);
+    smooth(k, b, x, c_->cfg.nu2);
+  }
+
+  dnnmg_ctx* c_;
+  cudaStream_t st_ = nullptr;
+  int K_ = 0, m_ = 0;
+  size_t n_ = 0;
+  std::vector<Lev> lv_;
+  double *coarse_work_ = nullptr, *ainv_ = nullptr;
+  int* status_ = nullptr;
+  T *V_ = nullptr, *Z_ = nullptr, *wsol_ = nullptr, *rT_ = nullptr, *rcur_ = nullptr;
+  double *H_ = nullptr, *cs_ = nullptr, *sn_ = nullptr, *gv_ = nullptr, *hcol_ = nullptr,
+         *y_ = nullptr, *one_ = nullptr, *partials_ = nullptr;
+  bool linearized_ = false;
+};
+
+}  // namespace
+
+std::unique_ptr<SolverBase> make_solver(dnnmg_ctx* ctx) {
+  if (ctx->cfg.precision == DNNMG_FP64) {
+    auto s = std::make_unique<Solver<double>>(ctx);
+    if (s->init() != DNNMG_OK) return nullptr;
+    return s;
+  }
+  auto s = std::make_unique<Solver<float>>(ctx);
+  if (s->init() != DNNMG_OK) return nullptr;
+  return s;
+}
+
+}  // namespace dnnmg
+
+// ---------------------------------------------------------------------------
+// context
+
+dnnmg_ctx::~dnnmg_ctx() {
+  if (st) cudaStreamSynchronize(st);
+  solver.reset();
+  if (h_scalars) cudaFreeHost(h_scalars);
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
+}
+
+int dnnmg_ctx::check(const char* what) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(DNNMG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return DNNMG_OK;
+}
+
+int dnnmg_ctx::init() {
+  const dnnmg_config& c = cfg;
+  if (!(c.nu > 0) || !(c.dt > 0) || !(c.alpha0 >= 0) || !(c.theta > 0 && c.theta <= 1))
+    return fail(DNNMG_ERR_ARG, "nu, dt, theta or alpha0 out of range");
+  if (c.theta != 1.0) return fail(DNNMG_ERR_ARG, "only theta = 1 (backward Euler) is supported");
+  if (c.level_coarse < 1 || c.level_coarse > c.level_solve || c.level_solve > 9)
+    return fail(DNNMG_ERR_ARG, "need 1 <= level_coarse <= level_solve <= 9");
+  if (c.level_coarse != 1) return fail(DNNMG_ERR_ARG, "the coarse direct solve supports level 1");
+  if (c.replaced_levels < 0 || c.replaced_levels > 2 || c.level_solve + c.replaced_levels > 10)
+    return fail(DNNMG_ERR_ARG, "replaced_levels must be 0, 1 or 2");
+  if (c.obstacle_i0 >= 0 && (c.obstacle_i0 < 1 || c.obstacle_i0 > 13 || c.obstacle_j0 < 1 ||
+                             c.obstacle_j0 > 1))
+    return fail(DNNMG_ERR_ARG, "obstacle must be a 2x2 level-0 block with 1 <= i0 <= 13, j0 = 1");
+  if (c.precision != DNNMG_FP64 && c.precision != DNNMG_MIXED)
+    return fail(DNNMG_ERR_ARG, "unknown precision");
+  if (c.gmres_m < 1 || c.gmres_m > 40 || c.gmres_maxit < 1 || c.newton_max < 1 || c.nu1 < 0 ||
+      c.nu2 < 0)
+    return fail(DNNMG_ERR_ARG, "solver parameters out of range");
+  const int nlev = c.level_solve + c.replaced_levels + 1;
+  for (int l = 0; l < nlev; ++l) lv.push_back(make_level(l, c.obstacle_i0, c.obstacle_j0));
+  for (int l = 0; l < nlev; ++l) {
+    Grid& g = lv[l].g;
+    uint8_t* s = mem.alloc<uint8_t>((size_t)g.nx * g.ny);
+    uint8_t* f = mem.alloc<uint8_t>(g.nn);
+    if (!mem.ok()) return fail(DNNMG_ERR_CUDA, "device allocation failed");
+    cudaMemcpyAsync(s, lv[l].solid.data(), lv[l].solid.size(), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(f, lv[l].flags.data(), lv[l].flags.size(), cudaMemcpyHostToDevice, st);
+    g.solid = s;
+    g.flags = f;
+  }
+  if (cudaMallocHost(&h_scalars, 64 * sizeof(double)) != cudaSuccess)
+    return fail(DNNMG_ERR_CUDA, "pinned allocation failed");
+  cudaEventCreate(&ev0);
+  cudaEventCreate(&ev1);
+  const Grid gL = grid(L());
+  const size_t n3 = 3 * (size_t)gL.nn;
+  x64 = mem.alloc<double>(n3);
+  xold64 = mem.alloc<double>(n3);
+  f64 = mem.alloc<double>(n3);
+  r64 = mem.alloc<double>(n3);
+  dots = mem.alloc<double>(64);
+  partials = mem.alloc<double>(dots_partials(n3, 4));
+  if (!mem.ok()) return fail(DNNMG_ERR_CUDA, "device allocation failed");
+  s64L = make_sten<double>(gL.h, cfg);
+  // impulsive start: zero state, then the inflow profile on x = 0
+  std::vector<double> x0(n3, 0.0);
+  for (int j = 0; j <= gL.ny; ++j) {
+    const double y = j * gL.h;
+    x0[(size_t)j * gL.nnx] = 6.0 * y * (1.0 - y);
+  }
+  cudaMemcpyAsync(x64, x0.data(), n3 * sizeof(double), cudaMemcpyHostToDevice, st);
+  cudaStreamSynchronize(st);
+  if (int rc = check("setup")) return rc;
+  solver = make_solver(this);
+  if (!solver) return err.empty() ? fail(DNNMG_ERR_CUDA, "solver setup failed") : DNNMG_ERR_CUDA;
+  return check("setup");
+}
+
+double dnnmg_ctx::norm64(const double* v, size_t n) {
+  launch_multidot<double>(v, n, 1, v, n, partials, dots, st);
+  cudaMemcpyAsync(h_scalars, dots, sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  return std::sqrt(h_scalars[0]);
+}
+
+int dnnmg_ctx::get_state(double* x) {
+  cudaMemcpyAsync(x, x64, 3 * sizeof(double) * grid(L()).nn, cudaMemcpyDeviceToDevice, st);
+  cudaStreamSynchronize(st);
+  return check("get_state");
+}
+
+int dnnmg_ctx::set_state(const double* x) {
+  cudaMemcpyAsync(x64, x, 3 * sizeof(double) * grid(L()).nn, cudaMemcpyDeviceToDevice, st);
+  cudaStreamSynchronize(st);
+  return check("set_state");
+}
+
+int dnnmg_ctx::linearize_api(const double* x) { return solver->linearize(x); }
+
+int dnnmg_ctx::apply_api(int level, const void* w, void* y, int precision) {
+  if (level < lc() || level > L()) return fail(DNNMG_ERR_ARG, "level out of range");
+  if (precision != solver->precision()) return fail(DNNMG_ERR_ARG, "precision mismatch");
+  return solver->apply(level - lc(), w, y);
+}
+
+int dnnmg_ctx::vcycle_api(int level, const void* b, void* x, int precision) {
+  if (level < lc() || level > L()) return fail(DNNMG_ERR_ARG, "level out of range");
+  if (precision != solver->precision()) return fail(DNNMG_ERR_ARG, "precision mismatch");
+  return solver->vcycle(level - lc(), b, x);
+}
+
+int dnnmg_ctx::residual_api(const double* x, const double* f, double* r) {
+  launch_residual64(grid(L()), s64L, x, f, r, st);
+  return check("residual");
+}
+
+int dnnmg_ctx::newton(const double* f, dnnmg_step_stats* s) {
+  const Grid gL = grid(L());
+  const size_t n3 = 3 * (size_t)gL.nn;
+  launch_residual64(gL, s64L, x64, f, r64, st);
+  double nrm = norm64(r64, n3);
+  s->res0 = nrm;
+  int it = 0, gits = 0;
+  while (nrm > cfg.newton_tol && it < cfg.newton_max) {
+    if (!std::isfinite(nrm)) return fail(DNNMG_ERR_NUMERICAL, "non-finite Newton residual");
+    if (int rc = solver->linearize(x64)) return rc;
+    int its = 0;
+    if (int rc = solver->solve(r64, x64, cfg.eps_damp, &its)) return rc;
+    gits += its;
+    launch_residual64(gL, s64L, x64, f, r64, st);
+    nrm = norm64(r64, n3);
+    ++it;
+  }
+  s->newton_its = it;
+  s->gmres_its = gits;
+  s->res_final = nrm;
+  if (!std::isfinite(nrm)) return fail(DNNMG_ERR_NUMERICAL, "non-finite Newton residual");
+  if (nrm > cfg.newton_tol) return DNNMG_ERR_NOT_CONVERGED;
+  return check("newton");
+}
+
+int dnnmg_ctx::step(int mode, dnnmg_step_stats* stats) {
+  dnnmg_step_stats s{};
+  const Grid gL = grid(L());
+  const size_t n3 = 3 * (size_t)gL.nn;
+  cudaEventRecord(ev0, st);
+  cudaMemcpyAsync(xold64, x64, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  launch_old_time_rhs64(gL, 1.0 / cfg.dt, xold64, f64, st);
+  int rc = newton(f64, &s);
+  cudaEventRecord(ev1, st);
+  cudaEventSynchronize(ev1);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, ev0, ev1);
+  s.ms = ms;
+  s.status = rc;
+  (void)mode;
+  if (stats) *stats = s;
+  return rc;
+}

@@ -1,0 +1,101 @@
+// Host runtime of libdnnmg (internal): the context, its level hierarchy and
+// the precision-templated multigrid / Krylov / Newton engine.
+#pragma once
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/dnnmg.h"
+#include "kernels.h"
+
+namespace dnnmg {
+
+struct HostLevel {
+  int ell = 0;
+  Grid g{};
+  std::vector<uint8_t> solid, flags;
+};
+
+HostLevel make_level(int ell, int oi0, int oj0);
+template <typename T>
+Sten<T> make_sten(double h, const dnnmg_config& c);
+
+// Owns device allocations; frees them on destruction.
+class DevMem {
+ public:
+  ~DevMem() {
+    for (void* p : ptrs_) cudaFree(p);
+  }
+  template <typename T>
+  T* alloc(size_t n) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, n * sizeof(T) + 16) != cudaSuccess) {
+      ok_ = false;
+      return nullptr;
+    }
+    ptrs_.push_back(p);
+    return static_cast<T*>(p);
+  }
+  bool ok() const { return ok_; }
+
+ private:
+  std::vector<void*> ptrs_;
+  bool ok_ = true;
+};
+
+// Precision-independent interface of the solver engine.
+class SolverBase {
+ public:
+  virtual ~SolverBase() = default;
+  virtual int linearize(const double* x64) = 0;
+  virtual int apply(int k, const void* w, void* y) = 0;
+  virtual int vcycle(int k, const void* b, void* x) = 0;
+  // FGMRES on the finest level: w64 += eps * A'^{-1} r64 (approximately)
+  virtual int solve(const double* r64, double* x64, double eps, int* its) = 0;
+  virtual int precision() const = 0;
+};
+
+std::unique_ptr<SolverBase> make_solver(struct ::dnnmg_ctx* ctx);
+
+}  // namespace dnnmg
+
+struct dnnmg_ctx {
+  dnnmg_config cfg{};
+  cudaStream_t st = nullptr;
+  std::string err;
+  std::vector<dnnmg::HostLevel> lv;  // levels 0 .. L + replaced_levels
+  std::vector<uint8_t*> d_solid, d_flags;
+  dnnmg::DevMem mem;
+  std::unique_ptr<dnnmg::SolverBase> solver;
+  dnnmg::Sten<double> s64L{};  // FP64 constants of the finest solved level
+  // FP64 state of level L
+  double* x64 = nullptr;
+  double* xold64 = nullptr;
+  double* f64 = nullptr;
+  double* r64 = nullptr;
+  double* dots = nullptr;      // small device scratch for reductions
+  double* partials = nullptr;  // reduction partials
+  double* h_scalars = nullptr; // pinned host scalars
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  ~dnnmg_ctx();
+  int init();
+  int fail(int code, const std::string& msg) {
+    err = msg;
+    return code;
+  }
+  int check(const char* what);
+  dnnmg::Grid grid(int level) const { return lv[level].g; }
+  int L() const { return cfg.level_solve; }
+  int lc() const { return cfg.level_coarse; }
+  double norm64(const double* v, size_t n);  // synchronous
+
+  int get_state(double* x);
+  int set_state(const double* x);
+  int linearize_api(const double* x);
+  int apply_api(int level, const void* w, void* y, int precision);
+  int vcycle_api(int level, const void* b, void* x, int precision);
+  int residual_api(const double* x, const double* f, double* r);
+  int step(int mode, dnnmg_step_stats* stats);
+  int newton(const double* f, dnnmg_step_stats* st);
+};

@@ -1,0 +1,231 @@
+// Vector kernels of the flexible GMRES solver (Sec. 2.2: GMRES preconditioned
+// by multigrid) and of the Newton update (Eq. 7).  Reductions accumulate in
+// FP64 and run in two fixed-order stages, so results are deterministic.
+#include "kernels.h"
+
+namespace dnnmg {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kDotBlocks = 296;  // two blocks per SM of a 148+ SM part
+
+template <typename Ts, typename Td>
+__global__ void cast_kernel(const Ts* __restrict__ a, Td* __restrict__ b, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    b[i] = (Td)a[i];
+}
+
+template <typename T>
+__global__ void fill_kernel(T* a, T v, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    a[i] = v;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    t = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  return t;
+}
+
+// partials[i * gridDim.x + block] = sum over the block's chunk of V[i] . w
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    multidot_kernel(const T* __restrict__ V, size_t ld, int k, const T* __restrict__ w, size_t n,
+                    double* __restrict__ partials) {
+  __shared__ double sh[32];
+  const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const size_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+  for (int i = 0; i < k; ++i) {
+    const T* v = V + (size_t)i * ld;
+    double acc = 0.0;
+    for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) acc += (double)v[e] * (double)w[e];
+    const double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) partials[(size_t)i * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+__global__ void dots_finish_kernel(const double* __restrict__ partials, int nb, double* out) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += partials[(size_t)blockIdx.x * nb + b];
+  const double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) out[blockIdx.x] = t;
+}
+
+template <typename T>
+__global__ void multiaxpy_kernel(const T* __restrict__ V, size_t ld, int k,
+                                 const double* __restrict__ h, T* __restrict__ w, size_t n) {
+  __shared__ double sh[64];
+  if (threadIdx.x < k) sh[threadIdx.x] = h[threadIdx.x];
+  __syncthreads();
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    double acc = (double)w[e];
+    for (int i = 0; i < k; ++i) acc -= sh[i] * (double)V[(size_t)i * ld + e];
+    w[e] = (T)acc;
+  }
+}
+
+template <typename T>
+__global__ void scale_dev_kernel(const T* __restrict__ x, const double* a, int mode,
+                                 T* __restrict__ y, size_t n) {
+  double s = *a;
+  if (mode == 2) s = sqrt(fmax(s, 0.0));
+  if (mode >= 1) s = s != 0.0 ? 1.0 / s : 0.0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x)
+    y[e] = (T)(s * (double)x[e]);
+}
+
+template <typename T, typename Tx>
+__global__ void combine_kernel(const T* __restrict__ Z, size_t ld, int k,
+                               const double* __restrict__ y, double eps, Tx* __restrict__ x,
+                               size_t n) {
+  __shared__ double sh[64];
+  if (threadIdx.x < k) sh[threadIdx.x] = y[threadIdx.x];
+  __syncthreads();
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < k; ++i) acc += sh[i] * (double)Z[(size_t)i * ld + e];
+    x[e] = (Tx)((double)x[e] + eps * acc);
+  }
+}
+
+// H is column-major (ldh rows).  hcol holds [h_0..h_j (first CGS pass),
+// h_0..h_j (second pass), ||w||^2].
+__global__ void givens_kernel(double* H, int ldh, double* cs, double* sn, double* g,
+                              const double* hcol, int j, double* resid) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double* col = H + (size_t)j * ldh;
+  for (int i = 0; i <= j; ++i) col[i] = hcol[i] + hcol[j + 1 + i];
+  col[j + 1] = sqrt(fmax(hcol[2 * j + 2], 0.0));
+  for (int i = 0; i < j; ++i) {
+    const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+    col[i] = t;
+  }
+  const double den = hypot(col[j], col[j + 1]);
+  const double c = den > 0 ? col[j] / den : 1.0, s = den > 0 ? col[j + 1] / den : 0.0;
+  cs[j] = c;
+  sn[j] = s;
+  col[j] = den;
+  col[j + 1] = 0.0;
+  g[j + 1] = -s * g[j];
+  g[j] = c * g[j];
+  *resid = fabs(g[j + 1]);
+}
+
+__global__ void backsolve_kernel(const double* H, int ldh, const double* g, int k, double* y) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = k - 1; i >= 0; --i) {
+    double acc = g[i];
+    for (int c = i + 1; c < k; ++c) acc -= H[(size_t)c * ldh + i] * y[c];
+    const double d = H[(size_t)i * ldh + i];
+    y[i] = d != 0.0 ? acc / d : 0.0;
+  }
+}
+
+template <typename T>
+__global__ void gmres_start_kernel(const T* __restrict__ r, const double* nrm2, T* __restrict__ v0,
+                                   double* g, size_t n) {
+  const double beta = sqrt(fmax(*nrm2, 0.0));
+  const double s = beta > 0 ? 1.0 / beta : 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) g[0] = beta;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x)
+    v0[e] = (T)(s * (double)r[e]);
+}
+
+inline int blocks_for(size_t n) {
+  size_t b = (n + kThreads - 1) / kThreads;
+  return (int)(b > 4096 ? 4096 : (b < 1 ? 1 : b));
+}
+
+}  // namespace
+
+size_t dots_partials(size_t n, int k) { return (size_t)kDotBlocks * (k > 0 ? k : 1); }
+
+template <typename Ts, typename Td>
+void launch_cast(const Ts* a, Td* b, size_t n, cudaStream_t st) {
+  cast_kernel<Ts, Td><<<blocks_for(n), kThreads, 0, st>>>(a, b, n);
+}
+
+template <typename T>
+void launch_fill(T* a, T v, size_t n, cudaStream_t st) {
+  fill_kernel<T><<<blocks_for(n), kThreads, 0, st>>>(a, v, n);
+}
+
+template <typename T>
+void launch_multidot(const T* V, size_t ld, int k, const T* w, size_t n, double* partials,
+                     double* out, cudaStream_t st) {
+  multidot_kernel<T><<<kDotBlocks, kThreads, 0, st>>>(V, ld, k, w, n, partials);
+  dots_finish_kernel<<<k, kThreads, 0, st>>>(partials, kDotBlocks, out);
+}
+
+template <typename T>
+void launch_multiaxpy(const T* V, size_t ld, int k, const double* h, T* w, size_t n,
+                      cudaStream_t st) {
+  multiaxpy_kernel<T><<<blocks_for(n), kThreads, 0, st>>>(V, ld, k, h, w, n);
+}
+
+template <typename T>
+void launch_scale_dev(const T* x, const double* a, int mode, T* y, size_t n, cudaStream_t st) {
+  scale_dev_kernel<T><<<blocks_for(n), kThreads, 0, st>>>(x, a, mode, y, n);
+}
+
+template <typename T, typename Tx>
+void launch_combine(const T* Z, size_t ld, int k, const double* y, double eps, Tx* x, size_t n,
+                    cudaStream_t st) {
+  combine_kernel<T, Tx><<<blocks_for(n), kThreads, 0, st>>>(Z, ld, k, y, eps, x, n);
+}
+
+void launch_givens(double* H, int ldh, double* cs, double* sn, double* gvec, const double* hcol,
+                   int j, double* resid, cudaStream_t st) {
+  givens_kernel<<<1, 32, 0, st>>>(H, ldh, cs, sn, gvec, hcol, j, resid);
+}
+
+void launch_backsolve(const double* H, int ldh, const double* gvec, int k, double* y,
+                      cudaStream_t st) {
+  backsolve_kernel<<<1, 32, 0, st>>>(H, ldh, gvec, k, y);
+}
+
+template <typename T>
+void launch_gmres_start(const T* r, const double* nrm2, T* v0, double* gvec, size_t n,
+                        cudaStream_t st) {
+  gmres_start_kernel<T><<<blocks_for(n), kThreads, 0, st>>>(r, nrm2, v0, gvec, n);
+}
+
+#define DNNMG_INST(T)                                                                          \
+  template void launch_fill<T>(T*, T, size_t, cudaStream_t);                                   \
+  template void launch_multidot<T>(const T*, size_t, int, const T*, size_t, double*, double*,  \
+                                   cudaStream_t);                                              \
+  template void launch_multiaxpy<T>(const T*, size_t, int, const double*, T*, size_t,          \
+                                    cudaStream_t);                                             \
+  template void launch_scale_dev<T>(const T*, const double*, int, T*, size_t, cudaStream_t);  \
+  template void launch_gmres_start<T>(const T*, const double*, T*, double*, size_t,            \
+                                      cudaStream_t);                                           \
+  template void launch_combine<T, T>(const T*, size_t, int, const double*, double, T*, size_t, \
+                                     cudaStream_t);
+DNNMG_INST(float)
+DNNMG_INST(double)
+#undef DNNMG_INST
+template void launch_combine<float, double>(const float*, size_t, int, const double*, double,
+                                            double*, size_t, cudaStream_t);
+template void launch_cast<double, float>(const double*, float*, size_t, cudaStream_t);
+template void launch_cast<float, double>(const float*, double*, size_t, cudaStream_t);
+template void launch_cast<double, double>(const double*, double*, size_t, cudaStream_t);
+template void launch_cast<float, float>(const float*, float*, size_t, cudaStream_t);
+
+}  // namespace dnnmg

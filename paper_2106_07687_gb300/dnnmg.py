@@ -1,0 +1,174 @@
+"""Thin Python binding of libdnnmg (argument marshalling only).
+
+Every computation runs in the CUDA library behind the C ABI declared in
+include/dnnmg.h; this module converts torch tensors into device pointers and
+status codes into exceptions.  It fails loudly when the library is missing.
+"""
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdnnmg.so")
+
+OK, ERR_ARG, ERR_CUDA, ERR_NOT_CONVERGED, ERR_NUMERICAL, ERR_TIMEOUT, ERR_STATE = range(7)
+FP64, MIXED = 0, 1
+PLAIN, NET = 0, 1
+
+c_double, c_int32, c_void_p = ctypes.c_double, ctypes.c_int32, ctypes.c_void_p
+
+
+class Config(ctypes.Structure):
+    """Mirror of dnnmg_config."""
+    _fields_ = [("nu", c_double), ("dt", c_double), ("theta", c_double), ("alpha0", c_double),
+                ("newton_tol", c_double), ("gmres_rtol", c_double), ("omega", c_double),
+                ("eps_damp", c_double), ("obstacle_i0", c_int32), ("obstacle_j0", c_int32),
+                ("level_solve", c_int32), ("level_coarse", c_int32), ("replaced_levels", c_int32),
+                ("precision", c_int32), ("newton_max", c_int32), ("gmres_m", c_int32),
+                ("gmres_maxit", c_int32), ("nu1", c_int32), ("nu2", c_int32), ("hidden", c_int32),
+                ("gru_layers", c_int32), ("mlp_width", c_int32), ("reserved", c_int32 * 8)]
+
+
+class StepStats(ctypes.Structure):
+    """Mirror of dnnmg_step_stats."""
+    _fields_ = [("newton_its", c_int32), ("gmres_its", c_int32), ("fallback", c_int32),
+                ("status", c_int32), ("res0", c_double), ("res_final", c_double), ("ms", c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class DnnmgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"dnnmg error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def _declare(lib):
+    P = c_void_p
+    sig = {
+        "dnnmg_default_config": ([P], ctypes.c_int),
+        "dnnmg_setup": ([P, P, P], ctypes.c_int),
+        "dnnmg_destroy": ([P], ctypes.c_int),
+        "dnnmg_last_error": ([P], ctypes.c_char_p),
+        "dnnmg_level_dims": ([P, ctypes.c_int, P, P], ctypes.c_int),
+        "dnnmg_get_state": ([P, P], ctypes.c_int),
+        "dnnmg_set_state": ([P, P], ctypes.c_int),
+        "dnnmg_linearize": ([P, P], ctypes.c_int),
+        "dnnmg_apply": ([P, ctypes.c_int, P, P, ctypes.c_int], ctypes.c_int),
+        "dnnmg_vcycle": ([P, ctypes.c_int, P, P, ctypes.c_int], ctypes.c_int),
+        "dnnmg_residual": ([P, P, P, P], ctypes.c_int),
+        "dnnmg_step": ([P, ctypes.c_int, P], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes, f.restype = args, res
+    return lib
+
+
+def load():
+    """Load libdnnmg.so from the package directory (raises if it is absent)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        _lib = _declare(ctypes.CDLL(LIB_PATH))
+    return _lib
+
+
+def default_config(**overrides):
+    cfg = Config()
+    load().dnnmg_default_config(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        if not hasattr(cfg, k):
+            raise KeyError(k)
+        setattr(cfg, k, v)
+    return cfg
+
+
+def _ptr(t):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return c_void_p(t.data_ptr())
+
+
+class Context:
+    """One DNN-MG solver context (wraps dnnmg_ctx)."""
+
+    def __init__(self, cfg=None, stream=None, **overrides):
+        self.lib = load()
+        self.cfg = cfg if cfg is not None else default_config(**overrides)
+        if cfg is not None:
+            for k, v in overrides.items():
+                setattr(self.cfg, k, v)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = c_void_p()
+        rc = self.lib.dnnmg_setup(ctypes.byref(self.cfg), c_void_p(self.stream.cuda_stream),
+                                  ctypes.byref(h))
+        if rc != OK:
+            raise DnnmgError(rc, self.lib.dnnmg_last_error(None).decode())
+        self.h = h
+        self.vdtype = torch.float64 if self.cfg.precision == FP64 else torch.float32
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dnnmg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, allow=()):
+        if rc != OK and rc not in allow:
+            raise DnnmgError(rc, self.lib.dnnmg_last_error(self.h).decode())
+        return rc
+
+    def level_dims(self, level):
+        nx, ny = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.dnnmg_level_dims(self.h, level, ctypes.byref(nx), ctypes.byref(ny)))
+        return nx.value, ny.value
+
+    def ndof(self, level):
+        nx, ny = self.level_dims(level)
+        return 3 * (nx + 1) * (ny + 1)
+
+    def get_state(self):
+        x = torch.empty(self.ndof(self.cfg.level_solve), dtype=torch.float64, device="cuda")
+        self._check(self.lib.dnnmg_get_state(self.h, _ptr(x)))
+        return x
+
+    def set_state(self, x):
+        self._check(self.lib.dnnmg_set_state(self.h, _ptr(x)))
+
+    def linearize(self, x):
+        self._check(self.lib.dnnmg_linearize(self.h, _ptr(x)))
+
+    def apply(self, level, w, y=None):
+        y = torch.empty_like(w) if y is None else y
+        self._check(self.lib.dnnmg_apply(self.h, level, _ptr(w), _ptr(y), self.cfg.precision))
+        return y
+
+    def vcycle(self, level, b, x=None):
+        x = torch.empty_like(b) if x is None else x
+        self._check(self.lib.dnnmg_vcycle(self.h, level, _ptr(b), _ptr(x), self.cfg.precision))
+        return x
+
+    def residual(self, x, f, r=None):
+        r = torch.empty_like(x) if r is None else r
+        self._check(self.lib.dnnmg_residual(self.h, _ptr(x), _ptr(f), _ptr(r)))
+        return r
+
+    def step(self, mode=PLAIN):
+        st = StepStats()
+        self._check(self.lib.dnnmg_step(self.h, mode, ctypes.byref(st)), allow=(ERR_NOT_CONVERGED,))
+        return st.as_dict()

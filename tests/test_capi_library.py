@@ -1,0 +1,52 @@
+"""The C-ABI library builds, loads without a GPU and exports every function
+that include/*.h declares; host-side argument checks return error codes."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?\w[\w\s\*]*?\b(dnnmg_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2106_07687_gb300 import build
+    return ctypes.CDLL(build.build())
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "dnnmg_setup" in names and "dnnmg_vcycle" in names and "dnnmg_step" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_default_config_and_argument_errors(lib):
+    from paper_2106_07687_gb300 import dnnmg
+    dnnmg.load()
+    cfg = dnnmg.default_config()
+    assert ctypes.sizeof(cfg) == 152
+    assert (cfg.nu, cfg.level_solve, cfg.level_coarse, cfg.gmres_m) == (0.01, 3, 1, 20)
+    L = dnnmg.load()
+    assert L.dnnmg_default_config(None) == dnnmg.ERR_ARG
+    out = ctypes.c_void_p(1)
+    assert L.dnnmg_setup(None, None, ctypes.byref(out)) == dnnmg.ERR_ARG
+    assert out.value is None
+    for bad in (dict(level_coarse=0), dict(level_solve=12), dict(nu=-1.0), dict(gmres_m=0),
+                dict(precision=7), dict(replaced_levels=5), dict(obstacle_i0=20)):
+        c = dnnmg.default_config(**bad)
+        assert L.dnnmg_setup(ctypes.byref(c), None, ctypes.byref(out)) == dnnmg.ERR_ARG, bad
+        assert out.value is None
+        assert len(L.dnnmg_last_error(None)) > 0
+    assert L.dnnmg_destroy(None) == dnnmg.OK
+    assert L.dnnmg_step(None, 0, None) == dnnmg.ERR_ARG

@@ -1,0 +1,91 @@
+"""Parity of the CUDA solver path (through the C ABI) with the FP64 oracle:
+Jacobian apply, nonlinear residual, V-cycle and whole Newton time steps.
+Tolerances: relative L2 1e-10 in FP64 mode and 1e-4 in mixed mode for
+solver results; operator rows match to rounding (1e-13 FP64, 1e-5 FP32)."""
+import numpy as np
+import pytest
+
+import synthetic
+from oracle import fem, mesh, mg, newton
+from tests.gpu_util import lib, rel, seeded_state
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _ctx(dn, L, precision, obstacle=(2, 1), nu=0.01, dt=0.01, **kw):
+    o = obstacle if obstacle is not None else (-1, -1)
+    return dn.Context(level_solve=L, precision=precision, obstacle_i0=o[0], obstacle_j0=o[1],
+                      nu=nu, dt=dt, **kw)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("L,obstacle", [(2, (2, 1)), (3, (3, 1)), (4, None)])
+def test_apply_matches_assembled_jacobian(precision, L, obstacle):
+    dn = lib()
+    prm = fem.Params(nu=0.008, dt=0.02)
+    ctx = _ctx(dn, L, precision, obstacle, prm.nu, prm.dt)
+    levels = mesh.hierarchy(L, obstacle=obstacle)
+    x = seeded_state(levels[-1], 11)
+    ctx.linearize(torch.from_numpy(x).cuda())
+    H = mg.Hierarchy(levels, x, prm)
+    dt = ctx.vdtype
+    for k, lev in enumerate(levels):
+        w = synthetic.random_vector(100 + k, lev.ndof)
+        y = ctx.apply(lev.ell, torch.from_numpy(w).to(dt).cuda()).double().cpu().numpy()
+        ref = H.ops[k].A @ w
+        assert rel(y, ref) < (1e-13 if precision == 0 else 1e-5), (lev.ell, rel(y, ref))
+
+
+@pytest.mark.parametrize("L", [2, 4])
+def test_residual_matches_oracle(L):
+    dn = lib()
+    prm = fem.Params(nu=0.005, dt=0.005)
+    ctx = _ctx(dn, L, 0, (3, 1), prm.nu, prm.dt)
+    lev = mesh.Level(L, obstacle=(3, 1))
+    x = seeded_state(lev, 5)
+    xo = seeded_state(lev, 6)
+    f = fem.old_time_rhs(lev, xo, prm)
+    r = ctx.residual(torch.from_numpy(x).cuda(), torch.from_numpy(f).cuda()).cpu().numpy()
+    ref = fem.residual(lev, x, f, prm)
+    scale = np.linalg.norm(f) + np.linalg.norm(fem.operator(lev, x, prm))
+    assert np.linalg.norm(r - ref) < 1e-13 * scale
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-4)])
+@pytest.mark.parametrize("L,obstacle,seed", [(1, (2, 1), 1), (3, (2, 1), 2), (4, (3, 1), 3),
+                                             (5, None, 4)])
+def test_vcycle_matches_oracle(precision, tol, L, obstacle, seed):
+    dn = lib()
+    prm = fem.Params(nu=0.01, dt=0.01)
+    ctx = _ctx(dn, L, precision, obstacle, prm.nu, prm.dt)
+    levels = mesh.hierarchy(L, obstacle=obstacle)
+    lev = levels[-1]
+    x = seeded_state(lev, seed)
+    ctx.linearize(torch.from_numpy(x).cuda())
+    b = synthetic.random_vector(seed + 50, lev.ndof)
+    b[lev.cons] = 0.0
+    xg = ctx.vcycle(L, torch.from_numpy(b).to(ctx.vdtype).cuda()).double().cpu().numpy()
+    H = mg.Hierarchy(levels, x, prm)
+    xr = mg.vcycle(H, len(levels) - 1, b)
+    assert rel(xg, xr) < tol, rel(xg, xr)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_plain_steps_match_oracle(precision):
+    """Small FP64 workload: 128x32 channel (level 3), nu = 0.01, dt = 0.01,
+    Newton tolerance 1e-10; three time steps from the impulsive start."""
+    dn = lib()
+    obstacle = synthetic.obstacle_block(1000)
+    prm = fem.Params(nu=0.01, dt=0.01)
+    ctx = _ctx(dn, 3, precision, obstacle, prm.nu, prm.dt, newton_tol=1e-11)
+    levels = mesh.hierarchy(3, obstacle=obstacle)
+    opt = newton.SolverOptions(newton_tol=1e-11)
+    x = mesh.initial_state(levels[-1])
+    np.testing.assert_allclose(ctx.get_state().cpu().numpy(), x, atol=1e-15)
+    for n in range(3):
+        st = ctx.step(dn.PLAIN)
+        x, nit, _, nrm = newton.time_step(levels, x, prm, opt)
+        xg = ctx.get_state().cpu().numpy()
+        assert st["res_final"] <= 1e-11
+        assert rel(xg, x) < (1e-10 if precision == 0 else 1e-4), (n, rel(xg, x), st)
