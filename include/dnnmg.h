@@ -164,6 +164,32 @@ int dnnmg_residual(dnnmg_ctx* ctx, const double* x, const double* f, double* r);
  * taken), DNNMG_ERR_NUMERICAL on NaN/Inf. */
 int dnnmg_step(dnnmg_ctx* ctx, int mode, dnnmg_step_stats* stats);
 
+/* Per-stage device timers (tracing).  Stages: */
+#define DNNMG_STAGE_VANKA_PASS 0    /* one colour pass of the Vanka smoother */
+#define DNNMG_STAGE_VANKA_SETUP 1   /* local 12x12 inverses of one level */
+#define DNNMG_STAGE_APPLY 2         /* Jacobian apply inside FGMRES */
+#define DNNMG_STAGE_DEFECT 3        /* defect before restriction */
+#define DNNMG_STAGE_TRANSFER 4      /* restriction / prolongation */
+#define DNNMG_STAGE_COARSE_FACTOR 5 /* coarse-level LU and inverse */
+#define DNNMG_STAGE_COARSE_SOLVE 6  /* coarse-level solve in the V-cycle */
+#define DNNMG_STAGE_KRYLOV 7        /* FGMRES orthogonalisation and updates */
+#define DNNMG_STAGE_RESIDUAL 8      /* FP64 nonlinear residual */
+#define DNNMG_STAGE_NETWORK 9       /* DNN-MG gather, patch network, scatter and Rhs */
+#define DNNMG_STAGE_TRAIN 10        /* training forward, backward and optimiser */
+
+/* enable != 0: reset the timers and record CUDA events around the launches
+ * of each stage from now on; enable = 0: stop recording.  Recording costs one
+ * event pair per timed launch group; results are exact device times. */
+int dnnmg_profile(dnnmg_ctx* ctx, int enable);
+
+/* Accumulated device time (ms) and number of timed launch groups of `stage`
+ * on mesh level `level` (level = -1: all levels) since the last reset.
+ * Synchronises the context's stream. */
+int dnnmg_profile_read(dnnmg_ctx* ctx, int stage, int level, int64_t* launches, double* ms);
+
+/* Number of kernels this library has launched in this process so far. */
+uint64_t dnnmg_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

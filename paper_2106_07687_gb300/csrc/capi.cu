@@ -228,4 +228,28 @@ int dnnmg_step(dnnmg_ctx* ctx, int mode, dnnmg_step_stats* stats) {
   return ctx->step(mode, stats);
 }
 
+int dnnmg_profile(dnnmg_ctx* ctx, int enable) {
+  if (!ctx) return DNNMG_ERR_ARG;
+  ctx->prof.enable(enable != 0);
+  return DNNMG_OK;
+}
+
+int dnnmg_profile_read(dnnmg_ctx* ctx, int stage, int level, int64_t* launches, double* ms) {
+  if (!ctx || stage < 0 || stage >= kStages || level < -1 || level >= kMaxLevels)
+    return DNNMG_ERR_ARG;
+  ctx->prof.collect(ctx->st);
+  long long n = 0;
+  double t = 0;
+  for (int l = 0; l < kMaxLevels; ++l)
+    if (level < 0 || l == level) {
+      n += ctx->prof.count(stage, l);
+      t += ctx->prof.ms(stage, l);
+    }
+  if (launches) *launches = n;
+  if (ms) *ms = t;
+  return DNNMG_OK;
+}
+
+uint64_t dnnmg_kernel_launches(void) { return dnnmg::launches(); }
+
 }  // extern "C"

@@ -98,33 +98,35 @@ __global__ void assemble_kernel(Grid g, Sten<double> s, const double* __restrict
 }
 
 // Banded LU with partial pivoting in one thread block (dgbtf2 ordering).
+// The rows k..k+kl that elimination step k touches live in a shared-memory
+// window of kWin row slots (row r in slot r % kWin, same per-row band offset
+// as in global memory); a row is loaded when it enters the window and written
+// back once it is final.
 constexpr int kLUThreads = 1024;
+constexpr int kWin = 64;
 __global__ void __launch_bounds__(kLUThreads)
     band_lu_kernel(Grid g, double* __restrict__ ab, int* __restrict__ piv, int* status) {
   const Band bd = band_of(g);
-  __shared__ double s_val[32];
-  __shared__ int s_idx[32];
+  extern __shared__ double win[];  // kWin * W
   __shared__ int s_p;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  auto W = [&](int r, int col) -> double& {
+    return win[(size_t)(r % kWin) * bd.W + (col - r + bd.kl)];
+  };
+  // rows 0..kl enter the window
+  for (int r = 0; r <= min(bd.kl, bd.n - 1); ++r)
+    for (int e = tid; e < bd.W; e += kLUThreads)
+      win[(size_t)(r % kWin) * bd.W + e] = ab[(size_t)r * bd.W + e];
+  __syncthreads();
   for (int k = 0; k < bd.n; ++k) {
     const int rmax = min(bd.n - 1, k + bd.kl);
-    // pivot search over rows k..rmax of column k
     double best = -1.0;
     int bi = k;
-    for (int r = k + tid; r <= rmax; r += kLUThreads) {
-      const double v = fabs(AB(ab, bd, r, k));
-      if (v > best) best = v, bi = r;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_down_sync(0xffffffffu, best, o);
-      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-      if (ov > best || (ov == best && oi < bi)) best = ov, bi = oi;
-    }
-    if (lane == 0) s_val[warp] = best, s_idx[warp] = bi;
-    __syncthreads();
     if (warp == 0) {
-      best = s_val[lane];
-      bi = s_idx[lane];
+      for (int r = k + lane; r <= rmax; r += 32) {
+        const double v = fabs(W(r, k));
+        if (v > best) best = v, bi = r;
+      }
       for (int o = 16; o > 0; o >>= 1) {
         const double ov = __shfl_down_sync(0xffffffffu, best, o);
         const int oi = __shfl_down_sync(0xffffffffu, bi, o);
@@ -141,20 +143,29 @@ __global__ void __launch_bounds__(kLUThreads)
     const int cmax = min(bd.n - 1, k + bd.ku + bd.kl);
     if (p != k)
       for (int col = k + tid; col <= cmax; col += kLUThreads) {
-        const double t = AB(ab, bd, k, col);
-        AB(ab, bd, k, col) = AB(ab, bd, p, col);
-        AB(ab, bd, p, col) = t;
+        const double t = W(k, col);
+        W(k, col) = W(p, col);
+        W(p, col) = t;
       }
     __syncthreads();
-    const double d = AB(ab, bd, k, k);
+    const double d = W(k, k);
     const double id = d != 0.0 ? 1.0 / d : 0.0;
-    for (int r = k + 1 + tid; r <= rmax; r += kLUThreads) AB(ab, bd, r, k) *= id;
+    for (int r = k + 1 + tid; r <= rmax; r += kLUThreads) W(r, k) *= id;
     __syncthreads();
     const int nr = rmax - k, nc = cmax - k;
     for (int e = tid; e < nr * nc; e += kLUThreads) {
       const int r = k + 1 + e / nc, col = k + 1 + e % nc;
-      AB(ab, bd, r, col) -= AB(ab, bd, r, k) * AB(ab, bd, k, col);
+      W(r, col) -= W(r, k) * W(k, col);
     }
+    __syncthreads();
+    // row k is final: write it back; row k + kl + 1 enters the window
+    for (int e = tid; e < bd.W; e += kLUThreads)
+      ab[(size_t)k * bd.W + e] = win[(size_t)(k % kWin) * bd.W + e];
+    __syncthreads();
+    const int rn = k + bd.kl + 1;
+    if (rn < bd.n)
+      for (int e = tid; e < bd.W; e += kLUThreads)
+        win[(size_t)(rn % kWin) * bd.W + e] = ab[(size_t)rn * bd.W + e];
     __syncthreads();
   }
 }
@@ -221,6 +232,12 @@ __global__ void __launch_bounds__(32 * kSolveWarps)
 
 }  // namespace
 
+bool coarse_supported(const Grid& g) {
+  const Band bd = band_of(g);
+  return bd.kl + 1 <= kWin && sizeof(double) * kWin * bd.W <= 200 * 1024 &&
+         sizeof(double) * bd.n * kInvWarps <= 48 * 1024;
+}
+
 size_t coarse_work_doubles(const Grid& g) {
   const Band bd = band_of(g);
   return (size_t)bd.n * bd.W + (size_t)bd.n;  // band + pivots (as ints, over-allocated)
@@ -231,15 +248,22 @@ void launch_coarse_factor(const Grid& g, const Sten<double>& s, const double* vb
   const Band bd = band_of(g);
   double* ab = work;
   int* piv = reinterpret_cast<int*>(work + (size_t)bd.n * bd.W);
+  note_launch();
   assemble_kernel<<<cdiv(bd.n, 128), 128, 0, st>>>(g, s, vb, ab);
-  band_lu_kernel<<<1, kLUThreads, 0, st>>>(g, ab, piv, status);
+  const size_t win_bytes = sizeof(double) * kWin * bd.W;
+  cudaFuncSetAttribute(band_lu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)win_bytes);
+  note_launch();
+  band_lu_kernel<<<1, kLUThreads, win_bytes, st>>>(g, ab, piv, status);
   const size_t smem = sizeof(double) * bd.n * kInvWarps;
+  note_launch();
   band_inverse_kernel<<<cdiv(bd.n, kInvWarps), 32 * kInvWarps, smem, st>>>(g, ab, piv, Ainv);
 }
 
 template <typename T>
 void launch_coarse_solve(const Grid& g, const double* Ainv, const T* b, T* x, cudaStream_t st) {
   const Band bd = band_of(g);
+  note_launch();
   coarse_solve_kernel<T><<<cdiv(bd.n, kSolveWarps), 32 * kSolveWarps, sizeof(double) * bd.n, st>>>(
       g, Ainv, b, x);
 }

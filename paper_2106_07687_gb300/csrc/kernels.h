@@ -7,6 +7,10 @@
 
 namespace dnnmg {
 
+// Process-wide count of kernels launched by this library.
+void note_launch();
+unsigned long long launches();
+
 // Operator rows (stencil.cu) ---------------------------------------------
 // y = A'(vbar) w on free DOFs, y = w on constrained DOFs (Eq. 7).
 template <typename T>
@@ -58,6 +62,7 @@ inline int vanka_slots(const Grid& g) { return (g.nx / 2 + 1) * (g.ny / 2 + 1); 
 // partial pivoting and form the explicit inverse Ainv (ndof x ndof, FP64,
 // unknowns in band order).  `work` needs coarse_work_doubles(g) doubles.
 size_t coarse_work_doubles(const Grid& g);
+bool coarse_supported(const Grid& g);  // band fits the shared-memory window
 void launch_coarse_factor(const Grid& g, const Sten<double>& s, const double* vb, double* work,
                           double* Ainv, int* status, cudaStream_t st);
 // x = Ainv b, b and x in the [3][nn] layout of the level

@@ -24,7 +24,8 @@ class Solver final : public SolverBase {
     lv_.resize(K_ + 1);
     for (int k = 0; k <= K_; ++k) {
       Lev& l = lv_[k];
-      l.g = c_->grid(cfg.level_coarse + k);
+      l.level = cfg.level_coarse + k;
+      l.g = c_->grid(l.level);
       const size_t n3 = 3 * (size_t)l.g.nn, n2 = 2 * (size_t)l.g.nn;
       l.s = make_sten<T>(l.g.h, cfg);
       l.s64 = make_sten<double>(l.g.h, cfg);
@@ -37,6 +38,7 @@ class Solver final : public SolverBase {
       if (k > 0) l.inv = c_->mem.alloc<T>((size_t)4 * 144 * vanka_slots(l.g));
     }
     const Grid& g0 = lv_[0].g;
+    if (!coarse_supported(g0)) return c_->fail(DNNMG_ERR_ARG, "coarse level too large");
     coarse_work_ = c_->mem.alloc<double>(coarse_work_doubles(g0));
     ainv_ = c_->mem.alloc<double>((size_t)9 * g0.nn * g0.nn);
     status_ = c_->mem.alloc<int>(4);
@@ -65,7 +67,7 @@ class Solver final : public SolverBase {
 
   // Linearise every level at the velocity of x64 (level L): nodal injection
   // down the hierarchy, Vanka inverses, coarse LU and inverse.
-  int linearize(const double* x64) override {
+  int linearize(const double* x64, bool coarse) override {
     cudaMemcpyAsync(lv_[K_].vb64, x64, 2 * sizeof(double) * lv_[K_].g.nn,
                     cudaMemcpyDeviceToDevice, st_);
     for (int k = K_; k > 0; --k)
@@ -73,9 +75,18 @@ class Solver final : public SolverBase {
     cudaMemsetAsync(status_, 0, sizeof(int), st_);
     for (int k = 0; k <= K_; ++k) {
       launch_cast<double, T>(lv_[k].vb64, lv_[k].vb, 2 * (size_t)lv_[k].g.nn, st_);
-      if (k > 0) launch_vanka_setup<T>(lv_[k].g, lv_[k].s, lv_[k].vb, lv_[k].inv, status_, st_);
+      if (k > 0) {
+        const int p = c_->prof.begin(DNNMG_STAGE_VANKA_SETUP, lv_[k].level, st_);
+        launch_vanka_setup<T>(lv_[k].g, lv_[k].s, lv_[k].vb, lv_[k].inv, status_, st_);
+        c_->prof.end(p, st_);
+      }
     }
-    launch_coarse_factor(lv_[0].g, lv_[0].s64, lv_[0].vb64, coarse_work_, ainv_, status_, st_);
+    if (coarse || !coarse_done_) {
+      const int p = c_->prof.begin(DNNMG_STAGE_COARSE_FACTOR, lv_[0].level, st_);
+      launch_coarse_factor(lv_[0].g, lv_[0].s64, lv_[0].vb64, coarse_work_, ainv_, status_, st_);
+      c_->prof.end(p, st_);
+      coarse_done_ = true;
+    }
     int status = 0;
     cudaMemcpyAsync(c_->h_scalars, status_, sizeof(int), cudaMemcpyDeviceToHost, st_);
     if (int rc = c_->check("linearize")) return rc;
@@ -128,7 +139,10 @@ class Solver final : public SolverBase {
         T* w = V_ + (size_t)(j + 1) * n_;
         launch_fill<T>(zj, T(0), n_, st_);
         cycle(K_, vj, zj);
+        int p = c_->prof.begin(DNNMG_STAGE_APPLY, lv_[K_].level, st_);
         launch_apply<T>(lv_[K_].g, lv_[K_].s, zj, lv_[K_].vb, w, st_);
+        c_->prof.end(p, st_);
+        p = c_->prof.begin(DNNMG_STAGE_KRYLOV, lv_[K_].level, st_);
         launch_multidot<T>(V_, n_, j + 1, w, n_, partials_, hcol_, st_);
         launch_multiaxpy<T>(V_, n_, j + 1, hcol_, w, n_, st_);
         launch_multidot<T>(V_, n_, j + 1, w, n_, partials_, hcol_ + j + 1, st_);
@@ -136,6 +150,7 @@ class Solver final : public SolverBase {
         launch_multidot<T>(w, n_, 1, w, n_, partials_, hcol_ + 2 * j + 2, st_);
         launch_givens(H_, m_ + 1, cs_, sn_, gv_, hcol_, j, y_ + m_, st_);
         launch_scale_dev<T>(w, hcol_ + 2 * j + 2, 2, w, n_, st_);
+        c_->prof.end(p, st_);
         ++its;
         k = j + 1;
         double res = 0;
@@ -160,6 +175,7 @@ class Solver final : public SolverBase {
 
  private:
   struct Lev {
+    int level = 0;
     Grid g{};
     Sten<T> s{};
     Sten<double> s64{};
@@ -182,7 +198,9 @@ class Solver final : public SolverBase {
     T* nxt = l.x2;
     for (int s = 0; s < sweeps; ++s)
       for (int colour = 0; colour < 4; ++colour) {
+        const int p = c_->prof.begin(DNNMG_STAGE_VANKA_PASS, l.level, st_);
         launch_vanka_pass<T>(l.g, l.s, colour, b, cur, l.vb, l.inv, (T)c_->cfg.omega, nxt, st_);
+        c_->prof.end(p, st_);
         T* t = cur;
         cur = nxt;
         nxt = t;
@@ -193,16 +211,24 @@ class Solver final : public SolverBase {
   void cycle(int k, const T* b, T* x) {
     Lev& l = lv_[k];
     if (k == 0) {
+      const int p = c_->prof.begin(DNNMG_STAGE_COARSE_SOLVE, l.level, st_);
       launch_coarse_solve<T>(l.g, ainv_, b, x, st_);
+      c_->prof.end(p, st_);
       return;
     }
     Lev& lc = lv_[k - 1];
     smooth(k, b, x, c_->cfg.nu1);
+    int p = c_->prof.begin(DNNMG_STAGE_DEFECT, l.level, st_);
     launch_defect<T>(l.g, l.s, b, x, l.vb, l.d, true, st_);
+    c_->prof.end(p, st_);
+    p = c_->prof.begin(DNNMG_STAGE_TRANSFER, l.level, st_);
     launch_restrict<T>(l.g, lc.g, l.d, lc.b, st_);
     launch_fill<T>(lc.x, T(0), 3 * (size_t)lc.g.nn, st_);
+    c_->prof.end(p, st_);
     cycle(k - 1, lc.b, lc.x);
+    p = c_->prof.begin(DNNMG_STAGE_TRANSFER, l.level, st_);
     launch_prolong_add<T>(l.g, lc.g, lc.x, x, st_);
+    c_->prof.end(p, st_);
     smooth(k, b, x, c_->cfg.nu2);
   }
 
@@ -217,6 +243,7 @@ class Solver final : public SolverBase {
   double *H_ = nullptr, *cs_ = nullptr, *sn_ = nullptr, *gv_ = nullptr, *hcol_ = nullptr,
          *y_ = nullptr, *one_ = nullptr, *partials_ = nullptr;
   bool linearized_ = false;
+  bool coarse_done_ = false;
 };
 
 }  // namespace
@@ -350,17 +377,22 @@ int dnnmg_ctx::residual_api(const double* x, const double* f, double* r) {
 int dnnmg_ctx::newton(const double* f, dnnmg_step_stats* s) {
   const Grid gL = grid(L());
   const size_t n3 = 3 * (size_t)gL.nn;
+  int p = prof.begin(DNNMG_STAGE_RESIDUAL, L(), st);
   launch_residual64(gL, s64L, x64, f, r64, st);
+  prof.end(p, st);
   double nrm = norm64(r64, n3);
   s->res0 = nrm;
   int it = 0, gits = 0;
   while (nrm > cfg.newton_tol && it < cfg.newton_max) {
     if (!std::isfinite(nrm)) return fail(DNNMG_ERR_NUMERICAL, "non-finite Newton residual");
-    if (int rc = solver->linearize(x64)) return rc;
+    // the coarse-level factorisation is refreshed once per time step
+    if (int rc = solver->linearize(x64, it == 0)) return rc;
     int its = 0;
     if (int rc = solver->solve(r64, x64, cfg.eps_damp, &its)) return rc;
     gits += its;
+    p = prof.begin(DNNMG_STAGE_RESIDUAL, L(), st);
     launch_residual64(gL, s64L, x64, f, r64, st);
+    prof.end(p, st);
     nrm = norm64(r64, n3);
     ++it;
   }
@@ -386,6 +418,7 @@ int dnnmg_ctx::step(int mode, dnnmg_step_stats* stats) {
   cudaEventElapsedTime(&ms, ev0, ev1);
   s.ms = ms;
   s.status = rc;
+  prof.collect(st);
   (void)mode;
   if (stats) *stats = s;
   return rc;

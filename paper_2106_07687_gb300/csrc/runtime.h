@@ -43,11 +43,75 @@ class DevMem {
   bool ok_ = true;
 };
 
+// Per-stage device timers: CUDA events recorded on the context's stream
+// around kernel launches, read back after the stream has synchronised.
+constexpr int kStages = 12;
+class Prof {
+ public:
+  ~Prof() {
+    for (cudaEvent_t e : ev_) cudaEventDestroy(e);
+  }
+  void enable(bool on) {
+    on_ = on;
+    reset();
+    if (on && ev_.empty()) {
+      ev_.resize(kPool);
+      for (auto& e : ev_) cudaEventCreate(&e);
+    }
+  }
+  bool on() const { return on_; }
+  void reset() {
+    recs_.clear();
+    used_ = 0;
+    for (auto& r : ms_) for (auto& v : r) v = 0;
+    for (auto& r : cnt_) for (auto& v : r) v = 0;
+  }
+  // returns the record slot or -1
+  int begin(int stage, int level, cudaStream_t st) {
+    if (!on_ || used_ + 2 > kPool) return -1;
+    const int e0 = used_;
+    used_ += 2;
+    cudaEventRecord(ev_[e0], st);
+    recs_.push_back({stage, level, e0});
+    return e0;
+  }
+  void end(int e0, cudaStream_t st) {
+    if (e0 >= 0) cudaEventRecord(ev_[e0 + 1], st);
+  }
+  void collect(cudaStream_t st) {
+    if (recs_.empty()) return;
+    cudaStreamSynchronize(st);
+    for (const Rec& r : recs_) {
+      float t = 0;
+      cudaEventElapsedTime(&t, ev_[r.e0], ev_[r.e0 + 1]);
+      ms_[r.stage][r.level] += t;
+      cnt_[r.stage][r.level] += 1;
+    }
+    recs_.clear();
+    used_ = 0;
+  }
+  double ms(int stage, int level) const { return ms_[stage][level]; }
+  long long count(int stage, int level) const { return cnt_[stage][level]; }
+
+ private:
+  struct Rec {
+    int stage, level, e0;
+  };
+  static constexpr int kPool = 1 << 14;
+  bool on_ = false;
+  std::vector<cudaEvent_t> ev_;
+  std::vector<Rec> recs_;
+  int used_ = 0;
+  double ms_[kStages][kMaxLevels] = {};
+  long long cnt_[kStages][kMaxLevels] = {};
+};
+
 // Precision-independent interface of the solver engine.
 class SolverBase {
  public:
   virtual ~SolverBase() = default;
-  virtual int linearize(const double* x64) = 0;
+  // coarse = false keeps the coarse-level factorisation of the previous call
+  virtual int linearize(const double* x64, bool coarse = true) = 0;
   virtual int apply(int k, const void* w, void* y) = 0;
   virtual int vcycle(int k, const void* b, void* x) = 0;
   // FGMRES on the finest level: w64 += eps * A'^{-1} r64 (approximately)
@@ -77,6 +141,7 @@ struct dnnmg_ctx {
   double* partials = nullptr;  // reduction partials
   double* h_scalars = nullptr; // pinned host scalars
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  dnnmg::Prof prof;
 
   ~dnnmg_ctx();
   int init();

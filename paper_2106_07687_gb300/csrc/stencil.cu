@@ -97,22 +97,26 @@ inline dim3 node_grid(const Grid& g) { return dim3(cdiv(g.nnx, kBX), cdiv(g.nny,
 
 template <typename T>
 void launch_apply(const Grid& g, const Sten<T>& s, const T* w, const T* vb, T* y, cudaStream_t st) {
+  note_launch();
   apply_kernel<T><<<node_grid(g), dim3(kBX, kBY), 0, st>>>(g, s, w, vb, y);
 }
 
 template <typename T>
 void launch_defect(const Grid& g, const Sten<T>& s, const T* b, const T* x, const T* vb, T* d,
                    bool masked, cudaStream_t st) {
+  note_launch();
   defect_kernel<T><<<node_grid(g), dim3(kBX, kBY), 0, st>>>(g, s, b, x, vb, d, masked);
 }
 
 void launch_residual64(const Grid& g, const Sten<double>& s, const double* x, const double* f,
                        double* r, cudaStream_t st) {
+  note_launch();
   residual64_kernel<<<node_grid(g), dim3(kBX, kBY), 0, st>>>(g, s, x, f, r);
 }
 
 void launch_old_time_rhs64(const Grid& g, double inv_k, const double* x_old, double* f,
                            cudaStream_t st) {
+  note_launch();
   old_rhs64_kernel<<<node_grid(g), dim3(kBX, kBY), 0, st>>>(g, inv_k, x_old, f);
 }
 

@@ -98,27 +98,32 @@ inline dim3 grid_of(const Grid& g) { return dim3(cdiv(g.nnx, kBX), cdiv(g.nny, k
 
 template <typename T>
 void launch_restrict(const Grid& fine, const Grid& coarse, const T* d, T* bc, cudaStream_t st) {
+  note_launch();
   restrict_kernel<T, true><<<grid_of(coarse), dim3(kBX, kBY), 0, st>>>(fine, coarse, d, bc, 3);
 }
 
 template <typename T>
 void launch_prolong_add(const Grid& fine, const Grid& coarse, const T* xc, T* x, cudaStream_t st) {
+  note_launch();
   prolong_add_kernel<T><<<grid_of(fine), dim3(kBX, kBY), 0, st>>>(fine, coarse, xc, x);
 }
 
 template <typename T>
 void launch_inject(const Grid& fine, const Grid& coarse, const T* xf, T* xc, int ncomp,
                    cudaStream_t st) {
+  note_launch();
   inject_kernel<T><<<grid_of(coarse), dim3(kBX, kBY), 0, st>>>(fine, coarse, xf, xc, ncomp);
 }
 
 void launch_prolong_state64(const Grid& fine, const Grid& coarse, const double* xc, double* xf,
                             int ncomp, cudaStream_t st) {
+  note_launch();
   prolong_state_kernel<<<grid_of(fine), dim3(kBX, kBY), 0, st>>>(fine, coarse, xc, xf, ncomp);
 }
 
 void launch_restrict_full64(const Grid& fine, const Grid& coarse, const double* bf, double* bc,
                             int ncomp, cudaStream_t st) {
+  note_launch();
   restrict_kernel<double, false><<<grid_of(coarse), dim3(kBX, kBY), 0, st>>>(fine, coarse, bf, bc,
                                                                              ncomp);
 }

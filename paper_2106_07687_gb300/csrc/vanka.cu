@@ -192,6 +192,7 @@ template <typename T>
 void launch_vanka_setup(const Grid& g, const Sten<T>& s, const T* vb, T* inv, int* status,
                         cudaStream_t st) {
   dim3 grid(cdiv(vanka_slots(g), kSetupThreads), 4);
+  note_launch();
   vanka_setup_kernel<T><<<grid, kSetupThreads, 0, st>>>(g, s, vb, inv, status);
 }
 
@@ -199,6 +200,7 @@ template <typename T>
 void launch_vanka_pass(const Grid& g, const Sten<T>& s, int colour, const T* b, const T* xin,
                        const T* vb, const T* inv, T omega, T* xout, cudaStream_t st) {
   const int threads = 4 * vanka_slots(g);
+  note_launch();
   vanka_pass_kernel<T><<<cdiv(threads, kPassThreads), kPassThreads, 0, st>>>(
       g, s, colour, b, xin, vb, inv, omega, xout);
 }

@@ -1,6 +1,8 @@
 // Vector kernels of the flexible GMRES solver (Sec. 2.2: GMRES preconditioned
 // by multigrid) and of the Newton update (Eq. 7).  Reductions accumulate in
 // FP64 and run in two fixed-order stages, so results are deterministic.
+#include <atomic>
+
 #include "kernels.h"
 
 namespace dnnmg {
@@ -155,55 +157,71 @@ inline int blocks_for(size_t n) {
 
 }  // namespace
 
+namespace {
+std::atomic<unsigned long long> g_launches{0};
+}
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+unsigned long long launches() { return g_launches.load(std::memory_order_relaxed); }
+
 size_t dots_partials(size_t n, int k) { return (size_t)kDotBlocks * (k > 0 ? k : 1); }
 
 template <typename Ts, typename Td>
 void launch_cast(const Ts* a, Td* b, size_t n, cudaStream_t st) {
+  note_launch();
   cast_kernel<Ts, Td><<<blocks_for(n), kThreads, 0, st>>>(a, b, n);
 }
 
 template <typename T>
 void launch_fill(T* a, T v, size_t n, cudaStream_t st) {
+  note_launch();
   fill_kernel<T><<<blocks_for(n), kThreads, 0, st>>>(a, v, n);
 }
 
 template <typename T>
 void launch_multidot(const T* V, size_t ld, int k, const T* w, size_t n, double* partials,
                      double* out, cudaStream_t st) {
+  note_launch();
   multidot_kernel<T><<<kDotBlocks, kThreads, 0, st>>>(V, ld, k, w, n, partials);
+  note_launch();
   dots_finish_kernel<<<k, kThreads, 0, st>>>(partials, kDotBlocks, out);
 }
 
 template <typename T>
 void launch_multiaxpy(const T* V, size_t ld, int k, const double* h, T* w, size_t n,
                       cudaStream_t st) {
+  note_launch();
   multiaxpy_kernel<T><<<blocks_for(n), kThreads, 0, st>>>(V, ld, k, h, w, n);
 }
 
 template <typename T>
 void launch_scale_dev(const T* x, const double* a, int mode, T* y, size_t n, cudaStream_t st) {
+  note_launch();
   scale_dev_kernel<T><<<blocks_for(n), kThreads, 0, st>>>(x, a, mode, y, n);
 }
 
 template <typename T, typename Tx>
 void launch_combine(const T* Z, size_t ld, int k, const double* y, double eps, Tx* x, size_t n,
                     cudaStream_t st) {
+  note_launch();
   combine_kernel<T, Tx><<<blocks_for(n), kThreads, 0, st>>>(Z, ld, k, y, eps, x, n);
 }
 
 void launch_givens(double* H, int ldh, double* cs, double* sn, double* gvec, const double* hcol,
                    int j, double* resid, cudaStream_t st) {
+  note_launch();
   givens_kernel<<<1, 32, 0, st>>>(H, ldh, cs, sn, gvec, hcol, j, resid);
 }
 
 void launch_backsolve(const double* H, int ldh, const double* gvec, int k, double* y,
                       cudaStream_t st) {
+  note_launch();
   backsolve_kernel<<<1, 32, 0, st>>>(H, ldh, gvec, k, y);
 }
 
 template <typename T>
 void launch_gmres_start(const T* r, const double* nrm2, T* v0, double* gvec, size_t n,
                         cudaStream_t st) {
+  note_launch();
   gmres_start_kernel<T><<<blocks_for(n), kThreads, 0, st>>>(r, nrm2, v0, gvec, n);
 }
 

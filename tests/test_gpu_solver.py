@@ -73,19 +73,23 @@ def test_vcycle_matches_oracle(precision, tol, L, obstacle, seed):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_plain_steps_match_oracle(precision):
-    """Small FP64 workload: 128x32 channel (level 3), nu = 0.01, dt = 0.01,
-    Newton tolerance 1e-10; three time steps from the impulsive start."""
+    """Small FP64 workload: 128x32 channel (level 3), nu = 0.01, dt = 0.01;
+    three time steps from the impulsive start.  Both sides iterate Newton to
+    ||r|| <= 1e-12 so that the distance between their converged states (at
+    most ~||A'^-1|| * 2 tol) sits well below the 1e-10 bar; the solvers reach
+    that state by different iterates (the GPU keeps the coarse LU for a whole
+    step)."""
     dn = lib()
     obstacle = synthetic.obstacle_block(1000)
     prm = fem.Params(nu=0.01, dt=0.01)
-    ctx = _ctx(dn, 3, precision, obstacle, prm.nu, prm.dt, newton_tol=1e-11)
+    ctx = _ctx(dn, 3, precision, obstacle, prm.nu, prm.dt, newton_tol=1e-12)
     levels = mesh.hierarchy(3, obstacle=obstacle)
-    opt = newton.SolverOptions(newton_tol=1e-11)
+    opt = newton.SolverOptions(newton_tol=1e-12)
     x = mesh.initial_state(levels[-1])
     np.testing.assert_allclose(ctx.get_state().cpu().numpy(), x, atol=1e-15)
     for n in range(3):
         st = ctx.step(dn.PLAIN)
         x, nit, _, nrm = newton.time_step(levels, x, prm, opt)
         xg = ctx.get_state().cpu().numpy()
-        assert st["res_final"] <= 1e-11
+        assert st["res_final"] <= 1e-12
         assert rel(xg, x) < (1e-10 if precision == 0 else 1e-4), (n, rel(xg, x), st)
