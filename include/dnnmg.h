@@ -115,7 +115,8 @@ int dnnmg_setup(const dnnmg_config* cfg, void* stream, dnnmg_ctx** out);
 int dnnmg_destroy(dnnmg_ctx* ctx);
 
 /* Message of the last failure on ctx ("" if none), owned by ctx.  With
- * ctx = NULL: the message of this thread's last failed dnnmg_setup(). */
+ * ctx = NULL: the message of this thread's last failed dnnmg_setup() or
+ * dnnmg_coarse_solve_noalloc() call. */
 const char* dnnmg_last_error(const dnnmg_ctx* ctx);
 
 /* Cells of mesh level `level` (any level from 0 to L + replaced_levels). */
@@ -163,6 +164,33 @@ int dnnmg_residual(dnnmg_ctx* ctx, const double* x, const double* f, double* r);
  * Returns DNNMG_ERR_NOT_CONVERGED if Newton hit newton_max (the step is still
  * taken), DNNMG_ERR_NUMERICAL on NaN/Inf. */
 int dnnmg_step(dnnmg_ctx* ctx, int mode, dnnmg_step_stats* stats);
+
+/* Direct solve of the coarsest multigrid level without any device allocation
+ * (the paper has no counterpart: this is a deployment variant).
+ *
+ * For callers that cannot call cudaMalloc - e.g. code that runs under an
+ * external memory manager owning the whole device heap, or inside a
+ * real-time loop where an allocation and the synchronisation it may cause
+ * are not allowed - and therefore cannot create a context.  It assembles the
+ * Jacobian A'(vbar) (Eq. 7, with LPS) of level cfg->level_coarse, factors it
+ * by banded LU with partial pivoting and returns x = A'(vbar)^{-1} b: the
+ * same operator the coarse level of dnnmg_vcycle() inverts.
+ *   cfg  : host pointer; uses nu, dt, theta (must be 1), alpha0, obstacle_i0,
+ *          obstacle_j0 and level_coarse.
+ *   vbar : device, [2][nn] doubles, linearisation velocity on that level.
+ *   b, x : device, [3][nn] doubles on that level (b and x may not alias).
+ *   stream: cudaStream_t to issue the work on; the call synchronises it.
+ * Working memory is one file-scope __device__ array of 2 MiB that every GPU
+ * which loads this library holds until the process exits; it fits level 1
+ * only (891 unknowns, ~1.34 MB).  Larger levels return DNNMG_ERR_ARG.
+ * The first call on a device looks up that array's device address (with the
+ * device current); make that first call before any stream capture.  All
+ * calls share the array and it keeps the last call's contents, so calls that
+ * overlap on the GPU (other streams, other threads) race: serialise them.
+ * Errors: DNNMG_ERR_ARG, DNNMG_ERR_CUDA, DNNMG_ERR_NUMERICAL (singular
+ * matrix); the message is read with dnnmg_last_error(NULL). */
+int dnnmg_coarse_solve_noalloc(const dnnmg_config* cfg, const double* vbar, const double* b,
+                               double* x, void* stream);
 
 /* Per-stage device timers (tracing).  Stages: */
 #define DNNMG_STAGE_VANKA_PASS 0    /* one colour pass of the Vanka smoother */

@@ -126,7 +126,11 @@ template Sten<double> make_sten<double>(double, const dnnmg_config&);
 // C ABI
 
 namespace {
-thread_local std::string g_setup_error;  // message of this thread's last failed setup
+thread_local std::string g_setup_error;  // message of this thread's last context-free failure
+}
+
+namespace dnnmg {
+void set_thread_error(const char* msg) { g_setup_error = msg; }
 }
 
 extern "C" {

@@ -230,7 +230,74 @@ __global__ void __launch_bounds__(32 * kSolveWarps)
   if (lane == 0) x[lidx(g, r)] = (T)acc;
 }
 
+// x = (LU)^{-1} b with the factors and pivots of band_lu_kernel; one block,
+// b and x in the [3][nn] layout of the level, work in shared memory.
+__global__ void __launch_bounds__(1024)
+    band_solve_kernel(Grid g, const double* __restrict__ ab, const int* __restrict__ piv,
+                      const double* __restrict__ b, double* __restrict__ x) {
+  const Band bd = band_of(g);
+  extern __shared__ double sx[];
+  const int tid = threadIdx.x;
+  for (int p = tid; p < bd.n; p += blockDim.x) sx[p] = b[lidx(g, p)];
+  __syncthreads();
+  for (int k = 0; k < bd.n; ++k) {
+    const int p = piv[k];
+    if (tid == 0 && p != k) {
+      const double t = sx[k];
+      sx[k] = sx[p];
+      sx[p] = t;
+    }
+    __syncthreads();
+    const double xk = sx[k];
+    const int rmax = min(bd.n - 1, k + bd.kl);
+    for (int r = k + 1 + tid; r <= rmax; r += blockDim.x)
+      sx[r] -= ab[(size_t)r * bd.W + (k - r + bd.kl)] * xk;
+    __syncthreads();
+  }
+  __shared__ double red[32];
+  for (int k = bd.n - 1; k >= 0; --k) {
+    const int cmax = min(bd.n - 1, k + bd.ku + bd.kl);
+    double acc = 0.0;
+    for (int c2 = k + 1 + tid; c2 <= cmax; c2 += blockDim.x)
+      acc += ab[(size_t)k * bd.W + (c2 - k + bd.kl)] * sx[c2];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((tid & 31) == 0) red[tid >> 5] = acc;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+      sx[k] = (sx[k] - t) / ab[(size_t)k * bd.W + bd.kl];
+    }
+    __syncthreads();
+  }
+  for (int p = tid; p < bd.n; p += blockDim.x) x[lidx(g, p)] = sx[p];
+}
+
 }  // namespace
+
+size_t coarse_band_doubles(const Grid& g) {
+  const Band bd = band_of(g);
+  return (size_t)bd.n * bd.W;
+}
+
+void launch_coarse_lu(const Grid& g, const Sten<double>& s, const double* vb, double* band,
+                      int* piv, int* status, cudaStream_t st) {
+  const Band bd = band_of(g);
+  note_launch();
+  assemble_kernel<<<cdiv(bd.n, 128), 128, 0, st>>>(g, s, vb, band);
+  const size_t win_bytes = sizeof(double) * kWin * bd.W;
+  cudaFuncSetAttribute(band_lu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)win_bytes);
+  note_launch();
+  band_lu_kernel<<<1, kLUThreads, win_bytes, st>>>(g, band, piv, status);
+}
+
+void launch_coarse_lu_solve(const Grid& g, const double* band, const int* piv, const double* b,
+                            double* x, cudaStream_t st) {
+  const Band bd = band_of(g);
+  note_launch();
+  band_solve_kernel<<<1, 1024, sizeof(double) * bd.n, st>>>(g, band, piv, b, x);
+}
 
 bool coarse_supported(const Grid& g) {
   const Band bd = band_of(g);

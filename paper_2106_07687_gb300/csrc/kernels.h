@@ -63,6 +63,13 @@ inline int vanka_slots(const Grid& g) { return (g.nx / 2 + 1) * (g.ny / 2 + 1); 
 // unknowns in band order).  `work` needs coarse_work_doubles(g) doubles.
 size_t coarse_work_doubles(const Grid& g);
 bool coarse_supported(const Grid& g);  // band fits the shared-memory window
+// Assemble + factor into caller-provided band storage (coarse_band_doubles(g)
+// doubles) and pivots (3 nn ints), and solve with those factors.
+size_t coarse_band_doubles(const Grid& g);
+void launch_coarse_lu(const Grid& g, const Sten<double>& s, const double* vb, double* band,
+                      int* piv, int* status, cudaStream_t st);
+void launch_coarse_lu_solve(const Grid& g, const double* band, const int* piv, const double* b,
+                            double* x, cudaStream_t st);
 void launch_coarse_factor(const Grid& g, const Sten<double>& s, const double* vb, double* work,
                           double* Ainv, int* status, cudaStream_t st);
 // x = Ainv b, b and x in the [3][nn] layout of the level
