@@ -165,6 +165,43 @@ int dnnmg_residual(dnnmg_ctx* ctx, const double* x, const double* f, double* r);
  * taken), DNNMG_ERR_NUMERICAL on NaN/Inf. */
 int dnnmg_step(dnnmg_ctx* ctx, int mode, dnnmg_step_stats* stats);
 
+/* ---- patch network (Sec. 2.2, Sec. 3.1, Table 1) ------------------------------
+ * Two stacked GRU cells (hidden 64, PyTorch gate convention r, z, n) and a
+ * dense head Linear(64, 128) + ReLU + Linear(128, C_out), applied to every
+ * patch independently.  With one replaced level a patch is one level-L cell:
+ * C_in = 40 inputs (prolongated velocity u, v and fine velocity residual
+ * r_u, r_v at its 3x3 fine nodes, then 4 geometry/flow features), C_out = 18
+ * outputs (velocity correction u, v at the 3x3 nodes).  Weights are BF16 on
+ * the tensor cores with FP32 accumulation; the hidden state is FP32.
+ * Flat FP32 parameter order (PyTorch's): per GRU layer W_ih [192][C_l],
+ * W_hh [192][64], b_ih [192], b_hh [192]; then W1 [128][64], b1 [128],
+ * W2 [C_out][128], b2 [C_out].  A new context has all weights zero. */
+
+/* Number of network parameters (55,954 for C_in = 40, C_out = 18). */
+size_t dnnmg_num_params(const dnnmg_ctx* ctx);
+
+/* Network input and output widths of the context. */
+int dnnmg_net_dims(const dnnmg_ctx* ctx, int* c_in, int* c_out);
+
+/* Copy the FP32 parameters from / to HOST memory (dnnmg_num_params floats).
+ * set_weights re-packs the BF16 tensor-core copy. */
+int dnnmg_set_weights(dnnmg_ctx* ctx, const float* w);
+int dnnmg_get_weights(dnnmg_ctx* ctx, float* w);
+
+/* One recurrent step of the network for P patches (Algorithm 1 line 7):
+ *   x   : device [P][C_in] bfloat16 (raw uint16 bits), normalised inputs
+ *   h   : device [2][P][64] float, hidden state, updated in place
+ *   out : device [P][C_out] float, predicted correction
+ * P = 0 is a no-op.  Errors: DNNMG_ERR_ARG (unsupported network shape),
+ * DNNMG_ERR_TIMEOUT (a tensor-core completion wait hit its bound). */
+int dnnmg_patch_infer(dnnmg_ctx* ctx, const uint16_t* x, float* h, float* out, int P);
+
+/* C = A B^T on the tensor cores: A device [M][K], B device [N][K] bfloat16
+ * row-major, C device [M][N] float row-major; M % 128 == 0,
+ * 16 <= N <= 256 with N % 16 == 0, K % 16 == 0 (else DNNMG_ERR_ARG). */
+int dnnmg_gemm_bf16(dnnmg_ctx* ctx, const uint16_t* A, const uint16_t* B, float* C, int M, int N,
+                    int K);
+
 /* Direct solve of the coarsest multigrid level without any device allocation
  * (the paper has no counterpart: this is a deployment variant).
  *

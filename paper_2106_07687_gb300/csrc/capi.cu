@@ -256,4 +256,37 @@ int dnnmg_profile_read(dnnmg_ctx* ctx, int stage, int level, int64_t* launches, 
 
 uint64_t dnnmg_kernel_launches(void) { return dnnmg::launches(); }
 
+size_t dnnmg_num_params(const dnnmg_ctx* ctx) { return ctx ? ctx->nd.num_params() : 0; }
+
+int dnnmg_net_dims(const dnnmg_ctx* ctx, int* c_in, int* c_out) {
+  if (!ctx || !c_in || !c_out) return DNNMG_ERR_ARG;
+  *c_in = ctx->nd.c_in;
+  *c_out = ctx->nd.c_out;
+  return DNNMG_OK;
+}
+
+int dnnmg_set_weights(dnnmg_ctx* ctx, const float* w) {
+  if (!ctx || !w) return DNNMG_ERR_ARG;
+  return ctx->set_weights(w);
+}
+
+int dnnmg_get_weights(dnnmg_ctx* ctx, float* w) {
+  if (!ctx || !w) return DNNMG_ERR_ARG;
+  return ctx->get_weights(w);
+}
+
+int dnnmg_patch_infer(dnnmg_ctx* ctx, const uint16_t* x, float* h, float* out, int P) {
+  if (!ctx || (P > 0 && (!x || !h || !out))) return DNNMG_ERR_ARG;
+  return ctx->patch_infer(x, h, out, P);
+}
+
+int dnnmg_gemm_bf16(dnnmg_ctx* ctx, const uint16_t* A, const uint16_t* B, float* C, int M, int N,
+                    int K) {
+  if (!ctx || !A || !B || !C) return DNNMG_ERR_ARG;
+  if (!ctx->net_status) return ctx->fail(DNNMG_ERR_STATE, "no tensor-core status word");
+  if (dnnmg::launch_umma_gemm(A, B, C, M, N, K, ctx->net_status, ctx->st))
+    return ctx->fail(DNNMG_ERR_ARG, "gemm: need M % 128 == 0, 16 <= N <= 256, N % 16 == 0, K % 16 == 0");
+  return ctx->net_check("gemm");
+}
+
 }  // extern "C"

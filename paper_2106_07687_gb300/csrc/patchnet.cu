@@ -1,0 +1,434 @@
+// Patch network on fifth-generation tensor cores (Sec. 2.2 / Sec. 3.1: GRU
+// cells with memory per patch, then dense layers; inputs and outputs per
+// patch as in Algorithm 1 line 7).
+//
+// patchnet_forward_kernel: persistent, one 128-patch tile at a time per CTA,
+// 128 threads, thread t owns patch row t of the tile (TMEM lane t).  All
+// weights live in shared memory as BF16 K-major operands; per GRU layer the
+// tensor core accumulates in TMEM (256 FP32 columns)
+//   [0,128)   x W_ih[r,z]^T + h W_hh[r,z]^T      (gates r and z)
+//   [128,192) x W_ih[n]^T                        (input part of gate n)
+//   [192,256) h W_hh[n]^T                        (hidden part of gate n)
+// and each thread applies the gate nonlinearities to its row in registers,
+// writing the new hidden state (FP32) to HBM and (BF16) to shared memory as
+// the next GEMM's operand.  The dense head reuses TMEM columns [0,128) and
+// [128,128+N2).
+#include "kernels.h"
+#include "patchnet.cuh"
+#include "umma.cuh"
+
+namespace dnnmg {
+
+namespace {
+
+using namespace umma;
+
+constexpr uint32_t kWaitPolls = 1u << 22;  // bound of every mbarrier wait
+constexpr int kTile = 128;
+
+__device__ __forceinline__ uint16_t f2bf(float v) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+
+__device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + __expf(-x)); }
+
+// -- packing -----------------------------------------------------------------
+__global__ void pack_block_kernel(const float* __restrict__ src, int ld, int row0, int rows_valid,
+                                  int cols_valid, int R, int K, uint16_t* __restrict__ dst) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < R * K; idx += gridDim.x * blockDim.x) {
+    const int r = idx / K, k = idx % K;
+    const float v = (r < rows_valid && k < cols_valid) ? src[(size_t)(row0 + r) * ld + k] : 0.0f;
+    dst[kmajor_offset(r, k, K) >> 1] = f2bf(v);
+  }
+}
+
+__global__ void pack_bias_kernel(const float* __restrict__ w, NetDims d, float* __restrict__ bias) {
+  const int H = d.hidden;
+  size_t off = 0;
+  for (int l = 0; l < d.layers; ++l) {
+    const int c = l == 0 ? d.c_in : H;
+    const float* bih = w + off + (size_t)3 * H * c + (size_t)3 * H * H;
+    const float* bhh = bih + 3 * H;
+    for (int j = threadIdx.x; j < H; j += blockDim.x) {
+      float* b = bias + (size_t)l * 4 * H;
+      b[j] = bih[j] + bhh[j];
+      b[H + j] = bih[H + j] + bhh[H + j];
+      b[2 * H + j] = bih[2 * H + j];
+      b[3 * H + j] = bhh[2 * H + j];
+    }
+    off += (size_t)3 * H * c + (size_t)3 * H * H + 6 * H;
+  }
+  const float* b1 = w + off + (size_t)d.mlp * H;
+  const float* b2 = b1 + d.mlp + (size_t)d.c_out * d.mlp;
+  float* ob = bias + (size_t)d.layers * 4 * H;
+  for (int j = threadIdx.x; j < d.mlp; j += blockDim.x) ob[j] = b1[j];
+  for (int j = threadIdx.x; j < d.nout(); j += blockDim.x) ob[d.mlp + j] = j < d.c_out ? b2[j] : 0.f;
+}
+
+// -- shared-memory plan of the forward kernel ---------------------------------
+struct FwdSmem {
+  uint32_t w, bias, x, h0, h1, t, m, bar, tmem, total;
+  static __host__ __device__ uint32_t up(uint32_t v) { return (v + 127u) & ~127u; }
+  static __host__ __device__ FwdSmem of(const NetDims& d, size_t w_elems) {
+    FwdSmem s{};
+    uint32_t o = 0;
+    s.w = o;    o = up(o + (uint32_t)(w_elems * 2));
+    s.bias = o; o = up(o + (uint32_t)((d.layers * 4 * d.hidden + d.mlp + d.nout()) * 4));
+    s.x = o;    o = up(o + kTile * d.kx0() * 2);
+    s.h0 = o;   o = up(o + kTile * 64 * 2);
+    s.h1 = o;   o = up(o + kTile * 64 * 2);
+    s.t = o;    o = up(o + kTile * 64 * 2);
+    s.m = o;    o = up(o + kTile * 128 * 2);
+    s.bar = o;  o += 16;
+    s.tmem = o; o += 16;
+    s.total = o;
+    return s;
+  }
+};
+
+// write 16 consecutive values of row r (columns k0..k0+15) as BF16 operand
+__device__ __forceinline__ void store_row16(uint8_t* buf, int r, int k0, int K, const float* v) {
+  uint32_t p[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) p[i] = (uint32_t)f2bf(v[2 * i]) | ((uint32_t)f2bf(v[2 * i + 1]) << 16);
+  *reinterpret_cast<uint4*>(buf + kmajor_offset(r, k0, K)) = make_uint4(p[0], p[1], p[2], p[3]);
+  *reinterpret_cast<uint4*>(buf + kmajor_offset(r, k0 + 8, K)) = make_uint4(p[4], p[5], p[6], p[7]);
+}
+
+// Issue D(+)= A * B^T over K (in 16-wide slices) for one accumulator.
+__device__ __forceinline__ void mma_run(uint32_t d_tmem, uint32_t a_addr, int a_K, uint32_t b_addr,
+                                        int b_K, int N, int K, bool acc_first) {
+  const uint32_t id = idesc_bf16(kTile, N);
+  for (int ks = 0; ks < K / 16; ++ks) {
+    const uint64_t da = smem_desc(a_addr + ks * 256, 128, (a_K / 8) * 128);
+    const uint64_t db = smem_desc(b_addr + ks * 256, 128, (b_K / 8) * 128);
+    mma_bf16(d_tmem, da, db, id, (ks > 0 || acc_first) ? 1u : 0u);
+  }
+}
+
+// One GRU layer's epilogue for this thread's row: gates from TMEM, new
+// hidden state into hreg (FP32), `next` (BF16 operand) and HBM.
+__device__ __forceinline__ void gru_epilogue(uint32_t tm, const float* bias, float* hreg,
+                                             uint8_t* next, int row, float* hout, bool valid) {
+  constexpr int H = 64;
+#pragma unroll 1
+  for (int c = 0; c < 4; ++c) {
+    float rp[16], zp[16], ip[16], hp[16];
+    tmem_ld16(tm + c * 16, rp);
+    tmem_ld16(tm + 64 + c * 16, zp);
+    tmem_ld16(tm + 128 + c * 16, ip);
+    tmem_ld16(tm + 192 + c * 16, hp);
+    float hn[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int j = c * 16 + i;
+      const float r = sigmoidf_(rp[i] + bias[j]);
+      const float z = sigmoidf_(zp[i] + bias[H + j]);
+      const float n = tanhf(ip[i] + bias[2 * H + j] + r * (hp[i] + bias[3 * H + j]));
+      hn[i] = (1.0f - z) * n + z * hreg[j];
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) hreg[c * 16 + i] = hn[i];
+    store_row16(next, row, c * 16, H, hn);
+    if (valid) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        reinterpret_cast<float4*>(hout)[c * 4 + q] =
+            make_float4(hn[4 * q], hn[4 * q + 1], hn[4 * q + 2], hn[4 * q + 3]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kTile, 1)
+    patchnet_forward_kernel(NetDims d, PackLayout L, const uint16_t* __restrict__ wimg,
+                            const float* __restrict__ bias_g, const uint16_t* __restrict__ x,
+                            const float* __restrict__ h, float* __restrict__ h_out,
+                            float* __restrict__ out, int P, int* status) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  const FwdSmem S = FwdSmem::of(d, L.total);
+  const int t = threadIdx.x, warp = t >> 5;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + S.bar);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S.tmem);
+  float* bias = reinterpret_cast<float*>(sm + S.bias);
+
+  // weights and biases: one copy per CTA
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(wimg);
+    uint4* dst = reinterpret_cast<uint4*>(sm + S.w);
+    for (size_t i = t; i < L.total / 8; i += kTile) dst[i] = src[i];
+    const int nb = d.layers * 4 * d.hidden + d.mlp + d.nout();
+    for (int i = t; i < nb; i += kTile) bias[i] = bias_g[i];
+  }
+  if (warp == 0) tmem_alloc(tslot, 256);
+  if (t == 0) mbar_init(bar, 1);
+  fence_async_smem();
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tbase = *tslot;
+  const uint32_t tm = tbase + ((uint32_t)(warp * 32) << 16);  // this warp's lanes
+  const uint32_t sbase = smem_u32(sm);
+  const int kx0 = d.kx0();
+  uint32_t phase = 0;
+  bool failed = false;
+  const int ntiles = (P + kTile - 1) / kTile;
+  const size_t HP = (size_t)P * 64;
+
+  for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
+    const int p = tile * kTile + t;
+    const bool valid = p < P;
+    // ---- stage the tile: x (BF16), h0 and h1 (FP32 registers + BF16 operands)
+    {
+      const uint4 zero = make_uint4(0, 0, 0, 0);
+      for (int q = 0; q < kx0 / 8; ++q) {
+        uint4 v = zero;
+        if (valid && q * 8 < d.c_in) v = reinterpret_cast<const uint4*>(x + (size_t)p * d.c_in)[q];
+        *reinterpret_cast<uint4*>(sm + S.x + kmajor_offset(t, q * 8, kx0)) = v;
+      }
+    }
+    float h0r[64], h1r[64];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      float4 a = make_float4(0, 0, 0, 0), b = a;
+      if (valid) {
+        a = reinterpret_cast<const float4*>(h + (size_t)p * 64)[q];
+        b = reinterpret_cast<const float4*>(h + HP + (size_t)p * 64)[q];
+      }
+      h0r[4 * q] = a.x, h0r[4 * q + 1] = a.y, h0r[4 * q + 2] = a.z, h0r[4 * q + 3] = a.w;
+      h1r[4 * q] = b.x, h1r[4 * q + 1] = b.y, h1r[4 * q + 2] = b.z, h1r[4 * q + 3] = b.w;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      store_row16(sm + S.h0, t, c * 16, 64, h0r + c * 16);
+      store_row16(sm + S.h1, t, c * 16, 64, h1r + c * 16);
+    }
+    // ---- two GRU layers
+#pragma unroll 1
+    for (int l = 0; l < 2; ++l) {
+      fence_async_smem();
+      fence_before_sync();
+      __syncthreads();
+      const uint32_t ax = sbase + (l == 0 ? S.x : S.t);
+      const int kx = l == 0 ? kx0 : 64;
+      const uint32_t ah = sbase + (l == 0 ? S.h0 : S.h1);
+      if (t == 0) {
+        fence_after_sync();
+        mma_run(tbase + 0, ax, kx, sbase + S.w + 2 * L.rz[l], kx, 128, kx, false);
+        mma_run(tbase + 0, ah, 64, sbase + S.w + 2 * L.hrz[l], 64, 128, 64, true);
+        mma_run(tbase + 128, ax, kx, sbase + S.w + 2 * L.in[l], kx, 64, kx, false);
+        mma_run(tbase + 192, ah, 64, sbase + S.w + 2 * L.hn[l], 64, 64, 64, false);
+        mma_commit(bar);
+      }
+      if (!mbar_wait(bar, phase, kWaitPolls)) failed = true;
+      phase ^= 1;
+      if (__syncthreads_or(failed)) {
+        failed = true;
+        break;
+      }
+      fence_after_sync();
+      // layer 0 writes its new state into S.t (layer 1 input); layer 1 into
+      // S.h0 (free after layer 0) as the dense head's input
+      gru_epilogue(tm, bias + l * 4 * 64, l == 0 ? h0r : h1r, sm + (l == 0 ? S.t : S.h0), t,
+                   h_out + l * HP + (size_t)p * 64, valid);
+    }
+    if (failed) break;
+    // ---- dense head: relu(h1 W1^T + b1) W2^T + b2
+    fence_async_smem();
+    fence_before_sync();
+    __syncthreads();
+    if (t == 0) {
+      fence_after_sync();
+      mma_run(tbase + 0, sbase + S.h0, 64, sbase + S.w + 2 * L.w1, 64, 128, 64, false);
+      mma_commit(bar);
+    }
+    if (!mbar_wait(bar, phase, kWaitPolls)) failed = true;
+    phase ^= 1;
+    if (__syncthreads_or(failed)) {
+      failed = true;
+      break;
+    }
+    fence_after_sync();
+    const float* b1 = bias + 2 * 4 * 64;
+#pragma unroll 1
+    for (int c = 0; c < 8; ++c) {
+      float v[16];
+      tmem_ld16(tm + c * 16, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] + b1[c * 16 + i], 0.0f);
+      store_row16(sm + S.m, t, c * 16, 128, v);
+    }
+    fence_async_smem();
+    fence_before_sync();
+    __syncthreads();
+    const int n2 = d.nout();
+    if (t == 0) {
+      fence_after_sync();
+      mma_run(tbase + 128, sbase + S.m, 128, sbase + S.w + 2 * L.w2, 128, n2, 128, false);
+      mma_commit(bar);
+    }
+    if (!mbar_wait(bar, phase, kWaitPolls)) failed = true;
+    phase ^= 1;
+    if (__syncthreads_or(failed)) {
+      failed = true;
+      break;
+    }
+    fence_after_sync();
+    const float* b2 = b1 + d.mlp;
+#pragma unroll 1
+    for (int c = 0; c < n2 / 16; ++c) {
+      float v[16];
+      tmem_ld16(tm + 128 + c * 16, v);
+      if (valid)
+        for (int i = 0; i < 16; ++i) {
+          const int j = c * 16 + i;
+          if (j < d.c_out) out[(size_t)p * d.c_out + j] = v[i] + b2[j];
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+  }
+  if (failed) {
+    if (t == 0) atomicOr(status, 4);
+    // let MMAs still in flight finish before the accumulator is released
+    mbar_wait(bar, phase, kWaitPolls);
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after_sync();
+    tmem_dealloc(tbase, 256);
+  }
+}
+
+// -- generic GEMM: C = A B^T ----------------------------------------------------
+constexpr int kKC = 64;
+__global__ void __launch_bounds__(kTile, 1)
+    umma_gemm_kernel(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B,
+                     float* __restrict__ C, int M, int N, int K, uint32_t ncols, int* status) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  uint8_t* sa = sm;                       // 128 x kKC
+  uint8_t* sb = sm + kTile * kKC * 2;     // N x kKC
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sb + 256 * kKC * 2);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  const int t = threadIdx.x, warp = t >> 5;
+  if (warp == 0) tmem_alloc(tslot, ncols);
+  if (t == 0) mbar_init(bar, 1);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tbase = *tslot;
+  const int row0 = blockIdx.x * kTile;
+  uint32_t phase = 0;
+  bool failed = false;
+  for (int k0 = 0; k0 < K && !failed; k0 += kKC) {
+    const int kc = min(kKC, K - k0);
+    for (int e = t; e < kTile * (kc / 8); e += kTile) {
+      const int r = e / (kc / 8), q = e % (kc / 8);
+      *reinterpret_cast<uint4*>(sa + kmajor_offset(r, q * 8, kc)) =
+          *reinterpret_cast<const uint4*>(A + (size_t)(row0 + r) * K + k0 + q * 8);
+    }
+    for (int e = t; e < N * (kc / 8); e += kTile) {
+      const int r = e / (kc / 8), q = e % (kc / 8);
+      *reinterpret_cast<uint4*>(sb + kmajor_offset(r, q * 8, kc)) =
+          *reinterpret_cast<const uint4*>(B + (size_t)r * K + k0 + q * 8);
+    }
+    fence_async_smem();
+    fence_before_sync();
+    __syncthreads();
+    if (t == 0) {
+      fence_after_sync();
+      mma_run(tbase, smem_u32(sa), kc, smem_u32(sb), kc, N, kc, k0 > 0);
+      mma_commit(bar);
+    }
+    if (!mbar_wait(bar, phase, kWaitPolls)) failed = true;
+    phase ^= 1;
+    failed = __syncthreads_or(failed);
+    fence_after_sync();
+  }
+  if (!failed) {
+    const int r = row0 + t;
+    for (int c = 0; c < N / 16; ++c) {
+      float v[16];
+      tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + c * 16, v);
+      for (int i = 0; i < 16; ++i) C[(size_t)r * N + c * 16 + i] = v[i];
+    }
+  } else {
+    if (t == 0) atomicOr(status, 4);
+    mbar_wait(bar, phase, kWaitPolls);
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after_sync();
+    tmem_dealloc(tbase, ncols);
+  }
+}
+
+}  // namespace
+
+bool net_supported(const NetDims& d) {
+  if (d.hidden != 64 || d.layers != 2 || d.mlp != 128 || d.c_in % 8 != 0 || d.c_out > 64)
+    return false;
+  const PackLayout L = PackLayout::of(d);
+  return FwdSmem::of(d, L.total).total <= 227 * 1024;
+}
+
+void launch_pack_weights(const NetDims& d, const float* w, PackedNet& pk, cudaStream_t st) {
+  const PackLayout L = PackLayout::of(d);
+  const int H = d.hidden;
+  size_t off = 0;
+  for (int l = 0; l < 2; ++l) {
+    const int c = l == 0 ? d.c_in : H;
+    const float* Wih = w + off;
+    const float* Whh = Wih + (size_t)3 * H * c;
+    const int kx = L.kx[l];
+    note_launch();
+    pack_block_kernel<<<64, 256, 0, st>>>(Wih, c, 0, 128, c, 128, kx, pk.w + L.rz[l]);
+    note_launch();
+    pack_block_kernel<<<64, 256, 0, st>>>(Wih, c, 128, 64, c, 64, kx, pk.w + L.in[l]);
+    note_launch();
+    pack_block_kernel<<<64, 256, 0, st>>>(Whh, H, 0, 128, H, 128, 64, pk.w + L.hrz[l]);
+    note_launch();
+    pack_block_kernel<<<64, 256, 0, st>>>(Whh, H, 128, 64, H, 64, 64, pk.w + L.hn[l]);
+    off += (size_t)3 * H * c + (size_t)3 * H * H + 6 * H;
+  }
+  const float* W1 = w + off;
+  const float* W2 = W1 + (size_t)d.mlp * H + d.mlp;
+  note_launch();
+  pack_block_kernel<<<64, 256, 0, st>>>(W1, H, 0, 128, H, 128, 64, pk.w + L.w1);
+  note_launch();
+  pack_block_kernel<<<64, 256, 0, st>>>(W2, d.mlp, 0, d.c_out, d.mlp, d.nout(), 128, pk.w + L.w2);
+  note_launch();
+  pack_bias_kernel<<<1, 128, 0, st>>>(w, d, pk.bias);
+}
+
+void launch_patchnet_forward(const NetDims& d, const PackedNet& pk, const uint16_t* x,
+                             const float* h, float* h_out, float* out, int P, int* status,
+                             cudaStream_t st) {
+  if (P <= 0) return;
+  const PackLayout L = PackLayout::of(d);
+  const FwdSmem S = FwdSmem::of(d, L.total);
+  cudaFuncSetAttribute(patchnet_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)S.total);
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int ntiles = (P + kTile - 1) / kTile;
+  note_launch();
+  patchnet_forward_kernel<<<ntiles < sms ? ntiles : sms, kTile, S.total, st>>>(
+      d, L, pk.w, pk.bias, x, h, h_out, out, P, status);
+}
+
+int launch_umma_gemm(const uint16_t* A, const uint16_t* B, float* C, int M, int N, int K,
+                     int* status, cudaStream_t st) {
+  if (M <= 0 || M % kTile || N < 16 || N > 256 || N % 16 || K < 16 || K % 16) return 1;
+  uint32_t ncols = 32;
+  while (ncols < (uint32_t)N) ncols <<= 1;
+  const size_t smem = (size_t)kTile * kKC * 2 + (size_t)256 * kKC * 2 + 64;
+  cudaFuncSetAttribute(umma_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  note_launch();
+  umma_gemm_kernel<<<M / kTile, kTile, smem, st>>>(A, B, C, M, N, K, ncols, status);
+  return 0;
+}
+
+}  // namespace dnnmg

@@ -1,0 +1,75 @@
+// Patch network of DNN-MG (Sec. 2.2, Sec. 3.1): two stacked GRU cells with
+// hidden size 64 and a dense head Linear(64 -> 128) + ReLU + Linear(128 ->
+// C_out), evaluated for every patch with tcgen05 tensor-core GEMMs.
+//
+// Flat FP32 parameter order (PyTorch's GRU order, gate rows r, z, n):
+//   per layer l: W_ih (192 x C_l), W_hh (192 x 64), b_ih (192), b_hh (192)
+//   then W1 (128 x 64), b1 (128), W2 (C_out x 128), b2 (C_out)
+// with C_0 = C_in (40 for one replaced level) and C_1 = 64.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace dnnmg {
+
+struct NetDims {
+  int c_in = 40, hidden = 64, layers = 2, mlp = 128, c_out = 18;
+  __host__ __device__ int kx0() const { return (c_in + 15) / 16 * 16; }  // padded K of layer 0
+  __host__ __device__ int nout() const {
+    return (c_out + 15) / 16 * 16 < 32 ? 32 : (c_out + 15) / 16 * 16;
+  }
+  __host__ __device__ size_t num_params() const {
+    size_t n = 0;
+    for (int l = 0; l < layers; ++l) {
+      const int c = l == 0 ? c_in : hidden;
+      n += (size_t)3 * hidden * c + (size_t)3 * hidden * hidden + 6 * hidden;
+    }
+    return n + (size_t)mlp * hidden + mlp + (size_t)c_out * mlp + c_out;
+  }
+};
+
+// Packed BF16 operand image of the weights (the shared-memory layout of the
+// forward kernel, copied verbatim) and FP32 biases.
+struct PackedNet {
+  uint16_t* w = nullptr;     // BF16 operand image
+  float* bias = nullptr;     // [layers][4][64] (r: b_ir+b_hr, z: b_iz+b_hz, b_in, b_hn), b1, b2
+  size_t w_elems = 0;
+  size_t bias_elems = 0;
+};
+
+// element offsets of the packed operand blocks
+struct PackLayout {
+  size_t rz[2], in[2], hrz[2], hn[2], w1, w2, total;
+  int kx[2];
+  __host__ __device__ static PackLayout of(const NetDims& d) {
+    PackLayout p{};
+    size_t o = 0;
+    for (int l = 0; l < 2; ++l) {
+      p.kx[l] = l == 0 ? d.kx0() : d.hidden;
+      p.rz[l] = o;  o += (size_t)128 * p.kx[l];
+      p.in[l] = o;  o += (size_t)64 * p.kx[l];
+      p.hrz[l] = o; o += (size_t)128 * 64;
+      p.hn[l] = o;  o += (size_t)64 * 64;
+    }
+    p.w1 = o; o += (size_t)128 * 64;
+    p.w2 = o; o += (size_t)d.nout() * 128;
+    p.total = o;
+    return p;
+  }
+};
+
+bool net_supported(const NetDims& d);
+// master FP32 flat weights -> packed BF16 operands + fused biases
+void launch_pack_weights(const NetDims& d, const float* w, PackedNet& pk, cudaStream_t st);
+// one recurrent step for P patches: x [P][C_in] BF16, h [2][P][64] FP32 in,
+// h_out [2][P][64] (may alias h), out [P][C_out] FP32
+void launch_patchnet_forward(const NetDims& d, const PackedNet& pk, const uint16_t* x,
+                             const float* h, float* h_out, float* out, int P, int* status,
+                             cudaStream_t st);
+// C[M x N] = A[M x K] * B[N x K]^T (BF16 row-major inputs, FP32 row-major out)
+int launch_umma_gemm(const uint16_t* A, const uint16_t* B, float* C, int M, int N, int K,
+                     int* status, cudaStream_t st);
+
+}  // namespace dnnmg

@@ -333,7 +333,73 @@ int dnnmg_ctx::init() {
   if (int rc = check("setup")) return rc;
   solver = make_solver(this);
   if (!solver) return err.empty() ? fail(DNNMG_ERR_CUDA, "solver setup failed") : DNNMG_ERR_CUDA;
+  if (int rc = init_net()) return rc;
   return check("setup");
+}
+
+// Network dimensions follow the patch: one level-L cell covers
+// (2^r + 1)^2 nodes of level L + r; inputs are the prolongated velocity and
+// the fine residual at those nodes plus 4 geometry features.
+int dnnmg_ctx::init_net() {
+  const int r = cfg.replaced_levels > 0 ? cfg.replaced_levels : 1;
+  const int k = (1 << r) + 1;
+  nd.c_in = 4 * k * k + 4;
+  nd.c_out = 2 * k * k;
+  nd.hidden = cfg.hidden;
+  nd.layers = cfg.gru_layers;
+  nd.mlp = cfg.mlp_width;
+  net_ok = net_supported(nd);
+  if (!net_ok) return DNNMG_OK;  // network calls report the unsupported shape
+  const PackLayout L = PackLayout::of(nd);
+  w_master = mem.alloc<float>(nd.num_params());
+  pk.w = mem.alloc<uint16_t>(L.total);
+  pk.w_elems = L.total;
+  pk.bias_elems = (size_t)nd.layers * 4 * nd.hidden + nd.mlp + nd.nout();
+  pk.bias = mem.alloc<float>(pk.bias_elems);
+  net_status = mem.alloc<int>(4);
+  if (!mem.ok()) return fail(DNNMG_ERR_CUDA, "device allocation failed");
+  cudaMemsetAsync(w_master, 0, sizeof(float) * nd.num_params(), st);
+  cudaMemsetAsync(net_status, 0, sizeof(int) * 4, st);
+  launch_pack_weights(nd, w_master, pk, st);
+  return check("network setup");
+}
+
+int dnnmg_ctx::net_check(const char* what) {
+  if (int rc = check(what)) return rc;
+  int s = 0;
+  cudaMemcpyAsync(h_scalars, net_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return check(what);
+  std::memcpy(&s, h_scalars, sizeof(int));
+  if (s & 4) {
+    cudaMemsetAsync(net_status, 0, sizeof(int), st);
+    return fail(DNNMG_ERR_TIMEOUT, std::string(what) + ": tensor-core wait timed out");
+  }
+  return DNNMG_OK;
+}
+
+int dnnmg_ctx::set_weights(const float* w_host) {
+  if (!net_ok) return fail(DNNMG_ERR_ARG, "network shape not supported");
+  cudaMemcpyAsync(w_master, w_host, sizeof(float) * nd.num_params(), cudaMemcpyHostToDevice, st);
+  launch_pack_weights(nd, w_master, pk, st);
+  cudaStreamSynchronize(st);
+  return check("set_weights");
+}
+
+int dnnmg_ctx::get_weights(float* w_host) {
+  if (!net_ok) return fail(DNNMG_ERR_ARG, "network shape not supported");
+  cudaMemcpyAsync(w_host, w_master, sizeof(float) * nd.num_params(), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  return check("get_weights");
+}
+
+int dnnmg_ctx::patch_infer(const uint16_t* x, float* h, float* out, int P) {
+  if (!net_ok) return fail(DNNMG_ERR_ARG, "network shape not supported");
+  if (P < 0) return fail(DNNMG_ERR_ARG, "negative patch count");
+  if (P == 0) return DNNMG_OK;
+  const int p = prof.begin(DNNMG_STAGE_NETWORK, 0, st);
+  launch_patchnet_forward(nd, pk, x, h, h, out, P, net_status, st);
+  prof.end(p, st);
+  return net_check("patch_infer");
 }
 
 double dnnmg_ctx::norm64(const double* v, size_t n) {

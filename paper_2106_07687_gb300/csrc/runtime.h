@@ -7,6 +7,7 @@
 
 #include "../../include/dnnmg.h"
 #include "kernels.h"
+#include "patchnet.cuh"
 
 namespace dnnmg {
 
@@ -142,6 +143,12 @@ struct dnnmg_ctx {
   double* h_scalars = nullptr; // pinned host scalars
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   dnnmg::Prof prof;
+  // patch network
+  dnnmg::NetDims nd{};
+  bool net_ok = false;
+  float* w_master = nullptr;   // FP32 flat parameters
+  dnnmg::PackedNet pk{};
+  int* net_status = nullptr;
 
   ~dnnmg_ctx();
   int init();
@@ -162,5 +169,10 @@ struct dnnmg_ctx {
   int vcycle_api(int level, const void* b, void* x, int precision);
   int residual_api(const double* x, const double* f, double* r);
   int step(int mode, dnnmg_step_stats* stats);
+  int init_net();
+  int set_weights(const float* w_host);
+  int get_weights(float* w_host);
+  int patch_infer(const uint16_t* x, float* h, float* out, int P);
+  int net_check(const char* what);
   int newton(const double* f, dnnmg_step_stats* st);
 };

@@ -63,6 +63,12 @@ def _declare(lib):
         "dnnmg_vcycle": ([P, ctypes.c_int, P, P, ctypes.c_int], ctypes.c_int),
         "dnnmg_residual": ([P, P, P, P], ctypes.c_int),
         "dnnmg_step": ([P, ctypes.c_int, P], ctypes.c_int),
+        "dnnmg_num_params": ([P], ctypes.c_size_t),
+        "dnnmg_net_dims": ([P, P, P], ctypes.c_int),
+        "dnnmg_set_weights": ([P, P], ctypes.c_int),
+        "dnnmg_get_weights": ([P, P], ctypes.c_int),
+        "dnnmg_patch_infer": ([P, P, P, P, ctypes.c_int], ctypes.c_int),
+        "dnnmg_gemm_bf16": ([P, P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -167,6 +173,43 @@ class Context:
         r = torch.empty_like(x) if r is None else r
         self._check(self.lib.dnnmg_residual(self.h, _ptr(x), _ptr(f), _ptr(r)))
         return r
+
+    # -- patch network ---------------------------------------------------
+    def num_params(self):
+        return int(self.lib.dnnmg_num_params(self.h))
+
+    def net_dims(self):
+        ci, co = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.dnnmg_net_dims(self.h, ctypes.byref(ci), ctypes.byref(co)))
+        return ci.value, co.value
+
+    def set_weights(self, w):
+        """w: host float32 array-like of num_params() values."""
+        t = torch.as_tensor(w, dtype=torch.float32).contiguous().cpu()
+        if t.numel() != self.num_params():
+            raise ValueError("wrong parameter count")
+        self._check(self.lib.dnnmg_set_weights(self.h, c_void_p(t.data_ptr())))
+
+    def get_weights(self):
+        t = torch.empty(self.num_params(), dtype=torch.float32)
+        self._check(self.lib.dnnmg_get_weights(self.h, c_void_p(t.data_ptr())))
+        return t
+
+    def patch_infer(self, x_bf16, h, out=None):
+        """x_bf16: cuda bfloat16 [P, C_in]; h: cuda float32 [2, P, 64] (updated)."""
+        P = x_bf16.shape[0]
+        out = torch.empty(P, self.net_dims()[1], dtype=torch.float32, device="cuda") \
+            if out is None else out
+        self._check(self.lib.dnnmg_patch_infer(self.h, _ptr(x_bf16), _ptr(h), _ptr(out), P))
+        return out
+
+    def gemm_bf16(self, A, B):
+        """C = A @ B.T on the tensor cores (A [M,K], B [N,K] cuda bfloat16)."""
+        M, K = A.shape
+        N = B.shape[0]
+        C = torch.empty(M, N, dtype=torch.float32, device="cuda")
+        self._check(self.lib.dnnmg_gemm_bf16(self.h, _ptr(A), _ptr(B), _ptr(C), M, N, K))
+        return C
 
     def step(self, mode=PLAIN):
         st = StepStats()
