@@ -81,7 +81,8 @@ typedef struct dnnmg_config {
   int32_t hidden;          /* GRU hidden size (64) */
   int32_t gru_layers;      /* stacked GRU cells (2) */
   int32_t mlp_width;       /* width of the hidden dense layer (128) */
-  int32_t reserved[8];
+  int32_t fallback_newton_its; /* DNN-MG step redone without the network if Newton needs more */
+  int32_t reserved[7];
 } dnnmg_config;
 
 /* Per-step statistics returned by dnnmg_step(). */
@@ -99,7 +100,8 @@ typedef struct dnnmg_step_stats {
  * newton_tol = 1e-10, gmres_rtol = 1e-4, omega = 0.8, eps_damp = 1,
  * obstacle at level-0 cell (2, 1), L = 3, coarse level 1, replaced_levels = 1,
  * FP64, newton_max = 20, gmres_m = 20, gmres_maxit = 200, V(2,2), GRU 2 x 64,
- * dense width 128.  Returns DNNMG_ERR_ARG if cfg is NULL. */
+ * dense width 128, fallback_newton_its = 8.  Returns DNNMG_ERR_ARG if cfg is
+ * NULL. */
 int dnnmg_default_config(dnnmg_config* cfg);
 
 /* Create a context: builds the level hierarchy coarse..L (and L+1..L+r for the
@@ -201,6 +203,30 @@ int dnnmg_patch_infer(dnnmg_ctx* ctx, const uint16_t* x, float* h, float* out, i
  * 16 <= N <= 256 with N % 16 == 0, K % 16 == 0 (else DNNMG_ERR_ARG). */
 int dnnmg_gemm_bf16(dnnmg_ctx* ctx, const uint16_t* A, const uint16_t* B, float* C, int M, int N,
                     int K);
+
+/* ---- DNN-MG state (Algorithm 1 lines 6-9) -----------------------------------
+ * A DNNMG_NET step ends with: v~ = P(v^L) on level L+1; the fine residual
+ * r = f - A(v~, P p^L) of Eq. 6 on level L+1 with f built from the previous
+ * corrected fine velocity; the patch inputs; one network step (the hidden
+ * state persists across steps); v_corr = v~ + d with d averaged over the
+ * patches sharing a node and zero on Dirichlet nodes; b^{L+1} = Rhs(v_corr) =
+ * (1/k) M v_corr; and b^L = R b^{L+1}, the velocity right-hand side of the
+ * next step.  Patches are the fluid cells of level L in cell order
+ * (j * nx + i). */
+
+/* Number of patches (fluid cells of level L). */
+int dnnmg_num_patches(const dnnmg_ctx* ctx);
+
+/* Per-feature standardisation of the network inputs, host arrays [C_in]:
+ * input = (feature - mean) / std.  Default mean 0, std 1. */
+int dnnmg_set_feature_stats(dnnmg_ctx* ctx, const float* mean, const float* std);
+
+/* Corrected fine velocity v_corr of the last DNN-MG step: device
+ * [2][nn of level L+1] doubles.  DNNMG_ERR_STATE before the first one. */
+int dnnmg_get_fine_velocity(dnnmg_ctx* ctx, double* v);
+
+/* Network inputs of the last DNN-MG step: device [P][C_in] bfloat16. */
+int dnnmg_get_patch_inputs(dnnmg_ctx* ctx, uint16_t* x);
 
 /* Direct solve of the coarsest multigrid level without any device allocation
  * (the paper has no counterpart: this is a deployment variant).

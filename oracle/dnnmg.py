@@ -107,3 +107,42 @@ def rhs_and_restrict(coarse, fine, levels_between, v_corr, prm):
         Pn = mg.prolongation_nodes(c, f)
         bL = np.concatenate([Pn.T @ bL[i * f.nn:(i + 1) * f.nn] for i in range(3)])
     return b, bL
+
+
+def time_step(levels, fine, x_old, state, spec, params, prm, opt, mean=None, std=None,
+              fallback_its=8, bf16=True):
+    """One DNN-MG time step (Algorithm 1): Newton on level L with the
+    restricted right-hand side of the previous step (if any; otherwise the
+    plain old-time term), redone without it if Newton needs more than
+    `fallback_its` iterations (Sec. 3.3), then lines 6-9.
+
+    state: dict(bL, vcorr, h) from the previous step (None, None, zeros at
+    the start).  Returns (x_new, new_state, info)."""
+    from . import net, newton
+    coarse = levels[-1]
+    plain_f = fem.old_time_rhs(coarse, x_old, prm)
+    f = state["bL"] if state["bL"] is not None else plain_f
+    x, nit, git, nrm = newton.newton_solve(levels, x_old, f, prm, opt)
+    fallback = False
+    if state["bL"] is not None and (nrm > opt.newton_tol or nit > fallback_its):
+        x, nit2, git2, nrm = newton.newton_solve(levels, x_old, plain_f, prm, opt)
+        nit, git, fallback = nit + nit2, git + git2, True
+    nn = fine.nn
+    if state["vcorr"] is not None:
+        vprev = state["vcorr"]
+    else:
+        vprev = prolongate_state(coarse, fine, x_old)
+        vprev[2 * nn:] = 0.0
+    xt = prolongate_state(coarse, fine, x)
+    r = fine_residual(fine, xt, vprev, prm)
+    X = patch_features(coarse, fine, 2, xt, r, prm, mean, std)
+    if bf16:
+        X = net.bf16_round(X)
+    y, h = net.step_forward(spec, params, X, state["h"], bf16)
+    d = scatter_average(coarse, fine, 2, y)
+    vcorr = xt.copy()
+    vcorr[:2 * nn] += d
+    vcorr[2 * nn:] = 0.0
+    _, bL = rhs_and_restrict(coarse, fine, [coarse, fine], vcorr, prm)
+    info = dict(newton_its=nit, gmres_its=git, res=nrm, fallback=fallback, X=X, y=y)
+    return x, dict(bL=bL, vcorr=vcorr, h=h), info

@@ -160,6 +160,7 @@ int dnnmg_default_config(dnnmg_config* c) {
   c->hidden = 64;
   c->gru_layers = 2;
   c->mlp_width = 128;
+  c->fallback_newton_its = 8;
   return DNNMG_OK;
 }
 
@@ -278,6 +279,23 @@ int dnnmg_get_weights(dnnmg_ctx* ctx, float* w) {
 int dnnmg_patch_infer(dnnmg_ctx* ctx, const uint16_t* x, float* h, float* out, int P) {
   if (!ctx || (P > 0 && (!x || !h || !out))) return DNNMG_ERR_ARG;
   return ctx->patch_infer(x, h, out, P);
+}
+
+int dnnmg_num_patches(const dnnmg_ctx* ctx) { return ctx ? ctx->P : 0; }
+
+int dnnmg_set_feature_stats(dnnmg_ctx* ctx, const float* mean, const float* stdv) {
+  if (!ctx || !mean || !stdv) return DNNMG_ERR_ARG;
+  return ctx->set_feature_stats(mean, stdv);
+}
+
+int dnnmg_get_fine_velocity(dnnmg_ctx* ctx, double* v) {
+  if (!ctx || !v) return DNNMG_ERR_ARG;
+  return ctx->get_fine_velocity(v);
+}
+
+int dnnmg_get_patch_inputs(dnnmg_ctx* ctx, uint16_t* x) {
+  if (!ctx || !x) return DNNMG_ERR_ARG;
+  return ctx->get_patch_inputs(x);
 }
 
 int dnnmg_gemm_bf16(dnnmg_ctx* ctx, const uint16_t* A, const uint16_t* B, float* C, int M, int N,

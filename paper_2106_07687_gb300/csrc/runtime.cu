@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "dnnmg_step.h"
 #include "runtime.h"
 
 using namespace dnnmg;
@@ -334,7 +335,96 @@ int dnnmg_ctx::init() {
   solver = make_solver(this);
   if (!solver) return err.empty() ? fail(DNNMG_ERR_CUDA, "solver setup failed") : DNNMG_ERR_CUDA;
   if (int rc = init_net()) return rc;
+  if (int rc = init_dnnmg()) return rc;
   return check("setup");
+}
+
+// Patch lists and level L+1 buffers of the DNN-MG correction.
+int dnnmg_ctx::init_dnnmg() {
+  if (cfg.replaced_levels != 1 || !net_ok) return DNNMG_OK;  // NET steps report it
+  const HostLevel& hl = lv[L()];
+  std::vector<int> pc, cp(hl.solid.size(), -1);
+  for (size_t c = 0; c < hl.solid.size(); ++c)
+    if (!hl.solid[c]) {
+      cp[c] = (int)pc.size();
+      pc.push_back((int)c);
+    }
+  P = (int)pc.size();
+  const Grid gF = grid(L() + 1);
+  const size_t n3 = 3 * (size_t)gF.nn;
+  patch_cell = mem.alloc<int>(P);
+  cell_patch = mem.alloc<int>(cp.size());
+  xtF = mem.alloc<double>(n3);
+  ximpF = mem.alloc<double>(n3);
+  fF = mem.alloc<double>(n3);
+  rF = mem.alloc<double>(n3);
+  vcorr = mem.alloc<double>(n3);
+  bF = mem.alloc<double>(n3);
+  bL = mem.alloc<double>(3 * (size_t)grid(L()).nn);
+  X = mem.alloc<uint16_t>((size_t)P * nd.c_in);
+  net_out = mem.alloc<float>((size_t)P * nd.c_out);
+  hid = mem.alloc<float>((size_t)2 * P * nd.hidden);
+  feat_mean = mem.alloc<float>(nd.c_in);
+  feat_std = mem.alloc<float>(nd.c_in);
+  if (!mem.ok()) return fail(DNNMG_ERR_CUDA, "device allocation failed");
+  cudaMemcpyAsync(patch_cell, pc.data(), sizeof(int) * P, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(cell_patch, cp.data(), sizeof(int) * cp.size(), cudaMemcpyHostToDevice, st);
+  std::vector<float> zero(nd.c_in, 0.0f), one(nd.c_in, 1.0f);
+  cudaMemcpyAsync(feat_mean, zero.data(), sizeof(float) * nd.c_in, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(feat_std, one.data(), sizeof(float) * nd.c_in, cudaMemcpyHostToDevice, st);
+  cudaMemsetAsync(hid, 0, sizeof(float) * 2 * P * nd.hidden, st);
+  s64F = make_sten<double>(gF.h, cfg);
+  cudaStreamSynchronize(st);
+  return check("dnnmg setup");
+}
+
+// Algorithm 1 lines 6-9 after the level-L solve of this step (x64 = v^L_n).
+int dnnmg_ctx::dnnmg_correction() {
+  const Grid gL = grid(L()), gF = grid(L() + 1);
+  const size_t n3F = 3 * (size_t)gF.nn;
+  const int pr = prof.begin(DNNMG_STAGE_NETWORK, L(), st);
+  if (!have_vcorr) {  // first correction: the previous fine velocity is P(v^L_{n-1})
+    launch_prolong_state64(gF, gL, xold64, vcorr, 2, st);
+    cudaMemsetAsync(vcorr + 2 * gF.nn, 0, sizeof(double) * gF.nn, st);
+  }
+  launch_prolong_state64(gF, gL, x64, xtF, 3, st);                     // line 6
+  launch_old_time_rhs64(gF, 1.0 / cfg.dt, vcorr, fF, st);
+  cudaMemcpyAsync(ximpF, xtF, n3F * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  launch_impose_dirichlet64(gF, ximpF, st);
+  launch_residual64(gF, s64F, ximpF, fF, rF, st);                     // input: fine residual
+  launch_gather(gL, gF, patch_cell, P, xtF, rF, feat_mean, feat_std, cfg.nu, cfg.dt, X, st);
+  launch_patchnet_forward(nd, pk, X, hid, hid, net_out, P, net_status, st);  // line 7
+  launch_scatter(gL, gF, cell_patch, net_out, nd.c_out, xtF, vcorr, st);
+  launch_old_time_rhs64(gF, 1.0 / cfg.dt, vcorr, bF, st);             // line 8
+  cudaMemsetAsync(bL, 0, 3 * sizeof(double) * gL.nn, st);
+  launch_restrict_full64(gF, gL, bF, bL, 2, st);                      // line 9
+  prof.end(pr, st);
+  have_vcorr = have_net_rhs = true;
+  return net_check("dnnmg correction");
+}
+
+int dnnmg_ctx::set_feature_stats(const float* mean, const float* stdv) {
+  if (!feat_mean) return fail(DNNMG_ERR_STATE, "no DNN-MG network in this context");
+  for (int k = 0; k < nd.c_in; ++k)
+    if (!(stdv[k] > 0.0f)) return fail(DNNMG_ERR_ARG, "feature std must be positive");
+  cudaMemcpyAsync(feat_mean, mean, sizeof(float) * nd.c_in, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(feat_std, stdv, sizeof(float) * nd.c_in, cudaMemcpyHostToDevice, st);
+  cudaStreamSynchronize(st);
+  return check("set_feature_stats");
+}
+
+int dnnmg_ctx::get_fine_velocity(double* v) {
+  if (!have_vcorr) return fail(DNNMG_ERR_STATE, "no DNN-MG step taken yet");
+  cudaMemcpyAsync(v, vcorr, 2 * sizeof(double) * grid(L() + 1).nn, cudaMemcpyDeviceToDevice, st);
+  cudaStreamSynchronize(st);
+  return check("get_fine_velocity");
+}
+
+int dnnmg_ctx::get_patch_inputs(uint16_t* x) {
+  if (!have_vcorr) return fail(DNNMG_ERR_STATE, "no DNN-MG step taken yet");
+  cudaMemcpyAsync(x, X, sizeof(uint16_t) * P * nd.c_in, cudaMemcpyDeviceToDevice, st);
+  cudaStreamSynchronize(st);
+  return check("get_patch_inputs");
 }
 
 // Network dimensions follow the patch: one level-L cell covers
@@ -417,6 +507,9 @@ int dnnmg_ctx::get_state(double* x) {
 
 int dnnmg_ctx::set_state(const double* x) {
   cudaMemcpyAsync(x64, x, 3 * sizeof(double) * grid(L()).nn, cudaMemcpyDeviceToDevice, st);
+  launch_impose_dirichlet64(grid(L()), x64, st);
+  have_net_rhs = have_vcorr = false;
+  if (hid) cudaMemsetAsync(hid, 0, sizeof(float) * 2 * P * nd.hidden, st);
   cudaStreamSynchronize(st);
   return check("set_state");
 }
@@ -474,10 +567,30 @@ int dnnmg_ctx::step(int mode, dnnmg_step_stats* stats) {
   dnnmg_step_stats s{};
   const Grid gL = grid(L());
   const size_t n3 = 3 * (size_t)gL.nn;
+  if (mode == DNNMG_NET && (cfg.replaced_levels != 1 || !net_ok || !X))
+    return fail(DNNMG_ERR_ARG, "DNN-MG steps need replaced_levels = 1 and the default network");
   cudaEventRecord(ev0, st);
   cudaMemcpyAsync(xold64, x64, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
-  launch_old_time_rhs64(gL, 1.0 / cfg.dt, xold64, f64, st);
+  const bool use_net_rhs = mode == DNNMG_NET && have_net_rhs;
+  if (use_net_rhs)
+    cudaMemcpyAsync(f64, bL, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  else
+    launch_old_time_rhs64(gL, 1.0 / cfg.dt, xold64, f64, st);
   int rc = newton(f64, &s);
+  if (use_net_rhs && (rc != DNNMG_OK || s.newton_its > cfg.fallback_newton_its)) {
+    // the corrected right-hand side slowed Newton down: redo the step without it
+    cudaMemcpyAsync(x64, xold64, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    launch_old_time_rhs64(gL, 1.0 / cfg.dt, xold64, f64, st);
+    const int first_its = s.newton_its, first_gits = s.gmres_its;
+    rc = newton(f64, &s);
+    s.newton_its += first_its;
+    s.gmres_its += first_gits;
+    s.fallback = 1;
+  }
+  if (mode == DNNMG_NET && (rc == DNNMG_OK || rc == DNNMG_ERR_NOT_CONVERGED)) {
+    const int rc2 = dnnmg_correction();
+    if (rc2 != DNNMG_OK) rc = rc2;
+  }
   cudaEventRecord(ev1, st);
   cudaEventSynchronize(ev1);
   float ms = 0;

@@ -149,6 +149,16 @@ struct dnnmg_ctx {
   float* w_master = nullptr;   // FP32 flat parameters
   dnnmg::PackedNet pk{};
   int* net_status = nullptr;
+  // DNN-MG correction state (level L+1 fields)
+  int P = 0;                       // patches = fluid cells of level L
+  int* patch_cell = nullptr;       // [P] cell id of each patch
+  int* cell_patch = nullptr;       // [nx_L * ny_L] patch id or -1
+  dnnmg::Sten<double> s64F{};
+  double *xtF = nullptr, *ximpF = nullptr, *fF = nullptr, *rF = nullptr, *vcorr = nullptr,
+         *bF = nullptr, *bL = nullptr;
+  uint16_t* X = nullptr;
+  float *net_out = nullptr, *hid = nullptr, *feat_mean = nullptr, *feat_std = nullptr;
+  bool have_net_rhs = false, have_vcorr = false;
 
   ~dnnmg_ctx();
   int init();
@@ -174,5 +184,10 @@ struct dnnmg_ctx {
   int get_weights(float* w_host);
   int patch_infer(const uint16_t* x, float* h, float* out, int P);
   int net_check(const char* what);
+  int init_dnnmg();
+  int dnnmg_correction();
+  int set_feature_stats(const float* mean, const float* stdv);
+  int get_fine_velocity(double* v);
+  int get_patch_inputs(uint16_t* x);
   int newton(const double* f, dnnmg_step_stats* st);
 };

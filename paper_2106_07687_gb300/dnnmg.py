@@ -27,7 +27,8 @@ class Config(ctypes.Structure):
                 ("level_solve", c_int32), ("level_coarse", c_int32), ("replaced_levels", c_int32),
                 ("precision", c_int32), ("newton_max", c_int32), ("gmres_m", c_int32),
                 ("gmres_maxit", c_int32), ("nu1", c_int32), ("nu2", c_int32), ("hidden", c_int32),
-                ("gru_layers", c_int32), ("mlp_width", c_int32), ("reserved", c_int32 * 8)]
+                ("gru_layers", c_int32), ("mlp_width", c_int32), ("fallback_newton_its", c_int32),
+                ("reserved", c_int32 * 7)]
 
 
 class StepStats(ctypes.Structure):
@@ -69,6 +70,10 @@ def _declare(lib):
         "dnnmg_get_weights": ([P, P], ctypes.c_int),
         "dnnmg_patch_infer": ([P, P, P, P, ctypes.c_int], ctypes.c_int),
         "dnnmg_gemm_bf16": ([P, P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "dnnmg_num_patches": ([P], ctypes.c_int),
+        "dnnmg_set_feature_stats": ([P, P, P], ctypes.c_int),
+        "dnnmg_get_fine_velocity": ([P, P], ctypes.c_int),
+        "dnnmg_get_patch_inputs": ([P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -202,6 +207,26 @@ class Context:
             if out is None else out
         self._check(self.lib.dnnmg_patch_infer(self.h, _ptr(x_bf16), _ptr(h), _ptr(out), P))
         return out
+
+    def num_patches(self):
+        return int(self.lib.dnnmg_num_patches(self.h))
+
+    def set_feature_stats(self, mean, std):
+        m = torch.as_tensor(mean, dtype=torch.float32).contiguous().cpu()
+        s = torch.as_tensor(std, dtype=torch.float32).contiguous().cpu()
+        self._check(self.lib.dnnmg_set_feature_stats(self.h, c_void_p(m.data_ptr()),
+                                                     c_void_p(s.data_ptr())))
+
+    def get_fine_velocity(self):
+        nx, ny = self.level_dims(self.cfg.level_solve + 1)
+        v = torch.empty(2 * (nx + 1) * (ny + 1), dtype=torch.float64, device="cuda")
+        self._check(self.lib.dnnmg_get_fine_velocity(self.h, _ptr(v)))
+        return v
+
+    def get_patch_inputs(self):
+        x = torch.empty(self.num_patches(), self.net_dims()[0], dtype=torch.bfloat16, device="cuda")
+        self._check(self.lib.dnnmg_get_patch_inputs(self.h, _ptr(x)))
+        return x
 
     def gemm_bf16(self, A, B):
         """C = A @ B.T on the tensor cores (A [M,K], B [N,K] cuda bfloat16)."""
