@@ -82,7 +82,9 @@ typedef struct dnnmg_config {
   int32_t gru_layers;      /* stacked GRU cells (2) */
   int32_t mlp_width;       /* width of the hidden dense layer (128) */
   int32_t fallback_newton_its; /* DNN-MG step redone without the network if Newton needs more */
-  int32_t reserved[7];
+  int32_t train_batch;     /* largest training batch B (sequences) of dnnmg_train_*, 0 = none */
+  int32_t train_seq;       /* largest training sequence length T */
+  int32_t reserved[5];
 } dnnmg_config;
 
 /* Per-step statistics returned by dnnmg_step(). */
@@ -227,6 +229,31 @@ int dnnmg_get_fine_velocity(dnnmg_ctx* ctx, double* v);
 
 /* Network inputs of the last DNN-MG step: device [P][C_in] bfloat16. */
 int dnnmg_get_patch_inputs(dnnmg_ctx* ctx, uint16_t* x);
+
+/* ---- training (Eq. 8, Sec. 3.1) -------------------------------------------------
+ * One batch = B patch sequences of T steps; the hidden state starts at zero
+ * for every sequence.  Loss = mean over (b, t, outputs) of (y - Y)^2 (Eq. 8
+ * as a mean).  Gradients by backpropagation through time on the tensor
+ * cores (BF16 operands, FP32 accumulation); weight gradients are split-K
+ * GEMMs with a fixed-order reduction (deterministic).  The workspace is
+ * allocated by dnnmg_setup() for cfg.train_batch x cfg.train_seq.
+ *   X : device [B][T][C_in] bfloat16     Y : device [B][T][C_out] float
+ * Requirements: B % 16 == 0, 16 <= B <= train_batch, 1 <= T <= train_seq
+ * (else DNNMG_ERR_ARG; DNNMG_ERR_STATE without a training workspace). */
+
+/* Loss (host *loss) and gradient (device grad, dnnmg_num_params floats, in
+ * the flat parameter order) at the current weights; no update. */
+int dnnmg_train_grad(dnnmg_ctx* ctx, const uint16_t* X, const float* Y, int B, int T, float* grad,
+                     float* loss);
+
+/* One Adam step (beta = (0.9, 0.999), eps = 1e-8, bias-corrected) with
+ * learning rate lr on the FP32 weights; the BF16 copies are re-packed.
+ * *loss (host, may be NULL) receives the loss before the update. */
+int dnnmg_train_step(dnnmg_ctx* ctx, const uint16_t* X, const float* Y, int B, int T, float lr,
+                     float* loss);
+
+/* Zero the Adam moments and step count. */
+int dnnmg_reset_optimizer(dnnmg_ctx* ctx);
 
 /* Direct solve of the coarsest multigrid level without any device allocation
  * (the paper has no counterpart: this is a deployment variant).

@@ -298,6 +298,23 @@ int dnnmg_get_patch_inputs(dnnmg_ctx* ctx, uint16_t* x) {
   return ctx->get_patch_inputs(x);
 }
 
+int dnnmg_train_grad(dnnmg_ctx* ctx, const uint16_t* X, const float* Y, int B, int T, float* grad,
+                     float* loss) {
+  if (!ctx || !X || !Y) return DNNMG_ERR_ARG;
+  return ctx->train_grad(X, Y, B, T, grad, loss);
+}
+
+int dnnmg_train_step(dnnmg_ctx* ctx, const uint16_t* X, const float* Y, int B, int T, float lr,
+                     float* loss) {
+  if (!ctx || !X || !Y || !(lr >= 0.0f)) return DNNMG_ERR_ARG;
+  return ctx->train_step(X, Y, B, T, lr, loss);
+}
+
+int dnnmg_reset_optimizer(dnnmg_ctx* ctx) {
+  if (!ctx) return DNNMG_ERR_ARG;
+  return ctx->reset_optimizer();
+}
+
 int dnnmg_gemm_bf16(dnnmg_ctx* ctx, const uint16_t* A, const uint16_t* B, float* C, int M, int N,
                     int K) {
   if (!ctx || !A || !B || !C) return DNNMG_ERR_ARG;

@@ -107,9 +107,13 @@ __device__ __forceinline__ void mma_run(uint32_t d_tmem, uint32_t a_addr, int a_
 }
 
 // One GRU layer's epilogue for this thread's row: gates from TMEM, new
-// hidden state into hreg (FP32), `next` (BF16 operand) and HBM.
+// hidden state into hreg (FP32), `next` (BF16 operand) and `hout` (FP32,
+// HBM).  With `gsave` the gates r, z, n and the hidden part of gate n
+// (incl. bias) are stored for the backward pass; with `hT` the new state is
+// also written transposed in BF16 (column `col`, row stride ldT).
 __device__ __forceinline__ void gru_epilogue(uint32_t tm, const float* bias, float* hreg,
-                                             uint8_t* next, int row, float* hout, bool valid) {
+                                             uint8_t* next, int row, float* hout, bool valid,
+                                             float* gsave, uint16_t* hT, size_t ldT) {
   constexpr int H = 64;
 #pragma unroll 1
   for (int c = 0; c < 4; ++c) {
@@ -124,8 +128,10 @@ __device__ __forceinline__ void gru_epilogue(uint32_t tm, const float* bias, flo
       const int j = c * 16 + i;
       const float r = sigmoidf_(rp[i] + bias[j]);
       const float z = sigmoidf_(zp[i] + bias[H + j]);
-      const float n = tanhf(ip[i] + bias[2 * H + j] + r * (hp[i] + bias[3 * H + j]));
+      const float ghn = hp[i] + bias[3 * H + j];
+      const float n = tanhf(ip[i] + bias[2 * H + j] + r * ghn);
       hn[i] = (1.0f - z) * n + z * hreg[j];
+      rp[i] = r, zp[i] = z, ip[i] = n, hp[i] = ghn;
     }
 #pragma unroll
     for (int i = 0; i < 16; ++i) hreg[c * 16 + i] = hn[i];
@@ -135,21 +141,56 @@ __device__ __forceinline__ void gru_epilogue(uint32_t tm, const float* bias, flo
       for (int q = 0; q < 4; ++q)
         reinterpret_cast<float4*>(hout)[c * 4 + q] =
             make_float4(hn[4 * q], hn[4 * q + 1], hn[4 * q + 2], hn[4 * q + 3]);
+      if (gsave) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          reinterpret_cast<float4*>(gsave)[c * 4 + q] =
+              make_float4(rp[4 * q], rp[4 * q + 1], rp[4 * q + 2], rp[4 * q + 3]);
+          reinterpret_cast<float4*>(gsave + H)[c * 4 + q] =
+              make_float4(zp[4 * q], zp[4 * q + 1], zp[4 * q + 2], zp[4 * q + 3]);
+          reinterpret_cast<float4*>(gsave + 2 * H)[c * 4 + q] =
+              make_float4(ip[4 * q], ip[4 * q + 1], ip[4 * q + 2], ip[4 * q + 3]);
+          reinterpret_cast<float4*>(gsave + 3 * H)[c * 4 + q] =
+              make_float4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
+        }
+      }
+      if (hT)
+#pragma unroll
+        for (int i = 0; i < 16; ++i) hT[(size_t)(c * 16 + i) * ldT] = f2bf(hn[i]);
     }
   }
 }
 
+// Arguments of the forward kernel.  Inference: T = 1, hidden state read from
+// h_in and written to h_out.  Training: the hidden state starts at zero and
+// the kernel stores, per (t, p), the activations the backward pass needs
+// (act, FP32) and transposed BF16 copies of the GEMM inputs for the weight
+// gradients (column index t * P + p, see TrainLayout).
+struct FwdArgs {
+  const uint16_t* x;  // [P][T][C_in]
+  int P, T;
+  const float* h_in;  // [2][P][64]
+  float* h_out;       // [2][P][64]
+  float* out;         // [P][T][C_out]
+  float* act;         // [T][P][kAct]
+  uint16_t* xT;       // [kx0 + 16][T * P]
+  uint16_t* h0T;      // [80][(T + 1) * P], state of step t at column (t + 1) * P + p
+  uint16_t* h1T;      // [80][(T + 1) * P]
+  uint16_t* y1T;      // [144][T * P]
+  int* status;
+};
+
+template <bool TRAIN>
 __global__ void __launch_bounds__(kTile, 1)
     patchnet_forward_kernel(NetDims d, PackLayout L, const uint16_t* __restrict__ wimg,
-                            const float* __restrict__ bias_g, const uint16_t* __restrict__ x,
-                            const float* __restrict__ h, float* __restrict__ h_out,
-                            float* __restrict__ out, int P, int* status) {
+                            const float* __restrict__ bias_g, FwdArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
   const FwdSmem S = FwdSmem::of(d, L.total);
   const int t = threadIdx.x, warp = t >> 5;
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + S.bar);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S.tmem);
   float* bias = reinterpret_cast<float*>(sm + S.bias);
+  const int P = a.P, T = a.T;
 
   // weights and biases: one copy per CTA
   {
@@ -173,50 +214,84 @@ __global__ void __launch_bounds__(kTile, 1)
   bool failed = false;
   const int ntiles = (P + kTile - 1) / kTile;
   const size_t HP = (size_t)P * 64;
+  const size_t ld = (size_t)T * P, ldh = (size_t)(T + 1) * P;
 
   for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
     const int p = tile * kTile + t;
     const bool valid = p < P;
-    // ---- stage the tile: x (BF16), h0 and h1 (FP32 registers + BF16 operands)
-    {
-      const uint4 zero = make_uint4(0, 0, 0, 0);
-      for (int q = 0; q < kx0 / 8; ++q) {
-        uint4 v = zero;
-        if (valid && q * 8 < d.c_in) v = reinterpret_cast<const uint4*>(x + (size_t)p * d.c_in)[q];
-        *reinterpret_cast<uint4*>(sm + S.x + kmajor_offset(t, q * 8, kx0)) = v;
-      }
-    }
     float h0r[64], h1r[64];
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      float4 a = make_float4(0, 0, 0, 0), b = a;
-      if (valid) {
-        a = reinterpret_cast<const float4*>(h + (size_t)p * 64)[q];
-        b = reinterpret_cast<const float4*>(h + HP + (size_t)p * 64)[q];
+      float4 u = make_float4(0, 0, 0, 0), v = u;
+      if (!TRAIN && valid) {
+        u = reinterpret_cast<const float4*>(a.h_in + (size_t)p * 64)[q];
+        v = reinterpret_cast<const float4*>(a.h_in + HP + (size_t)p * 64)[q];
       }
-      h0r[4 * q] = a.x, h0r[4 * q + 1] = a.y, h0r[4 * q + 2] = a.z, h0r[4 * q + 3] = a.w;
-      h1r[4 * q] = b.x, h1r[4 * q + 1] = b.y, h1r[4 * q + 2] = b.z, h1r[4 * q + 3] = b.w;
+      h0r[4 * q] = u.x, h0r[4 * q + 1] = u.y, h0r[4 * q + 2] = u.z, h0r[4 * q + 3] = u.w;
+      h1r[4 * q] = v.x, h1r[4 * q + 1] = v.y, h1r[4 * q + 2] = v.z, h1r[4 * q + 3] = v.w;
     }
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      store_row16(sm + S.h0, t, c * 16, 64, h0r + c * 16);
-      store_row16(sm + S.h1, t, c * 16, 64, h1r + c * 16);
-    }
-    // ---- two GRU layers
 #pragma unroll 1
-    for (int l = 0; l < 2; ++l) {
+    for (int step = 0; step < T && !failed; ++step) {
+      const size_t col = (size_t)step * P + p;
+      float* act = TRAIN ? a.act + col * kAct : nullptr;
+      // ---- stage x_t (BF16) and the hidden states (BF16 operands)
+      {
+        const uint4 zero = make_uint4(0, 0, 0, 0);
+        const uint16_t* xr = a.x + ((size_t)p * T + step) * d.c_in;
+        for (int q = 0; q < kx0 / 8; ++q) {
+          uint4 v = zero;
+          if (valid && q * 8 < d.c_in) v = reinterpret_cast<const uint4*>(xr)[q];
+          *reinterpret_cast<uint4*>(sm + S.x + kmajor_offset(t, q * 8, kx0)) = v;
+          if (TRAIN && valid && q * 8 < d.c_in) {
+            const uint16_t* e = reinterpret_cast<const uint16_t*>(&v);
+            for (int i = 0; i < 8; ++i) a.xT[(size_t)(q * 8 + i) * ld + col] = e[i];
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        store_row16(sm + S.h0, t, c * 16, 64, h0r + c * 16);
+        store_row16(sm + S.h1, t, c * 16, 64, h1r + c * 16);
+      }
+      // ---- two GRU layers
+#pragma unroll 1
+      for (int l = 0; l < 2; ++l) {
+        fence_async_smem();
+        fence_before_sync();
+        __syncthreads();
+        const uint32_t ax = sbase + (l == 0 ? S.x : S.t);
+        const int kx = l == 0 ? kx0 : 64;
+        const uint32_t ah = sbase + (l == 0 ? S.h0 : S.h1);
+        if (t == 0) {
+          fence_after_sync();
+          mma_run(tbase + 0, ax, kx, sbase + S.w + 2 * L.rz[l], kx, 128, kx, false);
+          mma_run(tbase + 0, ah, 64, sbase + S.w + 2 * L.hrz[l], 64, 128, 64, true);
+          mma_run(tbase + 128, ax, kx, sbase + S.w + 2 * L.in[l], kx, 64, kx, false);
+          mma_run(tbase + 192, ah, 64, sbase + S.w + 2 * L.hn[l], 64, 64, 64, false);
+          mma_commit(bar);
+        }
+        if (!mbar_wait(bar, phase, kWaitPolls)) failed = true;
+        phase ^= 1;
+        if (__syncthreads_or(failed)) {
+          failed = true;
+          break;
+        }
+        fence_after_sync();
+        // layer 0 writes its new state into S.t (layer 1 input); layer 1 into
+        // S.h0 (free after layer 0) as the dense head's input
+        float* hout = TRAIN ? act + kActH0 + l * 64 : a.h_out + l * HP + (size_t)p * 64;
+        uint16_t* hT = TRAIN ? (l == 0 ? a.h0T : a.h1T) + ldh - ld + col : nullptr;
+        gru_epilogue(tm, bias + l * 4 * 64, l == 0 ? h0r : h1r, sm + (l == 0 ? S.t : S.h0), t,
+                     hout, valid, TRAIN ? act + kActG0 + l * 256 : nullptr, hT, ldh);
+      }
+      if (failed) break;
+      // ---- dense head: relu(h1 W1^T + b1) W2^T + b2
       fence_async_smem();
       fence_before_sync();
       __syncthreads();
-      const uint32_t ax = sbase + (l == 0 ? S.x : S.t);
-      const int kx = l == 0 ? kx0 : 64;
-      const uint32_t ah = sbase + (l == 0 ? S.h0 : S.h1);
       if (t == 0) {
         fence_after_sync();
-        mma_run(tbase + 0, ax, kx, sbase + S.w + 2 * L.rz[l], kx, 128, kx, false);
-        mma_run(tbase + 0, ah, 64, sbase + S.w + 2 * L.hrz[l], 64, 128, 64, true);
-        mma_run(tbase + 128, ax, kx, sbase + S.w + 2 * L.in[l], kx, 64, kx, false);
-        mma_run(tbase + 192, ah, 64, sbase + S.w + 2 * L.hn[l], 64, 64, 64, false);
+        mma_run(tbase + 0, sbase + S.h0, 64, sbase + S.w + 2 * L.w1, 64, 128, 64, false);
         mma_commit(bar);
       }
       if (!mbar_wait(bar, phase, kWaitPolls)) failed = true;
@@ -226,69 +301,59 @@ __global__ void __launch_bounds__(kTile, 1)
         break;
       }
       fence_after_sync();
-      // layer 0 writes its new state into S.t (layer 1 input); layer 1 into
-      // S.h0 (free after layer 0) as the dense head's input
-      gru_epilogue(tm, bias + l * 4 * 64, l == 0 ? h0r : h1r, sm + (l == 0 ? S.t : S.h0), t,
-                   h_out + l * HP + (size_t)p * 64, valid);
-    }
-    if (failed) break;
-    // ---- dense head: relu(h1 W1^T + b1) W2^T + b2
-    fence_async_smem();
-    fence_before_sync();
-    __syncthreads();
-    if (t == 0) {
-      fence_after_sync();
-      mma_run(tbase + 0, sbase + S.h0, 64, sbase + S.w + 2 * L.w1, 64, 128, 64, false);
-      mma_commit(bar);
-    }
-    if (!mbar_wait(bar, phase, kWaitPolls)) failed = true;
-    phase ^= 1;
-    if (__syncthreads_or(failed)) {
-      failed = true;
-      break;
-    }
-    fence_after_sync();
-    const float* b1 = bias + 2 * 4 * 64;
+      const float* b1 = bias + 2 * 4 * 64;
 #pragma unroll 1
-    for (int c = 0; c < 8; ++c) {
-      float v[16];
-      tmem_ld16(tm + c * 16, v);
+      for (int c = 0; c < 8; ++c) {
+        float v[16];
+        tmem_ld16(tm + c * 16, v);
+        if (TRAIN && valid) {
 #pragma unroll
-      for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] + b1[c * 16 + i], 0.0f);
-      store_row16(sm + S.m, t, c * 16, 128, v);
-    }
-    fence_async_smem();
-    fence_before_sync();
-    __syncthreads();
-    const int n2 = d.nout();
-    if (t == 0) {
-      fence_after_sync();
-      mma_run(tbase + 128, sbase + S.m, 128, sbase + S.w + 2 * L.w2, 128, n2, 128, false);
-      mma_commit(bar);
-    }
-    if (!mbar_wait(bar, phase, kWaitPolls)) failed = true;
-    phase ^= 1;
-    if (__syncthreads_or(failed)) {
-      failed = true;
-      break;
-    }
-    fence_after_sync();
-    const float* b2 = b1 + d.mlp;
-#pragma unroll 1
-    for (int c = 0; c < n2 / 16; ++c) {
-      float v[16];
-      tmem_ld16(tm + 128 + c * 16, v);
-      if (valid)
-        for (int i = 0; i < 16; ++i) {
-          const int j = c * 16 + i;
-          if (j < d.c_out) out[(size_t)p * d.c_out + j] = v[i] + b2[j];
+          for (int q = 0; q < 4; ++q)
+            reinterpret_cast<float4*>(act + kActA1)[c * 4 + q] =
+                make_float4(v[4 * q] + b1[c * 16 + 4 * q], v[4 * q + 1] + b1[c * 16 + 4 * q + 1],
+                            v[4 * q + 2] + b1[c * 16 + 4 * q + 2],
+                            v[4 * q + 3] + b1[c * 16 + 4 * q + 3]);
         }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] + b1[c * 16 + i], 0.0f);
+        store_row16(sm + S.m, t, c * 16, 128, v);
+        if (TRAIN && valid)
+#pragma unroll
+          for (int i = 0; i < 16; ++i) a.y1T[(size_t)(c * 16 + i) * ld + col] = f2bf(v[i]);
+      }
+      fence_async_smem();
+      fence_before_sync();
+      __syncthreads();
+      const int n2 = d.nout();
+      if (t == 0) {
+        fence_after_sync();
+        mma_run(tbase + 128, sbase + S.m, 128, sbase + S.w + 2 * L.w2, 128, n2, 128, false);
+        mma_commit(bar);
+      }
+      if (!mbar_wait(bar, phase, kWaitPolls)) failed = true;
+      phase ^= 1;
+      if (__syncthreads_or(failed)) {
+        failed = true;
+        break;
+      }
+      fence_after_sync();
+      const float* b2 = b1 + d.mlp;
+#pragma unroll 1
+      for (int c = 0; c < n2 / 16; ++c) {
+        float v[16];
+        tmem_ld16(tm + 128 + c * 16, v);
+        if (valid)
+          for (int i = 0; i < 16; ++i) {
+            const int j = c * 16 + i;
+            if (j < d.c_out) a.out[((size_t)p * T + step) * d.c_out + j] = v[i] + b2[j];
+          }
+      }
+      fence_before_sync();
+      __syncthreads();
     }
-    fence_before_sync();
-    __syncthreads();
   }
   if (failed) {
-    if (t == 0) atomicOr(status, 4);
+    if (t == 0) atomicOr(a.status, 4);
     // let MMAs still in flight finish before the accumulator is released
     mbar_wait(bar, phase, kWaitPolls);
   }
@@ -364,6 +429,21 @@ __global__ void __launch_bounds__(kTile, 1)
   }
 }
 
+template <bool TRAIN>
+void launch_forward_impl(const NetDims& d, const PackedNet& pk, const FwdArgs& a, cudaStream_t st) {
+  const PackLayout L = PackLayout::of(d);
+  const FwdSmem S = FwdSmem::of(d, L.total);
+  cudaFuncSetAttribute(patchnet_forward_kernel<TRAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)S.total);
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int ntiles = (a.P + kTile - 1) / kTile;
+  note_launch();
+  patchnet_forward_kernel<TRAIN><<<ntiles < sms ? ntiles : sms, kTile, S.total, st>>>(
+      d, L, pk.w, pk.bias, a);
+}
+
 }  // namespace
 
 bool net_supported(const NetDims& d) {
@@ -406,17 +486,33 @@ void launch_patchnet_forward(const NetDims& d, const PackedNet& pk, const uint16
                              const float* h, float* h_out, float* out, int P, int* status,
                              cudaStream_t st) {
   if (P <= 0) return;
-  const PackLayout L = PackLayout::of(d);
-  const FwdSmem S = FwdSmem::of(d, L.total);
-  cudaFuncSetAttribute(patchnet_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)S.total);
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int ntiles = (P + kTile - 1) / kTile;
-  note_launch();
-  patchnet_forward_kernel<<<ntiles < sms ? ntiles : sms, kTile, S.total, st>>>(
-      d, L, pk.w, pk.bias, x, h, h_out, out, P, status);
+  FwdArgs a{};
+  a.x = x;
+  a.P = P;
+  a.T = 1;
+  a.h_in = h;
+  a.h_out = h_out;
+  a.out = out;
+  a.status = status;
+  launch_forward_impl<false>(d, pk, a, st);
+}
+
+void launch_patchnet_train_forward(const NetDims& d, const PackedNet& pk, const uint16_t* x, int B,
+                                   int T, float* ypred, const TrainBufs& tb, int* status,
+                                   cudaStream_t st) {
+  if (B <= 0 || T <= 0) return;
+  FwdArgs a{};
+  a.x = x;
+  a.P = B;
+  a.T = T;
+  a.out = ypred;
+  a.act = tb.act;
+  a.xT = tb.xT;
+  a.h0T = tb.h0T;
+  a.h1T = tb.h1T;
+  a.y1T = tb.y1T;
+  a.status = status;
+  launch_forward_impl<true>(d, pk, a, st);
 }
 
 int launch_umma_gemm(const uint16_t* A, const uint16_t* B, float* C, int M, int N, int K,

@@ -60,6 +60,24 @@ struct PackLayout {
   }
 };
 
+// Per (step, patch) activations saved by the training forward pass (FP32):
+// new hidden states, gates (r, z, n, hidden part of n incl. bias) of both
+// layers and the pre-activation of the hidden dense layer.
+constexpr int kActH0 = 0, kActH1 = 64, kActG0 = 128, kActG1 = 384, kActA1 = 640, kAct = 768;
+
+// Buffers of one training step for B sequences of T steps.  Columns of the
+// transposed BF16 streams are indexed t * B + b; h0T / h1T hold a leading
+// block of B zero columns so that the previous step's state of column
+// t * B + b is at the same column of the unshifted view.  Row 40 of xT and
+// row 64 of h0T / h1T and row 128 of y1T hold ones (bias gradients).
+struct TrainBufs {
+  float* act = nullptr;      // [T][B][kAct]
+  uint16_t* xT = nullptr;    // [48][T B]
+  uint16_t* h0T = nullptr;   // [80][(T+1) B]
+  uint16_t* h1T = nullptr;   // [80][(T+1) B]
+  uint16_t* y1T = nullptr;   // [144][T B]
+};
+
 bool net_supported(const NetDims& d);
 // master FP32 flat weights -> packed BF16 operands + fused biases
 void launch_pack_weights(const NetDims& d, const float* w, PackedNet& pk, cudaStream_t st);
@@ -68,6 +86,10 @@ void launch_pack_weights(const NetDims& d, const float* w, PackedNet& pk, cudaSt
 void launch_patchnet_forward(const NetDims& d, const PackedNet& pk, const uint16_t* x,
                              const float* h, float* h_out, float* out, int P, int* status,
                              cudaStream_t st);
+// training forward over T steps from a zero hidden state, saving activations
+void launch_patchnet_train_forward(const NetDims& d, const PackedNet& pk, const uint16_t* x, int B,
+                                   int T, float* ypred, const TrainBufs& tb, int* status,
+                                   cudaStream_t st);
 // C[M x N] = A[M x K] * B[N x K]^T (BF16 row-major inputs, FP32 row-major out)
 int launch_umma_gemm(const uint16_t* A, const uint16_t* B, float* C, int M, int N, int K,
                      int* status, cudaStream_t st);

@@ -2,6 +2,7 @@
 // (Sec. 2.2, Eq. 7, Algorithm 1 lines 2-4), sequencing the kernels of this
 // library on the context's stream.
 #include <cmath>
+#include <algorithm>
 #include <cstring>
 
 #include "dnnmg_step.h"
@@ -336,7 +337,145 @@ int dnnmg_ctx::init() {
   if (!solver) return err.empty() ? fail(DNNMG_ERR_CUDA, "solver setup failed") : DNNMG_ERR_CUDA;
   if (int rc = init_net()) return rc;
   if (int rc = init_dnnmg()) return rc;
+  if (int rc = init_train()) return rc;
   return check("setup");
+}
+
+int dnnmg_ctx::init_train() {
+  if (cfg.train_batch <= 0 || cfg.train_seq <= 0 || !net_ok) return DNNMG_OK;
+  const size_t B = cfg.train_batch, T = cfg.train_seq, K = B * T, Kh = (T + 1) * B;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  tr_blocks_max = sms;
+  tr_splits_max = 160;
+  tb.act = mem.alloc<float>(K * kAct);
+  tb.xT = mem.alloc<uint16_t>(48 * K);
+  tb.h0T = mem.alloc<uint16_t>(80 * Kh);
+  tb.h1T = mem.alloc<uint16_t>(80 * Kh);
+  tb.y1T = mem.alloc<uint16_t>(144 * K);
+  tr_ypred = mem.alloc<float>(K * nd.c_out);
+  dyT = mem.alloc<uint16_t>(128 * K);
+  da1T = mem.alloc<uint16_t>(128 * K);
+  gi0T = mem.alloc<uint16_t>(256 * K);
+  gh0T = mem.alloc<uint16_t>(256 * K);
+  gi1T = mem.alloc<uint16_t>(256 * K);
+  gh1T = mem.alloc<uint16_t>(256 * K);
+  loss_part = mem.alloc<double>(tr_blocks_max);
+  loss_dev = mem.alloc<float>(4);
+  grad = mem.alloc<float>(nd.num_params());
+  adam_m = mem.alloc<float>(nd.num_params());
+  adam_v = mem.alloc<float>(nd.num_params());
+  cpart = mem.alloc<float>((size_t)tr_splits_max * 256 * 144);
+  wT = mem.alloc<uint16_t>(BwdPack::kTotal);
+  if (!mem.ok()) return fail(DNNMG_ERR_CUDA, "training workspace allocation failed");
+  return reset_optimizer();
+}
+
+int dnnmg_ctx::reset_optimizer() {
+  if (!adam_m) return fail(DNNMG_ERR_STATE, "no training workspace (set train_batch, train_seq)");
+  cudaMemsetAsync(adam_m, 0, sizeof(float) * nd.num_params(), st);
+  cudaMemsetAsync(adam_v, 0, sizeof(float) * nd.num_params(), st);
+  adam_step = 0;
+  return check("reset_optimizer");
+}
+
+namespace {
+// BF16 one in rows [r0, r1) of a row-major [rows][ld] array
+void fill_rows_one(uint16_t* a, size_t ld, int r0, int r1, cudaStream_t st) {
+  launch_fill<uint16_t>(a + (size_t)r0 * ld, (uint16_t)0x3F80, (size_t)(r1 - r0) * ld, st);
+}
+}  // namespace
+
+int dnnmg_ctx::train_grad_impl(const uint16_t* Xd, const float* Yd, int B, int T) {
+  if (!grad) return fail(DNNMG_ERR_STATE, "no training workspace (set train_batch, train_seq)");
+  if (B < 16 || B % 16 || B > cfg.train_batch || T < 1 || T > cfg.train_seq)
+    return fail(DNNMG_ERR_ARG, "need B % 16 == 0, 16 <= B <= train_batch, 1 <= T <= train_seq");
+  const size_t K = (size_t)B * T, Kh = (size_t)(T + 1) * B;
+  if (B != tr_layout_B || T != tr_layout_T) {
+    cudaMemsetAsync(tb.xT, 0, 2 * 48 * K, st);
+    cudaMemsetAsync(tb.h0T, 0, 2 * 80 * Kh, st);
+    cudaMemsetAsync(tb.h1T, 0, 2 * 80 * Kh, st);
+    cudaMemsetAsync(tb.y1T, 0, 2 * 144 * K, st);
+    cudaMemsetAsync(dyT, 0, 2 * 128 * K, st);
+    for (uint16_t* g : {gi0T, gh0T, gi1T, gh1T}) cudaMemsetAsync(g, 0, 2 * 256 * K, st);
+    fill_rows_one(tb.xT, K, nd.c_in, nd.c_in + 1, st);
+    fill_rows_one(tb.h0T, Kh, 64, 65, st);
+    fill_rows_one(tb.h1T, Kh, 64, 65, st);
+    fill_rows_one(tb.y1T, K, 128, 129, st);
+    tr_layout_B = B;
+    tr_layout_T = T;
+  }
+  const int p = prof.begin(DNNMG_STAGE_TRAIN, 0, st);
+  launch_pack_backward(nd, w_master, wT, st);
+  launch_patchnet_train_forward(nd, pk, Xd, B, T, tr_ypred, tb, net_status, st);
+  BwdArgs a{};
+  a.act = tb.act;
+  a.ypred = tr_ypred;
+  a.Y = Yd;
+  a.B = B;
+  a.T = T;
+  a.scale = (float)(2.0 / ((double)B * T * nd.c_out));
+  a.dyT = dyT;
+  a.da1T = da1T;
+  a.gi0T = gi0T;
+  a.gh0T = gh0T;
+  a.gi1T = gi1T;
+  a.gh1T = gh1T;
+  a.loss_partial = loss_part;
+  a.status = net_status;
+  const int nb = std::min((B + 127) / 128, tr_blocks_max);
+  launch_patchnet_backward(nd, wT, a, nb, st);
+  launch_loss(loss_part, nb, 1.0 / ((double)B * T * nd.c_out), loss_dev, st);
+  // weight gradients: dW = sum over columns of dG^T x (split-K), bias = ones row
+  const int H = nd.hidden;
+  const size_t oWih0 = 0, oWhh0 = oWih0 + (size_t)3 * H * nd.c_in, obih0 = oWhh0 + (size_t)3 * H * H,
+               obhh0 = obih0 + 3 * H, oWih1 = obhh0 + 3 * H, oWhh1 = oWih1 + (size_t)3 * H * H,
+               obih1 = oWhh1 + (size_t)3 * H * H, obhh1 = obih1 + 3 * H, oW1 = obhh1 + 3 * H,
+               ob1 = oW1 + (size_t)nd.mlp * H, oW2 = ob1 + nd.mlp,
+               ob2 = oW2 + (size_t)nd.c_out * nd.mlp;
+  int splits = (int)std::min<size_t>(std::max<size_t>(K / 1024, 1), (size_t)tr_splits_max);
+  struct G {
+    const uint16_t* A;
+    const uint16_t* Bm;
+    size_t ldb;
+    int M, N, mv, nv, bcol;
+    size_t ow, ob;
+  } gs[] = {
+      {gi0T, tb.xT, K, 256, 48, 3 * H, nd.c_in, nd.c_in, oWih0, obih0},
+      {gh0T, tb.h0T, Kh, 256, 80, 3 * H, H, H, oWhh0, obhh0},
+      {gi1T, tb.h0T + B, Kh, 256, 80, 3 * H, H, H, oWih1, obih1},
+      {gh1T, tb.h1T, Kh, 256, 80, 3 * H, H, H, oWhh1, obhh1},
+      {da1T, tb.h1T + B, Kh, 128, 80, nd.mlp, H, H, oW1, ob1},
+      {dyT, tb.y1T, K, 128, 144, nd.c_out, nd.mlp, nd.mlp, oW2, ob2},
+  };
+  for (const G& g : gs) {
+    if (launch_splitk_gemm(g.A, K, g.Bm, g.ldb, cpart, g.M, g.N, (int)K, splits, net_status, st))
+      return fail(DNNMG_ERR_ARG, "weight-gradient GEMM shape");
+    launch_reduce_grad(cpart, splits, g.M, g.N, g.mv, g.nv, g.bcol, grad + g.ow, grad + g.ob, st);
+  }
+  prof.end(p, st);
+  return net_check("train");
+}
+
+int dnnmg_ctx::train_grad(const uint16_t* X, const float* Y, int B, int T, float* g, float* loss) {
+  if (int rc = train_grad_impl(X, Y, B, T)) return rc;
+  if (g) cudaMemcpyAsync(g, grad, sizeof(float) * nd.num_params(), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(h_scalars, loss_dev, sizeof(float), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  if (loss) std::memcpy(loss, h_scalars, sizeof(float));
+  return check("train_grad");
+}
+
+int dnnmg_ctx::train_step(const uint16_t* X, const float* Y, int B, int T, float lr, float* loss) {
+  if (int rc = train_grad_impl(X, Y, B, T)) return rc;
+  ++adam_step;
+  launch_adam(w_master, grad, adam_m, adam_v, nd.num_params(), lr, adam_step, st);
+  launch_pack_weights(nd, w_master, pk, st);
+  cudaMemcpyAsync(h_scalars, loss_dev, sizeof(float), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  if (loss) std::memcpy(loss, h_scalars, sizeof(float));
+  return check("train_step");
 }
 
 // Patch lists and level L+1 buffers of the DNN-MG correction.

@@ -8,6 +8,7 @@
 #include "../../include/dnnmg.h"
 #include "kernels.h"
 #include "patchnet.cuh"
+#include "train.h"
 
 namespace dnnmg {
 
@@ -159,6 +160,14 @@ struct dnnmg_ctx {
   uint16_t* X = nullptr;
   float *net_out = nullptr, *hid = nullptr, *feat_mean = nullptr, *feat_std = nullptr;
   bool have_net_rhs = false, have_vcorr = false;
+  // training workspace (capacity cfg.train_batch x cfg.train_seq)
+  dnnmg::TrainBufs tb{};
+  float *tr_ypred = nullptr, *loss_dev = nullptr, *grad = nullptr, *adam_m = nullptr,
+        *adam_v = nullptr, *cpart = nullptr;
+  uint16_t *dyT = nullptr, *da1T = nullptr, *gi0T = nullptr, *gh0T = nullptr, *gi1T = nullptr,
+           *gh1T = nullptr, *wT = nullptr;
+  double* loss_part = nullptr;
+  int tr_layout_B = -1, tr_layout_T = -1, adam_step = 0, tr_blocks_max = 0, tr_splits_max = 0;
 
   ~dnnmg_ctx();
   int init();
@@ -189,5 +198,10 @@ struct dnnmg_ctx {
   int set_feature_stats(const float* mean, const float* stdv);
   int get_fine_velocity(double* v);
   int get_patch_inputs(uint16_t* x);
+  int init_train();
+  int train_grad_impl(const uint16_t* X, const float* Y, int B, int T);
+  int train_grad(const uint16_t* X, const float* Y, int B, int T, float* g, float* loss);
+  int train_step(const uint16_t* X, const float* Y, int B, int T, float lr, float* loss);
+  int reset_optimizer();
   int newton(const double* f, dnnmg_step_stats* st);
 };

@@ -1,0 +1,48 @@
+// Training kernels of the patch network (internal to libdnnmg).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include "patchnet.cuh"
+
+namespace dnnmg {
+
+// Element offsets of the transposed BF16 weight operands used by the
+// backward pass (B operands of dY W2, dA1 W1, dG_h W_hh, dG_i W_ih1).
+struct BwdPack {
+  static constexpr int kW2T = 0;                 // [128][32]  W2^T
+  static constexpr int kW1T = kW2T + 128 * 32;   // [64][128]  W1^T
+  static constexpr int kWhh0T = kW1T + 64 * 128; // [64][192]  W_hh0^T
+  static constexpr int kWhh1T = kWhh0T + 64 * 192;
+  static constexpr int kWih1T = kWhh1T + 64 * 192;
+  static constexpr int kTotal = kWih1T + 64 * 192;
+};
+
+struct BwdArgs {
+  const float* act;      // [T][B][kAct] from the training forward
+  const float* ypred;    // [B][T][C_out]
+  const float* Y;        // [B][T][C_out] targets
+  int B, T;
+  float scale;           // 2 / (B T C_out)
+  uint16_t* dyT;         // [128][T B]   rows >= C_out stay zero
+  uint16_t* da1T;        // [128][T B]
+  uint16_t* gi0T;        // [256][T B]   rows >= 192 stay zero
+  uint16_t* gh0T;
+  uint16_t* gi1T;
+  uint16_t* gh1T;
+  double* loss_partial;  // [gridDim]
+  int* status;
+};
+
+void launch_pack_backward(const NetDims& d, const float* w, uint16_t* wT, cudaStream_t st);
+void launch_patchnet_backward(const NetDims& d, const uint16_t* wT, const BwdArgs& a, int nblocks,
+                              cudaStream_t st);
+int launch_splitk_gemm(const uint16_t* A, size_t lda, const uint16_t* B, size_t ldb, float* Cpart,
+                       int M, int N, int K, int splits, int* status, cudaStream_t st);
+void launch_reduce_grad(const float* Cpart, int splits, int M, int N, int m_valid, int n_valid,
+                        int bias_col, float* gw, float* gb, cudaStream_t st);
+void launch_loss(const double* part, int n, double inv, float* out, cudaStream_t st);
+void launch_adam(float* w, const float* g, float* m, float* v, size_t n, float lr, int step,
+                 cudaStream_t st);
+
+}  // namespace dnnmg

@@ -241,6 +241,7 @@ DNNMG_INST(double)
 #undef DNNMG_INST
 template void launch_combine<float, double>(const float*, size_t, int, const double*, double,
                                             double*, size_t, cudaStream_t);
+template void launch_fill<uint16_t>(uint16_t*, uint16_t, size_t, cudaStream_t);
 template void launch_cast<double, float>(const double*, float*, size_t, cudaStream_t);
 template void launch_cast<float, double>(const float*, double*, size_t, cudaStream_t);
 template void launch_cast<double, double>(const double*, double*, size_t, cudaStream_t);

@@ -28,7 +28,7 @@ class Config(ctypes.Structure):
                 ("precision", c_int32), ("newton_max", c_int32), ("gmres_m", c_int32),
                 ("gmres_maxit", c_int32), ("nu1", c_int32), ("nu2", c_int32), ("hidden", c_int32),
                 ("gru_layers", c_int32), ("mlp_width", c_int32), ("fallback_newton_its", c_int32),
-                ("reserved", c_int32 * 7)]
+                ("train_batch", c_int32), ("train_seq", c_int32), ("reserved", c_int32 * 5)]
 
 
 class StepStats(ctypes.Structure):
@@ -74,6 +74,9 @@ def _declare(lib):
         "dnnmg_set_feature_stats": ([P, P, P], ctypes.c_int),
         "dnnmg_get_fine_velocity": ([P, P], ctypes.c_int),
         "dnnmg_get_patch_inputs": ([P, P], ctypes.c_int),
+        "dnnmg_train_grad": ([P, P, P, ctypes.c_int, ctypes.c_int, P, P], ctypes.c_int),
+        "dnnmg_train_step": ([P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_float, P], ctypes.c_int),
+        "dnnmg_reset_optimizer": ([P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -227,6 +230,14 @@ class Context:
         x = torch.empty(self.num_patches(), self.net_dims()[0], dtype=torch.bfloat16, device="cuda")
         self._check(self.lib.dnnmg_get_patch_inputs(self.h, _ptr(x)))
         return x
+
+    def train_step(self, X, Y, B, T, lr):
+        """One Adam step on a batch (X cuda bfloat16 [B,T,C_in], Y cuda float [B,T,C_out]);
+        returns the loss before the update."""
+        loss = ctypes.c_float()
+        self._check(self.lib.dnnmg_train_step(self.h, _ptr(X), _ptr(Y), B, T, lr,
+                                              ctypes.byref(loss)))
+        return loss.value
 
     def gemm_bf16(self, A, B):
         """C = A @ B.T on the tensor cores (A [M,K], B [N,K] cuda bfloat16)."""

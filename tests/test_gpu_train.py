@@ -1,0 +1,79 @@
+"""Training kernels of the patch network against the oracle (Eq. 8 loss,
+backpropagation through time, Adam).  The GPU path uses bfloat16 operands
+for every product, including the gate gradients fed to the weight-gradient
+GEMMs, while the oracle's gradient keeps them in FP64 (with the forward's
+bfloat16 rounding mimicked): the loss must agree to 1e-3 relative and the
+gradient to 3e-2 relative L2 (each bfloat16 rounding is 2^-9 relative and
+they accumulate over T steps)."""
+import numpy as np
+import pytest
+
+import synthetic
+from oracle import net
+from tests.gpu_util import lib, rel
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _ctx(dn, B, T):
+    return dn.Context(level_solve=2, train_batch=B, train_seq=T)
+
+
+def _grad(ctx, dn, X, Y, B, T):
+    g = torch.empty(ctx.num_params(), dtype=torch.float32, device="cuda")
+    loss = __import__("ctypes").c_float()
+    rc = ctx.lib.dnnmg_train_grad(ctx.h, dn._ptr(X), dn._ptr(Y), B, T, dn._ptr(g),
+                                  __import__("ctypes").byref(loss))
+    ctx._check(rc)
+    return g.double().cpu().numpy(), loss.value
+
+
+@pytest.mark.parametrize("B,T", [(16, 1), (32, 3), (144, 4)])
+def test_gradient_matches_oracle(B, T):
+    dn = lib()
+    ctx = _ctx(dn, 160, 4)
+    spec = net.NetSpec()
+    w = synthetic.random_weights(B + T, spec.num_params(), 0.2).astype(np.float32)
+    ctx.set_weights(w)
+    X = net.bf16_round(synthetic.random_patch_inputs(B * 10 + T, (B, T, 40)))
+    Y = synthetic.random_patch_inputs(B * 10 + T + 1, (B, T, 18), 0.3)
+    Xg = torch.from_numpy(X).to(torch.bfloat16).cuda().contiguous()
+    Yg = torch.from_numpy(Y).float().cuda().contiguous()
+    g, loss = _grad(ctx, dn, Xg, Yg, B, T)
+    L_ref, g_ref = net.sequence_backward(spec, spec.unflatten(w.astype(np.float64)), X,
+                                         Y.astype(np.float32).astype(np.float64), bf16=True)
+    assert abs(loss - L_ref) < 1e-3 * L_ref, (loss, L_ref)
+    assert rel(g, g_ref) < 3e-2, rel(g, g_ref)
+    # every parameter block individually
+    o = 0
+    for name, shape in spec.shapes():
+        n = int(np.prod(shape))
+        assert rel(g[o:o + n], g_ref[o:o + n]) < 6e-2, (name, rel(g[o:o + n], g_ref[o:o + n]))
+        o += n
+    g2, loss2 = _grad(ctx, dn, Xg, Yg, B, T)
+    np.testing.assert_array_equal(g, g2)          # fixed-order reductions
+    assert loss == loss2
+
+
+def test_adam_step_and_learning():
+    dn = lib()
+    B, T = 64, 3
+    ctx = _ctx(dn, B, T)
+    spec = net.NetSpec()
+    w = synthetic.random_weights(5, spec.num_params(), 0.2).astype(np.float32)
+    ctx.set_weights(w)
+    X = net.bf16_round(synthetic.random_patch_inputs(50, (B, T, 40)))
+    Y = synthetic.random_patch_inputs(51, (B, T, 18), 0.3)
+    Xg = torch.from_numpy(X).to(torch.bfloat16).cuda().contiguous()
+    Yg = torch.from_numpy(Y).float().cuda().contiguous()
+    _, g_ref = net.sequence_backward(spec, spec.unflatten(w.astype(np.float64)), X,
+                                     Y.astype(np.float32).astype(np.float64), bf16=True)
+    lr = 1e-3
+    ctx.train_step(Xg, Yg, B, T, lr)
+    dw = ctx.get_weights().double().numpy() - w
+    big = np.abs(g_ref) > 1e-3 * np.abs(g_ref).max()
+    # Adam's first step is -lr * sign(g) up to eps
+    np.testing.assert_allclose(dw[big], -lr * np.sign(g_ref[big]), rtol=0, atol=2e-5)
+    losses = [ctx.train_step(Xg, Yg, B, T, lr) for _ in range(30)]
+    assert losses[-1] < 0.8 * losses[0], losses
