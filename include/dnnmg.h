@@ -255,6 +255,34 @@ int dnnmg_train_step(dnnmg_ctx* ctx, const uint16_t* X, const float* Y, int B, i
 /* Zero the Adam moments and step count. */
 int dnnmg_reset_optimizer(dnnmg_ctx* ctx);
 
+/* ---- training corpus from plain fine-level trajectories (Sec. 3.1) ----------
+ * Training data comes from high-fidelity solutions on level L+1, localised
+ * to the time steps and patches.  Given two consecutive fine states
+ * x^{L+1}_{n-1}, x^{L+1}_n (device [3][nn of level L+1] doubles, e.g. from a
+ * second context with level_solve = L+1), dnnmg_make_sample injects
+ * x^{L+1}_{n-1} to level L, solves the level-L step with the right-hand side
+ * an exact correction would give, b^L = R (1/k) M^{L+1} v^{L+1}_{n-1}, and
+ * writes for every patch the raw (unstandardised) inputs at P(v^L_n)
+ * (device [P][C_in] float) and the targets v^{L+1}_n - P(v^L_n) at its fine
+ * nodes, zero on Dirichlet nodes (device [P][C_out] float).  It overwrites the
+ * context's level-L state and clears its DNN-MG state. */
+int dnnmg_make_sample(dnnmg_ctx* ctx, const double* xf_prev, const double* xf_next, float* X,
+                      float* Y, dnnmg_step_stats* stats);
+
+/* Per-feature mean and standard deviation (population, FP64 sums in fixed
+ * order) of `rows` raw input rows (device [rows][C_in] float); they become the
+ * context's standardisation (features with zero spread get std 1).  mean /
+ * std (host [C_in], may be NULL) receive them. */
+int dnnmg_feature_stats(dnnmg_ctx* ctx, const float* X, int64_t rows, float* mean, float* std);
+
+/* Assemble a training batch from a raw corpus laid out row = s * stride + p
+ * (s: time-step slot, p: patch): sequence b takes rows
+ * (idx[2b] + t) * stride + idx[2b+1], t = 0..T-1.  idx: device [B][2] int32.
+ * Writes Xb (device [B][T][C_in] bfloat16, standardised) and Yb (device
+ * [B][T][C_out] float). */
+int dnnmg_gather_batch(dnnmg_ctx* ctx, const float* X, const float* Y, const int* idx, int B,
+                       int T, int64_t stride, uint16_t* Xb, float* Yb);
+
 /* Direct solve of the coarsest multigrid level without any device allocation
  * (the paper has no counterpart: this is a deployment variant).
  *

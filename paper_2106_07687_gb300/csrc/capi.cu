@@ -315,6 +315,23 @@ int dnnmg_reset_optimizer(dnnmg_ctx* ctx) {
   return ctx->reset_optimizer();
 }
 
+int dnnmg_make_sample(dnnmg_ctx* ctx, const double* xf_prev, const double* xf_next, float* X,
+                      float* Y, dnnmg_step_stats* stats) {
+  if (!ctx || !xf_prev || !xf_next || !X || !Y) return DNNMG_ERR_ARG;
+  return ctx->make_sample(xf_prev, xf_next, X, Y, stats);
+}
+
+int dnnmg_feature_stats(dnnmg_ctx* ctx, const float* X, int64_t rows, float* mean, float* stdv) {
+  if (!ctx || !X) return DNNMG_ERR_ARG;
+  return ctx->feature_stats(X, rows, mean, stdv);
+}
+
+int dnnmg_gather_batch(dnnmg_ctx* ctx, const float* X, const float* Y, const int* idx, int B,
+                       int T, int64_t stride, uint16_t* Xb, float* Yb) {
+  if (!ctx || !X || !Y || !idx || !Xb || !Yb) return DNNMG_ERR_ARG;
+  return ctx->gather_batch(X, Y, idx, B, T, stride, Xb, Yb);
+}
+
 int dnnmg_gemm_bf16(dnnmg_ctx* ctx, const uint16_t* A, const uint16_t* B, float* C, int M, int N,
                     int K) {
   if (!ctx || !A || !B || !C) return DNNMG_ERR_ARG;

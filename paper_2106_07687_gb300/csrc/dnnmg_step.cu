@@ -33,10 +33,12 @@ __global__ void impose_dirichlet_kernel(Grid g, double* __restrict__ x) {
   if (f & kPFix) x[2 * g.nn + n] = 0.0;
 }
 
+template <bool RAW>
 __global__ void gather_kernel(Grid gL, Grid gF, const int* __restrict__ patch_cell, int P,
                               const double* __restrict__ xt, const double* __restrict__ r,
                               const float* __restrict__ mean, const float* __restrict__ stdv,
-                              double nu, double dt, uint16_t* __restrict__ X) {
+                              double nu, double dt, uint16_t* __restrict__ X,
+                              float* __restrict__ Xraw) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
   const int cell = patch_cell[p];
@@ -59,10 +61,96 @@ __global__ void gather_kernel(Grid gL, Grid gF, const int* __restrict__ patch_ce
   f[37] = 1.0f;
   f[38] = (float)(sqrt(su * su + sv * sv) / 9.0 * hL / nu);
   f[39] = (float)(dt / hL);
+  if (RAW) {
+#pragma unroll
+    for (int k = 0; k < 40; ++k) Xraw[(size_t)p * 40 + k] = f[k];
+    return;
+  }
   uint16_t* out = X + (size_t)p * 40;
 #pragma unroll
   for (int k = 0; k < 40; ++k)
     out[k] = __bfloat16_as_ushort(__float2bfloat16_rn((f[k] - mean[k]) / stdv[k]));
+}
+
+// Training target of a patch: (next fine velocity - prolongated velocity) at
+// its 3x3 nodes, zero on velocity Dirichlet nodes (where the correction is
+// forced to zero).
+__global__ void target_kernel(Grid gL, Grid gF, const int* __restrict__ patch_cell, int P,
+                              const double* __restrict__ xnext, const double* __restrict__ xt,
+                              float* __restrict__ Y) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const int cell = patch_cell[p];
+  const int I = cell % gL.nx, J = cell / gL.nx;
+#pragma unroll
+  for (int m = 0; m < 9; ++m) {
+    const int n = (2 * J + m / 3) * gF.nnx + 2 * I + m % 3;
+    const bool dir = gF.flags[n] & kVDir;
+    Y[(size_t)p * 18 + m] = dir ? 0.0f : (float)(xnext[n] - xt[n]);
+    Y[(size_t)p * 18 + 9 + m] = dir ? 0.0f : (float)(xnext[gF.nn + n] - xt[gF.nn + n]);
+  }
+}
+
+// Per-feature sums (x, x^2) over row chunks: partial[block][C][2] (FP64).
+__global__ void feature_sums_kernel(const float* __restrict__ X, long long rows, int C,
+                                    double* __restrict__ partial) {
+  extern __shared__ double sh[];  // [C][2] per warp: blockDim/32 * C * 2
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const long long chunk = (rows + gridDim.x - 1) / gridDim.x;
+  const long long lo = blockIdx.x * chunk, hi = min(rows, lo + chunk);
+  for (int c = lane; c < C; c += 32) {
+    double s = 0, q = 0;
+    for (long long r = lo + warp; r < hi; r += nw) {
+      const double v = X[r * C + c];
+      s += v;
+      q += v * v;
+    }
+    sh[(warp * C + c) * 2] = s;
+    sh[(warp * C + c) * 2 + 1] = q;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    double s = 0, q = 0;
+    for (int w = 0; w < nw; ++w) s += sh[(w * C + c) * 2], q += sh[(w * C + c) * 2 + 1];
+    partial[((size_t)blockIdx.x * C + c) * 2] = s;
+    partial[((size_t)blockIdx.x * C + c) * 2 + 1] = q;
+  }
+}
+
+__global__ void feature_stats_kernel(const double* __restrict__ partial, int nb, int C,
+                                     long long rows, float* __restrict__ mean,
+                                     float* __restrict__ stdv) {
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    double s = 0, q = 0;
+    for (int b = 0; b < nb; ++b) s += partial[((size_t)b * C + c) * 2], q += partial[((size_t)b * C + c) * 2 + 1];
+    const double m = s / (double)rows;
+    const double var = fmax(q / (double)rows - m * m, 0.0);
+    const double sd = sqrt(var);
+    mean[c] = (float)m;
+    stdv[c] = sd > 1e-6 * fmax(1.0, fabs(m)) ? (float)sd : 1.0f;  // constant features
+  }
+}
+
+// Batch b = rows idx[b][0] + t * stride + idx[b][1] (t = 0..T-1) of the raw
+// corpus, standardised and rounded to bfloat16; targets copied.
+__global__ void gather_batch_kernel(const float* __restrict__ Xraw, const float* __restrict__ Yc,
+                                    const int* __restrict__ idx, int B, int T, long long stride,
+                                    int Ci, int Co, const float* __restrict__ mean,
+                                    const float* __restrict__ stdv, uint16_t* __restrict__ Xb,
+                                    float* __restrict__ Yb) {
+  const long long total = (long long)B * T * (Ci + Co);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(e % (Ci + Co));
+    const long long bt = e / (Ci + Co);
+    const int t = (int)(bt % T), b = (int)(bt / T);
+    const long long row = (long long)idx[2 * b] * stride + (long long)t * stride + idx[2 * b + 1];
+    if (k < Ci)
+      Xb[bt * Ci + k] = __bfloat16_as_ushort(
+          __float2bfloat16_rn((Xraw[row * Ci + k] - mean[k]) / stdv[k]));
+    else
+      Yb[bt * Co + (k - Ci)] = Yc[row * Co + (k - Ci)];
+  }
 }
 
 // v_corr = xt + d at every fine node, d = mean of the predictions of the
@@ -110,7 +198,39 @@ void launch_gather(const Grid& gL, const Grid& gF, const int* patch_cell, int P,
                    uint16_t* X, cudaStream_t st) {
   if (P <= 0) return;
   note_launch();
-  gather_kernel<<<cdiv(P, 128), 128, 0, st>>>(gL, gF, patch_cell, P, xt, r, mean, stdv, nu, dt, X);
+  gather_kernel<false><<<cdiv(P, 128), 128, 0, st>>>(gL, gF, patch_cell, P, xt, r, mean, stdv, nu,
+                                                     dt, X, nullptr);
+}
+
+void launch_gather_raw(const Grid& gL, const Grid& gF, const int* patch_cell, int P,
+                       const double* xt, const double* r, double nu, double dt, float* Xraw,
+                       cudaStream_t st) {
+  if (P <= 0) return;
+  note_launch();
+  gather_kernel<true><<<cdiv(P, 128), 128, 0, st>>>(gL, gF, patch_cell, P, xt, r, nullptr, nullptr,
+                                                    nu, dt, nullptr, Xraw);
+}
+
+void launch_targets(const Grid& gL, const Grid& gF, const int* patch_cell, int P,
+                    const double* xnext, const double* xt, float* Y, cudaStream_t st) {
+  if (P <= 0) return;
+  note_launch();
+  target_kernel<<<cdiv(P, 128), 128, 0, st>>>(gL, gF, patch_cell, P, xnext, xt, Y);
+}
+
+void launch_feature_stats(const float* X, long long rows, int C, double* partial, int nb,
+                          float* mean, float* stdv, cudaStream_t st) {
+  note_launch();
+  feature_sums_kernel<<<nb, 256, sizeof(double) * 8 * C * 2, st>>>(X, rows, C, partial);
+  note_launch();
+  feature_stats_kernel<<<1, 64, 0, st>>>(partial, nb, C, rows, mean, stdv);
+}
+
+void launch_gather_batch(const float* Xraw, const float* Yc, const int* idx, int B, int T,
+                         long long stride, int Ci, int Co, const float* mean, const float* stdv,
+                         uint16_t* Xb, float* Yb, cudaStream_t st) {
+  note_launch();
+  gather_batch_kernel<<<1024, 256, 0, st>>>(Xraw, Yc, idx, B, T, stride, Ci, Co, mean, stdv, Xb, Yb);
 }
 
 void launch_scatter(const Grid& gL, const Grid& gF, const int* cell_patch, const float* out,

@@ -15,4 +15,18 @@ void launch_gather(const Grid& gL, const Grid& gF, const int* patch_cell, int P,
 void launch_scatter(const Grid& gL, const Grid& gF, const int* cell_patch, const float* out,
                     int c_out, const double* xt, double* vcorr, cudaStream_t st);
 
+// raw (unstandardised FP32) features and training targets of every patch
+void launch_gather_raw(const Grid& gL, const Grid& gF, const int* patch_cell, int P,
+                       const double* xt, const double* r, double nu, double dt, float* Xraw,
+                       cudaStream_t st);
+void launch_targets(const Grid& gL, const Grid& gF, const int* patch_cell, int P,
+                    const double* xnext, const double* xt, float* Y, cudaStream_t st);
+// per-feature mean / std (FP64 sums, fixed order) of rows x C features;
+// partial needs nb * C * 2 doubles
+void launch_feature_stats(const float* X, long long rows, int C, double* partial, int nb,
+                          float* mean, float* stdv, cudaStream_t st);
+void launch_gather_batch(const float* Xraw, const float* Yc, const int* idx, int B, int T,
+                         long long stride, int Ci, int Co, const float* mean, const float* stdv,
+                         uint16_t* Xb, float* Yb, cudaStream_t st);
+
 }  // namespace dnnmg

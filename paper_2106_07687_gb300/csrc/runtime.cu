@@ -505,6 +505,7 @@ int dnnmg_ctx::init_dnnmg() {
   hid = mem.alloc<float>((size_t)2 * P * nd.hidden);
   feat_mean = mem.alloc<float>(nd.c_in);
   feat_std = mem.alloc<float>(nd.c_in);
+  stat_partial = mem.alloc<double>((size_t)128 * nd.c_in * 2);
   if (!mem.ok()) return fail(DNNMG_ERR_CUDA, "device allocation failed");
   cudaMemcpyAsync(patch_cell, pc.data(), sizeof(int) * P, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(cell_patch, cp.data(), sizeof(int) * cp.size(), cudaMemcpyHostToDevice, st);
@@ -540,6 +541,56 @@ int dnnmg_ctx::dnnmg_correction() {
   prof.end(pr, st);
   have_vcorr = have_net_rhs = true;
   return net_check("dnnmg correction");
+}
+
+// One training sample per patch (corpus generation): the level-L step from
+// the injected fine state x^{L+1}_{n-1} with the right-hand side the DNN-MG
+// correction would produce if it were exact, b^L = R (1/k) M^{L+1} v^{L+1}_{n-1};
+// then the network inputs at P(v^L_n) and the targets v^{L+1}_n - P(v^L_n).
+int dnnmg_ctx::make_sample(const double* xf_prev, const double* xf_next, float* Xraw, float* Y,
+                           dnnmg_step_stats* s) {
+  if (!X) return fail(DNNMG_ERR_STATE, "DNN-MG needs replaced_levels = 1 and the default network");
+  const Grid gL = grid(L()), gF = grid(L() + 1);
+  const size_t n3L = 3 * (size_t)gL.nn;
+  launch_inject<double>(gF, gL, xf_prev, x64, 3, st);
+  launch_impose_dirichlet64(gL, x64, st);
+  cudaMemcpyAsync(xold64, x64, n3L * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(vcorr, xf_prev, 2 * sizeof(double) * gF.nn, cudaMemcpyDeviceToDevice, st);
+  cudaMemsetAsync(vcorr + 2 * gF.nn, 0, sizeof(double) * gF.nn, st);
+  launch_old_time_rhs64(gF, 1.0 / cfg.dt, vcorr, fF, st);
+  cudaMemsetAsync(f64, 0, n3L * sizeof(double), st);
+  launch_restrict_full64(gF, gL, fF, f64, 2, st);
+  dnnmg_step_stats tmp{};
+  int rc = newton(f64, s ? s : &tmp);
+  if (rc != DNNMG_OK && rc != DNNMG_ERR_NOT_CONVERGED) return rc;
+  launch_prolong_state64(gF, gL, x64, xtF, 3, st);
+  cudaMemcpyAsync(ximpF, xtF, 3 * sizeof(double) * gF.nn, cudaMemcpyDeviceToDevice, st);
+  launch_impose_dirichlet64(gF, ximpF, st);
+  launch_residual64(gF, s64F, ximpF, fF, rF, st);
+  launch_gather_raw(gL, gF, patch_cell, P, xtF, rF, cfg.nu, cfg.dt, Xraw, st);
+  launch_targets(gL, gF, patch_cell, P, xf_next, xtF, Y, st);
+  have_net_rhs = have_vcorr = false;
+  cudaStreamSynchronize(st);
+  return check("make_sample");
+}
+
+int dnnmg_ctx::feature_stats(const float* Xraw, long long rows, float* mean_h, float* std_h) {
+  if (!feat_mean) return fail(DNNMG_ERR_STATE, "no DNN-MG network in this context");
+  if (rows <= 0) return fail(DNNMG_ERR_ARG, "no rows");
+  launch_feature_stats(Xraw, rows, nd.c_in, stat_partial, 128, feat_mean, feat_std, st);
+  if (mean_h) cudaMemcpyAsync(mean_h, feat_mean, sizeof(float) * nd.c_in, cudaMemcpyDeviceToHost, st);
+  if (std_h) cudaMemcpyAsync(std_h, feat_std, sizeof(float) * nd.c_in, cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  return check("feature_stats");
+}
+
+int dnnmg_ctx::gather_batch(const float* Xraw, const float* Yc, const int* idx, int B, int T,
+                            long long stride, uint16_t* Xb, float* Yb) {
+  if (!feat_mean) return fail(DNNMG_ERR_STATE, "no DNN-MG network in this context");
+  if (B <= 0 || T <= 0 || stride <= 0) return fail(DNNMG_ERR_ARG, "bad batch shape");
+  launch_gather_batch(Xraw, Yc, idx, B, T, stride, nd.c_in, nd.c_out, feat_mean, feat_std, Xb, Yb,
+                      st);
+  return check("gather_batch");
 }
 
 int dnnmg_ctx::set_feature_stats(const float* mean, const float* stdv) {

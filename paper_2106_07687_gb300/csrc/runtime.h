@@ -160,6 +160,7 @@ struct dnnmg_ctx {
   uint16_t* X = nullptr;
   float *net_out = nullptr, *hid = nullptr, *feat_mean = nullptr, *feat_std = nullptr;
   bool have_net_rhs = false, have_vcorr = false;
+  double* stat_partial = nullptr;  // [128][C_in][2] feature-statistics partials
   // training workspace (capacity cfg.train_batch x cfg.train_seq)
   dnnmg::TrainBufs tb{};
   float *tr_ypred = nullptr, *loss_dev = nullptr, *grad = nullptr, *adam_m = nullptr,
@@ -203,5 +204,10 @@ struct dnnmg_ctx {
   int train_grad(const uint16_t* X, const float* Y, int B, int T, float* g, float* loss);
   int train_step(const uint16_t* X, const float* Y, int B, int T, float lr, float* loss);
   int reset_optimizer();
+  int make_sample(const double* xf_prev, const double* xf_next, float* Xraw, float* Y,
+                  dnnmg_step_stats* s);
+  int feature_stats(const float* Xraw, long long rows, float* mean_h, float* std_h);
+  int gather_batch(const float* Xraw, const float* Yc, const int* idx, int B, int T,
+                   long long stride, uint16_t* Xb, float* Yb);
   int newton(const double* f, dnnmg_step_stats* st);
 };

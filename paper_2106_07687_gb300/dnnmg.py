@@ -77,6 +77,10 @@ def _declare(lib):
         "dnnmg_train_grad": ([P, P, P, ctypes.c_int, ctypes.c_int, P, P], ctypes.c_int),
         "dnnmg_train_step": ([P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_float, P], ctypes.c_int),
         "dnnmg_reset_optimizer": ([P], ctypes.c_int),
+        "dnnmg_make_sample": ([P, P, P, P, P, P], ctypes.c_int),
+        "dnnmg_feature_stats": ([P, P, ctypes.c_int64, P, P], ctypes.c_int),
+        "dnnmg_gather_batch": ([P, P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int64, P, P],
+                               ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -238,6 +242,36 @@ class Context:
         self._check(self.lib.dnnmg_train_step(self.h, _ptr(X), _ptr(Y), B, T, lr,
                                               ctypes.byref(loss)))
         return loss.value
+
+    def make_sample(self, xf_prev, xf_next, X=None, Y=None):
+        """Raw inputs [P, C_in] and targets [P, C_out] (cuda float) from two fine states."""
+        ci, co = self.net_dims()
+        P = self.num_patches()
+        X = torch.empty(P, ci, dtype=torch.float32, device="cuda") if X is None else X
+        Y = torch.empty(P, co, dtype=torch.float32, device="cuda") if Y is None else Y
+        st = StepStats()
+        self._check(self.lib.dnnmg_make_sample(self.h, _ptr(xf_prev), _ptr(xf_next), _ptr(X),
+                                               _ptr(Y), ctypes.byref(st)), allow=(ERR_NOT_CONVERGED,))
+        return X, Y
+
+    def feature_stats(self, X, rows=None):
+        ci = self.net_dims()[0]
+        rows = X.numel() // ci if rows is None else rows
+        m = torch.empty(ci, dtype=torch.float32)
+        s = torch.empty(ci, dtype=torch.float32)
+        self._check(self.lib.dnnmg_feature_stats(self.h, _ptr(X), rows, c_void_p(m.data_ptr()),
+                                                 c_void_p(s.data_ptr())))
+        return m, s
+
+    def gather_batch(self, X, Y, idx, T, stride):
+        """idx: cuda int32 [B, 2]; returns (Xb bfloat16 [B,T,C_in], Yb float [B,T,C_out])."""
+        ci, co = self.net_dims()
+        B = idx.shape[0]
+        Xb = torch.empty(B, T, ci, dtype=torch.bfloat16, device="cuda")
+        Yb = torch.empty(B, T, co, dtype=torch.float32, device="cuda")
+        self._check(self.lib.dnnmg_gather_batch(self.h, _ptr(X), _ptr(Y), _ptr(idx), B, T, stride,
+                                                _ptr(Xb), _ptr(Yb)))
+        return Xb, Yb
 
     def gemm_bf16(self, A, B):
         """C = A @ B.T on the tensor cores (A [M,K], B [N,K] cuda bfloat16)."""
