@@ -1,15 +1,22 @@
-"""Benchmark of the DNN-MG hot path on one GB300 (or N replicas).
+"""Benchmark of the DNN-MG hot path on one GB300 (or N independent replicas).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--mode step|vcycle]
 
-Workload: a mixed-precision plain multigrid time step on the 1024x256
-channel (level 6, 790,275 DOFs, nu = 0.005, dt = 0.005; obstacle seeded);
-the input is the solver state already resident in HBM.  One JSON line is
-printed by rank 0.  --impl reference times the FP64 CPU oracle on the host
-cores on a bounded sample of the same workload.
+Workload (the DNN-MG configuration): multigrid solve on the 512x128 channel
+(level 5, 198,531 DOFs) and the patch network on the 1024x256 level
+(61,440 patches, 2-layer GRU with hidden size 64 + MLP 128, BF16 with FP32
+accumulation); held-out viscosity nu = 0.0065, dt = 0.005, mixed FP32/FP64
+solver, obstacle seeded.  Before the timed region the network is trained by
+the library's own kernels on a bounded corpus from plain fine trajectories
+(nu = 0.005 and 0.008).  Timed: K DNN-MG steps, and for comparison K plain
+MG(L) steps, K plain MG(L+1) steps (the reference) and K MG(L+1) steps at a
+loose tolerance, each from the impulsive start, L2 flushed before each step.
+`value` = DNN-MG time steps per second over all ranks.  One JSON line is
+printed by rank 0.  --impl reference times the FP64 CPU oracle (DNN-MG step)
+on the host cores on a bounded sample of the same workload.
 """
 import argparse
-import ctypes
 import json
 import os
 import subprocess
@@ -21,9 +28,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "time/step & V-cycle DOF/s: DNN-MG vs plain MG on 1 GB300 at equal L2 err; %HBM/TC peak"
-LEVEL, NU, DT = 6, 0.005, 0.005
-WORKLOAD = "plain MG time step, 1024x256 channel (level 6, 790,275 DOFs), nu=0.005, dt=0.005, mixed FP32/FP64"
-ORACLE_LEVEL = 5          # bounded CPU sample: one oracle step on 512x128, scaled by DOFs
+L, NU, DT = 5, 0.0065, 0.005
+NU_TRAIN = (0.005, 0.008)
+CORPUS_STEPS, TRAIN_ITERS, TRAIN_B, TRAIN_T = 24, 150, 4096, 8
+WORKLOAD = ("DNN-MG time step: multigrid on the 512x128 channel (level 5, 198,531 DOFs) + patch "
+            "network on 1024x256 (level 6, 61,440 patches, GRU 2x64 + MLP 128, BF16), nu=0.0065, "
+            "dt=0.005, mixed FP32/FP64")
+ORACLE_L = 4              # bounded CPU sample: oracle DNN-MG step with L = 4, scaled by DOFs
 L2_BYTES = 129 * 2 ** 20
 
 
@@ -31,29 +42,37 @@ def ndof(level):
     return 3 * (16 * 2 ** level + 1) * (4 * 2 ** level + 1)
 
 
+def nnodes(level):
+    return ndof(level) // 3
+
+
 def fluid_cells(level):
-    n = 16 * 4 * 4 ** level
-    return n - 4 * 4 ** level
+    return 16 * 4 * 4 ** level - 4 * 4 ** level
 
 
-def oracle_step_seconds(level, steps=1, warm=1):
-    """Time the FP64 oracle on `steps` plain time steps (after `warm`) in a
-    fresh single-threaded process; returns seconds per step."""
+def oracle_dnnmg_seconds(level, steps=1, warm=1):
+    """FP64 oracle DNN-MG steps (level-L solve + fine residual, features,
+    network, scatter, Rhs, restriction) in a fresh single-threaded process."""
     code = f"""
 import time, sys
+import numpy as np
 sys.path.insert(0, {ROOT!r})
 import synthetic
-from oracle import fem, mesh, newton
+from oracle import dnnmg, fem, mesh, net, newton
 ob = synthetic.obstacle_block(1000)
 levels = mesh.hierarchy({level}, obstacle=ob)
+fine = mesh.Level({level} + 1, obstacle=ob)
 prm = fem.Params(nu={NU}, dt={DT})
 opt = newton.SolverOptions()
+spec = net.NetSpec()
+params = spec.unflatten(synthetic.random_weights(1, spec.num_params(), 0.02))
 x = mesh.initial_state(levels[-1])
+state = dict(bL=None, vcorr=None, h=np.zeros((2, len(levels[-1].fluid_cells), 64)))
 for _ in range({warm}):
-    x, *_ = newton.time_step(levels, x, prm, opt)
+    x, state, _ = dnnmg.time_step(levels, fine, x, state, spec, params, prm, opt)
 t = time.perf_counter()
 for _ in range({steps}):
-    x, *_ = newton.time_step(levels, x, prm, opt)
+    x, state, _ = dnnmg.time_step(levels, fine, x, state, spec, params, prm, opt)
 print((time.perf_counter() - t) / {steps})
 """
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
@@ -63,13 +82,13 @@ print((time.perf_counter() - t) / {steps})
 
 
 def cpu_baseline(steps=1):
-    s = oracle_step_seconds(ORACLE_LEVEL, steps=steps)
-    scale = ndof(LEVEL) / ndof(ORACLE_LEVEL)
+    s = oracle_dnnmg_seconds(ORACLE_L, steps=steps)
+    scale = ndof(L) / ndof(ORACLE_L)
     return {"value": 1.0 / (s * scale), "unit": "time steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"{steps} plain time step(s) of the FP64 oracle on the 512x128 channel "
-                      f"(level {ORACLE_LEVEL}, {ndof(ORACLE_LEVEL)} DOFs, same physics) after one "
-                      f"warm-up step, {s:.2f} s/step, scaled by the DOF ratio "
-                      f"{scale:.3f} to level {LEVEL}; single-threaded"}
+            "sample": f"{steps} DNN-MG time step(s) of the FP64 oracle with the solve on the "
+                      f"256x64 channel (level {ORACLE_L}) and the network on 512x128, after one "
+                      f"warm-up step, {s:.2f} s/step, scaled by the level-L DOF ratio "
+                      f"{scale:.3f} to the benchmarked level {L}; single-threaded"}
 
 
 class ClockSampler:
@@ -106,8 +125,9 @@ class ClockSampler:
     def summary(self):
         if not self.rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
-        sm = sorted(float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit())
-        mx = max(float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit())
+        num = lambda v: v.replace(".", "", 1).isdigit()
+        sm = sorted(float(r[0]) for r in self.rows if num(r[0]))
+        mx = max(float(r[1]) for r in self.rows if num(r[1]))
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i] == "Active"})
         return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
@@ -118,135 +138,228 @@ def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             p = json.load(f)
-        return p["hbm_gbs"], p.get("bf16_tflops"), "measured"
+        return p["hbm_gbs"], p["bf16_tflops"], p.get("bf16_tflops_sustained", p["bf16_tflops"]), \
+            "measured"
     except (OSError, KeyError, ValueError):
-        return 6800.0, 1900.0, "fallback"
+        return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+def net_flops(c_in=40, H=64, mlp=128, c_out=18):
+    """FLOPs (2 per multiply-add) per patch and step: forward, and forward +
+    backward (activation gradients of all but the first layer's input, weight
+    gradients of every layer)."""
+    fwd = 3 * H * c_in + 3 * H * H + 3 * H * H + 3 * H * H + mlp * H + c_out * mlp
+    act = c_out * mlp + mlp * H + 3 * H * H + 3 * H * H + 3 * H * H
+    return 2 * fwd, 2 * (fwd + act + fwd)
 
 
 def run_ours(args, rank, world):
+    import numpy as np
     import torch
-    from paper_2106_07687_gb300 import build, dnnmg
+    from paper_2106_07687_gb300 import build, dnnmg as dn
     import synthetic
 
     build.build()
-    lib = dnnmg.load()
-    lib.dnnmg_profile.argtypes = [ctypes.c_void_p, ctypes.c_int]
-    lib.dnnmg_profile_read.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
-                                       ctypes.c_void_p, ctypes.c_void_p]
-    lib.dnnmg_kernel_launches.restype = ctypes.c_uint64
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
     ob = synthetic.obstacle_block(1000 + rank)
-    ctx = dnnmg.Context(level_solve=LEVEL, precision=dnnmg.MIXED, nu=NU, dt=DT,
-                        obstacle_i0=ob[0], obstacle_j0=ob[1])
+    common = dict(precision=dn.MIXED, dt=DT, obstacle_i0=ob[0], obstacle_j0=ob[1])
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    hbm, bf16, bf16_sus, peak_kind = peaks()
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    stats = []
-    for _ in range(args.warmup):
-        ctx.step(dnnmg.PLAIN)
-    barrier()
-    lib.dnnmg_profile(ctx.h, 1)
-    launches0 = lib.dnnmg_kernel_launches()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    with ClockSampler(dev) as clk:
-        t_wall = time.perf_counter()
-        for k in range(args.steps):
-            flush.zero_()
-            ev[k][0].record(stream)
-            stats.append(ctx.step(dnnmg.PLAIN))
-            ev[k][1].record(stream)
-        torch.cuda.synchronize()
-        t_wall = time.perf_counter() - t_wall
-    barrier()
-    launches = lib.dnnmg_kernel_launches() - launches0
-    ms_steps = sum(a.elapsed_time(b) for a, b in ev)
-    stage = {}
-    names = ["vanka_pass", "vanka_setup", "apply", "defect", "transfer", "coarse_factor",
-             "coarse_solve", "krylov", "residual64"]
-    for sid, nm in enumerate(names):
-        n, t = ctypes.c_int64(), ctypes.c_double()
-        lib.dnnmg_profile_read(ctx.h, sid, -1, ctypes.byref(n), ctypes.byref(t))
-        stage[nm] = {"launches": n.value, "ms": round(t.value, 4)}
-    n, t = ctypes.c_int64(), ctypes.c_double()
-    lib.dnnmg_profile_read(ctx.h, 0, LEVEL, ctypes.byref(n), ctypes.byref(t))
-    vp_launches, vp_ms = n.value, t.value
-    lib.dnnmg_profile(ctx.h, 0)
-
-    # V-cycle throughput on level 6 at the current linearisation
-    x = ctx.get_state()
-    ctx.linearize(x)
-    b = torch.from_numpy(synthetic.random_vector(7, ndof(LEVEL))).float().cuda()
-    xv = torch.empty_like(b)
+    # ---- corpus from plain fine trajectories and training (untimed setup) ----
+    net_ctx = dn.Context(level_solve=L, nu=NU, train_batch=TRAIN_B, train_seq=TRAIN_T, **common)
+    P = net_ctx.num_patches()
+    Xs, Ys = [], []
+    for nu in NU_TRAIN:
+        fctx = dn.Context(level_solve=L + 1, nu=nu, **common)
+        sctx = dn.Context(level_solve=L, nu=nu, **common)
+        prev = fctx.get_state()
+        for _ in range(CORPUS_STEPS):
+            fctx.step(dn.PLAIN)
+            cur = fctx.get_state()
+            X, Y = sctx.make_sample(prev, cur)
+            Xs.append(X)
+            Ys.append(Y)
+            prev = cur
+        fctx.close()
+        sctx.close()
+    Xc, Yc = torch.cat(Xs).contiguous(), torch.cat(Ys).contiguous()
+    del Xs, Ys
+    net_ctx.feature_stats(Xc)
+    net_ctx.set_weights(synthetic.random_weights(77, net_ctx.num_params(), 0.05).astype(np.float32))
+    rng = np.random.default_rng(3)
+    idx_all = []
+    for _ in range(TRAIN_ITERS):
+        tid = rng.integers(0, len(NU_TRAIN), TRAIN_B)
+        start = rng.integers(0, CORPUS_STEPS - TRAIN_T + 1, TRAIN_B)
+        idx_all.append(np.stack([tid * CORPUS_STEPS + start, rng.integers(0, P, TRAIN_B)], 1))
+    idx_dev = torch.from_numpy(np.stack(idx_all).astype(np.int32)).cuda()
+    losses = []
+    for it in range(5):   # warm-up
+        Xb, Yb = net_ctx.gather_batch(Xc, Yc, idx_dev[it].contiguous(), TRAIN_T, P)
+        losses.append(net_ctx.train_step(Xb, Yb, TRAIN_B, TRAIN_T, 2e-3))
+    torch.cuda.synchronize()
+    te0, te1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    te0.record(stream)
+    for it in range(5, TRAIN_ITERS):
+        Xb, Yb = net_ctx.gather_batch(Xc, Yc, idx_dev[it].contiguous(), TRAIN_T, P)
+        lr = 2e-3 if it < 0.7 * TRAIN_ITERS else 5e-4
+        losses.append(net_ctx.train_step(Xb, Yb, TRAIN_B, TRAIN_T, lr))
+    te1.record(stream)
+    torch.cuda.synchronize()
+    train_ms = te0.elapsed_time(te1) / (TRAIN_ITERS - 5)
+    del Xc, Yc
+    # network forward alone (dnnmg_patch_infer over all patches)
+    xin = torch.randn(P, 40, device="cuda").to(torch.bfloat16)
+    hin = torch.zeros(2, P, 64, device="cuda")
+    out = torch.empty(P, 18, device="cuda")
     for _ in range(3):
-        ctx.vcycle(LEVEL, b, xv)
+        net_ctx.patch_infer(xin, hin, out)
+    torch.cuda.synchronize()
+    te0.record(stream)
     R = 20
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
     for _ in range(R):
-        ctx.vcycle(LEVEL, b, xv)
-    e1.record(stream)
+        net_ctx.patch_infer(xin, hin, out)
+    te1.record(stream)
     torch.cuda.synchronize()
-    vcycle_ms = e0.elapsed_time(e1) / R
+    infer_ms = te0.elapsed_time(te1) / R
 
-    # end to end through the public API with host buffers: H2D state, step, D2H state
-    host_x = torch.empty(ndof(LEVEL), dtype=torch.float64).pin_memory()
-    host_x.copy_(x.cpu())
-    dev_x = torch.empty_like(x)
-    E = max(2, min(args.steps, 5))
+    # ---- timed comparison from the impulsive start -----------------------------
+    ref_ctx = dn.Context(level_solve=L + 1, nu=NU, **common)
+    loose_ctx = dn.Context(level_solve=L + 1, nu=NU, newton_tol=1e-5, gmres_rtol=1e-2, **common)
+    coarse_ctx = dn.Context(level_solve=L, nu=NU, **common)
+    runs = {"dnnmg": (net_ctx, dn.NET), "mg_L": (coarse_ctx, dn.PLAIN),
+            "mg_L+1": (ref_ctx, dn.PLAIN), "mg_L+1_loose": (loose_ctx, dn.PLAIN)}
+    for name, (c, mode) in runs.items():
+        for _ in range(args.warmup):
+            c.step(mode)
+    barrier()
+    launches0 = dn.kernel_launches()
+    times = {k: 0.0 for k in runs}
+    stats = {k: [] for k in runs}
+    errs = {k: [] for k in runs}
+    net_ctx.profile(True)
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    with ClockSampler(dev) as clk:
+        for k in range(args.steps):
+            for name, (c, mode) in runs.items():
+                flush.zero_()
+                ev[0].record(stream)
+                stats[name].append(c.step(mode))
+                ev[1].record(stream)
+                torch.cuda.synchronize()
+                times[name] += ev[0].elapsed_time(ev[1])
+            vref = ref_ctx.get_state()[:2 * nnodes(L + 1)]
+            nref = float(torch.linalg.vector_norm(vref))
+            d = lambda v: float(torch.linalg.vector_norm(v - vref)) / nref
+            errs["dnnmg"].append(d(net_ctx.get_fine_velocity()))
+            errs["mg_L"].append(d(coarse_ctx.prolongate(L, coarse_ctx.get_state())[:2 * nnodes(L + 1)]))
+            errs["mg_L+1_loose"].append(d(loose_ctx.get_state()[:2 * nnodes(L + 1)]))
+            errs["mg_L+1"].append(0.0)
+    barrier()
+    launches = dn.kernel_launches() - launches0
+    stage = {}
+    for sid, nm in enumerate(dn.STAGES):
+        n, t = net_ctx.profile_read(sid)
+        stage[nm] = {"launches": n, "ms": round(t, 4)}
+    vp_n, vp_ms = net_ctx.profile_read(0, L)
+    net_ctx.profile(False)
+
+    # ---- V-cycle throughput at levels 6 and 5 (current linearisations) -----------
+    def vcycle_ms(c, level):
+        x = c.get_state()
+        c.linearize(x)
+        b = torch.from_numpy(synthetic.random_vector(7, ndof(level))).float().cuda()
+        xv = torch.empty_like(b)
+        for _ in range(3):
+            c.vcycle(level, b, xv)
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for _ in range(10):
+            c.vcycle(level, b, xv)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / 10
+    vc6, vc5 = vcycle_ms(ref_ctx, L + 1), vcycle_ms(coarse_ctx, L)
+
+    # ---- end to end: DNN-MG steps with the state exchanged through host memory ----
+    host_in = torch.empty(ndof(L), dtype=torch.float64).pin_memory()
+    host_out = torch.empty(ndof(L), dtype=torch.float64).pin_memory()
+    host_in.copy_(net_ctx.get_state().cpu())
+    E = max(3, min(args.steps, 8))
     torch.cuda.synchronize()
     t_e2e = time.perf_counter()
     for _ in range(E):
-        dev_x.copy_(host_x, non_blocking=True)
-        ctx.set_state(dev_x)
-        ctx.step(dnnmg.PLAIN)
-        host_x.copy_(ctx.get_state(), non_blocking=True)
+        net_ctx.step_io(dn.NET, host_in, host_out)
+        host_in, host_out = host_out, host_in
     torch.cuda.synchronize()
     t_e2e = (time.perf_counter() - t_e2e) / E
 
-    local = {"ms": ms_steps, "wall": t_wall, "vp_ms": vp_ms, "vp_launches": vp_launches}
+    ms = times["dnnmg"]
     if world > 1:
-        t = torch.tensor([ms_steps], dtype=torch.float64, device="cuda")
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        local["ms"] = float(t.item())
+        ms = float(t.item())
     if rank != 0:
         return None
-
-    ms_per_step = local["ms"] / args.steps
-    hbm, _, peak_kind = peaks()
-    bytes_per_pass = fluid_cells(LEVEL) / 4 * 576 + ndof(LEVEL) / 3 * 44
-    avg_pass_ms = vp_ms / max(vp_launches, 1)
+    K = args.steps
+    bytes_per_pass = fluid_cells(L) / 4 * 576 + nnodes(L) * 44
+    avg_pass_ms = vp_ms / max(vp_n, 1)
     achieved = bytes_per_pass / (avg_pass_ms * 1e-3) / 1e9
+    f_fwd, f_train = net_flops()
+    mean = lambda v: sum(v) / len(v)
+    comparison = {
+        name: {"ms_per_step": times[name] / K,
+               "newton_its": mean([s["newton_its"] for s in stats[name]]),
+               "gmres_its": mean([s["gmres_its"] for s in stats[name]]),
+               "fallbacks": sum(s["fallback"] for s in stats[name]),
+               "vel_l2_err_vs_mg_L+1": mean(errs[name]),
+               "vel_l2_err_last": errs[name][-1]}
+        for name in runs}
     return {
         "metric": METRIC,
-        "value": world * args.steps / (local["ms"] * 1e-3),
+        "value": world * K / (ms * 1e-3),
         "unit": "time steps/s",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_per_step,
+        "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": ms / K,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "level": LEVEL, "dofs": ndof(LEVEL),
-                   "obstacle_block": list(ob), "l2": "flushed (256 MB write) before every step",
-                   "parallelism": f"replicas x{world}"},
-        "vcycle": {"ms": vcycle_ms, "dof_per_s": ndof(LEVEL) / (vcycle_ms * 1e-3)},
-        "newton_its_per_step": sum(s["newton_its"] for s in stats) / len(stats),
-        "gmres_its_per_step": sum(s["gmres_its"] for s in stats) / len(stats),
-        "stages_ms": stage,
-        "roofline": {"kernel": "vanka_pass (level 6, FP32)", "bound": "hbm",
-                     "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "peak_kind": peak_kind, "traffic": None,
+        "dtype": "f32+f64 solver, bf16 network", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "level_solve": L, "level_net": L + 1, "dofs_L": ndof(L),
+                   "dofs_L+1": ndof(L + 1), "patches": P, "obstacle_block": list(ob),
+                   "nu": NU, "dt": DT, "l2": "flushed (256 MB write) before every step",
+                   "parallelism": f"independent replicas x{world}",
+                   "network_training": f"{TRAIN_ITERS} Adam steps, B={TRAIN_B}, T={TRAIN_T}, "
+                                       f"corpus {len(NU_TRAIN)} fine trajectories x "
+                                       f"{CORPUS_STEPS} steps (nu {NU_TRAIN})"},
+        "comparison": comparison,
+        "vcycle": {"level6_ms": vc6, "level6_dof_per_s": ndof(6) / (vc6 * 1e-3),
+                   "level5_ms": vc5, "level5_dof_per_s": ndof(5) / (vc5 * 1e-3)},
+        "stages_ms_dnnmg": stage,
+        "roofline": {"kernel": f"vanka_pass_kernel<float> (level {L}, one colour pass)",
+                     "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
                      "algorithmic_bytes_per_launch": bytes_per_pass,
-                     "avg_launch_ms": avg_pass_ms},
+                     "avg_launch_ms": avg_pass_ms, "launches": vp_n},
+        "network": {"forward_ms": infer_ms, "patches": P,
+                    "forward_tflops": f_fwd * P / (infer_ms * 1e-3) / 1e12,
+                    "forward_frac_bf16": f_fwd * P / (infer_ms * 1e-3) / 1e12 / bf16,
+                    "forward_hbm_gbs": P * (80 + 1024 + 72) / (infer_ms * 1e-3) / 1e9,
+                    "train_ms_per_iter": train_ms,
+                    "train_patch_steps_per_s": TRAIN_B * TRAIN_T / (train_ms * 1e-3),
+                    "train_tflops": f_train * TRAIN_B * TRAIN_T / (train_ms * 1e-3) / 1e12,
+                    "train_frac_bf16_sustained":
+                        f_train * TRAIN_B * TRAIN_T / (train_ms * 1e-3) / 1e12 / bf16_sus,
+                    "loss_first": losses[0], "loss_last": losses[-1]},
         "clocks": clk.summary(),
         "e2e": {"value": 1.0 / t_e2e, "unit": "time steps/s",
-                "h2d_bytes_per_step": 8 * ndof(LEVEL), "d2h_bytes_per_step": 8 * ndof(LEVEL)},
+                "h2d_bytes_per_step": 8 * ndof(L), "d2h_bytes_per_step": 8 * ndof(L)},
         "gpu_launches": int(launches),
     }
 
@@ -255,31 +368,28 @@ def run_vcycles(args):
     """Level-6 V-cycles only (after --warmup untimed ones): a short command
     for kernel profilers."""
     import torch
-    from paper_2106_07687_gb300 import build, dnnmg
+    from paper_2106_07687_gb300 import build, dnnmg as dn
     import synthetic
     build.build()
     ob = synthetic.obstacle_block(1000)
-    ctx = dnnmg.Context(level_solve=LEVEL, precision=dnnmg.MIXED, nu=NU, dt=DT,
-                        obstacle_i0=ob[0], obstacle_j0=ob[1])
+    ctx = dn.Context(level_solve=6, precision=dn.MIXED, nu=0.005, dt=DT, obstacle_i0=ob[0],
+                     obstacle_j0=ob[1])
     x = ctx.get_state()
     ctx.linearize(x)
-    b = torch.from_numpy(synthetic.random_vector(7, ndof(LEVEL))).float().cuda()
+    b = torch.from_numpy(synthetic.random_vector(7, ndof(6))).float().cuda()
     xv = torch.empty_like(b)
     for _ in range(args.warmup + args.steps):
-        ctx.vcycle(LEVEL, b, xv)
+        ctx.vcycle(6, b, xv)
     torch.cuda.synchronize()
-    print(json.dumps({"mode": "vcycle", "level": LEVEL, "cycles": args.warmup + args.steps,
+    print(json.dumps({"mode": "vcycle", "level": 6, "cycles": args.warmup + args.steps,
                       "norm": float(xv.norm())}))
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    steps = []
-    for _ in range(args.warmup):
-        pass
     t = time.perf_counter()
-    per = [oracle_step_seconds(4, steps=1, warm=0) * ndof(LEVEL) / ndof(4)
+    per = [oracle_dnnmg_seconds(ORACLE_L - 1, steps=1, warm=0) * ndof(L) / ndof(ORACLE_L - 1)
            for _ in range(args.steps)]
     mean = sum(per) / len(per)
     v = 1.0 / mean
@@ -287,11 +397,12 @@ def run_reference(args, rank, world):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": mean * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "level": LEVEL, "dofs": ndof(LEVEL)},
+            "config": {"workload": WORKLOAD, "level_solve": L, "dofs_L": ndof(L)},
             "cpu_baseline": {"value": v, "unit": "time steps/s", "cores": 1, "kind": "oracle",
-                             "sample": "each step: the first plain time step of the FP64 oracle "
-                                       "on the 256x64 channel (level 4) from the impulsive start, "
-                                       "scaled by the DOF ratio to level 6; single-threaded"},
+                             "sample": f"each step: the first DNN-MG time step of the FP64 oracle "
+                                       f"with the solve on the 128x32 channel (level "
+                                       f"{ORACLE_L - 1}) from the impulsive start, scaled by the "
+                                       f"level-L DOF ratio to level {L}; single-threaded"},
             "e2e": {"value": v, "unit": "time steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
             "wall_s": time.perf_counter() - t}

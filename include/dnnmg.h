@@ -84,7 +84,8 @@ typedef struct dnnmg_config {
   int32_t fallback_newton_its; /* DNN-MG step redone without the network if Newton needs more */
   int32_t train_batch;     /* largest training batch B (sequences) of dnnmg_train_*, 0 = none */
   int32_t train_seq;       /* largest training sequence length T */
-  int32_t reserved[5];
+  int32_t coarse_refresh;  /* time steps between refactorisations of the coarse level (>= 1) */
+  int32_t reserved[4];
 } dnnmg_config;
 
 /* Per-step statistics returned by dnnmg_step(). */
@@ -102,8 +103,8 @@ typedef struct dnnmg_step_stats {
  * newton_tol = 1e-10, gmres_rtol = 1e-4, omega = 0.8, eps_damp = 1,
  * obstacle at level-0 cell (2, 1), L = 3, coarse level 1, replaced_levels = 1,
  * FP64, newton_max = 20, gmres_m = 20, gmres_maxit = 200, V(2,2), GRU 2 x 64,
- * dense width 128, fallback_newton_its = 8.  Returns DNNMG_ERR_ARG if cfg is
- * NULL. */
+ * dense width 128, fallback_newton_its = 8, coarse_refresh = 4.  Returns
+ * DNNMG_ERR_ARG if cfg is NULL. */
 int dnnmg_default_config(dnnmg_config* cfg);
 
 /* Create a context: builds the level hierarchy coarse..L (and L+1..L+r for the
@@ -168,6 +169,21 @@ int dnnmg_residual(dnnmg_ctx* ctx, const double* x, const double* f, double* r);
  * Returns DNNMG_ERR_NOT_CONVERGED if Newton hit newton_max (the step is still
  * taken), DNNMG_ERR_NUMERICAL on NaN/Inf. */
 int dnnmg_step(dnnmg_ctx* ctx, int mode, dnnmg_step_stats* stats);
+
+/* One time step with the level-L state exchanged through HOST memory (the
+ * coupling of a host-resident application, e.g. an FE code that owns the
+ * state): x_in ([3][nn] doubles, host, pinned for best speed) becomes the
+ * state v^L_{n-1} (Dirichlet values imposed; the network's hidden state and
+ * stored right-hand side are kept), the step runs as dnnmg_step(), and the new
+ * state is copied to x_out (host).  Either pointer may be NULL to skip that
+ * copy. */
+int dnnmg_step_io(dnnmg_ctx* ctx, int mode, const double* x_in, double* x_out,
+                  dnnmg_step_stats* stats);
+
+/* Unmasked bilinear prolongation P of all three fields from level `level`
+ * to level + 1 (Algorithm 1 line 6): xc device [3][nn(level)] doubles, xf
+ * device [3][nn(level + 1)] doubles; level + 1 <= L + replaced_levels. */
+int dnnmg_prolongate(dnnmg_ctx* ctx, int level, const double* xc, double* xf);
 
 /* ---- patch network (Sec. 2.2, Sec. 3.1, Table 1) ------------------------------
  * Two stacked GRU cells (hidden 64, PyTorch gate convention r, z, n) and a

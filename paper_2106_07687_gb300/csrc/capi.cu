@@ -11,6 +11,7 @@
 
 #include "../../include/dnnmg.h"
 #include "kernels.h"
+#include "dnnmg_step.h"
 #include "runtime.h"
 
 using namespace dnnmg;
@@ -161,6 +162,7 @@ int dnnmg_default_config(dnnmg_config* c) {
   c->gru_layers = 2;
   c->mlp_width = 128;
   c->fallback_newton_its = 8;
+  c->coarse_refresh = 4;
   return DNNMG_OK;
 }
 
@@ -231,6 +233,31 @@ int dnnmg_step(dnnmg_ctx* ctx, int mode, dnnmg_step_stats* stats) {
   if (!ctx) return DNNMG_ERR_ARG;
   if (mode != DNNMG_PLAIN && mode != DNNMG_NET) return ctx->fail(DNNMG_ERR_ARG, "unknown mode");
   return ctx->step(mode, stats);
+}
+
+int dnnmg_step_io(dnnmg_ctx* ctx, int mode, const double* x_in, double* x_out,
+                  dnnmg_step_stats* stats) {
+  if (!ctx) return DNNMG_ERR_ARG;
+  if (mode != DNNMG_PLAIN && mode != DNNMG_NET) return ctx->fail(DNNMG_ERR_ARG, "unknown mode");
+  const size_t bytes = 3 * sizeof(double) * ctx->grid(ctx->L()).nn;
+  if (x_in) {
+    cudaMemcpyAsync(ctx->x64, x_in, bytes, cudaMemcpyHostToDevice, ctx->st);
+    dnnmg::launch_impose_dirichlet64(ctx->grid(ctx->L()), ctx->x64, ctx->st);
+  }
+  int rc = ctx->step(mode, stats);
+  if (x_out && (rc == DNNMG_OK || rc == DNNMG_ERR_NOT_CONVERGED)) {
+    cudaMemcpyAsync(x_out, ctx->x64, bytes, cudaMemcpyDeviceToHost, ctx->st);
+    if (cudaStreamSynchronize(ctx->st) != cudaSuccess) return ctx->check("step_io");
+  }
+  return rc;
+}
+
+int dnnmg_prolongate(dnnmg_ctx* ctx, int level, const double* xc, double* xf) {
+  if (!ctx || !xc || !xf) return DNNMG_ERR_ARG;
+  if (level < 0 || level + 1 >= (int)ctx->lv.size())
+    return ctx->fail(DNNMG_ERR_ARG, "level out of range");
+  dnnmg::launch_prolong_state64(ctx->grid(level + 1), ctx->grid(level), xc, xf, 3, ctx->st);
+  return ctx->check("prolongate");
 }
 
 int dnnmg_profile(dnnmg_ctx* ctx, int enable) {

@@ -296,7 +296,7 @@ int dnnmg_ctx::init() {
   if (c.precision != DNNMG_FP64 && c.precision != DNNMG_MIXED)
     return fail(DNNMG_ERR_ARG, "unknown precision");
   if (c.gmres_m < 1 || c.gmres_m > 40 || c.gmres_maxit < 1 || c.newton_max < 1 || c.nu1 < 0 ||
-      c.nu2 < 0)
+      c.nu2 < 0 || c.coarse_refresh < 1)
     return fail(DNNMG_ERR_ARG, "solver parameters out of range");
   const int nlev = c.level_solve + c.replaced_levels + 1;
   for (int l = 0; l < nlev; ++l) lv.push_back(make_level(l, c.obstacle_i0, c.obstacle_j0));
@@ -561,6 +561,7 @@ int dnnmg_ctx::make_sample(const double* xf_prev, const double* xf_next, float* 
   cudaMemsetAsync(f64, 0, n3L * sizeof(double), st);
   launch_restrict_full64(gF, gL, fF, f64, 2, st);
   dnnmg_step_stats tmp{};
+  steps_taken = 0;  // a new state: refactor the coarse level
   int rc = newton(f64, s ? s : &tmp);
   if (rc != DNNMG_OK && rc != DNNMG_ERR_NOT_CONVERGED) return rc;
   launch_prolong_state64(gF, gL, x64, xtF, 3, st);
@@ -570,6 +571,7 @@ int dnnmg_ctx::make_sample(const double* xf_prev, const double* xf_next, float* 
   launch_gather_raw(gL, gF, patch_cell, P, xtF, rF, cfg.nu, cfg.dt, Xraw, st);
   launch_targets(gL, gF, patch_cell, P, xf_next, xtF, Y, st);
   have_net_rhs = have_vcorr = false;
+  steps_taken = 0;
   cudaStreamSynchronize(st);
   return check("make_sample");
 }
@@ -699,6 +701,7 @@ int dnnmg_ctx::set_state(const double* x) {
   cudaMemcpyAsync(x64, x, 3 * sizeof(double) * grid(L()).nn, cudaMemcpyDeviceToDevice, st);
   launch_impose_dirichlet64(grid(L()), x64, st);
   have_net_rhs = have_vcorr = false;
+  steps_taken = 0;  // the next step refactors the coarse level
   if (hid) cudaMemsetAsync(hid, 0, sizeof(float) * 2 * P * nd.hidden, st);
   cudaStreamSynchronize(st);
   return check("set_state");
@@ -734,8 +737,10 @@ int dnnmg_ctx::newton(const double* f, dnnmg_step_stats* s) {
   int it = 0, gits = 0;
   while (nrm > cfg.newton_tol && it < cfg.newton_max) {
     if (!std::isfinite(nrm)) return fail(DNNMG_ERR_NUMERICAL, "non-finite Newton residual");
-    // the coarse-level factorisation is refreshed once per time step
-    if (int rc = solver->linearize(x64, it == 0)) return rc;
+    // the coarse-level factorisation is refreshed at the first Newton step of
+    // every coarse_refresh-th time step (a lagged preconditioner component)
+    const bool refresh = it == 0 && steps_taken % cfg.coarse_refresh == 0;
+    if (int rc = solver->linearize(x64, refresh)) return rc;
     int its = 0;
     if (int rc = solver->solve(r64, x64, cfg.eps_damp, &its)) return rc;
     gits += its;
@@ -781,6 +786,7 @@ int dnnmg_ctx::step(int mode, dnnmg_step_stats* stats) {
     const int rc2 = dnnmg_correction();
     if (rc2 != DNNMG_OK) rc = rc2;
   }
+  ++steps_taken;
   cudaEventRecord(ev1, st);
   cudaEventSynchronize(ev1);
   float ms = 0;

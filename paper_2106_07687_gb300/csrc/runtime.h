@@ -144,6 +144,7 @@ struct dnnmg_ctx {
   double* h_scalars = nullptr; // pinned host scalars
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   dnnmg::Prof prof;
+  long long steps_taken = 0;   // time steps since setup (coarse refresh schedule)
   // patch network
   dnnmg::NetDims nd{};
   bool net_ok = false;

@@ -13,6 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libdnnmg.so")
 
 OK, ERR_ARG, ERR_CUDA, ERR_NOT_CONVERGED, ERR_NUMERICAL, ERR_TIMEOUT, ERR_STATE = range(7)
+STAGES = ("vanka_pass", "vanka_setup", "apply", "defect", "transfer", "coarse_factor",
+          "coarse_solve", "krylov", "residual64", "network", "train")
 FP64, MIXED = 0, 1
 PLAIN, NET = 0, 1
 
@@ -28,7 +30,8 @@ class Config(ctypes.Structure):
                 ("precision", c_int32), ("newton_max", c_int32), ("gmres_m", c_int32),
                 ("gmres_maxit", c_int32), ("nu1", c_int32), ("nu2", c_int32), ("hidden", c_int32),
                 ("gru_layers", c_int32), ("mlp_width", c_int32), ("fallback_newton_its", c_int32),
-                ("train_batch", c_int32), ("train_seq", c_int32), ("reserved", c_int32 * 5)]
+                ("train_batch", c_int32), ("train_seq", c_int32), ("coarse_refresh", c_int32),
+                ("reserved", c_int32 * 4)]
 
 
 class StepStats(ctypes.Structure):
@@ -79,6 +82,11 @@ def _declare(lib):
         "dnnmg_reset_optimizer": ([P], ctypes.c_int),
         "dnnmg_make_sample": ([P, P, P, P, P, P], ctypes.c_int),
         "dnnmg_feature_stats": ([P, P, ctypes.c_int64, P, P], ctypes.c_int),
+        "dnnmg_step_io": ([P, ctypes.c_int, P, P, P], ctypes.c_int),
+        "dnnmg_prolongate": ([P, ctypes.c_int, P, P], ctypes.c_int),
+        "dnnmg_profile": ([P, ctypes.c_int], ctypes.c_int),
+        "dnnmg_profile_read": ([P, ctypes.c_int, ctypes.c_int, P, P], ctypes.c_int),
+        "dnnmg_kernel_launches": ([], ctypes.c_uint64),
         "dnnmg_gather_batch": ([P, P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int64, P, P],
                                ctypes.c_int),
     }
@@ -86,6 +94,11 @@ def _declare(lib):
         f = getattr(lib, name)
         f.argtypes, f.restype = args, res
     return lib
+
+
+def kernel_launches():
+    """Kernels launched by libdnnmg in this process so far."""
+    return int(load().dnnmg_kernel_launches())
 
 
 def load():
@@ -280,6 +293,29 @@ class Context:
         C = torch.empty(M, N, dtype=torch.float32, device="cuda")
         self._check(self.lib.dnnmg_gemm_bf16(self.h, _ptr(A), _ptr(B), _ptr(C), M, N, K))
         return C
+
+    def step_io(self, mode, x_in_host, x_out_host):
+        """Time step with the state exchanged through host memory (CPU tensors)."""
+        st = StepStats()
+        pin = c_void_p(x_in_host.data_ptr()) if x_in_host is not None else None
+        pout = c_void_p(x_out_host.data_ptr()) if x_out_host is not None else None
+        self._check(self.lib.dnnmg_step_io(self.h, mode, pin, pout, ctypes.byref(st)),
+                    allow=(ERR_NOT_CONVERGED,))
+        return st.as_dict()
+
+    def prolongate(self, level, xc):
+        xf = torch.empty(self.ndof(level + 1), dtype=torch.float64, device="cuda")
+        self._check(self.lib.dnnmg_prolongate(self.h, level, _ptr(xc), _ptr(xf)))
+        return xf
+
+    def profile(self, enable=True):
+        self._check(self.lib.dnnmg_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self, stage, level=-1):
+        n, t = ctypes.c_int64(), ctypes.c_double()
+        self._check(self.lib.dnnmg_profile_read(self.h, stage, level, ctypes.byref(n),
+                                                ctypes.byref(t)))
+        return n.value, t.value
 
     def step(self, mode=PLAIN):
         st = StepStats()
