@@ -85,7 +85,8 @@ typedef struct dnnmg_config {
   int32_t train_batch;     /* largest training batch B (sequences) of dnnmg_train_*, 0 = none */
   int32_t train_seq;       /* largest training sequence length T */
   int32_t coarse_refresh;  /* time steps between refactorisations of the coarse level (>= 1) */
-  int32_t reserved[4];
+  int32_t persistent_vcycle; /* 1: one cooperative launch per V-cycle; 0: one launch per stage */
+  int32_t reserved[3];
 } dnnmg_config;
 
 /* Per-step statistics returned by dnnmg_step(). */
@@ -103,8 +104,8 @@ typedef struct dnnmg_step_stats {
  * newton_tol = 1e-10, gmres_rtol = 1e-4, omega = 0.8, eps_damp = 1,
  * obstacle at level-0 cell (2, 1), L = 3, coarse level 1, replaced_levels = 1,
  * FP64, newton_max = 20, gmres_m = 20, gmres_maxit = 200, V(2,2), GRU 2 x 64,
- * dense width 128, fallback_newton_its = 8, coarse_refresh = 4.  Returns
- * DNNMG_ERR_ARG if cfg is NULL. */
+ * dense width 128, fallback_newton_its = 8, coarse_refresh = 4,
+ * persistent_vcycle = 0.  Returns DNNMG_ERR_ARG if cfg is NULL. */
 int dnnmg_default_config(dnnmg_config* cfg);
 
 /* Create a context: builds the level hierarchy coarse..L (and L+1..L+r for the
@@ -338,6 +339,7 @@ int dnnmg_coarse_solve_noalloc(const dnnmg_config* cfg, const double* vbar, cons
 #define DNNMG_STAGE_RESIDUAL 8      /* FP64 nonlinear residual */
 #define DNNMG_STAGE_NETWORK 9       /* DNN-MG gather, patch network, scatter and Rhs */
 #define DNNMG_STAGE_TRAIN 10        /* training forward, backward and optimiser */
+#define DNNMG_STAGE_VCYCLE 11       /* one persistent V-cycle launch (all of the above in it) */
 
 /* enable != 0: reset the timers and record CUDA events around the launches
  * of each stage from now on; enable = 0: stop recording.  Recording costs one

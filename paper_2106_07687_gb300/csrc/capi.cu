@@ -163,6 +163,7 @@ int dnnmg_default_config(dnnmg_config* c) {
   c->mlp_width = 128;
   c->fallback_newton_its = 8;
   c->coarse_refresh = 4;
+  c->persistent_vcycle = 0;
   return DNNMG_OK;
 }
 

@@ -55,7 +55,7 @@ void launch_vanka_setup(const Grid& g, const Sten<T>& s, const T* vb, T* inv, in
 template <typename T>
 void launch_vanka_pass(const Grid& g, const Sten<T>& s, int colour, const T* b, const T* xin,
                        const T* vb, const T* inv, T omega, T* xout, cudaStream_t st);
-inline int vanka_slots(const Grid& g) { return (g.nx / 2 + 1) * (g.ny / 2 + 1); }
+__host__ __device__ inline int vanka_slots(const Grid& g) { return (g.nx / 2 + 1) * (g.ny / 2 + 1); }
 
 // Coarse direct solve (coarse.cu) -------------------------------------------
 // Assemble the banded Jacobian of the coarsest level (FP64), factor it with

@@ -7,6 +7,7 @@
 
 #include "dnnmg_step.h"
 #include "runtime.h"
+#include "vcycle.h"
 
 using namespace dnnmg;
 
@@ -60,6 +61,28 @@ class Solver final : public SolverBase {
     one_ = c_->mem.alloc<double>(1);
     partials_ = c_->mem.alloc<double>(dots_partials(n_, 2 * m_ + 4));
     if (!c_->mem.ok()) return c_->fail(DNNMG_ERR_CUDA, "device allocation failed");
+    // persistent V-cycle: level table and one phase list per possible top level
+    if (cfg.persistent_vcycle) {
+      std::vector<VLevel<T>> hv(K_ + 1);
+      for (int k = 0; k <= K_; ++k)
+        hv[k] = VLevel<T>{lv_[k].g, lv_[k].s, lv_[k].x, lv_[k].x2, lv_[k].b, lv_[k].d,
+                          lv_[k].vb, lv_[k].inv};
+      dlv_ = c_->mem.alloc<VLevel<T>>(K_ + 1);
+      std::vector<Phase> all;
+      for (int k = 0; k <= K_; ++k) {
+        const std::vector<Phase> p = vcycle_phases(k, cfg.nu1, cfg.nu2);
+        ph_off_.push_back((int)all.size());
+        ph_n_.push_back((int)p.size());
+        all.insert(all.end(), p.begin(), p.end());
+      }
+      dph_ = c_->mem.alloc<Phase>(all.size());
+      if (!c_->mem.ok()) return c_->fail(DNNMG_ERR_CUDA, "device allocation failed");
+      cudaMemcpyAsync(dlv_, hv.data(), sizeof(VLevel<T>) * hv.size(), cudaMemcpyHostToDevice, st_);
+      cudaMemcpyAsync(dph_, all.data(), sizeof(Phase) * all.size(), cudaMemcpyHostToDevice, st_);
+      cudaStreamSynchronize(st_);
+      coarse_nd_ = 3 * lv_[0].g.nn;
+      vgrid_ = vcycle_grid<T>(coarse_nd_);
+    }
     const double one = 1.0;
     cudaMemcpyAsync(one_, &one, sizeof(double), cudaMemcpyHostToDevice, st_);
     return c_->check("solver init");
@@ -211,6 +234,16 @@ class Solver final : public SolverBase {
 
   // One V(nu1, nu2) cycle on level k for A x = b with x = 0 on entry.
   void cycle(int k, const T* b, T* x) {
+    if (vgrid_ > 0 && !persistent_failed_) {
+      const int p = c_->prof.begin(DNNMG_STAGE_VCYCLE, lv_[k].level, st_);
+      const int rc = launch_vcycle_persistent<T>(dlv_, dph_ + ph_off_[k], ph_n_[k], k, b, x, ainv_,
+                                                 (T)c_->cfg.omega, vgrid_, coarse_nd_, st_);
+      c_->prof.end(p, st_);
+      if (rc == 0) return;
+      persistent_failed_ = true;  // fall back to one launch per stage
+      cudaGetLastError();
+      launch_fill<T>(x, T(0), 3 * (size_t)lv_[k].g.nn, st_);
+    }
     Lev& l = lv_[k];
     if (k == 0) {
       const int p = c_->prof.begin(DNNMG_STAGE_COARSE_SOLVE, l.level, st_);
@@ -246,6 +279,11 @@ class Solver final : public SolverBase {
          *y_ = nullptr, *one_ = nullptr, *partials_ = nullptr;
   bool linearized_ = false;
   bool coarse_done_ = false;
+  VLevel<T>* dlv_ = nullptr;
+  Phase* dph_ = nullptr;
+  std::vector<int> ph_off_, ph_n_;
+  int vgrid_ = 0, coarse_nd_ = 0;
+  bool persistent_failed_ = false;
 };
 
 }  // namespace

@@ -4,6 +4,7 @@
 // One thread per node; the 2D block of 32x4 threads covers a tile of nodes
 // with x fastest, so each warp reads contiguous rows of the SoA fields.
 #include "kernels.h"
+#include "vbody.cuh"
 
 namespace dnnmg {
 
@@ -32,22 +33,7 @@ __global__ void __launch_bounds__(kBX* kBY)
                   const T* __restrict__ vb, T* __restrict__ d, bool masked) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   if (i >= g.nnx || j >= g.nny) return;
-  const int n = j * g.nnx + i;
-  T ru, rv, rp;
-  node_rows<T, false, true>(g, s, i, j, x, vb, ru, rv, rp);
-  const uint8_t f = g.flags[n];
-  const int nn = g.nn;
-  if (f & kVDir) {
-    d[n] = masked ? T(0) : b[n] - x[n];
-    d[nn + n] = masked ? T(0) : b[nn + n] - x[nn + n];
-  } else {
-    d[n] = b[n] - ru;
-    d[nn + n] = b[nn + n] - rv;
-  }
-  if (f & kPFix)
-    d[2 * nn + n] = masked ? T(0) : b[2 * nn + n] - x[2 * nn + n];
-  else
-    d[2 * nn + n] = b[2 * nn + n] - rp;
+  defect_node<T>(g, s, b, x, vb, d, masked, i, j);
 }
 
 __global__ void __launch_bounds__(kBX* kBY)

@@ -3,6 +3,7 @@
 // Inside the V-cycle both P and R act on free DOFs only; the DNN-MG state and
 // right-hand-side transfers use the unmasked operators.
 #include "kernels.h"
+#include "vbody.cuh"
 
 namespace dnnmg {
 
@@ -10,68 +11,19 @@ namespace {
 
 constexpr int kBX = 32, kBY = 4;
 
-__device__ __forceinline__ uint8_t bit_of(int c) { return c < 2 ? kVDir : kPFix; }
-
-// Weight of fine offset o in {-1, 0, 1} in the full-weighting stencil.
-template <typename T>
-__device__ __forceinline__ T wt(int o) {
-  return o == 0 ? T(1) : T(0.5);
-}
-
 template <typename T, bool MASK>
 __global__ void restrict_kernel(Grid f, Grid c, const T* __restrict__ d, T* __restrict__ bc,
                                 int ncomp) {
   const int I = blockIdx.x * kBX + threadIdx.x, J = blockIdx.y * kBY + threadIdx.y;
   if (I >= c.nnx || J >= c.nny) return;
-  const int nc = J * c.nnx + I;
-  for (int comp = 0; comp < ncomp; ++comp) {
-    const uint8_t bit = bit_of(comp);
-    T acc = 0;
-    if (!(MASK && (c.flags[nc] & bit))) {
-      for (int dj = -1; dj <= 1; ++dj) {
-        const int j = 2 * J + dj;
-        if (j < 0 || j >= f.nny) continue;
-        for (int di = -1; di <= 1; ++di) {
-          const int i = 2 * I + di;
-          if (i < 0 || i >= f.nnx) continue;
-          const int nf = j * f.nnx + i;
-          if (MASK && (f.flags[nf] & bit)) continue;
-          acc += wt<T>(di) * wt<T>(dj) * d[comp * f.nn + nf];
-        }
-      }
-    }
-    bc[comp * c.nn + nc] = acc;
-  }
-}
-
-// value of the bilinear interpolant of coarse field xc at fine node (i, j)
-template <typename T, bool MASK>
-__device__ __forceinline__ T interp(const Grid& c, const T* __restrict__ xc, uint8_t bit, int i,
-                                    int j) {
-  const int I0 = i >> 1, J0 = j >> 1;
-  const int nI = (i & 1) ? 2 : 1, nJ = (j & 1) ? 2 : 1;
-  const T w = T(1) / T(nI * nJ);
-  T acc = 0;
-  for (int b = 0; b < nJ; ++b)
-    for (int a = 0; a < nI; ++a) {
-      const int n = (J0 + b) * c.nnx + I0 + a;
-      if (MASK && (c.flags[n] & bit)) continue;
-      acc += xc[n];
-    }
-  return w * acc;
+  restrict_node<T, MASK>(f, c, d, bc, ncomp, I, J);
 }
 
 template <typename T>
 __global__ void prolong_add_kernel(Grid f, Grid c, const T* __restrict__ xc, T* __restrict__ x) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   if (i >= f.nnx || j >= f.nny) return;
-  const int n = j * f.nnx + i;
-  const uint8_t fl = f.flags[n];
-  for (int comp = 0; comp < 3; ++comp) {
-    const uint8_t bit = bit_of(comp);
-    if (fl & bit) continue;
-    x[comp * f.nn + n] += interp<T, true>(c, xc + comp * c.nn, bit, i, j);
-  }
+  prolong_add_node<T>(f, c, xc, x, i, j);
 }
 
 __global__ void prolong_state_kernel(Grid f, Grid c, const double* __restrict__ xc,
@@ -80,7 +32,7 @@ __global__ void prolong_state_kernel(Grid f, Grid c, const double* __restrict__ 
   if (i >= f.nnx || j >= f.nny) return;
   const int n = j * f.nnx + i;
   for (int comp = 0; comp < ncomp; ++comp)
-    xf[comp * f.nn + n] = interp<double, false>(c, xc + comp * c.nn, 0, i, j);
+    xf[comp * f.nn + n] = interp_node<double, false>(c, xc + comp * c.nn, 0, i, j);
 }
 
 template <typename T>

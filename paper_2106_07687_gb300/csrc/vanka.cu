@@ -14,6 +14,7 @@
 // nodes outside the colour's fluid cells are copied, so x_out is complete and
 // the next colour reads it without races.
 #include "kernels.h"
+#include "vbody.cuh"
 
 namespace dnnmg {
 
@@ -138,52 +139,8 @@ __global__ void __launch_bounds__(kPassThreads)
     vanka_pass_kernel(Grid g, Sten<T> s, int colour, const T* __restrict__ b,
                       const T* __restrict__ xin, const T* __restrict__ vb,
                       const T* __restrict__ inv, T omega, T* __restrict__ xout) {
-  const int cx = colour & 1, cy = colour >> 1;
-  const int sx = g.nx / 2 + 1;
-  const int nslots = sx * (g.ny / 2 + 1);
-  const int tid = blockIdx.x * kPassThreads + threadIdx.x;
-  const int slot = tid >> 2, a = tid & 3;
-  const bool slot_ok = slot < nslots;
-  const int ci = 2 * (slot % sx) - cx, cj = 2 * (slot / sx) - cy;
-  const int i = ci + (a & 1), j = cj + (a >> 1);
-  const bool node_ok = slot_ok && i >= 0 && j >= 0 && i <= g.nx && j <= g.ny;
-  const bool cell_ok = slot_ok && ci >= 0 && cj >= 0 && ci < g.nx && cj < g.ny &&
-                       !g.solid[(cj < 0 ? 0 : cj) * g.nx + (ci < 0 ? 0 : ci)];
-  const int nn = g.nn;
-  const int n = node_ok ? j * g.nnx + i : 0;
-  T du = 0, dv = 0, dp = 0;
-  if (node_ok && cell_ok) {
-    T ru, rv, rp;
-    node_rows<T, false, true>(g, s, i, j, xin, vb, ru, rv, rp);
-    const uint8_t f = g.flags[n];
-    du = b[n] - ((f & kVDir) ? xin[n] : ru);
-    dv = b[nn + n] - ((f & kVDir) ? xin[nn + n] : rv);
-    dp = b[2 * nn + n] - ((f & kPFix) ? xin[2 * nn + n] : rp);
-  }
-  const int lane = threadIdx.x & 31, base = lane & ~3;
-  T d[12];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    d[k] = __shfl_sync(0xffffffffu, du, base + k);
-    d[4 + k] = __shfl_sync(0xffffffffu, dv, base + k);
-    d[8 + k] = __shfl_sync(0xffffffffu, dp, base + k);
-  }
-  if (!node_ok) return;
-  if (cell_ok) {
-    const T* row0 = inv + (size_t)colour * 144 * nslots + slot;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const int r = c * 4 + a;
-      T acc = 0;
-#pragma unroll
-      for (int k = 0; k < 12; ++k) acc += row0[(size_t)(r * 12 + k) * nslots] * d[k];
-      xout[c * nn + n] = xin[c * nn + n] + omega * acc;
-    }
-  } else {
-    xout[n] = xin[n];
-    xout[nn + n] = xin[nn + n];
-    xout[2 * nn + n] = xin[2 * nn + n];
-  }
+  vanka_pass_thread<T>(g, s, colour, b, xin, vb, inv, omega, xout,
+                       blockIdx.x * kPassThreads + threadIdx.x);
 }
 
 }  // namespace

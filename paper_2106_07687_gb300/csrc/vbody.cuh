@@ -1,0 +1,153 @@
+// Per-thread bodies of the multigrid kernels, shared by the one-launch-per-
+// stage kernels and the persistent V-cycle kernel.
+#pragma once
+#include "common.cuh"
+
+namespace dnnmg {
+
+// One colour pass of the Vanka smoother for global thread `tid` (four
+// consecutive threads form the quad of one cell; every lane of a warp must
+// call this together because of the shuffles).  See vanka.cu.
+template <typename T>
+__device__ __forceinline__ void vanka_pass_thread(const Grid& g, const Sten<T>& s, int colour,
+                                                  const T* __restrict__ b,
+                                                  const T* __restrict__ xin,
+                                                  const T* __restrict__ vb,
+                                                  const T* __restrict__ inv, T omega,
+                                                  T* __restrict__ xout, int tid) {
+  const int cx = colour & 1, cy = colour >> 1;
+  const int sx = g.nx / 2 + 1;
+  const int nslots = sx * (g.ny / 2 + 1);
+  const int slot = tid >> 2, a = tid & 3;
+  const bool slot_ok = slot < nslots;
+  const int ci = 2 * (slot % sx) - cx, cj = 2 * (slot / sx) - cy;
+  const int i = ci + (a & 1), j = cj + (a >> 1);
+  const bool node_ok = slot_ok && i >= 0 && j >= 0 && i <= g.nx && j <= g.ny;
+  const bool cell_ok = slot_ok && ci >= 0 && cj >= 0 && ci < g.nx && cj < g.ny &&
+                       !g.solid[(cj < 0 ? 0 : cj) * g.nx + (ci < 0 ? 0 : ci)];
+  const int nn = g.nn;
+  const int n = node_ok ? j * g.nnx + i : 0;
+  T du = 0, dv = 0, dp = 0;
+  if (node_ok && cell_ok) {
+    T ru, rv, rp;
+    node_rows<T, false, true>(g, s, i, j, xin, vb, ru, rv, rp);
+    const uint8_t f = g.flags[n];
+    du = b[n] - ((f & kVDir) ? xin[n] : ru);
+    dv = b[nn + n] - ((f & kVDir) ? xin[nn + n] : rv);
+    dp = b[2 * nn + n] - ((f & kPFix) ? xin[2 * nn + n] : rp);
+  }
+  const int lane = threadIdx.x & 31, base = lane & ~3;
+  T d[12];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    d[k] = __shfl_sync(0xffffffffu, du, base + k);
+    d[4 + k] = __shfl_sync(0xffffffffu, dv, base + k);
+    d[8 + k] = __shfl_sync(0xffffffffu, dp, base + k);
+  }
+  if (!node_ok) return;
+  if (cell_ok) {
+    const T* row0 = inv + (size_t)colour * 144 * nslots + slot;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int r = c * 4 + a;
+      T acc = 0;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) acc += row0[(size_t)(r * 12 + k) * nslots] * d[k];
+      xout[c * nn + n] = xin[c * nn + n] + omega * acc;
+    }
+  } else {
+    xout[n] = xin[n];
+    xout[nn + n] = xin[nn + n];
+    xout[2 * nn + n] = xin[2 * nn + n];
+  }
+}
+
+// d = b - A'(vbar) x at node (i, j); constrained rows: b - x, or 0 if masked.
+template <typename T>
+__device__ __forceinline__ void defect_node(const Grid& g, const Sten<T>& s, const T* __restrict__ b,
+                                            const T* __restrict__ x, const T* __restrict__ vb,
+                                            T* __restrict__ d, bool masked, int i, int j) {
+  const int n = j * g.nnx + i;
+  T ru, rv, rp;
+  node_rows<T, false, true>(g, s, i, j, x, vb, ru, rv, rp);
+  const uint8_t f = g.flags[n];
+  const int nn = g.nn;
+  if (f & kVDir) {
+    d[n] = masked ? T(0) : b[n] - x[n];
+    d[nn + n] = masked ? T(0) : b[nn + n] - x[nn + n];
+  } else {
+    d[n] = b[n] - ru;
+    d[nn + n] = b[nn + n] - rv;
+  }
+  if (f & kPFix)
+    d[2 * nn + n] = masked ? T(0) : b[2 * nn + n] - x[2 * nn + n];
+  else
+    d[2 * nn + n] = b[2 * nn + n] - rp;
+}
+
+__device__ __forceinline__ uint8_t field_bit(int c) { return c < 2 ? kVDir : kPFix; }
+
+// Coarse node (I, J) of R d = P^T d on free DOFs (full-weighting stencil).
+template <typename T, bool MASK>
+__device__ __forceinline__ void restrict_node(const Grid& f, const Grid& c, const T* __restrict__ d,
+                                              T* __restrict__ bc, int ncomp, int I, int J) {
+  const int nc = J * c.nnx + I;
+  for (int comp = 0; comp < ncomp; ++comp) {
+    const uint8_t bit = field_bit(comp);
+    T acc = 0;
+    if (!(MASK && (c.flags[nc] & bit))) {
+      for (int dj = -1; dj <= 1; ++dj) {
+        const int j = 2 * J + dj;
+        if (j < 0 || j >= f.nny) continue;
+        for (int di = -1; di <= 1; ++di) {
+          const int i = 2 * I + di;
+          if (i < 0 || i >= f.nnx) continue;
+          const int nf = j * f.nnx + i;
+          if (MASK && (f.flags[nf] & bit)) continue;
+          acc += (di == 0 ? T(1) : T(0.5)) * (dj == 0 ? T(1) : T(0.5)) * d[comp * f.nn + nf];
+        }
+      }
+    }
+    bc[comp * c.nn + nc] = acc;
+  }
+}
+
+// Value of the bilinear interpolant of a coarse field at fine node (i, j).
+template <typename T, bool MASK>
+__device__ __forceinline__ T interp_node(const Grid& c, const T* __restrict__ xc, uint8_t bit,
+                                         int i, int j) {
+  const int I0 = i >> 1, J0 = j >> 1;
+  const int nI = (i & 1) ? 2 : 1, nJ = (j & 1) ? 2 : 1;
+  const T w = T(1) / T(nI * nJ);
+  T acc = 0;
+  for (int bb = 0; bb < nJ; ++bb)
+    for (int aa = 0; aa < nI; ++aa) {
+      const int n = (J0 + bb) * c.nnx + I0 + aa;
+      if (MASK && (c.flags[n] & bit)) continue;
+      acc += xc[n];
+    }
+  return w * acc;
+}
+
+// x += P xc at fine node (i, j) on free DOFs.
+template <typename T>
+__device__ __forceinline__ void prolong_add_node(const Grid& f, const Grid& c,
+                                                 const T* __restrict__ xc, T* __restrict__ x,
+                                                 int i, int j) {
+  const int n = j * f.nnx + i;
+  const uint8_t fl = f.flags[n];
+  for (int comp = 0; comp < 3; ++comp) {
+    const uint8_t bit = field_bit(comp);
+    if (fl & bit) continue;
+    x[comp * f.nn + n] += interp_node<T, true>(c, xc + comp * c.nn, bit, i, j);
+  }
+}
+
+// Band numbering of the coarsest level: DOF p = (i * nny + j) * 3 + c.
+__host__ __device__ inline int band_to_level(const Grid& g, int p) {
+  const int c = p % 3, node = p / 3;
+  const int i = node / g.nny, j = node % g.nny;
+  return c * g.nn + j * g.nnx + i;
+}
+
+}  // namespace dnnmg

@@ -1,0 +1,37 @@
+// Persistent V-cycle (internal to libdnnmg).
+#pragma once
+#include <vector>
+
+#include "kernels.h"
+
+namespace dnnmg {
+
+// Everything the cycle needs on one level; an array of these lives in
+// device memory (index = level - coarsest level).
+template <typename T>
+struct VLevel {
+  Grid g;
+  Sten<T> s;
+  T *x, *x2, *b, *d, *vb, *inv;
+};
+
+enum PhaseType { kPhasePass, kPhaseDefect, kPhaseRestrict, kPhaseCoarse, kPhaseProlong, kPhaseZeroTop };
+
+// in / out select the level's iterate (0: x, the caller's buffer on the top
+// level; 1: the second buffer x2)
+struct Phase {
+  int type, level, colour, in, out;
+};
+
+// phase list of one V(nu1, nu2) cycle with top level `top`, x zeroed first
+std::vector<Phase> vcycle_phases(int top, int nu1, int nu2);
+// co-resident grid size for the cooperative launch (0 if not available)
+template <typename T>
+int vcycle_grid(int coarse_nd);
+// returns 0 on success
+template <typename T>
+int launch_vcycle_persistent(const VLevel<T>* lv, const Phase* ph, int nph, int top, const T* topb,
+                             T* topx, const double* Ainv, T omega, int grid, int coarse_nd,
+                             cudaStream_t st);
+
+}  // namespace dnnmg

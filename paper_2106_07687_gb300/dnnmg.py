@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "libdnnmg.so")
 
 OK, ERR_ARG, ERR_CUDA, ERR_NOT_CONVERGED, ERR_NUMERICAL, ERR_TIMEOUT, ERR_STATE = range(7)
 STAGES = ("vanka_pass", "vanka_setup", "apply", "defect", "transfer", "coarse_factor",
-          "coarse_solve", "krylov", "residual64", "network", "train")
+          "coarse_solve", "krylov", "residual64", "network", "train", "vcycle")
 FP64, MIXED = 0, 1
 PLAIN, NET = 0, 1
 
@@ -31,7 +31,7 @@ class Config(ctypes.Structure):
                 ("gmres_maxit", c_int32), ("nu1", c_int32), ("nu2", c_int32), ("hidden", c_int32),
                 ("gru_layers", c_int32), ("mlp_width", c_int32), ("fallback_newton_its", c_int32),
                 ("train_batch", c_int32), ("train_seq", c_int32), ("coarse_refresh", c_int32),
-                ("reserved", c_int32 * 4)]
+                ("persistent_vcycle", c_int32), ("reserved", c_int32 * 3)]
 
 
 class StepStats(ctypes.Structure):
