@@ -286,7 +286,7 @@ def run_ours(args, rank, world):
     for sid, nm in enumerate(dn.STAGES):
         n, t = net_ctx.profile_read(sid)
         stage[nm] = {"launches": n, "ms": round(t, 4)}
-    vc_n, vc_ms_prof = net_ctx.profile_read(11, L)
+    vp_n, vp_ms = net_ctx.profile_read(0, L)
     net_ctx.profile(False)
 
     # ---- V-cycle throughput at levels 6 and 5 (current linearisations) -----------
@@ -327,9 +327,9 @@ def run_ours(args, rank, world):
     if rank != 0:
         return None
     K = args.steps
-    bytes_per_cycle = vcycle_bytes(L)
-    avg_cycle_ms = vc_ms_prof / max(vc_n, 1)
-    achieved = bytes_per_cycle / (avg_cycle_ms * 1e-3) / 1e9
+    bytes_per_pass = fluid_cells(L) / 4 * 576 + nnodes(L) * 44
+    avg_pass_ms = vp_ms / max(vp_n, 1)
+    achieved = bytes_per_pass / (avg_pass_ms * 1e-3) / 1e9 if vp_n else 0.0
     f_fwd, f_train = net_flops()
     mean = lambda v: sum(v) / len(v)
     comparison = {
@@ -356,16 +356,19 @@ def run_ours(args, rank, world):
                                        f"corpus {len(NU_TRAIN)} fine trajectories x "
                                        f"{CORPUS_STEPS} steps (nu {NU_TRAIN})"},
         "comparison": comparison,
-        "vcycle": {"level6_ms": vc6, "level6_dof_per_s": ndof(6) / (vc6 * 1e-3),
+        "vcycle": {"split_level_dnnmg": net_ctx.vcycle_split(), "split_level_fine": ref_ctx.vcycle_split(),
+                   "level6_ms": vc6, "level6_dof_per_s": ndof(6) / (vc6 * 1e-3),
                    "level6_gbs": vcycle_bytes(6) / (vc6 * 1e-3) / 1e9,
                    "level5_ms": vc5, "level5_dof_per_s": ndof(5) / (vc5 * 1e-3),
                    "level5_gbs": vcycle_bytes(5) / (vc5 * 1e-3) / 1e9},
         "stages_ms_dnnmg": stage,
-        "roofline": {"kernel": f"vcycle_kernel<float> (one persistent V(2,2) cycle, top level {L})",
+        "roofline": {"kernel": f"vanka_pass_tiled_kernel<float> (level {L}, one colour pass)",
                      "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
-                     "algorithmic_bytes_per_launch": bytes_per_cycle,
-                     "avg_launch_ms": avg_cycle_ms, "launches": vc_n},
+                     "algorithmic_bytes_per_launch": bytes_per_pass,
+                     "avg_launch_ms": avg_pass_ms, "launches": vp_n,
+                     "vcycle_level5_frac": vcycle_bytes(5) / (vc5 * 1e-3) / 1e9 / hbm,
+                     "vcycle_level6_frac": vcycle_bytes(6) / (vc6 * 1e-3) / 1e9 / hbm},
         "network": {"forward_ms": infer_ms, "patches": P,
                     "forward_tflops": f_fwd * P / (infer_ms * 1e-3) / 1e12,
                     "forward_frac_bf16": f_fwd * P / (infer_ms * 1e-3) / 1e12 / bf16,

@@ -85,8 +85,11 @@ typedef struct dnnmg_config {
   int32_t train_batch;     /* largest training batch B (sequences) of dnnmg_train_*, 0 = none */
   int32_t train_seq;       /* largest training sequence length T */
   int32_t coarse_refresh;  /* time steps between refactorisations of the coarse level (>= 1) */
-  int32_t persistent_vcycle; /* 1: one cooperative launch per V-cycle; 0: one launch per stage */
-  int32_t reserved[3];
+  int32_t persistent_vcycle; /* levels <= this one run their part of a V-cycle as one
+                                cooperative launch; 0: none; -1: chosen by timing */
+  int32_t precond_lag;     /* 1: the multigrid preconditioner keeps the linearisation of a
+                              step's first Newton iteration (the matvec is always current) */
+  int32_t reserved[2];
 } dnnmg_config;
 
 /* Per-step statistics returned by dnnmg_step(). */
@@ -104,8 +107,9 @@ typedef struct dnnmg_step_stats {
  * newton_tol = 1e-10, gmres_rtol = 1e-4, omega = 0.8, eps_damp = 1,
  * obstacle at level-0 cell (2, 1), L = 3, coarse level 1, replaced_levels = 1,
  * FP64, newton_max = 20, gmres_m = 20, gmres_maxit = 200, V(2,2), GRU 2 x 64,
- * dense width 128, fallback_newton_its = 8, coarse_refresh = 4,
- * persistent_vcycle = 0.  Returns DNNMG_ERR_ARG if cfg is NULL. */
+ * dense width 128, fallback_newton_its = 8, coarse_refresh = 8,
+ * persistent_vcycle = -1, precond_lag = 1.  Returns DNNMG_ERR_ARG if cfg is
+ * NULL. */
 int dnnmg_default_config(dnnmg_config* cfg);
 
 /* Create a context: builds the level hierarchy coarse..L (and L+1..L+r for the
@@ -350,6 +354,10 @@ int dnnmg_profile(dnnmg_ctx* ctx, int enable);
  * on mesh level `level` (level = -1: all levels) since the last reset.
  * Synchronises the context's stream. */
 int dnnmg_profile_read(dnnmg_ctx* ctx, int stage, int level, int64_t* launches, double* ms);
+
+/* Level from which the V-cycle runs as one cooperative launch (0: none),
+ * as configured or chosen by timing at the first linearisation; -1 on error. */
+int dnnmg_vcycle_split(const dnnmg_ctx* ctx);
 
 /* Number of kernels this library has launched in this process so far. */
 uint64_t dnnmg_kernel_launches(void);

@@ -162,8 +162,9 @@ int dnnmg_default_config(dnnmg_config* c) {
   c->gru_layers = 2;
   c->mlp_width = 128;
   c->fallback_newton_its = 8;
-  c->coarse_refresh = 4;
-  c->persistent_vcycle = 0;
+  c->coarse_refresh = 8;
+  c->persistent_vcycle = -1;
+  c->precond_lag = 1;
   return DNNMG_OK;
 }
 
@@ -284,6 +285,10 @@ int dnnmg_profile_read(dnnmg_ctx* ctx, int stage, int level, int64_t* launches, 
 }
 
 uint64_t dnnmg_kernel_launches(void) { return dnnmg::launches(); }
+
+int dnnmg_vcycle_split(const dnnmg_ctx* ctx) {
+  return ctx && ctx->solver ? ctx->solver->split_level() : -1;
+}
 
 size_t dnnmg_num_params(const dnnmg_ctx* ctx) { return ctx ? ctx->nd.num_params() : 0; }
 

@@ -240,4 +240,66 @@ __device__ __forceinline__ void elem_pair(const Sten<T>& s, const GaussData<T>& 
   J[2][2] = T(0);
 }
 
+// All twelve rows (u0..u3, v0..v3, p0..p3) of one fluid cell's contribution
+// to A'(vbar) w (NONLIN = false) or A(w) (NONLIN = true); the Gauss-point
+// values are computed once for the cell.  Pressure rows hold the divergence
+// only (LPS is added per patch).
+template <typename T, bool NONLIN>
+__device__ __forceinline__ void cell_all_rows(const Sten<T>& s, const T wu[4], const T wv[4],
+                                              const T wp[4], const T bu[4], const T bv[4],
+                                              T r[12]) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    T ru = 0, rv = 0, rp = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      ru += s.E[a * 4 + b] * wu[b] - s.Dx[b * 4 + a] * wp[b];
+      rv += s.E[a * 4 + b] * wv[b] - s.Dy[b * 4 + a] * wp[b];
+      rp += s.Dx[a * 4 + b] * wu[b] + s.Dy[a * 4 + b] * wv[b];
+    }
+    r[a] = ru, r[4 + a] = rv, r[8 + a] = rp;
+  }
+  const T sc = s.wq * s.ih;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    T phi[4], dx[4], dy[4];
+    shape_at<T>(q, phi, dx, dy);
+    T Wu = 0, Wv = 0, Wux = 0, Wuy = 0, Wvx = 0, Wvy = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      Wu += phi[b] * wu[b];
+      Wv += phi[b] * wv[b];
+      Wux += dx[b] * wu[b];
+      Wuy += dy[b] * wu[b];
+      Wvx += dx[b] * wv[b];
+      Wvy += dy[b] * wv[b];
+    }
+    T cu, cv;
+    if (NONLIN) {
+      cu = Wu * Wux + Wv * Wuy;
+      cv = Wu * Wvx + Wv * Wvy;
+    } else {
+      T Bu = 0, Bv = 0, Bux = 0, Buy = 0, Bvx = 0, Bvy = 0;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        Bu += phi[b] * bu[b];
+        Bv += phi[b] * bv[b];
+        Bux += dx[b] * bu[b];
+        Buy += dy[b] * bu[b];
+        Bvx += dx[b] * bv[b];
+        Bvy += dy[b] * bv[b];
+      }
+      cu = Bu * Wux + Bv * Wuy + Wu * Bux + Wv * Buy;
+      cv = Bu * Wvx + Bv * Wvy + Wu * Bvx + Wv * Bvy;
+    }
+    cu *= sc;
+    cv *= sc;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      r[a] += phi[a] * cu;
+      r[4 + a] += phi[a] * cv;
+    }
+  }
+}
+
 }  // namespace dnnmg

@@ -59,10 +59,11 @@ class Solver final : public SolverBase {
     hcol_ = c_->mem.alloc<double>(2 * m_ + 4);
     y_ = c_->mem.alloc<double>(m_ + 1);
     one_ = c_->mem.alloc<double>(1);
+    vbJ_ = c_->mem.alloc<T>(2 * (size_t)lv_[K_].g.nn);
     partials_ = c_->mem.alloc<double>(dots_partials(n_, 2 * m_ + 4));
     if (!c_->mem.ok()) return c_->fail(DNNMG_ERR_CUDA, "device allocation failed");
-    // persistent V-cycle: level table and one phase list per possible top level
-    if (cfg.persistent_vcycle) {
+    // persistent sub-cycles: level table and one phase list per possible top level
+    if (cfg.persistent_vcycle != 0) {
       std::vector<VLevel<T>> hv(K_ + 1);
       for (int k = 0; k <= K_; ++k)
         hv[k] = VLevel<T>{lv_[k].g, lv_[k].s, lv_[k].x, lv_[k].x2, lv_[k].b, lv_[k].d,
@@ -82,6 +83,7 @@ class Solver final : public SolverBase {
       cudaStreamSynchronize(st_);
       coarse_nd_ = 3 * lv_[0].g.nn;
       vgrid_ = vcycle_grid<T>(coarse_nd_);
+      split_ = cfg.persistent_vcycle > 0 ? cfg.persistent_vcycle : -1;  // -1: tune later
     }
     const double one = 1.0;
     cudaMemcpyAsync(one_, &one, sizeof(double), cudaMemcpyHostToDevice, st_);
@@ -92,7 +94,11 @@ class Solver final : public SolverBase {
 
   // Linearise every level at the velocity of x64 (level L): nodal injection
   // down the hierarchy, Vanka inverses, coarse LU and inverse.
-  int linearize(const double* x64, bool coarse) override {
+  int linearize(const double* x64, bool coarse, bool precond) override {
+    // the Jacobian of the FGMRES matvec always follows the current iterate
+    launch_cast<double, T>(x64, vbJ_, 2 * (size_t)lv_[K_].g.nn, st_);
+    linearized_j_ = true;
+    if (!precond && linearized_) return c_->check("linearize");
     cudaMemcpyAsync(lv_[K_].vb64, x64, 2 * sizeof(double) * lv_[K_].g.nn,
                     cudaMemcpyDeviceToDevice, st_);
     for (int k = K_; k > 0; --k)
@@ -118,6 +124,7 @@ class Solver final : public SolverBase {
     cudaStreamSynchronize(st_);
     std::memcpy(&status, c_->h_scalars, sizeof(int));
     linearized_ = true;
+    if (split_ == -1) tune_split();
     if (status & 1) return c_->fail(DNNMG_ERR_NUMERICAL, "singular local Vanka matrix");
     if (status & 2) return c_->fail(DNNMG_ERR_NUMERICAL, "singular coarse-level matrix");
     return DNNMG_OK;
@@ -125,8 +132,8 @@ class Solver final : public SolverBase {
 
   int apply(int k, const void* w, void* y) override {
     if (!linearized_) return c_->fail(DNNMG_ERR_STATE, "apply before linearize");
-    launch_apply<T>(lv_[k].g, lv_[k].s, static_cast<const T*>(w), lv_[k].vb, static_cast<T*>(y),
-                    st_);
+    launch_apply<T>(lv_[k].g, lv_[k].s, static_cast<const T*>(w), k == K_ ? vbJ_ : lv_[k].vb,
+                    static_cast<T*>(y), st_);
     return c_->check("apply");
   }
 
@@ -165,7 +172,7 @@ class Solver final : public SolverBase {
         launch_fill<T>(zj, T(0), n_, st_);
         cycle(K_, vj, zj);
         int p = c_->prof.begin(DNNMG_STAGE_APPLY, lv_[K_].level, st_);
-        launch_apply<T>(lv_[K_].g, lv_[K_].s, zj, lv_[K_].vb, w, st_);
+        launch_apply<T>(lv_[K_].g, lv_[K_].s, zj, vbJ_, w, st_);
         c_->prof.end(p, st_);
         p = c_->prof.begin(DNNMG_STAGE_KRYLOV, lv_[K_].level, st_);
         launch_multidot<T>(V_, n_, j + 1, w, n_, partials_, hcol_, st_);
@@ -190,7 +197,7 @@ class Solver final : public SolverBase {
       launch_combine<T, T>(Z_, n_, k, y_, 1.0, wsol_, n_, st_);
       if (!done) {
         // restart from the true residual of the current iterate
-        launch_defect<T>(lv_[K_].g, lv_[K_].s, rT_, wsol_, lv_[K_].vb, rcur_, false, st_);
+        launch_defect<T>(lv_[K_].g, lv_[K_].s, rT_, wsol_, vbJ_, rcur_, false, st_);
       }
     }
     launch_combine<T, double>(wsol_, n_, 1, one_, eps, x64, n_, st_);
@@ -232,12 +239,53 @@ class Solver final : public SolverBase {
       }
   }
 
-  // One V(nu1, nu2) cycle on level k for A x = b with x = 0 on entry.
+  int split_level() const { return split_ > 0 ? split_ : 0; }
+
+  // Time the top-level cycle with the persistent sub-cycle starting at each
+  // candidate level (0 = none) and keep the fastest (autotuner).
+  void tune_split() {
+    split_ = 0;
+    if (vgrid_ <= 0) return;
+    const int top = K_;
+    T* b = lv_[top].d;
+    T* x = lv_[top].x2 == nullptr ? nullptr : wsol_;
+    launch_fill<T>(b, T(0), 3 * (size_t)lv_[top].g.nn, st_);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int best_s = 0;
+    const bool prof_on = c_->prof.on();
+    if (prof_on) c_->prof.enable(false);
+    for (int cand = lv_[top].level; cand >= 0; --cand) {
+      if (cand > 0 && cand < lv_[0].level + 1) continue;
+      split_ = cand;
+      cycle(top, b, x);  // warm-up
+      cudaEventRecord(e0, st_);
+      for (int r = 0; r < 3; ++r) cycle(top, b, x);
+      cudaEventRecord(e1, st_);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (cudaGetLastError() != cudaSuccess || persistent_failed_) ms = 1e30f;
+      if (ms < best) best = ms, best_s = cand;
+    }
+    if (prof_on) c_->prof.enable(true);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    split_ = best_s;
+  }
+
+  // One V(nu1, nu2) cycle on level k for A x = b with x = 0 on entry.  Levels
+  // at or below split_ run their whole sub-cycle as one cooperative launch.
   void cycle(int k, const T* b, T* x) {
-    if (vgrid_ > 0 && !persistent_failed_) {
+    if (split_ > 0 && lv_[k].level <= split_ && vgrid_ > 0 && !persistent_failed_) {
+      int blocks = cdiv(4 * vanka_slots(lv_[k].g), 256);
+      blocks = blocks < 64 ? 64 : blocks;
+      blocks = blocks > vgrid_ ? vgrid_ : blocks;
       const int p = c_->prof.begin(DNNMG_STAGE_VCYCLE, lv_[k].level, st_);
       const int rc = launch_vcycle_persistent<T>(dlv_, dph_ + ph_off_[k], ph_n_[k], k, b, x, ainv_,
-                                                 (T)c_->cfg.omega, vgrid_, coarse_nd_, st_);
+                                                 (T)c_->cfg.omega, blocks, coarse_nd_, st_);
       c_->prof.end(p, st_);
       if (rc == 0) return;
       persistent_failed_ = true;  // fall back to one launch per stage
@@ -277,12 +325,14 @@ class Solver final : public SolverBase {
   T *V_ = nullptr, *Z_ = nullptr, *wsol_ = nullptr, *rT_ = nullptr, *rcur_ = nullptr;
   double *H_ = nullptr, *cs_ = nullptr, *sn_ = nullptr, *gv_ = nullptr, *hcol_ = nullptr,
          *y_ = nullptr, *one_ = nullptr, *partials_ = nullptr;
-  bool linearized_ = false;
+  bool linearized_ = false, linearized_j_ = false;
   bool coarse_done_ = false;
+  T* vbJ_ = nullptr;  // top-level linearisation of the FGMRES matvec
   VLevel<T>* dlv_ = nullptr;
   Phase* dph_ = nullptr;
   std::vector<int> ph_off_, ph_n_;
   int vgrid_ = 0, coarse_nd_ = 0;
+  int split_ = 0;  // levels <= split_ (> 0) run as one cooperative launch; -1: not tuned yet
   bool persistent_failed_ = false;
 };
 
@@ -745,7 +795,7 @@ int dnnmg_ctx::set_state(const double* x) {
   return check("set_state");
 }
 
-int dnnmg_ctx::linearize_api(const double* x) { return solver->linearize(x); }
+int dnnmg_ctx::linearize_api(const double* x) { return solver->linearize(x, true, true); }
 
 int dnnmg_ctx::apply_api(int level, const void* w, void* y, int precision) {
   if (level < lc() || level > L()) return fail(DNNMG_ERR_ARG, "level out of range");
@@ -778,7 +828,10 @@ int dnnmg_ctx::newton(const double* f, dnnmg_step_stats* s) {
     // the coarse-level factorisation is refreshed at the first Newton step of
     // every coarse_refresh-th time step (a lagged preconditioner component)
     const bool refresh = it == 0 && steps_taken % cfg.coarse_refresh == 0;
-    if (int rc = solver->linearize(x64, refresh)) return rc;
+    // with precond_lag the multigrid preconditioner keeps the linearisation
+    // of the step's first Newton iteration; the matvec always uses the current one
+    const bool precond = it == 0 || !cfg.precond_lag;
+    if (int rc = solver->linearize(x64, refresh, precond)) return rc;
     int its = 0;
     if (int rc = solver->solve(r64, x64, cfg.eps_damp, &its)) return rc;
     gits += its;

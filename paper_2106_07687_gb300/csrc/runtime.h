@@ -112,13 +112,16 @@ class Prof {
 class SolverBase {
  public:
   virtual ~SolverBase() = default;
-  // coarse = false keeps the coarse-level factorisation of the previous call
-  virtual int linearize(const double* x64, bool coarse = true) = 0;
+  // coarse = false keeps the coarse-level factorisation of the previous call;
+  // precond = false only updates the Jacobian of the FGMRES matvec
+  virtual int linearize(const double* x64, bool coarse, bool precond) = 0;
   virtual int apply(int k, const void* w, void* y) = 0;
   virtual int vcycle(int k, const void* b, void* x) = 0;
   // FGMRES on the finest level: w64 += eps * A'^{-1} r64 (approximately)
   virtual int solve(const double* r64, double* x64, double eps, int* its) = 0;
   virtual int precision() const = 0;
+  // level from which the V-cycle runs as one cooperative launch (0: none)
+  virtual int split_level() const = 0;
 };
 
 std::unique_ptr<SolverBase> make_solver(struct ::dnnmg_ctx* ctx);

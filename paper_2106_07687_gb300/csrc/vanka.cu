@@ -143,6 +143,200 @@ __global__ void __launch_bounds__(kPassThreads)
                        blockIdx.x * kPassThreads + threadIdx.x);
 }
 
+// Tiled colour pass: a block owns kTCX x kTCY cells of the colour, i.e. the
+// (2 kTCX) x (2 kTCY) nodes they cover.  It stages the masked iterate, vbar
+// and the flags of those nodes plus a two-node halo in shared memory,
+// computes the 12 rows of every cell touching the tile and the 9 LPS rows of
+// every patch touching it once, sums them per node, and finishes like the
+// quad kernel (shuffle of the 12 defects, 12x12 inverse, update).
+constexpr int kTCX = 16, kTCY = 4;
+constexpr int kTileThreads = 4 * kTCX * kTCY;       // 256
+constexpr int kSX = 2 * kTCX + 4, kSY = 2 * kTCY + 4;  // staged nodes (tile + 2 halo)
+constexpr int kCX = 2 * kTCX + 1, kCY = 2 * kTCY + 1;  // cells touching the tile
+constexpr int kPX = kTCX + 2, kPY = kTCY + 2;          // patches touching the tile
+
+template <typename T>
+struct PassSmem {
+  T w[3][kSY][kSX];
+  T vb[2][kSY][kSX];
+  uint8_t fl[kSY][kSX];
+  T cres[kCY * kCX][12];
+  T pres[kPY * kPX][9];
+  int8_t cvalid[kCY * kCX];
+  int8_t pvalid[kPY * kPX];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kTileThreads)
+    vanka_pass_tiled_kernel(Grid g, Sten<T> s, int colour, const T* __restrict__ b,
+                            const T* __restrict__ xin, const T* __restrict__ vb,
+                            const T* __restrict__ inv, T omega, T* __restrict__ xout) {
+  extern __shared__ __align__(16) uint8_t smraw[];
+  PassSmem<T>& S = *reinterpret_cast<PassSmem<T>*>(smraw);
+  const int cx = colour & 1, cy = colour >> 1;
+  const int sx = g.nx / 2 + 1, sy = g.ny / 2 + 1;
+  const int nslots = sx * sy;
+  const int nn = g.nn;
+  const int tx0 = blockIdx.x * kTCX, ty0 = blockIdx.y * kTCY;
+  const int i0 = 2 * tx0 - cx, j0 = 2 * ty0 - cy;  // first node of the tile
+  const int t = threadIdx.x;
+  // ---- this thread's node (quad q, local node a) and its loads that do not
+  // depend on the defect: b, x_in and its three rows of the cell's inverse,
+  // issued first so that their latency overlaps the stencil work below
+  const int q = t >> 2, a = t & 3;
+  const int ti = tx0 + (q % kTCX), tj = ty0 + (q / kTCX);
+  const bool slot_ok = ti < sx && tj < sy;
+  const int slot = tj * sx + ti;
+  const int ci = 2 * ti - cx, cj = 2 * tj - cy;
+  const int i = ci + (a & 1), j = cj + (a >> 1);
+  const bool node_ok = slot_ok && i >= 0 && j >= 0 && i <= g.nx && j <= g.ny;
+  const bool cell_ok = slot_ok && ci >= 0 && cj >= 0 && ci < g.nx && cj < g.ny &&
+                       !g.solid[(cj < 0 ? 0 : cj) * g.nx + (ci < 0 ? 0 : ci)];
+  const int n = node_ok ? j * g.nnx + i : 0;
+  T xu = 0, xv = 0, xp = 0, bu0 = 0, bv0 = 0, bp0 = 0;
+  T iv[36];
+  if (node_ok) {
+    xu = xin[n], xv = xin[nn + n], xp = xin[2 * nn + n];
+    bu0 = b[n], bv0 = b[nn + n], bp0 = b[2 * nn + n];
+  }
+  if (node_ok && cell_ok) {
+    const T* row0 = inv + (size_t)colour * 144 * nslots + slot;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int k = 0; k < 12; ++k) iv[c * 12 + k] = row0[(size_t)((c * 4 + a) * 12 + k) * nslots];
+  }
+  // ---- stage nodes [i0-2, i0-2+kSX) x [j0-2, j0-2+kSY)
+  for (int e = t; e < kSX * kSY; e += kTileThreads) {
+    const int li = e % kSX, lj = e / kSX;
+    const int i = i0 - 2 + li, j = j0 - 2 + lj;
+    T wu = 0, wv = 0, wp = 0, bu = 0, bvv = 0;
+    uint8_t f = 0xFF;
+    if (i >= 0 && j >= 0 && i <= g.nx && j <= g.ny) {
+      const int n = j * g.nnx + i;
+      f = g.flags[n];
+      wu = (f & kVDir) ? T(0) : xin[n];
+      wv = (f & kVDir) ? T(0) : xin[nn + n];
+      wp = (f & kPFix) ? T(0) : xin[2 * nn + n];
+      bu = vb[n];
+      bvv = vb[nn + n];
+    }
+    S.w[0][lj][li] = wu;
+    S.w[1][lj][li] = wv;
+    S.w[2][lj][li] = wp;
+    S.vb[0][lj][li] = bu;
+    S.vb[1][lj][li] = bvv;
+    S.fl[lj][li] = f;
+  }
+  __syncthreads();
+  // ---- cells [i0-1, i0-1+kCX) x [j0-1, j0-1+kCY): 12 rows each
+  for (int e = t; e < kCX * kCY; e += kTileThreads) {
+    const int lc = e % kCX, lr = e / kCX;
+    const int ci = i0 - 1 + lc, cj = j0 - 1 + lr;
+    const bool ok = ci >= 0 && cj >= 0 && ci < g.nx && cj < g.ny && !g.solid[cj * g.nx + ci];
+    S.cvalid[e] = ok;
+    if (!ok) continue;
+    T wu[4], wv[4], wp[4], bu[4], bv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int li = lc + 1 + (a & 1), lj = lr + 1 + (a >> 1);  // staged coords of the node
+      wu[a] = S.w[0][lj][li];
+      wv[a] = S.w[1][lj][li];
+      wp[a] = S.w[2][lj][li];
+      bu[a] = S.vb[0][lj][li];
+      bv[a] = S.vb[1][lj][li];
+    }
+    T r[12];
+    cell_all_rows<T, false>(s, wu, wv, wp, bu, bv, r);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) S.cres[e][k] = r[k];
+  }
+  // ---- patches touching the tile: 9 LPS rows each
+  // patches touching the tile: from ceil((i0 - 2) / 2) (also for negative
+  // i0) to floor((i0 + 2 kTCX - 1) / 2), likewise in y
+  const int PI0 = (i0 - 1) >> 1, PJ0 = (j0 - 1) >> 1;
+  const int PI1 = (i0 + 2 * kTCX - 1) >> 1, PJ1 = (j0 + 2 * kTCY - 1) >> 1;
+  for (int e = t; e < kPX * kPY; e += kTileThreads) {
+    const int pi = PI0 + e % kPX, pj = PJ0 + e / kPX;
+    const bool ok = pi <= PI1 && pj <= PJ1 && pi >= 0 && pj >= 0 && pi < g.nx / 2 &&
+                    pj < g.ny / 2 && !g.solid[(2 * pj) * g.nx + 2 * pi];
+    S.pvalid[e] = ok;
+    if (!ok) continue;
+    T p[9];
+#pragma unroll
+    for (int m = 0; m < 9; ++m) {
+      const int li = 2 * pi + m % 3 - (i0 - 2), lj = 2 * pj + m / 3 - (j0 - 2);
+      p[m] = S.w[2][lj][li];
+    }
+#pragma unroll
+    for (int mn = 0; mn < 9; ++mn) {
+      T acc = 0;
+#pragma unroll
+      for (int m = 0; m < 9; ++m) acc += s.S9[mn * 9 + m] * p[m];
+      S.pres[e][mn] = acc;
+    }
+  }
+  __syncthreads();
+  T du = 0, dv = 0, dp = 0;
+  if (node_ok && cell_ok) {
+    T ru = 0, rv = 0, rp = 0;
+#pragma unroll
+    for (int dyy = 0; dyy < 2; ++dyy)
+#pragma unroll
+      for (int dxx = 0; dxx < 2; ++dxx) {
+        const int lc = i - 1 + dxx - (i0 - 1), lr = j - 1 + dyy - (j0 - 1);
+        const int e = lr * kCX + lc;
+        if (!S.cvalid[e]) continue;
+        const int al = (1 - dxx) + 2 * (1 - dyy);
+        ru += S.cres[e][al];
+        rv += S.cres[e][4 + al];
+        rp += S.cres[e][8 + al];
+      }
+#pragma unroll
+    for (int dJ = 0; dJ < 2; ++dJ) {
+      const int PJ = (j >> 1) - dJ;
+      if (j - 2 * PJ > 2) continue;
+#pragma unroll
+      for (int dI = 0; dI < 2; ++dI) {
+        const int PI = (i >> 1) - dI;
+        if (i - 2 * PI > 2) continue;
+        const int e = (PJ - PJ0) * kPX + (PI - PI0);
+        if (!S.pvalid[e]) continue;
+        rp += S.pres[e][(i - 2 * PI) + 3 * (j - 2 * PJ)];
+      }
+    }
+    const uint8_t f = S.fl[j - (j0 - 2)][i - (i0 - 2)];
+    du = bu0 - ((f & kVDir) ? xu : ru);
+    dv = bv0 - ((f & kVDir) ? xv : rv);
+    dp = bp0 - ((f & kPFix) ? xp : rp);
+  }
+  const int lane = t & 31, base = lane & ~3;
+  T d[12];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    d[k] = __shfl_sync(0xffffffffu, du, base + k);
+    d[4 + k] = __shfl_sync(0xffffffffu, dv, base + k);
+    d[8 + k] = __shfl_sync(0xffffffffu, dp, base + k);
+  }
+  if (!node_ok) return;
+  if (cell_ok) {
+    T acc[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      acc[c] = 0;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) acc[c] += iv[c * 12 + k] * d[k];
+    }
+    xout[n] = xu + omega * acc[0];
+    xout[nn + n] = xv + omega * acc[1];
+    xout[2 * nn + n] = xp + omega * acc[2];
+  } else {
+    xout[n] = xu;
+    xout[nn + n] = xv;
+    xout[2 * nn + n] = xp;
+  }
+}
+
 }  // namespace
 
 template <typename T>
@@ -156,10 +350,14 @@ void launch_vanka_setup(const Grid& g, const Sten<T>& s, const T* vb, T* inv, in
 template <typename T>
 void launch_vanka_pass(const Grid& g, const Sten<T>& s, int colour, const T* b, const T* xin,
                        const T* vb, const T* inv, T omega, T* xout, cudaStream_t st) {
-  const int threads = 4 * vanka_slots(g);
+  const dim3 grid(cdiv(g.nx / 2 + 1, kTCX), cdiv(g.ny / 2 + 1, kTCY));
+  const size_t smem = sizeof(PassSmem<T>);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(vanka_pass_tiled_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
   note_launch();
-  vanka_pass_kernel<T><<<cdiv(threads, kPassThreads), kPassThreads, 0, st>>>(
-      g, s, colour, b, xin, vb, inv, omega, xout);
+  vanka_pass_tiled_kernel<T><<<grid, kTileThreads, smem, st>>>(g, s, colour, b, xin, vb, inv,
+                                                               omega, xout);
 }
 
 template void launch_vanka_setup<float>(const Grid&, const Sten<float>&, const float*, float*,

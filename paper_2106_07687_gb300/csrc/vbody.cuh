@@ -27,14 +27,28 @@ __device__ __forceinline__ void vanka_pass_thread(const Grid& g, const Sten<T>& 
                        !g.solid[(cj < 0 ? 0 : cj) * g.nx + (ci < 0 ? 0 : ci)];
   const int nn = g.nn;
   const int n = node_ok ? j * g.nnx + i : 0;
+  // loads independent of the defect first (latency overlaps the stencil)
+  T xu = 0, xv = 0, xp = 0, b0 = 0, b1 = 0, b2 = 0;
+  T iv[36];
+  if (node_ok) {
+    xu = xin[n], xv = xin[nn + n], xp = xin[2 * nn + n];
+    b0 = b[n], b1 = b[nn + n], b2 = b[2 * nn + n];
+  }
+  if (node_ok && cell_ok) {
+    const T* row0 = inv + (size_t)colour * 144 * nslots + slot;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int k = 0; k < 12; ++k) iv[c * 12 + k] = row0[(size_t)((c * 4 + a) * 12 + k) * nslots];
+  }
   T du = 0, dv = 0, dp = 0;
   if (node_ok && cell_ok) {
     T ru, rv, rp;
     node_rows<T, false, true>(g, s, i, j, xin, vb, ru, rv, rp);
     const uint8_t f = g.flags[n];
-    du = b[n] - ((f & kVDir) ? xin[n] : ru);
-    dv = b[nn + n] - ((f & kVDir) ? xin[nn + n] : rv);
-    dp = b[2 * nn + n] - ((f & kPFix) ? xin[2 * nn + n] : rp);
+    du = b0 - ((f & kVDir) ? xu : ru);
+    dv = b1 - ((f & kVDir) ? xv : rv);
+    dp = b2 - ((f & kPFix) ? xp : rp);
   }
   const int lane = threadIdx.x & 31, base = lane & ~3;
   T d[12];
@@ -46,19 +60,20 @@ __device__ __forceinline__ void vanka_pass_thread(const Grid& g, const Sten<T>& 
   }
   if (!node_ok) return;
   if (cell_ok) {
-    const T* row0 = inv + (size_t)colour * 144 * nslots + slot;
+    T acc[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const int r = c * 4 + a;
-      T acc = 0;
+      acc[c] = 0;
 #pragma unroll
-      for (int k = 0; k < 12; ++k) acc += row0[(size_t)(r * 12 + k) * nslots] * d[k];
-      xout[c * nn + n] = xin[c * nn + n] + omega * acc;
+      for (int k = 0; k < 12; ++k) acc[c] += iv[c * 12 + k] * d[k];
     }
+    xout[n] = xu + omega * acc[0];
+    xout[nn + n] = xv + omega * acc[1];
+    xout[2 * nn + n] = xp + omega * acc[2];
   } else {
-    xout[n] = xin[n];
-    xout[nn + n] = xin[nn + n];
-    xout[2 * nn + n] = xin[2 * nn + n];
+    xout[n] = xu;
+    xout[nn + n] = xv;
+    xout[2 * nn + n] = xp;
   }
 }
 

@@ -31,7 +31,7 @@ class Config(ctypes.Structure):
                 ("gmres_maxit", c_int32), ("nu1", c_int32), ("nu2", c_int32), ("hidden", c_int32),
                 ("gru_layers", c_int32), ("mlp_width", c_int32), ("fallback_newton_its", c_int32),
                 ("train_batch", c_int32), ("train_seq", c_int32), ("coarse_refresh", c_int32),
-                ("persistent_vcycle", c_int32), ("reserved", c_int32 * 3)]
+                ("persistent_vcycle", c_int32), ("precond_lag", c_int32), ("reserved", c_int32 * 2)]
 
 
 class StepStats(ctypes.Structure):
@@ -87,6 +87,7 @@ def _declare(lib):
         "dnnmg_profile": ([P, ctypes.c_int], ctypes.c_int),
         "dnnmg_profile_read": ([P, ctypes.c_int, ctypes.c_int, P, P], ctypes.c_int),
         "dnnmg_kernel_launches": ([], ctypes.c_uint64),
+        "dnnmg_vcycle_split": ([P], ctypes.c_int),
         "dnnmg_gather_batch": ([P, P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int64, P, P],
                                ctypes.c_int),
     }
@@ -307,6 +308,9 @@ class Context:
         xf = torch.empty(self.ndof(level + 1), dtype=torch.float64, device="cuda")
         self._check(self.lib.dnnmg_prolongate(self.h, level, _ptr(xc), _ptr(xf)))
         return xf
+
+    def vcycle_split(self):
+        return int(self.lib.dnnmg_vcycle_split(self.h))
 
     def profile(self, enable=True):
         self._check(self.lib.dnnmg_profile(self.h, 1 if enable else 0))
