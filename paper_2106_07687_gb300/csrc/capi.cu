@@ -118,6 +118,25 @@ Sten<T> make_sten(double h, const dnnmg_config& c) {
   return s;
 }
 
+// Constants of the explicit old-time bracket nu (grad v, grad phi) + (v.grad v, phi)
+// of the theta-scheme: E = nu K, no mass, no pressure, no LPS, Gauss weight h^2/4.
+Sten<double> make_explicit_sten(double h, const dnnmg_config& c) {
+  dnnmg_config e = c;
+  e.theta = 1.0;
+  Sten<double> s = make_sten<double>(h, e);
+  const double k1[2][2] = {{1 / h, -1 / h}, {-1 / h, 1 / h}};
+  const double m1[2][2] = {{h / 3, h / 6}, {h / 6, h / 3}};
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) {
+      const int ax = a & 1, ay = a >> 1, bx = b & 1, by = b >> 1;
+      s.E[a * 4 + b] = c.nu * (k1[ax][bx] * m1[ay][by] + m1[ax][bx] * k1[ay][by]);
+      s.Dx[a * 4 + b] = s.Dy[a * 4 + b] = 0.0;
+    }
+  for (int m = 0; m < 81; ++m) s.S9[m] = 0.0;
+  s.wq = h * h / 4.0;
+  return s;
+}
+
 template Sten<float> make_sten<float>(double, const dnnmg_config&);
 template Sten<double> make_sten<double>(double, const dnnmg_config&);
 

@@ -27,6 +27,11 @@ void launch_residual64(const Grid& g, const Sten<double>& s, const double* x, co
 void launch_old_time_rhs64(const Grid& g, double inv_k, const double* x_old, double* f,
                            cudaStream_t st);
 
+// f -= coef * (explicit transport + diffusion of x) on the velocity rows
+// (theta-scheme old-time terms); sx from make_explicit_sten
+void launch_explicit_sub64(const Grid& g, const Sten<double>& sx, double coef, const double* x,
+                           double* f, cudaStream_t st);
+
 // Transfers (transfer.cu) ----------------------------------------------------
 // bc = R d (R = P^T on free DOFs, coarse constrained rows zeroed)
 template <typename T>

@@ -372,7 +372,6 @@ int dnnmg_ctx::init() {
   const dnnmg_config& c = cfg;
   if (!(c.nu > 0) || !(c.dt > 0) || !(c.alpha0 >= 0) || !(c.theta > 0 && c.theta <= 1))
     return fail(DNNMG_ERR_ARG, "nu, dt, theta or alpha0 out of range");
-  if (c.theta != 1.0) return fail(DNNMG_ERR_ARG, "only theta = 1 (backward Euler) is supported");
   if (c.level_coarse < 1 || c.level_coarse > c.level_solve || c.level_solve > 9)
     return fail(DNNMG_ERR_ARG, "need 1 <= level_coarse <= level_solve <= 9");
   if (c.level_coarse != 1) return fail(DNNMG_ERR_ARG, "the coarse direct solve supports level 1");
@@ -412,6 +411,8 @@ int dnnmg_ctx::init() {
   partials = mem.alloc<double>(dots_partials(n3, 4));
   if (!mem.ok()) return fail(DNNMG_ERR_CUDA, "device allocation failed");
   s64L = make_sten<double>(gL.h, cfg);
+  sxL = make_explicit_sten(gL.h, cfg);
+  if ((int)lv.size() > L() + 1) sxF = make_explicit_sten(grid(L() + 1).h, cfg);
   // impulsive start: zero state, then the inflow profile on x = 0
   std::vector<double> x0(n3, 0.0);
   for (int j = 0; j <= gL.ny; ++j) {
@@ -616,14 +617,14 @@ int dnnmg_ctx::dnnmg_correction() {
     cudaMemsetAsync(vcorr + 2 * gF.nn, 0, sizeof(double) * gF.nn, st);
   }
   launch_prolong_state64(gF, gL, x64, xtF, 3, st);                     // line 6
-  launch_old_time_rhs64(gF, 1.0 / cfg.dt, vcorr, fF, st);
+  old_rhs(L() + 1, vcorr, fF);
   cudaMemcpyAsync(ximpF, xtF, n3F * sizeof(double), cudaMemcpyDeviceToDevice, st);
   launch_impose_dirichlet64(gF, ximpF, st);
   launch_residual64(gF, s64F, ximpF, fF, rF, st);                     // input: fine residual
   launch_gather(gL, gF, patch_cell, P, xtF, rF, feat_mean, feat_std, cfg.nu, cfg.dt, X, st);
   launch_patchnet_forward(nd, pk, X, hid, hid, net_out, P, net_status, st);  // line 7
   launch_scatter(gL, gF, cell_patch, net_out, nd.c_out, xtF, vcorr, st);
-  launch_old_time_rhs64(gF, 1.0 / cfg.dt, vcorr, bF, st);             // line 8
+  old_rhs(L() + 1, vcorr, bF);                                        // line 8
   cudaMemsetAsync(bL, 0, 3 * sizeof(double) * gL.nn, st);
   launch_restrict_full64(gF, gL, bF, bL, 2, st);                      // line 9
   prof.end(pr, st);
@@ -645,7 +646,7 @@ int dnnmg_ctx::make_sample(const double* xf_prev, const double* xf_next, float* 
   cudaMemcpyAsync(xold64, x64, n3L * sizeof(double), cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(vcorr, xf_prev, 2 * sizeof(double) * gF.nn, cudaMemcpyDeviceToDevice, st);
   cudaMemsetAsync(vcorr + 2 * gF.nn, 0, sizeof(double) * gF.nn, st);
-  launch_old_time_rhs64(gF, 1.0 / cfg.dt, vcorr, fF, st);
+  old_rhs(L() + 1, vcorr, fF);
   cudaMemsetAsync(f64, 0, n3L * sizeof(double), st);
   launch_restrict_full64(gF, gL, fF, f64, 2, st);
   dnnmg_step_stats tmp{};
@@ -772,6 +773,13 @@ int dnnmg_ctx::patch_infer(const uint16_t* x, float* h, float* out, int P) {
   return net_check("patch_infer");
 }
 
+void dnnmg_ctx::old_rhs(int level, const double* x_old, double* f) {
+  const Grid g = grid(level);
+  launch_old_time_rhs64(g, 1.0 / cfg.dt, x_old, f, st);
+  if (cfg.theta != 1.0)
+    launch_explicit_sub64(g, level == L() ? sxL : sxF, 1.0 - cfg.theta, x_old, f, st);
+}
+
 double dnnmg_ctx::norm64(const double* v, size_t n) {
   launch_multidot<double>(v, n, 1, v, n, partials, dots, st);
   cudaMemcpyAsync(h_scalars, dots, sizeof(double), cudaMemcpyDeviceToHost, st);
@@ -861,12 +869,12 @@ int dnnmg_ctx::step(int mode, dnnmg_step_stats* stats) {
   if (use_net_rhs)
     cudaMemcpyAsync(f64, bL, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
   else
-    launch_old_time_rhs64(gL, 1.0 / cfg.dt, xold64, f64, st);
+    old_rhs(L(), xold64, f64);
   int rc = newton(f64, &s);
   if (use_net_rhs && (rc != DNNMG_OK || s.newton_its > cfg.fallback_newton_its)) {
     // the corrected right-hand side slowed Newton down: redo the step without it
     cudaMemcpyAsync(x64, xold64, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
-    launch_old_time_rhs64(gL, 1.0 / cfg.dt, xold64, f64, st);
+    old_rhs(L(), xold64, f64);
     const int first_its = s.newton_its, first_gits = s.gmres_its;
     rc = newton(f64, &s);
     s.newton_its += first_its;

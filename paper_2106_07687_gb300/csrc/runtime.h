@@ -21,6 +21,7 @@ struct HostLevel {
 HostLevel make_level(int ell, int oi0, int oj0);
 template <typename T>
 Sten<T> make_sten(double h, const dnnmg_config& c);
+Sten<double> make_explicit_sten(double h, const dnnmg_config& c);
 
 // Owns device allocations; frees them on destruction.
 class DevMem {
@@ -137,6 +138,7 @@ struct dnnmg_ctx {
   dnnmg::DevMem mem;
   std::unique_ptr<dnnmg::SolverBase> solver;
   dnnmg::Sten<double> s64L{};  // FP64 constants of the finest solved level
+  dnnmg::Sten<double> sxL{}, sxF{};  // explicit theta-scheme bracket on levels L, L+1
   // FP64 state of level L
   double* x64 = nullptr;
   double* xold64 = nullptr;
@@ -199,6 +201,8 @@ struct dnnmg_ctx {
   int patch_infer(const uint16_t* x, float* h, float* out, int P);
   int net_check(const char* what);
   int init_dnnmg();
+  // f = old-time right-hand side of Eq. 5 from x_old on level `level`
+  void old_rhs(int level, const double* x_old, double* f);
   int dnnmg_correction();
   int set_feature_stats(const float* mean, const float* stdv);
   int get_fine_velocity(double* v);

@@ -77,6 +77,22 @@ __global__ void __launch_bounds__(kBX* kBY)
   f[2 * nn + n] = 0.0;
 }
 
+// f -= coef * [nu (grad v, grad phi) + (v . grad v, phi)] on the velocity
+// rows: the explicit part of the theta-scheme (Eq. 5 with weight 1 - theta).
+// sx holds nu K in E, the Gauss weight h^2/4 without theta, and no pressure
+// or LPS terms, so the nonlinear rows of sx are exactly that bracket.
+__global__ void __launch_bounds__(kBX* kBY)
+    explicit_sub64_kernel(Grid g, Sten<double> sx, double coef, const double* __restrict__ x,
+                          double* __restrict__ f) {
+  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
+  if (i >= g.nnx || j >= g.nny) return;
+  const int n = j * g.nnx + i;
+  double ru, rv, rp;
+  node_rows<double, true, false>(g, sx, i, j, x, nullptr, ru, rv, rp);
+  f[n] -= coef * ru;
+  f[g.nn + n] -= coef * rv;
+}
+
 inline dim3 node_grid(const Grid& g) { return dim3(cdiv(g.nnx, kBX), cdiv(g.nny, kBY)); }
 
 }  // namespace
@@ -104,6 +120,12 @@ void launch_old_time_rhs64(const Grid& g, double inv_k, const double* x_old, dou
                            cudaStream_t st) {
   note_launch();
   old_rhs64_kernel<<<node_grid(g), dim3(kBX, kBY), 0, st>>>(g, inv_k, x_old, f);
+}
+
+void launch_explicit_sub64(const Grid& g, const Sten<double>& sx, double coef, const double* x,
+                           double* f, cudaStream_t st) {
+  note_launch();
+  explicit_sub64_kernel<<<node_grid(g), dim3(kBX, kBY), 0, st>>>(g, sx, coef, x, f);
 }
 
 template void launch_apply<float>(const Grid&, const Sten<float>&, const float*, const float*,

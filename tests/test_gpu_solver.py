@@ -71,18 +71,18 @@ def test_vcycle_matches_oracle(precision, tol, L, obstacle, seed):
     assert rel(xg, xr) < tol, rel(xg, xr)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_plain_steps_match_oracle(precision):
+@pytest.mark.parametrize("precision,theta", [(0, 1.0), (1, 1.0), (0, 0.5)])
+def test_plain_steps_match_oracle(precision, theta):
     """Small FP64 workload: 128x32 channel (level 3), nu = 0.01, dt = 0.01;
     three time steps from the impulsive start.  Both sides iterate Newton to
     ||r|| <= 1e-12 so that the distance between their converged states (at
     most ~||A'^-1|| * 2 tol) sits well below the 1e-10 bar; the solvers reach
     that state by different iterates (the GPU keeps the coarse LU for a whole
-    step)."""
+    step).  theta = 1/2 is the Crank-Nicolson form of Eq. 5."""
     dn = lib()
     obstacle = synthetic.obstacle_block(1000)
-    prm = fem.Params(nu=0.01, dt=0.01)
-    ctx = _ctx(dn, 3, precision, obstacle, prm.nu, prm.dt, newton_tol=1e-12)
+    prm = fem.Params(nu=0.01, dt=0.01, theta=theta)
+    ctx = _ctx(dn, 3, precision, obstacle, prm.nu, prm.dt, newton_tol=1e-12, theta=theta)
     levels = mesh.hierarchy(3, obstacle=obstacle)
     opt = newton.SolverOptions(newton_tol=1e-12)
     x = mesh.initial_state(levels[-1])
