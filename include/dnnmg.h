@@ -359,6 +359,70 @@ int dnnmg_profile_read(dnnmg_ctx* ctx, int stage, int level, int64_t* launches, 
  * as configured or chosen by timing at the first linearisation; -1 on error. */
 int dnnmg_vcycle_split(const dnnmg_ctx* ctx);
 
+/* ------------------------------------------------------------------------
+ * Batched problems
+ *
+ * A batch advances many independent channel problems of uneven size in
+ * lock-step with the algorithm of a single context (Newton, FGMRES, one
+ * V-cycle per Krylov step; DNN-MG steps add the correction of Algorithm 1
+ * lines 6-9 with one network evaluation over the patches of all problems).
+ * Every stage (a Vanka colour pass on level k, a defect, a transfer, a
+ * Krylov vector operation, ...) is one kernel launch over a work list of
+ * the blocks of all problems that take part in it; problems that have
+ * converged are masked.  One FGMRES iteration is replayed as a CUDA graph.
+ *
+ * Problems may differ in nu, dt, theta, alpha0, the obstacle and
+ * level_solve; all other fields must be equal.  DNN-MG needs
+ * replaced_levels = 1 and one network shared by all problems.
+ *
+ * The finest solved level of every problem lives in concatenated vectors
+ * of `length` elements: problem p occupies [offset_p, offset_p + 3 nn_p)
+ * ([3][ny+1][nx+1] layout of its level), padded with zeros to the next
+ * problem.  The batch runs on an internal stream: each call waits for the
+ * stream given to dnnmg_batch_setup() first and returns with its own work
+ * complete.
+ * ------------------------------------------------------------------------ */
+typedef struct dnnmg_batch dnnmg_batch;
+
+/* Set up n >= 1 problems from cfgs[0..n) (validated like dnnmg_setup).  On
+ * failure *out is NULL and dnnmg_batch_last_error(NULL) holds the reason. */
+int dnnmg_batch_setup(const dnnmg_config* cfgs, int n, void* stream, dnnmg_batch** out);
+int dnnmg_batch_destroy(dnnmg_batch* b);
+/* message of the last failure of b (b = NULL: of this thread's last setup) */
+const char* dnnmg_batch_last_error(const dnnmg_batch* b);
+/* number of problems and length of the concatenated top-level vectors */
+int dnnmg_batch_size(const dnnmg_batch* b, int* n, int64_t* length);
+/* finest solved level and offset of problem `inst` in the concatenated vectors */
+int dnnmg_batch_layout(const dnnmg_batch* b, int inst, int* level, int64_t* offset);
+/* FP64 state of problem `inst` ([3][..] of its level, device) */
+int dnnmg_batch_get_state(dnnmg_batch* b, int inst, double* x);
+/* replaces the state (Dirichlet values re-imposed); resets the DNN-MG
+ * history of the batch and forces a coarse refactorisation at the next step */
+int dnnmg_batch_set_state(dnnmg_batch* b, int inst, const double* x);
+/* linearise every problem's hierarchy at its current state (like
+ * dnnmg_linearize of a single context) */
+int dnnmg_batch_linearize(dnnmg_batch* b);
+/* one V(nu1, nu2) cycle of every problem on its finest solved level from
+ * x = 0: rhs, x are concatenated device vectors of `length` elements in the
+ * batch precision (double for DNNMG_FP64, float for DNNMG_MIXED) */
+int dnnmg_batch_vcycle(dnnmg_batch* b, const void* rhs, void* x);
+/* One time step of every problem; stats[0..n) (nullable) receive each
+ * problem's counts and status (ms: the batch's step time).  Returns
+ * DNNMG_OK or the first non-OK problem status. */
+int dnnmg_batch_step(dnnmg_batch* b, int mode, dnnmg_step_stats* stats);
+/* shared network weights (host, flat order of dnnmg_set_weights) and
+ * feature standardisation (host, C_in floats each) */
+int dnnmg_batch_set_weights(dnnmg_batch* b, const float* w);
+int dnnmg_batch_set_feature_stats(dnnmg_batch* b, const float* mean, const float* std);
+/* corrected level L+1 velocity of problem `inst` after a DNN-MG step
+ * ([2][..] of level L+1, device) */
+int dnnmg_batch_get_fine_velocity(dnnmg_batch* b, int inst, double* v);
+/* on != 0 (default): replay FGMRES iterations as CUDA graphs */
+int dnnmg_batch_graphs(dnnmg_batch* b, int on);
+/* stage timers as dnnmg_profile / dnnmg_profile_read (levels are absolute) */
+int dnnmg_batch_profile(dnnmg_batch* b, int enable);
+int dnnmg_batch_profile_read(dnnmg_batch* b, int stage, int level, int64_t* launches, double* ms);
+
 /* Number of kernels this library has launched in this process so far. */
 uint64_t dnnmg_kernel_launches(void);
 

@@ -1,233 +1,43 @@
-// Direct solve on the coarsest multigrid level (level 1, 32x8 cells).
-//
-// The Jacobian of the coarsest level is assembled in FP64 into band storage
-// with the unknowns numbered node-major along y, p = (i * nny + j) * 3 + c,
-// which gives kl = ku = 6 * nny + 8.  It is factored by LU with partial
-// pivoting (row interchanges, multipliers kept in place), then the explicit
-// inverse is formed column by column.  A V-cycle's coarse solve is one dense
-// FP64 matrix-vector product with that inverse.
+// Direct solve on the coarsest multigrid level: launchers of the assembly,
+// banded LU, explicit inverse and the dense solve (bodies in coarse_body.cuh).
 #include <cstdio>
 
+#include "coarse_body.cuh"
 #include "kernels.h"
 
 namespace dnnmg {
 
 namespace {
 
-struct Band {
-  int n, kl, ku, W;  // W = 2 kl + ku + 1 stored columns per row
-};
-
-__host__ __device__ inline Band band_of(const Grid& g) {
-  Band b;
-  b.n = 3 * g.nn;
-  b.kl = b.ku = 6 * g.nny + 8;
-  b.W = 2 * b.kl + b.ku + 1;
-  return b;
-}
-
-// band index of DOF (comp c, node (i, j)) and back
-__host__ __device__ inline int bidx(const Grid& g, int c, int i, int j) {
-  return (i * g.nny + j) * 3 + c;
-}
-__host__ __device__ inline int lidx(const Grid& g, int p) {
-  const int c = p % 3, node = p / 3;
-  const int i = node / g.nny, j = node % g.nny;
-  return c * g.nn + j * g.nnx + i;
-}
-
-// entry (r, col) of the band matrix
-__device__ __forceinline__ double& AB(double* ab, const Band& b, int r, int col) {
-  return ab[(size_t)r * b.W + (col - r + b.kl)];
-}
-
 // One thread per row of the coarse Jacobian.
 __global__ void assemble_kernel(Grid g, Sten<double> s, const double* __restrict__ vb,
                                 double* __restrict__ ab) {
-  const Band bd = band_of(g);
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= bd.n) return;
-  for (int k = 0; k < bd.W; ++k) ab[(size_t)row * bd.W + k] = 0.0;
-  const int c = row % 3, node = row / 3;
-  const int i = node / g.nny, j = node % g.nny;
-  const uint8_t f = g.flags[j * g.nnx + i];
-  const bool cons = (c < 2) ? (f & kVDir) : (f & kPFix);
-  if (cons) {
-    AB(ab, bd, row, row) = 1.0;
-    return;
-  }
-  for (int cy = 0; cy < 2; ++cy)
-    for (int cx = 0; cx < 2; ++cx) {
-      const int ci = i - 1 + cx, cj = j - 1 + cy;
-      if (ci < 0 || cj < 0 || ci >= g.nx || cj >= g.ny || g.solid[cj * g.nx + ci]) continue;
-      const int al = (1 - cx) + 2 * (1 - cy);
-      double bu[4], bv[4];
-      load_cell<double, false>(g, vb, ci, cj, 0, bu);
-      load_cell<double, false>(g, vb + g.nn, ci, cj, 0, bv);
-      GaussData<double> gd;
-      gauss_data<double>(bu, bv, gd);
-      for (int be = 0; be < 4; ++be) {
-        const int ni = ci + (be & 1), nj = cj + (be >> 1);
-        const uint8_t fb = g.flags[nj * g.nnx + ni];
-        double J[3][3];
-        elem_pair<double>(s, gd, al, be, J);
-        for (int c2 = 0; c2 < 3; ++c2) {
-          const bool cons2 = (c2 < 2) ? (fb & kVDir) : (fb & kPFix);
-          if (cons2) continue;
-          AB(ab, bd, row, bidx(g, c2, ni, nj)) += J[c][c2];
-        }
-      }
-    }
-  if (c == 2) {
-    for (int dJ = 0; dJ < 2; ++dJ) {
-      const int PJ = (j >> 1) - dJ;
-      if (PJ < 0 || PJ >= g.ny / 2 || j - 2 * PJ > 2) continue;
-      for (int dI = 0; dI < 2; ++dI) {
-        const int PI = (i >> 1) - dI;
-        if (PI < 0 || PI >= g.nx / 2 || i - 2 * PI > 2) continue;
-        if (g.solid[(2 * PJ) * g.nx + 2 * PI]) continue;
-        const int mn = (i - 2 * PI) + 3 * (j - 2 * PJ);
-        for (int m = 0; m < 9; ++m) {
-          const int ni = 2 * PI + m % 3, nj = 2 * PJ + m / 3;
-          if (g.flags[nj * g.nnx + ni] & kPFix) continue;
-          AB(ab, bd, row, bidx(g, 2, ni, nj)) += s.S9[mn * 9 + m];
-        }
-      }
-    }
-  }
+  assemble_row(g, s, vb, ab, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-// Banded LU with partial pivoting in one thread block (dgbtf2 ordering).
-// The rows k..k+kl that elimination step k touches live in a shared-memory
-// window of kWin row slots (row r in slot r % kWin, same per-row band offset
-// as in global memory); a row is loaded when it enters the window and written
-// back once it is final.
-constexpr int kLUThreads = 1024;
-constexpr int kWin = 64;
 __global__ void __launch_bounds__(kLUThreads)
     band_lu_kernel(Grid g, double* __restrict__ ab, int* __restrict__ piv, int* status) {
-  const Band bd = band_of(g);
   extern __shared__ double win[];  // kWin * W
-  __shared__ int s_p;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  auto W = [&](int r, int col) -> double& {
-    return win[(size_t)(r % kWin) * bd.W + (col - r + bd.kl)];
-  };
-  // rows 0..kl enter the window
-  for (int r = 0; r <= min(bd.kl, bd.n - 1); ++r)
-    for (int e = tid; e < bd.W; e += kLUThreads)
-      win[(size_t)(r % kWin) * bd.W + e] = ab[(size_t)r * bd.W + e];
-  __syncthreads();
-  for (int k = 0; k < bd.n; ++k) {
-    const int rmax = min(bd.n - 1, k + bd.kl);
-    double best = -1.0;
-    int bi = k;
-    if (warp == 0) {
-      for (int r = k + lane; r <= rmax; r += 32) {
-        const double v = fabs(W(r, k));
-        if (v > best) best = v, bi = r;
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_down_sync(0xffffffffu, best, o);
-        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-        if (ov > best || (ov == best && oi < bi)) best = ov, bi = oi;
-      }
-      if (lane == 0) {
-        s_p = bi;
-        piv[k] = bi;
-        if (!(best > 0.0)) atomicOr(status, 2);
-      }
-    }
-    __syncthreads();
-    const int p = s_p;
-    const int cmax = min(bd.n - 1, k + bd.ku + bd.kl);
-    if (p != k)
-      for (int col = k + tid; col <= cmax; col += kLUThreads) {
-        const double t = W(k, col);
-        W(k, col) = W(p, col);
-        W(p, col) = t;
-      }
-    __syncthreads();
-    const double d = W(k, k);
-    const double id = d != 0.0 ? 1.0 / d : 0.0;
-    for (int r = k + 1 + tid; r <= rmax; r += kLUThreads) W(r, k) *= id;
-    __syncthreads();
-    const int nr = rmax - k, nc = cmax - k;
-    for (int e = tid; e < nr * nc; e += kLUThreads) {
-      const int r = k + 1 + e / nc, col = k + 1 + e % nc;
-      W(r, col) -= W(r, k) * W(k, col);
-    }
-    __syncthreads();
-    // row k is final: write it back; row k + kl + 1 enters the window
-    for (int e = tid; e < bd.W; e += kLUThreads)
-      ab[(size_t)k * bd.W + e] = win[(size_t)(k % kWin) * bd.W + e];
-    __syncthreads();
-    const int rn = k + bd.kl + 1;
-    if (rn < bd.n)
-      for (int e = tid; e < bd.W; e += kLUThreads)
-        win[(size_t)(rn % kWin) * bd.W + e] = ab[(size_t)rn * bd.W + e];
-    __syncthreads();
-  }
+  band_lu_block(g, ab, piv, status, win);
 }
 
 // Column `col` of the inverse: solve L U x = P e_col, one warp per column.
-constexpr int kInvWarps = 4;
 __global__ void __launch_bounds__(32 * kInvWarps)
     band_inverse_kernel(Grid g, const double* __restrict__ ab, const int* __restrict__ piv,
                         double* __restrict__ Ainv) {
-  const Band bd = band_of(g);
   extern __shared__ double sm[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int col = blockIdx.x * kInvWarps + warp;
-  if (col >= bd.n) return;
-  double* x = sm + (size_t)warp * bd.n;
-  for (int r = lane; r < bd.n; r += 32) x[r] = (r == col) ? 1.0 : 0.0;
-  __syncwarp();
-  for (int k = 0; k < bd.n; ++k) {
-    const int p = piv[k];
-    if (lane == 0 && p != k) {
-      const double t = x[k];
-      x[k] = x[p];
-      x[p] = t;
-    }
-    __syncwarp();
-    const double xk = x[k];
-    if (xk != 0.0) {
-      const int rmax = min(bd.n - 1, k + bd.kl);
-      for (int r = k + 1 + lane; r <= rmax; r += 32) x[r] -= AB(const_cast<double*>(ab), bd, r, k) * xk;
-    }
-    __syncwarp();
-  }
-  for (int k = bd.n - 1; k >= 0; --k) {
-    const int cmax = min(bd.n - 1, k + bd.ku + bd.kl);
-    double acc = 0.0;
-    for (int c2 = k + 1 + lane; c2 <= cmax; c2 += 32)
-      acc += AB(const_cast<double*>(ab), bd, k, c2) * x[c2];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) x[k] = (x[k] - acc) / AB(const_cast<double*>(ab), bd, k, k);
-    __syncwarp();
-  }
-  for (int r = lane; r < bd.n; r += 32) Ainv[(size_t)r * bd.n + col] = x[r];
+  const int warp = threadIdx.x >> 5;
+  band_inverse_col(g, ab, piv, Ainv, blockIdx.x * kInvWarps + warp,
+                   sm + (size_t)warp * 3 * g.nn);
 }
 
 // x = Ainv b with the band numbering on both sides; one warp per row.
-constexpr int kSolveWarps = 8;
 template <typename T>
 __global__ void __launch_bounds__(32 * kSolveWarps)
     coarse_solve_kernel(Grid g, const double* __restrict__ Ainv, const T* __restrict__ b,
                         T* __restrict__ x) {
-  const Band bd = band_of(g);
   extern __shared__ double sb[];
-  for (int p = threadIdx.x; p < bd.n; p += blockDim.x) sb[p] = (double)b[lidx(g, p)];
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int r = blockIdx.x * kSolveWarps + warp;
-  if (r >= bd.n) return;
-  const double* row = Ainv + (size_t)r * bd.n;
-  double acc = 0.0;
-  for (int c = lane; c < bd.n; c += 32) acc += row[c] * sb[c];
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) x[lidx(g, r)] = (T)acc;
+  coarse_solve_rows<T>(g, Ainv, b, x, blockIdx.x, sb);
 }
 
 // x = (LU)^{-1} b with the factors and pivots of band_lu_kernel; one block,

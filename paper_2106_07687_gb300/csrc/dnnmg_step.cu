@@ -12,6 +12,7 @@
 // each standardised as (value - mean) / std and rounded to bfloat16.
 #include <cuda_bf16.h>
 
+#include "dnnmg_body.cuh"
 #include "dnnmg_step.h"
 
 namespace dnnmg {
@@ -23,14 +24,7 @@ constexpr int kBX = 32, kBY = 4;
 __global__ void impose_dirichlet_kernel(Grid g, double* __restrict__ x) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   if (i >= g.nnx || j >= g.nny) return;
-  const int n = j * g.nnx + i;
-  const uint8_t f = g.flags[n];
-  if (f & kVDir) {
-    const double y = j * g.h;
-    x[n] = (i == 0) ? 6.0 * y * (1.0 - y) : 0.0;
-    x[g.nn + n] = 0.0;
-  }
-  if (f & kPFix) x[2 * g.nn + n] = 0.0;
+  impose_dirichlet_node(g, x, i, j);
 }
 
 template <bool RAW>
@@ -41,35 +35,8 @@ __global__ void gather_kernel(Grid gL, Grid gF, const int* __restrict__ patch_ce
                               float* __restrict__ Xraw) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
-  const int cell = patch_cell[p];
-  const int I = cell % gL.nx, J = cell / gL.nx;
-  float f[40];
-  double su = 0, sv = 0;
-#pragma unroll
-  for (int m = 0; m < 9; ++m) {
-    const int n = (2 * J + m / 3) * gF.nnx + 2 * I + m % 3;
-    const double u = xt[n], v = xt[gF.nn + n];
-    su += u;
-    sv += v;
-    f[m] = (float)u;
-    f[9 + m] = (float)v;
-    f[18 + m] = (float)r[n];
-    f[27 + m] = (float)r[gF.nn + n];
-  }
-  const double hL = gL.h;
-  f[36] = (float)(hL / 0.25);
-  f[37] = 1.0f;
-  f[38] = (float)(sqrt(su * su + sv * sv) / 9.0 * hL / nu);
-  f[39] = (float)(dt / hL);
-  if (RAW) {
-#pragma unroll
-    for (int k = 0; k < 40; ++k) Xraw[(size_t)p * 40 + k] = f[k];
-    return;
-  }
-  uint16_t* out = X + (size_t)p * 40;
-#pragma unroll
-  for (int k = 0; k < 40; ++k)
-    out[k] = __bfloat16_as_ushort(__float2bfloat16_rn((f[k] - mean[k]) / stdv[k]));
+  gather_patch<RAW>(gL, gF, patch_cell[p], xt, r, mean, stdv, nu, dt,
+                    RAW ? nullptr : X + (size_t)p * 40, RAW ? Xraw + (size_t)p * 40 : nullptr);
 }
 
 // Training target of a patch: (next fine velocity - prolongated velocity) at
@@ -153,35 +120,12 @@ __global__ void gather_batch_kernel(const float* __restrict__ Xraw, const float*
   }
 }
 
-// v_corr = xt + d at every fine node, d = mean of the predictions of the
-// patches containing the node, zero on velocity Dirichlet nodes; pressure 0.
 __global__ void scatter_kernel(Grid gL, Grid gF, const int* __restrict__ cell_patch,
                                const float* __restrict__ out, int c_out,
                                const double* __restrict__ xt, double* __restrict__ vcorr) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   if (i >= gF.nnx || j >= gF.nny) return;
-  const int n = j * gF.nnx + i;
-  double du = 0, dv = 0;
-  int cnt = 0;
-  for (int dJ = 0; dJ < 2; ++dJ) {
-    const int J = (j >> 1) - dJ;
-    if (J < 0 || J >= gL.ny || j - 2 * J > 2) continue;
-    for (int dI = 0; dI < 2; ++dI) {
-      const int I = (i >> 1) - dI;
-      if (I < 0 || I >= gL.nx || i - 2 * I > 2) continue;
-      const int p = cell_patch[J * gL.nx + I];
-      if (p < 0) continue;
-      const int m = (i - 2 * I) + 3 * (j - 2 * J);
-      du += out[(size_t)p * c_out + m];
-      dv += out[(size_t)p * c_out + 9 + m];
-      ++cnt;
-    }
-  }
-  if (cnt == 0 || (gF.flags[n] & kVDir)) du = dv = 0.0;
-  else du /= cnt, dv /= cnt;
-  vcorr[n] = xt[n] + du;
-  vcorr[gF.nn + n] = xt[gF.nn + n] + dv;
-  vcorr[2 * gF.nn + n] = 0.0;
+  scatter_node(gL, gF, cell_patch, out, c_out, xt, vcorr, i, j);
 }
 
 inline dim3 grid_of(const Grid& g) { return dim3(cdiv(g.nnx, kBX), cdiv(g.nny, kBY)); }

@@ -9,6 +9,7 @@ namespace dnnmg {
 
 // Process-wide count of kernels launched by this library.
 void note_launch();
+void note_launches(unsigned long long n);  // kernels of a replayed graph
 unsigned long long launches();
 
 // Operator rows (stencil.cu) ---------------------------------------------
@@ -56,10 +57,13 @@ void launch_restrict_full64(const Grid& fine, const Grid& coarse, const double* 
 template <typename T>
 void launch_vanka_setup(const Grid& g, const Sten<T>& s, const T* vb, T* inv, int* status,
                         cudaStream_t st);
-// one colour pass: xout = xin + omega A_c^{-1} (b - A xin)_c on the colour's cells
+// one colour pass: xout = xin + omega A_c^{-1} (b - A xin)_c on the colour's cells;
+// `shape` picks the tile of colour cells a block owns: 0 = 16x4, 1 = 8x4, 2 = 8x8
+constexpr int kPassShapes = 3;
 template <typename T>
 void launch_vanka_pass(const Grid& g, const Sten<T>& s, int colour, const T* b, const T* xin,
-                       const T* vb, const T* inv, T omega, T* xout, cudaStream_t st);
+                       const T* vb, const T* inv, T omega, T* xout, cudaStream_t st,
+                       int shape = 0);
 __host__ __device__ inline int vanka_slots(const Grid& g) { return (g.nx / 2 + 1) * (g.ny / 2 + 1); }
 
 // Coarse direct solve (coarse.cu) -------------------------------------------

@@ -368,23 +368,49 @@ int dnnmg_ctx::check(const char* what) {
   return DNNMG_OK;
 }
 
-int dnnmg_ctx::init() {
-  const dnnmg_config& c = cfg;
+namespace dnnmg {
+
+namespace {
+int fail_msg(std::string& err, int code, const char* msg) {
+  err = msg;
+  return code;
+}
+}  // namespace
+
+int check_config(const dnnmg_config& c, std::string& err) {
   if (!(c.nu > 0) || !(c.dt > 0) || !(c.alpha0 >= 0) || !(c.theta > 0 && c.theta <= 1))
-    return fail(DNNMG_ERR_ARG, "nu, dt, theta or alpha0 out of range");
+    return fail_msg(err, DNNMG_ERR_ARG, "nu, dt, theta or alpha0 out of range");
   if (c.level_coarse < 1 || c.level_coarse > c.level_solve || c.level_solve > 9)
-    return fail(DNNMG_ERR_ARG, "need 1 <= level_coarse <= level_solve <= 9");
-  if (c.level_coarse != 1) return fail(DNNMG_ERR_ARG, "the coarse direct solve supports level 1");
+    return fail_msg(err, DNNMG_ERR_ARG, "need 1 <= level_coarse <= level_solve <= 9");
+  if (c.level_coarse != 1) return fail_msg(err, DNNMG_ERR_ARG, "the coarse direct solve supports level 1");
   if (c.replaced_levels < 0 || c.replaced_levels > 2 || c.level_solve + c.replaced_levels > 10)
-    return fail(DNNMG_ERR_ARG, "replaced_levels must be 0, 1 or 2");
+    return fail_msg(err, DNNMG_ERR_ARG, "replaced_levels must be 0, 1 or 2");
   if (c.obstacle_i0 >= 0 && (c.obstacle_i0 < 1 || c.obstacle_i0 > 13 || c.obstacle_j0 < 1 ||
                              c.obstacle_j0 > 1))
-    return fail(DNNMG_ERR_ARG, "obstacle must be a 2x2 level-0 block with 1 <= i0 <= 13, j0 = 1");
+    return fail_msg(err, DNNMG_ERR_ARG, "obstacle must be a 2x2 level-0 block with 1 <= i0 <= 13, j0 = 1");
   if (c.precision != DNNMG_FP64 && c.precision != DNNMG_MIXED)
-    return fail(DNNMG_ERR_ARG, "unknown precision");
+    return fail_msg(err, DNNMG_ERR_ARG, "unknown precision");
   if (c.gmres_m < 1 || c.gmres_m > 40 || c.gmres_maxit < 1 || c.newton_max < 1 || c.nu1 < 0 ||
       c.nu2 < 0 || c.coarse_refresh < 1)
-    return fail(DNNMG_ERR_ARG, "solver parameters out of range");
+    return fail_msg(err, DNNMG_ERR_ARG, "solver parameters out of range");
+  return DNNMG_OK;
+}
+
+std::vector<double> initial_state(const Grid& g) {
+  // impulsive start: zero state, then the inflow profile on x = 0
+  std::vector<double> x0(3 * (size_t)g.nn, 0.0);
+  for (int j = 0; j <= g.ny; ++j) {
+    const double y = j * g.h;
+    x0[(size_t)j * g.nnx] = 6.0 * y * (1.0 - y);
+  }
+  return x0;
+}
+
+}  // namespace dnnmg
+
+int dnnmg_ctx::init() {
+  const dnnmg_config& c = cfg;
+  if (int rc = check_config(c, err)) return rc;
   const int nlev = c.level_solve + c.replaced_levels + 1;
   for (int l = 0; l < nlev; ++l) lv.push_back(make_level(l, c.obstacle_i0, c.obstacle_j0));
   for (int l = 0; l < nlev; ++l) {
@@ -413,12 +439,7 @@ int dnnmg_ctx::init() {
   s64L = make_sten<double>(gL.h, cfg);
   sxL = make_explicit_sten(gL.h, cfg);
   if ((int)lv.size() > L() + 1) sxF = make_explicit_sten(grid(L() + 1).h, cfg);
-  // impulsive start: zero state, then the inflow profile on x = 0
-  std::vector<double> x0(n3, 0.0);
-  for (int j = 0; j <= gL.ny; ++j) {
-    const double y = j * gL.h;
-    x0[(size_t)j * gL.nnx] = 6.0 * y * (1.0 - y);
-  }
+  const std::vector<double> x0 = initial_state(gL);
   cudaMemcpyAsync(x64, x0.data(), n3 * sizeof(double), cudaMemcpyHostToDevice, st);
   cudaStreamSynchronize(st);
   if (int rc = check("setup")) return rc;

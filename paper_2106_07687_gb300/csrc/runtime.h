@@ -19,6 +19,10 @@ struct HostLevel {
 };
 
 HostLevel make_level(int ell, int oi0, int oj0);
+// DNNMG_OK, or an error code with the reason in err
+int check_config(const dnnmg_config& c, std::string& err);
+// impulsive start on a level: zero state with the inflow profile on x = 0
+std::vector<double> initial_state(const Grid& g);
 template <typename T>
 Sten<T> make_sten(double h, const dnnmg_config& c);
 Sten<double> make_explicit_sten(double h, const dnnmg_config& c);

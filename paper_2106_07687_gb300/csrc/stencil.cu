@@ -18,13 +18,7 @@ __global__ void __launch_bounds__(kBX* kBY) apply_kernel(Grid g, Sten<T> s, cons
                                                          T* __restrict__ y) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   if (i >= g.nnx || j >= g.nny) return;
-  const int n = j * g.nnx + i;
-  T ru, rv, rp;
-  node_rows<T, false, true>(g, s, i, j, w, vb, ru, rv, rp);
-  const uint8_t f = g.flags[n];
-  y[n] = (f & kVDir) ? w[n] : ru;
-  y[g.nn + n] = (f & kVDir) ? w[g.nn + n] : rv;
-  y[2 * g.nn + n] = (f & kPFix) ? w[2 * g.nn + n] : rp;
+  apply_node<T>(g, s, w, vb, y, i, j);
 }
 
 template <typename T>
@@ -41,56 +35,22 @@ __global__ void __launch_bounds__(kBX* kBY)
                       const double* __restrict__ f, double* __restrict__ r) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   if (i >= g.nnx || j >= g.nny) return;
-  const int n = j * g.nnx + i;
-  double ru, rv, rp;
-  node_rows<double, true, false>(g, s, i, j, x, nullptr, ru, rv, rp);
-  const uint8_t fl = g.flags[n];
-  const int nn = g.nn;
-  r[n] = (fl & kVDir) ? 0.0 : f[n] - ru;
-  r[nn + n] = (fl & kVDir) ? 0.0 : f[nn + n] - rv;
-  r[2 * nn + n] = (fl & kPFix) ? 0.0 : f[2 * nn + n] - rp;
+  residual64_node(g, s, x, f, r, i, j);
 }
 
-// (1/k) (v_old, phi) with the Q1 mass matrix (h^2/36) [4 2 2 1] pattern.
 __global__ void __launch_bounds__(kBX* kBY)
     old_rhs64_kernel(Grid g, double inv_k, const double* __restrict__ x, double* __restrict__ f) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   if (i >= g.nnx || j >= g.nny) return;
-  const int n = j * g.nnx + i, nn = g.nn;
-  const double m = g.h * g.h / 36.0 * inv_k;
-  double fu = 0, fv = 0;
-  for (int cy = 0; cy < 2; ++cy)
-    for (int cx = 0; cx < 2; ++cx) {
-      const int ci = i - 1 + cx, cj = j - 1 + cy;
-      if (ci < 0 || cj < 0 || ci >= g.nx || cj >= g.ny || g.solid[cj * g.nx + ci]) continue;
-      const int ax = 1 - cx, ay = 1 - cy;
-      for (int b = 0; b < 4; ++b) {
-        const int bx = b & 1, by = b >> 1;
-        const double wgt = (ax == bx ? 2.0 : 1.0) * (ay == by ? 2.0 : 1.0);
-        const int nb = (cj + by) * g.nnx + ci + bx;
-        fu += wgt * x[nb];
-        fv += wgt * x[nn + nb];
-      }
-    }
-  f[n] = m * fu;
-  f[nn + n] = m * fv;
-  f[2 * nn + n] = 0.0;
+  old_rhs64_node(g, inv_k, x, f, i, j);
 }
 
-// f -= coef * [nu (grad v, grad phi) + (v . grad v, phi)] on the velocity
-// rows: the explicit part of the theta-scheme (Eq. 5 with weight 1 - theta).
-// sx holds nu K in E, the Gauss weight h^2/4 without theta, and no pressure
-// or LPS terms, so the nonlinear rows of sx are exactly that bracket.
 __global__ void __launch_bounds__(kBX* kBY)
     explicit_sub64_kernel(Grid g, Sten<double> sx, double coef, const double* __restrict__ x,
                           double* __restrict__ f) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   if (i >= g.nnx || j >= g.nny) return;
-  const int n = j * g.nnx + i;
-  double ru, rv, rp;
-  node_rows<double, true, false>(g, sx, i, j, x, nullptr, ru, rv, rp);
-  f[n] -= coef * ru;
-  f[g.nn + n] -= coef * rv;
+  explicit_sub64_node(g, sx, coef, x, f, i, j);
 }
 
 inline dim3 node_grid(const Grid& g) { return dim3(cdiv(g.nnx, kBX), cdiv(g.nny, kBY)); }

@@ -30,9 +30,7 @@ __global__ void prolong_state_kernel(Grid f, Grid c, const double* __restrict__ 
                                      double* __restrict__ xf, int ncomp) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   if (i >= f.nnx || j >= f.nny) return;
-  const int n = j * f.nnx + i;
-  for (int comp = 0; comp < ncomp; ++comp)
-    xf[comp * f.nn + n] = interp_node<double, false>(c, xc + comp * c.nn, 0, i, j);
+  prolong_state_node(f, c, xc, xf, ncomp, i, j);
 }
 
 template <typename T>
@@ -40,8 +38,7 @@ __global__ void inject_kernel(Grid f, Grid c, const T* __restrict__ xf, T* __res
                               int ncomp) {
   const int I = blockIdx.x * kBX + threadIdx.x, J = blockIdx.y * kBY + threadIdx.y;
   if (I >= c.nnx || J >= c.nny) return;
-  for (int comp = 0; comp < ncomp; ++comp)
-    xc[comp * c.nn + J * c.nnx + I] = xf[comp * f.nn + (2 * J) * f.nnx + 2 * I];
+  inject_node<T>(f, c, xf, xc, ncomp, I, J);
 }
 
 inline dim3 grid_of(const Grid& g) { return dim3(cdiv(g.nnx, kBX), cdiv(g.nny, kBY)); }

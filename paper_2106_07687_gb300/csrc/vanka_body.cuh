@@ -1,0 +1,323 @@
+// Per-thread and per-tile bodies of the Vanka smoother, shared by the
+// single-problem kernels (vanka.cu) and the batched kernels (batch.cu).
+//
+// Setup: for every fluid cell, the restriction of the global Jacobian to the
+// cell's 12 DOFs (its 4 nodes x u, v, p), with identity rows/columns on
+// constrained DOFs, is inverted by Gauss-Jordan elimination with partial
+// pivoting and stored as inv[colour][entry][slot] so that the smoothing pass
+// streams it with coalesced loads.
+//
+// Tiled colour pass: a block owns kTCX x kTCY cells of the colour, i.e. the
+// (2 kTCX) x (2 kTCY) nodes they cover.  It stages the masked iterate, vbar
+// and the flags of those nodes plus a two-node halo in shared memory,
+// computes the 12 rows of every cell touching the tile and the 9 LPS rows of
+// every patch touching it once, sums them per node, exchanges each cell's 12
+// defects among the cell's four threads by warp shuffles and applies the
+// 12x12 inverse.  Cells of one colour share no node; nodes outside the
+// colour's fluid cells are copied, so x_out is complete and the next colour
+// reads it without races.
+#pragma once
+#include "common.cuh"
+
+namespace dnnmg {
+
+template <typename T>
+__device__ __forceinline__ T vk_abs(T v) {
+  return v < T(0) ? -v : v;
+}
+
+// Inverse of the local 12x12 block of the cell of `slot` in `colour`.
+template <typename T>
+__device__ __forceinline__ void vanka_setup_cell(const Grid& g, const Sten<T>& s,
+                                                 const T* __restrict__ vb, T* __restrict__ inv,
+                                                 int* status, int colour, int slot) {
+  const int cx = colour & 1, cy = colour >> 1;
+  const int sx = g.nx / 2 + 1;
+  const int nslots = sx * (g.ny / 2 + 1);
+  if (slot >= nslots) return;
+  const int ci = 2 * (slot % sx) - cx, cj = 2 * (slot / sx) - cy;
+  if (ci < 0 || cj < 0 || ci >= g.nx || cj >= g.ny || g.solid[cj * g.nx + ci]) return;
+
+  T A[12][24];
+#pragma unroll
+  for (int r = 0; r < 12; ++r)
+#pragma unroll
+    for (int c = 0; c < 24; ++c) A[r][c] = T(0);
+
+  // element contributions of the (up to) 9 cells sharing a node with this one
+  for (int dy = -1; dy <= 1; ++dy)
+    for (int dx = -1; dx <= 1; ++dx) {
+      const int tx = ci + dx, ty = cj + dy;
+      if (tx < 0 || ty < 0 || tx >= g.nx || ty >= g.ny || g.solid[ty * g.nx + tx]) continue;
+      T bu[4], bv[4];
+      load_cell<T, false>(g, vb, tx, ty, 0, bu);
+      load_cell<T, false>(g, vb + g.nn, tx, ty, 0, bv);
+      GaussData<T> gd;
+      gauss_data<T>(bu, bv, gd);
+      for (int a = 0; a < 4; ++a) {
+        const int alx = (a & 1) - dx, aly = (a >> 1) - dy;
+        if (alx < 0 || alx > 1 || aly < 0 || aly > 1) continue;
+        for (int b = 0; b < 4; ++b) {
+          const int bex = (b & 1) - dx, bey = (b >> 1) - dy;
+          if (bex < 0 || bex > 1 || bey < 0 || bey > 1) continue;
+          T J[3][3];
+          elem_pair<T>(s, gd, alx + 2 * aly, bex + 2 * bey, J);
+          for (int c = 0; c < 3; ++c)
+            for (int c2 = 0; c2 < 3; ++c2) A[c * 4 + a][c2 * 4 + b] += J[c][c2];
+        }
+      }
+    }
+  // local projection stabilisation of the patches containing node pairs
+  const int PI0 = ci >> 1, PJ0 = cj >> 1;
+  for (int dJ = -1; dJ <= 1; ++dJ)
+    for (int dI = -1; dI <= 1; ++dI) {
+      const int PI = PI0 + dI, PJ = PJ0 + dJ;
+      if (PI < 0 || PJ < 0 || PI >= g.nx / 2 || PJ >= g.ny / 2) continue;
+      if (g.solid[(2 * PJ) * g.nx + 2 * PI]) continue;
+      for (int a = 0; a < 4; ++a) {
+        const int sa = ci + (a & 1) - 2 * PI, ta = cj + (a >> 1) - 2 * PJ;
+        if (sa < 0 || sa > 2 || ta < 0 || ta > 2) continue;
+        for (int b = 0; b < 4; ++b) {
+          const int sb = ci + (b & 1) - 2 * PI, tb = cj + (b >> 1) - 2 * PJ;
+          if (sb < 0 || sb > 2 || tb < 0 || tb > 2) continue;
+          A[8 + a][8 + b] += s.S9[(sa + 3 * ta) * 9 + sb + 3 * tb];
+        }
+      }
+    }
+  // identity rows and columns on constrained DOFs
+  for (int a = 0; a < 4; ++a) {
+    const uint8_t f = g.flags[(cj + (a >> 1)) * g.nnx + ci + (a & 1)];
+    for (int c = 0; c < 3; ++c) {
+      const bool cons = (c < 2) ? (f & kVDir) : (f & kPFix);
+      if (!cons) continue;
+      const int r = c * 4 + a;
+      for (int k = 0; k < 12; ++k) A[r][k] = A[k][r] = T(0);
+      A[r][r] = T(1);
+    }
+  }
+  for (int r = 0; r < 12; ++r) A[r][12 + r] = T(1);
+
+  // Gauss-Jordan elimination with partial pivoting on [A | I]
+  bool ok = true;
+  for (int k = 0; k < 12; ++k) {
+    int p = k;
+    T best = vk_abs(A[k][k]);
+    for (int r = k + 1; r < 12; ++r) {
+      const T v = vk_abs(A[r][k]);
+      if (v > best) best = v, p = r;
+    }
+    if (!(best > T(0))) {
+      ok = false;
+      break;
+    }
+    if (p != k)
+      for (int c = 0; c < 24; ++c) {
+        const T t = A[k][c];
+        A[k][c] = A[p][c];
+        A[p][c] = t;
+      }
+    const T ip = T(1) / A[k][k];
+    for (int c = 0; c < 24; ++c) A[k][c] *= ip;
+    for (int r = 0; r < 12; ++r) {
+      if (r == k) continue;
+      const T f = A[r][k];
+      if (f == T(0)) continue;
+      for (int c = 0; c < 24; ++c) A[r][c] -= f * A[k][c];
+    }
+  }
+  if (!ok) atomicOr(status, 1);
+  T* out = inv + (size_t)colour * 144 * nslots + slot;
+  for (int r = 0; r < 12; ++r)
+    for (int c = 0; c < 12; ++c) out[(size_t)(r * 12 + c) * nslots] = ok ? A[r][12 + c] : T(0);
+}
+
+
+template <typename T, int kTCX, int kTCY>
+struct PassSmem {
+  T w[3][2 * kTCY + 4][2 * kTCX + 4];
+  T vb[2][2 * kTCY + 4][2 * kTCX + 4];
+  uint8_t fl[2 * kTCY + 4][2 * kTCX + 4];
+  T cres[(2 * kTCY + 1) * (2 * kTCX + 1)][12];
+  T pres[(kTCY + 2) * (kTCX + 2)][9];
+  int8_t cvalid[(2 * kTCY + 1) * (2 * kTCX + 1)];
+  int8_t pvalid[(kTCY + 2) * (kTCX + 2)];
+};
+
+// Tile (bx, by) of the colour pass; all 4 kTCX kTCY threads of the block call it.
+template <typename T, int kTCX, int kTCY>
+__device__ __forceinline__ void vanka_pass_tile(const Grid& g, const Sten<T>& s, int colour,
+                                                const T* __restrict__ b, const T* __restrict__ xin,
+                                                const T* __restrict__ vb, const T* __restrict__ inv,
+                                                T omega, T* __restrict__ xout, int bx, int by,
+                                                PassSmem<T, kTCX, kTCY>& S) {
+  constexpr int kTileThreads = 4 * kTCX * kTCY;
+  constexpr int kSX = 2 * kTCX + 4;
+  constexpr int kCX = 2 * kTCX + 1, kCY = 2 * kTCY + 1;
+  constexpr int kPX = kTCX + 2, kPY = kTCY + 2;
+  constexpr int kSY = 2 * kTCY + 4;
+  const int cx = colour & 1, cy = colour >> 1;
+  const int sx = g.nx / 2 + 1, sy = g.ny / 2 + 1;
+  const int nslots = sx * sy;
+  const int nn = g.nn;
+  const int tx0 = bx * kTCX, ty0 = by * kTCY;
+  const int i0 = 2 * tx0 - cx, j0 = 2 * ty0 - cy;  // first node of the tile
+  const int t = threadIdx.x;
+  // ---- this thread's node (quad q, local node a) and its loads that do not
+  // depend on the defect: b, x_in and its three rows of the cell's inverse,
+  // issued first so that their latency overlaps the stencil work below
+  const int q = t >> 2, a = t & 3;
+  const int ti = tx0 + (q % kTCX), tj = ty0 + (q / kTCX);
+  const bool slot_ok = ti < sx && tj < sy;
+  const int slot = tj * sx + ti;
+  const int ci = 2 * ti - cx, cj = 2 * tj - cy;
+  const int i = ci + (a & 1), j = cj + (a >> 1);
+  const bool node_ok = slot_ok && i >= 0 && j >= 0 && i <= g.nx && j <= g.ny;
+  const bool cell_ok = slot_ok && ci >= 0 && cj >= 0 && ci < g.nx && cj < g.ny &&
+                       !g.solid[(cj < 0 ? 0 : cj) * g.nx + (ci < 0 ? 0 : ci)];
+  const int n = node_ok ? j * g.nnx + i : 0;
+  T xu = 0, xv = 0, xp = 0, bu0 = 0, bv0 = 0, bp0 = 0;
+  T iv[36];
+  if (node_ok) {
+    xu = xin[n], xv = xin[nn + n], xp = xin[2 * nn + n];
+    bu0 = b[n], bv0 = b[nn + n], bp0 = b[2 * nn + n];
+  }
+  if (node_ok && cell_ok) {
+    const T* row0 = inv + (size_t)colour * 144 * nslots + slot;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int k = 0; k < 12; ++k) iv[c * 12 + k] = row0[(size_t)((c * 4 + a) * 12 + k) * nslots];
+  }
+  // ---- stage nodes [i0-2, i0-2+kSX) x [j0-2, j0-2+kSY)
+  for (int e = t; e < kSX * kSY; e += kTileThreads) {
+    const int li = e % kSX, lj = e / kSX;
+    const int i = i0 - 2 + li, j = j0 - 2 + lj;
+    T wu = 0, wv = 0, wp = 0, bu = 0, bvv = 0;
+    uint8_t f = 0xFF;
+    if (i >= 0 && j >= 0 && i <= g.nx && j <= g.ny) {
+      const int n = j * g.nnx + i;
+      f = g.flags[n];
+      wu = (f & kVDir) ? T(0) : xin[n];
+      wv = (f & kVDir) ? T(0) : xin[nn + n];
+      wp = (f & kPFix) ? T(0) : xin[2 * nn + n];
+      bu = vb[n];
+      bvv = vb[nn + n];
+    }
+    S.w[0][lj][li] = wu;
+    S.w[1][lj][li] = wv;
+    S.w[2][lj][li] = wp;
+    S.vb[0][lj][li] = bu;
+    S.vb[1][lj][li] = bvv;
+    S.fl[lj][li] = f;
+  }
+  __syncthreads();
+  // ---- cells [i0-1, i0-1+kCX) x [j0-1, j0-1+kCY): 12 rows each
+  for (int e = t; e < kCX * kCY; e += kTileThreads) {
+    const int lc = e % kCX, lr = e / kCX;
+    const int ci = i0 - 1 + lc, cj = j0 - 1 + lr;
+    const bool ok = ci >= 0 && cj >= 0 && ci < g.nx && cj < g.ny && !g.solid[cj * g.nx + ci];
+    S.cvalid[e] = ok;
+    if (!ok) continue;
+    T wu[4], wv[4], wp[4], bu[4], bv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int li = lc + 1 + (a & 1), lj = lr + 1 + (a >> 1);  // staged coords of the node
+      wu[a] = S.w[0][lj][li];
+      wv[a] = S.w[1][lj][li];
+      wp[a] = S.w[2][lj][li];
+      bu[a] = S.vb[0][lj][li];
+      bv[a] = S.vb[1][lj][li];
+    }
+    T r[12];
+    cell_all_rows<T, false>(s, wu, wv, wp, bu, bv, r);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) S.cres[e][k] = r[k];
+  }
+  // ---- patches touching the tile: 9 LPS rows each
+  // patches touching the tile: from ceil((i0 - 2) / 2) (also for negative
+  // i0) to floor((i0 + 2 kTCX - 1) / 2), likewise in y
+  const int PI0 = (i0 - 1) >> 1, PJ0 = (j0 - 1) >> 1;
+  const int PI1 = (i0 + 2 * kTCX - 1) >> 1, PJ1 = (j0 + 2 * kTCY - 1) >> 1;
+  for (int e = t; e < kPX * kPY; e += kTileThreads) {
+    const int pi = PI0 + e % kPX, pj = PJ0 + e / kPX;
+    const bool ok = pi <= PI1 && pj <= PJ1 && pi >= 0 && pj >= 0 && pi < g.nx / 2 &&
+                    pj < g.ny / 2 && !g.solid[(2 * pj) * g.nx + 2 * pi];
+    S.pvalid[e] = ok;
+    if (!ok) continue;
+    T p[9];
+#pragma unroll
+    for (int m = 0; m < 9; ++m) {
+      const int li = 2 * pi + m % 3 - (i0 - 2), lj = 2 * pj + m / 3 - (j0 - 2);
+      p[m] = S.w[2][lj][li];
+    }
+#pragma unroll
+    for (int mn = 0; mn < 9; ++mn) {
+      T acc = 0;
+#pragma unroll
+      for (int m = 0; m < 9; ++m) acc += s.S9[mn * 9 + m] * p[m];
+      S.pres[e][mn] = acc;
+    }
+  }
+  __syncthreads();
+  T du = 0, dv = 0, dp = 0;
+  if (node_ok && cell_ok) {
+    T ru = 0, rv = 0, rp = 0;
+#pragma unroll
+    for (int dyy = 0; dyy < 2; ++dyy)
+#pragma unroll
+      for (int dxx = 0; dxx < 2; ++dxx) {
+        const int lc = i - 1 + dxx - (i0 - 1), lr = j - 1 + dyy - (j0 - 1);
+        const int e = lr * kCX + lc;
+        if (!S.cvalid[e]) continue;
+        const int al = (1 - dxx) + 2 * (1 - dyy);
+        ru += S.cres[e][al];
+        rv += S.cres[e][4 + al];
+        rp += S.cres[e][8 + al];
+      }
+#pragma unroll
+    for (int dJ = 0; dJ < 2; ++dJ) {
+      const int PJ = (j >> 1) - dJ;
+      if (j - 2 * PJ > 2) continue;
+#pragma unroll
+      for (int dI = 0; dI < 2; ++dI) {
+        const int PI = (i >> 1) - dI;
+        if (i - 2 * PI > 2) continue;
+        const int e = (PJ - PJ0) * kPX + (PI - PI0);
+        if (!S.pvalid[e]) continue;
+        rp += S.pres[e][(i - 2 * PI) + 3 * (j - 2 * PJ)];
+      }
+    }
+    const uint8_t f = S.fl[j - (j0 - 2)][i - (i0 - 2)];
+    du = bu0 - ((f & kVDir) ? xu : ru);
+    dv = bv0 - ((f & kVDir) ? xv : rv);
+    dp = bp0 - ((f & kPFix) ? xp : rp);
+  }
+  const int lane = t & 31, base = lane & ~3;
+  T d[12];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    d[k] = __shfl_sync(0xffffffffu, du, base + k);
+    d[4 + k] = __shfl_sync(0xffffffffu, dv, base + k);
+    d[8 + k] = __shfl_sync(0xffffffffu, dp, base + k);
+  }
+  if (!node_ok) return;
+  if (cell_ok) {
+    T acc[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      acc[c] = 0;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) acc[c] += iv[c * 12 + k] * d[k];
+    }
+    xout[n] = xu + omega * acc[0];
+    xout[nn + n] = xv + omega * acc[1];
+    xout[2 * nn + n] = xp + omega * acc[2];
+  } else {
+    xout[n] = xu;
+    xout[nn + n] = xv;
+    xout[2 * nn + n] = xp;
+  }
+}
+
+
+}  // namespace dnnmg

@@ -1,5 +1,5 @@
 // Per-thread bodies of the multigrid kernels, shared by the one-launch-per-
-// stage kernels and the persistent V-cycle kernel.
+// stage kernels, the persistent V-cycle kernel and the batched kernels.
 #pragma once
 #include "common.cuh"
 
@@ -156,6 +156,93 @@ __device__ __forceinline__ void prolong_add_node(const Grid& f, const Grid& c,
     if (fl & bit) continue;
     x[comp * f.nn + n] += interp_node<T, true>(c, xc + comp * c.nn, bit, i, j);
   }
+}
+
+// y = A'(vbar) w at node (i, j) on free DOFs, y = w on constrained DOFs.
+template <typename T>
+__device__ __forceinline__ void apply_node(const Grid& g, const Sten<T>& s, const T* __restrict__ w,
+                                           const T* __restrict__ vb, T* __restrict__ y, int i,
+                                           int j) {
+  const int n = j * g.nnx + i;
+  T ru, rv, rp;
+  node_rows<T, false, true>(g, s, i, j, w, vb, ru, rv, rp);
+  const uint8_t f = g.flags[n];
+  y[n] = (f & kVDir) ? w[n] : ru;
+  y[g.nn + n] = (f & kVDir) ? w[g.nn + n] : rv;
+  y[2 * g.nn + n] = (f & kPFix) ? w[2 * g.nn + n] : rp;
+}
+
+// r = f - A(x) at node (i, j) on free DOFs, 0 on constrained DOFs (FP64).
+__device__ __forceinline__ void residual64_node(const Grid& g, const Sten<double>& s,
+                                                const double* __restrict__ x,
+                                                const double* __restrict__ f,
+                                                double* __restrict__ r, int i, int j) {
+  const int n = j * g.nnx + i;
+  double ru, rv, rp;
+  node_rows<double, true, false>(g, s, i, j, x, nullptr, ru, rv, rp);
+  const uint8_t fl = g.flags[n];
+  const int nn = g.nn;
+  r[n] = (fl & kVDir) ? 0.0 : f[n] - ru;
+  r[nn + n] = (fl & kVDir) ? 0.0 : f[nn + n] - rv;
+  r[2 * nn + n] = (fl & kPFix) ? 0.0 : f[2 * nn + n] - rp;
+}
+
+// f = (1/k) (v_old, phi) at node (i, j) with the Q1 mass matrix
+// (h^2/36) [4 2 2 1] pattern; pressure rows 0.
+__device__ __forceinline__ void old_rhs64_node(const Grid& g, double inv_k,
+                                               const double* __restrict__ x,
+                                               double* __restrict__ f, int i, int j) {
+  const int n = j * g.nnx + i, nn = g.nn;
+  const double m = g.h * g.h / 36.0 * inv_k;
+  double fu = 0, fv = 0;
+  for (int cy = 0; cy < 2; ++cy)
+    for (int cx = 0; cx < 2; ++cx) {
+      const int ci = i - 1 + cx, cj = j - 1 + cy;
+      if (ci < 0 || cj < 0 || ci >= g.nx || cj >= g.ny || g.solid[cj * g.nx + ci]) continue;
+      const int ax = 1 - cx, ay = 1 - cy;
+      for (int b = 0; b < 4; ++b) {
+        const int bx = b & 1, by = b >> 1;
+        const double wgt = (ax == bx ? 2.0 : 1.0) * (ay == by ? 2.0 : 1.0);
+        const int nb = (cj + by) * g.nnx + ci + bx;
+        fu += wgt * x[nb];
+        fv += wgt * x[nn + nb];
+      }
+    }
+  f[n] = m * fu;
+  f[nn + n] = m * fv;
+  f[2 * nn + n] = 0.0;
+}
+
+// f -= coef * [nu (grad v, grad phi) + (v . grad v, phi)] on the velocity
+// rows of node (i, j): the explicit part of the theta-scheme (Eq. 5 with
+// weight 1 - theta).  sx holds nu K in E, the Gauss weight h^2/4 without
+// theta, and no pressure or LPS terms.
+__device__ __forceinline__ void explicit_sub64_node(const Grid& g, const Sten<double>& sx,
+                                                    double coef, const double* __restrict__ x,
+                                                    double* __restrict__ f, int i, int j) {
+  const int n = j * g.nnx + i;
+  double ru, rv, rp;
+  node_rows<double, true, false>(g, sx, i, j, x, nullptr, ru, rv, rp);
+  f[n] -= coef * ru;
+  f[g.nn + n] -= coef * rv;
+}
+
+// coarse (I, J) <- fine (2I, 2J) for ncomp fields
+template <typename T>
+__device__ __forceinline__ void inject_node(const Grid& f, const Grid& c, const T* __restrict__ xf,
+                                            T* __restrict__ xc, int ncomp, int I, int J) {
+  for (int comp = 0; comp < ncomp; ++comp)
+    xc[comp * c.nn + J * c.nnx + I] = xf[comp * f.nn + (2 * J) * f.nnx + 2 * I];
+}
+
+// unmasked bilinear prolongation of ncomp fields at fine node (i, j)
+__device__ __forceinline__ void prolong_state_node(const Grid& f, const Grid& c,
+                                                   const double* __restrict__ xc,
+                                                   double* __restrict__ xf, int ncomp, int i,
+                                                   int j) {
+  const int n = j * f.nnx + i;
+  for (int comp = 0; comp < ncomp; ++comp)
+    xf[comp * f.nn + n] = interp_node<double, false>(c, xc + comp * c.nn, 0, i, j);
 }
 
 // Band numbering of the coarsest level: DOF p = (i * nny + j) * 3 + c.

@@ -4,6 +4,7 @@
 #include <atomic>
 
 #include "kernels.h"
+#include "krylov_body.cuh"
 
 namespace dnnmg {
 
@@ -24,20 +25,6 @@ __global__ void fill_kernel(T* a, T v, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x)
     a[i] = v;
-}
-
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) sh[warp] = v;
-  __syncthreads();
-  double t = 0.0;
-  if (warp == 0) {
-    t = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-  }
-  return t;
 }
 
 // partials[i * gridDim.x + block] = sum over the block's chunk of V[i] . w
@@ -105,38 +92,15 @@ __global__ void combine_kernel(const T* __restrict__ Z, size_t ld, int k,
   }
 }
 
-// H is column-major (ldh rows).  hcol holds [h_0..h_j (first CGS pass),
-// h_0..h_j (second pass), ||w||^2].
 __global__ void givens_kernel(double* H, int ldh, double* cs, double* sn, double* g,
                               const double* hcol, int j, double* resid) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double* col = H + (size_t)j * ldh;
-  for (int i = 0; i <= j; ++i) col[i] = hcol[i] + hcol[j + 1 + i];
-  col[j + 1] = sqrt(fmax(hcol[2 * j + 2], 0.0));
-  for (int i = 0; i < j; ++i) {
-    const double t = cs[i] * col[i] + sn[i] * col[i + 1];
-    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
-    col[i] = t;
-  }
-  const double den = hypot(col[j], col[j + 1]);
-  const double c = den > 0 ? col[j] / den : 1.0, s = den > 0 ? col[j + 1] / den : 0.0;
-  cs[j] = c;
-  sn[j] = s;
-  col[j] = den;
-  col[j + 1] = 0.0;
-  g[j + 1] = -s * g[j];
-  g[j] = c * g[j];
-  *resid = fabs(g[j + 1]);
+  *resid = givens_column(H, ldh, cs, sn, g, hcol, j);
 }
 
 __global__ void backsolve_kernel(const double* H, int ldh, const double* g, int k, double* y) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  for (int i = k - 1; i >= 0; --i) {
-    double acc = g[i];
-    for (int c = i + 1; c < k; ++c) acc -= H[(size_t)c * ldh + i] * y[c];
-    const double d = H[(size_t)i * ldh + i];
-    y[i] = d != 0.0 ? acc / d : 0.0;
-  }
+  backsolve_small(H, ldh, g, k, y);
 }
 
 template <typename T>
@@ -161,6 +125,7 @@ namespace {
 std::atomic<unsigned long long> g_launches{0};
 }
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 unsigned long long launches() { return g_launches.load(std::memory_order_relaxed); }
 
 size_t dots_partials(size_t n, int k) { return (size_t)kDotBlocks * (k > 0 ? k : 1); }

@@ -90,6 +90,22 @@ def _declare(lib):
         "dnnmg_vcycle_split": ([P], ctypes.c_int),
         "dnnmg_gather_batch": ([P, P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int64, P, P],
                                ctypes.c_int),
+        "dnnmg_batch_setup": ([P, ctypes.c_int, P, P], ctypes.c_int),
+        "dnnmg_batch_destroy": ([P], ctypes.c_int),
+        "dnnmg_batch_last_error": ([P], ctypes.c_char_p),
+        "dnnmg_batch_size": ([P, P, P], ctypes.c_int),
+        "dnnmg_batch_layout": ([P, ctypes.c_int, P, P], ctypes.c_int),
+        "dnnmg_batch_get_state": ([P, ctypes.c_int, P], ctypes.c_int),
+        "dnnmg_batch_set_state": ([P, ctypes.c_int, P], ctypes.c_int),
+        "dnnmg_batch_linearize": ([P], ctypes.c_int),
+        "dnnmg_batch_vcycle": ([P, P, P], ctypes.c_int),
+        "dnnmg_batch_step": ([P, ctypes.c_int, P], ctypes.c_int),
+        "dnnmg_batch_set_weights": ([P, P], ctypes.c_int),
+        "dnnmg_batch_set_feature_stats": ([P, P, P], ctypes.c_int),
+        "dnnmg_batch_get_fine_velocity": ([P, ctypes.c_int, P], ctypes.c_int),
+        "dnnmg_batch_graphs": ([P, ctypes.c_int], ctypes.c_int),
+        "dnnmg_batch_profile": ([P, ctypes.c_int], ctypes.c_int),
+        "dnnmg_batch_profile_read": ([P, ctypes.c_int, ctypes.c_int, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -325,3 +341,105 @@ class Context:
         st = StepStats()
         self._check(self.lib.dnnmg_step(self.h, mode, ctypes.byref(st)), allow=(ERR_NOT_CONVERGED,))
         return st.as_dict()
+
+
+def level_nodes(level):
+    """Nodes (nx+1)(ny+1) of mesh level `level` of the channel."""
+    return (16 * 2 ** level + 1) * (4 * 2 ** level + 1)
+
+
+class Batch:
+    """Many independent problems stepped in lock-step (wraps dnnmg_batch).
+
+    cfgs: list of Config (see dnnmg_batch_setup for the fields that may differ).
+    """
+
+    def __init__(self, cfgs, stream=None):
+        self.lib = load()
+        self.cfgs = list(cfgs)
+        arr = (Config * len(self.cfgs))(*self.cfgs)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = c_void_p()
+        rc = self.lib.dnnmg_batch_setup(arr, len(self.cfgs), c_void_p(self.stream.cuda_stream),
+                                        ctypes.byref(h))
+        if rc != OK:
+            raise DnnmgError(rc, self.lib.dnnmg_batch_last_error(None).decode())
+        self.h = h
+        n, length = ctypes.c_int(), ctypes.c_int64()
+        self._check(self.lib.dnnmg_batch_size(self.h, ctypes.byref(n), ctypes.byref(length)))
+        self.n, self.length = n.value, length.value
+        self.vdtype = torch.float64 if self.cfgs[0].precision == FP64 else torch.float32
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dnnmg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, allow=()):
+        if rc != OK and rc not in allow:
+            raise DnnmgError(rc, self.lib.dnnmg_batch_last_error(self.h).decode())
+        return rc
+
+    def layout(self, inst):
+        """(finest solved level, offset in the concatenated vectors) of problem inst."""
+        lev, off = ctypes.c_int(), ctypes.c_int64()
+        self._check(self.lib.dnnmg_batch_layout(self.h, inst, ctypes.byref(lev), ctypes.byref(off)))
+        return lev.value, off.value
+
+    def get_state(self, inst):
+        lev, _ = self.layout(inst)
+        x = torch.empty(3 * level_nodes(lev), dtype=torch.float64, device="cuda")
+        self._check(self.lib.dnnmg_batch_get_state(self.h, inst, _ptr(x)))
+        return x
+
+    def set_state(self, inst, x):
+        self._check(self.lib.dnnmg_batch_set_state(self.h, inst, _ptr(x)))
+
+    def linearize(self):
+        self._check(self.lib.dnnmg_batch_linearize(self.h))
+
+    def vcycle(self, b, x=None):
+        """b, x: concatenated cuda vectors of `length` elements (batch precision)."""
+        x = torch.empty_like(b) if x is None else x
+        self._check(self.lib.dnnmg_batch_vcycle(self.h, _ptr(b), _ptr(x)))
+        return x
+
+    def step(self, mode=PLAIN):
+        """One time step of every problem; returns the list of per-problem stats."""
+        st = (StepStats * self.n)()
+        self._check(self.lib.dnnmg_batch_step(self.h, mode, st), allow=(ERR_NOT_CONVERGED,))
+        return [s.as_dict() for s in st]
+
+    def set_weights(self, w):
+        t = torch.as_tensor(w, dtype=torch.float32).contiguous().cpu()
+        self._check(self.lib.dnnmg_batch_set_weights(self.h, c_void_p(t.data_ptr())))
+
+    def set_feature_stats(self, mean, std):
+        m = torch.as_tensor(mean, dtype=torch.float32).contiguous().cpu()
+        s = torch.as_tensor(std, dtype=torch.float32).contiguous().cpu()
+        self._check(self.lib.dnnmg_batch_set_feature_stats(self.h, c_void_p(m.data_ptr()),
+                                                           c_void_p(s.data_ptr())))
+
+    def get_fine_velocity(self, inst):
+        lev, _ = self.layout(inst)
+        v = torch.empty(2 * level_nodes(lev + 1), dtype=torch.float64, device="cuda")
+        self._check(self.lib.dnnmg_batch_get_fine_velocity(self.h, inst, _ptr(v)))
+        return v
+
+    def graphs(self, on=True):
+        self._check(self.lib.dnnmg_batch_graphs(self.h, 1 if on else 0))
+
+    def profile(self, enable=True):
+        self._check(self.lib.dnnmg_batch_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self, stage, level=-1):
+        n, t = ctypes.c_int64(), ctypes.c_double()
+        self._check(self.lib.dnnmg_batch_profile_read(self.h, stage, level, ctypes.byref(n),
+                                                      ctypes.byref(t)))
+        return n.value, t.value

@@ -51,3 +51,27 @@ def test_default_config_and_argument_errors(lib):
         assert len(L.dnnmg_last_error(None)) > 0
     assert L.dnnmg_destroy(None) == dnnmg.OK
     assert L.dnnmg_step(None, 0, None) == dnnmg.ERR_ARG
+
+
+def test_batch_argument_errors(lib):
+    """Batch setup rejects bad inputs before touching the device: no configs,
+    an invalid configuration, and problems that differ in a shared field."""
+    from paper_2106_07687_gb300 import dnnmg
+    L = dnnmg.load()
+    out = ctypes.c_void_p(1)
+    assert L.dnnmg_batch_setup(None, 0, None, ctypes.byref(out)) == dnnmg.ERR_ARG
+    assert out.value is None
+    assert len(L.dnnmg_batch_last_error(None)) > 0
+    a = dnnmg.default_config()
+    b = dnnmg.default_config(nu=-1.0)
+    arr = (dnnmg.Config * 2)(a, b)
+    assert L.dnnmg_batch_setup(arr, 2, None, ctypes.byref(out)) == dnnmg.ERR_ARG
+    assert b"problem 1" in L.dnnmg_batch_last_error(None)
+    c = dnnmg.default_config(gmres_m=10, level_solve=4)
+    arr = (dnnmg.Config * 2)(a, c)
+    assert L.dnnmg_batch_setup(arr, 2, None, ctypes.byref(out)) == dnnmg.ERR_ARG
+    assert out.value is None
+    assert L.dnnmg_batch_destroy(None) == dnnmg.OK
+    assert L.dnnmg_batch_step(None, 0, None) == dnnmg.ERR_ARG
+    n, length = ctypes.c_int(), ctypes.c_int64()
+    assert L.dnnmg_batch_size(None, ctypes.byref(n), ctypes.byref(length)) == dnnmg.ERR_ARG
