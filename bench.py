@@ -209,7 +209,7 @@ def run_ours(args, rank, world):
         sctx.close()
     Xc, Yc = torch.cat(Xs).contiguous(), torch.cat(Ys).contiguous()
     del Xs, Ys
-    net_ctx.feature_stats(Xc)
+    feat_mean, feat_std = net_ctx.feature_stats(Xc)
     net_ctx.set_weights(synthetic.random_weights(77, net_ctx.num_params(), 0.05).astype(np.float32))
     rng = np.random.default_rng(3)
     idx_all = []
@@ -319,6 +319,10 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     t_e2e = (time.perf_counter() - t_e2e) / E
 
+    # ---- batched problems: 64 uneven channels, one launch per stage ---------
+    batched = run_batched(dn, torch, stream, flush, args, net_ctx.get_weights(), feat_mean,
+                          feat_std, rank)
+
     ms = times["dnnmg"]
     if world > 1:
         t = torch.tensor([ms], dtype=torch.float64, device="cuda")
@@ -379,11 +383,98 @@ def run_ours(args, rank, world):
                     "train_frac_bf16_sustained":
                         f_train * TRAIN_B * TRAIN_T / (train_ms * 1e-3) / 1e12 / bf16_sus,
                     "loss_first": losses[0], "loss_last": losses[-1]},
+        "batched": batched,
         "clocks": clk.summary(),
         "e2e": {"value": 1.0 / t_e2e, "unit": "time steps/s",
                 "h2d_bytes_per_step": 8 * ndof(L), "d2h_bytes_per_step": 8 * ndof(L)},
         "gpu_launches": int(launches),
     }
+
+
+BATCH_N, BATCH_SEED = 64, 5000
+
+
+def batch_problems(dn, mode_levels, precision):
+    """64 channels with seeded obstacles and nu in [0.005, 0.02]; finest
+    solved levels cycle through mode_levels (uneven sizes)."""
+    import numpy as np
+    import synthetic
+    rng = np.random.default_rng(BATCH_SEED)
+    cfgs = []
+    for p in range(BATCH_N):
+        ob = synthetic.obstacle_block(BATCH_SEED + p)
+        cfgs.append(dn.default_config(level_solve=mode_levels[p % len(mode_levels)],
+                                      precision=precision, nu=float(rng.uniform(0.005, 0.02)),
+                                      dt=DT, obstacle_i0=ob[0], obstacle_j0=ob[1]))
+    return cfgs
+
+
+def run_batched(dn, torch, stream, flush, args, weights, feat_mean, feat_std, rank):
+    """Batched engine on 64 uneven problems: DNN-MG steps (solve on levels
+    3-5, network on 4-6: finest grids 256x64 .. 1024x256) and plain MG steps
+    (levels 4-6), each a lock-step batch with one launch per stage; plain MG
+    also run problem by problem with single contexts for comparison."""
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    out = {}
+    K = max(2, min(args.steps, 4))
+    for name, levels, mode in (("dnnmg", (3, 4, 5), dn.NET), ("plain", (4, 5, 6), dn.PLAIN)):
+        cfgs = batch_problems(dn, levels, dn.MIXED)
+        B = dn.Batch(cfgs)
+        if mode == dn.NET:
+            B.set_weights(weights)
+            B.set_feature_stats(feat_mean, feat_std)
+        for _ in range(max(2, args.warmup)):
+            B.step(mode)
+        torch.cuda.synchronize()
+        l0 = dn.kernel_launches()
+        t = 0.0
+        its = []
+        for _ in range(K):
+            flush.zero_()
+            ev[0].record(stream)
+            st = B.step(mode)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            t += ev[0].elapsed_time(ev[1])
+            its.append(sum(s["gmres_its"] for s in st) / len(st))
+        launches = dn.kernel_launches() - l0
+        B.profile(True)
+        B.step(mode)
+        stage = {}
+        for sid, nm in enumerate(dn.STAGES):
+            n, tt = B.profile_read(sid)
+            if n:
+                stage[nm] = {"launches": n, "ms": round(tt, 3)}
+        B.profile(False)
+        dofs = sum(ndof(c.level_solve) for c in cfgs)
+        out[name] = {"problems": len(cfgs), "levels_solved": list(levels),
+                     "dofs_solved": dofs, "ms_per_step": t / K,
+                     "problem_steps_per_s": len(cfgs) * K / (t * 1e-3),
+                     "dof_steps_per_s": dofs * K / (t * 1e-3),
+                     "mean_gmres_its_per_problem": sum(its) / len(its),
+                     "launches_per_step": launches / K, "stage_ms_one_step": stage}
+        del B
+        torch.cuda.empty_cache()
+    # the same plain problems one by one (single contexts, one timed step each)
+    cfgs = batch_problems(dn, (4, 5, 6), dn.MIXED)
+    t = 0.0
+    for c in cfgs:
+        ctx = dn.Context(cfg=c)
+        ctx.step(dn.PLAIN)
+        ctx.step(dn.PLAIN)
+        torch.cuda.synchronize()
+        flush.zero_()
+        ev[0].record(stream)
+        ctx.step(dn.PLAIN)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        t += ev[0].elapsed_time(ev[1])
+        ctx.close()
+    out["plain_sequential_ms_per_step"] = t
+    out["plain_batched_speedup"] = t / out["plain"]["ms_per_step"]
+    out["workload"] = ("64 channels, seeded obstacle, nu uniform in [0.005, 0.02], dt=0.005, "
+                       "mixed FP32/FP64; finest levels cycle 256x64, 512x128, 1024x256")
+    return out
 
 
 def run_vcycles(args):

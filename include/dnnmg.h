@@ -86,10 +86,12 @@ typedef struct dnnmg_config {
   int32_t train_seq;       /* largest training sequence length T */
   int32_t coarse_refresh;  /* time steps between refactorisations of the coarse level (>= 1) */
   int32_t persistent_vcycle; /* levels <= this one run their part of a V-cycle as one
-                                cooperative launch; 0: none; -1: chosen by timing */
+                                persistent launch; 0: none; -1: chosen by timing */
   int32_t precond_lag;     /* 1: the multigrid preconditioner keeps the linearisation of a
                               step's first Newton iteration (the matvec is always current) */
-  int32_t reserved[2];
+  int32_t persistent_mode; /* that launch: 0 = cooperative grid, 1 = one thread-block
+                              cluster, -1 = chosen by timing */
+  int32_t reserved[1];
 } dnnmg_config;
 
 /* Per-step statistics returned by dnnmg_step(). */
@@ -355,9 +357,18 @@ int dnnmg_profile(dnnmg_ctx* ctx, int enable);
  * Synchronises the context's stream. */
 int dnnmg_profile_read(dnnmg_ctx* ctx, int stage, int level, int64_t* launches, double* ms);
 
-/* Level from which the V-cycle runs as one cooperative launch (0: none),
+/* Level from which the V-cycle runs as one persistent launch (0: none),
  * as configured or chosen by timing at the first linearisation; -1 on error. */
 int dnnmg_vcycle_split(const dnnmg_ctx* ctx);
+
+/* The autotuned plan of the V-cycle (valid after the first linearisation):
+ * the split level as above; the kind of persistent launch below it (0: one
+ * cooperative grid with grid-wide barriers, 1: one thread-block cluster of
+ * up to 16 blocks with cluster barriers); and the tile of colour cells per
+ * block of the colour pass on `level` (0: 16x4, 1: 8x4, 2: 8x8; -1 if the
+ * level is not in the hierarchy). */
+int dnnmg_vcycle_plan(const dnnmg_ctx* ctx, int level, int* split_level, int* split_mode,
+                      int* pass_shape);
 
 /* ------------------------------------------------------------------------
  * Batched problems

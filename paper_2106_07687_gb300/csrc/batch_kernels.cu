@@ -37,7 +37,7 @@ __device__ __forceinline__ const BLev<T>& lev_of(const BView<T>& v, int p, int k
 // ---------------------------------------------------------------- V-cycle
 
 template <typename T, int TCX, int TCY>
-__global__ void __launch_bounds__(4 * TCX * TCY)
+__global__ void __launch_bounds__(4 * TCX * TCY, pass_min_blocks<T>(4 * TCX * TCY))
     bpass_kernel(BView<T> v, int k, int colour, int in, int out, const T* __restrict__ topb,
                  T* __restrict__ topx, T omega, const int2* __restrict__ work,
                  const int* __restrict__ act) {

@@ -184,6 +184,7 @@ int dnnmg_default_config(dnnmg_config* c) {
   c->coarse_refresh = 8;
   c->persistent_vcycle = -1;
   c->precond_lag = 1;
+  c->persistent_mode = -1;
   return DNNMG_OK;
 }
 
@@ -307,6 +308,15 @@ uint64_t dnnmg_kernel_launches(void) { return dnnmg::launches(); }
 
 int dnnmg_vcycle_split(const dnnmg_ctx* ctx) {
   return ctx && ctx->solver ? ctx->solver->split_level() : -1;
+}
+
+int dnnmg_vcycle_plan(const dnnmg_ctx* ctx, int level, int* split_level, int* split_mode,
+                      int* pass_shape) {
+  if (!ctx || !ctx->solver || !split_level || !split_mode || !pass_shape) return DNNMG_ERR_ARG;
+  *split_level = ctx->solver->split_level();
+  *split_mode = ctx->solver->split_mode();
+  *pass_shape = ctx->solver->pass_shape(level);
+  return DNNMG_OK;
 }
 
 size_t dnnmg_num_params(const dnnmg_ctx* ctx) { return ctx ? ctx->nd.num_params() : 0; }

@@ -82,9 +82,14 @@ class Solver final : public SolverBase {
       cudaMemcpyAsync(dph_, all.data(), sizeof(Phase) * all.size(), cudaMemcpyHostToDevice, st_);
       cudaStreamSynchronize(st_);
       coarse_nd_ = 3 * lv_[0].g.nn;
-      vgrid_ = vcycle_grid<T>(coarse_nd_);
+      bool fits = true;
+      for (int k = 0; k <= K_; ++k) fits = fits && vcycle_fits(ph_n_[k], k + 1);
+      vgrid_ = fits ? vcycle_grid<T>(coarse_nd_) : 0;
+      cluster_ = fits ? vcycle_cluster_size<T>(coarse_nd_) : 0;
       split_ = cfg.persistent_vcycle > 0 ? cfg.persistent_vcycle : -1;  // -1: tune later
+      split_mode_ = cfg.persistent_mode >= 0 ? cfg.persistent_mode : (vgrid_ > 0 ? 0 : 1);
     }
+    shape_.assign(K_ + 1, 0);
     const double one = 1.0;
     cudaMemcpyAsync(one_, &one, sizeof(double), cudaMemcpyHostToDevice, st_);
     return c_->check("solver init");
@@ -124,7 +129,10 @@ class Solver final : public SolverBase {
     cudaStreamSynchronize(st_);
     std::memcpy(&status, c_->h_scalars, sizeof(int));
     linearized_ = true;
-    if (split_ == -1) tune_split();
+    if (!tuned_) {
+      tune_split();
+      tuned_ = true;
+    }
     if (status & 1) return c_->fail(DNNMG_ERR_NUMERICAL, "singular local Vanka matrix");
     if (status & 2) return c_->fail(DNNMG_ERR_NUMERICAL, "singular coarse-level matrix");
     return DNNMG_OK;
@@ -231,7 +239,8 @@ class Solver final : public SolverBase {
     for (int s = 0; s < sweeps; ++s)
       for (int colour = 0; colour < 4; ++colour) {
         const int p = c_->prof.begin(DNNMG_STAGE_VANKA_PASS, l.level, st_);
-        launch_vanka_pass<T>(l.g, l.s, colour, b, cur, l.vb, l.inv, (T)c_->cfg.omega, nxt, st_);
+        launch_vanka_pass<T>(l.g, l.s, colour, b, cur, l.vb, l.inv, (T)c_->cfg.omega, nxt, st_,
+                             shape_[k]);
         c_->prof.end(p, st_);
         T* t = cur;
         cur = nxt;
@@ -239,53 +248,94 @@ class Solver final : public SolverBase {
       }
   }
 
-  int split_level() const { return split_ > 0 ? split_ : 0; }
+  int split_level() const override { return split_ > 0 ? split_ : 0; }
+  int split_mode() const override { return split_mode_; }
+  int pass_shape(int level) const override {
+    const int k = level - lv_[0].level;
+    return k >= 0 && k <= K_ ? shape_[k] : -1;
+  }
 
-  // Time the top-level cycle with the persistent sub-cycle starting at each
-  // candidate level (0 = none) and keep the fastest (autotuner).
+  // Autotuner, run once at the first linearisation: (1) the tile shape of
+  // the colour pass on every level, by timing four passes per shape; (2) the
+  // level from which the cycle runs as one persistent launch and the kind of
+  // that launch (cooperative grid or single cluster), by timing whole cycles
+  // of the top level for every candidate (0 = one launch per stage).
   void tune_split() {
-    split_ = 0;
-    if (vgrid_ <= 0) return;
-    const int top = K_;
-    T* b = lv_[top].d;
-    T* x = lv_[top].x2 == nullptr ? nullptr : wsol_;
-    launch_fill<T>(b, T(0), 3 * (size_t)lv_[top].g.nn, st_);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    float best = 1e30f;
-    int best_s = 0;
     const bool prof_on = c_->prof.on();
     if (prof_on) c_->prof.enable(false);
-    for (int cand = lv_[top].level; cand >= 0; --cand) {
-      if (cand > 0 && cand < lv_[0].level + 1) continue;
-      split_ = cand;
-      cycle(top, b, x);  // warm-up
+    auto time_ms = [&](auto&& f, int reps) {
+      f();  // warm-up
       cudaEventRecord(e0, st_);
-      for (int r = 0; r < 3; ++r) cycle(top, b, x);
+      for (int r = 0; r < reps; ++r) f();
       cudaEventRecord(e1, st_);
       cudaEventSynchronize(e1);
       float ms = 0;
       cudaEventElapsedTime(&ms, e0, e1);
-      if (cudaGetLastError() != cudaSuccess || persistent_failed_) ms = 1e30f;
-      if (ms < best) best = ms, best_s = cand;
+      return cudaGetLastError() == cudaSuccess ? ms : 1e30f;
+    };
+    for (int k = 1; k <= K_; ++k) {
+      float best = 1e30f;
+      int best_s = 0;
+      for (int sh = 0; sh < kPassShapes; ++sh) {
+        shape_[k] = sh;
+        const float ms = time_ms([&] { smooth(k, lv_[k].d, lv_[k].x, 1); }, 3);
+        if (ms < best) best = ms, best_s = sh;
+      }
+      shape_[k] = best_s;
+    }
+    const int top = K_;
+    if (split_ == -1) {
+      split_ = 0;
+      T* b = lv_[top].d;
+      T* x = wsol_;
+      launch_fill<T>(b, T(0), 3 * (size_t)lv_[top].g.nn, st_);
+      float best = 1e30f;
+      int best_s = 0, best_m = 0;
+      for (int cand = lv_[top].level; cand >= 0; --cand) {
+        if (cand > 0 && cand < lv_[0].level + 1) continue;
+        for (int mode = 0; mode < 2; ++mode) {
+          if (cand == 0 && mode == 1) continue;
+          if (cand > 0 && c_->cfg.persistent_mode >= 0 && mode != c_->cfg.persistent_mode) continue;
+          if (cand > 0 && ((mode == 0 && vgrid_ <= 0) || (mode == 1 && cluster_ <= 0))) continue;
+          split_ = cand;
+          split_mode_ = mode;
+          persistent_failed_ = false;
+          float ms = time_ms([&] { cycle(top, b, x); }, 3);
+          if (persistent_failed_) ms = 1e30f;
+          if (ms < best) best = ms, best_s = cand, best_m = mode;
+        }
+      }
+      split_ = best_s;
+      split_mode_ = best_m;
+      persistent_failed_ = false;
     }
     if (prof_on) c_->prof.enable(true);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    split_ = best_s;
   }
 
   // One V(nu1, nu2) cycle on level k for A x = b with x = 0 on entry.  Levels
   // at or below split_ run their whole sub-cycle as one cooperative launch.
   void cycle(int k, const T* b, T* x) {
-    if (split_ > 0 && lv_[k].level <= split_ && vgrid_ > 0 && !persistent_failed_) {
-      int blocks = cdiv(4 * vanka_slots(lv_[k].g), 256);
-      blocks = blocks < 64 ? 64 : blocks;
-      blocks = blocks > vgrid_ ? vgrid_ : blocks;
+    if (split_ > 0 && lv_[k].level <= split_ && !persistent_failed_ &&
+        (split_mode_ == 0 ? vgrid_ > 0 : cluster_ > 0)) {
       const int p = c_->prof.begin(DNNMG_STAGE_VCYCLE, lv_[k].level, st_);
-      const int rc = launch_vcycle_persistent<T>(dlv_, dph_ + ph_off_[k], ph_n_[k], k, b, x, ainv_,
-                                                 (T)c_->cfg.omega, blocks, coarse_nd_, st_);
+      int rc;
+      if (split_mode_ == 0) {
+        // one block per colour-pass tile of the sub-cycle's top level
+        const Grid& gk = lv_[k].g;
+        int blocks = cdiv(gk.nx / 2 + 1, 16) * cdiv(gk.ny / 2 + 1, 4);
+        blocks = blocks < 64 ? 64 : blocks;
+        blocks = blocks > vgrid_ ? vgrid_ : blocks;
+        rc = launch_vcycle_persistent<T>(dlv_, dph_ + ph_off_[k], ph_n_[k], k, b, x, ainv_,
+                                         (T)c_->cfg.omega, blocks, coarse_nd_, st_);
+      } else {
+        rc = launch_vcycle_cluster<T>(dlv_, dph_ + ph_off_[k], ph_n_[k], k, b, x, ainv_,
+                                      (T)c_->cfg.omega, cluster_, coarse_nd_, st_);
+      }
       c_->prof.end(p, st_);
       if (rc == 0) return;
       persistent_failed_ = true;  // fall back to one launch per stage
@@ -331,8 +381,11 @@ class Solver final : public SolverBase {
   VLevel<T>* dlv_ = nullptr;
   Phase* dph_ = nullptr;
   std::vector<int> ph_off_, ph_n_;
-  int vgrid_ = 0, coarse_nd_ = 0;
-  int split_ = 0;  // levels <= split_ (> 0) run as one cooperative launch; -1: not tuned yet
+  int vgrid_ = 0, coarse_nd_ = 0, cluster_ = 0;
+  int split_ = 0;  // levels <= split_ (> 0) run as one persistent launch; -1: not tuned yet
+  int split_mode_ = 0;        // 0: cooperative grid, 1: single cluster
+  std::vector<int> shape_;    // colour-pass tile shape per level
+  bool tuned_ = false;
   bool persistent_failed_ = false;
 };
 
@@ -391,7 +444,7 @@ int check_config(const dnnmg_config& c, std::string& err) {
   if (c.precision != DNNMG_FP64 && c.precision != DNNMG_MIXED)
     return fail_msg(err, DNNMG_ERR_ARG, "unknown precision");
   if (c.gmres_m < 1 || c.gmres_m > 40 || c.gmres_maxit < 1 || c.newton_max < 1 || c.nu1 < 0 ||
-      c.nu2 < 0 || c.coarse_refresh < 1)
+      c.nu2 < 0 || c.coarse_refresh < 1 || c.persistent_mode < -1 || c.persistent_mode > 1)
     return fail_msg(err, DNNMG_ERR_ARG, "solver parameters out of range");
   return DNNMG_OK;
 }

@@ -125,8 +125,12 @@ class SolverBase {
   // FGMRES on the finest level: w64 += eps * A'^{-1} r64 (approximately)
   virtual int solve(const double* r64, double* x64, double eps, int* its) = 0;
   virtual int precision() const = 0;
-  // level from which the V-cycle runs as one cooperative launch (0: none)
+  // level from which the V-cycle runs as one persistent launch (0: none),
+  // the kind of that launch (0: cooperative grid, 1: single cluster), and
+  // the colour-pass tile shape chosen for a level
   virtual int split_level() const = 0;
+  virtual int split_mode() const = 0;
+  virtual int pass_shape(int level) const = 0;
 };
 
 std::unique_ptr<SolverBase> make_solver(struct ::dnnmg_ctx* ctx);

@@ -19,7 +19,7 @@ __global__ void __launch_bounds__(kSetupThreads)
 }
 
 template <typename T, int TCX, int TCY>
-__global__ void __launch_bounds__(4 * TCX * TCY)
+__global__ void __launch_bounds__(4 * TCX * TCY, pass_min_blocks<T>(4 * TCX * TCY))
     vanka_pass_tiled_kernel(Grid g, Sten<T> s, int colour, const T* __restrict__ b,
                             const T* __restrict__ xin, const T* __restrict__ vb,
                             const T* __restrict__ inv, T omega, T* __restrict__ xout) {

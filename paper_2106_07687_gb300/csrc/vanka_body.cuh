@@ -132,24 +132,37 @@ __device__ __forceinline__ void vanka_setup_cell(const Grid& g, const Sten<T>& s
 }
 
 
+// Resident blocks per SM the pass kernels ask the compiler for: FP32 passes
+// are held to 128 registers per thread so that 512 threads per SM fit.
+template <typename T>
+constexpr int pass_min_blocks(int threads) {
+  return sizeof(T) == 4 ? (512 / threads > 0 ? 512 / threads : 1) : 1;
+}
+
 template <typename T, int kTCX, int kTCY>
 struct PassSmem {
   T w[3][2 * kTCY + 4][2 * kTCX + 4];
   T vb[2][2 * kTCY + 4][2 * kTCX + 4];
   uint8_t fl[2 * kTCY + 4][2 * kTCX + 4];
+  uint8_t sol[2 * kTCY + 4][2 * kTCX + 4];  // solid flag of the cell whose lower-left node this is
   T cres[(2 * kTCY + 1) * (2 * kTCX + 1)][12];
   T pres[(kTCY + 2) * (kTCX + 2)][9];
   int8_t cvalid[(2 * kTCY + 1) * (2 * kTCX + 1)];
   int8_t pvalid[(kTCY + 2) * (kTCX + 2)];
 };
 
-// Tile (bx, by) of the colour pass; all 4 kTCX kTCY threads of the block call it.
+// Tile (bx, by) of the colour pass, computed by 4 kTCX kTCY consecutive
+// threads of the block (a block may hold several such groups, each with its
+// own S; every thread of the block must call this together because of the
+// block barriers).  A group with active = false takes part in the barriers
+// only and writes nothing.
 template <typename T, int kTCX, int kTCY>
 __device__ __forceinline__ void vanka_pass_tile(const Grid& g, const Sten<T>& s, int colour,
                                                 const T* __restrict__ b, const T* __restrict__ xin,
                                                 const T* __restrict__ vb, const T* __restrict__ inv,
                                                 T omega, T* __restrict__ xout, int bx, int by,
-                                                PassSmem<T, kTCX, kTCY>& S) {
+                                                PassSmem<T, kTCX, kTCY>& S, bool active = true) {
+  if (!active) bx = by = 0;
   constexpr int kTileThreads = 4 * kTCX * kTCY;
   constexpr int kSX = 2 * kTCX + 4;
   constexpr int kCX = 2 * kTCX + 1, kCY = 2 * kTCY + 1;
@@ -161,7 +174,7 @@ __device__ __forceinline__ void vanka_pass_tile(const Grid& g, const Sten<T>& s,
   const int nn = g.nn;
   const int tx0 = bx * kTCX, ty0 = by * kTCY;
   const int i0 = 2 * tx0 - cx, j0 = 2 * ty0 - cy;  // first node of the tile
-  const int t = threadIdx.x;
+  const int t = threadIdx.x % kTileThreads;
   // ---- this thread's node (quad q, local node a) and its loads that do not
   // depend on the defect: b, x_in and its three rows of the cell's inverse,
   // issued first so that their latency overlaps the stencil work below
@@ -172,50 +185,56 @@ __device__ __forceinline__ void vanka_pass_tile(const Grid& g, const Sten<T>& s,
   const int ci = 2 * ti - cx, cj = 2 * tj - cy;
   const int i = ci + (a & 1), j = cj + (a >> 1);
   const bool node_ok = slot_ok && i >= 0 && j >= 0 && i <= g.nx && j <= g.ny;
-  const bool cell_ok = slot_ok && ci >= 0 && cj >= 0 && ci < g.nx && cj < g.ny &&
-                       !g.solid[(cj < 0 ? 0 : cj) * g.nx + (ci < 0 ? 0 : ci)];
   const int n = node_ok ? j * g.nnx + i : 0;
+  // every global load of the tile is issued before the first barrier, none
+  // depends on another: the thread's b, x_in and three inverse rows (read
+  // even for a solid cell, whose rows are then not used), and the staged
+  // nodes' flags, iterate, vbar and cell solid flags
   T xu = 0, xv = 0, xp = 0, bu0 = 0, bv0 = 0, bp0 = 0;
   T iv[36];
   if (node_ok) {
     xu = xin[n], xv = xin[nn + n], xp = xin[2 * nn + n];
     bu0 = b[n], bv0 = b[nn + n], bp0 = b[2 * nn + n];
-  }
-  if (node_ok && cell_ok) {
     const T* row0 = inv + (size_t)colour * 144 * nslots + slot;
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
       for (int k = 0; k < 12; ++k) iv[c * 12 + k] = row0[(size_t)((c * 4 + a) * 12 + k) * nslots];
   }
-  // ---- stage nodes [i0-2, i0-2+kSX) x [j0-2, j0-2+kSY)
+  // ---- stage nodes [i0-2, i0-2+kSX) x [j0-2, j0-2+kSY), and the solid flag
+  // of the cell whose lower-left node each one is
   for (int e = t; e < kSX * kSY; e += kTileThreads) {
     const int li = e % kSX, lj = e / kSX;
     const int i = i0 - 2 + li, j = j0 - 2 + lj;
-    T wu = 0, wv = 0, wp = 0, bu = 0, bvv = 0;
-    uint8_t f = 0xFF;
+    T xu1 = 0, xv1 = 0, xp1 = 0, bu = 0, bvv = 0;
+    uint8_t f = 0xFF, so = 1;
     if (i >= 0 && j >= 0 && i <= g.nx && j <= g.ny) {
       const int n = j * g.nnx + i;
       f = g.flags[n];
-      wu = (f & kVDir) ? T(0) : xin[n];
-      wv = (f & kVDir) ? T(0) : xin[nn + n];
-      wp = (f & kPFix) ? T(0) : xin[2 * nn + n];
+      xu1 = xin[n];
+      xv1 = xin[nn + n];
+      xp1 = xin[2 * nn + n];
       bu = vb[n];
       bvv = vb[nn + n];
+      if (i < g.nx && j < g.ny) so = g.solid[j * g.nx + i];
     }
-    S.w[0][lj][li] = wu;
-    S.w[1][lj][li] = wv;
-    S.w[2][lj][li] = wp;
+    S.w[0][lj][li] = (f & kVDir) ? T(0) : xu1;
+    S.w[1][lj][li] = (f & kVDir) ? T(0) : xv1;
+    S.w[2][lj][li] = (f & kPFix) ? T(0) : xp1;
     S.vb[0][lj][li] = bu;
     S.vb[1][lj][li] = bvv;
     S.fl[lj][li] = f;
+    S.sol[lj][li] = so;
   }
   __syncthreads();
+  // own cell (ci, cj) sits at staged index (ci - i0 + 2, cj - j0 + 2)
+  const bool cell_ok = slot_ok && ci >= 0 && cj >= 0 && ci < g.nx && cj < g.ny &&
+                       !S.sol[cj - j0 + 2][ci - i0 + 2];
   // ---- cells [i0-1, i0-1+kCX) x [j0-1, j0-1+kCY): 12 rows each
   for (int e = t; e < kCX * kCY; e += kTileThreads) {
     const int lc = e % kCX, lr = e / kCX;
     const int ci = i0 - 1 + lc, cj = j0 - 1 + lr;
-    const bool ok = ci >= 0 && cj >= 0 && ci < g.nx && cj < g.ny && !g.solid[cj * g.nx + ci];
+    const bool ok = ci >= 0 && cj >= 0 && ci < g.nx && cj < g.ny && !S.sol[lr + 1][lc + 1];
     S.cvalid[e] = ok;
     if (!ok) continue;
     T wu[4], wv[4], wp[4], bu[4], bv[4];
@@ -241,7 +260,7 @@ __device__ __forceinline__ void vanka_pass_tile(const Grid& g, const Sten<T>& s,
   for (int e = t; e < kPX * kPY; e += kTileThreads) {
     const int pi = PI0 + e % kPX, pj = PJ0 + e / kPX;
     const bool ok = pi <= PI1 && pj <= PJ1 && pi >= 0 && pj >= 0 && pi < g.nx / 2 &&
-                    pj < g.ny / 2 && !g.solid[(2 * pj) * g.nx + 2 * pi];
+                    pj < g.ny / 2 && !S.sol[2 * pj - j0 + 2][2 * pi - i0 + 2];
     S.pvalid[e] = ok;
     if (!ok) continue;
     T p[9];
@@ -300,7 +319,7 @@ __device__ __forceinline__ void vanka_pass_tile(const Grid& g, const Sten<T>& s,
     d[4 + k] = __shfl_sync(0xffffffffu, dv, base + k);
     d[8 + k] = __shfl_sync(0xffffffffu, dp, base + k);
   }
-  if (!node_ok) return;
+  if (!node_ok || !active) return;
   if (cell_ok) {
     T acc[3];
 #pragma unroll

@@ -25,9 +25,21 @@ struct Phase {
 
 // phase list of one V(nu1, nu2) cycle with top level `top`, x zeroed first
 std::vector<Phase> vcycle_phases(int top, int nu1, int nu2);
+// whether a launch of nphases phases over nlevels levels fits the kernels'
+// shared-memory tables
+bool vcycle_fits(int nphases, int nlevels);
 // co-resident grid size for the cooperative launch (0 if not available)
 template <typename T>
 int vcycle_grid(int coarse_nd);
+// blocks of the largest single-cluster launch that can be resident (16 or
+// 8; 0 if none)
+template <typename T>
+int vcycle_cluster_size(int coarse_nd);
+// the same cycle as one thread-block cluster of `cluster` blocks; 0 on success
+template <typename T>
+int launch_vcycle_cluster(const VLevel<T>* lv, const Phase* ph, int nph, int top, const T* topb,
+                          T* topx, const double* Ainv, T omega, int cluster, int coarse_nd,
+                          cudaStream_t st);
 // returns 0 on success
 template <typename T>
 int launch_vcycle_persistent(const VLevel<T>* lv, const Phase* ph, int nph, int top, const T* topb,

@@ -31,7 +31,8 @@ class Config(ctypes.Structure):
                 ("gmres_maxit", c_int32), ("nu1", c_int32), ("nu2", c_int32), ("hidden", c_int32),
                 ("gru_layers", c_int32), ("mlp_width", c_int32), ("fallback_newton_its", c_int32),
                 ("train_batch", c_int32), ("train_seq", c_int32), ("coarse_refresh", c_int32),
-                ("persistent_vcycle", c_int32), ("precond_lag", c_int32), ("reserved", c_int32 * 2)]
+                ("persistent_vcycle", c_int32), ("precond_lag", c_int32),
+                ("persistent_mode", c_int32), ("reserved", c_int32 * 1)]
 
 
 class StepStats(ctypes.Structure):
@@ -88,6 +89,7 @@ def _declare(lib):
         "dnnmg_profile_read": ([P, ctypes.c_int, ctypes.c_int, P, P], ctypes.c_int),
         "dnnmg_kernel_launches": ([], ctypes.c_uint64),
         "dnnmg_vcycle_split": ([P], ctypes.c_int),
+        "dnnmg_vcycle_plan": ([P, ctypes.c_int, P, P, P], ctypes.c_int),
         "dnnmg_gather_batch": ([P, P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int64, P, P],
                                ctypes.c_int),
         "dnnmg_batch_setup": ([P, ctypes.c_int, P, P], ctypes.c_int),
@@ -327,6 +329,16 @@ class Context:
 
     def vcycle_split(self):
         return int(self.lib.dnnmg_vcycle_split(self.h))
+
+    def vcycle_plan(self):
+        """{'split_level', 'split_mode', 'pass_shapes': {level: shape}} chosen by the autotuner."""
+        sl, sm, sh = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        shapes = {}
+        for lev in range(1, self.cfg.level_solve + 1):
+            self._check(self.lib.dnnmg_vcycle_plan(self.h, lev, ctypes.byref(sl), ctypes.byref(sm),
+                                                   ctypes.byref(sh)))
+            shapes[lev] = sh.value
+        return {"split_level": sl.value, "split_mode": sm.value, "pass_shapes": shapes}
 
     def profile(self, enable=True):
         self._check(self.lib.dnnmg_profile(self.h, 1 if enable else 0))

@@ -93,3 +93,28 @@ def test_plain_steps_match_oracle(precision, theta):
         xg = ctx.get_state().cpu().numpy()
         assert st["res_final"] <= 1e-12
         assert rel(xg, x) < (1e-10 if precision == 0 else 1e-4), (n, rel(xg, x), st)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-4)])
+@pytest.mark.parametrize("split,mode", [(3, 0), (3, 1), (2, 1), (4, 1)])
+def test_persistent_vcycle_kinds_match_oracle(precision, tol, split, mode):
+    """The levels at or below `split` run as one persistent launch: a
+    cooperative grid (mode 0) or a single thread-block cluster with cluster
+    barriers between phases (mode 1); 256x64 channel (level 4)."""
+    dn = lib()
+    L, obstacle, seed = 4, synthetic.obstacle_block(1003), 23
+    prm = fem.Params(nu=0.01, dt=0.01)
+    ctx = _ctx(dn, L, precision, obstacle, prm.nu, prm.dt, persistent_vcycle=split,
+               persistent_mode=mode)
+    levels = mesh.hierarchy(L, obstacle=obstacle)
+    lev = levels[-1]
+    x = seeded_state(lev, seed)
+    ctx.linearize(torch.from_numpy(x).cuda())
+    plan = ctx.vcycle_plan()
+    assert plan["split_level"] == split and plan["split_mode"] == mode, plan
+    b = synthetic.random_vector(seed + 50, lev.ndof)
+    b[lev.cons] = 0.0
+    xg = ctx.vcycle(L, torch.from_numpy(b).to(ctx.vdtype).cuda()).double().cpu().numpy()
+    H = mg.Hierarchy(levels, x, prm)
+    xr = mg.vcycle(H, len(levels) - 1, b)
+    assert rel(xg, xr) < tol, rel(xg, xr)
