@@ -289,6 +289,17 @@ __global__ void __launch_bounds__(kLUThreads)
   band_lu_block(C.g, ab, reinterpret_cast<int*>(ab + bandsz), status + p, win);
 }
 
+// the work area of a problem: band, pivots (n ints in n doubles), 1 / U(k, k)
+template <typename T>
+__global__ void brecip_kernel(BView<T> v, double* __restrict__ cwork, long long cstride,
+                              long long bandsz, const int* __restrict__ act) {
+  const int p = blockIdx.y;
+  if (masked(act, p)) return;
+  const BLev<T> C = lev_of(v, p, 1);
+  double* ab = cwork + (size_t)p * cstride;
+  band_diag_recip(C.g, ab, ab + bandsz + 3 * C.g.nn, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(32 * kInvWarps)
     binverse_kernel(BView<T> v, const double* __restrict__ cwork, long long cstride,
@@ -296,12 +307,11 @@ __global__ void __launch_bounds__(32 * kInvWarps)
                     const int* __restrict__ act) {
   const int p = blockIdx.y;
   if (masked(act, p)) return;
-  extern __shared__ double sm[];
+  extern __shared__ __align__(16) double sm[];
   const BLev<T> C = lev_of(v, p, 1);
   const double* ab = cwork + (size_t)p * cstride;
-  const int warp = threadIdx.x >> 5;
-  band_inverse_col(C.g, ab, reinterpret_cast<const int*>(ab + bandsz), Ainv + (size_t)p * astride,
-                   blockIdx.x * kInvWarps + warp, sm + (size_t)warp * 3 * C.g.nn);
+  band_inverse_block(C.g, ab, reinterpret_cast<const int*>(ab + bandsz), ab + bandsz + 3 * C.g.nn,
+                     Ainv + (size_t)p * astride, blockIdx.x * kInvWarps, sm);
 }
 
 // -------------------------------------------------------------- vectors
@@ -650,9 +660,15 @@ void bk_coarse_factor(const BView<T>& v, int nprob, int n1, double* cwork, long 
   note_launch();
   blu_kernel<T><<<nprob, kLUThreads, win_bytes, st>>>(v, cwork, cstride, bandsz, status, act);
   note_launch();
-  binverse_kernel<T><<<dim3(cdiv(n1, kInvWarps), nprob), 32 * kInvWarps,
-                       sizeof(double) * n1 * kInvWarps, st>>>(v, cwork, cstride, bandsz, Ainv,
-                                                              astride, act);
+  brecip_kernel<T><<<dim3(cdiv(n1, 128), nprob), 128, 0, st>>>(v, cwork, cstride, bandsz, act);
+  const size_t ism = sizeof(double) * inv_block_smem_doubles(n1);
+  static const bool inv_attr =
+      cudaFuncSetAttribute(binverse_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)ism) == cudaSuccess;
+  (void)inv_attr;
+  note_launch();
+  binverse_kernel<T><<<dim3(cdiv(n1, kInvWarps), nprob), 32 * kInvWarps, ism, st>>>(
+      v, cwork, cstride, bandsz, Ainv, astride, act);
 }
 
 template <typename T>

@@ -21,14 +21,16 @@ __global__ void __launch_bounds__(kLUThreads)
   band_lu_block(g, ab, piv, status, win);
 }
 
-// Column `col` of the inverse: solve L U x = P e_col, one warp per column.
+__global__ void diag_recip_kernel(Grid g, const double* __restrict__ ab, double* __restrict__ rd) {
+  band_diag_recip(g, ab, rd, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// Columns [kInvWarps * block, +kInvWarps) of the inverse.
 __global__ void __launch_bounds__(32 * kInvWarps)
     band_inverse_kernel(Grid g, const double* __restrict__ ab, const int* __restrict__ piv,
-                        double* __restrict__ Ainv) {
-  extern __shared__ double sm[];
-  const int warp = threadIdx.x >> 5;
-  band_inverse_col(g, ab, piv, Ainv, blockIdx.x * kInvWarps + warp,
-                   sm + (size_t)warp * 3 * g.nn);
+                        const double* __restrict__ rd, double* __restrict__ Ainv) {
+  extern __shared__ __align__(16) double sm[];
+  band_inverse_block(g, ab, piv, rd, Ainv, blockIdx.x * kInvWarps, sm);
 }
 
 // x = Ainv b with the band numbering on both sides; one warp per row.
@@ -111,13 +113,15 @@ void launch_coarse_lu_solve(const Grid& g, const double* band, const int* piv, c
 
 bool coarse_supported(const Grid& g) {
   const Band bd = band_of(g);
-  return bd.kl + 1 <= kWin && sizeof(double) * kWin * bd.W <= 200 * 1024 &&
-         sizeof(double) * bd.n * kInvWarps <= 48 * 1024;
+  return bd.kl + 2 <= kWin && bd.W <= kLUThreads && sizeof(double) * kWin * bd.W <= 200 * 1024 &&
+         bd.kl <= kInvLW && bd.ku + bd.kl + 1 <= kInvUW &&
+         sizeof(double) * inv_block_smem_doubles(bd.n) <= 200 * 1024;
 }
 
 size_t coarse_work_doubles(const Grid& g) {
   const Band bd = band_of(g);
-  return (size_t)bd.n * bd.W + (size_t)bd.n;  // band + pivots (as ints, over-allocated)
+  // band + pivots (as ints, over-allocated) + reciprocals of the U diagonal
+  return (size_t)bd.n * bd.W + (size_t)bd.n + (size_t)bd.n;
 }
 
 void launch_coarse_factor(const Grid& g, const Sten<double>& s, const double* vb, double* work,
@@ -132,9 +136,16 @@ void launch_coarse_factor(const Grid& g, const Sten<double>& s, const double* vb
                        (int)win_bytes);
   note_launch();
   band_lu_kernel<<<1, kLUThreads, win_bytes, st>>>(g, ab, piv, status);
-  const size_t smem = sizeof(double) * bd.n * kInvWarps;
+  double* rd = work + (size_t)bd.n * bd.W + bd.n;
   note_launch();
-  band_inverse_kernel<<<cdiv(bd.n, kInvWarps), 32 * kInvWarps, smem, st>>>(g, ab, piv, Ainv);
+  diag_recip_kernel<<<cdiv(bd.n, 128), 128, 0, st>>>(g, ab, rd);
+  const size_t smem = sizeof(double) * inv_block_smem_doubles(bd.n);
+  static const bool inv_attr =
+      cudaFuncSetAttribute(band_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) == cudaSuccess;
+  (void)inv_attr;
+  note_launch();
+  band_inverse_kernel<<<cdiv(bd.n, kInvWarps), 32 * kInvWarps, smem, st>>>(g, ab, piv, rd, Ainv);
 }
 
 template <typename T>

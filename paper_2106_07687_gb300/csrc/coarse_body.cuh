@@ -108,6 +108,7 @@ __device__ __forceinline__ void band_lu_block(const Grid& g, double* __restrict_
                                               int* __restrict__ piv, int* status, double* win) {
   const Band bd = band_of(g);
   __shared__ int s_p;
+  __shared__ double s_d, s_akk;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   auto W = [&](int r, int col) -> double& {
     return win[(size_t)(r % kWin) * bd.W + (col - r + bd.kl)];
@@ -119,9 +120,17 @@ __device__ __forceinline__ void band_lu_block(const Grid& g, double* __restrict_
   __syncthreads();
   for (int k = 0; k < bd.n; ++k) {
     const int rmax = min(bd.n - 1, k + bd.kl);
-    double best = -1.0;
-    int bi = k;
+    const int cmax = min(bd.n - 1, k + bd.ku + bd.kl);
+    // row k + kl + 1 enters the window at the end of this step (into the
+    // slot row k - 1 has left); its global load is issued first so that
+    // its latency overlaps the elimination (rows beyond k + kl are untouched)
+    const int rn = k + bd.kl + 1;
+    const bool pf_on = rn < bd.n && tid < bd.W;
+    const double pf = pf_on ? ab[(size_t)rn * bd.W + tid] : 0.0;
+    // pivot: largest |entry| of column k in rows k..rmax (lowest row on ties)
     if (warp == 0) {
+      double best = -1.0;
+      int bi = k;
       for (int r = k + lane; r <= rmax; r += 32) {
         const double v = fabs(W(r, k));
         if (v > best) best = v, bi = r;
@@ -133,23 +142,30 @@ __device__ __forceinline__ void band_lu_block(const Grid& g, double* __restrict_
       }
       if (lane == 0) {
         s_p = bi;
+        s_d = W(bi, k);
+        s_akk = W(k, k);
         piv[k] = bi;
         if (!(best > 0.0)) atomicOr(status, 2);
       }
     }
     __syncthreads();
     const int p = s_p;
-    const int cmax = min(bd.n - 1, k + bd.ku + bd.kl);
+    const double d = s_d;
+    const double id = d != 0.0 ? 1.0 / d : 0.0;
+    // interchange rows k and p right of column k, and form column k of L
+    // (row p of it receives the old diagonal entry)
     if (p != k)
-      for (int col = k + tid; col <= cmax; col += kLUThreads) {
+      for (int col = k + 1 + tid; col <= cmax; col += kLUThreads) {
         const double t = W(k, col);
         W(k, col) = W(p, col);
         W(p, col) = t;
       }
-    __syncthreads();
-    const double d = W(k, k);
-    const double id = d != 0.0 ? 1.0 / d : 0.0;
-    for (int r = k + 1 + tid; r <= rmax; r += kLUThreads) W(r, k) *= id;
+    for (int r = k + tid; r <= rmax; r += kLUThreads) {
+      if (r == k)
+        W(k, k) = d;
+      else
+        W(r, k) = (r == p ? s_akk : W(r, k)) * id;
+    }
     __syncthreads();
     const int nr = rmax - k, nc = cmax - k;
     for (int e = tid; e < nr * nc; e += kLUThreads) {
@@ -157,54 +173,136 @@ __device__ __forceinline__ void band_lu_block(const Grid& g, double* __restrict_
       W(r, col) -= W(r, k) * W(k, col);
     }
     __syncthreads();
-    // row k is final: write it back; row k + kl + 1 enters the window
+    // row k is final: write it back; the prefetched row takes its slot
     for (int e = tid; e < bd.W; e += kLUThreads)
       ab[(size_t)k * bd.W + e] = win[(size_t)(k % kWin) * bd.W + e];
-    __syncthreads();
-    const int rn = k + bd.kl + 1;
-    if (rn < bd.n)
-      for (int e = tid; e < bd.W; e += kLUThreads)
-        win[(size_t)(rn % kWin) * bd.W + e] = ab[(size_t)rn * bd.W + e];
+    if (pf_on) win[(size_t)(rn % kWin) * bd.W + tid] = pf;
     __syncthreads();
   }
 }
 
-// Column `col` of the inverse: solve L U x = P e_col, one warp per column.
-// Called by one whole warp; x is that warp's n doubles of shared memory.
-constexpr int kInvWarps = 4;
-__device__ __forceinline__ void band_inverse_col(const Grid& g, const double* __restrict__ ab,
-                                                 const int* __restrict__ piv,
-                                                 double* __restrict__ Ainv, int col, double* x) {
+// Columns [col0, col0 + kInvWarps) of the inverse: solve L U x = P e_col,
+// one warp per column, the warps of the block in step.  The factor entries
+// that step k needs (column k of L with the pivot, then row k of U) are
+// shared by all columns: the block streams them into a ring of kInvStages
+// shared-memory slots with asynchronous copies issued kInvStages - 1 steps
+// ahead, so no step waits on a global load.  All threads of the block call
+// it; sm holds inv_block_smem_doubles(n) doubles.
+constexpr int kInvWarps = 6;    // columns per block: 149 blocks cover the 891 columns
+constexpr int kInvStages = 8;
+constexpr int kInvLW = 64;   // >= kl: entries of one L column in a slot
+constexpr int kInvUW = 192;  // >= ku + kl + 1: entries of one U row in a slot
+
+__host__ __device__ inline size_t inv_block_smem_doubles(int n) {
+  return (size_t)kInvWarps * n + (size_t)kInvStages * (kInvLW + kInvUW + 1);
+}
+
+// rd[k] = 1 / U(k, k) of the factored band (one thread per row)
+__device__ __forceinline__ void band_diag_recip(const Grid& g, const double* __restrict__ ab,
+                                                double* __restrict__ rd, int k) {
   const Band bd = band_of(g);
-  const int lane = threadIdx.x & 31;
-  if (col >= bd.n) return;
-  for (int r = lane; r < bd.n; r += 32) x[r] = (r == col) ? 1.0 : 0.0;
-  __syncwarp();
-  for (int k = 0; k < bd.n; ++k) {
-    const int p = piv[k];
-    if (lane == 0 && p != k) {
-      const double t = x[k];
-      x[k] = x[p];
-      x[p] = t;
+  if (k < bd.n) rd[k] = 1.0 / ab[(size_t)k * bd.W + bd.kl];
+}
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void band_inverse_block(const Grid& g, const double* __restrict__ ab,
+                                                   const int* __restrict__ piv,
+                                                   const double* __restrict__ rd,
+                                                   double* __restrict__ Ainv, int col0, double* sm) {
+  const Band bd = band_of(g);
+  const int n = bd.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nt = blockDim.x;
+  double* xs = sm;                                   // [kInvWarps][n]
+  double* Lb = sm + (size_t)kInvWarps * n;           // [kInvStages][kInvLW]
+  double* Ub = Lb + (size_t)kInvStages * kInvLW;     // [kInvStages][kInvUW]
+  int* pb = reinterpret_cast<int*>(Ub + (size_t)kInvStages * kInvUW);  // [kInvStages]
+  const int col = col0 + warp;
+  double* x = xs + (size_t)warp * n;
+  // stage s of the forward sweep: L(s+1 .. s+kl, s) and piv[s]
+  auto issue_fwd = [&](int s) {
+    if (s < n) {
+      const int m = min(bd.kl, n - 1 - s);
+      for (int t = tid; t < m; t += nt)
+        cp_async8(Lb + (size_t)(s % kInvStages) * kInvLW + t,
+                  ab + (size_t)(s + 1 + t) * bd.W + (bd.kl - 1 - t));
+      if (tid == nt - 1) cp_async4(pb + s % kInvStages, piv + s);
     }
-    __syncwarp();
-    const double xk = x[k];
-    if (xk != 0.0) {
-      const int rmax = min(bd.n - 1, k + bd.kl);
-      for (int r = k + 1 + lane; r <= rmax; r += 32) x[r] -= AB(const_cast<double*>(ab), bd, r, k) * xk;
+    cp_async_commit();
+  };
+  // stage s of the backward sweep (row k = n - 1 - s): 1 / U(k, k) in slot
+  // entry 0, U(k, k+1 .. cmax) in entries 1..
+  auto issue_bwd = [&](int s) {
+    if (s < n) {
+      const int k = n - 1 - s;
+      const int m = min(bd.ku + bd.kl, n - 1 - k) + 1;
+      double* slot = Ub + (size_t)(s % kInvStages) * kInvUW;
+      for (int t = tid; t < m; t += nt)
+        cp_async8(slot + t, t == 0 ? rd + k : ab + (size_t)k * bd.W + bd.kl + t);
     }
-    __syncwarp();
+    cp_async_commit();
+  };
+  if (col < n)
+    for (int r = lane; r < n; r += 32) x[r] = (r == col) ? 1.0 : 0.0;
+  for (int s = 0; s < kInvStages - 1; ++s) issue_fwd(s);
+  for (int k = 0; k < n; ++k) {
+    cp_async_wait<kInvStages - 2>();  // stage k has landed (this thread's copies)
+    __syncthreads();                   // ... everybody's; slot (k - 1) % S is free
+    issue_fwd(k + kInvStages - 1);
+    if (col < n) {
+      const int p = pb[k % kInvStages];
+      if (lane == 0 && p != k) {
+        const double t = x[k];
+        x[k] = x[p];
+        x[p] = t;
+      }
+      __syncwarp();
+      const double xk = x[k];
+      if (xk != 0.0) {
+        const double* Lk = Lb + (size_t)(k % kInvStages) * kInvLW;
+        const int rmax = min(n - 1, k + bd.kl);
+        for (int r = k + 1 + lane; r <= rmax; r += 32) x[r] -= Lk[r - k - 1] * xk;
+      }
+      __syncwarp();
+    }
   }
-  for (int k = bd.n - 1; k >= 0; --k) {
-    const int cmax = min(bd.n - 1, k + bd.ku + bd.kl);
-    double acc = 0.0;
-    for (int c2 = k + 1 + lane; c2 <= cmax; c2 += 32)
-      acc += AB(const_cast<double*>(ab), bd, k, c2) * x[c2];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) x[k] = (x[k] - acc) / AB(const_cast<double*>(ab), bd, k, k);
-    __syncwarp();
+  cp_async_wait<0>();
+  __syncthreads();
+  for (int s = 0; s < kInvStages - 1; ++s) issue_bwd(s);
+  for (int s = 0; s < n; ++s) {
+    cp_async_wait<kInvStages - 2>();
+    __syncthreads();
+    issue_bwd(s + kInvStages - 1);
+    if (col < n) {
+      const int k = n - 1 - s;
+      const double* Uk = Ub + (size_t)(s % kInvStages) * kInvUW;
+      const int cmax = min(n - 1, k + bd.ku + bd.kl);
+      double acc = 0.0;
+      for (int c2 = k + 1 + lane; c2 <= cmax; c2 += 32) acc += Uk[c2 - k] * x[c2];
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) x[k] = (x[k] - acc) * Uk[0];
+      __syncwarp();
+    }
   }
-  for (int r = lane; r < bd.n; r += 32) Ainv[(size_t)r * bd.n + col] = x[r];
+  cp_async_wait<0>();
+  __syncthreads();
+  // Ainv[r][col0 .. col0 + kInvWarps): kInvWarps consecutive doubles per row
+  for (int e = tid; e < n * kInvWarps; e += nt) {
+    const int r = e / kInvWarps, w = e % kInvWarps;
+    if (col0 + w < n) Ainv[(size_t)r * n + col0 + w] = xs[(size_t)w * n + r];
+  }
 }
 
 // x = Ainv b with the band numbering on both sides; one warp per row.

@@ -3,16 +3,19 @@
 // patch as in Algorithm 1 line 7).
 //
 // patchnet_forward_kernel: persistent, one 128-patch tile at a time per CTA,
-// 128 threads, thread t owns patch row t of the tile (TMEM lane t).  All
-// weights live in shared memory as BF16 K-major operands; per GRU layer the
-// tensor core accumulates in TMEM (256 FP32 columns)
+// 512 threads in four warpgroups.  Patch row r of the tile is TMEM lane r;
+// warp w serves lanes 32 (w % 4) .. +31, and warpgroup w / 4 takes one
+// quarter of every accumulator's columns in the epilogues, so that the gate
+// nonlinearities of a tile are spread over 16 warps.  All weights live in
+// shared memory as BF16 K-major operands; per GRU layer the tensor core
+// accumulates in TMEM (256 FP32 columns)
 //   [0,128)   x W_ih[r,z]^T + h W_hh[r,z]^T      (gates r and z)
 //   [128,192) x W_ih[n]^T                        (input part of gate n)
 //   [192,256) h W_hh[n]^T                        (hidden part of gate n)
-// and each thread applies the gate nonlinearities to its row in registers,
-// writing the new hidden state (FP32) to HBM and (BF16) to shared memory as
-// the next GEMM's operand.  The dense head reuses TMEM columns [0,128) and
-// [128,128+N2).
+// and each thread applies the gate nonlinearities to 16 units of its row in
+// registers, writing the new hidden state (FP32) to HBM and (BF16) to shared
+// memory as the next GEMM's operand.  The dense head reuses TMEM columns
+// [0,128) and [128,128+N2).
 #include "kernels.h"
 #include "patchnet.cuh"
 #include "umma.cuh"
@@ -25,6 +28,8 @@ using namespace umma;
 
 constexpr uint32_t kWaitPolls = 1u << 22;  // bound of every mbarrier wait
 constexpr int kTile = 128;
+constexpr int kFwdWG = 4;                      // warpgroups of the forward kernel
+constexpr int kFwdThreads = kTile * kFwdWG;
 
 __device__ __forceinline__ uint16_t f2bf(float v) {
   return __bfloat16_as_ushort(__float2bfloat16_rn(v));
@@ -106,59 +111,57 @@ __device__ __forceinline__ void mma_run(uint32_t d_tmem, uint32_t a_addr, int a_
   }
 }
 
-// One GRU layer's epilogue for this thread's row: gates from TMEM, new
-// hidden state into hreg (FP32), `next` (BF16 operand) and `hout` (FP32,
-// HBM).  With `gsave` the gates r, z, n and the hidden part of gate n
-// (incl. bias) are stored for the backward pass; with `hT` the new state is
-// also written transposed in BF16 (column `col`, row stride ldT).
+// One GRU layer's epilogue for 16 units [u0, u0 + 16) of this thread's row:
+// gates from TMEM, new hidden state into hreg (FP32, these 16 units),
+// `next` (BF16 operand) and `hout` (FP32, HBM, the 16 units).  With `gsave`
+// the gates r, z, n and the hidden part of gate n (incl. bias) are stored
+// for the backward pass (row layout [r | z | n | hn], 64 each); with `hT`
+// the new state is also written transposed in BF16 (column `col`, row
+// stride ldT).
 __device__ __forceinline__ void gru_epilogue(uint32_t tm, const float* bias, float* hreg,
-                                             uint8_t* next, int row, float* hout, bool valid,
-                                             float* gsave, uint16_t* hT, size_t ldT) {
+                                             uint8_t* next, int row, int u0, float* hout,
+                                             bool valid, float* gsave, uint16_t* hT, size_t ldT) {
   constexpr int H = 64;
-#pragma unroll 1
-  for (int c = 0; c < 4; ++c) {
-    float rp[16], zp[16], ip[16], hp[16];
-    tmem_ld16(tm + c * 16, rp);
-    tmem_ld16(tm + 64 + c * 16, zp);
-    tmem_ld16(tm + 128 + c * 16, ip);
-    tmem_ld16(tm + 192 + c * 16, hp);
-    float hn[16];
+  float rp[16], zp[16], ip[16], hp[16];
+  tmem_ld16(tm + u0, rp);
+  tmem_ld16(tm + 64 + u0, zp);
+  tmem_ld16(tm + 128 + u0, ip);
+  tmem_ld16(tm + 192 + u0, hp);
+  float hn[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int j = c * 16 + i;
-      const float r = sigmoidf_(rp[i] + bias[j]);
-      const float z = sigmoidf_(zp[i] + bias[H + j]);
-      const float ghn = hp[i] + bias[3 * H + j];
-      const float n = tanhf(ip[i] + bias[2 * H + j] + r * ghn);
-      hn[i] = (1.0f - z) * n + z * hreg[j];
-      rp[i] = r, zp[i] = z, ip[i] = n, hp[i] = ghn;
-    }
+  for (int i = 0; i < 16; ++i) {
+    const int j = u0 + i;
+    const float r = sigmoidf_(rp[i] + bias[j]);
+    const float z = sigmoidf_(zp[i] + bias[H + j]);
+    const float ghn = hp[i] + bias[3 * H + j];
+    const float n = tanhf(ip[i] + bias[2 * H + j] + r * ghn);
+    hn[i] = (1.0f - z) * n + z * hreg[i];
+    rp[i] = r, zp[i] = z, ip[i] = n, hp[i] = ghn;
+  }
 #pragma unroll
-    for (int i = 0; i < 16; ++i) hreg[c * 16 + i] = hn[i];
-    store_row16(next, row, c * 16, H, hn);
-    if (valid) {
+  for (int i = 0; i < 16; ++i) hreg[i] = hn[i];
+  store_row16(next, row, u0, H, hn);
+  if (!valid) return;
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        reinterpret_cast<float4*>(hout)[c * 4 + q] =
-            make_float4(hn[4 * q], hn[4 * q + 1], hn[4 * q + 2], hn[4 * q + 3]);
-      if (gsave) {
+  for (int q = 0; q < 4; ++q)
+    reinterpret_cast<float4*>(hout + u0)[q] =
+        make_float4(hn[4 * q], hn[4 * q + 1], hn[4 * q + 2], hn[4 * q + 3]);
+  if (gsave) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          reinterpret_cast<float4*>(gsave)[c * 4 + q] =
-              make_float4(rp[4 * q], rp[4 * q + 1], rp[4 * q + 2], rp[4 * q + 3]);
-          reinterpret_cast<float4*>(gsave + H)[c * 4 + q] =
-              make_float4(zp[4 * q], zp[4 * q + 1], zp[4 * q + 2], zp[4 * q + 3]);
-          reinterpret_cast<float4*>(gsave + 2 * H)[c * 4 + q] =
-              make_float4(ip[4 * q], ip[4 * q + 1], ip[4 * q + 2], ip[4 * q + 3]);
-          reinterpret_cast<float4*>(gsave + 3 * H)[c * 4 + q] =
-              make_float4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
-        }
-      }
-      if (hT)
-#pragma unroll
-        for (int i = 0; i < 16; ++i) hT[(size_t)(c * 16 + i) * ldT] = f2bf(hn[i]);
+    for (int q = 0; q < 4; ++q) {
+      reinterpret_cast<float4*>(gsave + u0)[q] =
+          make_float4(rp[4 * q], rp[4 * q + 1], rp[4 * q + 2], rp[4 * q + 3]);
+      reinterpret_cast<float4*>(gsave + H + u0)[q] =
+          make_float4(zp[4 * q], zp[4 * q + 1], zp[4 * q + 2], zp[4 * q + 3]);
+      reinterpret_cast<float4*>(gsave + 2 * H + u0)[q] =
+          make_float4(ip[4 * q], ip[4 * q + 1], ip[4 * q + 2], ip[4 * q + 3]);
+      reinterpret_cast<float4*>(gsave + 3 * H + u0)[q] =
+          make_float4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
     }
   }
+  if (hT)
+#pragma unroll
+    for (int i = 0; i < 16; ++i) hT[(size_t)(u0 + i) * ldT] = f2bf(hn[i]);
 }
 
 // Arguments of the forward kernel.  Inference: T = 1, hidden state read from
@@ -181,12 +184,14 @@ struct FwdArgs {
 };
 
 template <bool TRAIN>
-__global__ void __launch_bounds__(kTile, 1)
+__global__ void __launch_bounds__(kFwdThreads, 1)
     patchnet_forward_kernel(NetDims d, PackLayout L, const uint16_t* __restrict__ wimg,
                             const float* __restrict__ bias_g, FwdArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
   const FwdSmem S = FwdSmem::of(d, L.total);
-  const int t = threadIdx.x, warp = t >> 5;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int row = (warp & 3) * 32 + lane;  // patch row of the tile = TMEM lane
+  const int cq = warp >> 2;                // column quarter of the epilogues
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + S.bar);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S.tmem);
   float* bias = reinterpret_cast<float*>(sm + S.bias);
@@ -196,9 +201,9 @@ __global__ void __launch_bounds__(kTile, 1)
   {
     const uint4* src = reinterpret_cast<const uint4*>(wimg);
     uint4* dst = reinterpret_cast<uint4*>(sm + S.w);
-    for (size_t i = t; i < L.total / 8; i += kTile) dst[i] = src[i];
+    for (size_t i = t; i < L.total / 8; i += kFwdThreads) dst[i] = src[i];
     const int nb = d.layers * 4 * d.hidden + d.mlp + d.nout();
-    for (int i = t; i < nb; i += kTile) bias[i] = bias_g[i];
+    for (int i = t; i < nb; i += kFwdThreads) bias[i] = bias_g[i];
   }
   if (warp == 0) tmem_alloc(tslot, 256);
   if (t == 0) mbar_init(bar, 1);
@@ -207,9 +212,10 @@ __global__ void __launch_bounds__(kTile, 1)
   __syncthreads();
   fence_after_sync();
   const uint32_t tbase = *tslot;
-  const uint32_t tm = tbase + ((uint32_t)(warp * 32) << 16);  // this warp's lanes
+  const uint32_t tm = tbase + ((uint32_t)((warp & 3) * 32) << 16);  // this warp's lanes
   const uint32_t sbase = smem_u32(sm);
   const int kx0 = d.kx0();
+  const int u0 = 16 * cq;  // this thread's 16 hidden units
   uint32_t phase = 0;
   bool failed = false;
   const int ntiles = (P + kTile - 1) / kTile;
@@ -217,15 +223,15 @@ __global__ void __launch_bounds__(kTile, 1)
   const size_t ld = (size_t)T * P, ldh = (size_t)(T + 1) * P;
 
   for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
-    const int p = tile * kTile + t;
+    const int p = tile * kTile + row;
     const bool valid = p < P;
-    float h0r[64], h1r[64];
+    float h0r[16], h1r[16];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
+    for (int q = 0; q < 4; ++q) {
       float4 u = make_float4(0, 0, 0, 0), v = u;
       if (!TRAIN && valid) {
-        u = reinterpret_cast<const float4*>(a.h_in + (size_t)p * 64)[q];
-        v = reinterpret_cast<const float4*>(a.h_in + HP + (size_t)p * 64)[q];
+        u = reinterpret_cast<const float4*>(a.h_in + (size_t)p * 64 + u0)[q];
+        v = reinterpret_cast<const float4*>(a.h_in + HP + (size_t)p * 64 + u0)[q];
       }
       h0r[4 * q] = u.x, h0r[4 * q + 1] = u.y, h0r[4 * q + 2] = u.z, h0r[4 * q + 3] = u.w;
       h1r[4 * q] = v.x, h1r[4 * q + 1] = v.y, h1r[4 * q + 2] = v.z, h1r[4 * q + 3] = v.w;
@@ -234,27 +240,29 @@ __global__ void __launch_bounds__(kTile, 1)
     for (int step = 0; step < T && !failed; ++step) {
       const size_t col = (size_t)step * P + p;
       float* act = TRAIN ? a.act + col * kAct : nullptr;
-      // ---- stage x_t (BF16) and the hidden states (BF16 operands)
+      // ---- stage x_t (BF16, 16-byte chunks spread over the block) and the
+      // hidden states (BF16 operands, this thread's 16 units)
       {
-        const uint4 zero = make_uint4(0, 0, 0, 0);
-        const uint16_t* xr = a.x + ((size_t)p * T + step) * d.c_in;
-        for (int q = 0; q < kx0 / 8; ++q) {
-          uint4 v = zero;
-          if (valid && q * 8 < d.c_in) v = reinterpret_cast<const uint4*>(xr)[q];
-          *reinterpret_cast<uint4*>(sm + S.x + kmajor_offset(t, q * 8, kx0)) = v;
-          if (TRAIN && valid && q * 8 < d.c_in) {
-            const uint16_t* e = reinterpret_cast<const uint16_t*>(&v);
-            for (int i = 0; i < 8; ++i) a.xT[(size_t)(q * 8 + i) * ld + col] = e[i];
+        const int nq = kx0 / 8;
+        for (int e = t; e < kTile * nq; e += kFwdThreads) {
+          const int r = e / nq, q = e % nq;
+          const int pr = tile * kTile + r;
+          uint4 v = make_uint4(0, 0, 0, 0);
+          const bool in = pr < P && q * 8 < d.c_in;
+          if (in) v = reinterpret_cast<const uint4*>(a.x + ((size_t)pr * T + step) * d.c_in)[q];
+          *reinterpret_cast<uint4*>(sm + S.x + kmajor_offset(r, q * 8, kx0)) = v;
+          if (TRAIN && in) {
+            const uint16_t* ev = reinterpret_cast<const uint16_t*>(&v);
+            const size_t cr = (size_t)step * P + pr;
+            for (int i = 0; i < 8; ++i) a.xT[(size_t)(q * 8 + i) * ld + cr] = ev[i];
           }
         }
       }
+      store_row16(sm + S.h0, row, u0, 64, h0r);
+      store_row16(sm + S.h1, row, u0, 64, h1r);
+      // ---- two GRU layers (unrolled, so that each layer's state stays in
+      // registers)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        store_row16(sm + S.h0, t, c * 16, 64, h0r + c * 16);
-        store_row16(sm + S.h1, t, c * 16, 64, h1r + c * 16);
-      }
-      // ---- two GRU layers
-#pragma unroll 1
       for (int l = 0; l < 2; ++l) {
         fence_async_smem();
         fence_before_sync();
@@ -281,8 +289,8 @@ __global__ void __launch_bounds__(kTile, 1)
         // S.h0 (free after layer 0) as the dense head's input
         float* hout = TRAIN ? act + kActH0 + l * 64 : a.h_out + l * HP + (size_t)p * 64;
         uint16_t* hT = TRAIN ? (l == 0 ? a.h0T : a.h1T) + ldh - ld + col : nullptr;
-        gru_epilogue(tm, bias + l * 4 * 64, l == 0 ? h0r : h1r, sm + (l == 0 ? S.t : S.h0), t,
-                     hout, valid, TRAIN ? act + kActG0 + l * 256 : nullptr, hT, ldh);
+        gru_epilogue(tm, bias + l * 4 * 64, l == 0 ? h0r : h1r, sm + (l == 0 ? S.t : S.h0), row,
+                     u0, hout, valid, TRAIN ? act + kActG0 + l * 256 : nullptr, hT, ldh);
       }
       if (failed) break;
       // ---- dense head: relu(h1 W1^T + b1) W2^T + b2
@@ -303,7 +311,7 @@ __global__ void __launch_bounds__(kTile, 1)
       fence_after_sync();
       const float* b1 = bias + 2 * 4 * 64;
 #pragma unroll 1
-      for (int c = 0; c < 8; ++c) {
+      for (int c = 2 * cq; c < 2 * cq + 2; ++c) {  // 32 of the 128 units
         float v[16];
         tmem_ld16(tm + c * 16, v);
         if (TRAIN && valid) {
@@ -316,7 +324,7 @@ __global__ void __launch_bounds__(kTile, 1)
         }
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] + b1[c * 16 + i], 0.0f);
-        store_row16(sm + S.m, t, c * 16, 128, v);
+        store_row16(sm + S.m, row, c * 16, 128, v);
         if (TRAIN && valid)
 #pragma unroll
           for (int i = 0; i < 16; ++i) a.y1T[(size_t)(c * 16 + i) * ld + col] = f2bf(v[i]);
@@ -338,13 +346,12 @@ __global__ void __launch_bounds__(kTile, 1)
       }
       fence_after_sync();
       const float* b2 = b1 + d.mlp;
-#pragma unroll 1
-      for (int c = 0; c < n2 / 16; ++c) {
+      if (cq < n2 / 16) {  // one 16-column chunk of the output per warpgroup
         float v[16];
-        tmem_ld16(tm + 128 + c * 16, v);
+        tmem_ld16(tm + 128 + cq * 16, v);
         if (valid)
           for (int i = 0; i < 16; ++i) {
-            const int j = c * 16 + i;
+            const int j = cq * 16 + i;
             if (j < d.c_out) a.out[((size_t)p * T + step) * d.c_out + j] = v[i] + b2[j];
           }
       }
@@ -440,14 +447,15 @@ void launch_forward_impl(const NetDims& d, const PackedNet& pk, const FwdArgs& a
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int ntiles = (a.P + kTile - 1) / kTile;
   note_launch();
-  patchnet_forward_kernel<TRAIN><<<ntiles < sms ? ntiles : sms, kTile, S.total, st>>>(
+  patchnet_forward_kernel<TRAIN><<<ntiles < sms ? ntiles : sms, kFwdThreads, S.total, st>>>(
       d, L, pk.w, pk.bias, a);
 }
 
 }  // namespace
 
 bool net_supported(const NetDims& d) {
-  if (d.hidden != 64 || d.layers != 2 || d.mlp != 128 || d.c_in % 8 != 0 || d.c_out > 64)
+  if (d.hidden != 64 || d.layers != 2 || d.mlp != 128 || d.c_in % 8 != 0 || d.c_out > 64 ||
+      d.nout() > 16 * kFwdWG)
     return false;
   const PackLayout L = PackLayout::of(d);
   return FwdSmem::of(d, L.total).total <= 227 * 1024;

@@ -529,7 +529,8 @@ int dnnmg_ctx::init_train() {
   grad = mem.alloc<float>(nd.num_params());
   adam_m = mem.alloc<float>(nd.num_params());
   adam_v = mem.alloc<float>(nd.num_params());
-  cpart = mem.alloc<float>((size_t)tr_splits_max * 256 * 144);
+  cpart_floats = (size_t)tr_splits_max * 256 * 144;
+  cpart = mem.alloc<float>(cpart_floats);
   wT = mem.alloc<uint16_t>(BwdPack::kTotal);
   if (!mem.ok()) return fail(DNNMG_ERR_CUDA, "training workspace allocation failed");
   return reset_optimizer();
@@ -597,26 +598,22 @@ int dnnmg_ctx::train_grad_impl(const uint16_t* Xd, const float* Yd, int B, int T
                obih1 = oWhh1 + (size_t)3 * H * H, obhh1 = obih1 + 3 * H, oW1 = obhh1 + 3 * H,
                ob1 = oW1 + (size_t)nd.mlp * H, oW2 = ob1 + nd.mlp,
                ob2 = oW2 + (size_t)nd.c_out * nd.mlp;
-  int splits = (int)std::min<size_t>(std::max<size_t>(K / 1024, 1), (size_t)tr_splits_max);
-  struct G {
-    const uint16_t* A;
-    const uint16_t* Bm;
-    size_t ldb;
-    int M, N, mv, nv, bcol;
-    size_t ow, ob;
-  } gs[] = {
-      {gi0T, tb.xT, K, 256, 48, 3 * H, nd.c_in, nd.c_in, oWih0, obih0},
-      {gh0T, tb.h0T, Kh, 256, 80, 3 * H, H, H, oWhh0, obhh0},
-      {gi1T, tb.h0T + B, Kh, 256, 80, 3 * H, H, H, oWih1, obih1},
-      {gh1T, tb.h1T, Kh, 256, 80, 3 * H, H, H, oWhh1, obhh1},
-      {da1T, tb.h1T + B, Kh, 128, 80, nd.mlp, H, H, oW1, ob1},
-      {dyT, tb.y1T, K, 128, 144, nd.c_out, nd.mlp, nd.mlp, oW2, ob2},
+  const WGradJob jobs[] = {
+      {gi0T, tb.xT, K, K, 256, 48, 3 * H, nd.c_in, nd.c_in, grad + oWih0, grad + obih0},
+      {gh0T, tb.h0T, K, Kh, 256, 80, 3 * H, H, H, grad + oWhh0, grad + obhh0},
+      {gi1T, tb.h0T + B, K, Kh, 256, 80, 3 * H, H, H, grad + oWih1, grad + obih1},
+      {gh1T, tb.h1T, K, Kh, 256, 80, 3 * H, H, H, grad + oWhh1, grad + obhh1},
+      {da1T, tb.h1T + B, K, Kh, 128, 80, nd.mlp, H, H, grad + oW1, grad + ob1},
+      {dyT, tb.y1T, K, K, 128, 144, nd.c_out, nd.mlp, nd.mlp, grad + oW2, grad + ob2},
   };
-  for (const G& g : gs) {
-    if (launch_splitk_gemm(g.A, K, g.Bm, g.ldb, cpart, g.M, g.N, (int)K, splits, net_status, st))
-      return fail(DNNMG_ERR_ARG, "weight-gradient GEMM shape");
-    launch_reduce_grad(cpart, splits, g.M, g.N, g.mv, g.nv, g.bcol, grad + g.ow, grad + g.ob, st);
-  }
+  const int njobs = 6;
+  // about two blocks per SM, at least four K chunks of 64 per block
+  int tiles = 0;
+  for (const WGradJob& j : jobs) tiles += j.M / 128;
+  int splits = std::max(1, std::min((2 * tr_blocks_max + tiles - 1) / tiles, (int)(K / 256)));
+  while (splits > 1 && wgrad_partials(jobs, njobs, (int)K, splits) > cpart_floats) --splits;
+  if (launch_wgrad(jobs, njobs, (int)K, splits, cpart, net_status, st))
+    return fail(DNNMG_ERR_ARG, "weight-gradient GEMM shape");
   prof.end(p, st);
   return net_check("train");
 }

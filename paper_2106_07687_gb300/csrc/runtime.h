@@ -183,6 +183,7 @@ struct dnnmg_ctx {
            *gh1T = nullptr, *wT = nullptr;
   double* loss_part = nullptr;
   int tr_layout_B = -1, tr_layout_T = -1, adam_step = 0, tr_blocks_max = 0, tr_splits_max = 0;
+  size_t cpart_floats = 0;
 
   ~dnnmg_ctx();
   int init();

@@ -1,9 +1,12 @@
 // Matrix-free operator kernels: Jacobian apply, defect, FP64 nonlinear
 // residual and the old-time right-hand side (Sec. 2.1, Eqs. 4-7).
 //
-// One thread per node; the 2D block of 32x4 threads covers a tile of nodes
-// with x fastest, so each warp reads contiguous rows of the SoA fields.
+// Apply, defect and residual run tiled (32 x 8 nodes per block, cell and
+// patch rows computed once per tile, optile_body.cuh); the right-hand-side
+// kernels run one thread per node with 32 x 4 blocks, x fastest, so each
+// warp reads contiguous rows of the SoA fields.
 #include "kernels.h"
+#include "optile_body.cuh"
 #include "vbody.cuh"
 
 namespace dnnmg {
@@ -11,32 +14,6 @@ namespace dnnmg {
 namespace {
 
 constexpr int kBX = 32, kBY = 4;
-
-template <typename T>
-__global__ void __launch_bounds__(kBX* kBY) apply_kernel(Grid g, Sten<T> s, const T* __restrict__ w,
-                                                         const T* __restrict__ vb,
-                                                         T* __restrict__ y) {
-  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
-  if (i >= g.nnx || j >= g.nny) return;
-  apply_node<T>(g, s, w, vb, y, i, j);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kBX* kBY)
-    defect_kernel(Grid g, Sten<T> s, const T* __restrict__ b, const T* __restrict__ x,
-                  const T* __restrict__ vb, T* __restrict__ d, bool masked) {
-  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
-  if (i >= g.nnx || j >= g.nny) return;
-  defect_node<T>(g, s, b, x, vb, d, masked, i, j);
-}
-
-__global__ void __launch_bounds__(kBX* kBY)
-    residual64_kernel(Grid g, Sten<double> s, const double* __restrict__ x,
-                      const double* __restrict__ f, double* __restrict__ r) {
-  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
-  if (i >= g.nnx || j >= g.nny) return;
-  residual64_node(g, s, x, f, r, i, j);
-}
 
 __global__ void __launch_bounds__(kBX* kBY)
     old_rhs64_kernel(Grid g, double inv_k, const double* __restrict__ x, double* __restrict__ f) {
@@ -55,25 +32,100 @@ __global__ void __launch_bounds__(kBX* kBY)
 
 inline dim3 node_grid(const Grid& g) { return dim3(cdiv(g.nnx, kBX), cdiv(g.nny, kBY)); }
 
+// Tiled variants (optile_body.cuh): one block per TX x TY nodes.
+constexpr int kTX = 32, kTY = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(kTX* kTY)
+    apply_tiled_kernel(Grid g, Sten<T> s, const T* __restrict__ w, const T* __restrict__ vb,
+                       T* __restrict__ y) {
+  extern __shared__ __align__(16) uint8_t smraw[];
+  auto& S = *reinterpret_cast<OpSmem<T, kTX, kTY>*>(smraw);
+  T ru, rv, rp;
+  int n;
+  op_tile_rows<T, false, true, kTX, kTY>(g, s, w, vb, blockIdx.x, blockIdx.y, S, ru, rv, rp, n);
+  if (n < 0) return;
+  const uint8_t f = op_tile_flags<T, kTX, kTY>(S);
+  y[n] = (f & kVDir) ? w[n] : ru;
+  y[g.nn + n] = (f & kVDir) ? w[g.nn + n] : rv;
+  y[2 * g.nn + n] = (f & kPFix) ? w[2 * g.nn + n] : rp;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTX* kTY)
+    defect_tiled_kernel(Grid g, Sten<T> s, const T* __restrict__ b, const T* __restrict__ x,
+                        const T* __restrict__ vb, T* __restrict__ d, bool masked) {
+  extern __shared__ __align__(16) uint8_t smraw[];
+  auto& S = *reinterpret_cast<OpSmem<T, kTX, kTY>*>(smraw);
+  T ru, rv, rp;
+  int n;
+  op_tile_rows<T, false, true, kTX, kTY>(g, s, x, vb, blockIdx.x, blockIdx.y, S, ru, rv, rp, n);
+  if (n < 0) return;
+  const uint8_t f = op_tile_flags<T, kTX, kTY>(S);
+  const int nn = g.nn;
+  if (f & kVDir) {
+    d[n] = masked ? T(0) : b[n] - x[n];
+    d[nn + n] = masked ? T(0) : b[nn + n] - x[nn + n];
+  } else {
+    d[n] = b[n] - ru;
+    d[nn + n] = b[nn + n] - rv;
+  }
+  if (f & kPFix)
+    d[2 * nn + n] = masked ? T(0) : b[2 * nn + n] - x[2 * nn + n];
+  else
+    d[2 * nn + n] = b[2 * nn + n] - rp;
+}
+
+__global__ void __launch_bounds__(kTX* kTY)
+    residual64_tiled_kernel(Grid g, Sten<double> s, const double* __restrict__ x,
+                            const double* __restrict__ f, double* __restrict__ r) {
+  extern __shared__ __align__(16) uint8_t smraw[];
+  auto& S = *reinterpret_cast<OpSmem<double, kTX, kTY>*>(smraw);
+  double ru, rv, rp;
+  int n;
+  op_tile_rows<double, true, false, kTX, kTY>(g, s, x, nullptr, blockIdx.x, blockIdx.y, S, ru, rv,
+                                              rp, n);
+  if (n < 0) return;
+  const uint8_t fl = op_tile_flags<double, kTX, kTY>(S);
+  const int nn = g.nn;
+  r[n] = (fl & kVDir) ? 0.0 : f[n] - ru;
+  r[nn + n] = (fl & kVDir) ? 0.0 : f[nn + n] - rv;
+  r[2 * nn + n] = (fl & kPFix) ? 0.0 : f[2 * nn + n] - rp;
+}
+
+inline dim3 tile_grid(const Grid& g) { return dim3(cdiv(g.nnx, kTX), cdiv(g.nny, kTY)); }
+
+// opt a kernel in to `bytes` of dynamic shared memory; callers keep the
+// result in a function-local static, so each launcher does it once
+template <typename K>
+size_t smem_attr(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024)
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return bytes;
+}
+
 }  // namespace
 
 template <typename T>
 void launch_apply(const Grid& g, const Sten<T>& s, const T* w, const T* vb, T* y, cudaStream_t st) {
   note_launch();
-  apply_kernel<T><<<node_grid(g), dim3(kBX, kBY), 0, st>>>(g, s, w, vb, y);
+  static const size_t sm = smem_attr(apply_tiled_kernel<T>, sizeof(OpSmem<T, kTX, kTY>));
+  apply_tiled_kernel<T><<<tile_grid(g), kTX * kTY, sm, st>>>(g, s, w, vb, y);
 }
 
 template <typename T>
 void launch_defect(const Grid& g, const Sten<T>& s, const T* b, const T* x, const T* vb, T* d,
                    bool masked, cudaStream_t st) {
   note_launch();
-  defect_kernel<T><<<node_grid(g), dim3(kBX, kBY), 0, st>>>(g, s, b, x, vb, d, masked);
+  static const size_t sm = smem_attr(defect_tiled_kernel<T>, sizeof(OpSmem<T, kTX, kTY>));
+  defect_tiled_kernel<T><<<tile_grid(g), kTX * kTY, sm, st>>>(g, s, b, x, vb, d, masked);
 }
 
 void launch_residual64(const Grid& g, const Sten<double>& s, const double* x, const double* f,
                        double* r, cudaStream_t st) {
   note_launch();
-  residual64_kernel<<<node_grid(g), dim3(kBX, kBY), 0, st>>>(g, s, x, f, r);
+  static const size_t sm = smem_attr(residual64_tiled_kernel, sizeof(OpSmem<double, kTX, kTY>));
+  residual64_tiled_kernel<<<tile_grid(g), kTX * kTY, sm, st>>>(g, s, x, f, r);
 }
 
 void launch_old_time_rhs64(const Grid& g, double inv_k, const double* x_old, double* f,

@@ -42,7 +42,7 @@ struct BwdSmem {
     s.r2 = o;   o += kTile * 192 * 2;
     s.bar = o;  o += 16;
     s.tmem = o; o += 16;
-    s.red = o;  o += 4 * 8;
+    s.red = o;  o += 16 * 8;  // one double per warp
     s.total = o;
     return s;
   }
@@ -111,18 +111,23 @@ __device__ __forceinline__ void gru_backward_chunk(int c, const float* dh, const
   }
 }
 
-__global__ void __launch_bounds__(kTile, 1)
+constexpr int kBwdWG = 4;  // warpgroups: each takes a quarter of every accumulator's columns
+constexpr int kBwdThreads = kTile * kBwdWG;
+
+__global__ void __launch_bounds__(kBwdThreads, 1)
     patchnet_backward_kernel(NetDims d, const uint16_t* __restrict__ wT, BwdArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
   const BwdSmem S = BwdSmem::of();
-  const int t = threadIdx.x, warp = t >> 5;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int row = (warp & 3) * 32 + lane;  // patch row of the tile = TMEM lane
+  const int cq = warp >> 2;                // column quarter
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + S.bar);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S.tmem);
   double* red = reinterpret_cast<double*>(sm + S.red);
   {
     const uint4* src = reinterpret_cast<const uint4*>(wT);
     uint4* dst = reinterpret_cast<uint4*>(sm + S.w);
-    for (int i = t; i < BwdPack::kTotal / 8; i += kTile) dst[i] = src[i];
+    for (int i = t; i < BwdPack::kTotal / 8; i += kBwdThreads) dst[i] = src[i];
   }
   if (warp == 0) tmem_alloc(tslot, 256);
   if (t == 0) mbar_init(bar, 1);
@@ -131,12 +136,13 @@ __global__ void __launch_bounds__(kTile, 1)
   __syncthreads();
   fence_after_sync();
   const uint32_t tbase = *tslot;
-  const uint32_t tm = tbase + ((uint32_t)(warp * 32) << 16);
+  const uint32_t tm = tbase + ((uint32_t)((warp & 3) * 32) << 16);
   const uint32_t sb = smem_u32(sm);
   uint8_t* R1 = sm + S.r1;
   uint8_t* R2 = sm + S.r2;
   const int B = a.B, T = a.T, C = d.c_out;
   const size_t ld = (size_t)T * B;
+  const int u0 = 16 * cq;  // this thread's 16 hidden units
   uint32_t phase = 0;
   bool failed = false;
   double loss = 0.0;
@@ -158,38 +164,40 @@ __global__ void __launch_bounds__(kTile, 1)
   };
 
   for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
-    const int p = tile * kTile + t;
+    const int p = tile * kTile + row;
     const bool valid = p < B;
-    float dh0n[64], dh1n[64];
+    float dh0n[16], dh1n[16];  // gradients w.r.t. the previous step's states (these units)
 #pragma unroll
-    for (int j = 0; j < 64; ++j) dh0n[j] = dh1n[j] = 0.0f;
+    for (int j = 0; j < 16; ++j) dh0n[j] = dh1n[j] = 0.0f;
 #pragma unroll 1
     for (int step = T - 1; step >= 0 && !failed; --step) {
       const size_t col = (size_t)step * B + p;
       const float* act = a.act + col * kAct;
       const float* actp = step > 0 ? a.act + (col - B) * kAct : nullptr;
-      // ---- loss and dY (Eq. 8 as a mean): dY = 2 (y - Y) / (B T C)
-      {
-        float dy[32];
+      // ---- loss and dY (Eq. 8 as a mean): dY = 2 (y - Y) / (B T C); output
+      // columns 16 cq .. +15 (warpgroups 0 and 1)
+      if (cq < 2) {
+        float dy[16];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) dy[j] = 0.0f;
+        for (int i = 0; i < 16; ++i) dy[i] = 0.0f;
         if (valid) {
           const size_t o = ((size_t)p * T + step) * C;
-          for (int j = 0; j < C; ++j) {
+          for (int i = 0; i < 16; ++i) {
+            const int j = 16 * cq + i;
+            if (j >= C) break;
             const float e = a.ypred[o + j] - a.Y[o + j];
             loss += (double)e * e;
-            dy[j] = a.scale * e;
-            a.dyT[(size_t)j * ld + col] = f2bf(dy[j]);
+            dy[i] = a.scale * e;
+            a.dyT[(size_t)j * ld + col] = f2bf(dy[i]);
           }
         }
-        store_row16(R1, t, 0, 32, dy);
-        store_row16(R1, t, 16, 32, dy + 16);
+        store_row16(R1, row, 16 * cq, 32, dy);
       }
       sync_mma([&] { mma_run(tbase + 0, sb + S.r1, 32, sb + S.w + 2 * BwdPack::kW2T, 32, 128, 32); });
       if (failed) break;
-      // ---- dense head: da1 = (dY W2) * [a1 > 0]
-#pragma unroll 1
-      for (int c = 0; c < 8; ++c) {
+      // ---- dense head: da1 = (dY W2) * [a1 > 0], 32 of the 128 units
+#pragma unroll
+      for (int c = 2 * cq; c < 2 * cq + 2; ++c) {
         float v[16];
         tmem_ld16(tm + c * 16, v);
 #pragma unroll
@@ -198,23 +206,23 @@ __global__ void __launch_bounds__(kTile, 1)
           v[i] = (valid && act[kActA1 + j] > 0.0f) ? v[i] : 0.0f;
           if (valid) a.da1T[(size_t)j * ld + col] = f2bf(v[i]);
         }
-        store_row16(R1, t, c * 16, 128, v);
+        store_row16(R1, row, c * 16, 128, v);
       }
       sync_mma([&] { mma_run(tbase + 128, sb + S.r1, 128, sb + S.w + 2 * BwdPack::kW1T, 128, 64, 128); });
       if (failed) break;
       // ---- GRU layer 1
-#pragma unroll 1
-      for (int c = 0; c < 4; ++c) {
+      {
         float dh[16], hp[16], dp[16];
-        tmem_ld16(tm + 128 + c * 16, dh);
+        tmem_ld16(tm + 128 + u0, dh);
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-          dh[i] = valid ? dh[i] + dh1n[c * 16 + i] : 0.0f;
-          hp[i] = actp ? actp[kActH1 + c * 16 + i] : 0.0f;
+          dh[i] = valid ? dh[i] + dh1n[i] : 0.0f;
+          hp[i] = actp ? actp[kActH1 + u0 + i] : 0.0f;
         }
-        gru_backward_chunk(c, dh, act + kActG1, hp, dp, R1, R2, t, valid, a.gi1T + col, a.gh1T + col, ld);
+        gru_backward_chunk(cq, dh, act + kActG1, hp, dp, R1, R2, row, valid, a.gi1T + col,
+                           a.gh1T + col, ld);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) dh1n[c * 16 + i] = dp[i];
+        for (int i = 0; i < 16; ++i) dh1n[i] = dp[i];
       }
       sync_mma([&] {
         mma_run(tbase + 0, sb + S.r2, 192, sb + S.w + 2 * BwdPack::kWhh1T, 192, 64, 192);
@@ -222,30 +230,28 @@ __global__ void __launch_bounds__(kTile, 1)
       });
       if (failed) break;
       // ---- GRU layer 0 (its input gradient is not needed)
-#pragma unroll 1
-      for (int c = 0; c < 4; ++c) {
+      {
         float dmm[16], dtop[16], hp[16], dp[16];
-        tmem_ld16(tm + c * 16, dmm);
-        tmem_ld16(tm + 64 + c * 16, dtop);
+        tmem_ld16(tm + u0, dmm);
+        tmem_ld16(tm + 64 + u0, dtop);
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-          dh1n[c * 16 + i] += dmm[i];
-          dtop[i] = valid ? dtop[i] + dh0n[c * 16 + i] : 0.0f;
-          hp[i] = actp ? actp[kActH0 + c * 16 + i] : 0.0f;
+          dh1n[i] += dmm[i];
+          dtop[i] = valid ? dtop[i] + dh0n[i] : 0.0f;
+          hp[i] = actp ? actp[kActH0 + u0 + i] : 0.0f;
         }
-        gru_backward_chunk(c, dtop, act + kActG0, hp, dp, nullptr, R2, t, valid, a.gi0T + col,
+        gru_backward_chunk(cq, dtop, act + kActG0, hp, dp, nullptr, R2, row, valid, a.gi0T + col,
                            a.gh0T + col, ld);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) dh0n[c * 16 + i] = dp[i];
+        for (int i = 0; i < 16; ++i) dh0n[i] = dp[i];
       }
       sync_mma([&] { mma_run(tbase + 128, sb + S.r2, 192, sb + S.w + 2 * BwdPack::kWhh0T, 192, 64, 192); });
       if (failed) break;
-#pragma unroll 1
-      for (int c = 0; c < 4; ++c) {
+      {
         float dmm[16];
-        tmem_ld16(tm + 128 + c * 16, dmm);
+        tmem_ld16(tm + 128 + u0, dmm);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) dh0n[c * 16 + i] += dmm[i];
+        for (int i = 0; i < 16; ++i) dh0n[i] += dmm[i];
       }
       fence_before_sync();
       __syncthreads();
@@ -253,9 +259,13 @@ __global__ void __launch_bounds__(kTile, 1)
   }
   // per-CTA loss partial (fixed-order reduction)
   for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
-  if ((t & 31) == 0) red[warp] = loss;
+  if (lane == 0) red[warp] = loss;
   __syncthreads();
-  if (t == 0) a.loss_partial[blockIdx.x] = red[0] + red[1] + red[2] + red[3];
+  if (t == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kBwdThreads / 32; ++w) s += red[w];
+    a.loss_partial[blockIdx.x] = s;
+  }
   if (failed) {
     if (t == 0) atomicOr(a.status, 4);
     mbar_wait(bar, phase, kWaitPolls);
@@ -268,71 +278,117 @@ __global__ void __launch_bounds__(kTile, 1)
   }
 }
 
-// Split-K GEMM: Cpart[split][M][N] = A[M][k-range] B[N][k-range]^T with row
-// strides lda / ldb (elements).
+// Weight gradients of all layers in one launch: for every job, the partial
+// sums Cpart[job][split][M][N] = A[M][k-range] B[N][k-range]^T over a range
+// of the K = (steps x patches) columns.  A block owns one 128-row tile of one
+// job and one K range; its operands stream through a ring of kWStages
+// shared-memory stages filled by asynchronous 16-byte copies, so the copies
+// of chunk c + kWStages - 1 overlap the tensor-core MMAs of chunk c (a slot
+// is refilled once the MMAs that read it have completed).
 constexpr int kKC = 64;
+constexpr int kWStages = 4;
+constexpr int kWNmax = 144;
+constexpr size_t kWStageA = (size_t)kTile * kKC * 2;
+constexpr size_t kWStage = kWStageA + (size_t)kWNmax * kKC * 2;
+constexpr size_t kWSmem = kWStages * kWStage + 64;
+
+__device__ __forceinline__ void cp16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 __global__ void __launch_bounds__(kTile, 1)
-    splitk_gemm_kernel(const uint16_t* __restrict__ A, size_t lda, const uint16_t* __restrict__ B,
-                       size_t ldb, float* __restrict__ C, int M, int N, int K, int Ks,
-                       uint32_t ncols, int* status) {
+    wgrad_kernel(WGradArgs a, float* __restrict__ Cpart, int* status) {
   extern __shared__ __align__(1024) uint8_t sm[];
-  uint8_t* sa = sm;
-  uint8_t* sbm = sm + kTile * kKC * 2;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sbm + 256 * kKC * 2);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kWStages * kWStage);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + kWStages);
+  int jb = 0;
+  while (jb + 1 < a.njobs && (int)blockIdx.x >= a.first[jb + 1]) ++jb;
+  const WGradJob& J = a.job[jb];
+  const int nmt = J.M / kTile;
+  const int b = blockIdx.x - a.first[jb];
+  const int mt = b % nmt, split = b / nmt;
+  const int row0 = mt * kTile;
+  const int kbeg = split * a.Ks, kend = min(a.K, kbeg + a.Ks);
+  const int nch = kend > kbeg ? (kend - kbeg + kKC - 1) / kKC : 0;
+  uint32_t ncols = 32;
+  while (ncols < (uint32_t)J.N) ncols <<= 1;
   const int t = threadIdx.x, warp = t >> 5;
   if (warp == 0) tmem_alloc(tslot, ncols);
-  if (t == 0) mbar_init(bar, 1);
+  if (t == 0)
+    for (int q = 0; q < kWStages; ++q) mbar_init(bar + q, 1);
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
   const uint32_t tbase = *tslot;
-  const int row0 = blockIdx.x * kTile;
-  const int kbeg = blockIdx.y * Ks, kend = min(K, kbeg + Ks);
-  uint32_t phase = 0;
-  bool failed = false, any = false;
-  for (int k0 = kbeg; k0 < kend && !failed; k0 += kKC) {
-    const int kc = min(kKC, kend - k0);
-    for (int e = t; e < kTile * (kc / 8); e += kTile) {
-      const int r = e / (kc / 8), q = e % (kc / 8);
-      *reinterpret_cast<uint4*>(sa + kmajor_offset(r, q * 8, kc)) =
-          *reinterpret_cast<const uint4*>(A + (size_t)(row0 + r) * lda + k0 + q * 8);
+  auto load = [&](int c) {
+    if (c < nch) {
+      uint8_t* sa = sm + (size_t)(c % kWStages) * kWStage;
+      uint8_t* sb = sa + kWStageA;
+      const int k0 = kbeg + c * kKC;
+      const int q8 = min(kKC, kend - k0) / 8;
+      for (int e = t; e < kTile * q8; e += kTile) {
+        const int r = e / q8, q = e % q8;
+        cp16(sa + kmajor_offset(r, q * 8, kKC), J.A + (size_t)(row0 + r) * J.lda + k0 + q * 8);
+      }
+      for (int e = t; e < J.N * q8; e += kTile) {
+        const int r = e / q8, q = e % q8;
+        cp16(sb + kmajor_offset(r, q * 8, kKC), J.B + (size_t)r * J.ldb + k0 + q * 8);
+      }
     }
-    for (int e = t; e < N * (kc / 8); e += kTile) {
-      const int r = e / (kc / 8), q = e % (kc / 8);
-      *reinterpret_cast<uint4*>(sbm + kmajor_offset(r, q * 8, kc)) =
-          *reinterpret_cast<const uint4*>(B + (size_t)r * ldb + k0 + q * 8);
-    }
+    cp_commit();
+  };
+  for (int c = 0; c < kWStages - 1; ++c) load(c);
+  const uint32_t id = idesc_bf16(kTile, J.N);
+  bool failed = false;
+  int last = -1;  // last chunk whose MMAs were committed
+  for (int c = 0; c < nch && !failed; ++c) {
+    cp_wait<kWStages - 2>();  // chunk c has landed (this thread's copies)
     fence_async_smem();
     fence_before_sync();
     __syncthreads();
-    if (t == 0) {
-      fence_after_sync();
-      const uint32_t id = idesc_bf16(kTile, N);
-      for (int ks = 0; ks < kc / 16; ++ks) {
-        const uint64_t da = smem_desc(smem_u32(sa) + ks * 256, 128, (kc / 8) * 128);
-        const uint64_t db = smem_desc(smem_u32(sbm) + ks * 256, 128, (kc / 8) * 128);
-        mma_bf16(tbase, da, db, id, (any || ks > 0) ? 1u : 0u);
-      }
-      mma_commit(bar);
-    }
-    any = true;
-    if (!mbar_wait(bar, phase, kWaitPolls)) failed = true;
-    phase ^= 1;
-    failed = __syncthreads_or(failed);
     fence_after_sync();
+    if (t == 0) {
+      const uint8_t* sa = sm + (size_t)(c % kWStages) * kWStage;
+      const uint8_t* sb = sa + kWStageA;
+      const int kc = min(kKC, kend - (kbeg + c * kKC));
+      for (int ks = 0; ks < kc / 16; ++ks) {
+        const uint64_t da = smem_desc(smem_u32(sa) + ks * 256, 128, (kKC / 8) * 128);
+        const uint64_t db = smem_desc(smem_u32(sb) + ks * 256, 128, (kKC / 8) * 128);
+        mma_bf16(tbase, da, db, id, (c > 0 || ks > 0) ? 1u : 0u);
+      }
+      mma_commit(bar + c % kWStages);
+    }
+    last = c;
+    // refill the slot of chunk c - 1 once its MMAs are done
+    if (c >= 1 && !mbar_wait(bar + (c - 1) % kWStages, ((c - 1) / kWStages) & 1, kWaitPolls))
+      failed = true;
+    failed = __syncthreads_or(failed);
+    if (!failed) load(c + kWStages - 1);
   }
-  float* Cp = C + (size_t)blockIdx.y * M * N;
+  if (!failed && last >= 0 &&
+      !mbar_wait(bar + last % kWStages, (last / kWStages) & 1, kWaitPolls))
+    failed = true;
+  failed = __syncthreads_or(failed);
+  cp_wait<0>();
+  fence_after_sync();
+  float* Cp = Cpart + a.coff[jb] + (size_t)split * J.M * J.N;
   const int r = row0 + t;
   if (!failed) {
-    for (int c = 0; c < N / 16; ++c) {
+    for (int c = 0; c < J.N / 16; ++c) {
       float v[16];
-      if (any) tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + c * 16, v);
-      for (int i = 0; i < 16; ++i) Cp[(size_t)r * N + c * 16 + i] = any ? v[i] : 0.0f;
+      if (nch > 0) tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + c * 16, v);
+      for (int i = 0; i < 16; ++i) Cp[(size_t)r * J.N + c * 16 + i] = nch > 0 ? v[i] : 0.0f;
     }
   } else {
     if (t == 0) atomicOr(status, 4);
-    mbar_wait(bar, phase, kWaitPolls);
+    // the tensor core may still be working: wait (bounded) for the last commit
+    if (last >= 0) mbar_wait(bar + last % kWStages, (last / kWStages) & 1, kWaitPolls);
   }
   fence_before_sync();
   __syncthreads();
@@ -342,20 +398,24 @@ __global__ void __launch_bounds__(kTile, 1)
   }
 }
 
-// grad_w[m * n_valid + n] = sum_s Cpart[s][m][n]; grad_b[m] = sum_s Cpart[s][m][bias_col]
-__global__ void reduce_grad_kernel(const float* __restrict__ Cp, int S, int M, int N, int m_valid,
-                                   int n_valid, int bias_col, float* __restrict__ gw,
-                                   float* __restrict__ gb) {
-  const int total = m_valid * (n_valid + 1);
+// grad_w[m * n_valid + n] = sum_s Cpart[job][s][m][n] (fixed order, FP64),
+// grad_b[m] = sum_s Cpart[job][s][m][bias_col], all jobs in one launch
+__global__ void wgrad_reduce_kernel(WGradArgs a, const float* __restrict__ Cpart) {
+  const int total = a.eoff[a.njobs];
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-    const int m = e / (n_valid + 1), n = e % (n_valid + 1);
-    const int cn = n < n_valid ? n : bias_col;
+    int jb = 0;
+    while (jb + 1 < a.njobs && e >= a.eoff[jb + 1]) ++jb;
+    const WGradJob& J = a.job[jb];
+    const int le = e - a.eoff[jb];
+    const int m = le / (J.n_valid + 1), n = le % (J.n_valid + 1);
+    const int cn = n < J.n_valid ? n : J.bias_col;
+    const float* Cp = Cpart + a.coff[jb];
     double acc = 0.0;
-    for (int s = 0; s < S; ++s) acc += Cp[((size_t)s * M + m) * N + cn];
-    if (n < n_valid)
-      gw[(size_t)m * n_valid + n] = (float)acc;
+    for (int sp = 0; sp < a.splits; ++sp) acc += Cp[((size_t)sp * J.M + m) * J.N + cn];
+    if (n < J.n_valid)
+      J.gw[(size_t)m * J.n_valid + n] = (float)acc;
     else
-      gb[m] = (float)acc;
+      J.gb[m] = (float)acc;
   }
 }
 
@@ -416,29 +476,54 @@ void launch_patchnet_backward(const NetDims& d, const uint16_t* wT, const BwdArg
   cudaFuncSetAttribute(patchnet_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)S.total);
   note_launch();
-  patchnet_backward_kernel<<<nblocks, kTile, S.total, st>>>(d, wT, a);
+  patchnet_backward_kernel<<<nblocks, kBwdThreads, S.total, st>>>(d, wT, a);
 }
 
-int launch_splitk_gemm(const uint16_t* A, size_t lda, const uint16_t* B, size_t ldb, float* Cpart,
-                       int M, int N, int K, int splits, int* status, cudaStream_t st) {
-  if (M <= 0 || M % kTile || N < 16 || N > 256 || N % 16 || K % 16 || splits < 1) return 1;
+int launch_wgrad(const WGradJob* jobs, int njobs, int K, int splits, float* Cpart, int* status,
+                 cudaStream_t st) {
+  if (njobs < 1 || njobs > kMaxWGradJobs || K < 16 || K % 16 || splits < 1) return 1;
+  WGradArgs a{};
+  a.njobs = njobs;
+  a.K = K;
   int Ks = (K + splits - 1) / splits;
   Ks = (Ks + kKC - 1) / kKC * kKC;
-  uint32_t ncols = 32;
-  while (ncols < (uint32_t)N) ncols <<= 1;
-  const size_t smem = (size_t)kTile * kKC * 2 + (size_t)256 * kKC * 2 + 64;
-  cudaFuncSetAttribute(splitk_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  a.Ks = Ks;
+  a.splits = (K + Ks - 1) / Ks;
+  long long coff = 0;
+  int blocks = 0, elems = 0;
+  for (int q = 0; q < njobs; ++q) {
+    const WGradJob& J = jobs[q];
+    if (J.M <= 0 || J.M % kTile || J.N < 16 || J.N > kWNmax || J.N % 16 || J.lda % 8 ||
+        J.ldb % 8 || J.bias_col >= J.N || J.n_valid >= J.N || J.m_valid > J.M)
+      return 1;
+    a.job[q] = J;
+    a.coff[q] = coff;
+    a.first[q] = blocks;
+    a.eoff[q] = elems;
+    coff += (long long)a.splits * J.M * J.N;
+    blocks += (J.M / kTile) * a.splits;
+    elems += J.m_valid * (J.n_valid + 1);
+  }
+  a.first[njobs] = blocks;
+  a.eoff[njobs] = elems;
+  static const bool attr =
+      cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kWSmem) == cudaSuccess;
+  (void)attr;
   note_launch();
-  splitk_gemm_kernel<<<dim3(M / kTile, splits), kTile, smem, st>>>(A, lda, B, ldb, Cpart, M, N, K,
-                                                                    Ks, ncols, status);
+  wgrad_kernel<<<blocks, kTile, kWSmem, st>>>(a, Cpart, status);
+  note_launch();
+  wgrad_reduce_kernel<<<cdiv(elems, 256), 256, 0, st>>>(a, Cpart);
   return 0;
 }
 
-void launch_reduce_grad(const float* Cpart, int splits, int M, int N, int m_valid, int n_valid,
-                        int bias_col, float* gw, float* gb, cudaStream_t st) {
-  note_launch();
-  reduce_grad_kernel<<<cdiv(m_valid * (n_valid + 1), 256), 256, 0, st>>>(
-      Cpart, splits, M, N, m_valid, n_valid, bias_col, gw, gb);
+size_t wgrad_partials(const WGradJob* jobs, int njobs, int K, int splits) {
+  int Ks = (K + splits - 1) / splits;
+  Ks = (Ks + kKC - 1) / kKC * kKC;
+  const int sp = (K + Ks - 1) / Ks;
+  size_t n = 0;
+  for (int q = 0; q < njobs; ++q) n += (size_t)sp * jobs[q].M * jobs[q].N;
+  return n;
 }
 
 void launch_loss(const double* part, int n, double inv, float* out, cudaStream_t st) {

@@ -37,10 +37,33 @@ struct BwdArgs {
 void launch_pack_backward(const NetDims& d, const float* w, uint16_t* wT, cudaStream_t st);
 void launch_patchnet_backward(const NetDims& d, const uint16_t* wT, const BwdArgs& a, int nblocks,
                               cudaStream_t st);
-int launch_splitk_gemm(const uint16_t* A, size_t lda, const uint16_t* B, size_t ldb, float* Cpart,
-                       int M, int N, int K, int splits, int* status, cudaStream_t st);
-void launch_reduce_grad(const float* Cpart, int splits, int M, int N, int m_valid, int n_valid,
-                        int bias_col, float* gw, float* gb, cudaStream_t st);
+// One weight-gradient product dW = A B^T over the K = steps x patches
+// columns (A [M][lda], B [N][ldb], BF16, row-major); rows >= m_valid and
+// columns >= n_valid of the product are padding, column bias_col of B holds
+// ones so that column gives the bias gradient.
+struct WGradJob {
+  const uint16_t* A;
+  const uint16_t* B;
+  size_t lda, ldb;
+  int M, N;  // M a multiple of 128, N a multiple of 16, <= 144
+  int m_valid, n_valid, bias_col;
+  float* gw;  // [m_valid][n_valid]
+  float* gb;  // [m_valid]
+};
+constexpr int kMaxWGradJobs = 8;
+struct WGradArgs {
+  WGradJob job[kMaxWGradJobs];
+  long long coff[kMaxWGradJobs];  // offset of each job's partial sums
+  int first[kMaxWGradJobs + 1];   // first block of each job
+  int eoff[kMaxWGradJobs + 1];    // first reduced element of each job
+  int njobs, K, Ks, splits;
+};
+// All jobs' products, the K range split `splits` ways into partial sums
+// (Cpart: wgrad_partials() floats), then reduced in a fixed order.  Returns
+// nonzero on an unsupported shape.
+int launch_wgrad(const WGradJob* jobs, int njobs, int K, int splits, float* Cpart, int* status,
+                 cudaStream_t st);
+size_t wgrad_partials(const WGradJob* jobs, int njobs, int K, int splits);
 void launch_loss(const double* part, int n, double inv, float* out, cudaStream_t st);
 void launch_adam(float* w, const float* g, float* m, float* v, size_t n, float lr, int step,
                  cudaStream_t st);
