@@ -35,6 +35,10 @@ WORKLOAD = ("DNN-MG time step: multigrid on the 512x128 channel (level 5, 198,53
             "network on 1024x256 (level 6, 61,440 patches, GRU 2x64 + MLP 128, BF16), nu=0.0065, "
             "dt=0.005, mixed FP32/FP64")
 ORACLE_L = 4              # bounded CPU sample: oracle DNN-MG step with L = 4, scaled by DOFs
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel
+# as it stands (profiles/vcycle_subcycle_level5.md); a kernel change makes
+# the entry stale and it must then be removed.
+NCU_TRAFFIC = {"vcycle_kernel<float>@split4": 19742464 + 12032}
 L2_BYTES = 129 * 2 ** 20
 
 
@@ -182,6 +186,8 @@ def run_ours(args, rank, world):
     stream = torch.cuda.current_stream()
     ob = synthetic.obstacle_block(1000 + rank)
     common = dict(precision=dn.MIXED, dt=DT, obstacle_i0=ob[0], obstacle_j0=ob[1])
+    if args.split >= 0:  # a fixed V-cycle plan instead of the autotuned one
+        common.update(persistent_vcycle=args.split, persistent_mode=args.split_mode)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     hbm, bf16, bf16_sus, peak_kind = peaks()
 
@@ -267,9 +273,13 @@ def run_ours(args, rank, world):
         for k in range(args.steps):
             for name, (c, mode) in runs.items():
                 flush.zero_()
+                if name == "dnnmg":  # kernel profilers select these launches by this range
+                    torch.cuda.nvtx.range_push("dnnmg_step")
                 ev[0].record(stream)
                 stats[name].append(c.step(mode))
                 ev[1].record(stream)
+                if name == "dnnmg":
+                    torch.cuda.nvtx.range_pop()
                 torch.cuda.synchronize()
                 times[name] += ev[0].elapsed_time(ev[1])
             vref = ref_ctx.get_state()[:2 * nnodes(L + 1)]
@@ -291,6 +301,7 @@ def run_ours(args, rank, world):
         n, t = net_ctx.profile_read(sid)
         stage[nm] = {"launches": n, "ms": round(t, 4)}
     vp_n, vp_ms = net_ctx.profile_read(0, L)
+    vs_n, vs_ms = net_ctx.profile_read(11)  # persistent sub-cycle launches
     net_ctx.profile(False)
 
     # ---- V-cycle throughput at levels 6 and 5 (current linearisations) -----------
@@ -337,7 +348,25 @@ def run_ours(args, rank, world):
     K = args.steps
     bytes_per_pass = fluid_cells(L) / 4 * 576 + nnodes(L) * 44
     avg_pass_ms = vp_ms / max(vp_n, 1)
-    achieved = bytes_per_pass / (avg_pass_ms * 1e-3) / 1e9 if vp_n else 0.0
+    pass_gbs = bytes_per_pass / (avg_pass_ms * 1e-3) / 1e9 if vp_n else 0.0
+    # the dominant kernel of the DNN-MG step: the persistent sub-cycle of the
+    # small levels (if the plan has one and it takes longer), else the colour pass
+    plan = net_ctx.vcycle_plan()
+    if vs_n and vs_ms > vp_ms:
+        split = plan["split_level"]
+        kname = ("vcycle_kernel<float>" if plan["split_mode"] == 0 else
+                 "vcycle_cluster_kernel<float>")
+        dom_bytes = vcycle_bytes(split)
+        dom_ms = vs_ms / vs_n
+        dom = {"kernel": f"{kname} (V(2,2) sub-cycle of levels {split}..1, one launch)",
+               "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms,
+               "launches": vs_n,
+               "traffic": NCU_TRAFFIC.get(f"{kname}@split{split}")}
+    else:
+        dom = {"kernel": f"vanka_pass_tiled_kernel<float> (level {L}, one colour pass)",
+               "algorithmic_bytes_per_launch": bytes_per_pass, "avg_launch_ms": avg_pass_ms,
+               "launches": vp_n, "traffic": None}
+    achieved = dom["algorithmic_bytes_per_launch"] / (dom["avg_launch_ms"] * 1e-3) / 1e9
     f_fwd, f_train = net_flops()
     mean = lambda v: sum(v) / len(v)
     comparison = {
@@ -365,18 +394,28 @@ def run_ours(args, rank, world):
                                        f"{CORPUS_STEPS} steps (nu {NU_TRAIN})"},
         "comparison": comparison,
         "vcycle": {"split_level_dnnmg": net_ctx.vcycle_split(), "split_level_fine": ref_ctx.vcycle_split(),
+                   "plan_dnnmg": net_ctx.vcycle_plan(), "plan_fine": ref_ctx.vcycle_plan(),
                    "level6_ms": vc6, "level6_dof_per_s": ndof(6) / (vc6 * 1e-3),
                    "level6_gbs": vcycle_bytes(6) / (vc6 * 1e-3) / 1e9,
                    "level5_ms": vc5, "level5_dof_per_s": ndof(5) / (vc5 * 1e-3),
                    "level5_gbs": vcycle_bytes(5) / (vc5 * 1e-3) / 1e9},
         "stages_ms_dnnmg": stage,
-        "roofline": {"kernel": f"vanka_pass_tiled_kernel<float> (level {L}, one colour pass)",
-                     "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
-                     "algorithmic_bytes_per_launch": bytes_per_pass,
-                     "avg_launch_ms": avg_pass_ms, "launches": vp_n,
-                     "vcycle_level5_frac": vcycle_bytes(5) / (vc5 * 1e-3) / 1e9 / hbm,
-                     "vcycle_level6_frac": vcycle_bytes(6) / (vc6 * 1e-3) / 1e9 / hbm},
+        "roofline": {"kernel": dom["kernel"], "bound": "hbm", "achieved": achieved, "peak": hbm,
+                     "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,
+                     "traffic": dom["traffic"],
+                     "algorithmic_bytes_per_launch": dom["algorithmic_bytes_per_launch"],
+                     "avg_launch_ms": dom["avg_launch_ms"], "launches": dom["launches"],
+                     "timing": "CUDA events around each launch in a repeat of the timed steps",
+                     "others": {
+                         f"vanka_pass_tiled_kernel<float> level {L}": {
+                             "achieved_gbs": pass_gbs, "frac": pass_gbs / hbm,
+                             "avg_launch_ms": avg_pass_ms, "bytes_per_launch": bytes_per_pass},
+                         "V(2,2) cycle level 5 (whole cycle)": {
+                             "achieved_gbs": vcycle_bytes(5) / (vc5 * 1e-3) / 1e9,
+                             "frac": vcycle_bytes(5) / (vc5 * 1e-3) / 1e9 / hbm},
+                         "V(2,2) cycle level 6 (whole cycle)": {
+                             "achieved_gbs": vcycle_bytes(6) / (vc6 * 1e-3) / 1e9,
+                             "frac": vcycle_bytes(6) / (vc6 * 1e-3) / 1e9 / hbm}}},
         "network": {"forward_ms": infer_ms, "patches": P,
                     "forward_tflops": f_fwd * P / (infer_ms * 1e-3) / 1e12,
                     "forward_frac_bf16": f_fwd * P / (infer_ms * 1e-3) / 1e12 / bf16,
@@ -483,24 +522,94 @@ def run_batched(dn, torch, stream, flush, args, weights, feat_mean, feat_std, ra
 
 
 def run_vcycles(args):
-    """Level-6 V-cycles only (after --warmup untimed ones): a short command
-    for kernel profilers."""
+    """V-cycles on one level only (after --warmup untimed ones): a short
+    command for kernel profilers.  --level picks the level (default 6),
+    --split the persistent sub-cycle level (-1: autotuned)."""
     import torch
     from paper_2106_07687_gb300 import build, dnnmg as dn
     import synthetic
     build.build()
+    lev = args.level
     ob = synthetic.obstacle_block(1000)
-    ctx = dn.Context(level_solve=6, precision=dn.MIXED, nu=0.005, dt=DT, obstacle_i0=ob[0],
-                     obstacle_j0=ob[1])
+    kw = {} if args.split < 0 else dict(persistent_vcycle=args.split,
+                                        persistent_mode=args.split_mode)
+    ctx = dn.Context(level_solve=lev, precision=dn.MIXED, nu=0.005, dt=DT, obstacle_i0=ob[0],
+                     obstacle_j0=ob[1], **kw)
     x = ctx.get_state()
     ctx.linearize(x)
-    b = torch.from_numpy(synthetic.random_vector(7, ndof(6))).float().cuda()
+    b = torch.from_numpy(synthetic.random_vector(7, ndof(lev))).float().cuda()
     xv = torch.empty_like(b)
-    for _ in range(args.warmup + args.steps):
-        ctx.vcycle(6, b, xv)
+    for _ in range(args.warmup):
+        ctx.vcycle(lev, b, xv)
     torch.cuda.synchronize()
-    print(json.dumps({"mode": "vcycle", "level": 6, "cycles": args.warmup + args.steps,
-                      "norm": float(xv.norm())}))
+    torch.cuda.nvtx.range_push("vcycles")  # kernel profilers select these launches
+    for _ in range(args.steps):
+        ctx.vcycle(lev, b, xv)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"mode": "vcycle", "level": lev, "cycles": args.warmup + args.steps,
+                      "plan": ctx.vcycle_plan(), "norm": float(xv.norm())}))
+
+
+def run_net(args):
+    """Patch network only: --warmup + --steps inference passes over the
+    61,440 patches of the 1024x256 level, then as many training steps at the
+    benchmark's batch (random weights and data): a short command for kernel
+    profilers."""
+    import numpy as np
+    import torch
+    from paper_2106_07687_gb300 import build, dnnmg as dn
+    import synthetic
+    build.build()
+    ctx = dn.Context(level_solve=L, precision=dn.MIXED, nu=NU, dt=DT, train_batch=TRAIN_B,
+                     train_seq=TRAIN_T)
+    ctx.set_weights(synthetic.random_weights(77, ctx.num_params(), 0.05).astype(np.float32))
+    P = ctx.num_patches()
+    g = torch.Generator(device="cuda").manual_seed(5)
+    x = torch.randn(P, 40, device="cuda", generator=g).to(torch.bfloat16)
+    h = torch.zeros(2, P, 64, device="cuda")
+    out = torch.empty(P, 18, device="cuda")
+    X = torch.randn(TRAIN_B, TRAIN_T, 40, device="cuda", generator=g).to(torch.bfloat16)
+    Y = 0.01 * torch.randn(TRAIN_B, TRAIN_T, 18, device="cuda", generator=g)
+    for _ in range(args.warmup + args.steps):
+        ctx.patch_infer(x, h, out)
+    loss = [ctx.train_step(X, Y, TRAIN_B, TRAIN_T, 1e-4) for _ in range(args.warmup + args.steps)]
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "net", "patches": P, "train_batch": TRAIN_B, "train_seq": TRAIN_T,
+                      "loss_last": loss[-1]}))
+
+
+def summarize_launches(path):
+    """Per-kernel launches, total time and share of an ncu CSV launch list
+    (gpu__time_duration.sum per launch)."""
+    import collections
+    import csv
+    import re
+
+    def name(full):
+        t = full.replace("(anonymous namespace)", "").replace("<unnamed>", "")
+        t = re.sub(r"\(.*$", "", t)
+        t = re.sub(r"^void\s+", "", t.strip())
+        base = t.split("<")[0]
+        return base.split("::")[-1] + t[len(base):]
+
+    rows = list(csv.reader(open(path)))
+    hdr = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    h = rows[hdr]
+    ki, mi, vi, ui = (h.index(k) for k in ("Kernel Name", "Metric Name", "Metric Value",
+                                           "Metric Unit"))
+    scale = {"nsecond": 1e-3, "ns": 1e-3, "usecond": 1.0, "us": 1.0, "msecond": 1e3, "ms": 1e3}
+    agg = collections.defaultdict(lambda: [0, 0.0])
+    for r in rows[hdr + 1:]:
+        if len(r) <= vi or r[mi] != "gpu__time_duration.sum":
+            continue
+        a = agg[name(r[ki])]
+        a[0] += 1
+        a[1] += float(r[vi].replace(",", "")) * scale.get(r[ui], 1.0)
+    tot = sum(v[1] for v in agg.values())
+    print(f"{'kernel':44s} {'launches':>8s} {'total_us':>10s} {'share':>6s}")
+    for k, (n, t) in sorted(agg.items(), key=lambda kv: -kv[1][1]):
+        print(f"{k[:44]:44s} {n:8d} {t:10.1f} {100 * t / tot:5.1f}%")
 
 
 def run_reference(args, rank, world):
@@ -533,13 +642,27 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["step", "vcycle"], default="step",
-                    help="vcycle: only set up level 6 and run --steps V-cycles (profiling runs)")
+    ap.add_argument("--level", type=int, default=6, help="--mode vcycle: level")
+    ap.add_argument("--split", type=int, default=-1,
+                    help="fixed persistent V-cycle split level (-1: autotuned; 0: none)")
+    ap.add_argument("--split-mode", type=int, default=-1,
+                    help="with --split: 0 cooperative grid, 1 single cluster, -1 autotuned")
+    ap.add_argument("--summarize-launches", metavar="CSV", default=None,
+                    help="print the per-kernel table of an ncu launch list and exit")
+    ap.add_argument("--mode", choices=["step", "vcycle", "net"], default="step",
+                    help="vcycle: only V-cycles on --level; net: only the patch network "
+                         "(short runs for kernel profilers)")
     args = ap.parse_args()
+    if args.summarize_launches:
+        summarize_launches(args.summarize_launches)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.mode == "vcycle":
         run_vcycles(args)
+        return
+    if args.mode == "net":
+        run_net(args)
         return
     if args.impl == "reference":
         out = run_reference(args, rank, world)

@@ -5,14 +5,14 @@
  * (Sec. 2.1, Eq. 1 with the boundary conditions of Eq. 2) in a channel
  * [0,4] x [0,1] with a block obstacle, discretised by Q1/Q1 finite elements
  * with local projection stabilisation (Eqs. 4-5) on a hierarchy of uniformly
- * refined meshes.  Each time step solves A_n(x_n) = f_n (Eq. 6) by Newton's
- * method (Eq. 7) whose linear systems are solved by flexible GMRES
+ * refined meshes.  Each time step solves A_n(x_n) = f_n (Eq. 3) by Newton's
+ * method (Eq. 6) whose linear systems are solved by flexible GMRES
  * preconditioned with one geometric multigrid V-cycle (Sec. 2.2, Algorithm 1
  * lines 2-4).  In DNN-MG mode a patch-wise recurrent network (stacked GRUs +
  * dense layers, Sec. 2.2 and Sec. 3.1) predicts a velocity correction on the
  * level(s) above the finest solved one, which enters the next step through
  * the restricted right-hand side (Algorithm 1 lines 6-9); the network is
- * trained with the loss of Eq. 8.
+ * trained with the loss of Eq. 7.
  *
  * Conventions
  *  - Every function returns a status code (DNNMG_OK = 0).  On failure the
@@ -143,7 +143,7 @@ int dnnmg_set_state(dnnmg_ctx* ctx, const double* x);
 
 /* Linearise the multigrid hierarchy at the velocity of the FP64 device state
  * x ([3][nn] doubles on level L): the velocity is injected nodally to every
- * coarser level, every level's Jacobian A'(vbar) (Eq. 7) is set up (Vanka
+ * coarser level, every level's Jacobian A'(vbar) (Eq. 6) is set up (Vanka
  * inverses, coarse-level LU and inverse).  Needed before dnnmg_apply() and
  * dnnmg_vcycle(); dnnmg_step() does it itself.
  * Errors: DNNMG_ERR_NUMERICAL if a local Vanka matrix or the coarse matrix
@@ -166,7 +166,7 @@ int dnnmg_vcycle(dnnmg_ctx* ctx, int level, const void* b, void* x, int precisio
  * x, f, r: device [3][nn] doubles. */
 int dnnmg_residual(dnnmg_ctx* ctx, const double* x, const double* f, double* r);
 
-/* One time step (Eq. 6) from the context's state.  mode = DNNMG_PLAIN: the
+/* One time step (Eq. 3) from the context's state.  mode = DNNMG_PLAIN: the
  * right-hand side is the old-time term of Eq. 5; mode = DNNMG_NET: the step
  * uses the restricted right-hand side left by the previous DNN-MG step (if
  * any) and ends with Algorithm 1 lines 6-9 (prolongation, network, Rhs,
@@ -231,7 +231,7 @@ int dnnmg_gemm_bf16(dnnmg_ctx* ctx, const uint16_t* A, const uint16_t* B, float*
 
 /* ---- DNN-MG state (Algorithm 1 lines 6-9) -----------------------------------
  * A DNNMG_NET step ends with: v~ = P(v^L) on level L+1; the fine residual
- * r = f - A(v~, P p^L) of Eq. 6 on level L+1 with f built from the previous
+ * r = f - A(v~, P p^L) of Eq. 3 on level L+1 with f built from the previous
  * corrected fine velocity; the patch inputs; one network step (the hidden
  * state persists across steps); v_corr = v~ + d with d averaged over the
  * patches sharing a node and zero on Dirichlet nodes; b^{L+1} = Rhs(v_corr) =
@@ -253,9 +253,9 @@ int dnnmg_get_fine_velocity(dnnmg_ctx* ctx, double* v);
 /* Network inputs of the last DNN-MG step: device [P][C_in] bfloat16. */
 int dnnmg_get_patch_inputs(dnnmg_ctx* ctx, uint16_t* x);
 
-/* ---- training (Eq. 8, Sec. 3.1) -------------------------------------------------
+/* ---- training (Eq. 7, Sec. 3.1) -------------------------------------------------
  * One batch = B patch sequences of T steps; the hidden state starts at zero
- * for every sequence.  Loss = mean over (b, t, outputs) of (y - Y)^2 (Eq. 8
+ * for every sequence.  Loss = mean over (b, t, outputs) of (y - Y)^2 (Eq. 7
  * as a mean).  Gradients by backpropagation through time on the tensor
  * cores (BF16 operands, FP32 accumulation); weight gradients are split-K
  * GEMMs with a fixed-order reduction (deterministic).  The workspace is
@@ -313,7 +313,7 @@ int dnnmg_gather_batch(dnnmg_ctx* ctx, const float* X, const float* Y, const int
  * external memory manager owning the whole device heap, or inside a
  * real-time loop where an allocation and the synchronisation it may cause
  * are not allowed - and therefore cannot create a context.  It assembles the
- * Jacobian A'(vbar) (Eq. 7, with LPS) of level cfg->level_coarse, factors it
+ * Jacobian A'(vbar) (Eq. 6, with LPS) of level cfg->level_coarse, factors it
  * by banded LU with partial pivoting and returns x = A'(vbar)^{-1} b: the
  * same operator the coarse level of dnnmg_vcycle() inverts.
  *   cfg  : host pointer; uses nu, dt, theta (must be 1), alpha0, obstacle_i0,

@@ -9,11 +9,11 @@ matrices, and every solver step works on those matrices.
 
 Modules
   mesh    level hierarchy, obstacle, boundary masks (Sec. 2.1, Eq. 2)
-  fem     Q1/Q1 + LPS element matrices and assembly (Eqs. 4-6)
+  fem     Q1/Q1 + LPS element matrices and assembly (Eqs. 3-5)
   mg      transfers, cell-wise Vanka smoother, coarse LU, V-cycle (Sec. 2.2)
   krylov  flexible GMRES (Sec. 2.2)
-  newton  Newton time step (Eq. 7, Algorithm 1 lines 2-4)
-  net     patch GRU + dense network, BPTT backward, loss (Eq. 8), Adam
+  newton  Newton time step (Eq. 6, Algorithm 1 lines 2-4)
+  net     patch GRU + dense network, BPTT backward, loss (Eq. 7), Adam
   dnnmg   prolongation, network inputs, scatter, Rhs and restriction
           (Algorithm 1 lines 6-9)
 

@@ -5,7 +5,7 @@ Algorithm 1 lines 6-9 and Sec. 2.2: after the Newton solve on level L,
   7  d^{L+1}  = N(v~^{L+1}, Omega_L, Omega_{L+1})   (network, per patch)
   8  b^{L+1}_{n+1} = Rhs(v~^{L+1} + d^{L+1}, f_n, f_{n+1})
   9  b^L_{n+1} = R(b^{L+1}_{n+1})            (restriction to level L)
-The network input of a patch is the residual of Eq. 6 on level L+1, the
+The network input of a patch is the residual of Eq. 3 on level L+1, the
 prolongated velocity, geometric properties (aspect ratio) and the Peclet
 number over the patch; the output is a velocity correction only.
 
@@ -52,7 +52,7 @@ def patch_nodes(coarse, fine, ratio):
 
 
 def fine_residual(fine, xt, v_corr_prev, prm):
-    """Residual of Eq. 6 on the fine level at (v~, P p), velocity rows."""
+    """Residual of Eq. 3 on the fine level at (v~, P p), velocity rows."""
     f = fem.old_time_rhs(fine, v_corr_prev, prm)
     f[2 * fine.nn:] = 0.0
     x = xt.copy()

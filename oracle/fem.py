@@ -84,7 +84,7 @@ class Element:
 
 
 def element_jacobians(level, vbar, prm):
-    """12x12 Jacobians A'(vbar) of all fluid cells (Eq. 7), before LPS."""
+    """12x12 Jacobians A'(vbar) of all fluid cells (Eq. 6), before LPS."""
     el = Element(level.h)
     cells = level.fluid_cells
     nodes = level.cell_nodes[cells]
@@ -171,7 +171,7 @@ def constrain(level, A):
 
 
 def jacobian(level, vbar, prm):
-    """Global Jacobian A'_n(vbar) (Eq. 7) with LPS, constrained, CSR FP64."""
+    """Global Jacobian A'_n(vbar) (Eq. 6) with LPS, constrained, CSR FP64."""
     A = _assemble(level, element_jacobians(level, vbar, prm)) + lps_matrix(level, prm)
     return constrain(level, A)
 
@@ -240,7 +240,7 @@ def old_time_rhs(level, x_old, prm):
 
 
 def residual(level, x, f, prm, S=None):
-    """Nonlinear residual f_n - A_n(x) (Eq. 7 right-hand side), zero on
+    """Nonlinear residual f_n - A_n(x) (Eq. 6 right-hand side), zero on
     constrained DOFs."""
     r = f - operator(level, x, prm, S)
     r[level.cons] = 0.0

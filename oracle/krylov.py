@@ -1,6 +1,6 @@
 """Flexible GMRES with restarts (oracle, test only).
 
-Sec. 2.2 solves each Newton step (Eq. 7) with GMRES preconditioned by
+Sec. 2.2 solves each Newton step (Eq. 6) with GMRES preconditioned by
 geometric multigrid.  Because one V-cycle is used as the preconditioner (and
 in mixed precision it is not exactly a fixed linear map), the flexible,
 right-preconditioned variant is used: x = x0 + Z y with z_j = M^{-1} v_j.

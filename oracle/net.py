@@ -3,7 +3,7 @@
 Sec. 2.2 and Sec. 3.1: the network N acts on each patch separately, is
 recurrent with memory (stacked GRU cells, hidden size m, n cells stacked)
 and ends in dense layers that output the velocity correction d of the
-patch's fine nodes; it is trained with the loss of Eq. 8.
+patch's fine nodes; it is trained with the loss of Eq. 7.
 
 Readings:
   * GRU gates follow PyTorch (the paper used PyTorch, Sec. 3.1):
@@ -17,7 +17,7 @@ Readings:
     W_hh (3H x H), b_ih (3H), b_hh (3H); then W1 (F x H), b1 (F),
     W2 (C_out x F), b2 (C_out).  The bias-free variant of Table 1 simply
     drops the biases;
-  * loss (Eq. 8) as the mean over steps, patches and outputs of the squared
+  * loss (Eq. 7) as the mean over steps, patches and outputs of the squared
     difference (a mean instead of a sum only rescales the learning rate);
   * Adam with bias correction (the paper does not name its optimiser).
 
@@ -143,7 +143,7 @@ def sequence_forward(spec, p, X, bf16=False, h0=None, cache=None):
 
 
 def loss(Ypred, Y):
-    """Eq. 8 as a mean of squared differences."""
+    """Eq. 7 as a mean of squared differences."""
     return float(np.mean((Ypred - Y) ** 2))
 
 

@@ -1,6 +1,6 @@
 """Newton time stepping of the discrete Navier-Stokes system (oracle, test only).
 
-Eq. 6 / Eq. 7: each time step solves A_n(x_n) = f_n by Newton's method from
+Eq. 3 / Eq. 6: each time step solves A_n(x_n) = f_n by Newton's method from
 the initial guess x_{n-1}; every Newton correction w solves
 A'_n(x^{(l-1)}) w = f_n - A_n(x^{(l-1)}) by FGMRES preconditioned with one
 multigrid V-cycle (Sec. 2.2, Algorithm 1 lines 2-4), and the update is

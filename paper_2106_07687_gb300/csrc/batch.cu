@@ -1,6 +1,6 @@
 // Batched engine: many independent channel problems of uneven size (own
 // obstacle, viscosity, time step and finest level each) advanced by the same
-// time-step algorithm as a single context -- Newton's method (Eq. 7) with
+// time-step algorithm as a single context -- Newton's method (Eq. 6) with
 // right-preconditioned FGMRES and a multigrid V-cycle (Sec. 2.2), and for
 // DNN-MG steps the network correction of Algorithm 1 lines 6-9 -- with every
 // stage of every problem issued as one launch for the whole batch.

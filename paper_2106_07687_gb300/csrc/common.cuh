@@ -60,7 +60,7 @@ __device__ __forceinline__ void shape_at(int q, T phi[4], T dx[4], T dy[4]) {
 
 // Rows of local node a of one fluid cell, added to (ru, rv, rp).
 //   NONLIN = true : A(x) with x = (wu, wv, wp) (Eqs. 4-5), convection N(w)w.
-//   NONLIN = false: A'(vbar) w (Eq. 7), convection N(vbar)w + (w.grad)vbar.
+//   NONLIN = false: A'(vbar) w (Eq. 6), convection N(vbar)w + (w.grad)vbar.
 // The pressure row here holds the divergence only; LPS is added per patch.
 template <typename T, bool NONLIN>
 __device__ __forceinline__ void cell_rows(const Sten<T>& s, int a, const T wu[4], const T wv[4],
@@ -211,7 +211,7 @@ __device__ __forceinline__ void gauss_data(const T bu[4], const T bv[4], GaussDa
 }
 
 // Element Jacobian A'_T(vbar) entries between local nodes al (row) and be
-// (column): J[c][c'] for components (u, v, p) (Eq. 7, before LPS).
+// (column): J[c][c'] for components (u, v, p) (Eq. 6, before LPS).
 template <typename T>
 __device__ __forceinline__ void elem_pair(const Sten<T>& s, const GaussData<T>& gd, int al, int be,
                                           T J[3][3]) {

@@ -13,7 +13,7 @@ void note_launches(unsigned long long n);  // kernels of a replayed graph
 unsigned long long launches();
 
 // Operator rows (stencil.cu) ---------------------------------------------
-// y = A'(vbar) w on free DOFs, y = w on constrained DOFs (Eq. 7).
+// y = A'(vbar) w on free DOFs, y = w on constrained DOFs (Eq. 6).
 template <typename T>
 void launch_apply(const Grid& g, const Sten<T>& s, const T* w, const T* vb, T* y, cudaStream_t st);
 // d = b - A'(vbar) x with the same constrained handling; if `masked`,

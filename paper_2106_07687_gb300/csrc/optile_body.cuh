@@ -1,5 +1,5 @@
 // Tiled evaluation of the operator rows (Eqs. 4-5 and their linearisation,
-// Eq. 7) on a tile of TX x TY nodes: the block stages the field (and the
+// Eq. 6) on a tile of TX x TY nodes: the block stages the field (and the
 // linearisation velocity) of the tile plus a two-node halo in shared
 // memory, computes the 12 rows of every cell touching the tile once and the
 // 9 LPS rows of every patch touching it once, and each thread then sums the

@@ -1,5 +1,5 @@
 // Host runtime: multigrid V-cycle, flexible GMRES and Newton time step
-// (Sec. 2.2, Eq. 7, Algorithm 1 lines 2-4), sequencing the kernels of this
+// (Sec. 2.2, Eq. 6, Algorithm 1 lines 2-4), sequencing the kernels of this
 // library on the context's stream.
 #include <cmath>
 #include <algorithm>

@@ -1,5 +1,5 @@
 // Matrix-free operator kernels: Jacobian apply, defect, FP64 nonlinear
-// residual and the old-time right-hand side (Sec. 2.1, Eqs. 4-7).
+// residual and the old-time right-hand side (Sec. 2.1, Eqs. 3-6).
 //
 // Apply, defect and residual run tiled (32 x 8 nodes per block, cell and
 // patch rows computed once per tile, optile_body.cuh); the right-hand-side

@@ -1,4 +1,4 @@
-// Training of the patch network (Sec. 2.2 / Sec. 3.1): loss of Eq. 8 as a
+// Training of the patch network (Sec. 2.2 / Sec. 3.1): loss of Eq. 7 as a
 // mean of squared errors, backpropagation through time over T steps, and
 // Adam.  Weight gradients of a layer are sums over all (step, sequence)
 // columns of dG^T x, computed as split-K tcgen05 GEMMs on the transposed
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
       const size_t col = (size_t)step * B + p;
       const float* act = a.act + col * kAct;
       const float* actp = step > 0 ? a.act + (col - B) * kAct : nullptr;
-      // ---- loss and dY (Eq. 8 as a mean): dY = 2 (y - Y) / (B T C); output
+      // ---- loss and dY (Eq. 7 as a mean): dY = 2 (y - Y) / (B T C); output
       // columns 16 cq .. +15 (warpgroups 0 and 1)
       if (cq < 2) {
         float dy[16];

@@ -1,5 +1,5 @@
 // Vector kernels of the flexible GMRES solver (Sec. 2.2: GMRES preconditioned
-// by multigrid) and of the Newton update (Eq. 7).  Reductions accumulate in
+// by multigrid) and of the Newton update (Eq. 6).  Reductions accumulate in
 // FP64 and run in two fixed-order stages, so results are deterministic.
 #include <atomic>
 

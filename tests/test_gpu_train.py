@@ -1,4 +1,4 @@
-"""Training kernels of the patch network against the oracle (Eq. 8 loss,
+"""Training kernels of the patch network against the oracle (Eq. 7 loss,
 backpropagation through time, Adam).  The GPU path uses bfloat16 operands
 for every product, including the gate gradients fed to the weight-gradient
 GEMMs, while the oracle's gradient keeps them in FP64 (with the forward's

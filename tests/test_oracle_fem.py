@@ -1,4 +1,4 @@
-"""Pins of the oracle's discretisation (Sec. 2.1, Eqs. 4-7) to facts that do
+"""Pins of the oracle's discretisation (Sec. 2.1, Eqs. 3-6) to facts that do
 not come from the oracle itself: textbook Q1 element matrices, exact symbolic
 integrals, the discrete Poiseuille solution, finite differences and discrete
 mass conservation."""

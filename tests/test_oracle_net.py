@@ -1,4 +1,4 @@
-"""Pins of the oracle's patch network (Sec. 2.2, Sec. 3.1, Table 1, Eq. 8):
+"""Pins of the oracle's patch network (Sec. 2.2, Sec. 3.1, Table 1, Eq. 7):
 parameter counts of Table 1, forward pass against PyTorch's GRU and Linear in
 FP64, backward against central differences and PyTorch autograd, Adam
 against torch.optim.Adam, and bfloat16 rounding against torch's."""
