@@ -109,6 +109,13 @@ def rhs_and_restrict(coarse, fine, levels_between, v_corr, prm):
     return b, bL
 
 
+def prolongate_chain(chain, x):
+    """P applied once per level step of chain = [L, L+1, ..., fine]."""
+    for k in range(len(chain) - 1):
+        x = prolongate_state(chain[k], chain[k + 1], x)
+    return x
+
+
 def time_step(levels, fine, x_old, state, spec, params, prm, opt, mean=None, std=None,
               fallback_its=8, bf16=True):
     """One DNN-MG time step (Algorithm 1): Newton on level L with the
@@ -116,10 +123,18 @@ def time_step(levels, fine, x_old, state, spec, params, prm, opt, mean=None, std
     plain old-time term), redone without it if Newton needs more than
     `fallback_its` iterations (Sec. 3.3), then lines 6-9.
 
+    fine: the level above L (one replaced level) or the list of levels
+    [L+1, ..., L+r] that the network replaces (Sec. 2.2: one or multiple
+    finest levels); P and R are then applied once per replaced level and a
+    patch covers (2^r + 1)^2 nodes of level L+r.
+
     state: dict(bL, vcorr, h) from the previous step (None, None, zeros at
     the start).  Returns (x_new, new_state, info)."""
     from . import net, newton
     coarse = levels[-1]
+    chain = [coarse] + (list(fine) if isinstance(fine, (list, tuple)) else [fine])
+    fine = chain[-1]
+    ratio = 2 ** (len(chain) - 1)
     plain_f = fem.old_time_rhs(coarse, x_old, prm)
     f = state["bL"] if state["bL"] is not None else plain_f
     x, nit, git, nrm = newton.newton_solve(levels, x_old, f, prm, opt)
@@ -131,18 +146,18 @@ def time_step(levels, fine, x_old, state, spec, params, prm, opt, mean=None, std
     if state["vcorr"] is not None:
         vprev = state["vcorr"]
     else:
-        vprev = prolongate_state(coarse, fine, x_old)
+        vprev = prolongate_chain(chain, x_old)
         vprev[2 * nn:] = 0.0
-    xt = prolongate_state(coarse, fine, x)
+    xt = prolongate_chain(chain, x)
     r = fine_residual(fine, xt, vprev, prm)
-    X = patch_features(coarse, fine, 2, xt, r, prm, mean, std)
+    X = patch_features(coarse, fine, ratio, xt, r, prm, mean, std)
     if bf16:
         X = net.bf16_round(X)
     y, h = net.step_forward(spec, params, X, state["h"], bf16)
-    d = scatter_average(coarse, fine, 2, y)
+    d = scatter_average(coarse, fine, ratio, y)
     vcorr = xt.copy()
     vcorr[:2 * nn] += d
     vcorr[2 * nn:] = 0.0
-    _, bL = rhs_and_restrict(coarse, fine, [coarse, fine], vcorr, prm)
+    _, bL = rhs_and_restrict(coarse, fine, chain, vcorr, prm)
     info = dict(newton_its=nit, gmres_its=git, res=nrm, fallback=fallback, X=X, y=y)
     return x, dict(bL=bL, vcorr=vcorr, h=h), info

@@ -83,3 +83,58 @@ def test_patch_count_of_the_dnnmg_workload():
     coarse = mesh.Level(5, obstacle=(2, 1))
     assert coarse.nx * coarse.ny == 65536
     assert len(coarse.fluid_cells) == 65536 - 4096
+
+
+def test_two_replaced_levels_step_with_zero_network_equals_plain_step():
+    """Algorithm 1 with the network replacing two levels (5x5-node patches,
+    104 inputs, 50 outputs) and an all-zero network: the step after the
+    first one uses b^L = R R Rhs(P P v^L), which is the plain old-time term,
+    so the trajectory equals plain MG(L)."""
+    from oracle import net
+    levels = mesh.hierarchy(2, obstacle=(2, 1))
+    chain = [mesh.Level(3, obstacle=(2, 1)), mesh.Level(4, obstacle=(2, 1))]
+    prm = fem.Params(nu=0.01, dt=0.01)
+    opt = newton.SolverOptions(newton_tol=1e-12)
+    spec = net.NetSpec(c_in=104, c_out=50)
+    params = spec.unflatten(np.zeros(spec.num_params()))
+    P = len(levels[-1].fluid_cells)
+    state = dict(bL=None, vcorr=None, h=np.zeros((2, P, 64)))
+    x_dnn = x_plain = mesh.initial_state(levels[-1])
+    for n in range(3):
+        x_dnn, state, info = dnnmg.time_step(levels, chain, x_dnn, state, spec, params, prm, opt)
+        x_plain, *_ = newton.time_step(levels, x_plain, prm, opt)
+        assert info["X"].shape == (P, 104) and info["y"].shape == (P, 50)
+        assert not info["fallback"]
+        assert np.linalg.norm(x_dnn - x_plain) < 1e-10 * np.linalg.norm(x_plain), n
+
+
+def test_five_by_five_patches_and_scatter():
+    """Two replaced levels: a patch is one level-L cell = 4x4 cells = 5x5
+    nodes of level L+2; interior nodes shared by 1, 2 or 4 patches; a
+    constant prediction scatters to the same constant."""
+    coarse, fine = mesh.Level(1, obstacle=None), mesh.Level(3, obstacle=None)
+    nodes = dnnmg.patch_nodes(coarse, fine, 4)
+    assert nodes.shape == (coarse.nx * coarse.ny, 25)
+    # lower-left patch: nodes (s, t), s, t in 0..4 of the fine level
+    np.testing.assert_array_equal(nodes[0], [t * fine.nnx + s for t in range(5) for s in range(5)])
+    cnt = np.bincount(nodes.ravel(), minlength=fine.nn)
+    i, j = np.arange(fine.nn) % fine.nnx, np.arange(fine.nn) // fine.nnx
+    on_x = (i % 4 == 0) & (i > 0) & (i < fine.nx)
+    on_y = (j % 4 == 0) & (j > 0) & (j < fine.ny)
+    expect = np.where(on_x & on_y, 4, np.where(on_x | on_y, 2, 1))
+    np.testing.assert_array_equal(cnt, expect)
+    P = nodes.shape[0]
+    d = np.concatenate([np.full((P, 25), 0.3), np.full((P, 25), -1.1)], axis=1)
+    out = dnnmg.scatter_average(coarse, fine, 4, d)
+    ok = ~fine.vdir.ravel()
+    np.testing.assert_allclose(out[:fine.nn][ok], 0.3, rtol=1e-15)
+    np.testing.assert_allclose(out[fine.nn:][ok], -1.1, rtol=1e-15)
+    xt = np.concatenate([np.full(fine.nn, 0.6), np.full(fine.nn, 0.8), np.zeros(fine.nn)])
+    prm = fem.Params(nu=0.02, dt=0.005)
+    X = dnnmg.patch_features(coarse, fine, 4, xt, np.zeros(fine.ndof), prm)
+    assert X.shape == (P, 104)
+    np.testing.assert_allclose(X[:, :25], 0.6)
+    np.testing.assert_allclose(X[:, 25:50], 0.8)
+    np.testing.assert_allclose(X[:, 100], coarse.h / 0.25)
+    np.testing.assert_allclose(X[:, 102], 1.0 * coarse.h / prm.nu)
+    np.testing.assert_allclose(X[:, 103], prm.dt / coarse.h)
