@@ -195,16 +195,19 @@ int dnnmg_prolongate(dnnmg_ctx* ctx, int level, const double* xc, double* xf);
 /* ---- patch network (Sec. 2.2, Sec. 3.1, Table 1) ------------------------------
  * Two stacked GRU cells (hidden 64, PyTorch gate convention r, z, n) and a
  * dense head Linear(64, 128) + ReLU + Linear(128, C_out), applied to every
- * patch independently.  With one replaced level a patch is one level-L cell:
- * C_in = 40 inputs (prolongated velocity u, v and fine velocity residual
- * r_u, r_v at its 3x3 fine nodes, then 4 geometry/flow features), C_out = 18
- * outputs (velocity correction u, v at the 3x3 nodes).  Weights are BF16 on
+ * patch independently.  A patch is one level-L cell; with r replaced levels
+ * it covers K x K nodes of level L + r (K = 3 for r = 1, 5 for r = 2):
+ * C_in = 4 K^2 + 4 inputs (prolongated velocity u, v and fine velocity
+ * residual r_u, r_v at its K x K fine nodes, then 4 geometry/flow features:
+ * 40 or 104), C_out = 2 K^2 outputs (velocity correction u, v at the nodes:
+ * 18 or 50).  Weights are BF16 on
  * the tensor cores with FP32 accumulation; the hidden state is FP32.
  * Flat FP32 parameter order (PyTorch's): per GRU layer W_ih [192][C_l],
  * W_hh [192][64], b_ih [192], b_hh [192]; then W1 [128][64], b1 [128],
  * W2 [C_out][128], b2 [C_out].  A new context has all weights zero. */
 
-/* Number of network parameters (55,954 for C_in = 40, C_out = 18). */
+/* Number of network parameters (55,954 for C_in = 40, C_out = 18; 72,370
+ * for C_in = 104, C_out = 50). */
 size_t dnnmg_num_params(const dnnmg_ctx* ctx);
 
 /* Network input and output widths of the context. */
@@ -230,13 +233,14 @@ int dnnmg_gemm_bf16(dnnmg_ctx* ctx, const uint16_t* A, const uint16_t* B, float*
                     int K);
 
 /* ---- DNN-MG state (Algorithm 1 lines 6-9) -----------------------------------
- * A DNNMG_NET step ends with: v~ = P(v^L) on level L+1; the fine residual
- * r = f - A(v~, P p^L) of Eq. 3 on level L+1 with f built from the previous
- * corrected fine velocity; the patch inputs; one network step (the hidden
- * state persists across steps); v_corr = v~ + d with d averaged over the
- * patches sharing a node and zero on Dirichlet nodes; b^{L+1} = Rhs(v_corr) =
- * (1/k) M v_corr; and b^L = R b^{L+1}, the velocity right-hand side of the
- * next step.  Patches are the fluid cells of level L in cell order
+ * A DNNMG_NET step ends with: v~ = P(v^L) on the fine level F = L + r (P
+ * applied once per replaced level); the fine residual r = f - A(v~, P p^L)
+ * of Eq. 3 on level F with f built from the previous corrected fine
+ * velocity; the patch inputs; one network step (the hidden state persists
+ * across steps); v_corr = v~ + d with d averaged over the patches sharing a
+ * node and zero on Dirichlet nodes; b^F = Rhs(v_corr) = (1/k) M v_corr; and
+ * b^L = R b^F (R once per replaced level), the velocity right-hand side of
+ * the next step.  Patches are the fluid cells of level L in cell order
  * (j * nx + i). */
 
 /* Number of patches (fluid cells of level L). */
@@ -247,7 +251,8 @@ int dnnmg_num_patches(const dnnmg_ctx* ctx);
 int dnnmg_set_feature_stats(dnnmg_ctx* ctx, const float* mean, const float* std);
 
 /* Corrected fine velocity v_corr of the last DNN-MG step: device
- * [2][nn of level L+1] doubles.  DNNMG_ERR_STATE before the first one. */
+ * [2][nn of level L + replaced_levels] doubles.  DNNMG_ERR_STATE before the
+ * first one. */
 int dnnmg_get_fine_velocity(dnnmg_ctx* ctx, double* v);
 
 /* Network inputs of the last DNN-MG step: device [P][C_in] bfloat16. */
@@ -281,14 +286,15 @@ int dnnmg_reset_optimizer(dnnmg_ctx* ctx);
 /* ---- training corpus from plain fine-level trajectories (Sec. 3.1) ----------
  * Training data comes from high-fidelity solutions on level L+1, localised
  * to the time steps and patches.  Given two consecutive fine states
- * x^{L+1}_{n-1}, x^{L+1}_n (device [3][nn of level L+1] doubles, e.g. from a
- * second context with level_solve = L+1), dnnmg_make_sample injects
- * x^{L+1}_{n-1} to level L, solves the level-L step with the right-hand side
- * an exact correction would give, b^L = R (1/k) M^{L+1} v^{L+1}_{n-1}, and
- * writes for every patch the raw (unstandardised) inputs at P(v^L_n)
- * (device [P][C_in] float) and the targets v^{L+1}_n - P(v^L_n) at its fine
- * nodes, zero on Dirichlet nodes (device [P][C_out] float).  It overwrites the
- * context's level-L state and clears its DNN-MG state. */
+ * x^F_{n-1}, x^F_n on the fine level F = L + replaced_levels (device
+ * [3][nn of level F] doubles, e.g. from a second context with
+ * level_solve = F), dnnmg_make_sample injects x^F_{n-1} to level L, solves
+ * the level-L step with the right-hand side an exact correction would give,
+ * b^L = R (1/k) M^F v^F_{n-1} (R once per replaced level), and writes for
+ * every patch the raw (unstandardised) inputs at P(v^L_n) (device [P][C_in]
+ * float) and the targets v^F_n - P(v^L_n) at its fine nodes, zero on
+ * Dirichlet nodes (device [P][C_out] float).  It overwrites the context's
+ * level-L state and clears its DNN-MG state. */
 int dnnmg_make_sample(dnnmg_ctx* ctx, const double* xf_prev, const double* xf_next, float* X,
                       float* Y, dnnmg_step_stats* stats);
 

@@ -502,7 +502,7 @@ __global__ void bgather_kernel(BView<T> v, int P, const int* __restrict__ pinst,
   const BPar pr = v.par[p];
   const BLev<T>& L = lev_of(v, p, pr.L);
   const BLev<T>& F = lev_of(v, p, pr.L + 1);
-  gather_patch<false>(L.g, F.g, pcell[q], xt + F.off, r + F.off, mean, stdv, pr.nu, pr.dt,
+  gather_patch<false, 3>(L.g, F.g, pcell[q], xt + F.off, r + F.off, mean, stdv, pr.nu, pr.dt,
                       X + (size_t)q * 40, nullptr);
 }
 
@@ -517,7 +517,7 @@ __global__ void __launch_bounds__(kNB)
   const BLev<T> F = lev_of(v, wk.x, pr.L + 1), L = lev_of(v, wk.x, pr.L);
   const int n = wk.y * kNB + threadIdx.x;
   if (n >= F.g.nn) return;
-  scatter_node(L.g, F.g, cell_patch + pr.coff, out, c_out, xt + F.off, vcorr + F.off,
+  scatter_node<3>(L.g, F.g, cell_patch + pr.coff, out, c_out, xt + F.off, vcorr + F.off,
                n % F.g.nnx, n / F.g.nnx);
 }
 

@@ -2,13 +2,14 @@
 // the single-problem kernels (dnnmg_step.cu) and the batched kernels
 // (batch.cu).
 //
-// A patch is one fluid cell (I, J) of the finest solved level L; with one
-// replaced level it covers the 3x3 nodes (2I+s, 2J+t), s, t in 0..2, of
-// level L+1 (local index m = s + 3t).  Input features per patch (C_in = 40):
-//   [0,9)  prolongated u at the 9 nodes      [9,18)  prolongated v
-//   [18,27) fine residual of the u rows       [27,36) fine residual of v rows
-//   36: h_L / 0.25   37: aspect ratio h_x/h_y = 1   38: Peclet number
-//   |mean prolongated velocity over the patch| * h_L / nu   39: k / h_L
+// A patch is one fluid cell (I, J) of the finest solved level L; with r
+// replaced levels it covers the K x K nodes (S I + s, S J + t), s, t in
+// 0..S, of level L + r, with S = 2^r and K = S + 1 (local index
+// m = s + K t): 3x3 nodes for one replaced level, 5x5 for two.  Input
+// features per patch (C_in = 4 K^2 + 4: 40 or 104):
+//   prolongated u at the K^2 nodes, prolongated v, fine residual of the u
+//   rows, of the v rows, then h_L / 0.25, aspect ratio h_x/h_y = 1, Peclet
+//   number |mean prolongated velocity over the patch| * h_L / nu, k / h_L,
 // each standardised as (value - mean) / std and rounded to bfloat16.
 #pragma once
 #include <cuda_bf16.h>
@@ -30,65 +31,72 @@ __device__ __forceinline__ void impose_dirichlet_node(const Grid& g, double* __r
   if (f & kPFix) x[2 * g.nn + n] = 0.0;
 }
 
-// the 40 network inputs of the patch on level-L cell `cell`: standardised
-// BF16 into X[0..40) or, if RAW, unstandardised FP32 into Xraw[0..40)
-template <bool RAW>
+// The network inputs of the patch on level-L cell `cell` whose K x K nodes
+// (K = 2^r + 1 for r replaced levels: 3 or 5) lie on level L + r, in the
+// order [u at the K^2 nodes, v, residual u, residual v, h_L / 0.25,
+// aspect ratio 1, Peclet number, k / h_L] (4 K^2 + 4 values): standardised
+// BF16 into X or, if RAW, unstandardised FP32 into Xraw.
+template <bool RAW, int K>
 __device__ __forceinline__ void gather_patch(const Grid& gL, const Grid& gF, int cell,
                                              const double* __restrict__ xt,
                                              const double* __restrict__ r,
                                              const float* __restrict__ mean,
                                              const float* __restrict__ stdv, double nu, double dt,
                                              uint16_t* __restrict__ X, float* __restrict__ Xraw) {
+  constexpr int K2 = K * K, C = 4 * K2 + 4, S = K - 1;
   const int I = cell % gL.nx, J = cell / gL.nx;
-  float f[40];
+  float f[C];
   double su = 0, sv = 0;
 #pragma unroll
-  for (int m = 0; m < 9; ++m) {
-    const int n = (2 * J + m / 3) * gF.nnx + 2 * I + m % 3;
+  for (int m = 0; m < K2; ++m) {
+    const int n = (S * J + m / K) * gF.nnx + S * I + m % K;
     const double u = xt[n], v = xt[gF.nn + n];
     su += u;
     sv += v;
     f[m] = (float)u;
-    f[9 + m] = (float)v;
-    f[18 + m] = (float)r[n];
-    f[27 + m] = (float)r[gF.nn + n];
+    f[K2 + m] = (float)v;
+    f[2 * K2 + m] = (float)r[n];
+    f[3 * K2 + m] = (float)r[gF.nn + n];
   }
   const double hL = gL.h;
-  f[36] = (float)(hL / 0.25);
-  f[37] = 1.0f;
-  f[38] = (float)(sqrt(su * su + sv * sv) / 9.0 * hL / nu);
-  f[39] = (float)(dt / hL);
+  f[4 * K2] = (float)(hL / 0.25);
+  f[4 * K2 + 1] = 1.0f;
+  f[4 * K2 + 2] = (float)(sqrt(su * su + sv * sv) / K2 * hL / nu);
+  f[4 * K2 + 3] = (float)(dt / hL);
   if (RAW) {
 #pragma unroll
-    for (int k = 0; k < 40; ++k) Xraw[k] = f[k];
+    for (int k = 0; k < C; ++k) Xraw[k] = f[k];
     return;
   }
 #pragma unroll
-  for (int k = 0; k < 40; ++k)
+  for (int k = 0; k < C; ++k)
     X[k] = __bfloat16_as_ushort(__float2bfloat16_rn((f[k] - mean[k]) / stdv[k]));
 }
 
 // v_corr = xt + d at fine node (i, j), d = mean of the predictions of the
-// patches containing the node, zero on velocity Dirichlet nodes; pressure 0.
+// patches containing the node (K x K-node patches, K = 3 or 5), zero on
+// velocity Dirichlet nodes; pressure 0.
+template <int K>
 __device__ __forceinline__ void scatter_node(const Grid& gL, const Grid& gF,
                                              const int* __restrict__ cell_patch,
                                              const float* __restrict__ out, int c_out,
                                              const double* __restrict__ xt,
                                              double* __restrict__ vcorr, int i, int j) {
+  constexpr int S = K - 1, K2 = K * K;
   const int n = j * gF.nnx + i;
   double du = 0, dv = 0;
   int cnt = 0;
   for (int dJ = 0; dJ < 2; ++dJ) {
-    const int J = (j >> 1) - dJ;
-    if (J < 0 || J >= gL.ny || j - 2 * J > 2) continue;
+    const int J = j / S - dJ;
+    if (J < 0 || J >= gL.ny || j - S * J > S) continue;
     for (int dI = 0; dI < 2; ++dI) {
-      const int I = (i >> 1) - dI;
-      if (I < 0 || I >= gL.nx || i - 2 * I > 2) continue;
+      const int I = i / S - dI;
+      if (I < 0 || I >= gL.nx || i - S * I > S) continue;
       const int p = cell_patch[J * gL.nx + I];
       if (p < 0) continue;
-      const int m = (i - 2 * I) + 3 * (j - 2 * J);
+      const int m = (i - S * I) + K * (j - S * J);
       du += out[(size_t)p * c_out + m];
-      dv += out[(size_t)p * c_out + 9 + m];
+      dv += out[(size_t)p * c_out + K2 + m];
       ++cnt;
     }
   }
@@ -97,6 +105,24 @@ __device__ __forceinline__ void scatter_node(const Grid& gL, const Grid& gF,
   vcorr[n] = xt[n] + du;
   vcorr[gF.nn + n] = xt[gF.nn + n] + dv;
   vcorr[2 * gF.nn + n] = 0.0;
+}
+
+// Training target of a patch: (next fine velocity - prolongated velocity)
+// at its K x K nodes, zero on velocity Dirichlet nodes.
+template <int K>
+__device__ __forceinline__ void target_patch(const Grid& gL, const Grid& gF, int cell,
+                                             const double* __restrict__ xnext,
+                                             const double* __restrict__ xt,
+                                             float* __restrict__ Y) {
+  constexpr int S = K - 1, K2 = K * K;
+  const int I = cell % gL.nx, J = cell / gL.nx;
+#pragma unroll
+  for (int m = 0; m < K2; ++m) {
+    const int n = (S * J + m / K) * gF.nnx + S * I + m % K;
+    const bool dir = gF.flags[n] & kVDir;
+    Y[m] = dir ? 0.0f : (float)(xnext[n] - xt[n]);
+    Y[K2 + m] = dir ? 0.0f : (float)(xnext[gF.nn + n] - xt[gF.nn + n]);
+  }
 }
 
 }  // namespace dnnmg

@@ -27,35 +27,26 @@ __global__ void impose_dirichlet_kernel(Grid g, double* __restrict__ x) {
   impose_dirichlet_node(g, x, i, j);
 }
 
-template <bool RAW>
+template <bool RAW, int K>
 __global__ void gather_kernel(Grid gL, Grid gF, const int* __restrict__ patch_cell, int P,
                               const double* __restrict__ xt, const double* __restrict__ r,
                               const float* __restrict__ mean, const float* __restrict__ stdv,
                               double nu, double dt, uint16_t* __restrict__ X,
                               float* __restrict__ Xraw) {
+  constexpr int C = 4 * K * K + 4;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
-  gather_patch<RAW>(gL, gF, patch_cell[p], xt, r, mean, stdv, nu, dt,
-                    RAW ? nullptr : X + (size_t)p * 40, RAW ? Xraw + (size_t)p * 40 : nullptr);
+  gather_patch<RAW, K>(gL, gF, patch_cell[p], xt, r, mean, stdv, nu, dt,
+                       RAW ? nullptr : X + (size_t)p * C, RAW ? Xraw + (size_t)p * C : nullptr);
 }
 
-// Training target of a patch: (next fine velocity - prolongated velocity) at
-// its 3x3 nodes, zero on velocity Dirichlet nodes (where the correction is
-// forced to zero).
+template <int K>
 __global__ void target_kernel(Grid gL, Grid gF, const int* __restrict__ patch_cell, int P,
                               const double* __restrict__ xnext, const double* __restrict__ xt,
                               float* __restrict__ Y) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
-  const int cell = patch_cell[p];
-  const int I = cell % gL.nx, J = cell / gL.nx;
-#pragma unroll
-  for (int m = 0; m < 9; ++m) {
-    const int n = (2 * J + m / 3) * gF.nnx + 2 * I + m % 3;
-    const bool dir = gF.flags[n] & kVDir;
-    Y[(size_t)p * 18 + m] = dir ? 0.0f : (float)(xnext[n] - xt[n]);
-    Y[(size_t)p * 18 + 9 + m] = dir ? 0.0f : (float)(xnext[gF.nn + n] - xt[gF.nn + n]);
-  }
+  target_patch<K>(gL, gF, patch_cell[p], xnext, xt, Y + (size_t)p * 2 * K * K);
 }
 
 // Per-feature sums (x, x^2) over row chunks: partial[block][C][2] (FP64).
@@ -120,12 +111,13 @@ __global__ void gather_batch_kernel(const float* __restrict__ Xraw, const float*
   }
 }
 
+template <int K>
 __global__ void scatter_kernel(Grid gL, Grid gF, const int* __restrict__ cell_patch,
                                const float* __restrict__ out, int c_out,
                                const double* __restrict__ xt, double* __restrict__ vcorr) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   if (i >= gF.nnx || j >= gF.nny) return;
-  scatter_node(gL, gF, cell_patch, out, c_out, xt, vcorr, i, j);
+  scatter_node<K>(gL, gF, cell_patch, out, c_out, xt, vcorr, i, j);
 }
 
 inline dim3 grid_of(const Grid& g) { return dim3(cdiv(g.nnx, kBX), cdiv(g.nny, kBY)); }
@@ -137,29 +129,40 @@ void launch_impose_dirichlet64(const Grid& g, double* x, cudaStream_t st) {
   impose_dirichlet_kernel<<<grid_of(g), dim3(kBX, kBY), 0, st>>>(g, x);
 }
 
-void launch_gather(const Grid& gL, const Grid& gF, const int* patch_cell, int P, const double* xt,
-                   const double* r, const float* mean, const float* stdv, double nu, double dt,
-                   uint16_t* X, cudaStream_t st) {
+void launch_gather(const Grid& gL, const Grid& gF, int K, const int* patch_cell, int P,
+                   const double* xt, const double* r, const float* mean, const float* stdv,
+                   double nu, double dt, uint16_t* X, cudaStream_t st) {
   if (P <= 0) return;
   note_launch();
-  gather_kernel<false><<<cdiv(P, 128), 128, 0, st>>>(gL, gF, patch_cell, P, xt, r, mean, stdv, nu,
-                                                     dt, X, nullptr);
+  if (K == 5)
+    gather_kernel<false, 5><<<cdiv(P, 128), 128, 0, st>>>(gL, gF, patch_cell, P, xt, r, mean,
+                                                          stdv, nu, dt, X, nullptr);
+  else
+    gather_kernel<false, 3><<<cdiv(P, 128), 128, 0, st>>>(gL, gF, patch_cell, P, xt, r, mean,
+                                                          stdv, nu, dt, X, nullptr);
 }
 
-void launch_gather_raw(const Grid& gL, const Grid& gF, const int* patch_cell, int P,
+void launch_gather_raw(const Grid& gL, const Grid& gF, int K, const int* patch_cell, int P,
                        const double* xt, const double* r, double nu, double dt, float* Xraw,
                        cudaStream_t st) {
   if (P <= 0) return;
   note_launch();
-  gather_kernel<true><<<cdiv(P, 128), 128, 0, st>>>(gL, gF, patch_cell, P, xt, r, nullptr, nullptr,
-                                                    nu, dt, nullptr, Xraw);
+  if (K == 5)
+    gather_kernel<true, 5><<<cdiv(P, 128), 128, 0, st>>>(gL, gF, patch_cell, P, xt, r, nullptr,
+                                                         nullptr, nu, dt, nullptr, Xraw);
+  else
+    gather_kernel<true, 3><<<cdiv(P, 128), 128, 0, st>>>(gL, gF, patch_cell, P, xt, r, nullptr,
+                                                         nullptr, nu, dt, nullptr, Xraw);
 }
 
-void launch_targets(const Grid& gL, const Grid& gF, const int* patch_cell, int P,
+void launch_targets(const Grid& gL, const Grid& gF, int K, const int* patch_cell, int P,
                     const double* xnext, const double* xt, float* Y, cudaStream_t st) {
   if (P <= 0) return;
   note_launch();
-  target_kernel<<<cdiv(P, 128), 128, 0, st>>>(gL, gF, patch_cell, P, xnext, xt, Y);
+  if (K == 5)
+    target_kernel<5><<<cdiv(P, 128), 128, 0, st>>>(gL, gF, patch_cell, P, xnext, xt, Y);
+  else
+    target_kernel<3><<<cdiv(P, 128), 128, 0, st>>>(gL, gF, patch_cell, P, xnext, xt, Y);
 }
 
 void launch_feature_stats(const float* X, long long rows, int C, double* partial, int nb,
@@ -177,10 +180,15 @@ void launch_gather_batch(const float* Xraw, const float* Yc, const int* idx, int
   gather_batch_kernel<<<1024, 256, 0, st>>>(Xraw, Yc, idx, B, T, stride, Ci, Co, mean, stdv, Xb, Yb);
 }
 
-void launch_scatter(const Grid& gL, const Grid& gF, const int* cell_patch, const float* out,
+void launch_scatter(const Grid& gL, const Grid& gF, int K, const int* cell_patch, const float* out,
                     int c_out, const double* xt, double* vcorr, cudaStream_t st) {
   note_launch();
-  scatter_kernel<<<grid_of(gF), dim3(kBX, kBY), 0, st>>>(gL, gF, cell_patch, out, c_out, xt, vcorr);
+  if (K == 5)
+    scatter_kernel<5><<<grid_of(gF), dim3(kBX, kBY), 0, st>>>(gL, gF, cell_patch, out, c_out, xt,
+                                                              vcorr);
+  else
+    scatter_kernel<3><<<grid_of(gF), dim3(kBX, kBY), 0, st>>>(gL, gF, cell_patch, out, c_out, xt,
+                                                              vcorr);
 }
 
 }  // namespace dnnmg

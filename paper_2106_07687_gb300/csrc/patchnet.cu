@@ -71,19 +71,26 @@ __global__ void pack_bias_kernel(const float* __restrict__ w, NetDims d, float* 
 }
 
 // -- shared-memory plan of the forward kernel ---------------------------------
+// Operand regions are reused as soon as the MMA that reads them has
+// completed:
+//   a: x_t (layer 0 input, kx0 columns), then layer 0's new state (layer 1
+//      input, 64 columns);
+//   b: h0 (layer 0 hidden operand), then layer 1's new state (dense head input);
+//   c: h1 (layer 1 hidden operand);
+//   m: the dense head's hidden layer (128 columns), over a and b.
 struct FwdSmem {
-  uint32_t w, bias, x, h0, h1, t, m, bar, tmem, total;
+  uint32_t w, bias, a, b, c, m, bar, tmem, total;
   static __host__ __device__ uint32_t up(uint32_t v) { return (v + 127u) & ~127u; }
   static __host__ __device__ FwdSmem of(const NetDims& d, size_t w_elems) {
     FwdSmem s{};
     uint32_t o = 0;
     s.w = o;    o = up(o + (uint32_t)(w_elems * 2));
     s.bias = o; o = up(o + (uint32_t)((d.layers * 4 * d.hidden + d.mlp + d.nout()) * 4));
-    s.x = o;    o = up(o + kTile * d.kx0() * 2);
-    s.h0 = o;   o = up(o + kTile * 64 * 2);
-    s.h1 = o;   o = up(o + kTile * 64 * 2);
-    s.t = o;    o = up(o + kTile * 64 * 2);
-    s.m = o;    o = up(o + kTile * 128 * 2);
+    const uint32_t asz = kTile * (d.kx0() > 64 ? d.kx0() : 64) * 2;  // >= 16 KB
+    s.a = o;    o += asz;
+    s.b = o;    o += kTile * 64 * 2;    // a and b are contiguous: m needs 32 KB of them
+    s.m = s.a;
+    s.c = o;    o += kTile * 64 * 2;
     s.bar = o;  o += 16;
     s.tmem = o; o += 16;
     s.total = o;
@@ -250,7 +257,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
           uint4 v = make_uint4(0, 0, 0, 0);
           const bool in = pr < P && q * 8 < d.c_in;
           if (in) v = reinterpret_cast<const uint4*>(a.x + ((size_t)pr * T + step) * d.c_in)[q];
-          *reinterpret_cast<uint4*>(sm + S.x + kmajor_offset(r, q * 8, kx0)) = v;
+          *reinterpret_cast<uint4*>(sm + S.a + kmajor_offset(r, q * 8, kx0)) = v;
           if (TRAIN && in) {
             const uint16_t* ev = reinterpret_cast<const uint16_t*>(&v);
             const size_t cr = (size_t)step * P + pr;
@@ -258,8 +265,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
           }
         }
       }
-      store_row16(sm + S.h0, row, u0, 64, h0r);
-      store_row16(sm + S.h1, row, u0, 64, h1r);
+      store_row16(sm + S.b, row, u0, 64, h0r);
+      store_row16(sm + S.c, row, u0, 64, h1r);
       // ---- two GRU layers (unrolled, so that each layer's state stays in
       // registers)
 #pragma unroll
@@ -267,9 +274,9 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         fence_async_smem();
         fence_before_sync();
         __syncthreads();
-        const uint32_t ax = sbase + (l == 0 ? S.x : S.t);
+        const uint32_t ax = sbase + S.a;  // x_t, then layer 0's new state
         const int kx = l == 0 ? kx0 : 64;
-        const uint32_t ah = sbase + (l == 0 ? S.h0 : S.h1);
+        const uint32_t ah = sbase + (l == 0 ? S.b : S.c);
         if (t == 0) {
           fence_after_sync();
           mma_run(tbase + 0, ax, kx, sbase + S.w + 2 * L.rz[l], kx, 128, kx, false);
@@ -285,11 +292,12 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
           break;
         }
         fence_after_sync();
-        // layer 0 writes its new state into S.t (layer 1 input); layer 1 into
-        // S.h0 (free after layer 0) as the dense head's input
+        // layer 0 writes its new state into region a (x_t has been consumed)
+        // as layer 1's input; layer 1 into region b (h0 has been consumed) as
+        // the dense head's input
         float* hout = TRAIN ? act + kActH0 + l * 64 : a.h_out + l * HP + (size_t)p * 64;
         uint16_t* hT = TRAIN ? (l == 0 ? a.h0T : a.h1T) + ldh - ld + col : nullptr;
-        gru_epilogue(tm, bias + l * 4 * 64, l == 0 ? h0r : h1r, sm + (l == 0 ? S.t : S.h0), row,
+        gru_epilogue(tm, bias + l * 4 * 64, l == 0 ? h0r : h1r, sm + (l == 0 ? S.a : S.b), row,
                      u0, hout, valid, TRAIN ? act + kActG0 + l * 256 : nullptr, hT, ldh);
       }
       if (failed) break;
@@ -299,7 +307,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
       __syncthreads();
       if (t == 0) {
         fence_after_sync();
-        mma_run(tbase + 0, sbase + S.h0, 64, sbase + S.w + 2 * L.w1, 64, 128, 64, false);
+        mma_run(tbase + 0, sbase + S.b, 64, sbase + S.w + 2 * L.w1, 64, 128, 64, false);
         mma_commit(bar);
       }
       if (!mbar_wait(bar, phase, kWaitPolls)) failed = true;

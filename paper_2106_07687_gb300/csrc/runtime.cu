@@ -491,7 +491,7 @@ int dnnmg_ctx::init() {
   if (!mem.ok()) return fail(DNNMG_ERR_CUDA, "device allocation failed");
   s64L = make_sten<double>(gL.h, cfg);
   sxL = make_explicit_sten(gL.h, cfg);
-  if ((int)lv.size() > L() + 1) sxF = make_explicit_sten(grid(L() + 1).h, cfg);
+  if (cfg.replaced_levels > 0) sxF = make_explicit_sten(grid(fine_level()).h, cfg);
   const std::vector<double> x0 = initial_state(gL);
   cudaMemcpyAsync(x64, x0.data(), n3 * sizeof(double), cudaMemcpyHostToDevice, st);
   cudaStreamSynchronize(st);
@@ -513,7 +513,7 @@ int dnnmg_ctx::init_train() {
   tr_blocks_max = sms;
   tr_splits_max = 160;
   tb.act = mem.alloc<float>(K * kAct);
-  tb.xT = mem.alloc<uint16_t>(48 * K);
+  tb.xT = mem.alloc<uint16_t>((size_t)(nd.kx0() + 16) * K);
   tb.h0T = mem.alloc<uint16_t>(80 * Kh);
   tb.h1T = mem.alloc<uint16_t>(80 * Kh);
   tb.y1T = mem.alloc<uint16_t>(144 * K);
@@ -557,7 +557,7 @@ int dnnmg_ctx::train_grad_impl(const uint16_t* Xd, const float* Yd, int B, int T
     return fail(DNNMG_ERR_ARG, "need B % 16 == 0, 16 <= B <= train_batch, 1 <= T <= train_seq");
   const size_t K = (size_t)B * T, Kh = (size_t)(T + 1) * B;
   if (B != tr_layout_B || T != tr_layout_T) {
-    cudaMemsetAsync(tb.xT, 0, 2 * 48 * K, st);
+    cudaMemsetAsync(tb.xT, 0, 2 * (size_t)(nd.kx0() + 16) * K, st);
     cudaMemsetAsync(tb.h0T, 0, 2 * 80 * Kh, st);
     cudaMemsetAsync(tb.h1T, 0, 2 * 80 * Kh, st);
     cudaMemsetAsync(tb.y1T, 0, 2 * 144 * K, st);
@@ -599,7 +599,8 @@ int dnnmg_ctx::train_grad_impl(const uint16_t* Xd, const float* Yd, int B, int T
                ob1 = oW1 + (size_t)nd.mlp * H, oW2 = ob1 + nd.mlp,
                ob2 = oW2 + (size_t)nd.c_out * nd.mlp;
   const WGradJob jobs[] = {
-      {gi0T, tb.xT, K, K, 256, 48, 3 * H, nd.c_in, nd.c_in, grad + oWih0, grad + obih0},
+      {gi0T, tb.xT, K, K, 256, (nd.c_in + 1 + 15) / 16 * 16, 3 * H, nd.c_in, nd.c_in,
+       grad + oWih0, grad + obih0},
       {gh0T, tb.h0T, K, Kh, 256, 80, 3 * H, H, H, grad + oWhh0, grad + obhh0},
       {gi1T, tb.h0T + B, K, Kh, 256, 80, 3 * H, H, H, grad + oWih1, grad + obih1},
       {gh1T, tb.h1T, K, Kh, 256, 80, 3 * H, H, H, grad + oWhh1, grad + obhh1},
@@ -640,7 +641,7 @@ int dnnmg_ctx::train_step(const uint16_t* X, const float* Y, int B, int T, float
 
 // Patch lists and level L+1 buffers of the DNN-MG correction.
 int dnnmg_ctx::init_dnnmg() {
-  if (cfg.replaced_levels != 1 || !net_ok) return DNNMG_OK;  // NET steps report it
+  if (cfg.replaced_levels < 1 || !net_ok) return DNNMG_OK;  // NET steps report it
   const HostLevel& hl = lv[L()];
   std::vector<int> pc, cp(hl.solid.size(), -1);
   for (size_t c = 0; c < hl.solid.size(); ++c)
@@ -649,8 +650,12 @@ int dnnmg_ctx::init_dnnmg() {
       pc.push_back((int)c);
     }
   P = (int)pc.size();
-  const Grid gF = grid(L() + 1);
+  const Grid gF = grid(fine_level());
   const size_t n3 = 3 * (size_t)gF.nn;
+  if (cfg.replaced_levels == 2) {  // intermediate level L+1 of the transfers
+    midF = mem.alloc<double>(3 * (size_t)grid(L() + 1).nn);
+    if (!midF) return fail(DNNMG_ERR_CUDA, "device allocation failed");
+  }
   patch_cell = mem.alloc<int>(P);
   cell_patch = mem.alloc<int>(cp.size());
   xtF = mem.alloc<double>(n3);
@@ -678,26 +683,54 @@ int dnnmg_ctx::init_dnnmg() {
   return check("dnnmg setup");
 }
 
+// P applied once per replaced level: xc on level L -> xf on the fine level
+// (ncomp fields; midF holds the level L+1 values when two levels are replaced)
+void dnnmg_ctx::prolong_up(const double* xc, double* xf, int ncomp) {
+  const Grid gL = grid(L()), gF = grid(fine_level());
+  if (cfg.replaced_levels == 2) {
+    const Grid gM = grid(L() + 1);
+    launch_prolong_state64(gM, gL, xc, midF, ncomp, st);
+    launch_prolong_state64(gF, gM, midF, xf, ncomp, st);
+  } else {
+    launch_prolong_state64(gF, gL, xc, xf, ncomp, st);
+  }
+}
+
+// R = P^T once per replaced level, velocity fields: bf on the fine level ->
+// bc on level L (pressure rows 0)
+void dnnmg_ctx::restrict_down(const double* bf, double* bc) {
+  const Grid gL = grid(L()), gF = grid(fine_level());
+  cudaMemsetAsync(bc, 0, 3 * sizeof(double) * gL.nn, st);
+  if (cfg.replaced_levels == 2) {
+    const Grid gM = grid(L() + 1);
+    cudaMemsetAsync(midF, 0, 3 * sizeof(double) * gM.nn, st);
+    launch_restrict_full64(gF, gM, bf, midF, 2, st);
+    launch_restrict_full64(gM, gL, midF, bc, 2, st);
+  } else {
+    launch_restrict_full64(gF, gL, bf, bc, 2, st);
+  }
+}
+
 // Algorithm 1 lines 6-9 after the level-L solve of this step (x64 = v^L_n).
 int dnnmg_ctx::dnnmg_correction() {
-  const Grid gL = grid(L()), gF = grid(L() + 1);
+  const Grid gL = grid(L()), gF = grid(fine_level());
   const size_t n3F = 3 * (size_t)gF.nn;
+  const int K = (1 << cfg.replaced_levels) + 1;
   const int pr = prof.begin(DNNMG_STAGE_NETWORK, L(), st);
   if (!have_vcorr) {  // first correction: the previous fine velocity is P(v^L_{n-1})
-    launch_prolong_state64(gF, gL, xold64, vcorr, 2, st);
+    prolong_up(xold64, vcorr, 2);
     cudaMemsetAsync(vcorr + 2 * gF.nn, 0, sizeof(double) * gF.nn, st);
   }
-  launch_prolong_state64(gF, gL, x64, xtF, 3, st);                     // line 6
-  old_rhs(L() + 1, vcorr, fF);
+  prolong_up(x64, xtF, 3);                                            // line 6
+  old_rhs(fine_level(), vcorr, fF);
   cudaMemcpyAsync(ximpF, xtF, n3F * sizeof(double), cudaMemcpyDeviceToDevice, st);
   launch_impose_dirichlet64(gF, ximpF, st);
   launch_residual64(gF, s64F, ximpF, fF, rF, st);                     // input: fine residual
-  launch_gather(gL, gF, patch_cell, P, xtF, rF, feat_mean, feat_std, cfg.nu, cfg.dt, X, st);
+  launch_gather(gL, gF, K, patch_cell, P, xtF, rF, feat_mean, feat_std, cfg.nu, cfg.dt, X, st);
   launch_patchnet_forward(nd, pk, X, hid, hid, net_out, P, net_status, st);  // line 7
-  launch_scatter(gL, gF, cell_patch, net_out, nd.c_out, xtF, vcorr, st);
-  old_rhs(L() + 1, vcorr, bF);                                        // line 8
-  cudaMemsetAsync(bL, 0, 3 * sizeof(double) * gL.nn, st);
-  launch_restrict_full64(gF, gL, bF, bL, 2, st);                      // line 9
+  launch_scatter(gL, gF, K, cell_patch, net_out, nd.c_out, xtF, vcorr, st);
+  old_rhs(fine_level(), vcorr, bF);                                   // line 8
+  restrict_down(bF, bL);                                              // line 9
   prof.end(pr, st);
   have_vcorr = have_net_rhs = true;
   return net_check("dnnmg correction");
@@ -709,27 +742,33 @@ int dnnmg_ctx::dnnmg_correction() {
 // then the network inputs at P(v^L_n) and the targets v^{L+1}_n - P(v^L_n).
 int dnnmg_ctx::make_sample(const double* xf_prev, const double* xf_next, float* Xraw, float* Y,
                            dnnmg_step_stats* s) {
-  if (!X) return fail(DNNMG_ERR_STATE, "DNN-MG needs replaced_levels = 1 and the default network");
-  const Grid gL = grid(L()), gF = grid(L() + 1);
+  if (!X) return fail(DNNMG_ERR_STATE, "DNN-MG needs replaced_levels 1 or 2 and the default network");
+  const Grid gL = grid(L()), gF = grid(fine_level());
   const size_t n3L = 3 * (size_t)gL.nn;
-  launch_inject<double>(gF, gL, xf_prev, x64, 3, st);
+  const int K = (1 << cfg.replaced_levels) + 1;
+  if (cfg.replaced_levels == 2) {  // nodal injection fine -> L+1 -> L
+    const Grid gM = grid(L() + 1);
+    launch_inject<double>(gF, gM, xf_prev, midF, 3, st);
+    launch_inject<double>(gM, gL, midF, x64, 3, st);
+  } else {
+    launch_inject<double>(gF, gL, xf_prev, x64, 3, st);
+  }
   launch_impose_dirichlet64(gL, x64, st);
   cudaMemcpyAsync(xold64, x64, n3L * sizeof(double), cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(vcorr, xf_prev, 2 * sizeof(double) * gF.nn, cudaMemcpyDeviceToDevice, st);
   cudaMemsetAsync(vcorr + 2 * gF.nn, 0, sizeof(double) * gF.nn, st);
-  old_rhs(L() + 1, vcorr, fF);
-  cudaMemsetAsync(f64, 0, n3L * sizeof(double), st);
-  launch_restrict_full64(gF, gL, fF, f64, 2, st);
+  old_rhs(fine_level(), vcorr, fF);
+  restrict_down(fF, f64);
   dnnmg_step_stats tmp{};
   steps_taken = 0;  // a new state: refactor the coarse level
   int rc = newton(f64, s ? s : &tmp);
   if (rc != DNNMG_OK && rc != DNNMG_ERR_NOT_CONVERGED) return rc;
-  launch_prolong_state64(gF, gL, x64, xtF, 3, st);
+  prolong_up(x64, xtF, 3);
   cudaMemcpyAsync(ximpF, xtF, 3 * sizeof(double) * gF.nn, cudaMemcpyDeviceToDevice, st);
   launch_impose_dirichlet64(gF, ximpF, st);
   launch_residual64(gF, s64F, ximpF, fF, rF, st);
-  launch_gather_raw(gL, gF, patch_cell, P, xtF, rF, cfg.nu, cfg.dt, Xraw, st);
-  launch_targets(gL, gF, patch_cell, P, xf_next, xtF, Y, st);
+  launch_gather_raw(gL, gF, K, patch_cell, P, xtF, rF, cfg.nu, cfg.dt, Xraw, st);
+  launch_targets(gL, gF, K, patch_cell, P, xf_next, xtF, Y, st);
   have_net_rhs = have_vcorr = false;
   steps_taken = 0;
   cudaStreamSynchronize(st);
@@ -767,7 +806,7 @@ int dnnmg_ctx::set_feature_stats(const float* mean, const float* stdv) {
 
 int dnnmg_ctx::get_fine_velocity(double* v) {
   if (!have_vcorr) return fail(DNNMG_ERR_STATE, "no DNN-MG step taken yet");
-  cudaMemcpyAsync(v, vcorr, 2 * sizeof(double) * grid(L() + 1).nn, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(v, vcorr, 2 * sizeof(double) * grid(fine_level()).nn, cudaMemcpyDeviceToDevice, st);
   cudaStreamSynchronize(st);
   return check("get_fine_velocity");
 }
@@ -932,8 +971,8 @@ int dnnmg_ctx::step(int mode, dnnmg_step_stats* stats) {
   dnnmg_step_stats s{};
   const Grid gL = grid(L());
   const size_t n3 = 3 * (size_t)gL.nn;
-  if (mode == DNNMG_NET && (cfg.replaced_levels != 1 || !net_ok || !X))
-    return fail(DNNMG_ERR_ARG, "DNN-MG steps need replaced_levels = 1 and the default network");
+  if (mode == DNNMG_NET && (cfg.replaced_levels < 1 || !net_ok || !X))
+    return fail(DNNMG_ERR_ARG, "DNN-MG steps need replaced_levels 1 or 2 and the default network");
   cudaEventRecord(ev0, st);
   cudaMemcpyAsync(xold64, x64, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
   const bool use_net_rhs = mode == DNNMG_NET && have_net_rhs;

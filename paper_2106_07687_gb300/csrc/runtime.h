@@ -171,6 +171,7 @@ struct dnnmg_ctx {
   dnnmg::Sten<double> s64F{};
   double *xtF = nullptr, *ximpF = nullptr, *fF = nullptr, *rF = nullptr, *vcorr = nullptr,
          *bF = nullptr, *bL = nullptr;
+  double* midF = nullptr;  // level L+1 transfer buffer with two replaced levels
   uint16_t* X = nullptr;
   float *net_out = nullptr, *hid = nullptr, *feat_mean = nullptr, *feat_std = nullptr;
   bool have_net_rhs = false, have_vcorr = false;
@@ -194,6 +195,8 @@ struct dnnmg_ctx {
   int check(const char* what);
   dnnmg::Grid grid(int level) const { return lv[level].g; }
   int L() const { return cfg.level_solve; }
+  // the level the network corrects: L + replaced_levels
+  int fine_level() const { return cfg.level_solve + cfg.replaced_levels; }
   int lc() const { return cfg.level_coarse; }
   double norm64(const double* v, size_t n);  // synchronous
 
@@ -213,6 +216,8 @@ struct dnnmg_ctx {
   // f = old-time right-hand side of Eq. 5 from x_old on level `level`
   void old_rhs(int level, const double* x_old, double* f);
   int dnnmg_correction();
+  void prolong_up(const double* xc, double* xf, int ncomp);
+  void restrict_down(const double* bf, double* bc);
   int set_feature_stats(const float* mean, const float* stdv);
   int get_fine_velocity(double* v);
   int get_patch_inputs(uint16_t* x);

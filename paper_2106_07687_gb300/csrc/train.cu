@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
   const uint32_t sb = smem_u32(sm);
   uint8_t* R1 = sm + S.r1;
   uint8_t* R2 = sm + S.r2;
-  const int B = a.B, T = a.T, C = d.c_out;
+  const int B = a.B, T = a.T, C = d.c_out, NO = d.nout();
   const size_t ld = (size_t)T * B;
   const int u0 = 16 * cq;  // this thread's 16 hidden units
   uint32_t phase = 0;
@@ -175,8 +175,8 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
       const float* act = a.act + col * kAct;
       const float* actp = step > 0 ? a.act + (col - B) * kAct : nullptr;
       // ---- loss and dY (Eq. 7 as a mean): dY = 2 (y - Y) / (B T C); output
-      // columns 16 cq .. +15 (warpgroups 0 and 1)
-      if (cq < 2) {
+      // columns 16 cq .. +15 (one 16-column chunk of the nout per warpgroup)
+      if (cq < NO / 16) {
         float dy[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) dy[i] = 0.0f;
@@ -191,9 +191,9 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
             a.dyT[(size_t)j * ld + col] = f2bf(dy[i]);
           }
         }
-        store_row16(R1, row, 16 * cq, 32, dy);
+        store_row16(R1, row, 16 * cq, NO, dy);
       }
-      sync_mma([&] { mma_run(tbase + 0, sb + S.r1, 32, sb + S.w + 2 * BwdPack::kW2T, 32, 128, 32); });
+      sync_mma([&] { mma_run(tbase + 0, sb + S.r1, NO, sb + S.w + 2 * BwdPack::kW2T, NO, 128, NO); });
       if (failed) break;
       // ---- dense head: da1 = (dY W2) * [a1 > 0], 32 of the 128 units
 #pragma unroll
@@ -459,7 +459,7 @@ void launch_pack_backward(const NetDims& d, const float* w, uint16_t* wT, cudaSt
   const float* W1 = Whh1 + (size_t)3 * H * H + 6 * H;
   const float* W2 = W1 + (size_t)d.mlp * H + d.mlp;
   note_launch();
-  pack_transpose_kernel<<<64, 256, 0, st>>>(W2, d.mlp, 128, 32, d.c_out, wT + BwdPack::kW2T);
+  pack_transpose_kernel<<<64, 256, 0, st>>>(W2, d.mlp, 128, d.nout(), d.c_out, wT + BwdPack::kW2T);
   note_launch();
   pack_transpose_kernel<<<64, 256, 0, st>>>(W1, H, 64, 128, 128, wT + BwdPack::kW1T);
   note_launch();

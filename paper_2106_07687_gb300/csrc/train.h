@@ -10,8 +10,8 @@ namespace dnnmg {
 // Element offsets of the transposed BF16 weight operands used by the
 // backward pass (B operands of dY W2, dA1 W1, dG_h W_hh, dG_i W_ih1).
 struct BwdPack {
-  static constexpr int kW2T = 0;                 // [128][32]  W2^T
-  static constexpr int kW1T = kW2T + 128 * 32;   // [64][128]  W1^T
+  static constexpr int kW2T = 0;                 // [128][nout <= 64]  W2^T
+  static constexpr int kW1T = kW2T + 128 * 64;   // [64][128]  W1^T
   static constexpr int kWhh0T = kW1T + 64 * 128; // [64][192]  W_hh0^T
   static constexpr int kWhh1T = kWhh0T + 64 * 192;
   static constexpr int kWih1T = kWhh1T + 64 * 192;

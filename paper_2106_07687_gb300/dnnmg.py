@@ -257,7 +257,7 @@ class Context:
                                                      c_void_p(s.data_ptr())))
 
     def get_fine_velocity(self):
-        nx, ny = self.level_dims(self.cfg.level_solve + 1)
+        nx, ny = self.level_dims(self.cfg.level_solve + self.cfg.replaced_levels)
         v = torch.empty(2 * (nx + 1) * (ny + 1), dtype=torch.float64, device="cuda")
         self._check(self.lib.dnnmg_get_fine_velocity(self.h, _ptr(v)))
         return v

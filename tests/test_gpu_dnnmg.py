@@ -81,3 +81,51 @@ def test_fallback_drops_the_network_rhs():
     b.step(dn.PLAIN)
     assert st["fallback"] == 1
     assert rel(a.get_state().cpu().numpy(), b.get_state().cpu().numpy()) < 1e-10
+
+
+def test_two_replaced_levels_dnnmg_steps_match_oracle():
+    """The network replaces levels L+1 and L+2 (5x5-node patches, 104
+    inputs, 50 outputs): P and R act twice, the fine residual and the
+    right-hand side live on level L+2."""
+    dn = lib()
+    ob = synthetic.obstacle_block(1001)
+    ctx = _ctx(dn, ob, replaced_levels=2)
+    spec = net.NetSpec(c_in=104, c_out=50)
+    assert ctx.net_dims() == (104, 50)
+    w = synthetic.random_weights(12, spec.num_params(), 0.05).astype(np.float32)
+    ctx.set_weights(w)
+    rng = np.random.default_rng(6)
+    mean = rng.normal(0, 0.1, 104).astype(np.float32)
+    std = rng.uniform(0.5, 2.0, 104).astype(np.float32)
+    ctx.set_feature_stats(mean, std)
+    levels = mesh.hierarchy(L, obstacle=ob)
+    chain = [mesh.Level(L + 1, obstacle=ob), mesh.Level(L + 2, obstacle=ob)]
+    fine = chain[-1]
+    opt = newton.SolverOptions(newton_tol=1e-12)
+    prm = fem.Params(nu=NU, dt=DT)
+    params = spec.unflatten(w.astype(np.float64))
+    x = mesh.initial_state(levels[-1])
+    state = dict(bL=None, vcorr=None, h=np.zeros((2, len(levels[-1].fluid_cells), 64)))
+    P = ctx.num_patches()
+    for n in range(3):
+        st = ctx.step(dn.NET)
+        x, state, info = dnnmg.time_step(levels, chain, x, state, spec, params, prm, opt,
+                                         mean.astype(np.float64), std.astype(np.float64))
+        assert rel(ctx.get_state().cpu().numpy(), x) < 1e-4, n
+        vg = ctx.get_fine_velocity().cpu().numpy()
+        assert vg.size == 2 * fine.nn
+        assert rel(vg, state["vcorr"][:2 * fine.nn]) < 1e-4, n
+        Xg = torch.empty(P, 104, dtype=torch.bfloat16, device="cuda")
+        ctx.lib.dnnmg_get_patch_inputs(ctx.h, dn._ptr(Xg))
+        assert rel(Xg.double().cpu().numpy(), info["X"]) < 5e-3, n
+        assert st["fallback"] == int(info["fallback"])
+
+
+def test_two_replaced_levels_zero_network_equals_plain_multigrid():
+    dn = lib()
+    ob = synthetic.obstacle_block(1000)
+    a, b = _ctx(dn, ob, replaced_levels=2), _ctx(dn, ob)
+    for n in range(3):
+        a.step(dn.NET)
+        b.step(dn.PLAIN)
+        assert rel(a.get_state().cpu().numpy(), b.get_state().cpu().numpy()) < 1e-10, n

@@ -23,14 +23,15 @@ torch = pytest.importorskip("torch")
 L, DT = 2, 0.01
 
 
-def test_make_sample_matches_oracle():
+@pytest.mark.parametrize("replaced", [1, 2])
+def test_make_sample_matches_oracle(replaced):
     dn = lib()
     ob = synthetic.obstacle_block(1000)
     nu = 0.01
-    fine_ctx = dn.Context(level_solve=L + 1, precision=dn.FP64, obstacle_i0=ob[0],
+    fine_ctx = dn.Context(level_solve=L + replaced, precision=dn.FP64, obstacle_i0=ob[0],
                           obstacle_j0=ob[1], nu=nu, dt=DT, newton_tol=1e-12)
     ctx = dn.Context(level_solve=L, precision=dn.FP64, obstacle_i0=ob[0], obstacle_j0=ob[1],
-                     nu=nu, dt=DT, newton_tol=1e-12)
+                     nu=nu, dt=DT, newton_tol=1e-12, replaced_levels=replaced)
     for _ in range(2):
         fine_ctx.step(dn.PLAIN)
     xp = fine_ctx.get_state()
@@ -39,19 +40,22 @@ def test_make_sample_matches_oracle():
     X, Y = ctx.make_sample(xp, xn)
     # oracle
     levels = mesh.hierarchy(L, obstacle=ob)
-    coarse, fine = levels[-1], mesh.Level(L + 1, obstacle=ob)
+    chain = [levels[-1]] + [mesh.Level(L + k, obstacle=ob) for k in range(1, replaced + 1)]
+    coarse, fine = chain[0], chain[-1]
+    ratio = 2 ** replaced
     prm = fem.Params(nu=nu, dt=DT)
     xp_h, xn_h = xp.cpu().numpy(), xn.cpu().numpy()
-    xL = np.concatenate([mg.inject(xp_h[c * fine.nn:(c + 1) * fine.nn][None].ravel(), coarse, fine, 1)
-                         for c in range(3)])
+    xL = xp_h
+    for k in range(replaced, 0, -1):   # nodal injection, one level at a time
+        xL = mg.inject(xL, chain[k - 1], chain[k], 3)
     vprev = xp_h.copy()
     vprev[2 * fine.nn:] = 0.0
-    _, bL = dnnmg.rhs_and_restrict(coarse, fine, [coarse, fine], vprev, prm)
+    _, bL = dnnmg.rhs_and_restrict(coarse, fine, chain, vprev, prm)
     x, *_ = newton.newton_solve(levels, xL, bL, prm, newton.SolverOptions(newton_tol=1e-12))
-    xt = dnnmg.prolongate_state(coarse, fine, x)
+    xt = dnnmg.prolongate_chain(chain, x)
     r = dnnmg.fine_residual(fine, xt, vprev, prm)
-    Xr = dnnmg.patch_features(coarse, fine, 2, xt, r, prm)
-    nodes = dnnmg.patch_nodes(coarse, fine, 2)
+    Xr = dnnmg.patch_features(coarse, fine, ratio, xt, r, prm)
+    nodes = dnnmg.patch_nodes(coarse, fine, ratio)
     vd = fine.vdir.ravel()[nodes]
     Yr = np.concatenate([np.where(vd, 0, xn_h[:fine.nn][nodes] - xt[:fine.nn][nodes]),
                          np.where(vd, 0, xn_h[fine.nn:2 * fine.nn][nodes] - xt[fine.nn:2 * fine.nn][nodes])],

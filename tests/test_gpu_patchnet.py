@@ -33,17 +33,21 @@ def _weights(spec, seed, scale=0.25):
     return synthetic.random_weights(seed, spec.num_params(), scale).astype(np.float32)
 
 
-@pytest.mark.parametrize("P,seed", [(1, 1), (128, 2), (1000, 3), (61440, 4)])
-def test_patch_infer_matches_oracle(P, seed):
+@pytest.mark.parametrize("P,seed,replaced", [(1, 1, 1), (128, 2, 1), (1000, 3, 1), (61440, 4, 1),
+                                             (1, 5, 2), (1000, 6, 2), (61440, 7, 2)])
+def test_patch_infer_matches_oracle(P, seed, replaced):
+    """One replaced level: 3x3-node patches, 40 inputs, 18 outputs; two:
+    5x5-node patches, 104 inputs, 50 outputs."""
     dn = lib()
-    ctx = dn.Context(level_solve=2)
-    spec = net.NetSpec()
-    assert ctx.num_params() == spec.num_params() == 55954
-    assert ctx.net_dims() == (40, 18)
+    ctx = dn.Context(level_solve=2, replaced_levels=replaced)
+    k = 2 ** replaced + 1
+    spec = net.NetSpec(c_in=4 * k * k + 4, c_out=2 * k * k)
+    assert ctx.num_params() == spec.num_params() == (55954 if replaced == 1 else 72370)
+    assert ctx.net_dims() == (spec.c_in, spec.c_out)
     w = _weights(spec, seed)
     ctx.set_weights(w)
     np.testing.assert_array_equal(ctx.get_weights().numpy(), w)
-    x = net.bf16_round(synthetic.random_patch_inputs(seed, (P, 40)))
+    x = net.bf16_round(synthetic.random_patch_inputs(seed, (P, spec.c_in)))
     h = synthetic.random_patch_inputs(seed + 1, (2, P, 64), 0.5).astype(np.float32).astype(np.float64)
     xg = torch.from_numpy(x).to(torch.bfloat16).cuda()
     hg = torch.from_numpy(h).float().cuda()

@@ -16,8 +16,8 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def _ctx(dn, B, T):
-    return dn.Context(level_solve=2, train_batch=B, train_seq=T)
+def _ctx(dn, B, T, replaced=1):
+    return dn.Context(level_solve=2, train_batch=B, train_seq=T, replaced_levels=replaced)
 
 
 def _grad(ctx, dn, X, Y, B, T):
@@ -29,15 +29,17 @@ def _grad(ctx, dn, X, Y, B, T):
     return g.double().cpu().numpy(), loss.value
 
 
-@pytest.mark.parametrize("B,T", [(16, 1), (32, 3), (144, 4)])
-def test_gradient_matches_oracle(B, T):
+@pytest.mark.parametrize("B,T,replaced", [(16, 1, 1), (32, 3, 1), (144, 4, 1), (48, 3, 2)])
+def test_gradient_matches_oracle(B, T, replaced):
+    """Also for the two-replaced-level network (104 inputs, 50 outputs)."""
     dn = lib()
-    ctx = _ctx(dn, 160, 4)
-    spec = net.NetSpec()
+    ctx = _ctx(dn, 160, 4, replaced)
+    k = 2 ** replaced + 1
+    spec = net.NetSpec(c_in=4 * k * k + 4, c_out=2 * k * k)
     w = synthetic.random_weights(B + T, spec.num_params(), 0.2).astype(np.float32)
     ctx.set_weights(w)
-    X = net.bf16_round(synthetic.random_patch_inputs(B * 10 + T, (B, T, 40)))
-    Y = synthetic.random_patch_inputs(B * 10 + T + 1, (B, T, 18), 0.3)
+    X = net.bf16_round(synthetic.random_patch_inputs(B * 10 + T, (B, T, spec.c_in)))
+    Y = synthetic.random_patch_inputs(B * 10 + T + 1, (B, T, spec.c_out), 0.3)
     Xg = torch.from_numpy(X).to(torch.bfloat16).cuda().contiguous()
     Yg = torch.from_numpy(Y).float().cuda().contiguous()
     g, loss = _grad(ctx, dn, Xg, Yg, B, T)
