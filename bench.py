@@ -31,6 +31,7 @@ METRIC = "time/step & V-cycle DOF/s: DNN-MG vs plain MG on 1 GB300 at equal L2 e
 L, NU, DT = 5, 0.0065, 0.005
 NU_TRAIN = (0.005, 0.008)
 CORPUS_STEPS, TRAIN_ITERS, TRAIN_B, TRAIN_T = 24, 150, 16384, 10
+LARGE_CORPUS_STEPS, LARGE_TRAIN_ITERS = 16, 100  # two replaced levels
 WORKLOAD = ("DNN-MG time step: multigrid on the 512x128 channel (level 5, 198,531 DOFs) + patch "
             "network on 1024x256 (level 6, 61,440 patches, GRU 2x64 + MLP 128, BF16), nu=0.0065, "
             "dt=0.005, mixed FP32/FP64")
@@ -174,6 +175,117 @@ def net_flops(c_in=40, H=64, mlp=128, c_out=18):
     return 2 * fwd, 2 * (fwd + act + fwd)
 
 
+def train_network(dn, torch, stream, common, level, replaced, nu, nus_train, corpus_steps, iters):
+    """Corpus from plain trajectories on level `level + replaced` (one per
+    viscosity in nus_train, `corpus_steps` steps each), feature statistics,
+    and `iters` Adam steps at batch TRAIN_B x TRAIN_T, all with the library's
+    kernels.  Returns (context, mean, std, losses, ms per training step)."""
+    import numpy as np
+    import synthetic
+    net_ctx = dn.Context(level_solve=level, nu=nu, replaced_levels=replaced, train_batch=TRAIN_B,
+                         train_seq=TRAIN_T, **common)
+    P = net_ctx.num_patches()
+    Xs, Ys = [], []
+    for v in nus_train:
+        fctx = dn.Context(level_solve=level + replaced, nu=v, **common)
+        sctx = dn.Context(level_solve=level, nu=v, replaced_levels=replaced, **common)
+        prev = fctx.get_state()
+        for _ in range(corpus_steps):
+            fctx.step(dn.PLAIN)
+            cur = fctx.get_state()
+            X, Y = sctx.make_sample(prev, cur)
+            Xs.append(X)
+            Ys.append(Y)
+            prev = cur
+        fctx.close()
+        sctx.close()
+    Xc, Yc = torch.cat(Xs).contiguous(), torch.cat(Ys).contiguous()
+    del Xs, Ys
+    feat_mean, feat_std = net_ctx.feature_stats(Xc)
+    net_ctx.set_weights(synthetic.random_weights(77, net_ctx.num_params(), 0.05).astype(np.float32))
+    rng = np.random.default_rng(3)
+    idx_all = []
+    for _ in range(iters):
+        tid = rng.integers(0, len(nus_train), TRAIN_B)
+        start = rng.integers(0, corpus_steps - TRAIN_T + 1, TRAIN_B)
+        idx_all.append(np.stack([tid * corpus_steps + start, rng.integers(0, P, TRAIN_B)], 1))
+    idx_dev = torch.from_numpy(np.stack(idx_all).astype(np.int32)).cuda()
+    losses = []
+    for it in range(5):   # warm-up
+        Xb, Yb = net_ctx.gather_batch(Xc, Yc, idx_dev[it].contiguous(), TRAIN_T, P)
+        losses.append(net_ctx.train_step(Xb, Yb, TRAIN_B, TRAIN_T, 2e-3))
+    torch.cuda.synchronize()
+    te0, te1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    te0.record(stream)
+    for it in range(5, iters):
+        Xb, Yb = net_ctx.gather_batch(Xc, Yc, idx_dev[it].contiguous(), TRAIN_T, P)
+        lr = 2e-3 if it < 0.7 * iters else 5e-4
+        losses.append(net_ctx.train_step(Xb, Yb, TRAIN_B, TRAIN_T, lr))
+    te1.record(stream)
+    torch.cuda.synchronize()
+    train_ms = te0.elapsed_time(te1) / (iters - 5)
+    del Xc, Yc, idx_dev
+    torch.cuda.empty_cache()
+    return net_ctx, feat_mean, feat_std, losses, train_ms
+
+
+def run_large(dn, torch, stream, flush, args, common):
+    """Large DNN-MG: solve on the 512x128 channel (level 5), the network
+    replaces levels 6 and 7 (5x5-node patches of the 2048x512 level, 104
+    inputs, 50 outputs); nu = 0.002, dt = 0.002.  Trained on a bounded
+    corpus of plain level-7 trajectories (nu 0.0016 and 0.0025); then K
+    timed steps each of DNN-MG, plain mixed-precision MG on level 5 and plain
+    FP64 MG on level 7 (the reference) from the impulsive start, with the velocity L2 error of
+    each against the reference after every step."""
+    lev, rep, nu, dt = 5, 2, 0.002, 0.002
+    com = dict(common, dt=dt)
+    net_ctx, _, _, losses, train_ms = train_network(
+        dn, torch, stream, com, lev, rep, nu, (0.0016, 0.0025), LARGE_CORPUS_STEPS, LARGE_TRAIN_ITERS)
+    ref = dn.Context(level_solve=lev + rep, nu=nu, **dict(com, precision=dn.FP64))
+    coarse = dn.Context(level_solve=lev, nu=nu, **com)
+    runs = {"dnnmg": (net_ctx, dn.NET), "mg_L": (coarse, dn.PLAIN), "mg_L+2": (ref, dn.PLAIN)}
+    for c, mode in runs.values():
+        for _ in range(max(1, args.warmup)):
+            c.step(mode)
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    K = args.steps
+    times = {k: 0.0 for k in runs}
+    errs = {k: [] for k in runs}
+    nF = nnodes(lev + rep)
+    for _ in range(K):
+        for name, (c, mode) in runs.items():
+            flush.zero_()
+            ev[0].record(stream)
+            c.step(mode)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            times[name] += ev[0].elapsed_time(ev[1])
+        vref = ref.get_state()[:2 * nF]
+        nref = float(torch.linalg.vector_norm(vref))
+        d = lambda v: float(torch.linalg.vector_norm(v - vref)) / nref
+        errs["dnnmg"].append(d(net_ctx.get_fine_velocity()))
+        # MG(L) prolongated twice (bilinear, Q1 interpolation) to the reference level
+        x7 = ref.prolongate(lev + 1, coarse.prolongate(lev, coarse.get_state()))
+        errs["mg_L"].append(d(x7[:2 * nF]))
+        errs["mg_L+2"].append(0.0)
+    mean = lambda v: sum(v) / len(v)
+    out = {"workload": "solve 512x128 (level 5), network replaces 1024x256 and 2048x512 "
+                       "(5x5-node patches, 104 inputs, 50 outputs), nu=0.002, dt=0.002, mixed "
+                       "FP32/FP64; reference: plain FP64 MG on 2048x512",
+           "patches": net_ctx.num_patches(), "dofs_L": ndof(lev), "dofs_L+2": ndof(lev + rep),
+           "steps": K,
+           "ms_per_step": {k: times[k] / K for k in runs},
+           "vel_l2_err_vs_mg_L+2": {k: mean(errs[k]) for k in runs},
+           "vel_l2_err_last": {k: errs[k][-1] for k in runs},
+           "train_ms_per_iter": train_ms, "loss_first": losses[0], "loss_last": losses[-1],
+           "training": f"{LARGE_TRAIN_ITERS} Adam steps, B={TRAIN_B}, T={TRAIN_T}, corpus 2 "
+                       f"level-7 trajectories x {LARGE_CORPUS_STEPS} steps (nu 0.0016, 0.0025)"}
+    for c in (net_ctx, ref, coarse):
+        c.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -197,48 +309,9 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
 
     # ---- corpus from plain fine trajectories and training (untimed setup) ----
-    net_ctx = dn.Context(level_solve=L, nu=NU, train_batch=TRAIN_B, train_seq=TRAIN_T, **common)
+    net_ctx, feat_mean, feat_std, losses, train_ms = train_network(
+        dn, torch, stream, common, L, 1, NU, NU_TRAIN, CORPUS_STEPS, TRAIN_ITERS)
     P = net_ctx.num_patches()
-    Xs, Ys = [], []
-    for nu in NU_TRAIN:
-        fctx = dn.Context(level_solve=L + 1, nu=nu, **common)
-        sctx = dn.Context(level_solve=L, nu=nu, **common)
-        prev = fctx.get_state()
-        for _ in range(CORPUS_STEPS):
-            fctx.step(dn.PLAIN)
-            cur = fctx.get_state()
-            X, Y = sctx.make_sample(prev, cur)
-            Xs.append(X)
-            Ys.append(Y)
-            prev = cur
-        fctx.close()
-        sctx.close()
-    Xc, Yc = torch.cat(Xs).contiguous(), torch.cat(Ys).contiguous()
-    del Xs, Ys
-    feat_mean, feat_std = net_ctx.feature_stats(Xc)
-    net_ctx.set_weights(synthetic.random_weights(77, net_ctx.num_params(), 0.05).astype(np.float32))
-    rng = np.random.default_rng(3)
-    idx_all = []
-    for _ in range(TRAIN_ITERS):
-        tid = rng.integers(0, len(NU_TRAIN), TRAIN_B)
-        start = rng.integers(0, CORPUS_STEPS - TRAIN_T + 1, TRAIN_B)
-        idx_all.append(np.stack([tid * CORPUS_STEPS + start, rng.integers(0, P, TRAIN_B)], 1))
-    idx_dev = torch.from_numpy(np.stack(idx_all).astype(np.int32)).cuda()
-    losses = []
-    for it in range(5):   # warm-up
-        Xb, Yb = net_ctx.gather_batch(Xc, Yc, idx_dev[it].contiguous(), TRAIN_T, P)
-        losses.append(net_ctx.train_step(Xb, Yb, TRAIN_B, TRAIN_T, 2e-3))
-    torch.cuda.synchronize()
-    te0, te1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    te0.record(stream)
-    for it in range(5, TRAIN_ITERS):
-        Xb, Yb = net_ctx.gather_batch(Xc, Yc, idx_dev[it].contiguous(), TRAIN_T, P)
-        lr = 2e-3 if it < 0.7 * TRAIN_ITERS else 5e-4
-        losses.append(net_ctx.train_step(Xb, Yb, TRAIN_B, TRAIN_T, lr))
-    te1.record(stream)
-    torch.cuda.synchronize()
-    train_ms = te0.elapsed_time(te1) / (TRAIN_ITERS - 5)
-    del Xc, Yc
     # network forward alone (dnnmg_patch_infer over all patches)
     xin = torch.randn(P, 40, device="cuda").to(torch.bfloat16)
     hin = torch.zeros(2, P, 64, device="cuda")
@@ -246,6 +319,7 @@ def run_ours(args, rank, world):
     for _ in range(3):
         net_ctx.patch_infer(xin, hin, out)
     torch.cuda.synchronize()
+    te0, te1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     te0.record(stream)
     R = 20
     for _ in range(R):
@@ -337,6 +411,8 @@ def run_ours(args, rank, world):
     # ---- batched problems: 64 uneven channels, one launch per stage ---------
     batched = run_batched(dn, torch, stream, flush, args, net_ctx.get_weights(), feat_mean,
                           feat_std, rank)
+    # ---- large DNN-MG: the network replaces two levels -----------------------
+    large = run_large(dn, torch, stream, flush, args, common)
 
     ms = times["dnnmg"]
     if world > 1:
@@ -428,6 +504,7 @@ def run_ours(args, rank, world):
                         f_train * TRAIN_B * TRAIN_T / (train_ms * 1e-3) / 1e12 / bf16_sus,
                     "loss_first": losses[0], "loss_last": losses[-1]},
         "batched": batched,
+        "large_dnnmg": large,
         "clocks": clk.summary(),
         "e2e": {"value": 1.0 / t_e2e, "unit": "time steps/s",
                 "h2d_bytes_per_step": 8 * ndof(L), "d2h_bytes_per_step": 8 * ndof(L)},
