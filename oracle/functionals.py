@@ -21,6 +21,7 @@ a fluid cell (the obstacle's boundary nodes); the solid-interior nodes touch
 no fluid cell and would contribute nothing.
 """
 import numpy as np
+import scipy.sparse as sp
 
 from . import fem
 
@@ -47,7 +48,8 @@ def momentum_residual(level, x, prm, x_old=None):
     (1/k) M (v - v_old) + nu K v + N(v) v - (p, div phi), with no constraint
     handling.  x_old = None drops the time-derivative term."""
     be = fem.Params(nu=prm.nu, dt=prm.dt, theta=1.0, alpha0=prm.alpha0)
-    A = fem.operator(level, x, be)
+    # the LPS term lives in the pressure rows only, which are not returned
+    A = fem.operator(level, x, be, S=sp.csr_matrix((level.ndof, level.ndof)))
     nn = level.nn
     Mg = fem.mass_matrix(level)
     old = x if x_old is None else x_old
