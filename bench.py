@@ -229,54 +229,108 @@ def train_network(dn, torch, stream, common, level, replaced, nu, nus_train, cor
     return net_ctx, feat_mean, feat_std, losses, train_ms
 
 
+def on_fine_level(c, net, ref, top):
+    """State of context c on level `top` (at or above its solved level): the
+    solution prolongated by the library's bilinear P (through the reference
+    context's hierarchy above c's own), with the network-corrected fine
+    velocity in place of the prolongated one for DNN-MG."""
+    lev = c.cfg.level_solve
+    x = c.get_state().clone()
+    for k in range(top - lev):
+        x = (c if k == 0 else ref).prolongate(lev + k, x)
+    if net:
+        nf = x.numel() // 3
+        x[:2 * nf] = c.get_fine_velocity()
+    return x
+
+
+def compare_runs(runs, ref_name, ref, lev, steps_up, stream, flush, torch, K, count,
+                 on_step=None):
+    """K steps of every run, each timed alone with CUDA events (L2 flushed
+    before each), then, untimed, every run's state on the reference's level:
+    velocity and pressure relative l2 errors against the reference and the
+    drag, lift and J_div functionals (Sec. 3.4), all by the library's
+    kernels.  Returns per-run times (ms, summed), error and functional
+    series, step statistics and the library's kernel launches inside the
+    timed steps (count() is the library's launch counter)."""
+    top = lev + steps_up
+    fine = lambda name, c, mode: on_fine_level(c, mode == 1, ref, top)
+    prev = {name: fine(name, c, mode) for name, (c, mode) in runs.items()}
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    times = {k: 0.0 for k in runs}
+    series = {k: {"vel_err": [], "p_err": [], "drag": [], "lift": [], "div": []} for k in runs}
+    stats = {k: [] for k in runs}
+    counts = {k: 0 for k in runs}
+    for _ in range(K):
+        for name, (c, mode) in runs.items():
+            flush.zero_()
+            if on_step:
+                on_step(name, True)
+            n0 = count()
+            ev[0].record(stream)
+            stats[name].append(c.step(mode))
+            ev[1].record(stream)
+            counts[name] += count() - n0
+            if on_step:
+                on_step(name, False)
+            torch.cuda.synchronize()
+            times[name] += ev[0].elapsed_time(ev[1])
+        cur = {name: fine(name, c, mode) for name, (c, mode) in runs.items()}
+        for name in runs:
+            ve, pe = ((0.0, 0.0) if name == ref_name else
+                      ref.relative_errors(top, cur[name], cur[ref_name]))
+            jd, fd, fl = ref.functionals(top, cur[name], prev[name])
+            for key, v in zip(("vel_err", "p_err", "drag", "lift", "div"), (ve, pe, fd, fl, jd)):
+                series[name][key].append(v)
+        prev = cur
+    return times, series, stats, counts
+
+
+def summarize_series(series, ref_name):
+    """Mean errors, last functional values and the force drift: the mean
+    over steps of |F - F_ref| / |F_ref| with F = (drag, lift)."""
+    mean = lambda v: sum(v) / len(v)
+    r = series[ref_name]
+    out = {}
+    for name, s in series.items():
+        drift = [((d - dr) ** 2 + (l - lr) ** 2) ** 0.5 / max((dr * dr + lr * lr) ** 0.5, 1e-300)
+                 for d, l, dr, lr in zip(s["drag"], s["lift"], r["drag"], r["lift"])]
+        out[name] = {"vel_l2_err_mean": mean(s["vel_err"]), "vel_l2_err_last": s["vel_err"][-1],
+                     "p_l2_err_mean": mean(s["p_err"]), "p_l2_err_last": s["p_err"][-1],
+                     "drag_last": s["drag"][-1], "lift_last": s["lift"][-1],
+                     "div_last": s["div"][-1], "force_drift_mean": mean(drift)}
+    return out
+
+
 def run_large(dn, torch, stream, flush, args, common):
     """Large DNN-MG: solve on the 512x128 channel (level 5), the network
     replaces levels 6 and 7 (5x5-node patches of the 2048x512 level, 104
     inputs, 50 outputs); nu = 0.002, dt = 0.002.  Trained on a bounded
     corpus of plain level-7 trajectories (nu 0.0016 and 0.0025); then K
     timed steps each of DNN-MG, plain mixed-precision MG on level 5 and plain
-    FP64 MG on level 7 (the reference) from the impulsive start, with the velocity L2 error of
-    each against the reference after every step."""
+    FP64 MG on level 7 (the reference) from the impulsive start, with the
+    errors, functionals and force drift of each against the reference."""
     lev, rep, nu, dt = 5, 2, 0.002, 0.002
     com = dict(common, dt=dt)
     net_ctx, _, _, losses, train_ms = train_network(
-        dn, torch, stream, com, lev, rep, nu, (0.0016, 0.0025), LARGE_CORPUS_STEPS, LARGE_TRAIN_ITERS)
+        dn, torch, stream, com, lev, rep, nu, (0.0016, 0.0025), LARGE_CORPUS_STEPS,
+        LARGE_TRAIN_ITERS)
     ref = dn.Context(level_solve=lev + rep, nu=nu, **dict(com, precision=dn.FP64))
     coarse = dn.Context(level_solve=lev, nu=nu, **com)
     runs = {"dnnmg": (net_ctx, dn.NET), "mg_L": (coarse, dn.PLAIN), "mg_L+2": (ref, dn.PLAIN)}
     for c, mode in runs.values():
         for _ in range(max(1, args.warmup)):
             c.step(mode)
-    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     K = args.steps
-    times = {k: 0.0 for k in runs}
-    errs = {k: [] for k in runs}
-    nF = nnodes(lev + rep)
-    for _ in range(K):
-        for name, (c, mode) in runs.items():
-            flush.zero_()
-            ev[0].record(stream)
-            c.step(mode)
-            ev[1].record(stream)
-            torch.cuda.synchronize()
-            times[name] += ev[0].elapsed_time(ev[1])
-        vref = ref.get_state()[:2 * nF]
-        nref = float(torch.linalg.vector_norm(vref))
-        d = lambda v: float(torch.linalg.vector_norm(v - vref)) / nref
-        errs["dnnmg"].append(d(net_ctx.get_fine_velocity()))
-        # MG(L) prolongated twice (bilinear, Q1 interpolation) to the reference level
-        x7 = ref.prolongate(lev + 1, coarse.prolongate(lev, coarse.get_state()))
-        errs["mg_L"].append(d(x7[:2 * nF]))
-        errs["mg_L+2"].append(0.0)
-    mean = lambda v: sum(v) / len(v)
+    times, series, _, _ = compare_runs(runs, "mg_L+2", ref, lev, rep, stream, flush, torch, K,
+                                       dn.kernel_launches)
     out = {"workload": "solve 512x128 (level 5), network replaces 1024x256 and 2048x512 "
                        "(5x5-node patches, 104 inputs, 50 outputs), nu=0.002, dt=0.002, mixed "
                        "FP32/FP64; reference: plain FP64 MG on 2048x512",
            "patches": net_ctx.num_patches(), "dofs_L": ndof(lev), "dofs_L+2": ndof(lev + rep),
            "steps": K,
            "ms_per_step": {k: times[k] / K for k in runs},
-           "vel_l2_err_vs_mg_L+2": {k: mean(errs[k]) for k in runs},
-           "vel_l2_err_last": {k: errs[k][-1] for k in runs},
+           "vs_mg_L+2": summarize_series(series, "mg_L+2"),
            "train_ms_per_iter": train_ms, "loss_first": losses[0], "loss_last": losses[-1],
            "training": f"{LARGE_TRAIN_ITERS} Adam steps, B={TRAIN_B}, T={TRAIN_T}, corpus 2 "
                        f"level-7 trajectories x {LARGE_CORPUS_STEPS} steps (nu 0.0016, 0.0025)"}
@@ -335,36 +389,19 @@ def run_ours(args, rank, world):
     runs = {"dnnmg": (net_ctx, dn.NET), "mg_L": (coarse_ctx, dn.PLAIN),
             "mg_L+1": (ref_ctx, dn.PLAIN), "mg_L+1_loose": (loose_ctx, dn.PLAIN)}
     for name, (c, mode) in runs.items():
-        for _ in range(args.warmup):
+        for _ in range(max(1, args.warmup)):
             c.step(mode)
     barrier()
-    launches0 = dn.kernel_launches()
-    times = {k: 0.0 for k in runs}
-    stats = {k: [] for k in runs}
-    errs = {k: [] for k in runs}
-    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+
+    def nvtx(name, begin):  # kernel profilers select the DNN-MG launches by this range
+        if name == "dnnmg":
+            torch.cuda.nvtx.range_push("dnnmg_step") if begin else torch.cuda.nvtx.range_pop()
+
     with ClockSampler(dev) as clk:
-        for k in range(args.steps):
-            for name, (c, mode) in runs.items():
-                flush.zero_()
-                if name == "dnnmg":  # kernel profilers select these launches by this range
-                    torch.cuda.nvtx.range_push("dnnmg_step")
-                ev[0].record(stream)
-                stats[name].append(c.step(mode))
-                ev[1].record(stream)
-                if name == "dnnmg":
-                    torch.cuda.nvtx.range_pop()
-                torch.cuda.synchronize()
-                times[name] += ev[0].elapsed_time(ev[1])
-            vref = ref_ctx.get_state()[:2 * nnodes(L + 1)]
-            nref = float(torch.linalg.vector_norm(vref))
-            d = lambda v: float(torch.linalg.vector_norm(v - vref)) / nref
-            errs["dnnmg"].append(d(net_ctx.get_fine_velocity()))
-            errs["mg_L"].append(d(coarse_ctx.prolongate(L, coarse_ctx.get_state())[:2 * nnodes(L + 1)]))
-            errs["mg_L+1_loose"].append(d(loose_ctx.get_state()[:2 * nnodes(L + 1)]))
-            errs["mg_L+1"].append(0.0)
+        times, series, stats, counts = compare_runs(runs, "mg_L+1", ref_ctx, L, 1, stream, flush,
+                                                    torch, args.steps, dn.kernel_launches, nvtx)
     barrier()
-    launches = dn.kernel_launches() - launches0
+    launches = counts["dnnmg"]
     # stage breakdown: the same DNN-MG steps again with per-stage events
     # (untimed; the events would perturb the timed steps)
     net_ctx.profile(True)
@@ -379,6 +416,8 @@ def run_ours(args, rank, world):
     net_ctx.profile(False)
 
     # ---- V-cycle throughput at levels 6 and 5 (current linearisations) -----------
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+
     def vcycle_ms(c, level):
         x = c.get_state()
         c.linearize(x)
@@ -445,13 +484,13 @@ def run_ours(args, rank, world):
     achieved = dom["algorithmic_bytes_per_launch"] / (dom["avg_launch_ms"] * 1e-3) / 1e9
     f_fwd, f_train = net_flops()
     mean = lambda v: sum(v) / len(v)
+    summary = summarize_series(series, "mg_L+1")
     comparison = {
         name: {"ms_per_step": times[name] / K,
                "newton_its": mean([s["newton_its"] for s in stats[name]]),
                "gmres_its": mean([s["gmres_its"] for s in stats[name]]),
                "fallbacks": sum(s["fallback"] for s in stats[name]),
-               "vel_l2_err_vs_mg_L+1": mean(errs[name]),
-               "vel_l2_err_last": errs[name][-1]}
+               **summary[name]}
         for name in runs}
     return {
         "metric": METRIC,

@@ -7,12 +7,12 @@
  * with local projection stabilisation (Eqs. 4-5) on a hierarchy of uniformly
  * refined meshes.  Each time step solves A_n(x_n) = f_n (Eq. 3) by Newton's
  * method (Eq. 6) whose linear systems are solved by flexible GMRES
- * preconditioned with one geometric multigrid V-cycle (Sec. 2.2, Algorithm 1
- * lines 2-4).  In DNN-MG mode a patch-wise recurrent network (stacked GRUs +
+ * preconditioned with one geometric multigrid V-cycle (Sec. 2.2, the Newton
+ * iteration of Algorithm 1).  In DNN-MG mode a patch-wise recurrent network (stacked GRUs +
  * dense layers, Sec. 2.2 and Sec. 3.1) predicts a velocity correction on the
  * level(s) above the finest solved one, which enters the next step through
- * the restricted right-hand side (Algorithm 1 lines 6-9); the network is
- * trained with the loss of Eq. 7.
+ * the restricted right-hand side (the network correction of Algorithm 1);
+ * the network is trained with the loss of Eq. 7.
  *
  * Conventions
  *  - Every function returns a status code (DNNMG_OK = 0).  On failure the
@@ -54,8 +54,8 @@ extern "C" {
 #define DNNMG_MIXED 1  /* V-cycle and GMRES in FP32 inside FP64 Newton (defect correction) */
 
 /* time-step modes */
-#define DNNMG_PLAIN 0  /* classical Newton-Krylov-multigrid step (Algorithm 1 lines 2-4) */
-#define DNNMG_NET 1    /* DNN-MG step (Algorithm 1 lines 2-9) */
+#define DNNMG_PLAIN 0  /* classical Newton-Krylov-multigrid step (Newton part of Algorithm 1) */
+#define DNNMG_NET 1    /* DNN-MG step (Algorithm 1) */
 
 typedef struct dnnmg_ctx dnnmg_ctx;
 
@@ -68,7 +68,7 @@ typedef struct dnnmg_config {
   double newton_tol;  /* stop when the l2 norm of f_n - A_n(x) over free DOFs <= newton_tol */
   double gmres_rtol;  /* relative residual reduction of FGMRES per Newton step */
   double omega;       /* damping of the Vanka update */
-  double eps_damp;    /* Newton damping epsilon (Algorithm 1 line 4) */
+  double eps_damp;    /* Newton damping epsilon (the damped update of Algorithm 1) */
   int32_t obstacle_i0, obstacle_j0; /* lower-left level-0 cell of the 2x2 solid block, -1 = none */
   int32_t level_solve;     /* finest level L solved by multigrid */
   int32_t level_coarse;    /* coarsest multigrid level (direct solve), >= 1 */
@@ -169,7 +169,7 @@ int dnnmg_residual(dnnmg_ctx* ctx, const double* x, const double* f, double* r);
 /* One time step (Eq. 3) from the context's state.  mode = DNNMG_PLAIN: the
  * right-hand side is the old-time term of Eq. 5; mode = DNNMG_NET: the step
  * uses the restricted right-hand side left by the previous DNN-MG step (if
- * any) and ends with Algorithm 1 lines 6-9 (prolongation, network, Rhs,
+ * any) and ends with the network correction of Algorithm 1 (prolongation, network, Rhs,
  * restriction).  If the Newton iteration count exceeds the fallback threshold
  * the step is recomputed without the network right-hand side (Sec. 3.3).
  * stats (host pointer, may be NULL) receives the step statistics.
@@ -188,9 +188,31 @@ int dnnmg_step_io(dnnmg_ctx* ctx, int mode, const double* x_in, double* x_out,
                   dnnmg_step_stats* stats);
 
 /* Unmasked bilinear prolongation P of all three fields from level `level`
- * to level + 1 (Algorithm 1 line 6): xc device [3][nn(level)] doubles, xf
- * device [3][nn(level + 1)] doubles; level + 1 <= L + replaced_levels. */
+ * to level + 1 (the prolongation P of Algorithm 1): xc device [3][nn(level)]
+ * doubles, xf device [3][nn(level + 1)] doubles; level + 1 <= L + replaced_levels. */
 int dnnmg_prolongate(dnnmg_ctx* ctx, int level, const double* xc, double* xf);
+
+/* ---- functionals (Sec. 3.4) ---------------------------------------------------
+ * dnnmg_functionals: out (host, 3 doubles) = {J_div, J_drag, J_lift} of the
+ * state x (device [3][nn(level)] doubles, any level 0 .. L + replaced_levels)
+ * with the context's nu and dt:
+ *   J_div  = int |div v|^2 dx over the fluid cells (2x2 Gauss per cell);
+ *   J_drag = -int_Gamma (nu grad v - p I) n . e_x ds, J_lift the same with
+ *            e_y, Gamma the obstacle boundary, n pointing into the obstacle.
+ * Drag and lift are evaluated in residual (volume) form: minus the
+ * backward-Euler momentum rows (1/k) M (v - v_old) + nu K v + N(v) v
+ * - (p, div phi) summed over the obstacle's boundary nodes.  x_old (device,
+ * same layout, velocity used) is the state one time step earlier; NULL drops
+ * the time-derivative term (steady form).  Fixed-order sums: repeated calls
+ * return identical values.  Synchronous on the context's stream.
+ *
+ * dnnmg_relative_errors: out (host, 2 doubles) = relative l2 errors of the
+ * velocity and of the pressure of x against x_ref (both device
+ * [3][nn(level)] doubles).  DNNMG_ERR_NUMERICAL if a reference part is zero. */
+int dnnmg_functionals(dnnmg_ctx* ctx, int level, const double* x, const double* x_old,
+                      double* out);
+int dnnmg_relative_errors(dnnmg_ctx* ctx, int level, const double* x, const double* x_ref,
+                          double* out);
 
 /* ---- patch network (Sec. 2.2, Sec. 3.1, Table 1) ------------------------------
  * Two stacked GRU cells (hidden 64, PyTorch gate convention r, z, n) and a
@@ -218,7 +240,7 @@ int dnnmg_net_dims(const dnnmg_ctx* ctx, int* c_in, int* c_out);
 int dnnmg_set_weights(dnnmg_ctx* ctx, const float* w);
 int dnnmg_get_weights(dnnmg_ctx* ctx, float* w);
 
-/* One recurrent step of the network for P patches (Algorithm 1 line 7):
+/* One recurrent step of the network for P patches (the network evaluation of Algorithm 1):
  *   x   : device [P][C_in] bfloat16 (raw uint16 bits), normalised inputs
  *   h   : device [2][P][64] float, hidden state, updated in place
  *   out : device [P][C_out] float, predicted correction
@@ -232,7 +254,7 @@ int dnnmg_patch_infer(dnnmg_ctx* ctx, const uint16_t* x, float* h, float* out, i
 int dnnmg_gemm_bf16(dnnmg_ctx* ctx, const uint16_t* A, const uint16_t* B, float* C, int M, int N,
                     int K);
 
-/* ---- DNN-MG state (Algorithm 1 lines 6-9) -----------------------------------
+/* ---- DNN-MG state (the network correction of Algorithm 1) -----------------------------------
  * A DNNMG_NET step ends with: v~ = P(v^L) on the fine level F = L + r (P
  * applied once per replaced level); the fine residual r = f - A(v~, P p^L)
  * of Eq. 3 on level F with f built from the previous corrected fine
@@ -381,8 +403,8 @@ int dnnmg_vcycle_plan(const dnnmg_ctx* ctx, int level, int* split_level, int* sp
  *
  * A batch advances many independent channel problems of uneven size in
  * lock-step with the algorithm of a single context (Newton, FGMRES, one
- * V-cycle per Krylov step; DNN-MG steps add the correction of Algorithm 1
- * lines 6-9 with one network evaluation over the patches of all problems).
+ * V-cycle per Krylov step; DNN-MG steps add the network correction of
+ * Algorithm 1 with one network evaluation over the patches of all problems).
  * Every stage (a Vanka colour pass on level k, a defect, a transfer, a
  * Krylov vector operation, ...) is one kernel launch over a work list of
  * the blocks of all problems that take part in it; problems that have

@@ -12,10 +12,10 @@ Modules
   fem     Q1/Q1 + LPS element matrices and assembly (Eqs. 3-5)
   mg      transfers, cell-wise Vanka smoother, coarse LU, V-cycle (Sec. 2.2)
   krylov  flexible GMRES (Sec. 2.2)
-  newton  Newton time step (Eq. 6, Algorithm 1 lines 2-4)
+  newton  Newton time step (Eq. 6, the Newton iteration of Algorithm 1)
   net     patch GRU + dense network, BPTT backward, loss (Eq. 7), Adam
   dnnmg   prolongation, network inputs, scatter, Rhs and restriction
-          (Algorithm 1 lines 6-9)
+          (the network correction of Algorithm 1)
 
 Readings of the paper where it is silent or garbled are stated in each
 module's docstring.  Pins that tie each function to the paper or to

@@ -1,6 +1,6 @@
 """The DNN-MG additions to a time step (oracle, test only).
 
-Algorithm 1 lines 6-9 and Sec. 2.2: after the Newton solve on level L,
+the network correction of Algorithm 1 and Sec. 2.2: after the Newton solve on level L,
   6  v~^{L+1} = P(v^L)                      (prolongation to level L+1)
   7  d^{L+1}  = N(v~^{L+1}, Omega_L, Omega_{L+1})   (network, per patch)
   8  b^{L+1}_{n+1} = Rhs(v~^{L+1} + d^{L+1}, f_n, f_{n+1})
@@ -23,7 +23,7 @@ Readings:
     standardised, (value - mean) / std, with statistics of the corpus;
   * the correction at a fine node is the mean of the predictions of all
     patches containing it, and zero on velocity Dirichlet nodes;
-  * Rhs (Alg. 1 line 8) for backward Euler is (1/k) M^{fine} (v~ + d)
+  * Rhs (the right-hand side Rhs of Algorithm 1) for backward Euler is (1/k) M^{fine} (v~ + d)
     (theta-scheme: minus (1-theta) times the explicit transport and
     diffusion of v~ + d), external force f = 0; R = P^T per component;
     Dirichlet rows of b^L are irrelevant (the Newton solve overwrites them).
@@ -94,7 +94,7 @@ def scatter_average(coarse, fine, ratio, d):
 
 
 def rhs_and_restrict(coarse, fine, levels_between, v_corr, prm):
-    """b^{fine} = Rhs(v_corr) (Alg. 1 line 8) and b^L = R b^{fine} (line 9).
+    """b^{fine} = Rhs(v_corr) and b^L = R b^{fine} (Algorithm 1).
 
     levels_between lists the levels from L to the fine level, so that R is
     applied once per replaced level.  Returns (b_fine, b_L) as full vectors
@@ -121,7 +121,7 @@ def time_step(levels, fine, x_old, state, spec, params, prm, opt, mean=None, std
     """One DNN-MG time step (Algorithm 1): Newton on level L with the
     restricted right-hand side of the previous step (if any; otherwise the
     plain old-time term), redone without it if Newton needs more than
-    `fallback_its` iterations (Sec. 3.3), then lines 6-9.
+    `fallback_its` iterations (Sec. 3.3), then the network correction.
 
     fine: the level above L (one replaced level) or the list of levels
     [L+1, ..., L+r] that the network replaces (Sec. 2.2: one or multiple

@@ -1,7 +1,7 @@
 """Geometric multigrid with cell-wise Vanka smoothing (oracle, test only).
 
 Sec. 2.2 preconditions GMRES with one geometric multigrid cycle per
-application (Algorithm 1 line 3) but does not say which smoother, transfers
+application (the preconditioned solve of Algorithm 1) but does not say which smoother, transfers
 or coarse solver it uses.  Readings:
   * operators on every level are rediscretised (fem.jacobian) at the
     linearisation point injected nodally from the finest solved level;

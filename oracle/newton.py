@@ -3,8 +3,8 @@
 Eq. 3 / Eq. 6: each time step solves A_n(x_n) = f_n by Newton's method from
 the initial guess x_{n-1}; every Newton correction w solves
 A'_n(x^{(l-1)}) w = f_n - A_n(x^{(l-1)}) by FGMRES preconditioned with one
-multigrid V-cycle (Sec. 2.2, Algorithm 1 lines 2-4), and the update is
-damped, z <- z + eps * w (Algorithm 1 line 4).
+multigrid V-cycle (Sec. 2.2, the Newton iteration of Algorithm 1), and the update is
+damped, z <- z + eps * w (the damped update of Algorithm 1).
 
 Readings: the iteration stops when the Euclidean norm of the nonlinear
 residual over free DOFs is at most newton_tol (absolute; default 1e-10), with

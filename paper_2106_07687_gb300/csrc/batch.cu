@@ -2,7 +2,7 @@
 // obstacle, viscosity, time step and finest level each) advanced by the same
 // time-step algorithm as a single context -- Newton's method (Eq. 6) with
 // right-preconditioned FGMRES and a multigrid V-cycle (Sec. 2.2), and for
-// DNN-MG steps the network correction of Algorithm 1 lines 6-9 -- with every
+// DNN-MG steps the network correction of the network correction of Algorithm 1 -- with every
 // stage of every problem issued as one launch for the whole batch.
 //
 // Lock-step control: all problems run Newton and FGMRES iterations together;
@@ -768,22 +768,22 @@ int Batch<T>::newton(const std::vector<int>& mask, std::vector<dnnmg_step_stats>
   return check("newton");
 }
 
-// Algorithm 1 lines 6-9 for every problem after the level-L solves.
+// the network correction of Algorithm 1 for every problem after the level-L solves.
 template <typename T>
 void Batch<T>::correction() {
   const Work wf = fine_.w();
   const int pr = prof_.begin(DNNMG_STAGE_NETWORK, Lmax_, st_);
   if (!have_vcorr_) bk_prolong_state<T>(v_, xold64_, vcorr_, 2, 1, wf, nullptr, st_);
-  bk_prolong_state<T>(v_, x64_, xtF_, 3, 0, wf, nullptr, st_);       // line 6
+  bk_prolong_state<T>(v_, x64_, xtF_, 3, 0, wf, nullptr, st_);       // P
   bk_old_rhs<T>(v_, 1, vcorr_, fF_, wf, nullptr, st_);
   bk_copy_impose<T>(v_, 1, xtF_, ximpF_, wf, nullptr, st_);
   bk_residual64<T>(v_, 1, ximpF_, fF_, rF_, wf, nullptr, st_);       // input: fine residual
   bk_gather<T>(v_, P_, pinst_, pcell_, xtF_, rF_, feat_mean_, feat_std_, X_, st_);
-  launch_patchnet_forward(nd_, pk_, X_, hid_, hid_, net_out_, P_, net_status_, st_);  // line 7
+  launch_patchnet_forward(nd_, pk_, X_, hid_, hid_, net_out_, P_, net_status_, st_);  // network
   bk_scatter<T>(v_, cell_patch_, net_out_, nd_.c_out, xtF_, vcorr_, wf, nullptr, st_);
-  bk_old_rhs<T>(v_, 1, vcorr_, bF_, wf, nullptr, st_);                // line 8
+  bk_old_rhs<T>(v_, 1, vcorr_, bF_, wf, nullptr, st_);                // Rhs
   cudaMemsetAsync(bL_, 0, sizeof(double) * N_, st_);
-  bk_restrict_full<T>(v_, bF_, bL_, 2, top_.w(), nullptr, st_);      // line 9
+  bk_restrict_full<T>(v_, bF_, bL_, 2, top_.w(), nullptr, st_);      // R
   prof_.end(pr, st_);
   have_vcorr_ = have_net_rhs_ = true;
 }

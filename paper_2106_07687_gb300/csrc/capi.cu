@@ -282,6 +282,22 @@ int dnnmg_prolongate(dnnmg_ctx* ctx, int level, const double* xc, double* xf) {
   return ctx->check("prolongate");
 }
 
+int dnnmg_functionals(dnnmg_ctx* ctx, int level, const double* x, const double* x_old,
+                      double* out) {
+  if (!ctx || !x || !out) return DNNMG_ERR_ARG;
+  if (level < 0 || level >= (int)ctx->lv.size())
+    return ctx->fail(DNNMG_ERR_ARG, "level out of range");
+  return ctx->functionals(level, x, x_old, out);
+}
+
+int dnnmg_relative_errors(dnnmg_ctx* ctx, int level, const double* x, const double* x_ref,
+                          double* out) {
+  if (!ctx || !x || !x_ref || !out) return DNNMG_ERR_ARG;
+  if (level < 0 || level >= (int)ctx->lv.size())
+    return ctx->fail(DNNMG_ERR_ARG, "level out of range");
+  return ctx->rel_errors(level, x, x_ref, out);
+}
+
 int dnnmg_profile(dnnmg_ctx* ctx, int enable) {
   if (!ctx) return DNNMG_ERR_ARG;
   ctx->prof.enable(enable != 0);

@@ -1,4 +1,4 @@
-// Device bodies of the DNN-MG correction (Algorithm 1 lines 6-9), shared by
+// Device bodies of the DNN-MG correction (the network correction of Algorithm 1), shared by
 // the single-problem kernels (dnnmg_step.cu) and the batched kernels
 // (batch.cu).
 //

@@ -1,4 +1,4 @@
-// Kernels of the DNN-MG correction (Algorithm 1 lines 6-9, Sec. 2.2):
+// Kernels of the DNN-MG correction (the network correction of Algorithm 1, Sec. 2.2):
 // network input gathering per patch, scatter-averaging of the predicted
 // corrections to the fine nodes, and boundary values of prolongated states.
 //

@@ -119,4 +119,18 @@ template <typename T>
 void launch_gmres_start(const T* r, const double* nrm2, T* v0, double* gvec, size_t n,
                         cudaStream_t st);
 
+// ---- functionals of Sec. 3.4 (functionals.cu) --------------------------------
+// Backward-Euler constants of a level (theta = 1) and its mass matrix over k.
+struct FnConsts {
+  Sten<double> s;
+  double mk[16];
+};
+constexpr int kFnBlocks = 304;  // partial sums: part needs kFnBlocks * 4 doubles
+// out (device) = {J_div, J_drag, J_lift} of state x; x_old may be null (steady form)
+void launch_functionals(const Grid& g, const FnConsts& c, const double* x, const double* x_old,
+                        double* part, double* out, cudaStream_t st);
+// out (device) = {|v - v_ref|^2, |v_ref|^2, |p - p_ref|^2, |p_ref|^2}
+void launch_rel_errors(const Grid& g, const double* x, const double* x_ref, double* part,
+                       double* out, cudaStream_t st);
+
 }  // namespace dnnmg

@@ -1,6 +1,6 @@
 // Patch network on fifth-generation tensor cores (Sec. 2.2 / Sec. 3.1: GRU
 // cells with memory per patch, then dense layers; inputs and outputs per
-// patch as in Algorithm 1 line 7).
+// patch as in the network evaluation of Algorithm 1).
 //
 // patchnet_forward_kernel: persistent, one 128-patch tile at a time per CTA,
 // 512 threads in four warpgroups.  Patch row r of the tile is TMEM lane r;

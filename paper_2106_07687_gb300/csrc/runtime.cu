@@ -1,5 +1,5 @@
 // Host runtime: multigrid V-cycle, flexible GMRES and Newton time step
-// (Sec. 2.2, Eq. 6, Algorithm 1 lines 2-4), sequencing the kernels of this
+// (Sec. 2.2, Eq. 6, the Newton iteration of Algorithm 1), sequencing the kernels of this
 // library on the context's stream.
 #include <cmath>
 #include <algorithm>
@@ -488,6 +488,8 @@ int dnnmg_ctx::init() {
   r64 = mem.alloc<double>(n3);
   dots = mem.alloc<double>(64);
   partials = mem.alloc<double>(dots_partials(n3, 4));
+  fpart = mem.alloc<double>(4 * kFnBlocks);
+  fout = mem.alloc<double>(4);
   if (!mem.ok()) return fail(DNNMG_ERR_CUDA, "device allocation failed");
   s64L = make_sten<double>(gL.h, cfg);
   sxL = make_explicit_sten(gL.h, cfg);
@@ -711,7 +713,7 @@ void dnnmg_ctx::restrict_down(const double* bf, double* bc) {
   }
 }
 
-// Algorithm 1 lines 6-9 after the level-L solve of this step (x64 = v^L_n).
+// the network correction of Algorithm 1 after the level-L solve of this step (x64 = v^L_n).
 int dnnmg_ctx::dnnmg_correction() {
   const Grid gL = grid(L()), gF = grid(fine_level());
   const size_t n3F = 3 * (size_t)gF.nn;
@@ -721,16 +723,16 @@ int dnnmg_ctx::dnnmg_correction() {
     prolong_up(xold64, vcorr, 2);
     cudaMemsetAsync(vcorr + 2 * gF.nn, 0, sizeof(double) * gF.nn, st);
   }
-  prolong_up(x64, xtF, 3);                                            // line 6
+  prolong_up(x64, xtF, 3);                                            // P
   old_rhs(fine_level(), vcorr, fF);
   cudaMemcpyAsync(ximpF, xtF, n3F * sizeof(double), cudaMemcpyDeviceToDevice, st);
   launch_impose_dirichlet64(gF, ximpF, st);
   launch_residual64(gF, s64F, ximpF, fF, rF, st);                     // input: fine residual
   launch_gather(gL, gF, K, patch_cell, P, xtF, rF, feat_mean, feat_std, cfg.nu, cfg.dt, X, st);
-  launch_patchnet_forward(nd, pk, X, hid, hid, net_out, P, net_status, st);  // line 7
+  launch_patchnet_forward(nd, pk, X, hid, hid, net_out, P, net_status, st);  // network
   launch_scatter(gL, gF, K, cell_patch, net_out, nd.c_out, xtF, vcorr, st);
-  old_rhs(fine_level(), vcorr, bF);                                   // line 8
-  restrict_down(bF, bL);                                              // line 9
+  old_rhs(fine_level(), vcorr, bF);                                   // Rhs
+  restrict_down(bF, bL);                                              // R
   prof.end(pr, st);
   have_vcorr = have_net_rhs = true;
   return net_check("dnnmg correction");
@@ -802,6 +804,34 @@ int dnnmg_ctx::set_feature_stats(const float* mean, const float* stdv) {
   cudaMemcpyAsync(feat_std, stdv, sizeof(float) * nd.c_in, cudaMemcpyHostToDevice, st);
   cudaStreamSynchronize(st);
   return check("set_feature_stats");
+}
+
+int dnnmg_ctx::functionals(int level, const double* x, const double* x_old, double* out_host) {
+  const Grid g = grid(level);
+  dnnmg_config be = cfg;
+  be.theta = 1.0;
+  FnConsts c{};
+  c.s = make_sten<double>(g.h, be);
+  const double m1[2][2] = {{g.h / 3, g.h / 6}, {g.h / 6, g.h / 3}};
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b)
+      c.mk[a * 4 + b] = m1[a & 1][b & 1] * m1[a >> 1][b >> 1] / cfg.dt;
+  launch_functionals(g, c, x, x_old, fpart, fout, st);
+  cudaMemcpyAsync(out_host, fout, 3 * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return check("functionals");
+  return check("functionals");
+}
+
+int dnnmg_ctx::rel_errors(int level, const double* x, const double* x_ref, double* out_host) {
+  double s4[4];
+  launch_rel_errors(grid(level), x, x_ref, fpart, fout, st);
+  cudaMemcpyAsync(s4, fout, 4 * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return check("relative_errors");
+  if (int rc = check("relative_errors")) return rc;
+  if (!(s4[1] > 0.0) || !(s4[3] > 0.0)) return fail(DNNMG_ERR_NUMERICAL, "reference state is zero");
+  out_host[0] = std::sqrt(s4[0] / s4[1]);
+  out_host[1] = std::sqrt(s4[2] / s4[3]);
+  return DNNMG_OK;
 }
 
 int dnnmg_ctx::get_fine_velocity(double* v) {

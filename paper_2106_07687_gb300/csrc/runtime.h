@@ -155,6 +155,7 @@ struct dnnmg_ctx {
   double* dots = nullptr;      // small device scratch for reductions
   double* partials = nullptr;  // reduction partials
   double* h_scalars = nullptr; // pinned host scalars
+  double *fpart = nullptr, *fout = nullptr;  // functionals: partial sums, results
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   dnnmg::Prof prof;
   long long steps_taken = 0;   // time steps since setup (coarse refresh schedule)
@@ -220,6 +221,8 @@ struct dnnmg_ctx {
   void restrict_down(const double* bf, double* bc);
   int set_feature_stats(const float* mean, const float* stdv);
   int get_fine_velocity(double* v);
+  int functionals(int level, const double* x, const double* x_old, double* out_host);
+  int rel_errors(int level, const double* x, const double* x_ref, double* out_host);
   int get_patch_inputs(uint16_t* x);
   int init_train();
   int train_grad_impl(const uint16_t* X, const float* Y, int B, int T);

@@ -1,5 +1,5 @@
 // Grid transfers between nested Q1 levels: bilinear prolongation P, its
-// transpose R = P^T, and nodal injection (Sec. 2.2, Algorithm 1 lines 6 and 9).
+// transpose R = P^T, and nodal injection (Sec. 2.2, the prolongation and restriction of Algorithm 1).
 // Inside the V-cycle both P and R act on free DOFs only; the DNN-MG state and
 // right-hand-side transfers use the unmasked operators.
 #include "kernels.h"

@@ -85,6 +85,8 @@ def _declare(lib):
         "dnnmg_feature_stats": ([P, P, ctypes.c_int64, P, P], ctypes.c_int),
         "dnnmg_step_io": ([P, ctypes.c_int, P, P, P], ctypes.c_int),
         "dnnmg_prolongate": ([P, ctypes.c_int, P, P], ctypes.c_int),
+        "dnnmg_functionals": ([P, ctypes.c_int, P, P, P], ctypes.c_int),
+        "dnnmg_relative_errors": ([P, ctypes.c_int, P, P, P], ctypes.c_int),
         "dnnmg_profile": ([P, ctypes.c_int], ctypes.c_int),
         "dnnmg_profile_read": ([P, ctypes.c_int, ctypes.c_int, P, P], ctypes.c_int),
         "dnnmg_kernel_launches": ([], ctypes.c_uint64),
@@ -326,6 +328,28 @@ class Context:
         xf = torch.empty(self.ndof(level + 1), dtype=torch.float64, device="cuda")
         self._check(self.lib.dnnmg_prolongate(self.h, level, _ptr(xc), _ptr(xf)))
         return xf
+
+    def _check_state(self, level, *xs):
+        n = self.ndof(level)
+        for t in xs:
+            if t is not None and (t.dtype != torch.float64 or t.numel() != n):
+                raise ValueError(f"expected {n} float64 values for level {level}")
+
+    def functionals(self, level, x, x_old=None):
+        """(J_div, J_drag, J_lift) of state x on `level` (x_old: the state one
+        step earlier, None for the steady form)."""
+        self._check_state(level, x, x_old)
+        out = (ctypes.c_double * 3)()
+        xo = _ptr(x_old) if x_old is not None else None
+        self._check(self.lib.dnnmg_functionals(self.h, level, _ptr(x), xo, out))
+        return tuple(out)
+
+    def relative_errors(self, level, x, x_ref):
+        """(velocity, pressure) relative l2 errors of x against x_ref."""
+        self._check_state(level, x, x_ref)
+        out = (ctypes.c_double * 2)()
+        self._check(self.lib.dnnmg_relative_errors(self.h, level, _ptr(x), _ptr(x_ref), out))
+        return tuple(out)
 
     def vcycle_split(self):
         return int(self.lib.dnnmg_vcycle_split(self.h))

@@ -1,4 +1,4 @@
-"""Parity of the CUDA DNN-MG time step (Algorithm 1 lines 2-9) with the
+"""Parity of the CUDA DNN-MG time step (Algorithm 1) with the
 oracle's composition of the same steps, plus the zero-network invariant and
 the Newton-count fallback.  Solver in FP64 (Newton tolerance 1e-12), network
 in BF16 with FP32 accumulation: states are compared at relative L2 1e-4

@@ -1,4 +1,4 @@
-"""Pins of the oracle's DNN-MG pieces (Algorithm 1 lines 6-9): with a zero
+"""Pins of the oracle's DNN-MG pieces (the network correction of Algorithm 1): with a zero
 network correction the restricted right-hand side is exactly the coarse
 level's own old-time term (nested Q1 spaces, exact quadrature), so a DNN-MG
 step reduces to a plain MG(L) step; scatter averaging and patch features
@@ -35,7 +35,7 @@ def test_dnnmg_step_with_zero_network_equals_plain_step():
     opt = newton.SolverOptions(newton_tol=1e-12)
     x0 = mesh.initial_state(coarse)
     x1, *_ = newton.time_step(levels, x0, prm, opt)
-    # Alg. 1 lines 6-9 with d = 0, then the next step from b^L
+    # the network correction of Algorithm 1 with d = 0, then the next step from b^L
     xt = dnnmg.prolongate_state(coarse, fine, x1)
     _, bL = dnnmg.rhs_and_restrict(coarse, fine, [coarse, fine], xt, prm)
     x2_dnn, *_ = newton.newton_solve(levels, x1, bL, prm, opt)
