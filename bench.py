@@ -39,7 +39,7 @@ ORACLE_L = 4              # bounded CPU sample: oracle DNN-MG step with L = 4, s
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel
 # as it stands (profiles/vcycle_subcycle_level5.md); a kernel change makes
 # the entry stale and it must then be removed.
-NCU_TRAFFIC = {"vcycle_kernel<float>@split4": 19742464 + 12032}
+NCU_TRAFFIC = {"vcycle_kernel<float>@split4": 19723264 + 12544}
 L2_BYTES = 129 * 2 ** 20
 
 

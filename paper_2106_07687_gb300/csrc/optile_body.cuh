@@ -25,10 +25,12 @@ struct OpSmem {
 
 // Rows (ru, rv, rp) of the operator at this thread's node of tile (bx, by):
 // A(w) if NONLIN, else A'(vb) w; with MASK, constrained entries of w count
-// as zero.  Every thread of the TX * TY-thread block calls it (block
-// barriers inside); a thread whose node lies outside the level gets n = -1.
-// Constrained rows are returned like free ones (the caller overrides them).
-template <typename T, bool NONLIN, bool MASK, int TX, int TY>
+// as zero.  Every thread of the NTT-thread block calls it (block barriers
+// inside): the first TX * TY threads own a node each, any further ones help
+// stage the tile and compute its cell and patch rows.  A thread whose node
+// lies outside the level, and every helper, gets n = -1.  Constrained rows
+// are returned like free ones (the caller overrides them).
+template <typename T, bool NONLIN, bool MASK, int TX, int TY, int NTT = TX * TY>
 __device__ __forceinline__ void op_tile_rows(const Grid& g, const Sten<T>& s,
                                              const T* __restrict__ w, const T* __restrict__ vb,
                                              int bx, int by, OpSmem<T, TX, TY>& S, T& ru, T& rv,
@@ -38,9 +40,10 @@ __device__ __forceinline__ void op_tile_rows(const Grid& g, const Sten<T>& s,
   constexpr int kCX = TX + 1, kCY = TY + 1, kPX = TX / 2 + 1, kPY = TY / 2 + 1;
   const int nn = g.nn;
   const int i0 = bx * TX, j0 = by * TY;  // first node of the tile (even)
+  static_assert(NTT >= kNT, "thread group");
   const int t = threadIdx.x;
   // ---- stage nodes [i0-2, i0+TX+2) x [j0-2, j0+TY+2)
-  for (int e = t; e < kSX * kSY; e += kNT) {
+  for (int e = t; e < kSX * kSY; e += NTT) {
     const int li = e % kSX, lj = e / kSX;
     const int i = i0 - 2 + li, j = j0 - 2 + lj;
     T u = 0, v = 0, p = 0, bu = 0, bvv = 0;
@@ -66,46 +69,49 @@ __device__ __forceinline__ void op_tile_rows(const Grid& g, const Sten<T>& s,
     S.sol[lj][li] = so;
   }
   __syncthreads();
-  // ---- cells [i0-1, i0+TX) x [j0-1, j0+TY): 12 rows each
-  for (int e = t; e < kCX * kCY; e += kNT) {
-    const int lc = e % kCX, lr = e / kCX;
-    const int ci = i0 - 1 + lc, cj = j0 - 1 + lr;
-    const bool ok = ci >= 0 && cj >= 0 && ci < g.nx && cj < g.ny && !S.sol[lr + 1][lc + 1];
-    S.cvalid[e] = ok;
-    if (!ok) continue;
-    T wu[4], wv[4], wp[4], bu[4], bv[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int li = lc + 1 + (a & 1), lj = lr + 1 + (a >> 1);
-      wu[a] = S.w[0][lj][li];
-      wv[a] = S.w[1][lj][li];
-      wp[a] = S.w[2][lj][li];
-      bu[a] = S.vb[0][lj][li];
-      bv[a] = S.vb[1][lj][li];
-    }
-    T r[12];
-    cell_all_rows<T, NONLIN>(s, wu, wv, wp, bu, bv, r);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) S.cres[e][k] = r[k];
-  }
-  // ---- patches I in [i0/2 - 1, i0/2 + TX/2 - 1] (those with 2I <= i <= 2I+2
-  // for a node i of the tile), likewise J: 9 LPS rows each
+  // ---- cells [i0-1, i0+TX) x [j0-1, j0+TY): 12 rows each, and the patches
+  // I in [i0/2 - 1, i0/2 + TX/2 - 1] (those with 2I <= i <= 2I+2 for a node i
+  // of the tile), likewise J: 9 LPS rows each -- one list of work items
   const int PI0 = i0 / 2 - 1, PJ0 = j0 / 2 - 1;
-  for (int e = t; e < kPX * kPY; e += kNT) {
-    const int pi = PI0 + e % kPX, pj = PJ0 + e / kPX;
-    const bool ok = pi >= 0 && pj >= 0 && pi < g.nx / 2 && pj < g.ny / 2 &&
-                    !S.sol[2 * pj - j0 + 2][2 * pi - i0 + 2];
-    S.pvalid[e] = ok;
-    if (!ok) continue;
-    T p[9];
+  for (int wi = t; wi < kCX * kCY + kPX * kPY; wi += NTT) {
+    if (wi < kCX * kCY) {
+      const int e = wi;
+      const int lc = e % kCX, lr = e / kCX;
+      const int ci = i0 - 1 + lc, cj = j0 - 1 + lr;
+      const bool ok = ci >= 0 && cj >= 0 && ci < g.nx && cj < g.ny && !S.sol[lr + 1][lc + 1];
+      S.cvalid[e] = ok;
+      if (!ok) continue;
+      T wu[4], wv[4], wp[4], bu[4], bv[4];
 #pragma unroll
-    for (int m = 0; m < 9; ++m) p[m] = S.w[2][2 * pj + m / 3 - j0 + 2][2 * pi + m % 3 - i0 + 2];
+      for (int a = 0; a < 4; ++a) {
+        const int li = lc + 1 + (a & 1), lj = lr + 1 + (a >> 1);
+        wu[a] = S.w[0][lj][li];
+        wv[a] = S.w[1][lj][li];
+        wp[a] = S.w[2][lj][li];
+        bu[a] = S.vb[0][lj][li];
+        bv[a] = S.vb[1][lj][li];
+      }
+      T r[12];
+      cell_all_rows<T, NONLIN>(s, wu, wv, wp, bu, bv, r);
 #pragma unroll
-    for (int mn = 0; mn < 9; ++mn) {
-      T acc = 0;
+      for (int k = 0; k < 12; ++k) S.cres[e][k] = r[k];
+    } else {
+      const int e = wi - kCX * kCY;
+      const int pi = PI0 + e % kPX, pj = PJ0 + e / kPX;
+      const bool ok = pi >= 0 && pj >= 0 && pi < g.nx / 2 && pj < g.ny / 2 &&
+                      !S.sol[2 * pj - j0 + 2][2 * pi - i0 + 2];
+      S.pvalid[e] = ok;
+      if (!ok) continue;
+      T p[9];
 #pragma unroll
-      for (int m = 0; m < 9; ++m) acc += s.S9[mn * 9 + m] * p[m];
-      S.pres[e][mn] = acc;
+      for (int m = 0; m < 9; ++m) p[m] = S.w[2][2 * pj + m / 3 - j0 + 2][2 * pi + m % 3 - i0 + 2];
+#pragma unroll
+      for (int mn = 0; mn < 9; ++mn) {
+        T acc = 0;
+#pragma unroll
+        for (int m = 0; m < 9; ++m) acc += s.S9[mn * 9 + m] * p[m];
+        S.pres[e][mn] = acc;
+      }
     }
   }
   __syncthreads();
@@ -113,7 +119,7 @@ __device__ __forceinline__ void op_tile_rows(const Grid& g, const Sten<T>& s,
   const int i = i0 + t % TX, j = j0 + t / TX;
   ru = rv = rp = T(0);
   n = -1;
-  if (i > g.nx || j > g.ny) return;
+  if (t >= kNT || i > g.nx || j > g.ny) return;
   n = j * g.nnx + i;
 #pragma unroll
   for (int dyy = 0; dyy < 2; ++dyy)

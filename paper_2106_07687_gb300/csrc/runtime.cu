@@ -326,8 +326,7 @@ class Solver final : public SolverBase {
       int rc;
       if (split_mode_ == 0) {
         // one block per colour-pass tile of the sub-cycle's top level
-        const Grid& gk = lv_[k].g;
-        int blocks = cdiv(gk.nx / 2 + 1, 16) * cdiv(gk.ny / 2 + 1, 4);
+        int blocks = vcycle_coop_tiles(lv_[k].g);
         blocks = blocks < 64 ? 64 : blocks;
         blocks = blocks > vgrid_ ? vgrid_ : blocks;
         rc = launch_vcycle_persistent<T>(dlv_, dph_ + ph_off_[k], ph_n_[k], k, b, x, ainv_,

@@ -151,12 +151,15 @@ struct PassSmem {
   int8_t pvalid[(kTCY + 2) * (kTCX + 2)];
 };
 
-// Tile (bx, by) of the colour pass, computed by 4 kTCX kTCY consecutive
+// Tile (bx, by) of the colour pass, computed by a group of NTT consecutive
 // threads of the block (a block may hold several such groups, each with its
 // own S; every thread of the block must call this together because of the
-// block barriers).  A group with active = false takes part in the barriers
-// only and writes nothing.
-template <typename T, int kTCX, int kTCY>
+// block barriers).  The first 4 kTCX kTCY threads own one node of a colour
+// cell each; with NTT larger, the other threads help stage the tile and
+// compute the cell and patch rows, so that those take one round instead of
+// two.  A group with active = false takes part in the barriers only and
+// writes nothing.
+template <typename T, int kTCX, int kTCY, int NTT = 4 * kTCX * kTCY>
 __device__ __forceinline__ void vanka_pass_tile(const Grid& g, const Sten<T>& s, int colour,
                                                 const T* __restrict__ b, const T* __restrict__ xin,
                                                 const T* __restrict__ vb, const T* __restrict__ inv,
@@ -164,6 +167,7 @@ __device__ __forceinline__ void vanka_pass_tile(const Grid& g, const Sten<T>& s,
                                                 PassSmem<T, kTCX, kTCY>& S, bool active = true) {
   if (!active) bx = by = 0;
   constexpr int kTileThreads = 4 * kTCX * kTCY;
+  static_assert(NTT >= kTileThreads && NTT % 32 == 0 && kTileThreads % 32 == 0, "tile group");
   constexpr int kSX = 2 * kTCX + 4;
   constexpr int kCX = 2 * kTCX + 1, kCY = 2 * kTCY + 1;
   constexpr int kPX = kTCX + 2, kPY = kTCY + 2;
@@ -174,13 +178,14 @@ __device__ __forceinline__ void vanka_pass_tile(const Grid& g, const Sten<T>& s,
   const int nn = g.nn;
   const int tx0 = bx * kTCX, ty0 = by * kTCY;
   const int i0 = 2 * tx0 - cx, j0 = 2 * ty0 - cy;  // first node of the tile
-  const int t = threadIdx.x % kTileThreads;
+  const int t = threadIdx.x % NTT;
+  const bool owner = t < kTileThreads;  // owns a node of a colour cell
   // ---- this thread's node (quad q, local node a) and its loads that do not
   // depend on the defect: b, x_in and its three rows of the cell's inverse,
   // issued first so that their latency overlaps the stencil work below
   const int q = t >> 2, a = t & 3;
   const int ti = tx0 + (q % kTCX), tj = ty0 + (q / kTCX);
-  const bool slot_ok = ti < sx && tj < sy;
+  const bool slot_ok = owner && ti < sx && tj < sy;
   const int slot = tj * sx + ti;
   const int ci = 2 * ti - cx, cj = 2 * tj - cy;
   const int i = ci + (a & 1), j = cj + (a >> 1);
@@ -203,7 +208,7 @@ __device__ __forceinline__ void vanka_pass_tile(const Grid& g, const Sten<T>& s,
   }
   // ---- stage nodes [i0-2, i0-2+kSX) x [j0-2, j0-2+kSY), and the solid flag
   // of the cell whose lower-left node each one is
-  for (int e = t; e < kSX * kSY; e += kTileThreads) {
+  for (int e = t; e < kSX * kSY; e += NTT) {
     const int li = e % kSX, lj = e / kSX;
     const int i = i0 - 2 + li, j = j0 - 2 + lj;
     T xu1 = 0, xv1 = 0, xp1 = 0, bu = 0, bvv = 0;
@@ -230,54 +235,58 @@ __device__ __forceinline__ void vanka_pass_tile(const Grid& g, const Sten<T>& s,
   // own cell (ci, cj) sits at staged index (ci - i0 + 2, cj - j0 + 2)
   const bool cell_ok = slot_ok && ci >= 0 && cj >= 0 && ci < g.nx && cj < g.ny &&
                        !S.sol[cj - j0 + 2][ci - i0 + 2];
-  // ---- cells [i0-1, i0-1+kCX) x [j0-1, j0-1+kCY): 12 rows each
-  for (int e = t; e < kCX * kCY; e += kTileThreads) {
-    const int lc = e % kCX, lr = e / kCX;
-    const int ci = i0 - 1 + lc, cj = j0 - 1 + lr;
-    const bool ok = ci >= 0 && cj >= 0 && ci < g.nx && cj < g.ny && !S.sol[lr + 1][lc + 1];
-    S.cvalid[e] = ok;
-    if (!ok) continue;
-    T wu[4], wv[4], wp[4], bu[4], bv[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int li = lc + 1 + (a & 1), lj = lr + 1 + (a >> 1);  // staged coords of the node
-      wu[a] = S.w[0][lj][li];
-      wv[a] = S.w[1][lj][li];
-      wp[a] = S.w[2][lj][li];
-      bu[a] = S.vb[0][lj][li];
-      bv[a] = S.vb[1][lj][li];
-    }
-    T r[12];
-    cell_all_rows<T, false>(s, wu, wv, wp, bu, bv, r);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) S.cres[e][k] = r[k];
-  }
-  // ---- patches touching the tile: 9 LPS rows each
+  // ---- cells [i0-1, i0-1+kCX) x [j0-1, j0-1+kCY): 12 rows each, and the
+  // patches touching the tile: 9 LPS rows each -- one list of work items
   // patches touching the tile: from ceil((i0 - 2) / 2) (also for negative
   // i0) to floor((i0 + 2 kTCX - 1) / 2), likewise in y
   const int PI0 = (i0 - 1) >> 1, PJ0 = (j0 - 1) >> 1;
   const int PI1 = (i0 + 2 * kTCX - 1) >> 1, PJ1 = (j0 + 2 * kTCY - 1) >> 1;
-  for (int e = t; e < kPX * kPY; e += kTileThreads) {
-    const int pi = PI0 + e % kPX, pj = PJ0 + e / kPX;
-    const bool ok = pi <= PI1 && pj <= PJ1 && pi >= 0 && pj >= 0 && pi < g.nx / 2 &&
-                    pj < g.ny / 2 && !S.sol[2 * pj - j0 + 2][2 * pi - i0 + 2];
-    S.pvalid[e] = ok;
-    if (!ok) continue;
-    T p[9];
+  for (int w = t; w < kCX * kCY + kPX * kPY; w += NTT) {
+    if (w < kCX * kCY) {
+      const int e = w;
+      const int lc = e % kCX, lr = e / kCX;
+      const int ci = i0 - 1 + lc, cj = j0 - 1 + lr;
+      const bool ok = ci >= 0 && cj >= 0 && ci < g.nx && cj < g.ny && !S.sol[lr + 1][lc + 1];
+      S.cvalid[e] = ok;
+      if (!ok) continue;
+      T wu[4], wv[4], wp[4], bu[4], bv[4];
 #pragma unroll
-    for (int m = 0; m < 9; ++m) {
-      const int li = 2 * pi + m % 3 - (i0 - 2), lj = 2 * pj + m / 3 - (j0 - 2);
-      p[m] = S.w[2][lj][li];
-    }
+      for (int a = 0; a < 4; ++a) {
+        const int li = lc + 1 + (a & 1), lj = lr + 1 + (a >> 1);  // staged coords of the node
+        wu[a] = S.w[0][lj][li];
+        wv[a] = S.w[1][lj][li];
+        wp[a] = S.w[2][lj][li];
+        bu[a] = S.vb[0][lj][li];
+        bv[a] = S.vb[1][lj][li];
+      }
+      T r[12];
+      cell_all_rows<T, false>(s, wu, wv, wp, bu, bv, r);
 #pragma unroll
-    for (int mn = 0; mn < 9; ++mn) {
-      T acc = 0;
+      for (int k = 0; k < 12; ++k) S.cres[e][k] = r[k];
+    } else {
+      const int e = w - kCX * kCY;
+      const int pi = PI0 + e % kPX, pj = PJ0 + e / kPX;
+      const bool ok = pi <= PI1 && pj <= PJ1 && pi >= 0 && pj >= 0 && pi < g.nx / 2 &&
+                      pj < g.ny / 2 && !S.sol[2 * pj - j0 + 2][2 * pi - i0 + 2];
+      S.pvalid[e] = ok;
+      if (!ok) continue;
+      T p[9];
 #pragma unroll
-      for (int m = 0; m < 9; ++m) acc += s.S9[mn * 9 + m] * p[m];
-      S.pres[e][mn] = acc;
+      for (int m = 0; m < 9; ++m) {
+        const int li = 2 * pi + m % 3 - (i0 - 2), lj = 2 * pj + m / 3 - (j0 - 2);
+        p[m] = S.w[2][lj][li];
+      }
+#pragma unroll
+      for (int mn = 0; mn < 9; ++mn) {
+        T acc = 0;
+#pragma unroll
+        for (int m = 0; m < 9; ++m) acc += s.S9[mn * 9 + m] * p[m];
+        S.pres[e][mn] = acc;
+      }
     }
   }
   __syncthreads();
+  if (!owner) return;  // helpers are whole warps past the owners
   T du = 0, dv = 0, dp = 0;
   if (node_ok && cell_ok) {
     T ru = 0, rv = 0, rp = 0;

@@ -102,25 +102,42 @@ __device__ __forceinline__ void defect_node(const Grid& g, const Sten<T>& s, con
 
 __device__ __forceinline__ uint8_t field_bit(int c) { return c < 2 ? kVDir : kPFix; }
 
-// Coarse node (I, J) of R d = P^T d on free DOFs (full-weighting stencil).
+// Coarse node (I, J) of R d = P^T d on free DOFs (full-weighting stencil),
+// for the first ncomp <= 3 fields.  Every load (flags and the up to 27 fine
+// values) is issued in one round before any is used; the sums run in the
+// stencil's row order.
 template <typename T, bool MASK>
 __device__ __forceinline__ void restrict_node(const Grid& f, const Grid& c, const T* __restrict__ d,
                                               T* __restrict__ bc, int ncomp, int I, int J) {
   const int nc = J * c.nnx + I;
-  for (int comp = 0; comp < ncomp; ++comp) {
+  const uint8_t cfl = MASK ? c.flags[nc] : uint8_t(0);
+  int nf[9];
+  bool in[9];
+  uint8_t ffl[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    const int i = 2 * I + e % 3 - 1, j = 2 * J + e / 3 - 1;
+    in[e] = i >= 0 && i < f.nnx && j >= 0 && j < f.nny;
+    nf[e] = in[e] ? j * f.nnx + i : 0;
+    ffl[e] = (MASK && in[e]) ? f.flags[nf[e]] : uint8_t(0);
+  }
+  T v[3][9];
+#pragma unroll
+  for (int comp = 0; comp < 3; ++comp)
+#pragma unroll
+    for (int e = 0; e < 9; ++e)
+      v[comp][e] = (comp < ncomp && in[e]) ? d[comp * f.nn + nf[e]] : T(0);
+#pragma unroll
+  for (int comp = 0; comp < 3; ++comp) {
+    if (comp >= ncomp) break;
     const uint8_t bit = field_bit(comp);
     T acc = 0;
-    if (!(MASK && (c.flags[nc] & bit))) {
-      for (int dj = -1; dj <= 1; ++dj) {
-        const int j = 2 * J + dj;
-        if (j < 0 || j >= f.nny) continue;
-        for (int di = -1; di <= 1; ++di) {
-          const int i = 2 * I + di;
-          if (i < 0 || i >= f.nnx) continue;
-          const int nf = j * f.nnx + i;
-          if (MASK && (f.flags[nf] & bit)) continue;
-          acc += (di == 0 ? T(1) : T(0.5)) * (dj == 0 ? T(1) : T(0.5)) * d[comp * f.nn + nf];
-        }
+    if (!(MASK && (cfl & bit))) {
+#pragma unroll
+      for (int e = 0; e < 9; ++e) {
+        if (!in[e] || (MASK && (ffl[e] & bit))) continue;
+        const int di = e % 3 - 1, dj = e / 3 - 1;
+        acc += (di == 0 ? T(1) : T(0.5)) * (dj == 0 ? T(1) : T(0.5)) * v[comp][e];
       }
     }
     bc[comp * c.nn + nc] = acc;
@@ -144,17 +161,45 @@ __device__ __forceinline__ T interp_node(const Grid& c, const T* __restrict__ xc
   return w * acc;
 }
 
-// x += P xc at fine node (i, j) on free DOFs.
+// x += P xc at fine node (i, j) on free DOFs.  The fine flag, the flags and
+// values of the up to four coarse nodes and x are loaded in one round; the
+// interpolant sums the coarse nodes in the same order as interp_node.
 template <typename T>
 __device__ __forceinline__ void prolong_add_node(const Grid& f, const Grid& c,
                                                  const T* __restrict__ xc, T* __restrict__ x,
                                                  int i, int j) {
   const int n = j * f.nnx + i;
+  const int I0 = i >> 1, J0 = j >> 1;
+  const int nI = (i & 1) ? 2 : 1, nJ = (j & 1) ? 2 : 1;
+  int m[4];
+  bool use[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int aa = e & 1, bb = e >> 1;
+    use[e] = aa < nI && bb < nJ;
+    m[e] = use[e] ? (J0 + bb) * c.nnx + I0 + aa : 0;
+  }
   const uint8_t fl = f.flags[n];
+  uint8_t cfl[4];
+  T xv[3], cv[3][4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) cfl[e] = use[e] ? c.flags[m[e]] : uint8_t(0xFF);
+#pragma unroll
+  for (int comp = 0; comp < 3; ++comp) {
+    xv[comp] = x[comp * f.nn + n];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) cv[comp][e] = use[e] ? xc[comp * c.nn + m[e]] : T(0);
+  }
+  const T w = T(1) / T(nI * nJ);
+#pragma unroll
   for (int comp = 0; comp < 3; ++comp) {
     const uint8_t bit = field_bit(comp);
     if (fl & bit) continue;
-    x[comp * f.nn + n] += interp_node<T, true>(c, xc + comp * c.nn, bit, i, j);
+    T acc = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (!(cfl[e] & bit)) acc += cv[comp][e];
+    x[comp * f.nn + n] = xv[comp] + w * acc;
   }
 }
 

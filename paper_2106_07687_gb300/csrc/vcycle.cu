@@ -5,13 +5,15 @@
 // sequence of phases -- Vanka colour passes, defect, restriction (with the
 // coarse iterate zeroed), the coarse direct solve, prolongation -- built once
 // per top level on the host.  The kernel walks the phase list; all blocks
-// work on a phase with grid-stride loops and meet at a barrier (grid-wide,
-// or the hardware cluster barrier) before the next.  Every phase runs the same per-thread bodies as the
-// one-launch-per-stage kernels, so the arithmetic is identical; only the
+// share every phase and meet at a barrier (grid-wide, or the hardware cluster
+// barrier) before the next.  Every phase runs the same per-thread bodies as
+// the one-launch-per-stage kernels, so the arithmetic is identical; only the
 // ~20 kernel launches per level and cycle disappear.
+#include <algorithm>
 #include <cooperative_groups.h>
 
 #include "kernels.h"
+#include "optile_body.cuh"
 #include "vanka_body.cuh"
 #include "vbody.cuh"
 #include "vcycle.h"
@@ -22,14 +24,22 @@ namespace dnnmg {
 
 namespace {
 
-constexpr int kThreads = 256;        // threads per block, cooperative grid
+// Colour-pass tiles (colour cells).  The cooperative kernel takes 8 x 4
+// tiles, one per block at a time: on the small levels of a sub-cycle the
+// tile's cell rows (ALU-bound on one SM) are the longest part of a pass, and
+// smaller tiles spread a level over more SMs.  Its blocks have 256 threads:
+// 128 own the tile's nodes and 128 help stage it and compute its rows.  The
+// single-cluster kernel (16 blocks) keeps 16 x 4 tiles, two per block.
+constexpr int kCTX = 8, kCTY = 4;
+constexpr int kLTX = 16, kLTY = 4;
+constexpr int kCoopOwners = 4 * kCTX * kCTY;
+constexpr int kCoopThreads = 2 * kCoopOwners;
+constexpr int kClusterOwners = 4 * kLTX * kLTY;
 // threads per block of the single-cluster launch (FP64 needs more registers)
 template <typename T>
 constexpr int cluster_threads() {
-  return sizeof(T) == 4 ? 512 : 256;
+  return sizeof(T) == 4 ? 2 * kClusterOwners : kClusterOwners;
 }
-
-constexpr int kTCX = 16, kTCY = 4;  // colour-pass tile of the persistent kernels
 constexpr int kMaxPhases = 160;  // phases of one launch (a V(2,2) cycle from level 8)
 constexpr int kMaxVLevels = 10;
 
@@ -41,18 +51,35 @@ struct WalkSmem {
   Phase ph[kMaxPhases];
 };
 
+// Item n < count of a node-wise phase for every thread of the grid: chunks
+// of 32 consecutive items (one warp, coalesced) go round-robin over the
+// blocks first, so that a small level still spreads over all of them.
+template <int NT, class F>
+__device__ __forceinline__ void for_items(int count, F f) {
+  constexpr int kWarps = NT / 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nchunks = (count + 31) >> 5;
+  for (int c = blockIdx.x + gridDim.x * w; c < nchunks; c += gridDim.x * kWarps) {
+    const int n = (c << 5) + lane;
+    if (n < count) f(n);
+  }
+}
+
 // Walk the phase list; `sync` separates phases (a grid-wide barrier for the
 // cooperative launch, the cluster barrier for the single-cluster launch).
-// Threads of all blocks split every phase with grid-stride loops.
-template <typename T, int NT, class Sync>
+// Threads of all blocks split every node-wise phase; a colour pass gives each
+// group of NTT threads of a block one TCX x TCY tile at a time.
+template <typename T, int TCX, int TCY, int NT, int NTT, class Sync>
 __device__ __forceinline__ void walk_phases(const VLevel<T>* __restrict__ glv,
                                             const Phase* __restrict__ gph, int nph, int top,
                                             const T* __restrict__ topb, T* __restrict__ topx,
                                             const double* __restrict__ Ainv, T omega,
-                                            double* sbuf, PassSmem<T, kTCX, kTCY>* tsm,
-                                            WalkSmem<T>& S, Sync sync) {
-  const int nthreads = gridDim.x * NT;
-  const int gtid = blockIdx.x * NT + threadIdx.x;
+                                            uint8_t* dyn, WalkSmem<T>& S, Sync sync) {
+  // dynamic shared memory: the pass tiles, the defect tile or the coarse vector
+  double* sbuf = reinterpret_cast<double*>(dyn);
+  PassSmem<T, TCX, TCY>* tsm = reinterpret_cast<PassSmem<T, TCX, TCY>*>(dyn);
+  constexpr int kDX = 16, kDY = 8;  // defect tile: owners plus helpers, as a pass tile
+  auto& dsm = *reinterpret_cast<OpSmem<T, kDX, kDY>*>(dyn);
   {
     const int nl = top + 1;
     const int* src = reinterpret_cast<const int*>(glv);
@@ -64,6 +91,8 @@ __device__ __forceinline__ void walk_phases(const VLevel<T>* __restrict__ glv,
     for (int e = threadIdx.x; e < (int)(nph * sizeof(Phase) / sizeof(int)); e += NT) pd[e] = ps[e];
     __syncthreads();
   }
+  constexpr int kTiles = NT / NTT;  // pass tiles in flight per block
+  const int sub = threadIdx.x / NTT;
   for (int p = 0; p < nph; ++p) {
     const Phase f = S.ph[p];
     const int k = f.level;
@@ -74,61 +103,99 @@ __device__ __forceinline__ void walk_phases(const VLevel<T>* __restrict__ glv,
     T* x0 = k == top ? topx : L.x;
     switch (f.type) {
       case kPhasePass: {
-        // tiles of kTCX x kTCY colour cells, NT / (4 kTCX kTCY) tiles per block at a time
+        // tiles of TCX x TCY colour cells, kTiles per block at a time
         const T* xin = f.in ? L.x2 : x0;
         T* xout = f.out ? L.x2 : x0;
-        constexpr int kTiles = NT / (4 * kTCX * kTCY);
-        const int sub = threadIdx.x / (4 * kTCX * kTCY);
-        const int nbx = cdiv(g.nx / 2 + 1, kTCX);
-        const int nt = nbx * cdiv(g.ny / 2 + 1, kTCY);
+        const int nbx = cdiv(g.nx / 2 + 1, TCX);
+        const int nt = nbx * cdiv(g.ny / 2 + 1, TCY);
         for (int t0 = blockIdx.x * kTiles; t0 < nt; t0 += gridDim.x * kTiles) {
           const int t = t0 + sub;
-          vanka_pass_tile<T, kTCX, kTCY>(g, ss, f.colour, b, xin, L.vb, L.inv, omega, xout,
-                                         t % nbx, t / nbx, tsm[sub], t < nt);
+          vanka_pass_tile<T, TCX, TCY, NTT>(g, ss, f.colour, b, xin, L.vb, L.inv, omega, xout,
+                                            t % nbx, t / nbx, tsm[sub], t < nt);
           __syncthreads();  // the tile's shared memory is reused by the next tile
         }
         break;
       }
       case kPhaseDefect: {
+        // tiles of kDX x kDY nodes, each cell's rows computed once per tile
         const T* x = f.in ? L.x2 : x0;
-        for (int n = gtid; n < g.nn; n += nthreads)
-          defect_node<T>(g, ss, b, x, L.vb, L.d, true, n % g.nnx, n / g.nnx);
+        const int ntx = cdiv(g.nnx, kDX), ntiles = ntx * cdiv(g.nny, kDY);
+        const int nn = g.nn;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+          T ru, rv, rp;
+          int n;
+          op_tile_rows<T, false, true, kDX, kDY, NT>(g, ss, x, L.vb, t % ntx, t / ntx, dsm, ru, rv,
+                                                     rp, n);
+          if (n >= 0) {
+            const uint8_t fl = op_tile_flags<T, kDX, kDY>(dsm);
+            L.d[n] = (fl & kVDir) ? T(0) : b[n] - ru;
+            L.d[nn + n] = (fl & kVDir) ? T(0) : b[nn + n] - rv;
+            L.d[2 * nn + n] = (fl & kPFix) ? T(0) : b[2 * nn + n] - rp;
+          }
+          __syncthreads();  // the tile's shared memory is reused by the next tile
+        }
         break;
       }
       case kPhaseRestrict: {
         const VLevel<T>& C = S.lv[k - 1];
         const Grid& c = C.g;
-        for (int n = gtid; n < c.nn; n += nthreads) {
+        for_items<NT>(c.nn, [&](int n) {
           restrict_node<T, true>(g, c, L.d, C.b, 3, n % c.nnx, n / c.nnx);
           C.x[n] = T(0);
           C.x[c.nn + n] = T(0);
           C.x[2 * c.nn + n] = T(0);
-        }
+        });
         break;
       }
       case kPhaseCoarse: {
         const int nd = 3 * g.nn;
-        for (int q = threadIdx.x; q < nd; q += NT) sbuf[q] = (double)b[band_to_level(g, q)];
+        for (int q0 = threadIdx.x; q0 < nd; q0 += 4 * NT) {  // four loads in flight
+          double v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int q = q0 + u * NT;
+            v[u] = q < nd ? (double)b[band_to_level(g, q)] : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (q0 + u * NT < nd) sbuf[q0 + u * NT] = v[u];
+        }
         __syncthreads();
-        const int warp = gtid >> 5, lane = threadIdx.x & 31, nwarps = nthreads >> 5;
-        for (int r = warp; r < nd; r += nwarps) {
+        // one warp per row, rows round-robin over the blocks first
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        for (int r = blockIdx.x + gridDim.x * w; r < nd; r += gridDim.x * (NT / 32)) {
           const double* row = Ainv + (size_t)r * nd;
-          double acc = 0.0;
-          for (int c2 = lane; c2 < nd; c2 += 32) acc += row[c2] * sbuf[c2];
-          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-          if (lane == 0) x0[band_to_level(g, r)] = (T)acc;
+          // chunks of 16 entries per lane: every load of a chunk is issued
+          // before its products are summed, so that a row of up to 512
+          // entries costs one round trip to L2 instead of one per entry
+          double acc[4] = {0.0, 0.0, 0.0, 0.0};
+          for (int c0 = lane; c0 < nd; c0 += 16 * 32) {
+            double rv[16], sv[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+              const int c2 = c0 + 32 * u;
+              rv[u] = c2 < nd ? row[c2] : 0.0;
+              sv[u] = c2 < nd ? sbuf[c2] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 16; ++u) acc[u & 3] += rv[u] * sv[u];
+          }
+          double a = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+          for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+          if (lane == 0) x0[band_to_level(g, r)] = (T)a;
         }
         break;
       }
       case kPhaseProlong: {
         const VLevel<T>& C = S.lv[k - 1];
         T* x = f.in ? L.x2 : x0;
-        for (int n = gtid; n < g.nn; n += nthreads)
+        for_items<NT>(g.nn, [&](int n) {
           prolong_add_node<T>(g, C.g, C.x, x, n % g.nnx, n / g.nnx);
+        });
         break;
       }
       case kPhaseZeroTop: {
-        for (int n = gtid; n < 3 * g.nn; n += nthreads) topx[n] = T(0);
+        for_items<NT>(3 * g.nn, [&](int n) { topx[n] = T(0); });
         break;
       }
     }
@@ -137,17 +204,15 @@ __device__ __forceinline__ void walk_phases(const VLevel<T>* __restrict__ glv,
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kCoopThreads)
     vcycle_kernel(const VLevel<T>* __restrict__ lv, const Phase* __restrict__ ph, int nph, int top,
                   const T* __restrict__ topb, T* __restrict__ topx, const double* __restrict__ Ainv,
                   T omega) {
   extern __shared__ __align__(16) uint8_t dyn[];  // coarse vector or pass tiles
   __shared__ WalkSmem<T> S;
   cg::grid_group grid = cg::this_grid();
-  walk_phases<T, kThreads>(lv, ph, nph, top, topb, topx, Ainv, omega,
-                           reinterpret_cast<double*>(dyn),
-                           reinterpret_cast<PassSmem<T, kTCX, kTCY>*>(dyn), S,
-                           [&] { grid.sync(); });
+  walk_phases<T, kCTX, kCTY, kCoopThreads, kCoopThreads>(lv, ph, nph, top, topb, topx, Ainv,
+                                                         omega, dyn, S, [&] { grid.sync(); });
 }
 
 // The whole grid is one thread-block cluster; phases are separated by the
@@ -161,10 +226,8 @@ __global__ void __launch_bounds__(cluster_threads<T>())
   extern __shared__ __align__(16) uint8_t dyn[];  // coarse vector or pass tiles
   __shared__ WalkSmem<T> S;
   cg::cluster_group cl = cg::this_cluster();
-  walk_phases<T, cluster_threads<T>()>(lv, ph, nph, top, topb, topx, Ainv, omega,
-                                       reinterpret_cast<double*>(dyn),
-                                       reinterpret_cast<PassSmem<T, kTCX, kTCY>*>(dyn), S,
-                                       [&] { cl.sync(); });
+  walk_phases<T, kLTX, kLTY, cluster_threads<T>(), kClusterOwners>(
+      lv, ph, nph, top, topb, topx, Ainv, omega, dyn, S, [&] { cl.sync(); });
 }
 
 void build_phases(int k, int top, int nu1, int nu2, std::vector<Phase>& out) {
@@ -193,15 +256,21 @@ void build_phases(int k, int top, int nu1, int nu2, std::vector<Phase>& out) {
 }  // namespace
 
 namespace {
-// dynamic shared memory of a block of nt threads: the coarse right-hand
-// side (FP64) or the block's pass tiles, whichever is larger
-template <typename T>
-size_t walk_smem(int coarse_nd, int nt) {
-  const size_t tiles = sizeof(PassSmem<T, kTCX, kTCY>) * (nt / (4 * kTCX * kTCY));
-  const size_t cv = sizeof(double) * coarse_nd;
-  return tiles > cv ? tiles : cv;
+// dynamic shared memory of a block with `tiles_in_flight` TCX x TCY pass
+// tiles: the largest of the coarse right-hand side (FP64), the pass tiles and
+// the 16 x 8-node defect tile
+template <typename T, int TCX, int TCY>
+size_t walk_smem(int coarse_nd, int tiles_in_flight) {
+  size_t m = sizeof(PassSmem<T, TCX, TCY>) * tiles_in_flight;
+  m = std::max(m, sizeof(double) * coarse_nd);
+  m = std::max(m, sizeof(OpSmem<T, 16, 8>));
+  return m;
 }
 }  // namespace
+
+int vcycle_coop_tiles(const Grid& g) {
+  return cdiv(g.nx / 2 + 1, kCTX) * cdiv(g.ny / 2 + 1, kCTY);
+}
 
 bool vcycle_fits(int nphases, int nlevels) {
   return nphases <= kMaxPhases && nlevels <= kMaxVLevels;
@@ -219,13 +288,13 @@ int vcycle_grid(int coarse_nd) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const size_t smem = walk_smem<T>(coarse_nd, kThreads);
+  const size_t smem = walk_smem<T, kCTX, kCTY>(coarse_nd, 1);
   if (cudaFuncSetAttribute(vcycle_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, vcycle_kernel<T>, kThreads, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, vcycle_kernel<T>, kCoopThreads, smem) !=
           cudaSuccess ||
       per <= 0)
     return 0;
@@ -241,14 +310,14 @@ int launch_vcycle_persistent(const VLevel<T>* lv, const Phase* ph, int nph, int 
                   (void*)&topx, (void*)&Ainv, (void*)&omega};
   note_launch();
   const cudaError_t e =
-      cudaLaunchCooperativeKernel((void*)vcycle_kernel<T>, dim3(grid), dim3(kThreads), args,
-                                  walk_smem<T>(coarse_nd, kThreads), st);
+      cudaLaunchCooperativeKernel((void*)vcycle_kernel<T>, dim3(grid), dim3(kCoopThreads), args,
+                                  walk_smem<T, kCTX, kCTY>(coarse_nd, 1), st);
   return e == cudaSuccess ? 0 : 1;
 }
 
 template <typename T>
 int vcycle_cluster_size(int coarse_nd) {
-  const size_t smem = walk_smem<T>(coarse_nd, cluster_threads<T>());
+  const size_t smem = walk_smem<T, kLTX, kLTY>(coarse_nd, cluster_threads<T>() / kClusterOwners);
   if (cudaFuncSetAttribute(vcycle_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess) {
     cudaGetLastError();
@@ -293,7 +362,7 @@ int launch_vcycle_cluster(const VLevel<T>* lv, const Phase* ph, int nph, int top
   attr[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3(cluster);
   cfg.blockDim = dim3(cluster_threads<T>());
-  cfg.dynamicSmemBytes = walk_smem<T>(coarse_nd, cluster_threads<T>());
+  cfg.dynamicSmemBytes = walk_smem<T, kLTX, kLTY>(coarse_nd, cluster_threads<T>() / kClusterOwners);
   cfg.stream = st;
   cfg.attrs = attr;
   cfg.numAttrs = 1;

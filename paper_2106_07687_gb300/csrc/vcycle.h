@@ -28,6 +28,8 @@ std::vector<Phase> vcycle_phases(int top, int nu1, int nu2);
 // whether a launch of nphases phases over nlevels levels fits the kernels'
 // shared-memory tables
 bool vcycle_fits(int nphases, int nlevels);
+// colour-pass tiles of the cooperative kernel on a level (its natural grid)
+int vcycle_coop_tiles(const Grid& g);
 // co-resident grid size for the cooperative launch (0 if not available)
 template <typename T>
 int vcycle_grid(int coarse_nd);
