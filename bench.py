@@ -37,9 +37,12 @@ WORKLOAD = ("DNN-MG time step: multigrid on the 512x128 channel (level 5, 198,53
             "dt=0.005, mixed FP32/FP64")
 ORACLE_L = 4              # bounded CPU sample: oracle DNN-MG step with L = 4, scaled by DOFs
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel
-# as it stands (profiles/vcycle_subcycle_level5.md); a kernel change makes
-# the entry stale and it must then be removed.
-NCU_TRAFFIC = {"vcycle_kernel<float>@split4": 19723264 + 12544}
+# as it stands, per V-cycle plan (profiles/vcycle_subcycle_level5.md for the
+# level 4..1 sub-cycle, profiles/vcycle_level5_split5.md for the whole
+# level-5 cycle); a kernel change makes the entries stale and they must then
+# be removed.
+NCU_TRAFFIC = {"vcycle_kernel<float>@split4": 19723264 + 12544,
+               "vcycle_kernel<float>@split5": 59302400 + 979968}
 L2_BYTES = 129 * 2 ** 20
 
 
