@@ -71,47 +71,47 @@ __device__ __forceinline__ void op_tile_rows(const Grid& g, const Sten<T>& s,
   __syncthreads();
   // ---- cells [i0-1, i0+TX) x [j0-1, j0+TY): 12 rows each, and the patches
   // I in [i0/2 - 1, i0/2 + TX/2 - 1] (those with 2I <= i <= 2I+2 for a node i
-  // of the tile), likewise J: 9 LPS rows each -- one list of work items
+  // of the tile), likewise J: 9 LPS rows each
   const int PI0 = i0 / 2 - 1, PJ0 = j0 / 2 - 1;
-  for (int wi = t; wi < kCX * kCY + kPX * kPY; wi += NTT) {
-    if (wi < kCX * kCY) {
-      const int e = wi;
-      const int lc = e % kCX, lr = e / kCX;
-      const int ci = i0 - 1 + lc, cj = j0 - 1 + lr;
-      const bool ok = ci >= 0 && cj >= 0 && ci < g.nx && cj < g.ny && !S.sol[lr + 1][lc + 1];
-      S.cvalid[e] = ok;
-      if (!ok) continue;
-      T wu[4], wv[4], wp[4], bu[4], bv[4];
+  for (int e = t; e < kCX * kCY; e += NTT) {
+    const int lc = e % kCX, lr = e / kCX;
+    const int ci = i0 - 1 + lc, cj = j0 - 1 + lr;
+    const bool ok = ci >= 0 && cj >= 0 && ci < g.nx && cj < g.ny && !S.sol[lr + 1][lc + 1];
+    S.cvalid[e] = ok;
+    if (!ok) continue;
+    T wu[4], wv[4], wp[4], bu[4], bv[4];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const int li = lc + 1 + (a & 1), lj = lr + 1 + (a >> 1);
-        wu[a] = S.w[0][lj][li];
-        wv[a] = S.w[1][lj][li];
-        wp[a] = S.w[2][lj][li];
-        bu[a] = S.vb[0][lj][li];
-        bv[a] = S.vb[1][lj][li];
-      }
-      T r[12];
-      cell_all_rows<T, NONLIN>(s, wu, wv, wp, bu, bv, r);
+    for (int a = 0; a < 4; ++a) {
+      const int li = lc + 1 + (a & 1), lj = lr + 1 + (a >> 1);
+      wu[a] = S.w[0][lj][li];
+      wv[a] = S.w[1][lj][li];
+      wp[a] = S.w[2][lj][li];
+      bu[a] = S.vb[0][lj][li];
+      bv[a] = S.vb[1][lj][li];
+    }
+    T r[12];
+    cell_all_rows<T, NONLIN>(s, wu, wv, wp, bu, bv, r);
 #pragma unroll
-      for (int k = 0; k < 12; ++k) S.cres[e][k] = r[k];
-    } else {
-      const int e = wi - kCX * kCY;
-      const int pi = PI0 + e % kPX, pj = PJ0 + e / kPX;
-      const bool ok = pi >= 0 && pj >= 0 && pi < g.nx / 2 && pj < g.ny / 2 &&
-                      !S.sol[2 * pj - j0 + 2][2 * pi - i0 + 2];
-      S.pvalid[e] = ok;
-      if (!ok) continue;
-      T p[9];
+    for (int k = 0; k < 12; ++k) S.cres[e][k] = r[k];
+  }
+  // the patches start where the cells left off, on the threads that the
+  // cell loop leaves idle (a rotation of the thread index)
+  constexpr int kOff = (kCX * kCY) % NTT;
+  for (int e = (t + NTT - kOff) % NTT; e < kPX * kPY; e += NTT) {
+    const int pi = PI0 + e % kPX, pj = PJ0 + e / kPX;
+    const bool ok = pi >= 0 && pj >= 0 && pi < g.nx / 2 && pj < g.ny / 2 &&
+                    !S.sol[2 * pj - j0 + 2][2 * pi - i0 + 2];
+    S.pvalid[e] = ok;
+    if (!ok) continue;
+    T p[9];
 #pragma unroll
-      for (int m = 0; m < 9; ++m) p[m] = S.w[2][2 * pj + m / 3 - j0 + 2][2 * pi + m % 3 - i0 + 2];
+    for (int m = 0; m < 9; ++m) p[m] = S.w[2][2 * pj + m / 3 - j0 + 2][2 * pi + m % 3 - i0 + 2];
 #pragma unroll
-      for (int mn = 0; mn < 9; ++mn) {
-        T acc = 0;
+    for (int mn = 0; mn < 9; ++mn) {
+      T acc = 0;
 #pragma unroll
-        for (int m = 0; m < 9; ++m) acc += s.S9[mn * 9 + m] * p[m];
-        S.pres[e][mn] = acc;
-      }
+      for (int m = 0; m < 9; ++m) acc += s.S9[mn * 9 + m] * p[m];
+      S.pres[e][mn] = acc;
     }
   }
   __syncthreads();

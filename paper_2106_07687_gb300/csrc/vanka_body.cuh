@@ -235,54 +235,54 @@ __device__ __forceinline__ void vanka_pass_tile(const Grid& g, const Sten<T>& s,
   // own cell (ci, cj) sits at staged index (ci - i0 + 2, cj - j0 + 2)
   const bool cell_ok = slot_ok && ci >= 0 && cj >= 0 && ci < g.nx && cj < g.ny &&
                        !S.sol[cj - j0 + 2][ci - i0 + 2];
-  // ---- cells [i0-1, i0-1+kCX) x [j0-1, j0-1+kCY): 12 rows each, and the
-  // patches touching the tile: 9 LPS rows each -- one list of work items
-  // patches touching the tile: from ceil((i0 - 2) / 2) (also for negative
-  // i0) to floor((i0 + 2 kTCX - 1) / 2), likewise in y
+  // ---- cells [i0-1, i0-1+kCX) x [j0-1, j0-1+kCY): 12 rows each, then the
+  // patches touching the tile: 9 LPS rows each; these are the patches from
+  // ceil((i0 - 2) / 2) (also for negative i0) to floor((i0 + 2 kTCX - 1) / 2),
+  // likewise in y
   const int PI0 = (i0 - 1) >> 1, PJ0 = (j0 - 1) >> 1;
   const int PI1 = (i0 + 2 * kTCX - 1) >> 1, PJ1 = (j0 + 2 * kTCY - 1) >> 1;
-  for (int w = t; w < kCX * kCY + kPX * kPY; w += NTT) {
-    if (w < kCX * kCY) {
-      const int e = w;
-      const int lc = e % kCX, lr = e / kCX;
-      const int ci = i0 - 1 + lc, cj = j0 - 1 + lr;
-      const bool ok = ci >= 0 && cj >= 0 && ci < g.nx && cj < g.ny && !S.sol[lr + 1][lc + 1];
-      S.cvalid[e] = ok;
-      if (!ok) continue;
-      T wu[4], wv[4], wp[4], bu[4], bv[4];
+  for (int e = t; e < kCX * kCY; e += NTT) {
+    const int lc = e % kCX, lr = e / kCX;
+    const int ci = i0 - 1 + lc, cj = j0 - 1 + lr;
+    const bool ok = ci >= 0 && cj >= 0 && ci < g.nx && cj < g.ny && !S.sol[lr + 1][lc + 1];
+    S.cvalid[e] = ok;
+    if (!ok) continue;
+    T wu[4], wv[4], wp[4], bu[4], bv[4];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const int li = lc + 1 + (a & 1), lj = lr + 1 + (a >> 1);  // staged coords of the node
-        wu[a] = S.w[0][lj][li];
-        wv[a] = S.w[1][lj][li];
-        wp[a] = S.w[2][lj][li];
-        bu[a] = S.vb[0][lj][li];
-        bv[a] = S.vb[1][lj][li];
-      }
-      T r[12];
-      cell_all_rows<T, false>(s, wu, wv, wp, bu, bv, r);
+    for (int a = 0; a < 4; ++a) {
+      const int li = lc + 1 + (a & 1), lj = lr + 1 + (a >> 1);  // staged coords of the node
+      wu[a] = S.w[0][lj][li];
+      wv[a] = S.w[1][lj][li];
+      wp[a] = S.w[2][lj][li];
+      bu[a] = S.vb[0][lj][li];
+      bv[a] = S.vb[1][lj][li];
+    }
+    T r[12];
+    cell_all_rows<T, false>(s, wu, wv, wp, bu, bv, r);
 #pragma unroll
-      for (int k = 0; k < 12; ++k) S.cres[e][k] = r[k];
-    } else {
-      const int e = w - kCX * kCY;
-      const int pi = PI0 + e % kPX, pj = PJ0 + e / kPX;
-      const bool ok = pi <= PI1 && pj <= PJ1 && pi >= 0 && pj >= 0 && pi < g.nx / 2 &&
-                      pj < g.ny / 2 && !S.sol[2 * pj - j0 + 2][2 * pi - i0 + 2];
-      S.pvalid[e] = ok;
-      if (!ok) continue;
-      T p[9];
+    for (int k = 0; k < 12; ++k) S.cres[e][k] = r[k];
+  }
+  // the patches start where the cells left off, on the threads that the
+  // cell loop leaves idle (a rotation of the thread index)
+  constexpr int kOff = (kCX * kCY) % NTT;
+  for (int e = (t + NTT - kOff) % NTT; e < kPX * kPY; e += NTT) {
+    const int pi = PI0 + e % kPX, pj = PJ0 + e / kPX;
+    const bool ok = pi <= PI1 && pj <= PJ1 && pi >= 0 && pj >= 0 && pi < g.nx / 2 &&
+                    pj < g.ny / 2 && !S.sol[2 * pj - j0 + 2][2 * pi - i0 + 2];
+    S.pvalid[e] = ok;
+    if (!ok) continue;
+    T p[9];
 #pragma unroll
-      for (int m = 0; m < 9; ++m) {
-        const int li = 2 * pi + m % 3 - (i0 - 2), lj = 2 * pj + m / 3 - (j0 - 2);
-        p[m] = S.w[2][lj][li];
-      }
+    for (int m = 0; m < 9; ++m) {
+      const int li = 2 * pi + m % 3 - (i0 - 2), lj = 2 * pj + m / 3 - (j0 - 2);
+      p[m] = S.w[2][lj][li];
+    }
 #pragma unroll
-      for (int mn = 0; mn < 9; ++mn) {
-        T acc = 0;
+    for (int mn = 0; mn < 9; ++mn) {
+      T acc = 0;
 #pragma unroll
-        for (int m = 0; m < 9; ++m) acc += s.S9[mn * 9 + m] * p[m];
-        S.pres[e][mn] = acc;
-      }
+      for (int m = 0; m < 9; ++m) acc += s.S9[mn * 9 + m] * p[m];
+      S.pres[e][mn] = acc;
     }
   }
   __syncthreads();
