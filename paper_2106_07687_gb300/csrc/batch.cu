@@ -137,7 +137,7 @@ class Batch final : public BatchBase {
     std::vector<int2> it;
     for (int p = 0; p < n_; ++p)
       if (L_[p] >= k) {
-        const int nsb = cdiv(vanka_slots(hl_[p][k].g), 128);
+        const int nsb = cdiv(vanka_slots(hl_[p][k].g), kSetupCells);
         for (int b = 0; b < 4 * nsb; ++b) it.push_back(make_int2(p, b));
       }
     return make_table(it);

@@ -250,8 +250,6 @@ __global__ void __launch_bounds__(kNB)
   L.vb[L.g.nn + n] = (T)L.vb64[L.g.nn + n];
 }
 
-constexpr int kSetupThreads = 128;
-
 // work: (problem, colour * slot_blocks + slot_block)
 template <typename T>
 __global__ void __launch_bounds__(kSetupThreads)
@@ -262,9 +260,9 @@ __global__ void __launch_bounds__(kSetupThreads)
   __shared__ Sten<T> ss;
   const BLev<T> L = lev_of(v, wk.x, k);
   load_const(ss, v.sT[(size_t)wk.x * v.nL + k]);
-  const int nsb = cdiv(vanka_slots(L.g), kSetupThreads);
+  const int nsb = cdiv(vanka_slots(L.g), kSetupCells);
   vanka_setup_cell<T>(L.g, ss, L.vb, L.inv, status + wk.x, wk.y / nsb,
-                      (wk.y % nsb) * kSetupThreads + threadIdx.x);
+                      (wk.y % nsb) * kSetupCells + threadIdx.x / 16);
 }
 
 template <typename T>

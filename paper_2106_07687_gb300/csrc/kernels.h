@@ -65,6 +65,9 @@ void launch_vanka_pass(const Grid& g, const Sten<T>& s, int colour, const T* b, 
                        const T* vb, const T* inv, T omega, T* xout, cudaStream_t st,
                        int shape = 0);
 __host__ __device__ inline int vanka_slots(const Grid& g) { return (g.nx / 2 + 1) * (g.ny / 2 + 1); }
+// Vanka setup kernels: 16 lanes per cell, kSetupCells cells per block
+constexpr int kSetupThreads = 128;
+constexpr int kSetupCells = kSetupThreads / 16;
 
 // Coarse direct solve (coarse.cu) -------------------------------------------
 // Assemble the banded Jacobian of the coarsest level (FP64), factor it with

@@ -9,13 +9,13 @@ namespace dnnmg {
 
 namespace {
 
-constexpr int kSetupThreads = 128;
 
 template <typename T>
 __global__ void __launch_bounds__(kSetupThreads)
     vanka_setup_kernel(Grid g, Sten<T> s, const T* __restrict__ vb, T* __restrict__ inv,
                        int* status) {
-  vanka_setup_cell<T>(g, s, vb, inv, status, blockIdx.y, blockIdx.x * kSetupThreads + threadIdx.x);
+  vanka_setup_cell<T>(g, s, vb, inv, status, blockIdx.y,
+                      blockIdx.x * kSetupCells + threadIdx.x / 16);
 }
 
 template <typename T, int TCX, int TCY>
@@ -50,7 +50,7 @@ void pass_shape(const Grid& g, const Sten<T>& s, int colour, const T* b, const T
 template <typename T>
 void launch_vanka_setup(const Grid& g, const Sten<T>& s, const T* vb, T* inv, int* status,
                         cudaStream_t st) {
-  dim3 grid(cdiv(vanka_slots(g), kSetupThreads), 4);
+  dim3 grid(cdiv(vanka_slots(g), kSetupCells), 4);
   note_launch();
   vanka_setup_kernel<T><<<grid, kSetupThreads, 0, st>>>(g, s, vb, inv, status);
 }

@@ -26,7 +26,16 @@ __device__ __forceinline__ T vk_abs(T v) {
   return v < T(0) ? -v : v;
 }
 
-// Inverse of the local 12x12 block of the cell of `slot` in `colour`.
+// Inverse of the local 12x12 block of the cell of `slot` in `colour`,
+// computed by a group of 16 consecutive lanes (a half-warp; every lane of it
+// calls this with the same cell).  Lane r < 12 assembles row r = (c, a) of
+// the block (component c of local node a) from the cells around node a and
+// keeps row r of [A | I] in registers; Gauss-Jordan elimination with partial
+// pivoting then runs across the lanes: at step k the unused lane with the
+// largest |A[.][k]| (lowest lane on ties) is the pivot row, its normalised
+// row is broadcast by shuffles and every other lane eliminates column k.
+// Rows are never swapped; the lane that pivoted on column k ends with row k
+// of the inverse in its right half.
 template <typename T>
 __device__ __forceinline__ void vanka_setup_cell(const Grid& g, const Sten<T>& s,
                                                  const T* __restrict__ vb, T* __restrict__ inv,
@@ -37,100 +46,109 @@ __device__ __forceinline__ void vanka_setup_cell(const Grid& g, const Sten<T>& s
   if (slot >= nslots) return;
   const int ci = 2 * (slot % sx) - cx, cj = 2 * (slot / sx) - cy;
   if (ci < 0 || cj < 0 || ci >= g.nx || cj >= g.ny || g.solid[cj * g.nx + ci]) return;
+  const int lane = threadIdx.x & 15;
+  const unsigned mask = 0xFFFFu << (threadIdx.x & 16);  // this half-warp
+  const int r = lane < 12 ? lane : 0;                   // lanes 12..15 shadow row 0
+  const int c = r >> 2, a = r & 3;
+  const int ai = ci + (a & 1), aj = cj + (a >> 1);       // node a
 
-  T A[12][24];
+  T A[24];
 #pragma unroll
-  for (int r = 0; r < 12; ++r)
+  for (int k = 0; k < 24; ++k) A[k] = T(0);
+  // element contributions of the (up to) 4 cells around node a, in the
+  // order of the cells around the block's cell (rows first)
 #pragma unroll
-    for (int c = 0; c < 24; ++c) A[r][c] = T(0);
-
-  // element contributions of the (up to) 9 cells sharing a node with this one
-  for (int dy = -1; dy <= 1; ++dy)
-    for (int dx = -1; dx <= 1; ++dx) {
-      const int tx = ci + dx, ty = cj + dy;
-      if (tx < 0 || ty < 0 || tx >= g.nx || ty >= g.ny || g.solid[ty * g.nx + tx]) continue;
+  for (int ty = 0; ty < 2; ++ty)
+#pragma unroll
+    for (int tx = 0; tx < 2; ++tx) {
+      const int Tx = ai - 1 + tx, Ty = aj - 1 + ty;
+      if (Tx < 0 || Ty < 0 || Tx >= g.nx || Ty >= g.ny || g.solid[Ty * g.nx + Tx]) continue;
       T bu[4], bv[4];
-      load_cell<T, false>(g, vb, tx, ty, 0, bu);
-      load_cell<T, false>(g, vb + g.nn, tx, ty, 0, bv);
+      load_cell<T, false>(g, vb, Tx, Ty, 0, bu);
+      load_cell<T, false>(g, vb + g.nn, Tx, Ty, 0, bv);
       GaussData<T> gd;
       gauss_data<T>(bu, bv, gd);
-      for (int a = 0; a < 4; ++a) {
-        const int alx = (a & 1) - dx, aly = (a >> 1) - dy;
-        if (alx < 0 || alx > 1 || aly < 0 || aly > 1) continue;
-        for (int b = 0; b < 4; ++b) {
-          const int bex = (b & 1) - dx, bey = (b >> 1) - dy;
-          if (bex < 0 || bex > 1 || bey < 0 || bey > 1) continue;
-          T J[3][3];
-          elem_pair<T>(s, gd, alx + 2 * aly, bex + 2 * bey, J);
-          for (int c = 0; c < 3; ++c)
-            for (int c2 = 0; c2 < 3; ++c2) A[c * 4 + a][c2 * 4 + b] += J[c][c2];
-        }
+      const int al = (ai - Tx) + 2 * (aj - Ty);
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int bex = ci + (b & 1) - Tx, bey = cj + (b >> 1) - Ty;
+        if (bex < 0 || bex > 1 || bey < 0 || bey > 1) continue;
+        T J[3][3];
+        elem_pair<T>(s, gd, al, bex + 2 * bey, J);
+#pragma unroll
+        for (int c2 = 0; c2 < 3; ++c2)  // row c of J, selected without indexing
+          A[c2 * 4 + b] += c == 0 ? J[0][c2] : (c == 1 ? J[1][c2] : J[2][c2]);
       }
     }
-  // local projection stabilisation of the patches containing node pairs
-  const int PI0 = ci >> 1, PJ0 = cj >> 1;
-  for (int dJ = -1; dJ <= 1; ++dJ)
-    for (int dI = -1; dI <= 1; ++dI) {
-      const int PI = PI0 + dI, PJ = PJ0 + dJ;
-      if (PI < 0 || PJ < 0 || PI >= g.nx / 2 || PJ >= g.ny / 2) continue;
-      if (g.solid[(2 * PJ) * g.nx + 2 * PI]) continue;
-      for (int a = 0; a < 4; ++a) {
-        const int sa = ci + (a & 1) - 2 * PI, ta = cj + (a >> 1) - 2 * PJ;
+  // local projection stabilisation (pressure rows) of the patches
+  // containing node pairs
+  if (c == 2) {
+    const int PI0 = ci >> 1, PJ0 = cj >> 1;
+    for (int dJ = -1; dJ <= 1; ++dJ)
+      for (int dI = -1; dI <= 1; ++dI) {
+        const int PI = PI0 + dI, PJ = PJ0 + dJ;
+        if (PI < 0 || PJ < 0 || PI >= g.nx / 2 || PJ >= g.ny / 2) continue;
+        if (g.solid[(2 * PJ) * g.nx + 2 * PI]) continue;
+        const int sa = ai - 2 * PI, ta = aj - 2 * PJ;
         if (sa < 0 || sa > 2 || ta < 0 || ta > 2) continue;
+#pragma unroll
         for (int b = 0; b < 4; ++b) {
           const int sb = ci + (b & 1) - 2 * PI, tb = cj + (b >> 1) - 2 * PJ;
           if (sb < 0 || sb > 2 || tb < 0 || tb > 2) continue;
-          A[8 + a][8 + b] += s.S9[(sa + 3 * ta) * 9 + sb + 3 * tb];
+          A[8 + b] += s.S9[(sa + 3 * ta) * 9 + sb + 3 * tb];
         }
       }
-    }
-  // identity rows and columns on constrained DOFs
-  for (int a = 0; a < 4; ++a) {
-    const uint8_t f = g.flags[(cj + (a >> 1)) * g.nnx + ci + (a & 1)];
-    for (int c = 0; c < 3; ++c) {
-      const bool cons = (c < 2) ? (f & kVDir) : (f & kPFix);
-      if (!cons) continue;
-      const int r = c * 4 + a;
-      for (int k = 0; k < 12; ++k) A[r][k] = A[k][r] = T(0);
-      A[r][r] = T(1);
-    }
   }
-  for (int r = 0; r < 12; ++r) A[r][12 + r] = T(1);
-
-  // Gauss-Jordan elimination with partial pivoting on [A | I]
-  bool ok = true;
+  // identity rows and zero columns on constrained DOFs
+  uint8_t fl[4];
+#pragma unroll
+  for (int b = 0; b < 4; ++b) fl[b] = g.flags[(cj + (b >> 1)) * g.nnx + ci + (b & 1)];
+  const bool own_cons = g.flags[aj * g.nnx + ai] & (c < 2 ? kVDir : kPFix);
+#pragma unroll
   for (int k = 0; k < 12; ++k) {
-    int p = k;
-    T best = vk_abs(A[k][k]);
-    for (int r = k + 1; r < 12; ++r) {
-      const T v = vk_abs(A[r][k]);
-      if (v > best) best = v, p = r;
+    const bool col_cons = fl[k & 3] & (k < 8 ? kVDir : kPFix);
+    if (own_cons) A[k] = k == r ? T(1) : T(0);
+    else if (col_cons) A[k] = T(0);
+  }
+#pragma unroll
+  for (int k = 0; k < 12; ++k) A[12 + k] = k == r ? T(1) : T(0);
+
+  // Gauss-Jordan elimination with partial pivoting across the lanes
+  bool used = lane >= 12, ok = true;
+  int my_col = 0;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    T best = used ? T(-1) : vk_abs(A[k]);
+    int p = lane;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+      const T ob = __shfl_xor_sync(mask, best, o, 16);
+      const int op = __shfl_xor_sync(mask, p, o, 16);
+      if (ob > best || (ob == best && op < p)) best = ob, p = op;
     }
-    if (!(best > T(0))) {
-      ok = false;
-      break;
-    }
-    if (p != k)
-      for (int c = 0; c < 24; ++c) {
-        const T t = A[k][c];
-        A[k][c] = A[p][c];
-        A[p][c] = t;
+    ok = ok && best > T(0);  // the same in every lane of the group
+    if (ok) {
+      const T ip = T(1) / __shfl_sync(mask, A[k], p, 16);
+      const T f = A[k];
+      const bool piv = lane == p;
+      // columns before k are zero in the pivot row (eliminated earlier)
+#pragma unroll
+      for (int cc = k; cc < 24; ++cc) {
+        const T pn = __shfl_sync(mask, A[cc], p, 16) * ip;  // normalised pivot row
+        A[cc] = piv ? pn : A[cc] - f * pn;
       }
-    const T ip = T(1) / A[k][k];
-    for (int c = 0; c < 24; ++c) A[k][c] *= ip;
-    for (int r = 0; r < 12; ++r) {
-      if (r == k) continue;
-      const T f = A[r][k];
-      if (f == T(0)) continue;
-      for (int c = 0; c < 24; ++c) A[r][c] -= f * A[k][c];
+      if (piv) used = true, my_col = k;
     }
   }
-  if (!ok) atomicOr(status, 1);
+  if (!ok) {
+    if (lane == 0) atomicOr(status, 1);
+  }
+  if (lane >= 12) return;
   T* out = inv + (size_t)colour * 144 * nslots + slot;
-  for (int r = 0; r < 12; ++r)
-    for (int c = 0; c < 12; ++c) out[(size_t)(r * 12 + c) * nslots] = ok ? A[r][12 + c] : T(0);
+#pragma unroll
+  for (int cc = 0; cc < 12; ++cc)
+    out[(size_t)(my_col * 12 + cc) * nslots] = ok ? A[12 + cc] : T(0);
 }
-
 
 // Resident blocks per SM the pass kernels ask the compiler for: FP32 passes
 // are held to 128 registers per thread so that 512 threads per SM fit.
