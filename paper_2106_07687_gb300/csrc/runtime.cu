@@ -183,13 +183,16 @@ class Solver final : public SolverBase {
         launch_apply<T>(lv_[K_].g, lv_[K_].s, zj, vbJ_, w, st_);
         c_->prof.end(p, st_);
         p = c_->prof.begin(DNNMG_STAGE_KRYLOV, lv_[K_].level, st_);
-        launch_multidot<T>(V_, n_, j + 1, w, n_, partials_, hcol_, st_);
-        launch_multiaxpy<T>(V_, n_, j + 1, hcol_, w, n_, st_);
-        launch_multidot<T>(V_, n_, j + 1, w, n_, partials_, hcol_ + j + 1, st_);
-        launch_multiaxpy<T>(V_, n_, j + 1, hcol_ + j + 1, w, n_, st_);
-        launch_multidot<T>(w, n_, 1, w, n_, partials_, hcol_ + 2 * j + 2, st_);
-        launch_givens(H_, m_ + 1, cs_, sn_, gv_, hcol_, j, y_ + m_, st_);
-        launch_scale_dev<T>(w, hcol_ + 2 * j + 2, 2, w, n_, st_);
+        if (launch_arnoldi_step<T>(V_, n_, j, w, n_, partials_, hcol_, H_, m_ + 1, cs_, sn_, gv_,
+                                   y_ + m_, st_) != 0) {
+          launch_multidot<T>(V_, n_, j + 1, w, n_, partials_, hcol_, st_);
+          launch_multiaxpy<T>(V_, n_, j + 1, hcol_, w, n_, st_);
+          launch_multidot<T>(V_, n_, j + 1, w, n_, partials_, hcol_ + j + 1, st_);
+          launch_multiaxpy<T>(V_, n_, j + 1, hcol_ + j + 1, w, n_, st_);
+          launch_multidot<T>(w, n_, 1, w, n_, partials_, hcol_ + 2 * j + 2, st_);
+          launch_givens(H_, m_ + 1, cs_, sn_, gv_, hcol_, j, y_ + m_, st_);
+          launch_scale_dev<T>(w, hcol_ + 2 * j + 2, 2, w, n_, st_);
+        }
         c_->prof.end(p, st_);
         ++its;
         k = j + 1;

@@ -3,6 +3,8 @@
 // FP64 and run in two fixed-order stages, so results are deterministic.
 #include <atomic>
 
+#include <cooperative_groups.h>
+
 #include "kernels.h"
 #include "krylov_body.cuh"
 
@@ -114,6 +116,88 @@ __global__ void gmres_start_kernel(const T* __restrict__ r, const double* nrm2, 
     v0[e] = (T)(s * (double)r[e]);
 }
 
+// Sum over the kDotBlocks partials of row i, the second stage of a dot
+// product in the order of dots_finish_kernel; the block's result in *out.
+__device__ __forceinline__ void finish_row(const double* __restrict__ partials, int i,
+                                           double* sh, double* out) {
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < kDotBlocks; b += blockDim.x)
+    acc += partials[(size_t)i * kDotBlocks + b];
+  const double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) *out = t;
+}
+
+// One Arnoldi step of FGMRES for the new vector w against V[0..j] (CGS with
+// one re-orthogonalisation, then normalisation and the Givens update of
+// Hessenberg column j) in one cooperative launch of kDotBlocks blocks with
+// three grid barriers.  Block b owns the chunk of elements that multidot
+// assigns to it: it updates only that chunk, so the second pass's and the
+// norm's partial sums follow its own updates without a barrier, and every
+// block finishes the sums over all partials itself in the fixed order of
+// dots_finish_kernel.  Results are bitwise those of the sequence multidot,
+// multiaxpy, multidot, multiaxpy, multidot, givens, scale_dev.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    arnoldi_kernel(const T* __restrict__ V, size_t ld, int j, T* __restrict__ w, size_t n,
+                   double* __restrict__ partials, double* __restrict__ hcol, double* H, int ldh,
+                   double* cs, double* sn, double* g, double* resid) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double sh[32];
+  __shared__ double h[2][64];
+  __shared__ double nrm2;
+  const int k = j + 1;
+  const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const size_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+  double* p1 = partials;                           // [k][kDotBlocks]
+  double* p2 = partials + (size_t)k * kDotBlocks;  // [k][kDotBlocks]
+  double* p3 = partials + (size_t)2 * k * kDotBlocks;
+  auto dots = [&](double* part) {
+    for (int i = 0; i < k; ++i) {
+      const T* v = V + (size_t)i * ld;
+      double acc = 0.0;
+      for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x)
+        acc += (double)v[e] * (double)w[e];
+      const double t = block_sum(acc, sh);
+      if (threadIdx.x == 0) part[(size_t)i * gridDim.x + blockIdx.x] = t;
+    }
+  };
+  auto axpy = [&](const double* hh) {
+    for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+      double acc = (double)w[e];
+      for (int i = 0; i < k; ++i) acc -= hh[i] * (double)V[(size_t)i * ld + e];
+      w[e] = (T)acc;
+    }
+  };
+  dots(p1);
+  grid.sync();
+  for (int i = 0; i < k; ++i) finish_row(p1, i, sh, &h[0][i]);
+  __syncthreads();
+  axpy(h[0]);
+  dots(p2);
+  grid.sync();
+  for (int i = 0; i < k; ++i) finish_row(p2, i, sh, &h[1][i]);
+  __syncthreads();
+  axpy(h[1]);
+  {
+    double acc = 0.0;
+    for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) acc += (double)w[e] * (double)w[e];
+    const double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) p3[blockIdx.x] = t;
+  }
+  grid.sync();
+  finish_row(p3, 0, sh, &nrm2);
+  __syncthreads();
+  double s = sqrt(fmax(nrm2, 0.0));
+  s = s != 0.0 ? 1.0 / s : 0.0;
+  for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) w[e] = (T)(s * (double)w[e]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    for (int i = 0; i < k; ++i) hcol[i] = h[0][i], hcol[k + i] = h[1][i];
+    hcol[2 * k] = nrm2;
+    *resid = givens_column(H, ldh, cs, sn, g, hcol, j);
+  }
+}
+
 inline int blocks_for(size_t n) {
   size_t b = (n + kThreads - 1) / kThreads;
   return (int)(b > 4096 ? 4096 : (b < 1 ? 1 : b));
@@ -171,6 +255,34 @@ void launch_combine(const T* Z, size_t ld, int k, const double* y, double eps, T
   combine_kernel<T, Tx><<<blocks_for(n), kThreads, 0, st>>>(Z, ld, k, y, eps, x, n);
 }
 
+template <typename T>
+int launch_arnoldi_step(const T* V, size_t ld, int j, T* w, size_t n, double* partials,
+                        double* hcol, double* H, int ldh, double* cs, double* sn, double* gvec,
+                        double* resid, cudaStream_t st) {
+  if (j + 1 > 64) return 1;
+  static const bool fits = [] {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const bool ok = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, arnoldi_kernel<T>,
+                                                                  kThreads, 0) == cudaSuccess &&
+                    per * sms >= kDotBlocks;
+    cudaGetLastError();
+    return ok;
+  }();
+  if (!fits) return 1;
+  void* args[] = {(void*)&V, (void*)&ld, (void*)&j, (void*)&w, (void*)&n, (void*)&partials,
+                  (void*)&hcol, (void*)&H, (void*)&ldh, (void*)&cs, (void*)&sn, (void*)&gvec,
+                  (void*)&resid};
+  if (cudaLaunchCooperativeKernel((void*)arnoldi_kernel<T>, dim3(kDotBlocks), dim3(kThreads),
+                                  args, 0, st) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  note_launch();
+  return 0;
+}
+
 void launch_givens(double* H, int ldh, double* cs, double* sn, double* gvec, const double* hcol,
                    int j, double* resid, cudaStream_t st) {
   note_launch();
@@ -200,7 +312,10 @@ void launch_gmres_start(const T* r, const double* nrm2, T* v0, double* gvec, siz
   template void launch_gmres_start<T>(const T*, const double*, T*, double*, size_t,            \
                                       cudaStream_t);                                           \
   template void launch_combine<T, T>(const T*, size_t, int, const double*, double, T*, size_t, \
-                                     cudaStream_t);
+                                     cudaStream_t);                                            \
+  template int launch_arnoldi_step<T>(const T*, size_t, int, T*, size_t, double*, double*,     \
+                                      double*, int, double*, double*, double*, double*,        \
+                                      cudaStream_t);
 DNNMG_INST(float)
 DNNMG_INST(double)
 #undef DNNMG_INST
