@@ -19,6 +19,11 @@ template <typename T>
 class Solver final : public SolverBase {
  public:
   explicit Solver(dnnmg_ctx* c) : c_(c) {}
+  ~Solver() override {
+    for (cudaStream_t s : side_) cudaStreamDestroy(s);
+    for (cudaEvent_t e : side_ev_) cudaEventDestroy(e);
+    if (fork_ev_) cudaEventDestroy(fork_ev_);
+  }
 
   int init() {
     const dnnmg_config& cfg = c_->cfg;
@@ -90,6 +95,20 @@ class Solver final : public SolverBase {
       split_mode_ = cfg.persistent_mode >= 0 ? cfg.persistent_mode : (vgrid_ > 0 ? 0 : 1);
     }
     shape_.assign(K_ + 1, 0);
+    // side streams and events of the concurrent Vanka setups (levels 1..K-1)
+    if (K_ > 1) {
+      if (cudaEventCreateWithFlags(&fork_ev_, cudaEventDisableTiming) != cudaSuccess)
+        return c_->fail(DNNMG_ERR_CUDA, "event creation failed");
+      for (int k = 1; k < K_; ++k) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t e = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+          return c_->fail(DNNMG_ERR_CUDA, "stream creation failed");
+        side_.push_back(s);
+        side_ev_.push_back(e);
+      }
+    }
     const double one = 1.0;
     cudaMemcpyAsync(one_, &one, sizeof(double), cudaMemcpyHostToDevice, st_);
     return c_->check("solver init");
@@ -109,14 +128,26 @@ class Solver final : public SolverBase {
     for (int k = K_; k > 0; --k)
       launch_inject<double>(lv_[k].g, lv_[k - 1].g, lv_[k].vb64, lv_[k - 1].vb64, 2, st_);
     cudaMemsetAsync(status_, 0, sizeof(int), st_);
-    for (int k = 0; k <= K_; ++k) {
+    for (int k = 0; k <= K_; ++k)
       launch_cast<double, T>(lv_[k].vb64, lv_[k].vb, 2 * (size_t)lv_[k].g.nn, st_);
-      if (k > 0) {
-        const int p = c_->prof.begin(DNNMG_STAGE_VANKA_SETUP, lv_[k].level, st_);
-        launch_vanka_setup<T>(lv_[k].g, lv_[k].s, lv_[k].vb, lv_[k].inv, status_, st_);
-        c_->prof.end(p, st_);
+    // the levels' setups are independent and each leaves most of the GPU
+    // idle: levels below the top run on side streams beside it
+    const int p = c_->prof.begin(DNNMG_STAGE_VANKA_SETUP, lv_[K_].level, st_);
+    const bool fork = !side_.empty() && !capturing();
+    if (fork) cudaEventRecord(fork_ev_, st_);
+    for (int k = K_; k > 0; --k) {
+      cudaStream_t s = st_;
+      if (fork && k < K_) {
+        s = side_[k - 1];
+        cudaStreamWaitEvent(s, fork_ev_, 0);
+      }
+      launch_vanka_setup<T>(lv_[k].g, lv_[k].s, lv_[k].vb, lv_[k].inv, status_, s);
+      if (s != st_) {
+        cudaEventRecord(side_ev_[k - 1], s);
+        cudaStreamWaitEvent(st_, side_ev_[k - 1], 0);
       }
     }
+    c_->prof.end(p, st_);
     if (coarse || !coarse_done_) {
       const int p = c_->prof.begin(DNNMG_STAGE_COARSE_FACTOR, lv_[0].level, st_);
       launch_coarse_factor(lv_[0].g, lv_[0].s64, lv_[0].vb64, coarse_work_, ainv_, status_, st_);
@@ -381,6 +412,13 @@ class Solver final : public SolverBase {
   bool coarse_done_ = false;
   T* vbJ_ = nullptr;  // top-level linearisation of the FGMRES matvec
   VLevel<T>* dlv_ = nullptr;
+  std::vector<cudaStream_t> side_;   // side_[k - 1]: setup of level k < K
+  std::vector<cudaEvent_t> side_ev_;
+  cudaEvent_t fork_ev_ = nullptr;
+  bool capturing() const {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(st_, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+  }
   Phase* dph_ = nullptr;
   std::vector<int> ph_off_, ph_n_;
   int vgrid_ = 0, coarse_nd_ = 0, cluster_ = 0;
