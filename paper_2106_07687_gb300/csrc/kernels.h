@@ -111,9 +111,9 @@ void launch_combine(const T* Z, size_t ld, int k, const double* y, double eps, T
                     cudaStream_t st);
 size_t dots_partials(size_t n, int k);
 // One Arnoldi step (CGS2 against V[0..j], normalisation, Givens update of
-// column j, resid = |g[j+1]|) in one cooperative launch; bitwise equal to
-// the separate launches.  Returns nonzero (nothing launched) when the
-// cooperative grid cannot be resident.  partials needs (2 j + 3) x
+// column j, resid = |g[j+1]|) in one cooperative launch; products in the
+// vectors' precision, sums over threads and blocks in FP64.  Returns nonzero
+// (nothing launched) when the cooperative grid cannot be resident.  partials needs (2 j + 3) x
 // dots_partials(n, 1) doubles, hcol 2 j + 3.
 template <typename T>
 int launch_arnoldi_step(const T* V, size_t ld, int j, T* w, size_t n, double* partials,

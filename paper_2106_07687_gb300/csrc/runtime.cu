@@ -293,7 +293,8 @@ class Solver final : public SolverBase {
   // the colour pass on every level, by timing four passes per shape; (2) the
   // level from which the cycle runs as one persistent launch and the kind of
   // that launch (cooperative grid or single cluster), by timing whole cycles
-  // of the top level for every candidate (0 = one launch per stage).
+  // of the top level for every candidate (0 = one launch per stage); a lower
+  // split replaces a higher one only when it is more than 2 % faster.
   void tune_split() {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -337,9 +338,11 @@ class Solver final : public SolverBase {
           split_ = cand;
           split_mode_ = mode;
           persistent_failed_ = false;
-          float ms = time_ms([&] { cycle(top, b, x); }, 3);
+          float ms = time_ms([&] { cycle(top, b, x); }, 5);
           if (persistent_failed_) ms = 1e30f;
-          if (ms < best) best = ms, best_s = cand, best_m = mode;
+          // candidates come from the highest split down: a lower split (more
+          // launches) must be faster by more than the timing noise
+          if (ms < 0.98f * best) best = ms, best_s = cand, best_m = mode;
         }
       }
       split_ = best_s;

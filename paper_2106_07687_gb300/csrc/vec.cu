@@ -134,8 +134,10 @@ __device__ __forceinline__ void finish_row(const double* __restrict__ partials, 
 // assigns to it: it updates only that chunk, so the second pass's and the
 // norm's partial sums follow its own updates without a barrier, and every
 // block finishes the sums over all partials itself in the fixed order of
-// dots_finish_kernel.  Results are bitwise those of the sequence multidot,
-// multiaxpy, multidot, multiaxpy, multidot, givens, scale_dev.
+// dots_finish_kernel, so all blocks hold the same coefficients.  Products
+// and updates are taken in the vectors' precision T (a thread sums its few
+// products in T), the sums over threads and blocks in FP64: on this GPU an
+// FP64 operation per element would make the step FP64-bound.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     arnoldi_kernel(const T* __restrict__ V, size_t ld, int j, T* __restrict__ w, size_t n,
@@ -152,22 +154,25 @@ __global__ void __launch_bounds__(kThreads)
   double* p1 = partials;                           // [k][kDotBlocks]
   double* p2 = partials + (size_t)k * kDotBlocks;  // [k][kDotBlocks]
   double* p3 = partials + (size_t)2 * k * kDotBlocks;
+  __shared__ T hT[64];
   auto dots = [&](double* part) {
     for (int i = 0; i < k; ++i) {
       const T* v = V + (size_t)i * ld;
-      double acc = 0.0;
-      for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x)
-        acc += (double)v[e] * (double)w[e];
-      const double t = block_sum(acc, sh);
+      T acc = T(0);
+      for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) acc += v[e] * w[e];
+      const double t = block_sum((double)acc, sh);
       if (threadIdx.x == 0) part[(size_t)i * gridDim.x + blockIdx.x] = t;
     }
   };
   auto axpy = [&](const double* hh) {
+    if (threadIdx.x < k) hT[threadIdx.x] = (T)hh[threadIdx.x];
+    __syncthreads();
     for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
-      double acc = (double)w[e];
-      for (int i = 0; i < k; ++i) acc -= hh[i] * (double)V[(size_t)i * ld + e];
-      w[e] = (T)acc;
+      T acc = w[e];
+      for (int i = 0; i < k; ++i) acc -= hT[i] * V[(size_t)i * ld + e];
+      w[e] = acc;
     }
+    __syncthreads();  // hT is rewritten by the next pass
   };
   dots(p1);
   grid.sync();
@@ -180,9 +185,9 @@ __global__ void __launch_bounds__(kThreads)
   __syncthreads();
   axpy(h[1]);
   {
-    double acc = 0.0;
-    for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) acc += (double)w[e] * (double)w[e];
-    const double t = block_sum(acc, sh);
+    T acc = T(0);
+    for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) acc += w[e] * w[e];
+    const double t = block_sum((double)acc, sh);
     if (threadIdx.x == 0) p3[blockIdx.x] = t;
   }
   grid.sync();
@@ -190,7 +195,8 @@ __global__ void __launch_bounds__(kThreads)
   __syncthreads();
   double s = sqrt(fmax(nrm2, 0.0));
   s = s != 0.0 ? 1.0 / s : 0.0;
-  for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) w[e] = (T)(s * (double)w[e]);
+  const T sT = (T)s;
+  for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) w[e] *= sT;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     for (int i = 0; i < k; ++i) hcol[i] = h[0][i], hcol[k + i] = h[1][i];
     hcol[2 * k] = nrm2;
