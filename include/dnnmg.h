@@ -65,7 +65,11 @@ typedef struct dnnmg_config {
   double dt;          /* time step k (Eq. 5) */
   double theta;       /* time scheme weight: 1 = backward Euler, 0.5 = Crank-Nicolson (Eq. 5) */
   double alpha0;      /* LPS parameter, alpha_T = alpha0 * Re * h_T^2 (Sec. 2.1) */
-  double newton_tol;  /* stop when the l2 norm of f_n - A_n(x) over free DOFs <= newton_tol */
+  double newton_tol;  /* stop when the l2 norm of f_n - A_n(x) over free DOFs <= newton_tol;
+                         in DNNMG_MIXED the operator of that residual is evaluated in
+                         double-float (about 48 bits): its rounding floor is about
+                         1e-12 on the small channels, so smaller tolerances are
+                         not reached there */
   double gmres_rtol;  /* relative residual reduction of FGMRES per Newton step */
   double omega;       /* damping of the Vanka update */
   double eps_damp;    /* Newton damping epsilon (the damped update of Algorithm 1) */

@@ -22,8 +22,10 @@ template <typename T>
 void launch_defect(const Grid& g, const Sten<T>& s, const T* b, const T* x, const T* vb, T* d,
                    bool masked, cudaStream_t st);
 // r = f - A(x) on free DOFs, 0 on constrained DOFs (FP64 nonlinear residual).
+// With dfloat_ops, A(x) is evaluated in double-float arithmetic (about 48
+// significant bits, FP32 units) and only f - A(x) in FP64.
 void launch_residual64(const Grid& g, const Sten<double>& s, const double* x, const double* f,
-                       double* r, cudaStream_t st);
+                       double* r, cudaStream_t st, bool dfloat_ops = false);
 // f = (1/k) M v_old on the velocity rows, 0 on the pressure rows.
 void launch_old_time_rhs64(const Grid& g, double inv_k, const double* x_old, double* f,
                            cudaStream_t st);

@@ -29,10 +29,16 @@ struct OpSmem {
 // inside): the first TX * TY threads own a node each, any further ones help
 // stage the tile and compute its cell and patch rows.  A thread whose node
 // lies outside the level, and every helper, gets n = -1.  Constrained rows
-// are returned like free ones (the caller overrides them).
-template <typename T, bool NONLIN, bool MASK, int TX, int TY, int NTT = TX * TY>
+// are returned like free ones (the caller overrides them).  The fields are
+// stored as L and converted to the arithmetic type T when staged.
+template <class X>
+struct op_same {  // keeps a parameter out of template argument deduction
+  using type = X;
+};
+template <typename T, bool NONLIN, bool MASK, int TX, int TY, int NTT = TX * TY, typename L = T>
 __device__ __forceinline__ void op_tile_rows(const Grid& g, const Sten<T>& s,
-                                             const T* __restrict__ w, const T* __restrict__ vb,
+                                             const L* __restrict__ w,
+                                             const typename op_same<L>::type* __restrict__ vb,
                                              int bx, int by, OpSmem<T, TX, TY>& S, T& ru, T& rv,
                                              T& rp, int& n) {
   static_assert(TX % 2 == 0 && TY % 2 == 0, "even tile");
@@ -51,12 +57,12 @@ __device__ __forceinline__ void op_tile_rows(const Grid& g, const Sten<T>& s,
     if (i >= 0 && j >= 0 && i <= g.nx && j <= g.ny) {
       const int m = j * g.nnx + i;
       f = g.flags[m];
-      u = w[m];
-      v = w[nn + m];
-      p = w[2 * nn + m];
+      u = T(w[m]);
+      v = T(w[nn + m]);
+      p = T(w[2 * nn + m]);
       if (!NONLIN) {
-        bu = vb[m];
-        bvv = vb[nn + m];
+        bu = T(vb[m]);
+        bvv = T(vb[nn + m]);
       }
       if (i < g.nx && j < g.ny) so = g.solid[j * g.nx + i];
     }

@@ -770,7 +770,7 @@ int dnnmg_ctx::dnnmg_correction() {
   old_rhs(fine_level(), vcorr, fF);
   cudaMemcpyAsync(ximpF, xtF, n3F * sizeof(double), cudaMemcpyDeviceToDevice, st);
   launch_impose_dirichlet64(gF, ximpF, st);
-  launch_residual64(gF, s64F, ximpF, fF, rF, st);                     // input: fine residual
+  launch_residual64(gF, s64F, ximpF, fF, rF, st, mixed());                     // input: fine residual
   launch_gather(gL, gF, K, patch_cell, P, xtF, rF, feat_mean, feat_std, cfg.nu, cfg.dt, X, st);
   launch_patchnet_forward(nd, pk, X, hid, hid, net_out, P, net_status, st);  // network
   launch_scatter(gL, gF, K, cell_patch, net_out, nd.c_out, xtF, vcorr, st);
@@ -811,7 +811,7 @@ int dnnmg_ctx::make_sample(const double* xf_prev, const double* xf_next, float* 
   prolong_up(x64, xtF, 3);
   cudaMemcpyAsync(ximpF, xtF, 3 * sizeof(double) * gF.nn, cudaMemcpyDeviceToDevice, st);
   launch_impose_dirichlet64(gF, ximpF, st);
-  launch_residual64(gF, s64F, ximpF, fF, rF, st);
+  launch_residual64(gF, s64F, ximpF, fF, rF, st, mixed());
   launch_gather_raw(gL, gF, K, patch_cell, P, xtF, rF, cfg.nu, cfg.dt, Xraw, st);
   launch_targets(gL, gF, K, patch_cell, P, xf_next, xtF, Y, st);
   have_net_rhs = have_vcorr = false;
@@ -1001,7 +1001,7 @@ int dnnmg_ctx::vcycle_api(int level, const void* b, void* x, int precision) {
 }
 
 int dnnmg_ctx::residual_api(const double* x, const double* f, double* r) {
-  launch_residual64(grid(L()), s64L, x, f, r, st);
+  launch_residual64(grid(L()), s64L, x, f, r, st, mixed());
   return check("residual");
 }
 
@@ -1009,7 +1009,7 @@ int dnnmg_ctx::newton(const double* f, dnnmg_step_stats* s) {
   const Grid gL = grid(L());
   const size_t n3 = 3 * (size_t)gL.nn;
   int p = prof.begin(DNNMG_STAGE_RESIDUAL, L(), st);
-  launch_residual64(gL, s64L, x64, f, r64, st);
+  launch_residual64(gL, s64L, x64, f, r64, st, mixed());
   prof.end(p, st);
   double nrm = norm64(r64, n3);
   s->res0 = nrm;
@@ -1027,7 +1027,7 @@ int dnnmg_ctx::newton(const double* f, dnnmg_step_stats* s) {
     if (int rc = solver->solve(r64, x64, cfg.eps_damp, &its)) return rc;
     gits += its;
     p = prof.begin(DNNMG_STAGE_RESIDUAL, L(), st);
-    launch_residual64(gL, s64L, x64, f, r64, st);
+    launch_residual64(gL, s64L, x64, f, r64, st, mixed());
     prof.end(p, st);
     nrm = norm64(r64, n3);
     ++it;

@@ -199,6 +199,8 @@ struct dnnmg_ctx {
   // the level the network corrects: L + replaced_levels
   int fine_level() const { return cfg.level_solve + cfg.replaced_levels; }
   int lc() const { return cfg.level_coarse; }
+  // mixed precision: the FP64 residuals evaluate the operator in double-float
+  bool mixed() const { return cfg.precision == DNNMG_MIXED; }
   double norm64(const double* v, size_t n);  // synchronous
 
   int get_state(double* x);

@@ -6,6 +6,7 @@
 // kernels run one thread per node with 32 x 4 blocks, x fastest, so each
 // warp reads contiguous rows of the SoA fields.
 #include "kernels.h"
+#include "dfloat.cuh"
 #include "optile_body.cuh"
 #include "vbody.cuh"
 
@@ -93,6 +94,26 @@ __global__ void __launch_bounds__(kTX* kTY)
   r[2 * nn + n] = (fl & kPFix) ? 0.0 : f[2 * nn + n] - rp;
 }
 
+// The same residual with the operator evaluated in double-float arithmetic
+// (about 48 significant bits; the subtraction from f in FP64), for
+// mixed-precision contexts.
+__global__ void __launch_bounds__(kTX* kTY)
+    residual_df_tiled_kernel(Grid g, Sten<dfloat> s, const double* __restrict__ x,
+                             const double* __restrict__ f, double* __restrict__ r) {
+  extern __shared__ __align__(16) uint8_t smraw[];
+  auto& S = *reinterpret_cast<OpSmem<dfloat, kTX, kTY>*>(smraw);
+  dfloat ru, rv, rp;
+  int n;
+  op_tile_rows<dfloat, true, false, kTX, kTY, kTX * kTY, double>(
+      g, s, x, nullptr, blockIdx.x, blockIdx.y, S, ru, rv, rp, n);
+  if (n < 0) return;
+  const uint8_t fl = op_tile_flags<dfloat, kTX, kTY>(S);
+  const int nn = g.nn;
+  r[n] = (fl & kVDir) ? 0.0 : f[n] - (double)ru;
+  r[nn + n] = (fl & kVDir) ? 0.0 : f[nn + n] - (double)rv;
+  r[2 * nn + n] = (fl & kPFix) ? 0.0 : f[2 * nn + n] - (double)rp;
+}
+
 inline dim3 tile_grid(const Grid& g) { return dim3(cdiv(g.nnx, kTX), cdiv(g.nny, kTY)); }
 
 // opt a kernel in to `bytes` of dynamic shared memory; callers keep the
@@ -122,7 +143,23 @@ void launch_defect(const Grid& g, const Sten<T>& s, const T* b, const T* x, cons
 }
 
 void launch_residual64(const Grid& g, const Sten<double>& s, const double* x, const double* f,
-                       double* r, cudaStream_t st) {
+                       double* r, cudaStream_t st, bool dfloat_ops) {
+  if (dfloat_ops) {
+    Sten<dfloat> sd;
+    for (int e = 0; e < 16; ++e) {
+      sd.E[e] = dfloat(s.E[e]);
+      sd.Dx[e] = dfloat(s.Dx[e]);
+      sd.Dy[e] = dfloat(s.Dy[e]);
+    }
+    for (int e = 0; e < 81; ++e) sd.S9[e] = dfloat(s.S9[e]);
+    sd.wq = dfloat(s.wq);
+    sd.ih = dfloat(s.ih);
+    note_launch();
+    static const size_t smd =
+        smem_attr(residual_df_tiled_kernel, sizeof(OpSmem<dfloat, kTX, kTY>));
+    residual_df_tiled_kernel<<<tile_grid(g), kTX * kTY, smd, st>>>(g, sd, x, f, r);
+    return;
+  }
   note_launch();
   static const size_t sm = smem_attr(residual64_tiled_kernel, sizeof(OpSmem<double, kTX, kTY>));
   residual64_tiled_kernel<<<tile_grid(g), kTX * kTY, sm, st>>>(g, s, x, f, r);

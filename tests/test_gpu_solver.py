@@ -37,11 +37,14 @@ def test_apply_matches_assembled_jacobian(precision, L, obstacle):
         assert rel(y, ref) < (1e-13 if precision == 0 else 1e-5), (lev.ell, rel(y, ref))
 
 
+@pytest.mark.parametrize("precision,tol", [(0, 1e-13), (1, 1e-12)])
 @pytest.mark.parametrize("L", [2, 4])
-def test_residual_matches_oracle(L):
+def test_residual_matches_oracle(L, precision, tol):
+    """FP64 contexts evaluate the operator in FP64; mixed-precision contexts
+    in double-float (about 48 bits), so their bar is one decade looser."""
     dn = lib()
     prm = fem.Params(nu=0.005, dt=0.005)
-    ctx = _ctx(dn, L, 0, (3, 1), prm.nu, prm.dt)
+    ctx = _ctx(dn, L, precision, (3, 1), prm.nu, prm.dt)
     lev = mesh.Level(L, obstacle=(3, 1))
     x = seeded_state(lev, 5)
     xo = seeded_state(lev, 6)
@@ -49,7 +52,7 @@ def test_residual_matches_oracle(L):
     r = ctx.residual(torch.from_numpy(x).cuda(), torch.from_numpy(f).cuda()).cpu().numpy()
     ref = fem.residual(lev, x, f, prm)
     scale = np.linalg.norm(f) + np.linalg.norm(fem.operator(lev, x, prm))
-    assert np.linalg.norm(r - ref) < 1e-13 * scale
+    assert np.linalg.norm(r - ref) < tol * scale, np.linalg.norm(r - ref) / scale
 
 
 @pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-4)])
@@ -78,11 +81,15 @@ def test_plain_steps_match_oracle(precision, theta):
     ||r|| <= 1e-12 so that the distance between their converged states (at
     most ~||A'^-1|| * 2 tol) sits well below the 1e-10 bar; the solvers reach
     that state by different iterates (the GPU keeps the coarse LU for a whole
-    step).  theta = 1/2 is the Crank-Nicolson form of Eq. 5."""
+    step).  A mixed-precision context evaluates its residual in double-float,
+    whose rounding floor here is about 3e-12, so it iterates to the default
+    1e-10 (its bar is 1e-4).  theta = 1/2 is the Crank-Nicolson form of
+    Eq. 5."""
     dn = lib()
     obstacle = synthetic.obstacle_block(1000)
     prm = fem.Params(nu=0.01, dt=0.01, theta=theta)
-    ctx = _ctx(dn, 3, precision, obstacle, prm.nu, prm.dt, newton_tol=1e-12, theta=theta)
+    ntol = 1e-12 if precision == 0 else 1e-10
+    ctx = _ctx(dn, 3, precision, obstacle, prm.nu, prm.dt, newton_tol=ntol, theta=theta)
     levels = mesh.hierarchy(3, obstacle=obstacle)
     opt = newton.SolverOptions(newton_tol=1e-12)
     x = mesh.initial_state(levels[-1])
@@ -91,7 +98,7 @@ def test_plain_steps_match_oracle(precision, theta):
         st = ctx.step(dn.PLAIN)
         x, nit, _, nrm = newton.time_step(levels, x, prm, opt)
         xg = ctx.get_state().cpu().numpy()
-        assert st["res_final"] <= 1e-12
+        assert st["res_final"] <= ntol
         assert rel(xg, x) < (1e-10 if precision == 0 else 1e-4), (n, rel(xg, x), st)
 
 
