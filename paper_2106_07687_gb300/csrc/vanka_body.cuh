@@ -366,4 +366,61 @@ __device__ __forceinline__ void vanka_pass_tile(const Grid& g, const Sten<T>& s,
 }
 
 
+// The first colour pass of a smoothing sweep that starts from x = 0, for
+// item e = 4 * slot + a (node a of the colour cell of `slot`): the defect is
+// then b on every row (b - A 0 = b, and b - x = b on constrained rows), so
+// the pass needs neither the iterate nor any operator rows:
+// x_out = omega A_c^-1 b on the colour's fluid cells and 0 on every other
+// node, bitwise what the tiled pass computes from x = 0, and every node of the
+// level is written.  The four items of a cell are consecutive lanes of one
+// warp; all 32 lanes call this (valid = false for padding items).
+template <typename T>
+__device__ __forceinline__ void vanka_pass_zero_node(const Grid& g, int colour,
+                                                     const T* __restrict__ b,
+                                                     const T* __restrict__ inv, T omega,
+                                                     T* __restrict__ xout, int e, bool valid) {
+  const int cx = colour & 1, cy = colour >> 1;
+  const int sx = g.nx / 2 + 1, sy = g.ny / 2 + 1;
+  const int nslots = sx * sy;
+  const int nn = g.nn;
+  const int slot = e >> 2, a = e & 3;
+  const bool slot_ok = valid && slot < nslots;
+  const int ci = 2 * (slot % sx) - cx, cj = 2 * (slot / sx) - cy;
+  const int i = ci + (a & 1), j = cj + (a >> 1);
+  const bool node_ok = slot_ok && i >= 0 && j >= 0 && i <= g.nx && j <= g.ny;
+  const bool cell_ok = slot_ok && ci >= 0 && cj >= 0 && ci < g.nx && cj < g.ny &&
+                       !g.solid[cj * g.nx + ci];
+  const int n = node_ok ? j * g.nnx + i : 0;
+  T du = 0, dv = 0, dp = 0;
+  if (node_ok) du = b[n], dv = b[nn + n], dp = b[2 * nn + n];
+  const int base = (threadIdx.x & 31) & ~3;
+  T d[12];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    d[k] = __shfl_sync(0xffffffffu, du, base + k);
+    d[4 + k] = __shfl_sync(0xffffffffu, dv, base + k);
+    d[8 + k] = __shfl_sync(0xffffffffu, dp, base + k);
+  }
+  if (!node_ok) return;
+  if (cell_ok) {
+    // one row of the inverse at a time (fewer live registers)
+    const T* row0 = inv + (size_t)colour * 144 * nslots + slot;
+    T acc[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      acc[c] = 0;
+#pragma unroll
+      for (int k = 0; k < 12; ++k)
+        acc[c] += row0[(size_t)((c * 4 + a) * 12 + k) * nslots] * d[k];
+    }
+    xout[n] = T(0) + omega * acc[0];
+    xout[nn + n] = T(0) + omega * acc[1];
+    xout[2 * nn + n] = T(0) + omega * acc[2];
+  } else {
+    xout[n] = T(0);
+    xout[nn + n] = T(0);
+    xout[2 * nn + n] = T(0);
+  }
+}
+
 }  // namespace dnnmg

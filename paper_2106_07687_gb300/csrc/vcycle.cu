@@ -139,12 +139,28 @@ __device__ __forceinline__ void walk_phases(const VLevel<T>* __restrict__ glv,
       case kPhaseRestrict: {
         const VLevel<T>& C = S.lv[k - 1];
         const Grid& c = C.g;
+        const bool zero = f.colour == 1;
         for_items<NT>(c.nn, [&](int n) {
           restrict_node<T, true>(g, c, L.d, C.b, 3, n % c.nnx, n / c.nnx);
-          C.x[n] = T(0);
-          C.x[c.nn + n] = T(0);
-          C.x[2 * c.nn + n] = T(0);
+          if (zero) {
+            C.x[n] = T(0);
+            C.x[c.nn + n] = T(0);
+            C.x[2 * c.nn + n] = T(0);
+          }
         });
+        break;
+      }
+      case kPhasePassZero: {
+        // four items per colour cell, warp-sized chunks round-robin over the
+        // blocks; every lane of a warp takes part in the cell's shuffles
+        T* xout = f.out ? L.x2 : x0;
+        const int count = 4 * vanka_slots(g);
+        const int nchunks = (count + 31) >> 5;
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        for (int c = blockIdx.x + gridDim.x * w; c < nchunks; c += gridDim.x * (NT / 32)) {
+          const int e = (c << 5) + lane;
+          vanka_pass_zero_node<T>(g, f.colour, b, L.inv, omega, xout, e, e < count);
+        }
         break;
       }
       case kPhaseCoarse: {
@@ -235,14 +251,16 @@ void build_phases(int k, int top, int nu1, int nu2, std::vector<Phase>& out) {
     out.push_back({kPhaseCoarse, 0, 0, 0, 0});
     return;
   }
+  // with pre-smoothing, the first pass starts from the zero iterate and
+  // writes every node, so no level needs zeroing beforehand
   int cur = 0;
   for (int s = 0; s < nu1; ++s)
     for (int c = 0; c < 4; ++c) {
-      out.push_back({kPhasePass, k, c, cur, 1 - cur});
+      out.push_back({s == 0 && c == 0 ? kPhasePassZero : kPhasePass, k, c, cur, 1 - cur});
       cur ^= 1;
     }
   out.push_back({kPhaseDefect, k, 0, cur, 0});
-  out.push_back({kPhaseRestrict, k, 0, 0, 0});
+  out.push_back({kPhaseRestrict, k, nu1 > 0 ? 0 : 1, 0, 0});
   build_phases(k - 1, top, nu1, nu2, out);
   out.push_back({kPhaseProlong, k, 0, cur, 0});
   for (int s = 0; s < nu2; ++s)
@@ -278,7 +296,7 @@ bool vcycle_fits(int nphases, int nlevels) {
 
 std::vector<Phase> vcycle_phases(int top, int nu1, int nu2) {
   std::vector<Phase> out;
-  out.push_back({kPhaseZeroTop, top, 0, 0, 0});
+  if (nu1 == 0 || top == 0) out.push_back({kPhaseZeroTop, top, 0, 0, 0});
   build_phases(top, top, nu1, nu2, out);
   return out;
 }

@@ -15,10 +15,19 @@ struct VLevel {
   T *x, *x2, *b, *d, *vb, *inv;
 };
 
-enum PhaseType { kPhasePass, kPhaseDefect, kPhaseRestrict, kPhaseCoarse, kPhaseProlong, kPhaseZeroTop };
+enum PhaseType {
+  kPhasePass,
+  kPhaseDefect,
+  kPhaseRestrict,
+  kPhaseCoarse,
+  kPhaseProlong,
+  kPhaseZeroTop,
+  kPhasePassZero  // first pass of a sweep from x = 0 (the input is not read)
+};
 
 // in / out select the level's iterate (0: x, the caller's buffer on the top
-// level; 1: the second buffer x2)
+// level; 1: the second buffer x2); a restriction with colour = 1 also zeroes
+// the coarse iterate (needed when no pre-smoothing pass starts from zero)
 struct Phase {
   int type, level, colour, in, out;
 };
