@@ -41,8 +41,8 @@ ORACLE_L = 4              # bounded CPU sample: oracle DNN-MG step with L = 4, s
 # level 4..1 sub-cycle, profiles/vcycle_level5_split5.md for the whole
 # level-5 cycle); a kernel change makes the entries stale and they must then
 # be removed.
-NCU_TRAFFIC = {"vcycle_kernel<float>@split4": 19723264 + 12544,
-               "vcycle_kernel<float>@split5": 59302400 + 979968}
+NCU_TRAFFIC = {"vcycle_kernel<float>@split4": 19728128 + 7680,
+               "vcycle_kernel<float>@split5": 59351040 + 1429504}
 L2_BYTES = 129 * 2 ** 20
 
 
