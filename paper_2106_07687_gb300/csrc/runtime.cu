@@ -178,7 +178,7 @@ class Solver final : public SolverBase {
 
   int vcycle(int k, const void* b, void* x) override {
     if (!linearized_) return c_->fail(DNNMG_ERR_STATE, "vcycle before linearize");
-    launch_fill<T>(static_cast<T*>(x), T(0), 3 * (size_t)lv_[k].g.nn, st_);
+    if (!cycle_ignores_x(k)) launch_fill<T>(static_cast<T*>(x), T(0), 3 * (size_t)lv_[k].g.nn, st_);
     cycle(k, static_cast<const T*>(b), static_cast<T*>(x));
     return c_->check("vcycle");
   }
@@ -208,7 +208,7 @@ class Solver final : public SolverBase {
         T* vj = V_ + (size_t)j * n_;
         T* zj = Z_ + (size_t)j * n_;
         T* w = V_ + (size_t)(j + 1) * n_;
-        launch_fill<T>(zj, T(0), n_, st_);
+        if (!cycle_ignores_x(K_)) launch_fill<T>(zj, T(0), n_, st_);
         cycle(K_, vj, zj);
         int p = c_->prof.begin(DNNMG_STAGE_APPLY, lv_[K_].level, st_);
         launch_apply<T>(lv_[K_].g, lv_[K_].s, zj, vbJ_, w, st_);
@@ -354,8 +354,17 @@ class Solver final : public SolverBase {
     cudaEventDestroy(e1);
   }
 
-  // One V(nu1, nu2) cycle on level k for A x = b with x = 0 on entry.  Levels
-  // at or below split_ run their whole sub-cycle as one cooperative launch.
+  // Whether cycle(k, ...) runs as one persistent launch whose first pass
+  // starts from the zero iterate without reading x (then x need not be
+  // zeroed on entry; a failed launch zeroes it before the per-stage cycle).
+  bool cycle_ignores_x(int k) const {
+    return split_ > 0 && lv_[k].level <= split_ && !persistent_failed_ &&
+           (split_mode_ == 0 ? vgrid_ > 0 : cluster_ > 0) && c_->cfg.nu1 > 0 && k > 0;
+  }
+
+  // One V(nu1, nu2) cycle on level k for A x = b with x = 0 on entry (or any
+  // x when cycle_ignores_x(k)).  Levels at or below split_ run their whole
+  // sub-cycle as one cooperative launch.
   void cycle(int k, const T* b, T* x) {
     if (split_ > 0 && lv_[k].level <= split_ && !persistent_failed_ &&
         (split_mode_ == 0 ? vgrid_ > 0 : cluster_ > 0)) {
