@@ -50,10 +50,13 @@ DETA = np.array([b[2] for b in _B])
 
 
 class Params:
-    """Physical and discretisation parameters of one time step."""
+    """Physical and discretisation parameters of one time step.  lps selects
+    the projection of the stabilisation: "patch" (bilinear interpolation on
+    the 2h patch mesh) or "cell" (the cell mean of the gradient)."""
 
-    def __init__(self, nu=0.01, dt=0.01, theta=1.0, alpha0=0.1):
+    def __init__(self, nu=0.01, dt=0.01, theta=1.0, alpha0=0.1, lps="patch"):
         self.nu, self.dt, self.theta, self.alpha0 = nu, dt, theta, alpha0
+        self.lps = lps
 
 
 class Element:
@@ -123,13 +126,33 @@ def _interp_2h():
     return Pi
 
 
+def lps_matrix_cell(level, prm):
+    """Cellwise variant of the stabilisation (the alternative reading of
+    pi in Sec. 2.1: the projection onto cellwise constants):
+    s(p, xi) = sum_K alpha (grad p - pi_K grad p, grad xi - pi_K grad xi)_K,
+    pi_K the mean over the fluid cell K, i.e. per cell alpha (K - g g^T / |K|)
+    with g_a = int_K grad phi_a (2x2 Gauss, exact for Q1)."""
+    alpha = lps_alpha(level, prm)
+    el = Element(level.h)
+    g = np.stack([el.W @ el.DX, el.W @ el.DY], axis=1)       # [a, 2]
+    Sc = alpha * (el.K - g @ g.T / (level.h * level.h))
+    nodes = level.cell_nodes[level.fluid_cells] + 2 * level.nn
+    rows = np.repeat(nodes[:, :, None], 4, axis=2).ravel()
+    cols = np.repeat(nodes[:, None, :], 4, axis=1).ravel()
+    vals = np.broadcast_to(Sc, (len(nodes), 4, 4)).ravel()
+    return sp.coo_matrix((vals, (rows, cols)), shape=(level.ndof, level.ndof)).tocsr()
+
+
 def lps_matrix(level, prm):
-    """Pressure-pressure stabilisation matrix s(p, xi) on the whole level.
+    """Pressure-pressure stabilisation matrix s(p, xi) on the whole level
+    (patch projection; prm.lps == "cell" selects lps_matrix_cell).
 
     Patches are 2x2 blocks of cells (the cells of the parent level); on each
     patch K, s_K = alpha kappa^T K9 kappa with K9 the Q1 stiffness matrix of
     the patch's fluid cells on its 3x3 nodes and kappa = I - Pi.
     """
+    if getattr(prm, "lps", "patch") == "cell":
+        return lps_matrix_cell(level, prm)
     alpha = lps_alpha(level, prm)
     el = Element(level.h)
     nn, nnx = level.nn, level.nnx

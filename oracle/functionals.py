@@ -47,7 +47,7 @@ def momentum_residual(level, x, prm, x_old=None):
     """Momentum rows (ru, rv) of the backward-Euler operator at every node:
     (1/k) M (v - v_old) + nu K v + N(v) v - (p, div phi), with no constraint
     handling.  x_old = None drops the time-derivative term."""
-    be = fem.Params(nu=prm.nu, dt=prm.dt, theta=1.0, alpha0=prm.alpha0)
+    be = fem.Params(nu=prm.nu, dt=prm.dt, theta=1.0, alpha0=prm.alpha0, lps=prm.lps)
     # the LPS term lives in the pressure rows only, which are not returned
     A = fem.operator(level, x, be, S=sp.csr_matrix((level.ndof, level.ndof)))
     nn = level.nn

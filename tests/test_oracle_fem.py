@@ -48,15 +48,16 @@ def test_convection_terms_match_exact_integration():
     np.testing.assert_allclose(el.grad_mass(ub[None], el.DY)[0], G_ex, rtol=1e-12, atol=1e-14)
 
 
+@pytest.mark.parametrize("lps", ["patch", "cell"])
 @pytest.mark.parametrize("ell", [1, 2, 3, 4])
-def test_discrete_poiseuille_is_a_fixed_point(ell):
+def test_discrete_poiseuille_is_a_fixed_point(ell, lps):
     """u = 6y(1-y), v = 0, p = 12 nu (4 - x) solves the discrete steady and
     backward-Euler problem exactly: 1D linear elements are nodally exact for
     -nu u'' = const, convection vanishes, the mass terms cancel, the LPS
     fluctuation of a linear pressure is zero and p(4) = 0 matches the
     do-nothing outflow."""
     lev = mesh.Level(ell, obstacle=None)
-    prm = fem.Params(nu=0.01, dt=0.01)
+    prm = fem.Params(nu=0.01, dt=0.01, lps=lps)
     X, Y = lev.coords()
     x = np.concatenate([(6 * Y * (1 - Y)).ravel(), np.zeros(lev.nn), (12 * prm.nu * (4 - X)).ravel()])
     f = fem.old_time_rhs(lev, x, prm)
@@ -108,6 +109,42 @@ def test_lps_vanishes_on_patch_bilinear_pressure_only():
     Sd = S.toarray()
     assert np.abs(Sd - Sd.T).max() < 1e-15
     assert np.linalg.eigvalsh(Sd[2 * fine.nn:, 2 * fine.nn:]).min() > -1e-14
+
+
+@pytest.mark.parametrize("obstacle", [None, (2, 1)])
+def test_cellwise_lps_is_the_bilinear_mode_penalty(obstacle):
+    """The cellwise projection: on a square Q1 cell the stiffness matrix minus
+    the mean-gradient part is (1/6) c c^T with c = (1, -1, -1, 1), the cell's
+    bilinear mode, so p^T S p = alpha / 6 * sum over fluid cells of
+    (p_00 - p_10 - p_01 + p_11)^2; it vanishes on linear pressures and sees
+    p = x y."""
+    lev = mesh.Level(2, obstacle=obstacle)
+    prm = fem.Params(nu=0.02, lps="cell")
+    S = fem.lps_matrix(lev, prm)
+    alpha = fem.lps_alpha(lev, prm)
+    rng = np.random.default_rng(3)
+    p = rng.standard_normal(lev.nn)
+    x = np.zeros(lev.ndof)
+    x[2 * lev.nn:] = p
+    P = p.reshape(lev.nny, lev.nnx)
+    expect = 0.0
+    for cj in range(lev.ny):
+        for ci in range(lev.nx):
+            if lev.cell_solid[cj, ci]:
+                continue
+            m = P[cj, ci] - P[cj, ci + 1] - P[cj + 1, ci] + P[cj + 1, ci + 1]
+            expect += alpha / 6.0 * m * m
+    assert x @ (S @ x) == pytest.approx(expect, rel=1e-12)
+    X, Y = lev.coords()
+    for lin in (np.ones_like(X), X, Y, 2 * X - 3 * Y + 1):
+        x[2 * lev.nn:] = lin.ravel()
+        assert np.abs(S @ x).max() < 1e-13
+    x[2 * lev.nn:] = (X * Y).ravel()
+    assert x @ (S @ x) > 0.1 * alpha * lev.h ** 4
+    Sd = S.toarray()
+    assert np.abs(Sd - Sd.T).max() < 1e-15
+    # only pressure rows and columns
+    assert np.abs(Sd[:2 * lev.nn]).max() == 0 and np.abs(Sd[:, :2 * lev.nn]).max() == 0
 
 
 def test_mass_conservation_after_newton_step():
