@@ -113,6 +113,27 @@ Sten<T> make_sten(double h, const dnnmg_config& c) {
         for (int q = 0; q < 9; ++q) acc += kap[p][m] * K9[p][q] * kap[q][n];
       s.S9[m * 9 + n] = (T)(alpha * acc);
     }
+  if (c.lps_mode == 1) {
+    // The cellwise projection (the mean gradient of a cell) leaves, on a
+    // square Q1 cell, alpha / 6 times the outer product of its bilinear mode
+    // c = (1, -1, -1, 1).  Each fluid cell lies in exactly one patch, and
+    // patches are all fluid or all solid on every multigrid level, so the
+    // patch matrix is the sum of its four cells' blocks.
+    for (int m = 0; m < 81; ++m) s.S9[m] = (T)0;
+    double S9c[9][9] = {};
+    for (int cy = 0; cy < 2; ++cy)
+      for (int cx = 0; cx < 2; ++cx)
+        for (int a = 0; a < 4; ++a)
+          for (int b = 0; b < 4; ++b) {
+            const double ca = ((a & 1) == (a >> 1)) ? 1.0 : -1.0;
+            const double cb = ((b & 1) == (b >> 1)) ? 1.0 : -1.0;
+            const int ma = (cx + (a & 1)) + 3 * (cy + (a >> 1));
+            const int mb = (cx + (b & 1)) + 3 * (cy + (b >> 1));
+            S9c[ma][mb] += alpha / 6.0 * ca * cb;
+          }
+    for (int m = 0; m < 9; ++m)
+      for (int n = 0; n < 9; ++n) s.S9[m * 9 + n] = (T)S9c[m][n];
+  }
   s.wq = (T)(c.theta * h * h / 4.0);
   s.ih = (T)(1.0 / h);
   return s;

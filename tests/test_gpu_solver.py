@@ -125,3 +125,35 @@ def test_persistent_vcycle_kinds_match_oracle(precision, tol, split, mode):
     H = mg.Hierarchy(levels, x, prm)
     xr = mg.vcycle(H, len(levels) - 1, b)
     assert rel(xg, xr) < tol, rel(xg, xr)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_cellwise_stabilisation_matches_oracle(precision):
+    """lps_mode = 1, the cellwise projection of the stabilisation (the mean
+    gradient of each cell, alpha / 6 times the bilinear mode's outer product
+    per fluid cell): Jacobian rows on every level and the FP64 residual
+    against the oracle with lps = "cell".  (That stabilisation leaves the
+    line pressure mode free and the coarse matrix singular, so no solve is
+    compared; the oracle's pins show it.)"""
+    dn = lib()
+    L, obstacle = 3, synthetic.obstacle_block(1002)
+    prm = fem.Params(nu=0.01, dt=0.01, lps="cell")
+    ctx = _ctx(dn, L, precision, obstacle, prm.nu, prm.dt, lps_mode=1)
+    levels = mesh.hierarchy(L, obstacle=obstacle)
+    lev = levels[-1]
+    x = seeded_state(lev, 41)
+    ctx.linearize(torch.from_numpy(x).cuda())
+    H = mg.Hierarchy(levels, x, prm)
+    for k, lv in enumerate(levels):
+        w = synthetic.random_vector(200 + k, lv.ndof)
+        y = ctx.apply(lv.ell, torch.from_numpy(w).to(ctx.vdtype).cuda()).double().cpu().numpy()
+        assert rel(y, H.ops[k].A @ w) < (1e-13 if precision == 0 else 1e-5), lv.ell
+    f = fem.old_time_rhs(lev, seeded_state(lev, 42), prm)
+    r = ctx.residual(torch.from_numpy(x).cuda(), torch.from_numpy(f).cuda()).cpu().numpy()
+    ref = fem.residual(lev, x, f, prm)
+    scale = np.linalg.norm(f) + np.linalg.norm(fem.operator(lev, x, prm))
+    assert np.linalg.norm(r - ref) < (1e-13 if precision == 0 else 1e-12) * scale
+    # and the patch projection gives a different operator on the same state
+    Jp = fem.jacobian(lev, x, fem.Params(nu=0.01, dt=0.01))
+    w = synthetic.random_vector(7, lev.ndof)
+    assert rel(fem.jacobian(lev, x, prm) @ w, Jp @ w) > 1e-6

@@ -147,6 +147,32 @@ def test_cellwise_lps_is_the_bilinear_mode_penalty(obstacle):
     assert np.abs(Sd[:2 * lev.nn]).max() == 0 and np.abs(Sd[:, :2 * lev.nn]).max() == 0
 
 
+def test_cellwise_lps_leaves_the_line_mode_free():
+    """The line pressure mode p = (-1)^i (constant in y) has zero bilinear
+    part on every cell, so the cellwise stabilisation does not see it; the
+    Q1/Q1 divergence does not either, so with lps = "cell" it is a null
+    vector of the whole Jacobian and the coarsest-level matrix is singular.
+    The patch projection penalises it (its 2x2-cell patches do not hold a
+    bilinear line mode) and keeps the matrix regular."""
+    lev = mesh.hierarchy(1, obstacle=(2, 1))[-1]
+    x = mesh.initial_state(lev)
+    z = np.zeros(lev.ndof)
+    z[2 * lev.nn:] = np.tile((-1.0) ** np.arange(lev.nnx), lev.nny)
+    z[lev.cons] = 0.0                     # pressure nodes inside the obstacle
+    cond = {}
+    for lps in ("patch", "cell"):
+        prm = fem.Params(nu=0.01, dt=0.01, lps=lps)
+        J = fem.jacobian(lev, x, prm)
+        s = np.linalg.svd(J.toarray(), compute_uv=False)
+        cond[lps] = s[0] / s[-1]
+        seen = z @ (fem.lps_matrix(lev, prm) @ z)
+        if lps == "cell":
+            assert abs(seen) < 1e-12 and np.linalg.norm(J @ z) < 1e-14 * np.linalg.norm(z)
+        else:
+            assert seen > 1.0 and np.linalg.norm(J @ z) > 0.1 * np.linalg.norm(z)
+    assert cond["patch"] < 1e6 and cond["cell"] > 1e14, cond
+
+
 def test_mass_conservation_after_newton_step():
     """Summing all pressure rows (sum of xi_i = 1, LPS vanishes on constants)
     gives int div v = outflow flux - inflow flux, so a converged step carries
