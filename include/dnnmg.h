@@ -95,14 +95,16 @@ typedef struct dnnmg_config {
                               step's first Newton iteration (the matvec is always current) */
   int32_t persistent_mode; /* that launch: 0 = cooperative grid, 1 = one thread-block
                               cluster, -1 = chosen by timing */
-  int32_t lps_mode;        /* projection of the pressure stabilisation (Sec. 2.1): 0 =
-                              bilinear interpolation on the 2h patch mesh (default),
-                              1 = the mean of the gradient over each cell, which
-                              penalises only the bilinear mode of each cell: it
-                              leaves the line pressure mode (-1)^i free, so the
-                              Jacobian is singular and the solver does not
-                              converge with it; operator, residual and
-                              functionals are exact, for comparison runs only */
+  int32_t lps_mode;        /* projection pi_h of the pressure stabilisation (Sec. 2.1):
+                              0 = bilinear interpolation on the 2h patch mesh (default);
+                              1 = onto cellwise constants, so s is alpha times the
+                              pressure Laplacian (not consistent: O(alpha h) terms on
+                              the boundary for linear p; slower V-cycle contraction);
+                              2 = the gradient onto its cell mean, which penalises only
+                              each cell's bilinear mode and leaves the line pressure
+                              mode (-1)^i free: the Jacobian is singular and the solver
+                              does not converge with it (operator, residual and
+                              functionals only, for comparisons) */
 } dnnmg_config;
 
 /* Per-step statistics returned by dnnmg_step(). */

@@ -51,8 +51,10 @@ DETA = np.array([b[2] for b in _B])
 
 class Params:
     """Physical and discretisation parameters of one time step.  lps selects
-    the projection of the stabilisation: "patch" (bilinear interpolation on
-    the 2h patch mesh) or "cell" (the cell mean of the gradient)."""
+    the projection pi_h of the stabilisation (Sec. 2.1): "patch" (bilinear
+    interpolation on the 2h patch mesh), "cell" (onto cellwise constants, so
+    grad pi_h p = 0 and s is the pressure Laplacian) or "cellgrad" (the cell
+    mean of the gradient)."""
 
     def __init__(self, nu=0.01, dt=0.01, theta=1.0, alpha0=0.1, lps="patch"):
         self.nu, self.dt, self.theta, self.alpha0 = nu, dt, theta, alpha0
@@ -126,16 +128,8 @@ def _interp_2h():
     return Pi
 
 
-def lps_matrix_cell(level, prm):
-    """Cellwise variant of the stabilisation (the alternative reading of
-    pi in Sec. 2.1: the projection onto cellwise constants):
-    s(p, xi) = sum_K alpha (grad p - pi_K grad p, grad xi - pi_K grad xi)_K,
-    pi_K the mean over the fluid cell K, i.e. per cell alpha (K - g g^T / |K|)
-    with g_a = int_K grad phi_a (2x2 Gauss, exact for Q1)."""
-    alpha = lps_alpha(level, prm)
-    el = Element(level.h)
-    g = np.stack([el.W @ el.DX, el.W @ el.DY], axis=1)       # [a, 2]
-    Sc = alpha * (el.K - g @ g.T / (level.h * level.h))
+def _cellwise(level, Sc):
+    """Sum of the 4x4 pressure block Sc over the fluid cells of the level."""
     nodes = level.cell_nodes[level.fluid_cells] + 2 * level.nn
     rows = np.repeat(nodes[:, :, None], 4, axis=2).ravel()
     cols = np.repeat(nodes[:, None, :], 4, axis=1).ravel()
@@ -143,16 +137,41 @@ def lps_matrix_cell(level, prm):
     return sp.coo_matrix((vals, (rows, cols)), shape=(level.ndof, level.ndof)).tocsr()
 
 
+def lps_matrix_cell(level, prm):
+    """Projection onto cellwise constants (pi_h into W^(1) read as the
+    piecewise constants, Sec. 2.1): grad pi_h p = 0 inside each cell, so
+    s(p, xi) = sum_K alpha (grad p, grad xi)_K over the fluid cells, the Q1
+    stiffness matrix of the pressure scaled by alpha.  It does not vanish on
+    linear p: by the divergence theorem S p = alpha int_dOmega xi grad p . n."""
+    return _cellwise(level, lps_alpha(level, prm) * Element(level.h).K)
+
+
+def lps_matrix_cellgrad(level, prm):
+    """Projection of the gradient onto cellwise constants:
+    s(p, xi) = sum_K alpha (grad p - pi_K grad p, grad xi - pi_K grad xi)_K,
+    pi_K the mean over the fluid cell K, i.e. per cell alpha (K - g g^T / |K|)
+    with g_a = int_K grad phi_a (2x2 Gauss, exact for Q1)."""
+    alpha = lps_alpha(level, prm)
+    el = Element(level.h)
+    g = np.stack([el.W @ el.DX, el.W @ el.DY], axis=1)       # [a, 2]
+    return _cellwise(level, alpha * (el.K - g @ g.T / (level.h * level.h)))
+
+
 def lps_matrix(level, prm):
     """Pressure-pressure stabilisation matrix s(p, xi) on the whole level
-    (patch projection; prm.lps == "cell" selects lps_matrix_cell).
+    (patch projection; prm.lps == "cell" or "cellgrad" selects the
+    cellwise forms above).
 
     Patches are 2x2 blocks of cells (the cells of the parent level); on each
     patch K, s_K = alpha kappa^T K9 kappa with K9 the Q1 stiffness matrix of
     the patch's fluid cells on its 3x3 nodes and kappa = I - Pi.
     """
-    if getattr(prm, "lps", "patch") == "cell":
+    lps = getattr(prm, "lps", "patch")
+    if lps == "cell":
         return lps_matrix_cell(level, prm)
+    if lps == "cellgrad":
+        return lps_matrix_cellgrad(level, prm)
+    assert lps == "patch", lps
     alpha = lps_alpha(level, prm)
     el = Element(level.h)
     nn, nnx = level.nn, level.nnx

@@ -113,13 +113,17 @@ Sten<T> make_sten(double h, const dnnmg_config& c) {
         for (int q = 0; q < 9; ++q) acc += kap[p][m] * K9[p][q] * kap[q][n];
       s.S9[m * 9 + n] = (T)(alpha * acc);
     }
+  // Cellwise forms.  Each fluid cell lies in exactly one patch and patches
+  // are all fluid or all solid on every multigrid level, so a patch matrix
+  // that is the sum of its four cells' blocks gives the cellwise operator.
   if (c.lps_mode == 1) {
-    // The cellwise projection (the mean gradient of a cell) leaves, on a
-    // square Q1 cell, alpha / 6 times the outer product of its bilinear mode
-    // c = (1, -1, -1, 1).  Each fluid cell lies in exactly one patch, and
-    // patches are all fluid or all solid on every multigrid level, so the
-    // patch matrix is the sum of its four cells' blocks.
-    for (int m = 0; m < 81; ++m) s.S9[m] = (T)0;
+    // projection onto cellwise constants: grad pi p = 0, S = alpha K
+    for (int m = 0; m < 9; ++m)
+      for (int n = 0; n < 9; ++n) s.S9[m * 9 + n] = (T)(alpha * K9[m][n]);
+  } else if (c.lps_mode == 2) {
+    // projection of the gradient onto its cell mean: on a square Q1 cell
+    // the rest is alpha / 6 times the outer product of the bilinear mode
+    // c = (1, -1, -1, 1)
     double S9c[9][9] = {};
     for (int cy = 0; cy < 2; ++cy)
       for (int cx = 0; cx < 2; ++cx)

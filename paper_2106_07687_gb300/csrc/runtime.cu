@@ -497,7 +497,7 @@ int check_config(const dnnmg_config& c, std::string& err) {
     return fail_msg(err, DNNMG_ERR_ARG, "unknown precision");
   if (c.gmres_m < 1 || c.gmres_m > 40 || c.gmres_maxit < 1 || c.newton_max < 1 || c.nu1 < 0 ||
       c.nu2 < 0 || c.coarse_refresh < 1 || c.persistent_mode < -1 || c.persistent_mode > 1 ||
-      c.lps_mode < 0 || c.lps_mode > 1)
+      c.lps_mode < 0 || c.lps_mode > 2)
     return fail_msg(err, DNNMG_ERR_ARG, "solver parameters out of range");
   return DNNMG_OK;
 }

@@ -44,7 +44,7 @@ def test_default_config_and_argument_errors(lib):
     assert out.value is None
     for bad in (dict(level_coarse=0), dict(level_solve=12), dict(nu=-1.0), dict(gmres_m=0),
                 dict(precision=7), dict(replaced_levels=5), dict(obstacle_i0=20),
-                dict(coarse_refresh=0), dict(persistent_mode=3), dict(lps_mode=2)):
+                dict(coarse_refresh=0), dict(persistent_mode=3), dict(lps_mode=3), dict(lps_mode=-1)):
         c = dnnmg.default_config(**bad)
         assert L.dnnmg_setup(ctypes.byref(c), None, ctypes.byref(out)) == dnnmg.ERR_ARG, bad
         assert out.value is None

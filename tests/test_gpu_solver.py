@@ -128,17 +128,19 @@ def test_persistent_vcycle_kinds_match_oracle(precision, tol, split, mode):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-def test_cellwise_stabilisation_matches_oracle(precision):
-    """lps_mode = 1, the cellwise projection of the stabilisation (the mean
-    gradient of each cell, alpha / 6 times the bilinear mode's outer product
-    per fluid cell): Jacobian rows on every level and the FP64 residual
-    against the oracle with lps = "cell".  (That stabilisation leaves the
-    line pressure mode free and the coarse matrix singular, so no solve is
-    compared; the oracle's pins show it.)"""
+@pytest.mark.parametrize("mode,lps", [(1, "cell"), (2, "cellgrad")])
+def test_cellwise_stabilisation_matches_oracle(precision, mode, lps):
+    """The cellwise readings of the stabilisation's projection (Sec. 2.1):
+    lps_mode = 1 projects onto cellwise constants (s = alpha times the
+    pressure Laplacian), lps_mode = 2 projects the gradient onto its cell
+    mean.  Jacobian rows on every level and the residual against the oracle
+    for both; for mode 1 also a V-cycle and whole time steps.  Mode 2 leaves
+    the line pressure mode free and the coarse matrix singular (an oracle
+    pin shows it), so it gets no solve."""
     dn = lib()
     L, obstacle = 3, synthetic.obstacle_block(1002)
-    prm = fem.Params(nu=0.01, dt=0.01, lps="cell")
-    ctx = _ctx(dn, L, precision, obstacle, prm.nu, prm.dt, lps_mode=1)
+    prm = fem.Params(nu=0.01, dt=0.01, lps=lps)
+    ctx = _ctx(dn, L, precision, obstacle, prm.nu, prm.dt, lps_mode=mode)
     levels = mesh.hierarchy(L, obstacle=obstacle)
     lev = levels[-1]
     x = seeded_state(lev, 41)
@@ -153,7 +155,24 @@ def test_cellwise_stabilisation_matches_oracle(precision):
     ref = fem.residual(lev, x, f, prm)
     scale = np.linalg.norm(f) + np.linalg.norm(fem.operator(lev, x, prm))
     assert np.linalg.norm(r - ref) < (1e-13 if precision == 0 else 1e-12) * scale
-    # and the patch projection gives a different operator on the same state
+    # the patch projection gives a different operator on the same state
     Jp = fem.jacobian(lev, x, fem.Params(nu=0.01, dt=0.01))
     w = synthetic.random_vector(7, lev.ndof)
-    assert rel(fem.jacobian(lev, x, prm) @ w, Jp @ w) > 1e-6
+    assert rel(H.ops[-1].A @ w, Jp @ w) > 1e-6
+    if mode != 1:
+        return
+    tol = 1e-10 if precision == 0 else 1e-4
+    b = synthetic.random_vector(51, lev.ndof)
+    b[lev.cons] = 0.0
+    xg = ctx.vcycle(L, torch.from_numpy(b).to(ctx.vdtype).cuda()).double().cpu().numpy()
+    xr = mg.vcycle(H, len(levels) - 1, b)
+    assert rel(xg, xr) < tol, rel(xg, xr)
+    ntol = 1e-12 if precision == 0 else 1e-10
+    ctx = _ctx(dn, L, precision, obstacle, prm.nu, prm.dt, lps_mode=mode, newton_tol=ntol)
+    xo = mesh.initial_state(lev)
+    opt = newton.SolverOptions(newton_tol=1e-12)
+    for n in range(2):
+        st = ctx.step(dn.PLAIN)
+        xo, _, _, _ = newton.time_step(levels, xo, prm, opt)
+        assert st["res_final"] <= ntol, st
+        assert rel(ctx.get_state().cpu().numpy(), xo) < tol, (n, st)

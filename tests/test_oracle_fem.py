@@ -48,7 +48,7 @@ def test_convection_terms_match_exact_integration():
     np.testing.assert_allclose(el.grad_mass(ub[None], el.DY)[0], G_ex, rtol=1e-12, atol=1e-14)
 
 
-@pytest.mark.parametrize("lps", ["patch", "cell"])
+@pytest.mark.parametrize("lps", ["patch", "cellgrad"])
 @pytest.mark.parametrize("ell", [1, 2, 3, 4])
 def test_discrete_poiseuille_is_a_fixed_point(ell, lps):
     """u = 6y(1-y), v = 0, p = 12 nu (4 - x) solves the discrete steady and
@@ -113,13 +113,13 @@ def test_lps_vanishes_on_patch_bilinear_pressure_only():
 
 @pytest.mark.parametrize("obstacle", [None, (2, 1)])
 def test_cellwise_lps_is_the_bilinear_mode_penalty(obstacle):
-    """The cellwise projection: on a square Q1 cell the stiffness matrix minus
+    """The projection of the gradient onto cellwise constants: on a square Q1 cell the stiffness matrix minus
     the mean-gradient part is (1/6) c c^T with c = (1, -1, -1, 1), the cell's
     bilinear mode, so p^T S p = alpha / 6 * sum over fluid cells of
     (p_00 - p_10 - p_01 + p_11)^2; it vanishes on linear pressures and sees
     p = x y."""
     lev = mesh.Level(2, obstacle=obstacle)
-    prm = fem.Params(nu=0.02, lps="cell")
+    prm = fem.Params(nu=0.02, lps="cellgrad")
     S = fem.lps_matrix(lev, prm)
     alpha = fem.lps_alpha(lev, prm)
     rng = np.random.default_rng(3)
@@ -147,30 +147,92 @@ def test_cellwise_lps_is_the_bilinear_mode_penalty(obstacle):
     assert np.abs(Sd[:2 * lev.nn]).max() == 0 and np.abs(Sd[:, :2 * lev.nn]).max() == 0
 
 
-def test_cellwise_lps_leaves_the_line_mode_free():
+def test_cellwise_gradient_lps_leaves_the_line_mode_free():
     """The line pressure mode p = (-1)^i (constant in y) has zero bilinear
-    part on every cell, so the cellwise stabilisation does not see it; the
-    Q1/Q1 divergence does not either, so with lps = "cell" it is a null
-    vector of the whole Jacobian and the coarsest-level matrix is singular.
-    The patch projection penalises it (its 2x2-cell patches do not hold a
-    bilinear line mode) and keeps the matrix regular."""
+    part on every cell, so the stabilisation with the cell mean of the
+    gradient does not see it; the Q1/Q1 divergence does not either, so it is
+    a null vector of the whole Jacobian and the coarsest-level matrix is
+    singular.  The patch projection and the projection onto cellwise
+    constants penalise it and keep the matrix regular."""
     lev = mesh.hierarchy(1, obstacle=(2, 1))[-1]
     x = mesh.initial_state(lev)
     z = np.zeros(lev.ndof)
     z[2 * lev.nn:] = np.tile((-1.0) ** np.arange(lev.nnx), lev.nny)
     z[lev.cons] = 0.0                     # pressure nodes inside the obstacle
     cond = {}
-    for lps in ("patch", "cell"):
+    for lps in ("patch", "cell", "cellgrad"):
         prm = fem.Params(nu=0.01, dt=0.01, lps=lps)
         J = fem.jacobian(lev, x, prm)
         s = np.linalg.svd(J.toarray(), compute_uv=False)
         cond[lps] = s[0] / s[-1]
         seen = z @ (fem.lps_matrix(lev, prm) @ z)
-        if lps == "cell":
+        if lps == "cellgrad":
             assert abs(seen) < 1e-12 and np.linalg.norm(J @ z) < 1e-14 * np.linalg.norm(z)
         else:
             assert seen > 1.0 and np.linalg.norm(J @ z) > 0.1 * np.linalg.norm(z)
-    assert cond["patch"] < 1e6 and cond["cell"] > 1e14, cond
+    assert cond["patch"] < 1e6 and cond["cell"] < 1e6 and cond["cellgrad"] > 1e14, cond
+
+
+@pytest.mark.parametrize("obstacle", [None, (2, 1), (3, 1)])
+def test_cellwise_constant_lps_is_the_pressure_laplacian(obstacle):
+    """Projection onto cellwise constants: s(p, xi) = alpha (grad p, grad xi)
+    over the fluid cells.  For linear p = a + b x + c y the divergence
+    theorem gives (S p)_i = alpha * int over the fluid boundary of
+    xi_i (b, c) . n, built here from the mesh alone: each boundary edge of a
+    fluid cell (facing a solid cell or the outside) gives half its length
+    times alpha (b, c) . n to both of its nodes.  S is symmetric positive
+    semi-definite and its null space on the fluid pressures is the
+    constants."""
+    lev = mesh.Level(2, obstacle=obstacle)
+    prm = fem.Params(nu=0.02, lps="cell")
+    S = fem.lps_matrix(lev, prm).toarray()[2 * lev.nn:, 2 * lev.nn:]
+    alpha, h = fem.lps_alpha(lev, prm), lev.h
+    X, Y = lev.coords()
+    a, b, c = 0.7, -1.3, 2.1
+    got = S @ (a + b * X + c * Y).ravel()
+    expect = np.zeros(lev.nn)
+    solid = lambda cj, ci: (not (0 <= ci < lev.nx and 0 <= cj < lev.ny)) or lev.cell_solid[cj, ci]
+    node = lambda j, i: j * lev.nnx + i
+    for cj in range(lev.ny):
+        for ci in range(lev.nx):
+            if lev.cell_solid[cj, ci]:
+                continue
+            sides = [((0, -1), -b, [(cj, ci), (cj + 1, ci)]),          # left, n = (-1, 0)
+                     ((0, 1), b, [(cj, ci + 1), (cj + 1, ci + 1)]),     # right
+                     ((-1, 0), -c, [(cj, ci), (cj, ci + 1)]),           # bottom
+                     ((1, 0), c, [(cj + 1, ci), (cj + 1, ci + 1)])]     # top
+            for (dj, di), flux, ends in sides:
+                if solid(cj + dj, ci + di):
+                    for (j, i) in ends:
+                        expect[node(j, i)] += alpha * flux * h / 2
+    np.testing.assert_allclose(got, expect, rtol=0, atol=1e-13 * alpha)
+    assert np.abs(expect).max() > 0.1 * alpha * h
+    assert np.abs(S - S.T).max() < 1e-15
+    fluid = np.abs(S).sum(axis=1) > 0
+    ev = np.linalg.eigvalsh(S[np.ix_(fluid, fluid)])
+    assert ev[0] > -1e-13 * ev[-1] and abs(ev[0]) < 1e-13 * ev[-1] and ev[1] > 1e-6 * ev[-1]
+
+
+@pytest.mark.parametrize("ell", [1, 3])
+def test_poiseuille_under_cellwise_constant_lps_misses_by_the_boundary_term(ell):
+    """With the pressure Laplacian as stabilisation the Poiseuille flow is a
+    fixed point except on the inflow and outflow pressure rows, where the
+    residual is -(S p)_i = -alpha * int xi_i dp/dx n_x (p = 12 nu (4 - x):
+    dp/dx = -12 nu), O(alpha h)."""
+    lev = mesh.Level(ell, obstacle=None)
+    prm = fem.Params(nu=0.01, dt=0.01, lps="cell")
+    X, Y = lev.coords()
+    x = np.concatenate([(6 * Y * (1 - Y)).ravel(), np.zeros(lev.nn), (12 * prm.nu * (4 - X)).ravel()])
+    r = fem.residual(lev, x, fem.old_time_rhs(lev, x, prm), prm)
+    alpha, h = fem.lps_alpha(lev, prm), lev.h
+    expect = np.zeros(lev.ndof)
+    w = np.full(lev.nny, h)
+    w[[0, -1]] = h / 2                    # int xi_i dy along a vertical edge
+    rp = expect[2 * lev.nn:].reshape(lev.nny, lev.nnx)
+    rp[:, 0] = alpha * 12 * prm.nu * w    # (S p)_i on the inflow, n_x = -1
+    rp[:, -1] = -alpha * 12 * prm.nu * w  # outflow, n_x = +1
+    # residual = f - A(x): the stabilisation enters A with a plus sign
+    np.testing.assert_allclose(r, -expect, rtol=0, atol=1e-13)
 
 
 def test_mass_conservation_after_newton_step():
