@@ -525,9 +525,10 @@ def run_ours(args, rank, world):
                      "avg_launch_ms": dom["avg_launch_ms"], "launches": dom["launches"],
                      "timing": "CUDA events around each launch in a repeat of the timed steps",
                      "others": {
-                         f"vanka_pass_tiled_kernel<float> level {L}": {
+                         **({f"vanka_pass_tiled_kernel<float> level {L}": {
                              "achieved_gbs": pass_gbs, "frac": pass_gbs / hbm,
-                             "avg_launch_ms": avg_pass_ms, "bytes_per_launch": bytes_per_pass},
+                             "avg_launch_ms": avg_pass_ms, "bytes_per_launch": bytes_per_pass}}
+                            if vp_n else {}),           # not launched when level L is persistent
                          "V(2,2) cycle level 5 (whole cycle)": {
                              "achieved_gbs": vcycle_bytes(5) / (vc5 * 1e-3) / 1e9,
                              "frac": vcycle_bytes(5) / (vc5 * 1e-3) / 1e9 / hbm},

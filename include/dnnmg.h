@@ -82,9 +82,10 @@ typedef struct dnnmg_config {
   int32_t gmres_m;         /* FGMRES restart length (<= 40) */
   int32_t gmres_maxit;     /* total FGMRES iteration cap per Newton step */
   int32_t nu1, nu2;        /* pre- and post-smoothing sweeps of the V(nu1, nu2) cycle */
-  int32_t hidden;          /* GRU hidden size (64) */
-  int32_t gru_layers;      /* stacked GRU cells (2) */
-  int32_t mlp_width;       /* width of the hidden dense layer (128) */
+  int32_t hidden;          /* GRU hidden size m: 32 or 64 (default 64) */
+  int32_t gru_layers;      /* stacked GRU cells n: 1, 2 or 3 (default 2); m x n are
+                              the sizes of Table 1 */
+  int32_t mlp_width;       /* width of the hidden dense layer (128, the only value) */
   int32_t fallback_newton_its; /* DNN-MG step redone without the network if Newton needs more */
   int32_t train_batch;     /* largest training batch B (sequences) of dnnmg_train_*, 0 = none */
   int32_t train_seq;       /* largest training sequence length T */
@@ -228,21 +229,25 @@ int dnnmg_relative_errors(dnnmg_ctx* ctx, int level, const double* x, const doub
                           double* out);
 
 /* ---- patch network (Sec. 2.2, Sec. 3.1, Table 1) ------------------------------
- * Two stacked GRU cells (hidden 64, PyTorch gate convention r, z, n) and a
- * dense head Linear(64, 128) + ReLU + Linear(128, C_out), applied to every
- * patch independently.  A patch is one level-L cell; with r replaced levels
- * it covers K x K nodes of level L + r (K = 3 for r = 1, 5 for r = 2):
- * C_in = 4 K^2 + 4 inputs (prolongated velocity u, v and fine velocity
- * residual r_u, r_v at its K x K fine nodes, then 4 geometry/flow features:
- * 40 or 104), C_out = 2 K^2 outputs (velocity correction u, v at the nodes:
- * 18 or 50).  Weights are BF16 on
- * the tensor cores with FP32 accumulation; the hidden state is FP32.
- * Flat FP32 parameter order (PyTorch's): per GRU layer W_ih [192][C_l],
- * W_hh [192][64], b_ih [192], b_hh [192]; then W1 [128][64], b1 [128],
- * W2 [C_out][128], b2 [C_out].  A new context has all weights zero. */
+ * n stacked GRU cells of hidden size m (config gru_layers, hidden; m x n in
+ * {32, 64} x {1, 2, 3}, Table 1; default 64 x 2; PyTorch gate convention r,
+ * z, n) and a dense head Linear(m, 128) + ReLU + Linear(128, C_out), applied
+ * to every patch independently.  A patch is one level-L cell; with r
+ * replaced levels it covers K x K nodes of level L + r (K = 3 for r = 1, 5
+ * for r = 2): C_in = 4 K^2 + 4 inputs (prolongated velocity u, v and fine
+ * velocity residual r_u, r_v at its K x K fine nodes, then 4 geometry/flow
+ * features: 40 or 104), C_out = 2 K^2 outputs (velocity correction u, v at
+ * the nodes: 18 or 50).  Every size runs with C_in = 40; with C_in = 104 the
+ * 64 x 3 network does not fit the kernel's shared memory and its network
+ * calls return DNNMG_ERR_ARG.  Weights are BF16 on the tensor cores with
+ * FP32 accumulation; the hidden state is FP32.
+ * Flat FP32 parameter order (PyTorch's): per GRU layer W_ih [3m][C_l],
+ * W_hh [3m][m], b_ih [3m], b_hh [3m] (C_0 = C_in, C_l = m above); then
+ * W1 [128][m], b1 [128], W2 [C_out][128], b2 [C_out].  A new context has
+ * all weights zero. */
 
-/* Number of network parameters (55,954 for C_in = 40, C_out = 18; 72,370
- * for C_in = 104, C_out = 50). */
+/* Number of network parameters (55,954 for 64 x 2 with C_in = 40, C_out =
+ * 18; 72,370 for 64 x 2 with C_in = 104, C_out = 50). */
 size_t dnnmg_num_params(const dnnmg_ctx* ctx);
 
 /* Network input and output widths of the context. */
@@ -255,7 +260,7 @@ int dnnmg_get_weights(dnnmg_ctx* ctx, float* w);
 
 /* One recurrent step of the network for P patches (the network evaluation of Algorithm 1):
  *   x   : device [P][C_in] bfloat16 (raw uint16 bits), normalised inputs
- *   h   : device [2][P][64] float, hidden state, updated in place
+ *   h   : device [gru_layers][P][hidden] float, hidden state, updated in place
  *   out : device [P][C_out] float, predicted correction
  * P = 0 is a no-op.  Errors: DNNMG_ERR_ARG (unsupported network shape),
  * DNNMG_ERR_TIMEOUT (a tensor-core completion wait hit its bound). */

@@ -427,7 +427,7 @@ int Batch<T>::init() {
       bL_ = mem_.alloc<double>(N_);
       X_ = mem_.alloc<uint16_t>((size_t)P_ * nd_.c_in);
       net_out_ = mem_.alloc<float>((size_t)P_ * nd_.c_out);
-      hid_ = mem_.alloc<float>((size_t)2 * P_ * nd_.hidden);
+      hid_ = mem_.alloc<float>((size_t)nd_.layers * P_ * nd_.hidden);
       feat_mean_ = mem_.alloc<float>(nd_.c_in);
       feat_std_ = mem_.alloc<float>(nd_.c_in);
       const PackLayout pl = PackLayout::of(nd_);
@@ -444,7 +444,7 @@ int Batch<T>::init() {
       std::vector<float> zero(nd_.c_in, 0.0f), one(nd_.c_in, 1.0f);
       cudaMemcpyAsync(feat_mean_, zero.data(), sizeof(float) * nd_.c_in, cudaMemcpyHostToDevice, st_);
       cudaMemcpyAsync(feat_std_, one.data(), sizeof(float) * nd_.c_in, cudaMemcpyHostToDevice, st_);
-      cudaMemsetAsync(hid_, 0, sizeof(float) * 2 * P_ * nd_.hidden, st_);
+      cudaMemsetAsync(hid_, 0, sizeof(float) * nd_.layers * P_ * nd_.hidden, st_);
       cudaMemsetAsync(w_master_, 0, sizeof(float) * nd_.num_params(), st_);
       cudaMemsetAsync(net_status_, 0, sizeof(int) * 4, st_);
       launch_pack_weights(nd_, w_master_, pk_, st_);
@@ -872,7 +872,7 @@ int Batch<T>::set_state(int p, const double* x) {
   bk_copy_impose<T>(v_, 0, nullptr, x64_, top_.w(), upload_mask(one, sel_), st_);
   have_net_rhs_ = have_vcorr_ = false;
   steps_taken_ = 0;  // the next step refactors the coarse level
-  if (hid_) cudaMemsetAsync(hid_, 0, sizeof(float) * 2 * P_ * nd_.hidden, st_);
+  if (hid_) cudaMemsetAsync(hid_, 0, sizeof(float) * nd_.layers * P_ * nd_.hidden, st_);
   cudaStreamSynchronize(st_);
   return check("set_state");
 }

@@ -2,20 +2,23 @@
 // cells with memory per patch, then dense layers; inputs and outputs per
 // patch as in the network evaluation of Algorithm 1).
 //
-// patchnet_forward_kernel: persistent, one 128-patch tile at a time per CTA,
-// 512 threads in four warpgroups.  Patch row r of the tile is TMEM lane r;
-// warp w serves lanes 32 (w % 4) .. +31, and warpgroup w / 4 takes one
-// quarter of every accumulator's columns in the epilogues, so that the gate
-// nonlinearities of a tile are spread over 16 warps.  All weights live in
-// shared memory as BF16 K-major operands; per GRU layer the tensor core
-// accumulates in TMEM (256 FP32 columns)
-//   [0,128)   x W_ih[r,z]^T + h W_hh[r,z]^T      (gates r and z)
-//   [128,192) x W_ih[n]^T                        (input part of gate n)
-//   [192,256) h W_hh[n]^T                        (hidden part of gate n)
-// and each thread applies the gate nonlinearities to 16 units of its row in
+// patchnet_forward_kernel<TRAIN, m, n>: persistent, one 128-patch tile at a
+// time per CTA, 512 threads in four warpgroups.  Patch row r of the tile is
+// TMEM lane r; warp w serves lanes 32 (w % 4) .. +31, and warpgroup w / 4
+// takes one quarter of every accumulator's columns in the epilogues (m / 4
+// hidden units of its row), so that the gate nonlinearities of a tile are
+// spread over 16 warps.  All weights live in shared memory as BF16 K-major
+// operands; per GRU layer the tensor core accumulates in TMEM (4m FP32
+// columns)
+//   [0,2m)   x W_ih[r,z]^T + h W_hh[r,z]^T      (gates r and z)
+//   [2m,3m)  x W_ih[n]^T                        (input part of gate n)
+//   [3m,4m)  h W_hh[n]^T                        (hidden part of gate n)
+// and each thread applies the gate nonlinearities to its units in
 // registers, writing the new hidden state (FP32) to HBM and (BF16) to shared
-// memory as the next GEMM's operand.  The dense head reuses TMEM columns
-// [0,128) and [128,128+N2).
+// memory as the next GEMM's operand.  The previous state of a layer is read
+// back from HBM (the thread's own earlier write), so no layer's state stays
+// in registers between layers.  The dense head reuses TMEM columns [0,128)
+// and [128,128+N2).
 #include "kernels.h"
 #include "patchnet.cuh"
 #include "umma.cuh"
@@ -73,24 +76,25 @@ __global__ void pack_bias_kernel(const float* __restrict__ w, NetDims d, float* 
 // -- shared-memory plan of the forward kernel ---------------------------------
 // Operand regions are reused as soon as the MMA that reads them has
 // completed:
-//   a: x_t (layer 0 input, kx0 columns), then layer 0's new state (layer 1
-//      input, 64 columns);
-//   b: h0 (layer 0 hidden operand), then layer 1's new state (dense head input);
-//   c: h1 (layer 1 hidden operand);
+//   a: x_t (layer 0 input, kx0 columns), then each layer's new state (the
+//      next layer's input, m columns; the top layer's is the head's input);
+//   b: the previous state of the layer being evaluated (m columns), staged
+//      before that layer's MMAs;
 //   m: the dense head's hidden layer (128 columns), over a and b.
 struct FwdSmem {
-  uint32_t w, bias, a, b, c, m, bar, tmem, total;
+  uint32_t w, bias, a, b, m, bar, tmem, total;
   static __host__ __device__ uint32_t up(uint32_t v) { return (v + 127u) & ~127u; }
   static __host__ __device__ FwdSmem of(const NetDims& d, size_t w_elems) {
     FwdSmem s{};
     uint32_t o = 0;
     s.w = o;    o = up(o + (uint32_t)(w_elems * 2));
     s.bias = o; o = up(o + (uint32_t)((d.layers * 4 * d.hidden + d.mlp + d.nout()) * 4));
-    const uint32_t asz = kTile * (d.kx0() > 64 ? d.kx0() : 64) * 2;  // >= 16 KB
-    s.a = o;    o += asz;
-    s.b = o;    o += kTile * 64 * 2;    // a and b are contiguous: m needs 32 KB of them
+    const int ka = d.kx0() > d.hidden ? d.kx0() : d.hidden;
+    const uint32_t asz = kTile * ka * 2, bsz = kTile * d.hidden * 2, msz = kTile * 128 * 2;
+    s.a = o;
+    s.b = o + asz;
     s.m = s.a;
-    s.c = o;    o += kTile * 64 * 2;
+    o += asz + bsz > msz ? asz + bsz : msz;
     s.bar = o;  o += 16;
     s.tmem = o; o += 16;
     s.total = o;
@@ -98,13 +102,18 @@ struct FwdSmem {
   }
 };
 
-// write 16 consecutive values of row r (columns k0..k0+15) as BF16 operand
-__device__ __forceinline__ void store_row16(uint8_t* buf, int r, int k0, int K, const float* v) {
-  uint32_t p[8];
+// write U (8 or 16) consecutive values of row r (columns k0..) as BF16 operand
+template <int U>
+__device__ __forceinline__ void store_row(uint8_t* buf, int r, int k0, int K, const float* v) {
 #pragma unroll
-  for (int i = 0; i < 8; ++i) p[i] = (uint32_t)f2bf(v[2 * i]) | ((uint32_t)f2bf(v[2 * i + 1]) << 16);
-  *reinterpret_cast<uint4*>(buf + kmajor_offset(r, k0, K)) = make_uint4(p[0], p[1], p[2], p[3]);
-  *reinterpret_cast<uint4*>(buf + kmajor_offset(r, k0 + 8, K)) = make_uint4(p[4], p[5], p[6], p[7]);
+  for (int h = 0; h < U / 8; ++h) {
+    uint32_t p[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      p[i] = (uint32_t)f2bf(v[8 * h + 2 * i]) | ((uint32_t)f2bf(v[8 * h + 2 * i + 1]) << 16);
+    *reinterpret_cast<uint4*>(buf + kmajor_offset(r, k0 + 8 * h, K)) =
+        make_uint4(p[0], p[1], p[2], p[3]);
+  }
 }
 
 // Issue D(+)= A * B^T over K (in 16-wide slices) for one accumulator.
@@ -118,82 +127,85 @@ __device__ __forceinline__ void mma_run(uint32_t d_tmem, uint32_t a_addr, int a_
   }
 }
 
-// One GRU layer's epilogue for 16 units [u0, u0 + 16) of this thread's row:
-// gates from TMEM, new hidden state into hreg (FP32, these 16 units),
-// `next` (BF16 operand) and `hout` (FP32, HBM, the 16 units).  With `gsave`
-// the gates r, z, n and the hidden part of gate n (incl. bias) are stored
-// for the backward pass (row layout [r | z | n | hn], 64 each); with `hT`
-// the new state is also written transposed in BF16 (column `col`, row
-// stride ldT).
-__device__ __forceinline__ void gru_epilogue(uint32_t tm, const float* bias, float* hreg,
+template <int U>
+__device__ __forceinline__ void store_f32(float* dst, const float* v) {
+#pragma unroll
+  for (int q = 0; q < U / 4; ++q)
+    reinterpret_cast<float4*>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+template <int U>
+__device__ __forceinline__ void load_f32(const float* src, float* v) {
+#pragma unroll
+  for (int q = 0; q < U / 4; ++q) {
+    const float4 u = reinterpret_cast<const float4*>(src)[q];
+    v[4 * q] = u.x, v[4 * q + 1] = u.y, v[4 * q + 2] = u.z, v[4 * q + 3] = u.w;
+  }
+}
+
+// One GRU layer's epilogue for U units [u0, u0 + U) of this thread's row:
+// gates from TMEM, new hidden state from hprev into `next` (BF16 operand)
+// and `hout` (FP32, HBM, the U units).  With `gsave` the gates r, z, n and
+// the hidden part of gate n (incl. bias) are stored for the backward pass
+// (row layout [r | z | n | hn], m each); with `hT` the new state is also
+// written transposed in BF16 (column `col`, row stride ldT).
+template <int H, int U>
+__device__ __forceinline__ void gru_epilogue(uint32_t tm, const float* bias, const float* hprev,
                                              uint8_t* next, int row, int u0, float* hout,
                                              bool valid, float* gsave, uint16_t* hT, size_t ldT) {
-  constexpr int H = 64;
-  float rp[16], zp[16], ip[16], hp[16];
-  tmem_ld16(tm + u0, rp);
-  tmem_ld16(tm + 64 + u0, zp);
-  tmem_ld16(tm + 128 + u0, ip);
-  tmem_ld16(tm + 192 + u0, hp);
-  float hn[16];
+  float rp[U], zp[U], ip[U], hp[U];
+  tmem_ld<U>(tm + u0, rp);
+  tmem_ld<U>(tm + H + u0, zp);
+  tmem_ld<U>(tm + 2 * H + u0, ip);
+  tmem_ld<U>(tm + 3 * H + u0, hp);
+  float hn[U];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) {
+  for (int i = 0; i < U; ++i) {
     const int j = u0 + i;
     const float r = sigmoidf_(rp[i] + bias[j]);
     const float z = sigmoidf_(zp[i] + bias[H + j]);
     const float ghn = hp[i] + bias[3 * H + j];
     const float n = tanhf(ip[i] + bias[2 * H + j] + r * ghn);
-    hn[i] = (1.0f - z) * n + z * hreg[i];
+    hn[i] = (1.0f - z) * n + z * hprev[i];
     rp[i] = r, zp[i] = z, ip[i] = n, hp[i] = ghn;
   }
-#pragma unroll
-  for (int i = 0; i < 16; ++i) hreg[i] = hn[i];
-  store_row16(next, row, u0, H, hn);
+  store_row<U>(next, row, u0, H, hn);
   if (!valid) return;
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-    reinterpret_cast<float4*>(hout + u0)[q] =
-        make_float4(hn[4 * q], hn[4 * q + 1], hn[4 * q + 2], hn[4 * q + 3]);
+  store_f32<U>(hout + u0, hn);
   if (gsave) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      reinterpret_cast<float4*>(gsave + u0)[q] =
-          make_float4(rp[4 * q], rp[4 * q + 1], rp[4 * q + 2], rp[4 * q + 3]);
-      reinterpret_cast<float4*>(gsave + H + u0)[q] =
-          make_float4(zp[4 * q], zp[4 * q + 1], zp[4 * q + 2], zp[4 * q + 3]);
-      reinterpret_cast<float4*>(gsave + 2 * H + u0)[q] =
-          make_float4(ip[4 * q], ip[4 * q + 1], ip[4 * q + 2], ip[4 * q + 3]);
-      reinterpret_cast<float4*>(gsave + 3 * H + u0)[q] =
-          make_float4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
-    }
+    store_f32<U>(gsave + u0, rp);
+    store_f32<U>(gsave + H + u0, zp);
+    store_f32<U>(gsave + 2 * H + u0, ip);
+    store_f32<U>(gsave + 3 * H + u0, hp);
   }
   if (hT)
 #pragma unroll
-    for (int i = 0; i < 16; ++i) hT[(size_t)(u0 + i) * ldT] = f2bf(hn[i]);
+    for (int i = 0; i < U; ++i) hT[(size_t)(u0 + i) * ldT] = f2bf(hn[i]);
 }
 
 // Arguments of the forward kernel.  Inference: T = 1, hidden state read from
 // h_in and written to h_out.  Training: the hidden state starts at zero and
 // the kernel stores, per (t, p), the activations the backward pass needs
 // (act, FP32) and transposed BF16 copies of the GEMM inputs for the weight
-// gradients (column index t * P + p, see TrainLayout).
+// gradients (column index t * P + p).
 struct FwdArgs {
   const uint16_t* x;  // [P][T][C_in]
   int P, T;
-  const float* h_in;  // [2][P][64]
-  float* h_out;       // [2][P][64]
+  const float* h_in;  // [layers][P][m]
+  float* h_out;       // [layers][P][m]
   float* out;         // [P][T][C_out]
-  float* act;         // [T][P][kAct]
+  float* act;         // [T][P][act_size]
   uint16_t* xT;       // [kx0 + 16][T * P]
-  uint16_t* h0T;      // [80][(T + 1) * P], state of step t at column (t + 1) * P + p
-  uint16_t* h1T;      // [80][(T + 1) * P]
+  uint16_t* hT[kMaxLayers];  // [m + 16][(T + 1) * P], state of step t at column (t + 1) * P + p
   uint16_t* y1T;      // [144][T * P]
   int* status;
 };
 
-template <bool TRAIN>
+template <bool TRAIN, int H, int NL>
 __global__ void __launch_bounds__(kFwdThreads, 1)
     patchnet_forward_kernel(NetDims d, PackLayout L, const uint16_t* __restrict__ wimg,
                             const float* __restrict__ bias_g, FwdArgs a) {
+  constexpr int U = H / 4;  // hidden units of this thread's row
+  constexpr int KACT = act_size(H, NL);
   extern __shared__ __align__(1024) uint8_t sm[];
   const FwdSmem S = FwdSmem::of(d, L.total);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -209,7 +221,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     const uint4* src = reinterpret_cast<const uint4*>(wimg);
     uint4* dst = reinterpret_cast<uint4*>(sm + S.w);
     for (size_t i = t; i < L.total / 8; i += kFwdThreads) dst[i] = src[i];
-    const int nb = d.layers * 4 * d.hidden + d.mlp + d.nout();
+    const int nb = NL * 4 * H + d.mlp + d.nout();
     for (int i = t; i < nb; i += kFwdThreads) bias[i] = bias_g[i];
   }
   if (warp == 0) tmem_alloc(tslot, 256);
@@ -222,33 +234,34 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
   const uint32_t tm = tbase + ((uint32_t)((warp & 3) * 32) << 16);  // this warp's lanes
   const uint32_t sbase = smem_u32(sm);
   const int kx0 = d.kx0();
-  const int u0 = 16 * cq;  // this thread's 16 hidden units
+  const int u0 = U * cq;  // this thread's hidden units
   uint32_t phase = 0;
   bool failed = false;
   const int ntiles = (P + kTile - 1) / kTile;
-  const size_t HP = (size_t)P * 64;
+  const size_t HP = (size_t)P * H;
   const size_t ld = (size_t)T * P, ldh = (size_t)(T + 1) * P;
 
   for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
     const int p = tile * kTile + row;
     const bool valid = p < P;
-    float h0r[16], h1r[16];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float4 u = make_float4(0, 0, 0, 0), v = u;
-      if (!TRAIN && valid) {
-        u = reinterpret_cast<const float4*>(a.h_in + (size_t)p * 64 + u0)[q];
-        v = reinterpret_cast<const float4*>(a.h_in + HP + (size_t)p * 64 + u0)[q];
-      }
-      h0r[4 * q] = u.x, h0r[4 * q + 1] = u.y, h0r[4 * q + 2] = u.z, h0r[4 * q + 3] = u.w;
-      h1r[4 * q] = v.x, h1r[4 * q + 1] = v.y, h1r[4 * q + 2] = v.z, h1r[4 * q + 3] = v.w;
-    }
 #pragma unroll 1
     for (int step = 0; step < T && !failed; ++step) {
       const size_t col = (size_t)step * P + p;
-      float* act = TRAIN ? a.act + col * kAct : nullptr;
+      float* act = TRAIN ? a.act + col * KACT : nullptr;
+      // previous state of layer l (this thread's units): zero at the start
+      // of a training sequence, else the thread's own earlier write
+      auto load_prev = [&](int l, float* hv) {
+#pragma unroll
+        for (int i = 0; i < U; ++i) hv[i] = 0.0f;
+        if (!valid) return;
+        if (TRAIN) {
+          if (step > 0) load_f32<U>(act - (size_t)P * KACT + act_h(H, l) + u0, hv);
+        } else {
+          load_f32<U>(a.h_in + l * HP + (size_t)p * H + u0, hv);
+        }
+      };
       // ---- stage x_t (BF16, 16-byte chunks spread over the block) and the
-      // hidden states (BF16 operands, this thread's 16 units)
+      // first layer's previous state (BF16 operand, this thread's units)
       {
         const int nq = kx0 / 8;
         for (int e = t; e < kTile * nq; e += kFwdThreads) {
@@ -265,24 +278,25 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
           }
         }
       }
-      store_row16(sm + S.b, row, u0, 64, h0r);
-      store_row16(sm + S.c, row, u0, 64, h1r);
-      // ---- two GRU layers (unrolled, so that each layer's state stays in
-      // registers)
+      float hprev[U];
+      load_prev(0, hprev);
+      store_row<U>(sm + S.b, row, u0, H, hprev);
+      // ---- the GRU layers (unrolled); layer l reads its input from region
+      // a and its previous state from region b and writes its new state into
+      // region a
 #pragma unroll
-      for (int l = 0; l < 2; ++l) {
+      for (int l = 0; l < NL; ++l) {
         fence_async_smem();
         fence_before_sync();
         __syncthreads();
-        const uint32_t ax = sbase + S.a;  // x_t, then layer 0's new state
-        const int kx = l == 0 ? kx0 : 64;
-        const uint32_t ah = sbase + (l == 0 ? S.b : S.c);
+        const uint32_t ax = sbase + S.a, ah = sbase + S.b;
+        const int kx = l == 0 ? kx0 : H;
         if (t == 0) {
           fence_after_sync();
-          mma_run(tbase + 0, ax, kx, sbase + S.w + 2 * L.rz[l], kx, 128, kx, false);
-          mma_run(tbase + 0, ah, 64, sbase + S.w + 2 * L.hrz[l], 64, 128, 64, true);
-          mma_run(tbase + 128, ax, kx, sbase + S.w + 2 * L.in[l], kx, 64, kx, false);
-          mma_run(tbase + 192, ah, 64, sbase + S.w + 2 * L.hn[l], 64, 64, 64, false);
+          mma_run(tbase + 0, ax, kx, sbase + S.w + 2 * L.rz[l], kx, 2 * H, kx, false);
+          mma_run(tbase + 0, ah, H, sbase + S.w + 2 * L.hrz[l], H, 2 * H, H, true);
+          mma_run(tbase + 2 * H, ax, kx, sbase + S.w + 2 * L.in[l], kx, H, kx, false);
+          mma_run(tbase + 3 * H, ah, H, sbase + S.w + 2 * L.hn[l], H, H, H, false);
           mma_commit(bar);
         }
         if (!mbar_wait(bar, phase, kWaitPolls)) failed = true;
@@ -292,22 +306,23 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
           break;
         }
         fence_after_sync();
-        // layer 0 writes its new state into region a (x_t has been consumed)
-        // as layer 1's input; layer 1 into region b (h0 has been consumed) as
-        // the dense head's input
-        float* hout = TRAIN ? act + kActH0 + l * 64 : a.h_out + l * HP + (size_t)p * 64;
-        uint16_t* hT = TRAIN ? (l == 0 ? a.h0T : a.h1T) + ldh - ld + col : nullptr;
-        gru_epilogue(tm, bias + l * 4 * 64, l == 0 ? h0r : h1r, sm + (l == 0 ? S.a : S.b), row,
-                     u0, hout, valid, TRAIN ? act + kActG0 + l * 256 : nullptr, hT, ldh);
+        float* hout = TRAIN ? act + act_h(H, l) : a.h_out + l * HP + (size_t)p * H;
+        uint16_t* hT = TRAIN ? a.hT[l] + ldh - ld + col : nullptr;
+        gru_epilogue<H, U>(tm, bias + l * 4 * H, hprev, sm + S.a, row, u0, hout, valid,
+                           TRAIN ? act + act_g(H, NL, l) : nullptr, hT, ldh);
+        if (l + 1 < NL) {  // region b is free: stage the next layer's previous state
+          load_prev(l + 1, hprev);
+          store_row<U>(sm + S.b, row, u0, H, hprev);
+        }
       }
       if (failed) break;
-      // ---- dense head: relu(h1 W1^T + b1) W2^T + b2
+      // ---- dense head: relu(h W1^T + b1) W2^T + b2 on the top layer's state
       fence_async_smem();
       fence_before_sync();
       __syncthreads();
       if (t == 0) {
         fence_after_sync();
-        mma_run(tbase + 0, sbase + S.b, 64, sbase + S.w + 2 * L.w1, 64, 128, 64, false);
+        mma_run(tbase + 0, sbase + S.a, H, sbase + S.w + 2 * L.w1, H, 128, H, false);
         mma_commit(bar);
       }
       if (!mbar_wait(bar, phase, kWaitPolls)) failed = true;
@@ -317,22 +332,20 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         break;
       }
       fence_after_sync();
-      const float* b1 = bias + 2 * 4 * 64;
+      const float* b1 = bias + NL * 4 * H;
 #pragma unroll 1
       for (int c = 2 * cq; c < 2 * cq + 2; ++c) {  // 32 of the 128 units
         float v[16];
         tmem_ld16(tm + c * 16, v);
         if (TRAIN && valid) {
+          float pre[16];
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            reinterpret_cast<float4*>(act + kActA1)[c * 4 + q] =
-                make_float4(v[4 * q] + b1[c * 16 + 4 * q], v[4 * q + 1] + b1[c * 16 + 4 * q + 1],
-                            v[4 * q + 2] + b1[c * 16 + 4 * q + 2],
-                            v[4 * q + 3] + b1[c * 16 + 4 * q + 3]);
+          for (int i = 0; i < 16; ++i) pre[i] = v[i] + b1[c * 16 + i];
+          store_f32<16>(act + act_a1(H, NL) + c * 16, pre);
         }
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] + b1[c * 16 + i], 0.0f);
-        store_row16(sm + S.m, row, c * 16, 128, v);
+        store_row<16>(sm + S.m, row, c * 16, 128, v);
         if (TRAIN && valid)
 #pragma unroll
           for (int i = 0; i < 16; ++i) a.y1T[(size_t)(c * 16 + i) * ld + col] = f2bf(v[i]);
@@ -444,54 +457,73 @@ __global__ void __launch_bounds__(kTile, 1)
   }
 }
 
-template <bool TRAIN>
-void launch_forward_impl(const NetDims& d, const PackedNet& pk, const FwdArgs& a, cudaStream_t st) {
+template <bool TRAIN, int H, int NL>
+void launch_forward_shape(const NetDims& d, const PackedNet& pk, const FwdArgs& a,
+                          cudaStream_t st) {
   const PackLayout L = PackLayout::of(d);
   const FwdSmem S = FwdSmem::of(d, L.total);
-  cudaFuncSetAttribute(patchnet_forward_kernel<TRAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)S.total);
+  cudaFuncSetAttribute(patchnet_forward_kernel<TRAIN, H, NL>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.total);
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int ntiles = (a.P + kTile - 1) / kTile;
   note_launch();
-  patchnet_forward_kernel<TRAIN><<<ntiles < sms ? ntiles : sms, kFwdThreads, S.total, st>>>(
+  patchnet_forward_kernel<TRAIN, H, NL><<<ntiles < sms ? ntiles : sms, kFwdThreads, S.total, st>>>(
       d, L, pk.w, pk.bias, a);
+}
+
+// one instantiation per network size of Table 1
+template <bool TRAIN>
+void launch_forward_impl(const NetDims& d, const PackedNet& pk, const FwdArgs& a, cudaStream_t st) {
+  switch (d.hidden * 10 + d.layers) {
+    case 321: launch_forward_shape<TRAIN, 32, 1>(d, pk, a, st); break;
+    case 322: launch_forward_shape<TRAIN, 32, 2>(d, pk, a, st); break;
+    case 323: launch_forward_shape<TRAIN, 32, 3>(d, pk, a, st); break;
+    case 641: launch_forward_shape<TRAIN, 64, 1>(d, pk, a, st); break;
+    case 642: launch_forward_shape<TRAIN, 64, 2>(d, pk, a, st); break;
+    case 643: launch_forward_shape<TRAIN, 64, 3>(d, pk, a, st); break;
+    default: break;  // rejected by net_supported
+  }
 }
 
 }  // namespace
 
+size_t patchnet_forward_smem(const NetDims& d) {
+  return FwdSmem::of(d, PackLayout::of(d).total).total;
+}
+
 bool net_supported(const NetDims& d) {
-  if (d.hidden != 64 || d.layers != 2 || d.mlp != 128 || d.c_in % 8 != 0 || d.c_out > 64 ||
-      d.nout() > 16 * kFwdWG)
+  if ((d.hidden != 32 && d.hidden != 64) || d.layers < 1 || d.layers > kMaxLayers ||
+      d.mlp != 128 || d.c_in % 8 != 0 || d.c_out > 64 || d.nout() > 16 * kFwdWG)
     return false;
-  const PackLayout L = PackLayout::of(d);
-  return FwdSmem::of(d, L.total).total <= 227 * 1024;
+  constexpr size_t kSmemMax = 227 * 1024;
+  return patchnet_forward_smem(d) <= kSmemMax && patchnet_backward_smem(d) <= kSmemMax;
 }
 
 void launch_pack_weights(const NetDims& d, const float* w, PackedNet& pk, cudaStream_t st) {
   const PackLayout L = PackLayout::of(d);
   const int H = d.hidden;
   size_t off = 0;
-  for (int l = 0; l < 2; ++l) {
+  for (int l = 0; l < d.layers; ++l) {
     const int c = l == 0 ? d.c_in : H;
     const float* Wih = w + off;
     const float* Whh = Wih + (size_t)3 * H * c;
     const int kx = L.kx[l];
     note_launch();
-    pack_block_kernel<<<64, 256, 0, st>>>(Wih, c, 0, 128, c, 128, kx, pk.w + L.rz[l]);
+    pack_block_kernel<<<64, 256, 0, st>>>(Wih, c, 0, 2 * H, c, 2 * H, kx, pk.w + L.rz[l]);
     note_launch();
-    pack_block_kernel<<<64, 256, 0, st>>>(Wih, c, 128, 64, c, 64, kx, pk.w + L.in[l]);
+    pack_block_kernel<<<64, 256, 0, st>>>(Wih, c, 2 * H, H, c, H, kx, pk.w + L.in[l]);
     note_launch();
-    pack_block_kernel<<<64, 256, 0, st>>>(Whh, H, 0, 128, H, 128, 64, pk.w + L.hrz[l]);
+    pack_block_kernel<<<64, 256, 0, st>>>(Whh, H, 0, 2 * H, H, 2 * H, H, pk.w + L.hrz[l]);
     note_launch();
-    pack_block_kernel<<<64, 256, 0, st>>>(Whh, H, 128, 64, H, 64, 64, pk.w + L.hn[l]);
+    pack_block_kernel<<<64, 256, 0, st>>>(Whh, H, 2 * H, H, H, H, H, pk.w + L.hn[l]);
     off += (size_t)3 * H * c + (size_t)3 * H * H + 6 * H;
   }
   const float* W1 = w + off;
   const float* W2 = W1 + (size_t)d.mlp * H + d.mlp;
   note_launch();
-  pack_block_kernel<<<64, 256, 0, st>>>(W1, H, 0, 128, H, 128, 64, pk.w + L.w1);
+  pack_block_kernel<<<64, 256, 0, st>>>(W1, H, 0, 128, H, 128, H, pk.w + L.w1);
   note_launch();
   pack_block_kernel<<<64, 256, 0, st>>>(W2, d.mlp, 0, d.c_out, d.mlp, d.nout(), 128, pk.w + L.w2);
   note_launch();
@@ -524,8 +556,7 @@ void launch_patchnet_train_forward(const NetDims& d, const PackedNet& pk, const 
   a.out = ypred;
   a.act = tb.act;
   a.xT = tb.xT;
-  a.h0T = tb.h0T;
-  a.h1T = tb.h1T;
+  for (int l = 0; l < kMaxLayers; ++l) a.hT[l] = tb.hT[l];
   a.y1T = tb.y1T;
   a.status = status;
   launch_forward_impl<true>(d, pk, a, st);

@@ -1,11 +1,12 @@
-// Patch network of DNN-MG (Sec. 2.2, Sec. 3.1): two stacked GRU cells with
-// hidden size 64 and a dense head Linear(64 -> 128) + ReLU + Linear(128 ->
-// C_out), evaluated for every patch with tcgen05 tensor-core GEMMs.
+// Patch network of DNN-MG (Sec. 2.2, Sec. 3.1): n stacked GRU cells with
+// hidden size m (m x n in {32, 64} x {1, 2, 3}, the sizes of Table 1) and a
+// dense head Linear(m -> 128) + ReLU + Linear(128 -> C_out), evaluated for
+// every patch with tcgen05 tensor-core GEMMs.
 //
 // Flat FP32 parameter order (PyTorch's GRU order, gate rows r, z, n):
-//   per layer l: W_ih (192 x C_l), W_hh (192 x 64), b_ih (192), b_hh (192)
-//   then W1 (128 x 64), b1 (128), W2 (C_out x 128), b2 (C_out)
-// with C_0 = C_in (40 for one replaced level) and C_1 = 64.
+//   per layer l: W_ih (3m x C_l), W_hh (3m x m), b_ih (3m), b_hh (3m)
+//   then W1 (128 x m), b1 (128), W2 (C_out x 128), b2 (C_out)
+// with C_0 = C_in (40 for one replaced level) and C_l = m above.
 #pragma once
 #include <cstddef>
 #include <cstdint>
@@ -13,6 +14,8 @@
 #include <cuda_runtime.h>
 
 namespace dnnmg {
+
+constexpr int kMaxLayers = 3;
 
 struct NetDims {
   int c_in = 40, hidden = 64, layers = 2, mlp = 128, c_out = 18;
@@ -34,26 +37,29 @@ struct NetDims {
 // forward kernel, copied verbatim) and FP32 biases.
 struct PackedNet {
   uint16_t* w = nullptr;     // BF16 operand image
-  float* bias = nullptr;     // [layers][4][64] (r: b_ir+b_hr, z: b_iz+b_hz, b_in, b_hn), b1, b2
+  float* bias = nullptr;     // [layers][4][m] (r: b_ir+b_hr, z: b_iz+b_hz, b_in, b_hn), b1, b2
   size_t w_elems = 0;
   size_t bias_elems = 0;
 };
 
-// element offsets of the packed operand blocks
+// element offsets of the packed operand blocks: per layer the gate rows r, z
+// of W_ih (2m x kx) and W_hh (2m x m), the n rows of W_ih (m x kx) and W_hh
+// (m x m); then W1 (128 x m) and W2 (nout x 128)
 struct PackLayout {
-  size_t rz[2], in[2], hrz[2], hn[2], w1, w2, total;
-  int kx[2];
+  size_t rz[kMaxLayers], in[kMaxLayers], hrz[kMaxLayers], hn[kMaxLayers], w1, w2, total;
+  int kx[kMaxLayers];
   __host__ __device__ static PackLayout of(const NetDims& d) {
     PackLayout p{};
+    const size_t H = d.hidden;
     size_t o = 0;
-    for (int l = 0; l < 2; ++l) {
+    for (int l = 0; l < d.layers; ++l) {
       p.kx[l] = l == 0 ? d.kx0() : d.hidden;
-      p.rz[l] = o;  o += (size_t)128 * p.kx[l];
-      p.in[l] = o;  o += (size_t)64 * p.kx[l];
-      p.hrz[l] = o; o += (size_t)128 * 64;
-      p.hn[l] = o;  o += (size_t)64 * 64;
+      p.rz[l] = o;  o += 2 * H * p.kx[l];
+      p.in[l] = o;  o += H * p.kx[l];
+      p.hrz[l] = o; o += 2 * H * H;
+      p.hn[l] = o;  o += H * H;
     }
-    p.w1 = o; o += (size_t)128 * 64;
+    p.w1 = o; o += (size_t)128 * H;
     p.w2 = o; o += (size_t)d.nout() * 128;
     p.total = o;
     return p;
@@ -61,28 +67,35 @@ struct PackLayout {
 };
 
 // Per (step, patch) activations saved by the training forward pass (FP32):
-// new hidden states, gates (r, z, n, hidden part of n incl. bias) of both
-// layers and the pre-activation of the hidden dense layer.
-constexpr int kActH0 = 0, kActH1 = 64, kActG0 = 128, kActG1 = 384, kActA1 = 640, kAct = 768;
+// the new hidden state of every layer, the gates (r, z, n and the hidden
+// part of n incl. bias, m each) of every layer and the pre-activation of the
+// hidden dense layer.
+__host__ __device__ constexpr int act_h(int H, int l) { return l * H; }
+__host__ __device__ constexpr int act_g(int H, int NL, int l) { return NL * H + 4 * H * l; }
+__host__ __device__ constexpr int act_a1(int H, int NL) { return 5 * NL * H; }
+__host__ __device__ constexpr int act_size(int H, int NL) { return 5 * NL * H + 128; }
 
 // Buffers of one training step for B sequences of T steps.  Columns of the
-// transposed BF16 streams are indexed t * B + b; h0T / h1T hold a leading
+// transposed BF16 streams are indexed t * B + b; every hT[l] holds a leading
 // block of B zero columns so that the previous step's state of column
-// t * B + b is at the same column of the unshifted view.  Row 40 of xT and
-// row 64 of h0T / h1T and row 128 of y1T hold ones (bias gradients).
+// t * B + b is at the same column of the unshifted view.  Row C_in of xT,
+// row m of every hT[l] and row 128 of y1T hold ones (bias gradients).
 struct TrainBufs {
-  float* act = nullptr;      // [T][B][kAct]
-  uint16_t* xT = nullptr;    // [48][T B]
-  uint16_t* h0T = nullptr;   // [80][(T+1) B]
-  uint16_t* h1T = nullptr;   // [80][(T+1) B]
-  uint16_t* y1T = nullptr;   // [144][T B]
+  float* act = nullptr;                   // [T][B][act_size]
+  uint16_t* xT = nullptr;                 // [kx0 + 16][T B]
+  uint16_t* hT[kMaxLayers] = {};          // [m + 16][(T+1) B]
+  uint16_t* y1T = nullptr;                // [144][T B]
 };
 
+// Shared-memory bytes of the forward and backward kernels (0 if the shape
+// has no kernel).
+size_t patchnet_forward_smem(const NetDims& d);
+size_t patchnet_backward_smem(const NetDims& d);
 bool net_supported(const NetDims& d);
 // master FP32 flat weights -> packed BF16 operands + fused biases
 void launch_pack_weights(const NetDims& d, const float* w, PackedNet& pk, cudaStream_t st);
-// one recurrent step for P patches: x [P][C_in] BF16, h [2][P][64] FP32 in,
-// h_out [2][P][64] (may alias h), out [P][C_out] FP32
+// one recurrent step for P patches: x [P][C_in] BF16, h [layers][P][m] FP32
+// in, h_out [layers][P][m] (may alias h), out [P][C_out] FP32
 void launch_patchnet_forward(const NetDims& d, const PackedNet& pk, const uint16_t* x,
                              const float* h, float* h_out, float* out, int P, int* status,
                              cudaStream_t st);

@@ -567,18 +567,18 @@ int dnnmg_ctx::init_train() {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   tr_blocks_max = sms;
   tr_splits_max = 160;
-  tb.act = mem.alloc<float>(K * kAct);
+  const int H = nd.hidden, NL = nd.layers, MG = gate_rows(nd);
+  tb.act = mem.alloc<float>(K * act_size(H, NL));
   tb.xT = mem.alloc<uint16_t>((size_t)(nd.kx0() + 16) * K);
-  tb.h0T = mem.alloc<uint16_t>(80 * Kh);
-  tb.h1T = mem.alloc<uint16_t>(80 * Kh);
+  for (int l = 0; l < NL; ++l) tb.hT[l] = mem.alloc<uint16_t>((size_t)(H + 16) * Kh);
   tb.y1T = mem.alloc<uint16_t>(144 * K);
   tr_ypred = mem.alloc<float>(K * nd.c_out);
   dyT = mem.alloc<uint16_t>(128 * K);
   da1T = mem.alloc<uint16_t>(128 * K);
-  gi0T = mem.alloc<uint16_t>(256 * K);
-  gh0T = mem.alloc<uint16_t>(256 * K);
-  gi1T = mem.alloc<uint16_t>(256 * K);
-  gh1T = mem.alloc<uint16_t>(256 * K);
+  for (int l = 0; l < NL; ++l) {
+    giT[l] = mem.alloc<uint16_t>((size_t)MG * K);
+    ghT[l] = mem.alloc<uint16_t>((size_t)MG * K);
+  }
   loss_part = mem.alloc<double>(tr_blocks_max);
   loss_dev = mem.alloc<float>(4);
   grad = mem.alloc<float>(nd.num_params());
@@ -586,7 +586,7 @@ int dnnmg_ctx::init_train() {
   adam_v = mem.alloc<float>(nd.num_params());
   cpart_floats = (size_t)tr_splits_max * 256 * 144;
   cpart = mem.alloc<float>(cpart_floats);
-  wT = mem.alloc<uint16_t>(BwdPack::kTotal);
+  wT = mem.alloc<uint16_t>(BwdPack::of(nd).total);
   if (!mem.ok()) return fail(DNNMG_ERR_CUDA, "training workspace allocation failed");
   return reset_optimizer();
 }
@@ -611,16 +611,18 @@ int dnnmg_ctx::train_grad_impl(const uint16_t* Xd, const float* Yd, int B, int T
   if (B < 16 || B % 16 || B > cfg.train_batch || T < 1 || T > cfg.train_seq)
     return fail(DNNMG_ERR_ARG, "need B % 16 == 0, 16 <= B <= train_batch, 1 <= T <= train_seq");
   const size_t K = (size_t)B * T, Kh = (size_t)(T + 1) * B;
+  const int H = nd.hidden, NL = nd.layers, MG = gate_rows(nd);
   if (B != tr_layout_B || T != tr_layout_T) {
     cudaMemsetAsync(tb.xT, 0, 2 * (size_t)(nd.kx0() + 16) * K, st);
-    cudaMemsetAsync(tb.h0T, 0, 2 * 80 * Kh, st);
-    cudaMemsetAsync(tb.h1T, 0, 2 * 80 * Kh, st);
+    for (int l = 0; l < NL; ++l) {
+      cudaMemsetAsync(tb.hT[l], 0, 2 * (size_t)(H + 16) * Kh, st);
+      cudaMemsetAsync(giT[l], 0, 2 * (size_t)MG * K, st);
+      cudaMemsetAsync(ghT[l], 0, 2 * (size_t)MG * K, st);
+      fill_rows_one(tb.hT[l], Kh, H, H + 1, st);
+    }
     cudaMemsetAsync(tb.y1T, 0, 2 * 144 * K, st);
     cudaMemsetAsync(dyT, 0, 2 * 128 * K, st);
-    for (uint16_t* g : {gi0T, gh0T, gi1T, gh1T}) cudaMemsetAsync(g, 0, 2 * 256 * K, st);
     fill_rows_one(tb.xT, K, nd.c_in, nd.c_in + 1, st);
-    fill_rows_one(tb.h0T, Kh, 64, 65, st);
-    fill_rows_one(tb.h1T, Kh, 64, 65, st);
     fill_rows_one(tb.y1T, K, 128, 129, st);
     tr_layout_B = B;
     tr_layout_T = T;
@@ -637,35 +639,43 @@ int dnnmg_ctx::train_grad_impl(const uint16_t* Xd, const float* Yd, int B, int T
   a.scale = (float)(2.0 / ((double)B * T * nd.c_out));
   a.dyT = dyT;
   a.da1T = da1T;
-  a.gi0T = gi0T;
-  a.gh0T = gh0T;
-  a.gi1T = gi1T;
-  a.gh1T = gh1T;
+  for (int l = 0; l < NL; ++l) {
+    a.giT[l] = giT[l];
+    a.ghT[l] = ghT[l];
+  }
   a.loss_partial = loss_part;
   a.status = net_status;
   const int nb = std::min((B + 127) / 128, tr_blocks_max);
   launch_patchnet_backward(nd, wT, a, nb, st);
   launch_loss(loss_part, nb, 1.0 / ((double)B * T * nd.c_out), loss_dev, st);
-  // weight gradients: dW = sum over columns of dG^T x (split-K), bias = ones row
-  const int H = nd.hidden;
-  const size_t oWih0 = 0, oWhh0 = oWih0 + (size_t)3 * H * nd.c_in, obih0 = oWhh0 + (size_t)3 * H * H,
-               obhh0 = obih0 + 3 * H, oWih1 = obhh0 + 3 * H, oWhh1 = oWih1 + (size_t)3 * H * H,
-               obih1 = oWhh1 + (size_t)3 * H * H, obhh1 = obih1 + 3 * H, oW1 = obhh1 + 3 * H,
-               ob1 = oW1 + (size_t)nd.mlp * H, oW2 = ob1 + nd.mlp,
+  // weight gradients: dW = sum over columns of dG^T x (split-K), bias = ones
+  // row; per layer W_ih against the layer's input (x, or the state of the
+  // layer below at the same step: the shifted view of its stream) and W_hh
+  // against the layer's previous state (the unshifted view)
+  WGradJob jobs[kMaxWGradJobs];
+  int njobs = 0;
+  size_t off = 0;
+  for (int l = 0; l < NL; ++l) {
+    const int c = l == 0 ? nd.c_in : H;
+    const size_t oWih = off, oWhh = oWih + (size_t)3 * H * c, obih = oWhh + (size_t)3 * H * H,
+                 obhh = obih + 3 * H;
+    off = obhh + 3 * H;
+    if (l == 0)
+      jobs[njobs++] = {giT[0], tb.xT, K, K, MG, (nd.c_in + 1 + 15) / 16 * 16, 3 * H, nd.c_in,
+                       nd.c_in, grad + oWih, grad + obih};
+    else
+      jobs[njobs++] = {giT[l], tb.hT[l - 1] + B, K, Kh, MG, H + 16, 3 * H, H, H, grad + oWih,
+                       grad + obih};
+    jobs[njobs++] = {ghT[l], tb.hT[l], K, Kh, MG, H + 16, 3 * H, H, H, grad + oWhh, grad + obhh};
+  }
+  const size_t oW1 = off, ob1 = oW1 + (size_t)nd.mlp * H, oW2 = ob1 + nd.mlp,
                ob2 = oW2 + (size_t)nd.c_out * nd.mlp;
-  const WGradJob jobs[] = {
-      {gi0T, tb.xT, K, K, 256, (nd.c_in + 1 + 15) / 16 * 16, 3 * H, nd.c_in, nd.c_in,
-       grad + oWih0, grad + obih0},
-      {gh0T, tb.h0T, K, Kh, 256, 80, 3 * H, H, H, grad + oWhh0, grad + obhh0},
-      {gi1T, tb.h0T + B, K, Kh, 256, 80, 3 * H, H, H, grad + oWih1, grad + obih1},
-      {gh1T, tb.h1T, K, Kh, 256, 80, 3 * H, H, H, grad + oWhh1, grad + obhh1},
-      {da1T, tb.h1T + B, K, Kh, 128, 80, nd.mlp, H, H, grad + oW1, grad + ob1},
-      {dyT, tb.y1T, K, K, 128, 144, nd.c_out, nd.mlp, nd.mlp, grad + oW2, grad + ob2},
-  };
-  const int njobs = 6;
+  jobs[njobs++] = {da1T, tb.hT[NL - 1] + B, K, Kh, 128, H + 16, nd.mlp, H, H, grad + oW1,
+                   grad + ob1};
+  jobs[njobs++] = {dyT, tb.y1T, K, K, 128, 144, nd.c_out, nd.mlp, nd.mlp, grad + oW2, grad + ob2};
   // about two blocks per SM, at least four K chunks of 64 per block
   int tiles = 0;
-  for (const WGradJob& j : jobs) tiles += j.M / 128;
+  for (int q = 0; q < njobs; ++q) tiles += jobs[q].M / 128;
   int splits = std::max(1, std::min((2 * tr_blocks_max + tiles - 1) / tiles, (int)(K / 256)));
   while (splits > 1 && wgrad_partials(jobs, njobs, (int)K, splits) > cpart_floats) --splits;
   if (launch_wgrad(jobs, njobs, (int)K, splits, cpart, net_status, st))
@@ -722,7 +732,7 @@ int dnnmg_ctx::init_dnnmg() {
   bL = mem.alloc<double>(3 * (size_t)grid(L()).nn);
   X = mem.alloc<uint16_t>((size_t)P * nd.c_in);
   net_out = mem.alloc<float>((size_t)P * nd.c_out);
-  hid = mem.alloc<float>((size_t)2 * P * nd.hidden);
+  hid = mem.alloc<float>((size_t)nd.layers * P * nd.hidden);
   feat_mean = mem.alloc<float>(nd.c_in);
   feat_std = mem.alloc<float>(nd.c_in);
   stat_partial = mem.alloc<double>((size_t)128 * nd.c_in * 2);
@@ -732,7 +742,7 @@ int dnnmg_ctx::init_dnnmg() {
   std::vector<float> zero(nd.c_in, 0.0f), one(nd.c_in, 1.0f);
   cudaMemcpyAsync(feat_mean, zero.data(), sizeof(float) * nd.c_in, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(feat_std, one.data(), sizeof(float) * nd.c_in, cudaMemcpyHostToDevice, st);
-  cudaMemsetAsync(hid, 0, sizeof(float) * 2 * P * nd.hidden, st);
+  cudaMemsetAsync(hid, 0, sizeof(float) * nd.layers * P * nd.hidden, st);
   s64F = make_sten<double>(gF.h, cfg);
   cudaStreamSynchronize(st);
   return check("dnnmg setup");
@@ -991,7 +1001,7 @@ int dnnmg_ctx::set_state(const double* x) {
   launch_impose_dirichlet64(grid(L()), x64, st);
   have_net_rhs = have_vcorr = false;
   steps_taken = 0;  // the next step refactors the coarse level
-  if (hid) cudaMemsetAsync(hid, 0, sizeof(float) * 2 * P * nd.hidden, st);
+  if (hid) cudaMemsetAsync(hid, 0, sizeof(float) * nd.layers * P * nd.hidden, st);
   cudaStreamSynchronize(st);
   return check("set_state");
 }

@@ -181,8 +181,9 @@ struct dnnmg_ctx {
   dnnmg::TrainBufs tb{};
   float *tr_ypred = nullptr, *loss_dev = nullptr, *grad = nullptr, *adam_m = nullptr,
         *adam_v = nullptr, *cpart = nullptr;
-  uint16_t *dyT = nullptr, *da1T = nullptr, *gi0T = nullptr, *gh0T = nullptr, *gi1T = nullptr,
-           *gh1T = nullptr, *wT = nullptr;
+  uint16_t *dyT = nullptr, *da1T = nullptr, *wT = nullptr;
+  uint16_t* giT[dnnmg::kMaxLayers] = {};  // gate gradients of each layer (input side)
+  uint16_t* ghT[dnnmg::kMaxLayers] = {};  // (hidden side)
   double* loss_part = nullptr;
   int tr_layout_B = -1, tr_layout_T = -1, adam_step = 0, tr_blocks_max = 0, tr_splits_max = 0;
   size_t cpart_floats = 0;

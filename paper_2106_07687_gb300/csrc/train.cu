@@ -32,14 +32,20 @@ __global__ void pack_transpose_kernel(const float* __restrict__ src, int ld, int
   }
 }
 
+// Shared memory of the backward kernel: the transposed weights and one
+// operand region R of 128 rows, which holds in turn dY (nout columns), dA1
+// (128) and the gate gradients [dr | dz | dn | r * dn] of a layer (4m);
+// both products of a layer (dG_h W_hh over [dr | dz] and r * dn, dG_i W_ih
+// over [dr | dz | dn]) read it.
 struct BwdSmem {
-  uint32_t w, r1, r2, bar, tmem, red, total;
-  static __host__ __device__ BwdSmem of() {
+  uint32_t w, r, bar, tmem, red, total;
+  static __host__ __device__ uint32_t up(uint32_t v) { return (v + 127u) & ~127u; }
+  static __host__ __device__ BwdSmem of(const NetDims& d, size_t w_elems) {
     BwdSmem s{};
     uint32_t o = 0;
-    s.w = o;    o += (uint32_t)(BwdPack::kTotal * 2);
-    s.r1 = o;   o += kTile * 192 * 2;
-    s.r2 = o;   o += kTile * 192 * 2;
+    s.w = o;    o = up(o + (uint32_t)(w_elems * 2));
+    const int kr = 4 * d.hidden > 128 ? 4 * d.hidden : 128;
+    s.r = o;    o += kTile * kr * 2;
     s.bar = o;  o += 16;
     s.tmem = o; o += 16;
     s.red = o;  o += 16 * 8;  // one double per warp
@@ -48,37 +54,61 @@ struct BwdSmem {
   }
 };
 
-__device__ __forceinline__ void store_row16(uint8_t* buf, int r, int k0, int K, const float* v) {
-  uint32_t p[8];
+template <int U>
+__device__ __forceinline__ void store_row(uint8_t* buf, int r, int k0, int K, const float* v) {
 #pragma unroll
-  for (int i = 0; i < 8; ++i) p[i] = (uint32_t)f2bf(v[2 * i]) | ((uint32_t)f2bf(v[2 * i + 1]) << 16);
-  *reinterpret_cast<uint4*>(buf + kmajor_offset(r, k0, K)) = make_uint4(p[0], p[1], p[2], p[3]);
-  *reinterpret_cast<uint4*>(buf + kmajor_offset(r, k0 + 8, K)) = make_uint4(p[4], p[5], p[6], p[7]);
+  for (int h = 0; h < U / 8; ++h) {
+    uint32_t p[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      p[i] = (uint32_t)f2bf(v[8 * h + 2 * i]) | ((uint32_t)f2bf(v[8 * h + 2 * i + 1]) << 16);
+    *reinterpret_cast<uint4*>(buf + kmajor_offset(r, k0 + 8 * h, K)) =
+        make_uint4(p[0], p[1], p[2], p[3]);
+  }
+}
+
+template <int U>
+__device__ __forceinline__ void load_f32(const float* src, float* v) {
+#pragma unroll
+  for (int q = 0; q < U / 4; ++q) {
+    const float4 u = reinterpret_cast<const float4*>(src)[q];
+    v[4 * q] = u.x, v[4 * q + 1] = u.y, v[4 * q + 2] = u.z, v[4 * q + 3] = u.w;
+  }
 }
 
 __device__ __forceinline__ void mma_run(uint32_t d_tmem, uint32_t a_addr, int a_K, uint32_t b_addr,
-                                        int b_K, int N, int K) {
+                                        int b_K, int N, int K, bool acc_first) {
   const uint32_t id = idesc_bf16(kTile, N);
   for (int ks = 0; ks < K / 16; ++ks) {
     const uint64_t da = smem_desc(a_addr + ks * 256, 128, (a_K / 8) * 128);
     const uint64_t db = smem_desc(b_addr + ks * 256, 128, (b_K / 8) * 128);
-    mma_bf16(d_tmem, da, db, id, ks > 0 ? 1u : 0u);
+    mma_bf16(d_tmem, da, db, id, (ks > 0 || acc_first) ? 1u : 0u);
   }
 }
 
-// Gradient of one GRU layer for this thread's row, hidden units
-// c*16..c*16+15: dh (total gradient of the new state) -> gate gradients dgi,
-// dgh (rows of the operands in r_gi / r_gh and transposed in HBM) and the
-// direct part dh * z of the previous state's gradient.
-__device__ __forceinline__ void gru_backward_chunk(int c, const float* dh, const float* g,
-                                                   const float* hprev, float* dprev, uint8_t* r_gi,
-                                                   uint8_t* r_gh, int row, bool valid,
-                                                   uint16_t* giT, uint16_t* ghT, size_t ld) {
-  float dar[16], daz[16], dan[16], dhn[16];
+// Gradient of one GRU layer for this thread's row, hidden units u0..u0+U-1:
+// dh (total gradient of the new state) -> gate gradients (into the operand
+// region R as [dr | dz | dn | r * dn] and transposed into giT / ghT) and the
+// direct part dh * z of the previous state's gradient.  Rows past the batch
+// (valid false) read nothing and give zeros.
+template <int H, int U>
+__device__ __forceinline__ void gru_backward_chunk(int u0, const float* dh, const float* g,
+                                                   const float* hprev, float* dprev, uint8_t* R,
+                                                   int row, bool valid, uint16_t* giT,
+                                                   uint16_t* ghT, size_t ld) {
+  float gr[U], gz[U], gn[U], gh[U];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    const int j = c * 16 + i;
-    const float r = g[j], z = g[64 + j], n = g[128 + j], ghn = g[192 + j];
+  for (int i = 0; i < U; ++i) gr[i] = gz[i] = gn[i] = gh[i] = 0.0f;
+  if (valid) {
+    load_f32<U>(g + u0, gr);
+    load_f32<U>(g + H + u0, gz);
+    load_f32<U>(g + 2 * H + u0, gn);
+    load_f32<U>(g + 3 * H + u0, gh);
+  }
+  float dar[U], daz[U], dan[U], dhn[U];
+#pragma unroll
+  for (int i = 0; i < U; ++i) {
+    const float r = gr[i], z = gz[i], n = gn[i], ghn = gh[i];
     const float dn = dh[i] * (1.0f - z);
     const float dz = dh[i] * (hprev[i] - n);
     const float an = dn * (1.0f - n * n);
@@ -89,24 +119,20 @@ __device__ __forceinline__ void gru_backward_chunk(int c, const float* dh, const
     dhn[i] = an * r;
     dprev[i] = dh[i] * z;
   }
-  if (r_gi) {
-    store_row16(r_gi, row, c * 16, 192, dar);
-    store_row16(r_gi, row, 64 + c * 16, 192, daz);
-    store_row16(r_gi, row, 128 + c * 16, 192, dan);
-  }
-  store_row16(r_gh, row, c * 16, 192, dar);
-  store_row16(r_gh, row, 64 + c * 16, 192, daz);
-  store_row16(r_gh, row, 128 + c * 16, 192, dhn);
+  store_row<U>(R, row, u0, 4 * H, dar);
+  store_row<U>(R, row, H + u0, 4 * H, daz);
+  store_row<U>(R, row, 2 * H + u0, 4 * H, dan);
+  store_row<U>(R, row, 3 * H + u0, 4 * H, dhn);
   if (valid) {
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int j = c * 16 + i;
+    for (int i = 0; i < U; ++i) {
+      const int j = u0 + i;
       giT[(size_t)j * ld] = f2bf(dar[i]);
-      giT[(size_t)(64 + j) * ld] = f2bf(daz[i]);
-      giT[(size_t)(128 + j) * ld] = f2bf(dan[i]);
+      giT[(size_t)(H + j) * ld] = f2bf(daz[i]);
+      giT[(size_t)(2 * H + j) * ld] = f2bf(dan[i]);
       ghT[(size_t)j * ld] = f2bf(dar[i]);
-      ghT[(size_t)(64 + j) * ld] = f2bf(daz[i]);
-      ghT[(size_t)(128 + j) * ld] = f2bf(dhn[i]);
+      ghT[(size_t)(H + j) * ld] = f2bf(daz[i]);
+      ghT[(size_t)(2 * H + j) * ld] = f2bf(dhn[i]);
     }
   }
 }
@@ -114,10 +140,17 @@ __device__ __forceinline__ void gru_backward_chunk(int c, const float* dh, const
 constexpr int kBwdWG = 4;  // warpgroups: each takes a quarter of every accumulator's columns
 constexpr int kBwdThreads = kTile * kBwdWG;
 
+// Backpropagation through time for 128 sequences per tile, steps T-1 .. 0.
+// TMEM columns: [0,128) dY W2, [128,128+m) dA1 W1 (the top layer's state
+// gradient), then per layer [0,m) dG_h W_hh (the previous state's gradient)
+// and [m,2m) dG_i W_ih (the gradient of the layer's input, the state of the
+// layer below).
+template <int H, int NL>
 __global__ void __launch_bounds__(kBwdThreads, 1)
-    patchnet_backward_kernel(NetDims d, const uint16_t* __restrict__ wT, BwdArgs a) {
+    patchnet_backward_kernel(NetDims d, BwdPack W, const uint16_t* __restrict__ wT, BwdArgs a) {
+  constexpr int U = H / 4, KACT = act_size(H, NL), KR = 4 * H;
   extern __shared__ __align__(1024) uint8_t sm[];
-  const BwdSmem S = BwdSmem::of();
+  const BwdSmem S = BwdSmem::of(d, W.total);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int row = (warp & 3) * 32 + lane;  // patch row of the tile = TMEM lane
   const int cq = warp >> 2;                // column quarter
@@ -127,7 +160,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
   {
     const uint4* src = reinterpret_cast<const uint4*>(wT);
     uint4* dst = reinterpret_cast<uint4*>(sm + S.w);
-    for (int i = t; i < BwdPack::kTotal / 8; i += kBwdThreads) dst[i] = src[i];
+    for (size_t i = t; i < W.total / 8; i += kBwdThreads) dst[i] = src[i];
   }
   if (warp == 0) tmem_alloc(tslot, 256);
   if (t == 0) mbar_init(bar, 1);
@@ -138,11 +171,11 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
   const uint32_t tbase = *tslot;
   const uint32_t tm = tbase + ((uint32_t)((warp & 3) * 32) << 16);
   const uint32_t sb = smem_u32(sm);
-  uint8_t* R1 = sm + S.r1;
-  uint8_t* R2 = sm + S.r2;
+  uint8_t* R = sm + S.r;
+  const uint32_t sw = sb + S.w;
   const int B = a.B, T = a.T, C = d.c_out, NO = d.nout();
   const size_t ld = (size_t)T * B;
-  const int u0 = 16 * cq;  // this thread's 16 hidden units
+  const int u0 = U * cq;  // this thread's hidden units
   uint32_t phase = 0;
   bool failed = false;
   double loss = 0.0;
@@ -166,14 +199,16 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
   for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
     const int p = tile * kTile + row;
     const bool valid = p < B;
-    float dh0n[16], dh1n[16];  // gradients w.r.t. the previous step's states (these units)
+    float dcar[NL][U];  // gradients w.r.t. the previous step's states (these units)
 #pragma unroll
-    for (int j = 0; j < 16; ++j) dh0n[j] = dh1n[j] = 0.0f;
+    for (int l = 0; l < NL; ++l)
+#pragma unroll
+      for (int j = 0; j < U; ++j) dcar[l][j] = 0.0f;
 #pragma unroll 1
     for (int step = T - 1; step >= 0 && !failed; --step) {
       const size_t col = (size_t)step * B + p;
-      const float* act = a.act + col * kAct;
-      const float* actp = step > 0 ? a.act + (col - B) * kAct : nullptr;
+      const float* act = a.act + col * KACT;
+      const float* actp = step > 0 ? act - (size_t)B * KACT : nullptr;
       // ---- loss and dY (Eq. 7 as a mean): dY = 2 (y - Y) / (B T C); output
       // columns 16 cq .. +15 (one 16-column chunk of the nout per warpgroup)
       if (cq < NO / 16) {
@@ -191,9 +226,9 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
             a.dyT[(size_t)j * ld + col] = f2bf(dy[i]);
           }
         }
-        store_row16(R1, row, 16 * cq, NO, dy);
+        store_row<16>(R, row, 16 * cq, NO, dy);
       }
-      sync_mma([&] { mma_run(tbase + 0, sb + S.r1, NO, sb + S.w + 2 * BwdPack::kW2T, NO, 128, NO); });
+      sync_mma([&] { mma_run(tbase + 0, sb + S.r, NO, sw + 2 * W.w2t, NO, 128, NO, false); });
       if (failed) break;
       // ---- dense head: da1 = (dY W2) * [a1 > 0], 32 of the 128 units
 #pragma unroll
@@ -203,56 +238,42 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int j = c * 16 + i;
-          v[i] = (valid && act[kActA1 + j] > 0.0f) ? v[i] : 0.0f;
+          v[i] = (valid && act[act_a1(H, NL) + j] > 0.0f) ? v[i] : 0.0f;
           if (valid) a.da1T[(size_t)j * ld + col] = f2bf(v[i]);
         }
-        store_row16(R1, row, c * 16, 128, v);
+        store_row<16>(R, row, c * 16, 128, v);
       }
-      sync_mma([&] { mma_run(tbase + 128, sb + S.r1, 128, sb + S.w + 2 * BwdPack::kW1T, 128, 64, 128); });
+      sync_mma([&] { mma_run(tbase + 128, sb + S.r, 128, sw + 2 * W.w1t, 128, H, 128, false); });
       if (failed) break;
-      // ---- GRU layer 1
-      {
-        float dh[16], hp[16], dp[16];
-        tmem_ld16(tm + 128 + u0, dh);
+      float dtop[U];  // gradient of the current layer's new state from above
+      tmem_ld<U>(tm + 128 + u0, dtop);
+      // ---- GRU layers, top to bottom (the first layer's input gradient is
+      // not needed)
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          dh[i] = valid ? dh[i] + dh1n[i] : 0.0f;
-          hp[i] = actp ? actp[kActH1 + u0 + i] : 0.0f;
+      for (int l = NL - 1; l >= 0; --l) {
+        float dh[U], hp[U], dp[U];
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+          dh[i] = valid ? dtop[i] + dcar[l][i] : 0.0f;
+          hp[i] = 0.0f;
         }
-        gru_backward_chunk(cq, dh, act + kActG1, hp, dp, R1, R2, row, valid, a.gi1T + col,
-                           a.gh1T + col, ld);
+        if (valid && actp) load_f32<U>(actp + act_h(H, l) + u0, hp);
+        gru_backward_chunk<H, U>(u0, dh, act + act_g(H, NL, l), hp, dp, R, row, valid,
+                                 a.giT[l] + col, a.ghT[l] + col, ld);
+        sync_mma([&] {
+          const uint32_t r0 = sb + S.r, wh = sw + 2 * W.whh[l];
+          mma_run(tbase + 0, r0, KR, wh, 3 * H, H, 2 * H, false);                 // [dr | dz]
+          mma_run(tbase + 0, r0 + 3 * H * 16, KR, wh + 2 * H * 16, 3 * H, H, H, true);  // r * dn
+          if (l > 0) mma_run(tbase + H, r0, KR, sw + 2 * W.wih[l], 3 * H, H, 3 * H, false);
+        });
+        if (failed) break;
+        float dm[U];
+        tmem_ld<U>(tm + u0, dm);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) dh1n[i] = dp[i];
+        for (int i = 0; i < U; ++i) dcar[l][i] = dp[i] + dm[i];
+        if (l > 0) tmem_ld<U>(tm + H + u0, dtop);
       }
-      sync_mma([&] {
-        mma_run(tbase + 0, sb + S.r2, 192, sb + S.w + 2 * BwdPack::kWhh1T, 192, 64, 192);
-        mma_run(tbase + 64, sb + S.r1, 192, sb + S.w + 2 * BwdPack::kWih1T, 192, 64, 192);
-      });
       if (failed) break;
-      // ---- GRU layer 0 (its input gradient is not needed)
-      {
-        float dmm[16], dtop[16], hp[16], dp[16];
-        tmem_ld16(tm + u0, dmm);
-        tmem_ld16(tm + 64 + u0, dtop);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          dh1n[i] += dmm[i];
-          dtop[i] = valid ? dtop[i] + dh0n[i] : 0.0f;
-          hp[i] = actp ? actp[kActH0 + u0 + i] : 0.0f;
-        }
-        gru_backward_chunk(cq, dtop, act + kActG0, hp, dp, nullptr, R2, row, valid, a.gi0T + col,
-                           a.gh0T + col, ld);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) dh0n[i] = dp[i];
-      }
-      sync_mma([&] { mma_run(tbase + 128, sb + S.r2, 192, sb + S.w + 2 * BwdPack::kWhh0T, 192, 64, 192); });
-      if (failed) break;
-      {
-        float dmm[16];
-        tmem_ld16(tm + 128 + u0, dmm);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) dh0n[i] += dmm[i];
-      }
       fence_before_sync();
       __syncthreads();
     }
@@ -451,32 +472,60 @@ __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g,
 }  // namespace
 
 void launch_pack_backward(const NetDims& d, const float* w, uint16_t* wT, cudaStream_t st) {
+  const BwdPack W = BwdPack::of(d);
   const int H = d.hidden;
-  const float* Wih0 = w;
-  const float* Whh0 = Wih0 + (size_t)3 * H * d.c_in;
-  const float* Wih1 = Whh0 + (size_t)3 * H * H + 6 * H;
-  const float* Whh1 = Wih1 + (size_t)3 * H * H;
-  const float* W1 = Whh1 + (size_t)3 * H * H + 6 * H;
+  const float* Wih[kMaxLayers] = {};
+  const float* Whh[kMaxLayers] = {};
+  size_t off = 0;
+  for (int l = 0; l < d.layers; ++l) {
+    const int c = l == 0 ? d.c_in : H;
+    Wih[l] = w + off;
+    Whh[l] = Wih[l] + (size_t)3 * H * c;
+    off += (size_t)3 * H * c + (size_t)3 * H * H + 6 * H;
+  }
+  const float* W1 = w + off;
   const float* W2 = W1 + (size_t)d.mlp * H + d.mlp;
   note_launch();
-  pack_transpose_kernel<<<64, 256, 0, st>>>(W2, d.mlp, 128, d.nout(), d.c_out, wT + BwdPack::kW2T);
+  pack_transpose_kernel<<<64, 256, 0, st>>>(W2, d.mlp, 128, d.nout(), d.c_out, wT + W.w2t);
   note_launch();
-  pack_transpose_kernel<<<64, 256, 0, st>>>(W1, H, 64, 128, 128, wT + BwdPack::kW1T);
-  note_launch();
-  pack_transpose_kernel<<<64, 256, 0, st>>>(Whh0, H, 64, 192, 192, wT + BwdPack::kWhh0T);
-  note_launch();
-  pack_transpose_kernel<<<64, 256, 0, st>>>(Whh1, H, 64, 192, 192, wT + BwdPack::kWhh1T);
-  note_launch();
-  pack_transpose_kernel<<<64, 256, 0, st>>>(Wih1, H, 64, 192, 192, wT + BwdPack::kWih1T);
+  pack_transpose_kernel<<<64, 256, 0, st>>>(W1, H, H, 128, 128, wT + W.w1t);
+  for (int l = 0; l < d.layers; ++l) {
+    note_launch();
+    pack_transpose_kernel<<<64, 256, 0, st>>>(Whh[l], H, H, 3 * H, 3 * H, wT + W.whh[l]);
+    if (l == 0) continue;
+    note_launch();
+    pack_transpose_kernel<<<64, 256, 0, st>>>(Wih[l], H, H, 3 * H, 3 * H, wT + W.wih[l]);
+  }
 }
+
+size_t patchnet_backward_smem(const NetDims& d) {
+  return BwdSmem::of(d, BwdPack::of(d).total).total;
+}
+
+namespace {
+template <int H, int NL>
+void launch_backward_shape(const NetDims& d, const uint16_t* wT, const BwdArgs& a, int nblocks,
+                           cudaStream_t st) {
+  const BwdPack W = BwdPack::of(d);
+  const BwdSmem S = BwdSmem::of(d, W.total);
+  cudaFuncSetAttribute(patchnet_backward_kernel<H, NL>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.total);
+  note_launch();
+  patchnet_backward_kernel<H, NL><<<nblocks, kBwdThreads, S.total, st>>>(d, W, wT, a);
+}
+}  // namespace
 
 void launch_patchnet_backward(const NetDims& d, const uint16_t* wT, const BwdArgs& a,
                               int nblocks, cudaStream_t st) {
-  const BwdSmem S = BwdSmem::of();
-  cudaFuncSetAttribute(patchnet_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)S.total);
-  note_launch();
-  patchnet_backward_kernel<<<nblocks, kBwdThreads, S.total, st>>>(d, wT, a);
+  switch (d.hidden * 10 + d.layers) {
+    case 321: launch_backward_shape<32, 1>(d, wT, a, nblocks, st); break;
+    case 322: launch_backward_shape<32, 2>(d, wT, a, nblocks, st); break;
+    case 323: launch_backward_shape<32, 3>(d, wT, a, nblocks, st); break;
+    case 641: launch_backward_shape<64, 1>(d, wT, a, nblocks, st); break;
+    case 642: launch_backward_shape<64, 2>(d, wT, a, nblocks, st); break;
+    case 643: launch_backward_shape<64, 3>(d, wT, a, nblocks, st); break;
+    default: break;  // rejected by net_supported
+  }
 }
 
 int launch_wgrad(const WGradJob* jobs, int njobs, int K, int splits, float* Cpart, int* status,

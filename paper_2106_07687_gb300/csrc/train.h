@@ -8,28 +8,43 @@
 namespace dnnmg {
 
 // Element offsets of the transposed BF16 weight operands used by the
-// backward pass (B operands of dY W2, dA1 W1, dG_h W_hh, dG_i W_ih1).
+// backward pass (B operands of dY W2, dA1 W1, dG_h W_hh of every layer and
+// dG_i W_ih of the layers above the first; m = hidden size).
 struct BwdPack {
-  static constexpr int kW2T = 0;                 // [128][nout <= 64]  W2^T
-  static constexpr int kW1T = kW2T + 128 * 64;   // [64][128]  W1^T
-  static constexpr int kWhh0T = kW1T + 64 * 128; // [64][192]  W_hh0^T
-  static constexpr int kWhh1T = kWhh0T + 64 * 192;
-  static constexpr int kWih1T = kWhh1T + 64 * 192;
-  static constexpr int kTotal = kWih1T + 64 * 192;
+  size_t w2t, w1t, whh[kMaxLayers], wih[kMaxLayers], total;
+  __host__ __device__ static BwdPack of(const NetDims& d) {
+    BwdPack p{};
+    const size_t H = d.hidden;
+    size_t o = 0;
+    p.w2t = o; o += (size_t)128 * d.nout();  // [128][nout]  W2^T
+    p.w1t = o; o += H * 128;                 // [m][128]     W1^T
+    for (int l = 0; l < d.layers; ++l) {     // [m][3m]      W_hh^T
+      p.whh[l] = o;
+      o += H * 3 * H;
+    }
+    for (int l = 1; l < d.layers; ++l) {     // [m][3m]      W_ih^T (layers >= 1)
+      p.wih[l] = o;
+      o += H * 3 * H;
+    }
+    p.total = o;
+    return p;
+  }
 };
 
+// rows of the transposed gate-gradient streams: 3m rounded up to the 128-row
+// tiles of the weight-gradient GEMM (the rows above 3m stay zero)
+inline int gate_rows(const NetDims& d) { return (3 * d.hidden + 127) / 128 * 128; }
+
 struct BwdArgs {
-  const float* act;      // [T][B][kAct] from the training forward
+  const float* act;      // [T][B][act_size] from the training forward
   const float* ypred;    // [B][T][C_out]
   const float* Y;        // [B][T][C_out] targets
   int B, T;
   float scale;           // 2 / (B T C_out)
   uint16_t* dyT;         // [128][T B]   rows >= C_out stay zero
   uint16_t* da1T;        // [128][T B]
-  uint16_t* gi0T;        // [256][T B]   rows >= 192 stay zero
-  uint16_t* gh0T;
-  uint16_t* gi1T;
-  uint16_t* gh1T;
+  uint16_t* giT[kMaxLayers];  // [gate_rows][T B]  dG_i of layer l (r, z, n)
+  uint16_t* ghT[kMaxLayers];  // [gate_rows][T B]  dG_h of layer l (r, z, r * dn)
   double* loss_partial;  // [gridDim]
   int* status;
 };

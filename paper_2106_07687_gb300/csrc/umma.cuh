@@ -134,5 +134,29 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 lanes x 8 consecutive 32-bit columns (as tmem_ld16)
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// U = 8 or 16 columns
+template <int U>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float* v) {
+  static_assert(U == 8 || U == 16, "8 or 16 columns");
+  if constexpr (U == 16)
+    tmem_ld16(taddr, v);
+  else
+    tmem_ld8(taddr, v);
+}
+
 }  // namespace umma
 }  // namespace dnnmg

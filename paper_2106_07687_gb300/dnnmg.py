@@ -242,8 +242,11 @@ class Context:
         return t
 
     def patch_infer(self, x_bf16, h, out=None):
-        """x_bf16: cuda bfloat16 [P, C_in]; h: cuda float32 [2, P, 64] (updated)."""
+        """x_bf16: cuda bfloat16 [P, C_in]; h: cuda float32 [gru_layers, P, hidden]
+        (updated)."""
         P = x_bf16.shape[0]
+        if h.numel() != self.cfg.gru_layers * P * self.cfg.hidden:
+            raise ValueError("h must hold gru_layers x P x hidden floats")
         out = torch.empty(P, self.net_dims()[1], dtype=torch.float32, device="cuda") \
             if out is None else out
         self._check(self.lib.dnnmg_patch_infer(self.h, _ptr(x_bf16), _ptr(h), _ptr(out), P))
