@@ -178,16 +178,10 @@ def net_flops(c_in=40, H=64, mlp=128, c_out=18):
     return 2 * fwd, 2 * (fwd + act + fwd)
 
 
-def train_network(dn, torch, stream, common, level, replaced, nu, nus_train, corpus_steps, iters):
-    """Corpus from plain trajectories on level `level + replaced` (one per
-    viscosity in nus_train, `corpus_steps` steps each), feature statistics,
-    and `iters` Adam steps at batch TRAIN_B x TRAIN_T, all with the library's
-    kernels.  Returns (context, mean, std, losses, ms per training step)."""
-    import numpy as np
-    import synthetic
-    net_ctx = dn.Context(level_solve=level, nu=nu, replaced_levels=replaced, train_batch=TRAIN_B,
-                         train_seq=TRAIN_T, **common)
-    P = net_ctx.num_patches()
+def build_corpus(dn, torch, common, level, replaced, nus_train, corpus_steps):
+    """Training samples from plain trajectories on level `level + replaced`
+    (one per viscosity in nus_train, `corpus_steps` steps each), made by the
+    library's kernels.  Returns (X, Y) stacked over steps."""
     Xs, Ys = [], []
     for v in nus_train:
         fctx = dn.Context(level_solve=level + replaced, nu=v, **common)
@@ -202,14 +196,26 @@ def train_network(dn, torch, stream, common, level, replaced, nu, nus_train, cor
             prev = cur
         fctx.close()
         sctx.close()
-    Xc, Yc = torch.cat(Xs).contiguous(), torch.cat(Ys).contiguous()
-    del Xs, Ys
+    return torch.cat(Xs).contiguous(), torch.cat(Ys).contiguous()
+
+
+def train_on(dn, torch, stream, common, level, replaced, nu, corpus, n_traj, corpus_steps, iters,
+             **net):
+    """A network (sizes in `net`: hidden, gru_layers) trained by `iters` Adam
+    steps at batch TRAIN_B x TRAIN_T on the corpus, with its feature
+    statistics.  Returns (context, mean, std, losses, ms per training step)."""
+    import numpy as np
+    import synthetic
+    Xc, Yc = corpus
+    net_ctx = dn.Context(level_solve=level, nu=nu, replaced_levels=replaced, train_batch=TRAIN_B,
+                         train_seq=TRAIN_T, **net, **common)
+    P = net_ctx.num_patches()
     feat_mean, feat_std = net_ctx.feature_stats(Xc)
     net_ctx.set_weights(synthetic.random_weights(77, net_ctx.num_params(), 0.05).astype(np.float32))
     rng = np.random.default_rng(3)
     idx_all = []
     for _ in range(iters):
-        tid = rng.integers(0, len(nus_train), TRAIN_B)
+        tid = rng.integers(0, n_traj, TRAIN_B)
         start = rng.integers(0, corpus_steps - TRAIN_T + 1, TRAIN_B)
         idx_all.append(np.stack([tid * corpus_steps + start, rng.integers(0, P, TRAIN_B)], 1))
     idx_dev = torch.from_numpy(np.stack(idx_all).astype(np.int32)).cuda()
@@ -227,9 +233,39 @@ def train_network(dn, torch, stream, common, level, replaced, nu, nus_train, cor
     te1.record(stream)
     torch.cuda.synchronize()
     train_ms = te0.elapsed_time(te1) / (iters - 5)
-    del Xc, Yc, idx_dev
-    torch.cuda.empty_cache()
+    del idx_dev
     return net_ctx, feat_mean, feat_std, losses, train_ms
+
+
+def train_network(dn, torch, stream, common, level, replaced, nu, nus_train, corpus_steps, iters,
+                  keep_corpus=False):
+    """Corpus (build_corpus) and the default network trained on it
+    (train_on); with keep_corpus the corpus is returned as well."""
+    corpus = build_corpus(dn, torch, common, level, replaced, nus_train, corpus_steps)
+    out = train_on(dn, torch, stream, common, level, replaced, nu, corpus, len(nus_train),
+                   corpus_steps, iters)
+    if keep_corpus:
+        return out + (corpus,)
+    del corpus
+    torch.cuda.empty_cache()
+    return out
+
+
+def time_infer(ctx, torch, stream, P, c_in, c_out, layers, hidden, reps=20):
+    """Mean time of one dnnmg_patch_infer over P patches (ms)."""
+    xin = torch.randn(P, c_in, device="cuda").to(torch.bfloat16)
+    hin = torch.zeros(layers, P, hidden, device="cuda")
+    out = torch.empty(P, c_out, device="cuda")
+    for _ in range(3):
+        ctx.patch_infer(xin, hin, out)
+    torch.cuda.synchronize()
+    te0, te1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    te0.record(stream)
+    for _ in range(reps):
+        ctx.patch_infer(xin, hin, out)
+    te1.record(stream)
+    torch.cuda.synchronize()
+    return te0.elapsed_time(te1) / reps
 
 
 def on_fine_level(c, net, ref, top):
@@ -343,6 +379,50 @@ def run_large(dn, torch, stream, flush, args, common):
     return out
 
 
+TABLE1_SIZES = [(32, 1), (64, 1), (32, 2), (64, 2), (32, 3), (64, 3)]
+
+
+def run_sizes(dn, torch, stream, flush, args, common, corpus):
+    """The network sizes of Table 1 (m x n: GRU hidden size m, n stacked
+    cells) on the default DNN-MG workload.  Each is trained on the same
+    corpus with the same batches and schedule; reported: parameters,
+    training time per Adam step (and its factor against 32 x 1, the columns
+    of Table 1), forward time over all patches, the last training loss, and
+    K DNN-MG steps from the impulsive start against plain MG on the finer
+    level (time per step, velocity and pressure errors, force drift)."""
+    out = []
+    base = None
+    for m, n in TABLE1_SIZES:
+        ctx, _, _, losses, train_ms = train_on(
+            dn, torch, stream, common, L, 1, NU, corpus, len(NU_TRAIN), CORPUS_STEPS, TRAIN_ITERS,
+            hidden=m, gru_layers=n)
+        infer_ms = time_infer(ctx, torch, stream, ctx.num_patches(), 40, 18, n, m)
+        ref = dn.Context(level_solve=L + 1, nu=NU, **common)
+        runs = {"dnnmg": (ctx, dn.NET), "mg_L+1": (ref, dn.PLAIN)}
+        for c, mode in runs.values():
+            for _ in range(max(1, args.warmup)):
+                c.step(mode)
+        K = args.steps
+        times, series, stats, _ = compare_runs(runs, "mg_L+1", ref, L, 1, stream, flush, torch,
+                                               K, dn.kernel_launches)
+        err = summarize_series(series, "mg_L+1")["dnnmg"]
+        if base is None:
+            base = (ctx.num_params(), train_ms)
+        out.append({"size": f"{m}x{n}", "params": ctx.num_params(),
+                    "params_factor": ctx.num_params() / base[0],
+                    "train_ms_per_iter": train_ms, "train_factor": train_ms / base[1],
+                    "forward_ms": infer_ms, "loss_first": losses[0], "loss_last": losses[-1],
+                    "dnnmg_ms_per_step": times["dnnmg"] / K,
+                    "fallbacks": sum(st["fallback"] for st in stats["dnnmg"]),
+                    "vel_l2_err_mean": err["vel_l2_err_mean"],
+                    "p_l2_err_mean": err["p_l2_err_mean"],
+                    "force_drift_mean": err["force_drift_mean"]})
+        for c in (ctx, ref):
+            c.close()
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -366,24 +446,11 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
 
     # ---- corpus from plain fine trajectories and training (untimed setup) ----
-    net_ctx, feat_mean, feat_std, losses, train_ms = train_network(
-        dn, torch, stream, common, L, 1, NU, NU_TRAIN, CORPUS_STEPS, TRAIN_ITERS)
+    net_ctx, feat_mean, feat_std, losses, train_ms, corpus = train_network(
+        dn, torch, stream, common, L, 1, NU, NU_TRAIN, CORPUS_STEPS, TRAIN_ITERS, keep_corpus=True)
     P = net_ctx.num_patches()
     # network forward alone (dnnmg_patch_infer over all patches)
-    xin = torch.randn(P, 40, device="cuda").to(torch.bfloat16)
-    hin = torch.zeros(2, P, 64, device="cuda")
-    out = torch.empty(P, 18, device="cuda")
-    for _ in range(3):
-        net_ctx.patch_infer(xin, hin, out)
-    torch.cuda.synchronize()
-    te0, te1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    te0.record(stream)
-    R = 20
-    for _ in range(R):
-        net_ctx.patch_infer(xin, hin, out)
-    te1.record(stream)
-    torch.cuda.synchronize()
-    infer_ms = te0.elapsed_time(te1) / R
+    infer_ms = time_infer(net_ctx, torch, stream, P, 40, 18, 2, 64)
 
     # ---- timed comparison from the impulsive start -----------------------------
     ref_ctx = dn.Context(level_solve=L + 1, nu=NU, **common)
@@ -455,6 +522,10 @@ def run_ours(args, rank, world):
                           feat_std, rank)
     # ---- large DNN-MG: the network replaces two levels -----------------------
     large = run_large(dn, torch, stream, flush, args, common)
+    # ---- the network sizes of Table 1 on the same corpus ---------------------
+    sizes = run_sizes(dn, torch, stream, flush, args, common, corpus)
+    del corpus
+    torch.cuda.empty_cache()
 
     ms = times["dnnmg"]
     if world > 1:
@@ -548,6 +619,10 @@ def run_ours(args, rank, world):
                     "loss_first": losses[0], "loss_last": losses[-1]},
         "batched": batched,
         "large_dnnmg": large,
+        "network_sizes": {"sizes": sizes,
+                          "setup": f"each trained {TRAIN_ITERS} Adam steps on the corpus of "
+                                   f"the default network; {args.steps} DNN-MG steps vs plain MG "
+                                   f"on level {L + 1} after {max(1, args.warmup)} warm-up steps"},
         "clocks": clk.summary(),
         "e2e": {"value": 1.0 / t_e2e, "unit": "time steps/s",
                 "h2d_bytes_per_step": 8 * ndof(L), "d2h_bytes_per_step": 8 * ndof(L)},
