@@ -182,20 +182,18 @@ __device__ __forceinline__ void band_lu_block(const Grid& g, double* __restrict_
 }
 
 // Columns [col0, col0 + kInvWarps) of the inverse: solve L U x = P e_col,
-// one warp per column, the warps of the block in step.  The factor entries
-// that step k needs (column k of L with the pivot, then row k of U) are
-// shared by all columns: the block streams them into a ring of kInvStages
-// shared-memory slots with asynchronous copies issued kInvStages - 1 steps
-// ahead, so no step waits on a global load.  All threads of the block call
-// it; sm holds inv_block_smem_doubles(n) doubles.
+// one warp per column, with no barrier between the warps until the end.
+// Each warp streams the factor entries a step needs (column k of L and the
+// pivot, then column k of U and 1 / U(k, k)) from global memory into a
+// register ring kInvAhead steps ahead, so a step waits neither on a load nor
+// on the other warps.  The forward sweep starts at row col - kl: a swap at
+// step k touches rows k and piv[k] <= k + kl, so no earlier step reaches the
+// nonzero of e_col.  All threads of the block call it; sm holds
+// inv_block_smem_doubles(n) doubles.
 constexpr int kInvWarps = 6;    // columns per block: 149 blocks cover the 891 columns
-constexpr int kInvStages = 8;
-constexpr int kInvLW = 64;   // >= kl: entries of one L column in a slot
-constexpr int kInvUW = 192;  // >= ku + kl + 1: entries of one U row in a slot
+constexpr int kInvAhead = 8;    // steps of factor entries in flight per warp
 
-__host__ __device__ inline size_t inv_block_smem_doubles(int n) {
-  return (size_t)kInvWarps * n + (size_t)kInvStages * (kInvLW + kInvUW + 1);
-}
+__host__ __device__ inline size_t inv_block_smem_doubles(int n) { return (size_t)kInvWarps * n; }
 
 // rd[k] = 1 / U(k, k) of the factored band (one thread per row)
 __device__ __forceinline__ void band_diag_recip(const Grid& g, const double* __restrict__ ab,
@@ -204,104 +202,100 @@ __device__ __forceinline__ void band_diag_recip(const Grid& g, const double* __r
   if (k < bd.n) rd[k] = 1.0 / ab[(size_t)k * bd.W + bd.kl];
 }
 
-__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
-  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
-  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
 __device__ __forceinline__ void band_inverse_block(const Grid& g, const double* __restrict__ ab,
                                                    const int* __restrict__ piv,
                                                    const double* __restrict__ rd,
                                                    double* __restrict__ Ainv, int col0, double* sm) {
   const Band bd = band_of(g);
-  const int n = bd.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nt = blockDim.x;
-  double* xs = sm;                                   // [kInvWarps][n]
-  double* Lb = sm + (size_t)kInvWarps * n;           // [kInvStages][kInvLW]
-  double* Ub = Lb + (size_t)kInvStages * kInvLW;     // [kInvStages][kInvUW]
-  int* pb = reinterpret_cast<int*>(Ub + (size_t)kInvStages * kInvUW);  // [kInvStages]
+  const int n = bd.n, kl = bd.kl, KU2 = bd.ku + bd.kl, W = bd.W;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int col = col0 + warp;
-  double* x = xs + (size_t)warp * n;
-  // stage s of the forward sweep: L(s+1 .. s+kl, s) and piv[s]
-  auto issue_fwd = [&](int s) {
-    if (s < n) {
-      const int m = min(bd.kl, n - 1 - s);
-      for (int t = tid; t < m; t += nt)
-        cp_async8(Lb + (size_t)(s % kInvStages) * kInvLW + t,
-                  ab + (size_t)(s + 1 + t) * bd.W + (bd.kl - 1 - t));
-      if (tid == nt - 1) cp_async4(pb + s % kInvStages, piv + s);
-    }
-    cp_async_commit();
-  };
-  // stage s of the backward sweep (row k = n - 1 - s): 1 / U(k, k) in slot
-  // entry 0, U(k, k+1 .. cmax) in entries 1..
-  auto issue_bwd = [&](int s) {
-    if (s < n) {
-      const int k = n - 1 - s;
-      const int m = min(bd.ku + bd.kl, n - 1 - k) + 1;
-      double* slot = Ub + (size_t)(s % kInvStages) * kInvUW;
-      for (int t = tid; t < m; t += nt)
-        cp_async8(slot + t, t == 0 ? rd + k : ab + (size_t)k * bd.W + bd.kl + t);
-    }
-    cp_async_commit();
-  };
-  if (col < n)
+  double* x = sm + (size_t)warp * n;
+  constexpr int D = kInvAhead;
+  if (col < n) {  // warp-uniform
     for (int r = lane; r < n; r += 32) x[r] = (r == col) ? 1.0 : 0.0;
-  for (int s = 0; s < kInvStages - 1; ++s) issue_fwd(s);
-  for (int k = 0; k < n; ++k) {
-    cp_async_wait<kInvStages - 2>();  // stage k has landed (this thread's copies)
-    __syncthreads();                   // ... everybody's; slot (k - 1) % S is free
-    issue_fwd(k + kInvStages - 1);
-    if (col < n) {
-      const int p = pb[k % kInvStages];
-      if (lane == 0 && p != k) {
-        const double t = x[k];
-        x[k] = x[p];
-        x[p] = t;
+    __syncwarp();
+    // ---- forward: x <- L^{-1} P x; lane holds L(k+1+lane, k), L(k+33+lane, k)
+    double la[D], lb[D];
+    int pp[D];
+    auto load_fwd = [&](int s, double& l0, double& l1, int& pk) {
+      l0 = l1 = 0.0;
+      pk = 0;
+      if (s < n) {
+        const int rmax = min(n - 1, s + kl);
+        const int r0 = s + 1 + lane, r1 = r0 + 32;
+        if (r0 <= rmax) l0 = ab[(size_t)r0 * W + (s - r0 + kl)];
+        if (r1 <= rmax) l1 = ab[(size_t)r1 * W + (s - r1 + kl)];
+        pk = piv[s];
       }
-      __syncwarp();
-      const double xk = x[k];
-      if (xk != 0.0) {
-        const double* Lk = Lb + (size_t)(k % kInvStages) * kInvLW;
-        const int rmax = min(n - 1, k + bd.kl);
-        for (int r = k + 1 + lane; r <= rmax; r += 32) x[r] -= Lk[r - k - 1] * xk;
+    };
+    const int k0 = max(0, col - kl);
+#pragma unroll
+    for (int j = 0; j < D; ++j) load_fwd(k0 + j, la[j], lb[j], pp[j]);
+    for (int kb = k0; kb < n; kb += D) {
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        const int k = kb + j;
+        if (k < n) {
+          const int p = pp[j];
+          if (lane == 0 && p != k) {
+            const double t = x[k];
+            x[k] = x[p];
+            x[p] = t;
+          }
+          __syncwarp();
+          const double xk = x[k];
+          const int rmax = min(n - 1, k + kl);
+          const int r0 = k + 1 + lane, r1 = r0 + 32;
+          if (r0 <= rmax) x[r0] -= la[j] * xk;
+          if (r1 <= rmax) x[r1] -= lb[j] * xk;
+          __syncwarp();
+        }
+        load_fwd(k + D, la[j], lb[j], pp[j]);
       }
-      __syncwarp();
+    }
+    // ---- backward: x <- U^{-1} x by columns, k = n-1 .. 0: x[k] /= U(k, k),
+    // then x[r] -= U(r, k) x[k] for the rows r = k-1-lane-32i (i < 4, ku + kl
+    // <= 128) above it; lane holds those U(r, k) and 1 / U(k, k)
+    double u0[D], u1[D], u2[D], u3[D], ri[D];
+    auto load_bwd = [&](int k, double& v0, double& v1, double& v2, double& v3, double& rk) {
+      v0 = v1 = v2 = v3 = rk = 0.0;
+      if (k >= 0) {
+        const int rmin = max(0, k - KU2);
+        const int r = k - 1 - lane;  // U(r, k) at ab[r W + k - r + kl]
+        if (r >= rmin) v0 = ab[(size_t)r * W + (k - r + kl)];
+        if (r - 32 >= rmin) v1 = ab[(size_t)(r - 32) * W + (k - r + 32 + kl)];
+        if (r - 64 >= rmin) v2 = ab[(size_t)(r - 64) * W + (k - r + 64 + kl)];
+        if (r - 96 >= rmin) v3 = ab[(size_t)(r - 96) * W + (k - r + 96 + kl)];
+        rk = rd[k];
+      }
+    };
+#pragma unroll
+    for (int j = 0; j < D; ++j) load_bwd(n - 1 - j, u0[j], u1[j], u2[j], u3[j], ri[j]);
+    for (int kb = n - 1; kb >= 0; kb -= D) {
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        const int k = kb - j;
+        if (k >= 0) {
+          const double xk = x[k] * ri[j];
+          __syncwarp();
+          if (lane == 0) x[k] = xk;
+          const int rmin = max(0, k - KU2), r = k - 1 - lane;
+          if (r >= rmin) x[r] -= u0[j] * xk;
+          if (r - 32 >= rmin) x[r - 32] -= u1[j] * xk;
+          if (r - 64 >= rmin) x[r - 64] -= u2[j] * xk;
+          if (r - 96 >= rmin) x[r - 96] -= u3[j] * xk;
+          __syncwarp();
+        }
+        load_bwd(k - D, u0[j], u1[j], u2[j], u3[j], ri[j]);
+      }
     }
   }
-  cp_async_wait<0>();
-  __syncthreads();
-  for (int s = 0; s < kInvStages - 1; ++s) issue_bwd(s);
-  for (int s = 0; s < n; ++s) {
-    cp_async_wait<kInvStages - 2>();
-    __syncthreads();
-    issue_bwd(s + kInvStages - 1);
-    if (col < n) {
-      const int k = n - 1 - s;
-      const double* Uk = Ub + (size_t)(s % kInvStages) * kInvUW;
-      const int cmax = min(n - 1, k + bd.ku + bd.kl);
-      double acc = 0.0;
-      for (int c2 = k + 1 + lane; c2 <= cmax; c2 += 32) acc += Uk[c2 - k] * x[c2];
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) x[k] = (x[k] - acc) * Uk[0];
-      __syncwarp();
-    }
-  }
-  cp_async_wait<0>();
   __syncthreads();
   // Ainv[r][col0 .. col0 + kInvWarps): kInvWarps consecutive doubles per row
-  for (int e = tid; e < n * kInvWarps; e += nt) {
+  for (int e = tid; e < n * kInvWarps; e += blockDim.x) {
     const int r = e / kInvWarps, w = e % kInvWarps;
-    if (col0 + w < n) Ainv[(size_t)r * n + col0 + w] = xs[(size_t)w * n + r];
+    if (col0 + w < n) Ainv[(size_t)r * n + col0 + w] = sm[(size_t)w * n + r];
   }
 }
 
