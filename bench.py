@@ -774,6 +774,31 @@ def run_net(args):
                       "loss_last": loss[-1]}))
 
 
+def run_coarse(args):
+    """Coarse level only: --warmup + --steps refactorisations of the level-1
+    Jacobian (assembly, cluster band LU, explicit inverse) through
+    dnnmg_linearize on the state of the DNN-MG workload after three plain
+    steps; prints the mean time of one linearisation (CUDA events)."""
+    import torch
+    from paper_2106_07687_gb300 import build, dnnmg as dn
+    build.build()
+    ctx = dn.Context(level_solve=L, precision=dn.MIXED, nu=NU, dt=DT)
+    for _ in range(3):
+        ctx.step(dn.PLAIN)
+    x = ctx.get_state()
+    for _ in range(args.warmup):
+        ctx.linearize(x)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        ctx.linearize(x)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "coarse", "level": 1, "linearize_ms":
+                      e0.elapsed_time(e1) / max(args.steps, 1)}))
+
+
 def summarize_launches(path):
     """Per-kernel launches, total time and share of an ncu CSV launch list
     (gpu__time_duration.sum per launch)."""
@@ -844,9 +869,10 @@ def main():
                     help="with --split: 0 cooperative grid, 1 single cluster, -1 autotuned")
     ap.add_argument("--summarize-launches", metavar="CSV", default=None,
                     help="print the per-kernel table of an ncu launch list and exit")
-    ap.add_argument("--mode", choices=["step", "vcycle", "net"], default="step",
-                    help="vcycle: only V-cycles on --level; net: only the patch network "
-                         "(short runs for kernel profilers)")
+    ap.add_argument("--mode", choices=["step", "vcycle", "net", "coarse"], default="step",
+                    help="vcycle: only V-cycles on --level; net: only the patch network; "
+                         "coarse: only coarse-level factorisations (short runs for kernel "
+                         "profilers)")
     args = ap.parse_args()
     if args.summarize_launches:
         summarize_launches(args.summarize_launches)
@@ -858,6 +884,9 @@ def main():
         return
     if args.mode == "net":
         run_net(args)
+        return
+    if args.mode == "coarse":
+        run_coarse(args)
         return
     if args.impl == "reference":
         out = run_reference(args, rank, world)
