@@ -774,6 +774,149 @@ def run_net(args):
                       "loss_last": loss[-1]}))
 
 
+PERIODIC_T = 10.0              # end time (s) of the long run, as in Sec. 3.4
+PERIODIC_WINDOW = 1.0          # compared over [T - 1 s, T]
+PERIODIC_TRAIN = (1.0, 8.0)    # training windows are cut from the reference in this interval
+PERIODIC_WINDOWS, PERIODIC_WIN_STEPS, PERIODIC_ITERS = 8, 20, 300
+
+
+def series_summary(t, drag, lift):
+    """Mean and half peak-to-peak of drag and lift, and, when the lift
+    oscillates, its period from the upward crossings of its mean."""
+    import numpy as np
+    d, l = np.asarray(drag), np.asarray(lift)
+    out = {"drag_mean": float(d.mean()), "drag_amp": float((d.max() - d.min()) / 2),
+           "lift_mean": float(l.mean()), "lift_amp": float((l.max() - l.min()) / 2)}
+    z = l - l.mean()
+    up = [t[i] - z[i] * (t[i + 1] - t[i]) / (z[i + 1] - z[i])
+          for i in range(len(z) - 1) if z[i] < 0 <= z[i + 1]]
+    out["lift_period"] = float(np.diff(up).mean()) if len(up) >= 2 else None
+    return out
+
+
+def first_max(v):
+    """Index of the first interior local maximum of v (None if none)."""
+    for i in range(1, len(v) - 1):
+        if v[i] > v[i - 1] and v[i] >= v[i + 1]:
+            return i
+    return None
+
+
+def run_periodic(args):
+    """Long horizon (Sec. 3.4): the default DNN-MG workload from the
+    impulsive start to t = 10 s.  The plain multigrid reference on the finer
+    level runs first; it supplies the training corpus (windows of
+    consecutive steps cut from t in [1, 8] s) and its states over the
+    compared window [9, 10] s.  The network is trained on that corpus; then
+    DNN-MG and plain multigrid on the coarse level run from t = 0.  Printed:
+    per method the velocity and pressure errors against the reference over
+    the window, drag and lift means, amplitudes and lift period, and, when
+    the lift oscillates, the drag and lift differences after aligning the
+    phases on the first lift maximum of the window (the paper's procedure);
+    with --steps the series are printed every that many steps."""
+    import numpy as np
+    import torch
+    from paper_2106_07687_gb300 import build, dnnmg as dn
+    import synthetic
+    build.build()
+    stream = torch.cuda.current_stream()
+    ob = synthetic.obstacle_block(1000)
+    common = dict(precision=dn.MIXED, dt=DT, obstacle_i0=ob[0], obstacle_j0=ob[1])
+    nsteps = int(round(PERIODIC_T / DT))
+    w0 = nsteps - int(round(PERIODIC_WINDOW / DT))
+    top = L + 1
+    ref = dn.Context(level_solve=top, nu=NU, **common)
+    sctx = dn.Context(level_solve=L, nu=NU, replaced_levels=1, **common)
+    starts = np.linspace(PERIODIC_TRAIN[0] / DT, PERIODIC_TRAIN[1] / DT - PERIODIC_WIN_STEPS,
+                         PERIODIC_WINDOWS).astype(int)
+    sample_steps = set()
+    for s0 in starts:
+        sample_steps.update(range(int(s0), int(s0) + PERIODIC_WIN_STEPS))
+    Xs, Ys, ref_states = [], [], []
+    series = {k: {"drag": [], "lift": [], "div": [], "vel_err": [], "p_err": []}
+              for k in ("mg_L+1", "dnnmg", "mg_L")}
+    t_run = {}
+    prev = ref.get_state().clone()
+    t0 = time.perf_counter()
+    for n in range(nsteps):
+        ref.step(dn.PLAIN)
+        cur = ref.get_state().clone()
+        if n in sample_steps:
+            X, Y = sctx.make_sample(prev, cur)
+            Xs.append(X)
+            Ys.append(Y)
+        if n >= w0:
+            ref_states.append(cur)
+            jd, fd, fl = ref.functionals(top, cur, prev)
+            for key, v in zip(("drag", "lift", "div", "vel_err", "p_err"), (fd, fl, jd, 0.0, 0.0)):
+                series["mg_L+1"][key].append(v)
+        prev = cur
+    torch.cuda.synchronize()
+    t_run["mg_L+1"] = time.perf_counter() - t0
+    sctx.close()
+    corpus = (torch.cat(Xs).contiguous(), torch.cat(Ys).contiguous())
+    del Xs, Ys
+    net_ctx, _, _, losses, train_ms = train_on(dn, torch, stream, common, L, 1, NU, corpus,
+                                               PERIODIC_WINDOWS, PERIODIC_WIN_STEPS,
+                                               PERIODIC_ITERS)
+    del corpus
+    torch.cuda.empty_cache()
+    coarse = dn.Context(level_solve=L, nu=NU, **common)
+    fallbacks = 0
+    for name, c, mode in (("dnnmg", net_ctx, dn.NET), ("mg_L", coarse, dn.PLAIN)):
+        prev = None  # the state before the window, taken at step w0 - 1
+        t0 = time.perf_counter()
+        for n in range(nsteps):
+            st = c.step(mode)
+            if mode == dn.NET:
+                fallbacks += st["fallback"]
+            if n >= w0 - 1:
+                cur = on_fine_level(c, mode == dn.NET, ref, top)
+                if n >= w0:
+                    ve, pe = ref.relative_errors(top, cur, ref_states[n - w0])
+                    jd, fd, fl = ref.functionals(top, cur, prev)
+                    for key, v in zip(("drag", "lift", "div", "vel_err", "p_err"),
+                                      (fd, fl, jd, ve, pe)):
+                        series[name][key].append(v)
+                prev = cur
+        torch.cuda.synchronize()
+        t_run[name] = time.perf_counter() - t0
+    t = [(w0 + 1 + i) * DT for i in range(nsteps - w0)]
+    r = series["mg_L+1"]
+    periodic = series_summary(t, r["drag"], r["lift"])["lift_amp"] > 1e-3 * abs(np.mean(r["drag"]))
+    out = {"mode": "periodic", "workload": WORKLOAD, "t_end": PERIODIC_T,
+           "window": [PERIODIC_T - PERIODIC_WINDOW, PERIODIC_T], "steps": nsteps,
+           "training": f"{PERIODIC_ITERS} Adam steps on {PERIODIC_WINDOWS} windows of "
+                       f"{PERIODIC_WIN_STEPS} consecutive reference steps in t = "
+                       f"{PERIODIC_TRAIN[0]}..{PERIODIC_TRAIN[1]} s",
+           "loss_first": losses[0], "loss_last": losses[-1], "train_ms_per_iter": train_ms,
+           "dnnmg_fallbacks": fallbacks, "lift_oscillates": bool(periodic), "methods": {}}
+    i_ref = first_max(r["lift"]) if periodic else None
+    for name, sr in series.items():
+        m = {"wall_s": t_run[name], **series_summary(t, sr["drag"], sr["lift"]),
+             "vel_l2_err_mean": float(np.mean(sr["vel_err"])),
+             "p_l2_err_mean": float(np.mean(sr["p_err"])),
+             "div_mean": float(np.mean(sr["div"])),
+             "drag_rel_diff_mean": float(np.mean(np.abs(np.subtract(sr["drag"], r["drag"])))
+                                         / abs(np.mean(r["drag"])))}
+        if periodic:
+            i_m = first_max(sr["lift"])
+            if i_m is not None and i_ref is not None:
+                sh = i_m - i_ref
+                a0, a1 = max(0, -sh), min(len(t), len(t) - sh)
+                dd = [sr["drag"][i + sh] - r["drag"][i] for i in range(a0, a1)]
+                dl = [sr["lift"][i + sh] - r["lift"][i] for i in range(a0, a1)]
+                m.update({"phase_shift_s": sh * DT,
+                          "aligned_drag_maxdiff": float(np.max(np.abs(dd))),
+                          "aligned_lift_maxdiff": float(np.max(np.abs(dl)))})
+        if args.steps > 1:
+            m["series_every"] = args.steps
+            m["drag"] = sr["drag"][::args.steps]
+            m["lift"] = sr["lift"][::args.steps]
+        out["methods"][name] = m
+    print(json.dumps(out))
+
+
 def run_coarse(args):
     """Coarse level only: --warmup + --steps refactorisations of the level-1
     Jacobian (assembly, cluster band LU, explicit inverse) through
@@ -869,10 +1012,12 @@ def main():
                     help="with --split: 0 cooperative grid, 1 single cluster, -1 autotuned")
     ap.add_argument("--summarize-launches", metavar="CSV", default=None,
                     help="print the per-kernel table of an ncu launch list and exit")
-    ap.add_argument("--mode", choices=["step", "vcycle", "net", "coarse"], default="step",
+    ap.add_argument("--mode", choices=["step", "vcycle", "net", "coarse", "periodic"],
+                    default="step",
                     help="vcycle: only V-cycles on --level; net: only the patch network; "
                          "coarse: only coarse-level factorisations (short runs for kernel "
-                         "profilers)")
+                         "profilers); periodic: the long run to t = 10 s with the "
+                         "functionals over the last second")
     args = ap.parse_args()
     if args.summarize_launches:
         summarize_launches(args.summarize_launches)
@@ -887,6 +1032,9 @@ def main():
         return
     if args.mode == "coarse":
         run_coarse(args)
+        return
+    if args.mode == "periodic":
+        run_periodic(args)
         return
     if args.impl == "reference":
         out = run_reference(args, rank, world)
