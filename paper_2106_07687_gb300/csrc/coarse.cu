@@ -258,10 +258,11 @@ __global__ void __launch_bounds__(1024)
 void launch_band_lu(const Grid& g, double* ab, int* piv, int* status, cudaStream_t st) {
   const Band bd = band_of(g);
   const size_t csm = lu_cluster_smem(bd);
-  static int cluster_ok = -1;  // checked once per process
-  if (cluster_ok < 0) {
-    cluster_ok = 0;
-    if (csm <= 227 * 1024 && bd.kl + 1 <= 2 * 32 &&
+  // whether the cluster can be placed, checked once per process (thread-safe
+  // initialisation of a function-local static)
+  static const int cluster_ok = [&] {
+    int ok = 0;
+    if (csm <= 227 * 1024 &&
         cudaFuncSetAttribute(band_lu_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              227 * 1024) == cudaSuccess) {
       cudaLaunchConfig_t cfg = {};
@@ -278,10 +279,11 @@ void launch_band_lu(const Grid& g, double* ab, int* piv, int* status, cudaStream
       int n = 0;
       if (cudaOccupancyMaxActiveClusters(&n, (void*)band_lu_cluster_kernel, &cfg) == cudaSuccess &&
           n > 0)
-        cluster_ok = 1;
+        ok = 1;
     }
     cudaGetLastError();
-  }
+    return ok;
+  }();
   if (cluster_ok == 1 && csm <= 227 * 1024) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];

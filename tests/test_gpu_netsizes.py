@@ -73,6 +73,39 @@ def test_gradient_matches_oracle(m, n):
     assert losses[-1] < 0.8 * losses[0], losses
 
 
+@pytest.mark.parametrize("m,n", [(32, 1), (32, 3), (64, 1)])
+def test_two_replaced_levels_sizes_match_oracle(m, n):
+    """The 104-input, 50-output network of two replaced levels at other
+    sizes: one recurrent step and the gradient."""
+    dn = lib()
+    B, T, P = 32, 2, 700
+    ctx = _ctx(dn, m, n, replaced_levels=2, train_batch=B, train_seq=T)
+    spec = net.NetSpec(c_in=104, c_out=50, hidden=m, layers=n)
+    assert ctx.num_params() == spec.num_params() and ctx.net_dims() == (104, 50)
+    w = synthetic.random_weights(5 * m + n, spec.num_params(), 0.2).astype(np.float32)
+    ctx.set_weights(w)
+    params = spec.unflatten(w.astype(np.float64))
+    x = net.bf16_round(synthetic.random_patch_inputs(P + 2 * n, (P, 104)))
+    h = synthetic.random_patch_inputs(P + m, (n, P, m), 0.5).astype(np.float32).astype(np.float64)
+    hg = torch.from_numpy(h).float().cuda()
+    out = ctx.patch_infer(torch.from_numpy(x).to(torch.bfloat16).cuda(), hg)
+    y_ref, h_ref = net.step_forward(spec, params, x, h, bf16=True)
+    assert rel(out.double().cpu().numpy(), y_ref) < 5e-3
+    assert rel(hg.double().cpu().numpy(), h_ref) < 2e-3
+    X = net.bf16_round(synthetic.random_patch_inputs(m + n, (B, T, 104)))
+    Y = synthetic.random_patch_inputs(m + n + 1, (B, T, 50), 0.3)
+    Xg = torch.from_numpy(X).to(torch.bfloat16).cuda().contiguous()  # held for the call
+    Yg = torch.from_numpy(Y).float().cuda().contiguous()
+    g = torch.empty(ctx.num_params(), dtype=torch.float32, device="cuda")
+    loss = ctypes.c_float()
+    ctx._check(ctx.lib.dnnmg_train_grad(ctx.h, dn._ptr(Xg), dn._ptr(Yg), B, T, dn._ptr(g),
+                                        ctypes.byref(loss)))
+    L_ref, g_ref = net.sequence_backward(spec, params, X, Y.astype(np.float32).astype(np.float64),
+                                         bf16=True)
+    assert abs(loss.value - L_ref) < 1e-3 * L_ref
+    assert rel(g.double().cpu().numpy(), g_ref) < 3e-2
+
+
 @pytest.mark.parametrize("m,n", [(32, 3), (64, 1)])
 def test_dnnmg_step_matches_oracle(m, n):
     dn = lib()
