@@ -155,14 +155,53 @@ __global__ void __launch_bounds__(kThreads)
   double* p2 = partials + (size_t)k * kDotBlocks;  // [k][kDotBlocks]
   double* p3 = partials + (size_t)2 * k * kDotBlocks;
   __shared__ T hT[64];
-  auto dots = [&](double* part) {
-    for (int i = 0; i < k; ++i) {
-      const T* v = V + (size_t)i * ld;
-      T acc = T(0);
-      for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) acc += v[e] * w[e];
-      const double t = block_sum((double)acc, sh);
-      if (threadIdx.x == 0) part[(size_t)i * gridDim.x + blockIdx.x] = t;
+  constexpr int kG = 8;                // dot products reduced together
+  constexpr int kW = kThreads / 32;
+  __shared__ double sg[kW][kG];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // the k partial dot products <V[i], w> (or <w, w> if V is null) of this
+  // block's chunk, kG at a time in one pass over the elements: products and
+  // per-thread sums in T, then per value a shuffle tree in each warp and a
+  // second one over the warps' sums (the order of block_sum)
+  auto dots = [&](const T* Vb, int nk, double* part) {
+    for (int i0 = 0; i0 < nk; i0 += kG) {
+      const int gk = min(kG, nk - i0);
+      T acc[kG];
+#pragma unroll
+      for (int u = 0; u < kG; ++u) acc[u] = T(0);
+      for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+        const T we = w[e];
+#pragma unroll
+        for (int u = 0; u < kG; ++u)
+          if (u < gk) acc[u] += (Vb ? Vb[(size_t)(i0 + u) * ld + e] : we) * we;
+      }
+#pragma unroll
+      for (int u = 0; u < kG; ++u) {
+        if (u >= gk) break;
+        double v = (double)acc[u];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sg[warp][u] = v;
+      }
+      __syncthreads();
+      if (warp < gk) {  // warp u finishes value u
+        double t = lane < kW ? sg[lane][warp] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) part[(size_t)(i0 + warp) * gridDim.x + blockIdx.x] = t;
+      }
+      __syncthreads();  // sg is rewritten by the next group
     }
+  };
+  // out[i] = sum over the blocks' partials of row i, i < nk: one warp per
+  // row, lane l adding partials l, l + 32, ... in order, then a shuffle
+  // tree; the same fixed order in every block
+  auto finish = [&](const double* part, int nk, double* out) {
+    for (int i = warp; i < nk; i += kW) {
+      double t = 0.0;
+      for (int bb = lane; bb < kDotBlocks; bb += 32) t += part[(size_t)i * kDotBlocks + bb];
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) out[i] = t;
+    }
+    __syncthreads();
   };
   auto axpy = [&](const double* hh) {
     if (threadIdx.x < k) hT[threadIdx.x] = (T)hh[threadIdx.x];
@@ -174,25 +213,17 @@ __global__ void __launch_bounds__(kThreads)
     }
     __syncthreads();  // hT is rewritten by the next pass
   };
-  dots(p1);
+  dots(V, k, p1);
   grid.sync();
-  for (int i = 0; i < k; ++i) finish_row(p1, i, sh, &h[0][i]);
-  __syncthreads();
+  finish(p1, k, h[0]);
   axpy(h[0]);
-  dots(p2);
+  dots(V, k, p2);
   grid.sync();
-  for (int i = 0; i < k; ++i) finish_row(p2, i, sh, &h[1][i]);
-  __syncthreads();
+  finish(p2, k, h[1]);
   axpy(h[1]);
-  {
-    T acc = T(0);
-    for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) acc += w[e] * w[e];
-    const double t = block_sum((double)acc, sh);
-    if (threadIdx.x == 0) p3[blockIdx.x] = t;
-  }
+  dots(nullptr, 1, p3);
   grid.sync();
-  finish_row(p3, 0, sh, &nrm2);
-  __syncthreads();
+  finish(p3, 1, &nrm2);
   double s = sqrt(fmax(nrm2, 0.0));
   s = s != 0.0 ? 1.0 / s : 0.0;
   const T sT = (T)s;
