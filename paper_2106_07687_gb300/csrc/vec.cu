@@ -116,25 +116,14 @@ __global__ void gmres_start_kernel(const T* __restrict__ r, const double* nrm2, 
     v0[e] = (T)(s * (double)r[e]);
 }
 
-// Sum over the kDotBlocks partials of row i, the second stage of a dot
-// product in the order of dots_finish_kernel; the block's result in *out.
-__device__ __forceinline__ void finish_row(const double* __restrict__ partials, int i,
-                                           double* sh, double* out) {
-  double acc = 0.0;
-  for (int b = threadIdx.x; b < kDotBlocks; b += blockDim.x)
-    acc += partials[(size_t)i * kDotBlocks + b];
-  const double t = block_sum(acc, sh);
-  if (threadIdx.x == 0) *out = t;
-}
-
 // One Arnoldi step of FGMRES for the new vector w against V[0..j] (CGS with
 // one re-orthogonalisation, then normalisation and the Givens update of
 // Hessenberg column j) in one cooperative launch of kDotBlocks blocks with
 // three grid barriers.  Block b owns the chunk of elements that multidot
 // assigns to it: it updates only that chunk, so the second pass's and the
 // norm's partial sums follow its own updates without a barrier, and every
-// block finishes the sums over all partials itself in the fixed order of
-// dots_finish_kernel, so all blocks hold the same coefficients.  Products
+// block finishes the sums over all partials itself in one fixed order (one
+// warp per coefficient), so all blocks hold the same coefficients.  Products
 // and updates are taken in the vectors' precision T (a thread sums its few
 // products in T), the sums over threads and blocks in FP64: on this GPU an
 // FP64 operation per element would make the step FP64-bound.
@@ -145,7 +134,6 @@ __global__ void __launch_bounds__(kThreads)
                    double* cs, double* sn, double* g, double* resid) {
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
-  __shared__ double sh[32];
   __shared__ double h[2][64];
   __shared__ double nrm2;
   const int k = j + 1;
