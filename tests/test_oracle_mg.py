@@ -70,12 +70,12 @@ def test_level0_is_singular_with_the_obstacle():
     assert s1[-1] > 1e-8 * s1[0]
 
 
-def _rho(L, obstacle, omega=0.8):
+def _rho(L, obstacle, omega=0.8, alpha0=0.1):
     levels = mesh.hierarchy(L, obstacle=obstacle)
     lev = levels[-1]
     X, Y = lev.coords()
     vb = np.concatenate([(6 * Y * (1 - Y)).ravel(), np.zeros(2 * lev.nn)])
-    H = mg.Hierarchy(levels, vb, fem.Params(nu=0.01, dt=0.01), omega=omega)
+    H = mg.Hierarchy(levels, vb, fem.Params(nu=0.01, dt=0.01, alpha0=alpha0), omega=omega)
     A = H.ops[-1].A
     rng = np.random.default_rng(5)
     b = np.zeros(lev.ndof)
@@ -104,3 +104,13 @@ def test_vcycle_is_a_linear_map():
     lhs = mg.vcycle(H, k, 2.0 * b1 - 3.0 * b2)
     rhs = 2.0 * mg.vcycle(H, k, b1) - 3.0 * mg.vcycle(H, k, b2)
     assert np.linalg.norm(lhs - rhs) < 1e-12 * np.linalg.norm(lhs)
+
+
+@pytest.mark.parametrize("alpha0,bound", [(0.05, 0.2), (0.1, 0.2), (0.5, 0.6)])
+def test_vcycle_contraction_over_the_stabilisation_parameter(alpha0, bound):
+    """alpha_0 of Sec. 2.1 is not given by the paper (0.1 here): the
+    V(2,2) Vanka cycle contracts by at most 0.2 per cycle for alpha_0 <=
+    0.1 and degrades, without diverging, for a stabilisation five times
+    stronger (measured 0.38-0.52 at alpha_0 = 0.5)."""
+    rhos = [_rho(L, (2, 1), alpha0=alpha0) for L in (2, 3)]
+    assert max(rhos) < bound, rhos
