@@ -423,6 +423,24 @@ def run_sizes(dn, torch, stream, flush, args, common, corpus):
     return out
 
 
+def slowest_rank_ms(ms, world, device):
+    """The largest of the ranks' times (the whole job ends with its slowest
+    rank), by an all-reduce over the process group; the local time for one
+    rank."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(ms, steps, world):
+    """Whole-job time steps per second: every one of the world's ranks
+    stepped its own problem `steps` times in `ms` milliseconds."""
+    return world * steps / (ms * 1e-3)
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -527,11 +545,7 @@ def run_ours(args, rank, world):
     del corpus
     torch.cuda.empty_cache()
 
-    ms = times["dnnmg"]
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = slowest_rank_ms(times["dnnmg"], world, "cuda")
     if rank != 0:
         return None
     K = args.steps
@@ -568,7 +582,7 @@ def run_ours(args, rank, world):
         for name in runs}
     return {
         "metric": METRIC,
-        "value": world * K / (ms * 1e-3),
+        "value": job_throughput(ms, K, world),
         "unit": "time steps/s",
         "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms / K,
