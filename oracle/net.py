@@ -24,7 +24,11 @@ Readings:
 `bf16=True` rounds to bfloat16 exactly where the tensor-core path feeds a
 matrix product: weights, the input x, the hidden state multiplied by W_hh,
 the input of every layer above the first and the ReLU output.  Everything
-else stays FP64.
+else stays FP64.  In the backward pass, `bf16_grad=True` also rounds the
+gradients that feed a product: the output gradient dY, the gradient of the
+dense layer's pre-activation, and the gate gradients of every GRU layer
+(both the products with the weights and the weight and bias gradients then
+use the rounded values).
 """
 import numpy as np
 
@@ -147,12 +151,14 @@ def loss(Ypred, Y):
     return float(np.mean((Ypred - Y) ** 2))
 
 
-def sequence_backward(spec, p, X, Y, bf16=False):
+def sequence_backward(spec, p, X, Y, bf16=False, bf16_grad=False):
     """Loss and gradient (flat, FP64) by backpropagation through time.
 
     Weight gradients are taken with respect to the (rounded) weights the
-    forward pass used.
+    forward pass used.  bf16_grad: round the gradients that enter a matrix
+    product to bfloat16 (see the module docstring).
     """
+    qg = (lambda a: bf16_round(a)) if bf16_grad else (lambda a: a)
     B, T, _ = X.shape
     H = spec.hidden
     cache = []
@@ -164,11 +170,11 @@ def sequence_backward(spec, p, X, Y, bf16=False):
     dh_next = np.zeros((spec.layers, B, H))
     for t in range(T - 1, -1, -1):
         layer_cache, top, a1, y1 = cache[t]
-        dy = dY[:, t]
+        dy = qg(dY[:, t])
         g["W2"] += dy.T @ y1
         g["b2"] += dy.sum(0)
         if spec.mlp:
-            da1 = (dy @ W["W2"]) * (a1 > 0)
+            da1 = qg((dy @ W["W2"]) * (a1 > 0))
             g["W1"] += da1.T @ top
             g["b1"] += da1.sum(0)
             dinp = da1 @ W["W1"]
@@ -184,8 +190,8 @@ def sequence_backward(spec, p, X, Y, bf16=False):
             dr = dan * ghn
             dar = dr * r * (1.0 - r)
             daz = dz * z * (1.0 - z)
-            dgi = np.concatenate([dar, daz, dan], axis=1)
-            dgh = np.concatenate([dar, daz, dan * r], axis=1)
+            dgi = qg(np.concatenate([dar, daz, dan], axis=1))
+            dgh = qg(np.concatenate([dar, daz, dan * r], axis=1))
             g[f"W_ih{l}"] += dgi.T @ inp
             g[f"b_ih{l}"] += dgi.sum(0)
             g[f"W_hh{l}"] += dgh.T @ hq

@@ -126,3 +126,66 @@ def test_bf16_round_matches_torch():
                         [0.0, -0.0, 1.0, 1.00390625, 1.01171875]])
     t = torch.from_numpy(a.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
     np.testing.assert_array_equal(net.bf16_round(a), t)
+
+
+def _q_t(t):
+    """bfloat16 rounding of a float64 tensor through float32 (the oracle's path)."""
+    return t.float().to(torch.bfloat16).double()
+
+
+def _ste(t):
+    """bfloat16-rounded value whose gradient passes through unchanged."""
+    return t + (_q_t(t) - t).detach()
+
+
+def test_bf16_gradient_rounding_matches_autograd_with_hooks():
+    """bf16_grad=True against PyTorch autograd on a GRU built cell by cell:
+    the forward uses rounded weights and rounded product inputs (straight-
+    through, as the oracle's forward), and backward hooks round the gradients
+    of the output, of the dense pre-activation and of both gate
+    pre-activation vectors of every layer.  Autograd supplies the chain rule,
+    so a rounding point put at the wrong place, dropped, or a term that
+    skips the rounded value, shows up here."""
+    spec = net.NetSpec(c_in=12, hidden=8, layers=2, mlp=10, c_out=6)
+    rng = np.random.default_rng(7)
+    w = rng.uniform(-0.5, 0.5, spec.num_params())
+    B, T = 5, 4
+    X = net.bf16_round(rng.standard_normal((B, T, spec.c_in)))
+    Y = rng.standard_normal((B, T, spec.c_out))
+    L, g = net.sequence_backward(spec, spec.unflatten(w), X, Y, bf16=True, bf16_grad=True)
+    _, g_plain = net.sequence_backward(spec, spec.unflatten(w), X, Y, bf16=True)
+    p = spec.unflatten(w)
+    H = spec.hidden
+    tp = {}
+    for k, v in p.items():
+        t = torch.from_numpy(net.bf16_round(v) if k.startswith("W") else v.copy())
+        tp[k] = t.requires_grad_(True)
+    hook = lambda gr: _q_t(gr)
+    h = [torch.zeros(B, H, dtype=torch.float64) for _ in range(spec.layers)]
+    Xt = torch.from_numpy(X)
+    outs = []
+    for t in range(T):
+        inp = Xt[:, t]
+        for l in range(spec.layers):
+            gi = inp @ tp[f"W_ih{l}"].T + tp[f"b_ih{l}"]
+            gh = _ste(h[l]) @ tp[f"W_hh{l}"].T + tp[f"b_hh{l}"]
+            gi.register_hook(hook)
+            gh.register_hook(hook)
+            r = torch.sigmoid(gi[:, :H] + gh[:, :H])
+            z = torch.sigmoid(gi[:, H:2 * H] + gh[:, H:2 * H])
+            n = torch.tanh(gi[:, 2 * H:] + r * gh[:, 2 * H:])
+            h[l] = (1 - z) * n + z * h[l]
+            inp = _ste(h[l])
+        a1 = inp @ tp["W1"].T + tp["b1"]
+        a1.register_hook(hook)
+        y = _ste(torch.relu(a1)) @ tp["W2"].T + tp["b2"]
+        y.register_hook(hook)
+        outs.append(y)
+    Lt = torch.mean((torch.stack(outs, 1) - torch.from_numpy(Y)) ** 2)
+    Lt.backward()
+    gt = torch.cat([tp[k].grad.reshape(-1) for k in spec.param_names()]).numpy()
+    assert abs(L - Lt.item()) < 1e-13
+    np.testing.assert_allclose(g, gt, rtol=1e-9, atol=1e-13)
+    # the rounding is a real, bounded perturbation of the unrounded gradient
+    d = np.linalg.norm(g - g_plain) / np.linalg.norm(g_plain)
+    assert 1e-5 < d < 2e-2, d
