@@ -359,7 +359,7 @@ int dnnmg_gather_batch(dnnmg_ctx* ctx, const float* X, const float* Y, const int
  * external memory manager owning the whole device heap, or inside a
  * real-time loop where an allocation and the synchronisation it may cause
  * are not allowed - and therefore cannot create a context.  It assembles the
- * Jacobian A'(vbar) (Eq. 6, with LPS) of level cfg->level_coarse, factors it
+ * linearised operator A'(vbar) of level cfg->level_coarse, factors it
  * by banded LU with partial pivoting and returns x = A'(vbar)^{-1} b: the
  * same operator the coarse level of dnnmg_vcycle() inverts.
  *   cfg  : host pointer; uses nu, dt, theta (must be 1), alpha0, obstacle_i0,
@@ -374,8 +374,9 @@ int dnnmg_gather_batch(dnnmg_ctx* ctx, const float* X, const float* Y, const int
  * device current); make that first call before any stream capture.  All
  * calls share the array and it keeps the last call's contents, so calls that
  * overlap on the GPU (other streams, other threads) race: serialise them.
- * Errors: DNNMG_ERR_ARG, DNNMG_ERR_CUDA, DNNMG_ERR_NUMERICAL (singular
- * matrix); the message is read with dnnmg_last_error(NULL). */
+ * Errors: DNNMG_ERR_ARG, DNNMG_ERR_CUDA (also when a CUDA error of earlier
+ * work was already pending on entry: it is left pending), DNNMG_ERR_NUMERICAL
+ * (singular matrix); the message is read with dnnmg_last_error(NULL). */
 int dnnmg_coarse_solve_noalloc(const dnnmg_config* cfg, const double* vbar, const double* b,
                                double* x, void* stream);
 

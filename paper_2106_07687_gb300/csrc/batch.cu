@@ -2,7 +2,7 @@
 // obstacle, viscosity, time step and finest level each) advanced by the same
 // time-step algorithm as a single context -- Newton's method (Eq. 6) with
 // right-preconditioned FGMRES and a multigrid V-cycle (Sec. 2.2), and for
-// DNN-MG steps the network correction of the network correction of Algorithm 1 -- with every
+// DNN-MG steps the network correction of Algorithm 1 -- with every
 // stage of every problem issued as one launch for the whole batch.
 //
 // Lock-step control: all problems run Newton and FGMRES iterations together;

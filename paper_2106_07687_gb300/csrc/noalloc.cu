@@ -80,7 +80,7 @@ extern "C" int dnnmg_coarse_solve_noalloc(const dnnmg_config* cfg, const double*
   }
   const int ell = cfg->level_coarse;
   if (ell < 1 || ell > 9) {
-    set_thread_error("dnnmg_coarse_solve_noalloc: level_coarse must be >= 1");
+    set_thread_error("dnnmg_coarse_solve_noalloc: level_coarse must be in 1..9");
     return DNNMG_ERR_ARG;
   }
   Grid g{};
@@ -99,6 +99,12 @@ extern "C" int dnnmg_coarse_solve_noalloc(const dnnmg_config* cfg, const double*
     set_thread_error("dnnmg_coarse_solve_noalloc: the coarse level needs more than the 2 MiB "
                      "of static scratch (only level 1 fits)");
     return DNNMG_ERR_ARG;
+  }
+  // an error left pending by earlier, unrelated work of this thread is not
+  // ours to report or to clear: refuse to run on top of it
+  if (cudaPeekAtLastError() != cudaSuccess) {
+    set_thread_error("dnnmg_coarse_solve_noalloc: a CUDA error was pending before the call");
+    return DNNMG_ERR_CUDA;
   }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -128,21 +134,30 @@ extern "C" int dnnmg_coarse_solve_noalloc(const dnnmg_config* cfg, const double*
   int* status = reinterpret_cast<int*>(flags + flags_b);
   g.solid = solid;
   g.flags = flags;
+  auto fail = [](const char* what) {
+    set_thread_error(what);
+    return DNNMG_ERR_CUDA;
+  };
   // the status word keeps the previous call's value: clear it
-  cudaMemsetAsync(status, 0, sizeof(int), st);
+  if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess)
+    return fail("dnnmg_coarse_solve_noalloc: clearing the status word failed");
   note_launch();
   level_masks_kernel<<<cdiv(g.nn, 256), 256, 0, st>>>(ell, cfg->obstacle_i0, cfg->obstacle_j0,
                                                      g.nx, g.ny, solid, flags);
+  if (cudaGetLastError() != cudaSuccess)
+    return fail("dnnmg_coarse_solve_noalloc: launch of the mask kernel failed");
   const Sten<double> s = make_sten<double>(g.h, *cfg);
   launch_coarse_lu(g, s, vbar, band, piv, status, st);
+  if (cudaGetLastError() != cudaSuccess)
+    return fail("dnnmg_coarse_solve_noalloc: launch of the coarse LU failed");
   launch_coarse_lu_solve(g, band, piv, b, x, st);
+  if (cudaGetLastError() != cudaSuccess)
+    return fail("dnnmg_coarse_solve_noalloc: launch of the coarse solve failed");
   int h_status = 0;
-  const cudaError_t e = cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st);
-  if (e != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess ||
-      cudaGetLastError() != cudaSuccess) {
-    set_thread_error("dnnmg_coarse_solve_noalloc: CUDA error");
-    return DNNMG_ERR_CUDA;
-  }
+  if (cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return fail("dnnmg_coarse_solve_noalloc: reading the status word failed");
+  if (cudaStreamSynchronize(st) != cudaSuccess)
+    return fail("dnnmg_coarse_solve_noalloc: the solve failed on the device");
   if (h_status) {
     set_thread_error("dnnmg_coarse_solve_noalloc: singular coarse-level matrix");
     return DNNMG_ERR_NUMERICAL;

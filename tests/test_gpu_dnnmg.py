@@ -83,6 +83,38 @@ def test_fallback_drops_the_network_rhs():
     assert rel(a.get_state().cpu().numpy(), b.get_state().cpu().numpy()) < 1e-10
 
 
+def test_forced_fallback_matches_oracle():
+    """The switch-off of Sec. 3.3 forced on every step that has a network
+    right-hand side (threshold 0 Newton iterations): the GPU and the oracle
+    (time_step with fallback_its=0) both redo those steps with the plain
+    right-hand side, so states, corrected fine velocities and the fallback
+    flags agree, while the network still runs after each step."""
+    dn = lib()
+    ob = synthetic.obstacle_block(1000)
+    ctx = _ctx(dn, ob, fallback_newton_its=0)
+    spec = net.NetSpec()
+    w = synthetic.random_weights(3, spec.num_params(), 0.2).astype(np.float32)
+    ctx.set_weights(w)
+    levels = mesh.hierarchy(L, obstacle=ob)
+    fine = mesh.Level(L + 1, obstacle=ob)
+    opt = newton.SolverOptions(newton_tol=1e-12)
+    prm = fem.Params(nu=NU, dt=DT)
+    params = spec.unflatten(w.astype(np.float64))
+    zero, one = np.zeros(40), np.ones(40)
+    x = mesh.initial_state(levels[-1])
+    state = dict(bL=None, vcorr=None, h=np.zeros((2, len(levels[-1].fluid_cells), 64)))
+    flags = []
+    for n in range(3):
+        st = ctx.step(dn.NET)
+        x, state, info = dnnmg.time_step(levels, fine, x, state, spec, params, prm, opt,
+                                         zero, one, fallback_its=0)
+        assert st["fallback"] == int(info["fallback"]), (n, st, info["fallback"])
+        flags.append(st["fallback"])
+        assert rel(ctx.get_state().cpu().numpy(), x) < 1e-4, n
+        assert rel(ctx.get_fine_velocity().cpu().numpy(), state["vcorr"][:2 * fine.nn]) < 1e-4, n
+    assert flags == [0, 1, 1]
+
+
 def test_two_replaced_levels_dnnmg_steps_match_oracle():
     """The network replaces levels L+1 and L+2 (5x5-node patches, 104
     inputs, 50 outputs): P and R act twice, the fine residual and the

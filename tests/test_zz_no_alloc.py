@@ -29,12 +29,15 @@ def _entry(dn):
     return f
 
 
-def test_noalloc_coarse_solve_matches_context_vcycle():
+@pytest.mark.parametrize("with_obstacle", [True, False])
+def test_noalloc_coarse_solve_matches_context_vcycle(with_obstacle):
     dn = lib()
     f = _entry(dn)
-    obstacle = synthetic.obstacle_block(1000)
-    cfg = dn.default_config(level_solve=1, precision=dn.FP64, obstacle_i0=obstacle[0],
-                            obstacle_j0=obstacle[1], nu=0.006, dt=0.01)
+    # without an obstacle the device-side masks take their other branch
+    obstacle = synthetic.obstacle_block(1000) if with_obstacle else None
+    oi, oj = obstacle if obstacle else (-1, -1)
+    cfg = dn.default_config(level_solve=1, precision=dn.FP64, obstacle_i0=oi, obstacle_j0=oj,
+                            nu=0.006, dt=0.01)
     ctx = dn.Context(cfg)
     lev = mesh.Level(1, obstacle=obstacle)
     stream = torch.cuda.current_stream()
