@@ -1,22 +1,30 @@
 """Benchmark of the DNN-MG hot path on one GB300 (or N independent replicas).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--mode step|vcycle]
+                    [--mode step|vcycle|net|coarse|periodic]
 
 Workload (the DNN-MG configuration): multigrid solve on the 512x128 channel
 (level 5, 198,531 DOFs) and the patch network on the 1024x256 level
 (61,440 patches, 2-layer GRU with hidden size 64 + MLP 128, BF16 with FP32
 accumulation); held-out viscosity nu = 0.0065, dt = 0.005, mixed FP32/FP64
 solver, obstacle seeded.  Before the timed region the network is trained by
-the library's own kernels on a bounded corpus from plain fine trajectories
-(nu = 0.005 and 0.008).  Timed: K DNN-MG steps, and for comparison K plain
-MG(L) steps, K plain MG(L+1) steps (the reference) and K MG(L+1) steps at a
-loose tolerance, each from the impulsive start, L2 flushed before each step.
-`value` = DNN-MG time steps per second over all ranks.  One JSON line is
-printed by rank 0.  --impl reference times the FP64 CPU oracle (DNN-MG step)
-on the host cores on a bounded sample of the same workload.
+the library's own kernels (10-step windows) on the device corpus of 32 plain
+fine trajectories (seeded obstacle, nu uniform in [0.004, 0.01]).  All
+methods start from the same developed flow at t ~ 1 s (level-5 spin-up),
+then W untimed and K timed steps: DNN-MG, plain MG(L), plain FP64 MG(L+1)
+(the reference of the errors) and plain mixed-precision MG(L+1) at a sweep of
+Newton / FGMRES tolerances, each step timed alone with L2 flushed before it;
+the equal-error block reads off MG(L+1)'s time per step at DNN-MG's velocity
+error.  `value` = DNN-MG time steps per second over all ranks.  Also: the
+plain FP64 128x32 workload beside the oracle, the plain mixed 1024x256
+workload with its per-step error against an FP64 run, held-out trajectories,
+the batched, large and network-size workloads.  One JSON line is printed by
+rank 0.  --impl reference times the FP64 CPU oracle (DNN-MG step of the same
+workload) on the host cores.
 """
 import argparse
+import hashlib
+import glob
 import json
 import os
 import subprocess
@@ -29,21 +37,38 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time/step & V-cycle DOF/s: DNN-MG vs plain MG on 1 GB300 at equal L2 err; %HBM/TC peak"
 L, NU, DT = 5, 0.0065, 0.005
-NU_TRAIN = (0.005, 0.008)
-CORPUS_STEPS, TRAIN_ITERS, TRAIN_B, TRAIN_T = 24, 150, 16384, 10
+NU_RANGE = (0.004, 0.01)                 # viscosities of the corpus and held-out trajectories
+CORPUS_SEEDS = tuple(range(2000, 2032))  # 32 plain fine trajectories
+HELDOUT_SEEDS = tuple(range(2032, 2036))
+SPIN_STEPS, SPIN_DT, RELAX_STEPS = 50, 0.02, 4  # level-L spin-up to t = 1 s, fine relaxation
+CORPUS_T, TRAIN_ITERS, TRAIN_B, TRAIN_T = 16, 400, 16384, 10
 LARGE_CORPUS_STEPS, LARGE_TRAIN_ITERS = 16, 100  # two replaced levels
+# plain MG(L+1) tolerance sweep: (Newton tolerance, FGMRES relative tolerance,
+# Newton cap, FGMRES cap); the last point is one Newton step with one V-cycle
+SWEEP = ((1e-10, 1e-4, 20, 200), (1e-8, 1e-3, 20, 200), (1e-6, 1e-2, 20, 200),
+         (1e-5, 1e-1, 20, 200), (1e-4, 0.3, 20, 200), (1e-3, 0.5, 20, 200), (0.0, 0.5, 1, 1))
 WORKLOAD = ("DNN-MG time step: multigrid on the 512x128 channel (level 5, 198,531 DOFs) + patch "
             "network on 1024x256 (level 6, 61,440 patches, GRU 2x64 + MLP 128, BF16), nu=0.0065, "
-            "dt=0.005, mixed FP32/FP64")
-ORACLE_L = 4              # bounded CPU sample: oracle DNN-MG step with L = 4, scaled by DOFs
-# DRAM bytes (read + write) per launch from one ncu capture of the kernel
-# as it stands, per V-cycle plan (profiles/vcycle_subcycle_level5.md for the
-# level 4..1 sub-cycle, profiles/vcycle_level5_split5.md for the whole
-# level-5 cycle); a kernel change makes the entries stale and they must then
-# be removed.
-NCU_TRAFFIC = {"vcycle_kernel<float>@split4": 19728128 + 7680,
-               "vcycle_kernel<float>@split5": 59351040 + 1429504}
+            "dt=0.005, mixed FP32/FP64, developed flow (t ~ 1 s)")
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
+# capture, keyed by the hash of the library sources it was taken on; after
+# any source change the figure no longer describes the kernel and is not
+# reported (traffic = null) until a new capture is entered here.
+NCU_TRAFFIC = {}
 L2_BYTES = 129 * 2 ** 20
+
+
+def source_hash():
+    """First 16 hex digits of the SHA-256 of the library's CUDA/C++ sources
+    and headers (sorted by name): the build a traffic capture belongs to."""
+    h = hashlib.sha256()
+    pats = ("paper_2106_07687_gb300/csrc/*.cu", "paper_2106_07687_gb300/csrc/*.cuh",
+            "paper_2106_07687_gb300/csrc/*.h", "include/*.h")
+    for f in sorted(x for pat in pats for x in glob.glob(os.path.join(ROOT, pat))):
+        h.update(os.path.relpath(f, ROOT).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def ndof(level):
@@ -75,19 +100,16 @@ def vcycle_bytes(top, coarsest=1, sweeps=4):
     return total + 8 * nd * nd + 8 * nd
 
 
-def oracle_dnnmg_seconds(level, steps=1, warm=1):
-    """FP64 oracle DNN-MG steps (level-L solve + fine residual, features,
-    network, scatter, Rhs, restriction) in a fresh single-threaded process."""
-    code = f"""
-import time, sys
+_ORACLE_STEP = """
+import json, sys, time
 import numpy as np
-sys.path.insert(0, {ROOT!r})
+sys.path.insert(0, {root!r})
 import synthetic
 from oracle import dnnmg, fem, mesh, net, newton
 ob = synthetic.obstacle_block(1000)
 levels = mesh.hierarchy({level}, obstacle=ob)
 fine = mesh.Level({level} + 1, obstacle=ob)
-prm = fem.Params(nu={NU}, dt={DT})
+prm = fem.Params(nu={nu}, dt={dt})
 opt = newton.SolverOptions()
 spec = net.NetSpec()
 params = spec.unflatten(synthetic.random_weights(1, spec.num_params(), 0.02))
@@ -95,25 +117,48 @@ x = mesh.initial_state(levels[-1])
 state = dict(bL=None, vcorr=None, h=np.zeros((2, len(levels[-1].fluid_cells), 64)))
 for _ in range({warm}):
     x, state, _ = dnnmg.time_step(levels, fine, x, state, spec, params, prm, opt)
-t = time.perf_counter()
-for _ in range({steps}):
+times = []
+t_end = time.perf_counter() + {budget}
+for k in range({steps}):
+    t = time.perf_counter()
     x, state, _ = dnnmg.time_step(levels, fine, x, state, spec, params, prm, opt)
-print((time.perf_counter() - t) / {steps})
+    times.append(time.perf_counter() - t)
+    if time.perf_counter() > t_end:
+        break
+print(json.dumps(times))
 """
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+
+
+def oracle_dnnmg_steps(level, steps=1, warm=0, threads=1, budget=1e9):
+    """Seconds per FP64 oracle DNN-MG step (level-L solve + fine residual,
+    features, network, scatter, Rhs, restriction), consecutive steps from
+    the impulsive start in a fresh process with `threads` BLAS/OpenMP
+    threads; stops after `budget` seconds of timed steps (at least one)."""
+    code = _ORACLE_STEP.format(root=ROOT, level=level, nu=NU, dt=DT, warm=warm, steps=steps,
+                               budget=budget)
+    n = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=n, OPENBLAS_NUM_THREADS=n, MKL_NUM_THREADS=n)
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
                          check=True)
-    return float(out.stdout.strip().splitlines()[-1])
+    return json.loads(out.stdout.strip().splitlines()[-1])
 
 
-def cpu_baseline(steps=1):
-    s = oracle_dnnmg_seconds(ORACLE_L, steps=steps)
-    scale = ndof(L) / ndof(ORACLE_L)
-    return {"value": 1.0 / (s * scale), "unit": "time steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"{steps} DNN-MG time step(s) of the FP64 oracle with the solve on the "
-                      f"256x64 channel (level {ORACLE_L}) and the network on 512x128, after one "
-                      f"warm-up step, {s:.2f} s/step, scaled by the level-L DOF ratio "
-                      f"{scale:.3f} to the benchmarked level {L}; single-threaded"}
+def cpu_baseline():
+    """One oracle DNN-MG step of the benchmarked workload (solve on level 5,
+    network on level 6), the first step from the impulsive start, timed
+    single-threaded and with every host core."""
+    cores = os.cpu_count() or 1
+    one = oracle_dnnmg_steps(L, threads=1)[0]
+    allc = oracle_dnnmg_steps(L, threads=cores)[0]
+    best = min(one, allc)
+    return {"value": 1.0 / best, "unit": "time steps/s", "cores": cores if allc <= one else 1,
+            "kind": "oracle",
+            "single_thread": {"value": 1.0 / one, "s_per_step": one},
+            "all_cores": {"value": 1.0 / allc, "s_per_step": allc, "threads": cores},
+            "sample": f"the first DNN-MG time step of the FP64 oracle from the impulsive start on "
+                      f"the benchmarked workload (solve on 512x128, level {L}; network on "
+                      f"1024x256): {one:.1f} s single-threaded, {allc:.1f} s with {cores} "
+                      f"BLAS/OpenMP threads; value = the faster"}
 
 
 class ClockSampler:
@@ -178,10 +223,11 @@ def net_flops(c_in=40, H=64, mlp=128, c_out=18):
     return 2 * fwd, 2 * (fwd + act + fwd)
 
 
-def build_corpus(dn, torch, common, level, replaced, nus_train, corpus_steps):
+def rest_corpus(dn, torch, common, level, replaced, nus_train, corpus_steps):
     """Training samples from plain trajectories on level `level + replaced`
-    (one per viscosity in nus_train, `corpus_steps` steps each), made by the
-    library's kernels.  Returns (X, Y) stacked over steps."""
+    started from rest (one per viscosity in nus_train, `corpus_steps` steps
+    each), made by the library's kernels.  Returns (X, Y) stacked over
+    steps."""
     Xs, Ys = [], []
     for v in nus_train:
         fctx = dn.Context(level_solve=level + replaced, nu=v, **common)
@@ -197,6 +243,39 @@ def build_corpus(dn, torch, common, level, replaced, nus_train, corpus_steps):
         fctx.close()
         sctx.close()
     return torch.cat(Xs).contiguous(), torch.cat(Ys).contiguous()
+
+
+def device_corpus(dn, torch, precision):
+    """The corpus of Sec. 3.1 at the configured scale: 32 plain trajectories
+    (seeds CORPUS_SEEDS: seeded obstacle, nu uniform in NU_RANGE), each spun
+    up on level L to t = 1 s, relaxed on level L+1 and sampled over CORPUS_T
+    fine steps by dnnmg_make_corpus.  Trajectories are grouped by obstacle
+    position (one context per position).  Returns (X [32*T*P, 40],
+    Y [32*T*P, 18], seconds)."""
+    import synthetic
+    groups = {}
+    for sd in CORPUS_SEEDS:
+        groups.setdefault(synthetic.obstacle_block(sd), []).append(
+            synthetic.viscosity(sd, *NU_RANGE))
+    n = len(CORPUS_SEEDS)
+    P = None
+    X = Y = None
+    k = 0
+    t0 = time.perf_counter()
+    for ob, nus in sorted(groups.items()):
+        ctx = dn.Context(level_solve=L, replaced_levels=1, precision=precision, nu=NU, dt=DT,
+                         obstacle_i0=ob[0], obstacle_j0=ob[1])
+        if X is None:
+            P = ctx.num_patches()
+            ci, co = ctx.net_dims()
+            X = torch.empty(n, CORPUS_T, P, ci, dtype=torch.float32, device="cuda")
+            Y = torch.empty(n, CORPUS_T, P, co, dtype=torch.float32, device="cuda")
+        ctx.make_corpus(nus, SPIN_STEPS, SPIN_DT, RELAX_STEPS, CORPUS_T, X[k:k + len(nus)],
+                        Y[k:k + len(nus)])
+        k += len(nus)
+        ctx.close()
+    torch.cuda.synchronize()
+    return X.view(n * CORPUS_T * P, -1), Y.view(n * CORPUS_T * P, -1), time.perf_counter() - t0
 
 
 def train_on(dn, torch, stream, common, level, replaced, nu, corpus, n_traj, corpus_steps, iters,
@@ -237,18 +316,18 @@ def train_on(dn, torch, stream, common, level, replaced, nu, corpus, n_traj, cor
     return net_ctx, feat_mean, feat_std, losses, train_ms
 
 
-def train_network(dn, torch, stream, common, level, replaced, nu, nus_train, corpus_steps, iters,
-                  keep_corpus=False):
-    """Corpus (build_corpus) and the default network trained on it
-    (train_on); with keep_corpus the corpus is returned as well."""
-    corpus = build_corpus(dn, torch, common, level, replaced, nus_train, corpus_steps)
-    out = train_on(dn, torch, stream, common, level, replaced, nu, corpus, len(nus_train),
-                   corpus_steps, iters)
-    if keep_corpus:
-        return out + (corpus,)
-    del corpus
-    torch.cuda.empty_cache()
-    return out
+def spun_up_state(dn, nu, ob, precision):
+    """The developed flow the timed steps start from: SPIN_STEPS plain
+    level-L steps from rest with time step SPIN_DT (t = 1 s), then P to level
+    L+1.  Returns (level-L state, level-L+1 state) as device FP64 vectors."""
+    c = dn.Context(level_solve=L, replaced_levels=1, nu=nu, dt=SPIN_DT, precision=precision,
+                   obstacle_i0=ob[0], obstacle_j0=ob[1])
+    for _ in range(SPIN_STEPS):
+        c.step(dn.PLAIN)
+    x5 = c.get_state().clone()
+    x6 = c.prolongate(L, x5).clone()
+    c.close()
+    return x5, x6
 
 
 def time_infer(ctx, torch, stream, P, c_in, c_out, layers, hidden, reps=20):
@@ -351,9 +430,13 @@ def run_large(dn, torch, stream, flush, args, common):
     errors, functionals and force drift of each against the reference."""
     lev, rep, nu, dt = 5, 2, 0.002, 0.002
     com = dict(common, dt=dt)
-    net_ctx, _, _, losses, train_ms = train_network(
-        dn, torch, stream, com, lev, rep, nu, (0.0016, 0.0025), LARGE_CORPUS_STEPS,
-        LARGE_TRAIN_ITERS)
+    nus_train = (0.0016, 0.0025)
+    corpus = rest_corpus(dn, torch, com, lev, rep, nus_train, LARGE_CORPUS_STEPS)
+    net_ctx, _, _, losses, train_ms = train_on(dn, torch, stream, com, lev, rep, nu, corpus,
+                                               len(nus_train), LARGE_CORPUS_STEPS,
+                                               LARGE_TRAIN_ITERS)
+    del corpus
+    torch.cuda.empty_cache()
     ref = dn.Context(level_solve=lev + rep, nu=nu, **dict(com, precision=dn.FP64))
     coarse = dn.Context(level_solve=lev, nu=nu, **com)
     runs = {"dnnmg": (net_ctx, dn.NET), "mg_L": (coarse, dn.PLAIN), "mg_L+2": (ref, dn.PLAIN)}
@@ -382,22 +465,26 @@ def run_large(dn, torch, stream, flush, args, common):
 TABLE1_SIZES = [(32, 1), (64, 1), (32, 2), (64, 2), (32, 3), (64, 3)]
 
 
-def run_sizes(dn, torch, stream, flush, args, common, corpus):
+def run_sizes(dn, torch, stream, flush, args, common, corpus, start):
     """The network sizes of Table 1 (m x n: GRU hidden size m, n stacked
     cells) on the default DNN-MG workload.  Each is trained on the same
     corpus with the same batches and schedule; reported: parameters,
     training time per Adam step (and its factor against 32 x 1, the columns
     of Table 1), forward time over all patches, the last training loss, and
-    K DNN-MG steps from the impulsive start against plain MG on the finer
-    level (time per step, velocity and pressure errors, force drift)."""
+    K DNN-MG steps from the developed flow `start` = (level-L state,
+    level-L+1 state) against plain mixed-precision MG on the finer level
+    (time per step, velocity and pressure errors, force drift)."""
     out = []
     base = None
+    x5, x6 = start
     for m, n in TABLE1_SIZES:
         ctx, _, _, losses, train_ms = train_on(
-            dn, torch, stream, common, L, 1, NU, corpus, len(NU_TRAIN), CORPUS_STEPS, TRAIN_ITERS,
-            hidden=m, gru_layers=n)
+            dn, torch, stream, common, L, 1, NU, corpus, len(CORPUS_SEEDS), CORPUS_T,
+            TRAIN_ITERS, hidden=m, gru_layers=n)
         infer_ms = time_infer(ctx, torch, stream, ctx.num_patches(), 40, 18, n, m)
         ref = dn.Context(level_solve=L + 1, nu=NU, **common)
+        ctx.set_state(x5)
+        ref.set_state(x6)
         runs = {"dnnmg": (ctx, dn.NET), "mg_L+1": (ref, dn.PLAIN)}
         for c, mode in runs.values():
             for _ in range(max(1, args.warmup)):
@@ -441,6 +528,204 @@ def job_throughput(ms, steps, world):
     return world * steps / (ms * 1e-3)
 
 
+def equal_error(times, summary, K, names, target="dnnmg"):
+    """MG(L+1)'s time per step at the target method's mean velocity error:
+    the sweep points (mean velocity error, ms per step) sorted by error, and
+    log(time) interpolated linearly in log(error) between the two points
+    that bracket the target's error.  When every point is more accurate
+    than the target, the loosest point's time is an upper bound of MG(L+1)'s
+    time at equal error (bracketed = false)."""
+    import math
+    e_t = summary[target]["vel_l2_err_mean"]
+    pts = sorted((summary[n]["vel_l2_err_mean"], times[n] / K, n) for n in names)
+    out = {"target": target, "target_vel_l2_err_mean": e_t,
+           "target_ms_per_step": times[target] / K,
+           "sweep": [{"run": n, "vel_l2_err_mean": e, "ms_per_step": t} for e, t, n in pts]}
+    lo = [p for p in pts if p[0] <= e_t]
+    hi = [p for p in pts if p[0] > e_t]
+    if lo and hi:
+        (e0, t0, n0), (e1, t1, n1) = lo[-1], hi[0]
+        w = (math.log(e_t) - math.log(max(e0, 1e-300))) / (math.log(e1) - math.log(max(e0, 1e-300)))
+        t_eq = math.exp(math.log(t0) + w * (math.log(t1) - math.log(t0)))
+        out.update(bracketed=True, between=[n0, n1], mg_fine_ms_at_equal_error=t_eq)
+    elif lo:
+        e0, t0, n0 = lo[-1]
+        out.update(bracketed=False, between=[n0, None], mg_fine_ms_at_equal_error=t0,
+                   note="every MG(L+1) point is more accurate than the target; the loosest "
+                        "point's time bounds MG(L+1)'s time at equal error from above")
+    else:
+        out.update(bracketed=False, between=[None, pts[0][2]], mg_fine_ms_at_equal_error=None,
+                   note="the target is more accurate than every MG(L+1) point")
+    t_eq = out["mg_fine_ms_at_equal_error"]
+    out["speedup_vs_mg_fine"] = t_eq / out["target_ms_per_step"] if t_eq else None
+    return out
+
+
+def start_runs(runs, x5, x6, fine_names, warmup):
+    """Every run starts from the developed flow (level-L runs from x5, the
+    others from x6), then `warmup` untimed steps."""
+    for name, (c, mode) in runs.items():
+        c.set_state(x6 if name in fine_names else x5)
+    for name, (c, mode) in runs.items():
+        for _ in range(warmup):
+            c.step(mode)
+
+
+def run_heldout(dn, torch, stream, flush, args, weights, feat_mean, feat_std):
+    """Learning gain on held-out trajectories (seeds HELDOUT_SEEDS: own
+    obstacle and viscosity, not in the corpus): from each developed flow,
+    DNN-MG with the trained network and plain MG(L) against plain FP64
+    MG(L+1), mean velocity and pressure errors over the steps."""
+    import synthetic
+    out = []
+    K = max(2, min(args.steps, 10))
+    for sd in HELDOUT_SEEDS:
+        nu, ob = synthetic.viscosity(sd, *NU_RANGE), synthetic.obstacle_block(sd)
+        com = dict(precision=dn.MIXED, dt=DT, obstacle_i0=ob[0], obstacle_j0=ob[1])
+        x5, x6 = spun_up_state(dn, nu, ob, dn.MIXED)
+        d = dn.Context(level_solve=L, replaced_levels=1, nu=nu, **com)
+        d.set_weights(weights)
+        d.set_feature_stats(feat_mean, feat_std)
+        c = dn.Context(level_solve=L, nu=nu, **com)
+        r = dn.Context(level_solve=L + 1, nu=nu, **dict(com, precision=dn.FP64))
+        runs = {"dnnmg": (d, dn.NET), "mg_L": (c, dn.PLAIN), "mg_L+1_fp64": (r, dn.PLAIN)}
+        start_runs(runs, x5, x6, ("mg_L+1_fp64",), max(1, args.warmup))
+        _, series, stats, _ = compare_runs(runs, "mg_L+1_fp64", r, L, 1, stream, flush, torch, K,
+                                           dn.kernel_launches)
+        sm = summarize_series(series, "mg_L+1_fp64")
+        out.append({"seed": sd, "nu": nu, "obstacle_block": list(ob), "steps": K,
+                    "dnnmg_vel_err": sm["dnnmg"]["vel_l2_err_mean"],
+                    "mg_L_vel_err": sm["mg_L"]["vel_l2_err_mean"],
+                    "dnnmg_p_err": sm["dnnmg"]["p_l2_err_mean"],
+                    "mg_L_p_err": sm["mg_L"]["p_l2_err_mean"],
+                    "gain": sm["mg_L"]["vel_l2_err_mean"] / sm["dnnmg"]["vel_l2_err_mean"],
+                    "fallbacks": sum(s["fallback"] for s in stats["dnnmg"])})
+        for ctx in (d, c, r):
+            ctx.close()
+        torch.cuda.empty_cache()
+    return {"trajectories": out,
+            "mean_gain": sum(t["gain"] for t in out) / len(out),
+            "setup": f"seeds {HELDOUT_SEEDS[0]}-{HELDOUT_SEEDS[-1]} (nu uniform in {NU_RANGE}, "
+                     f"seeded obstacle), developed flow, {K} steps after "
+                     f"{max(1, args.warmup)} warm-up steps; errors against plain FP64 MG(L+1)"}
+
+
+def run_plain_fine(dn, torch, stream, flush, rank, steps=200):
+    """The plain mixed-precision workload: the 1024x256 channel (level 6),
+    nu = 0.005, dt = 0.005, seeded obstacle, `steps` steps from the impulsive
+    start, with the velocity l2 error of every step against the FP64 build
+    of the same solver stepping beside it (whose own parity with the oracle
+    is 1e-10 in the tests)."""
+    import synthetic
+    ob = synthetic.obstacle_block(1000 + rank)
+    com = dict(level_solve=6, nu=0.005, dt=0.005, obstacle_i0=ob[0], obstacle_j0=ob[1])
+    mx = dn.Context(precision=dn.MIXED, **com)
+    fp = dn.Context(precision=dn.FP64, **com)
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    t_mx = t_fp = 0.0
+    err, pe, its = [], [], []
+    for _ in range(steps):
+        for c, acc in ((mx, 0), (fp, 1)):
+            flush.zero_()
+            ev[0].record(stream)
+            st = c.step(dn.PLAIN)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            if acc == 0:
+                t_mx += ev[0].elapsed_time(ev[1])
+                its.append((st["newton_its"], st["gmres_its"]))
+            else:
+                t_fp += ev[0].elapsed_time(ev[1])
+        ve, p_e = fp.relative_errors(6, mx.get_state(), fp.get_state())
+        err.append(ve)
+        pe.append(p_e)
+    out = {"workload": "plain MG, 1024x256 channel (level 6, 790,275 DOFs), nu=0.005, dt=0.005, "
+                       "seeded obstacle, from the impulsive start; FP32 V-cycle in FP64 Newton",
+           "steps": steps, "ms_per_step_mixed": t_mx / steps, "ms_per_step_fp64": t_fp / steps,
+           "steps_per_s_mixed": steps / (t_mx * 1e-3),
+           "newton_its_mean": sum(a for a, _ in its) / steps,
+           "gmres_its_mean": sum(b for _, b in its) / steps,
+           "vel_l2_err_vs_fp64": {"max": max(err), "mean": sum(err) / steps, "last": err[-1],
+                                  "every_20th": err[19::20]},
+           "p_l2_err_vs_fp64": {"max": max(pe), "mean": sum(pe) / steps},
+           "error_reference": "the FP64 build of the same solver (oracle parity 1e-10 in "
+                              "tests/test_gpu_solver.py); the CPU oracle would take minutes "
+                              "per step at this size"}
+    mx.close()
+    fp.close()
+    return out
+
+
+def run_plain_small(dn, torch, stream, rank, steps=20):
+    """The plain FP64 workload: the 128x32 channel (level 3), nu = 0.01,
+    dt = 0.01, seeded obstacle, Newton tolerance 1e-10, `steps` steps from
+    the impulsive start.  Returns the block and the per-step states (host)
+    for the comparison with the oracle."""
+    import synthetic
+    ob = synthetic.obstacle_block(1000 + rank)
+    c = dn.Context(level_solve=3, precision=dn.FP64, nu=0.01, dt=0.01, newton_tol=1e-10,
+                   obstacle_i0=ob[0], obstacle_j0=ob[1])
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    t, states, its = 0.0, [], []
+    for _ in range(steps):
+        ev[0].record(stream)
+        st = c.step(dn.PLAIN)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        t += ev[0].elapsed_time(ev[1])
+        its.append((st["newton_its"], st["gmres_its"]))
+        states.append(c.get_state().cpu().numpy())
+    c.close()
+    return {"workload": "plain MG, FP64, 128x32 channel (level 3, 12,771 DOFs), nu=0.01, "
+                        "dt=0.01, seeded obstacle, Newton tolerance 1e-10, from the impulsive "
+                        "start",
+            "obstacle_block": list(ob), "steps": steps, "ms_per_step": t / steps,
+            "newton_its_mean": sum(a for a, _ in its) / steps,
+            "gmres_its_mean": sum(b for _, b in its) / steps}, states
+
+
+_ORACLE_PLAIN = """
+import json, sys, time
+import numpy as np
+sys.path.insert(0, {root!r})
+from oracle import fem, mesh, newton
+levels = mesh.hierarchy(3, obstacle=({i0}, {j0}))
+prm = fem.Params(nu=0.01, dt=0.01)
+opt = newton.SolverOptions(newton_tol=1e-10)
+x = mesh.initial_state(levels[-1])
+times, xs = [], []
+for _ in range({steps}):
+    t = time.perf_counter()
+    x, nit, git, nrm = newton.time_step(levels, x, prm, opt)
+    times.append(time.perf_counter() - t)
+    xs.append(x)
+np.save({path!r}, np.array(xs))
+print(json.dumps(times))
+"""
+
+
+def oracle_plain_small(block, states):
+    """The oracle beside the plain FP64 128x32 workload: the same steps in a
+    single-threaded process, timed; the GPU's state after every step is
+    compared with the oracle's (relative l2)."""
+    import tempfile
+    import numpy as np
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "x.npy")
+        code = _ORACLE_PLAIN.format(root=ROOT, i0=block["obstacle_block"][0],
+                                    j0=block["obstacle_block"][1], steps=block["steps"], path=path)
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                             env=env, check=True)
+        times = json.loads(out.stdout.strip().splitlines()[-1])
+        xs = np.load(path)
+    errs = [float(np.linalg.norm(g - o) / np.linalg.norm(o)) for g, o in zip(states, xs)]
+    s = sum(times)
+    return {"ms_per_step": 1e3 * s / len(times), "cores": 1,
+            "gpu_vs_oracle_rel_l2_max": max(errs), "gpu_vs_oracle_rel_l2_last": errs[-1],
+            "gpu_speedup": (1e3 * s / len(times)) / block["ms_per_step"]}
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -463,22 +748,27 @@ def run_ours(args, rank, world):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    # ---- corpus from plain fine trajectories and training (untimed setup) ----
-    net_ctx, feat_mean, feat_std, losses, train_ms, corpus = train_network(
-        dn, torch, stream, common, L, 1, NU, NU_TRAIN, CORPUS_STEPS, TRAIN_ITERS, keep_corpus=True)
+    # ---- device corpus of 32 trajectories and training (untimed setup) -------
+    Xc, Yc, corpus_s = device_corpus(dn, torch, dn.MIXED)
+    corpus = (Xc, Yc)
+    net_ctx, feat_mean, feat_std, losses, train_ms = train_on(
+        dn, torch, stream, common, L, 1, NU, corpus, len(CORPUS_SEEDS), CORPUS_T, TRAIN_ITERS)
     P = net_ctx.num_patches()
-    # network forward alone (dnnmg_patch_infer over all patches)
     infer_ms = time_infer(net_ctx, torch, stream, P, 40, 18, 2, 64)
 
-    # ---- timed comparison from the impulsive start -----------------------------
-    ref_ctx = dn.Context(level_solve=L + 1, nu=NU, **common)
-    loose_ctx = dn.Context(level_solve=L + 1, nu=NU, newton_tol=1e-5, gmres_rtol=1e-2, **common)
+    # ---- timed comparison from the developed flow ---------------------------
+    x5, x6 = spun_up_state(dn, NU, ob, dn.MIXED)
+    ref_ctx = dn.Context(level_solve=L + 1, nu=NU, **dict(common, precision=dn.FP64))
     coarse_ctx = dn.Context(level_solve=L, nu=NU, **common)
+    sweep = {}
+    for tol, rtol, nmax, gmax in SWEEP:
+        name = f"mg_L+1@{tol:g}" if nmax > 1 else "mg_L+1@one_newton_one_vcycle"
+        sweep[name] = dn.Context(level_solve=L + 1, nu=NU, newton_tol=tol, gmres_rtol=rtol,
+                                 newton_max=nmax, gmres_maxit=gmax, **common)
     runs = {"dnnmg": (net_ctx, dn.NET), "mg_L": (coarse_ctx, dn.PLAIN),
-            "mg_L+1": (ref_ctx, dn.PLAIN), "mg_L+1_loose": (loose_ctx, dn.PLAIN)}
-    for name, (c, mode) in runs.items():
-        for _ in range(max(1, args.warmup)):
-            c.step(mode)
+            "mg_L+1_fp64": (ref_ctx, dn.PLAIN), **{k: (c, dn.PLAIN) for k, c in sweep.items()}}
+    fine_names = ("mg_L+1_fp64",) + tuple(sweep)
+    start_runs(runs, x5, x6, fine_names, max(1, args.warmup))
     barrier()
 
     def nvtx(name, begin):  # kernel profilers select the DNN-MG launches by this range
@@ -486,12 +776,16 @@ def run_ours(args, rank, world):
             torch.cuda.nvtx.range_push("dnnmg_step") if begin else torch.cuda.nvtx.range_pop()
 
     with ClockSampler(dev) as clk:
-        times, series, stats, counts = compare_runs(runs, "mg_L+1", ref_ctx, L, 1, stream, flush,
-                                                    torch, args.steps, dn.kernel_launches, nvtx)
+        times, series, stats, counts = compare_runs(runs, "mg_L+1_fp64", ref_ctx, L, 1, stream,
+                                                    flush, torch, args.steps, dn.kernel_launches,
+                                                    nvtx)
     barrier()
     launches = counts["dnnmg"]
-    # stage breakdown: the same DNN-MG steps again with per-stage events
-    # (untimed; the events would perturb the timed steps)
+    K = args.steps
+    summary = summarize_series(series, "mg_L+1_fp64")
+    eq = equal_error(times, summary, K, list(sweep))
+    # stage breakdown: more DNN-MG steps with per-stage events (untimed; the
+    # events would perturb the timed steps)
     net_ctx.profile(True)
     for k in range(args.steps):
         net_ctx.step(dn.NET)
@@ -520,7 +814,8 @@ def run_ours(args, rank, world):
         ev[1].record(stream)
         torch.cuda.synchronize()
         return ev[0].elapsed_time(ev[1]) / 10
-    vc6, vc5 = vcycle_ms(ref_ctx, L + 1), vcycle_ms(coarse_ctx, L)
+    fine_mixed = sweep["mg_L+1@1e-10"]
+    vc6, vc5 = vcycle_ms(fine_mixed, L + 1), vcycle_ms(coarse_ctx, L)
 
     # ---- end to end: DNN-MG steps with the state exchanged through host memory ----
     host_in = torch.empty(ndof(L), dtype=torch.float64).pin_memory()
@@ -534,37 +829,43 @@ def run_ours(args, rank, world):
         host_in, host_out = host_out, host_in
     torch.cuda.synchronize()
     t_e2e = (time.perf_counter() - t_e2e) / E
+    plan_dnnmg, plan_fine = net_ctx.vcycle_plan(), fine_mixed.vcycle_plan()
+    weights = net_ctx.get_weights()
+    for c in [ref_ctx, coarse_ctx] + list(sweep.values()):
+        c.close()
+    torch.cuda.empty_cache()
 
+    # ---- held-out trajectories: what the trained network gains ---------------
+    heldout = run_heldout(dn, torch, stream, flush, args, weights, feat_mean, feat_std)
+    # ---- the plain workloads: FP64 128x32, mixed 1024x256 ----------------------
+    small, small_states = run_plain_small(dn, torch, stream, rank)
+    plain_fine = run_plain_fine(dn, torch, stream, flush, rank)
     # ---- batched problems: 64 uneven channels, one launch per stage ---------
-    batched = run_batched(dn, torch, stream, flush, args, net_ctx.get_weights(), feat_mean,
-                          feat_std, rank)
+    batched = run_batched(dn, torch, stream, flush, args, weights, feat_mean, feat_std, rank)
     # ---- large DNN-MG: the network replaces two levels -----------------------
     large = run_large(dn, torch, stream, flush, args, common)
     # ---- the network sizes of Table 1 on the same corpus ---------------------
-    sizes = run_sizes(dn, torch, stream, flush, args, common, corpus)
-    del corpus
+    sizes = run_sizes(dn, torch, stream, flush, args, common, corpus, (x5, x6))
+    del corpus, Xc, Yc
     torch.cuda.empty_cache()
 
     ms = slowest_rank_ms(times["dnnmg"], world, "cuda")
     if rank != 0:
         return None
-    K = args.steps
     bytes_per_pass = fluid_cells(L) / 4 * 576 + nnodes(L) * 44
     avg_pass_ms = vp_ms / max(vp_n, 1)
     pass_gbs = bytes_per_pass / (avg_pass_ms * 1e-3) / 1e9 if vp_n else 0.0
     # the dominant kernel of the DNN-MG step: the persistent sub-cycle of the
     # small levels (if the plan has one and it takes longer), else the colour pass
-    plan = net_ctx.vcycle_plan()
+    build_id = source_hash()
     if vs_n and vs_ms > vp_ms:
-        split = plan["split_level"]
-        kname = ("vcycle_kernel<float>" if plan["split_mode"] == 0 else
+        split = plan_dnnmg["split_level"]
+        kname = ("vcycle_kernel<float>" if plan_dnnmg["split_mode"] == 0 else
                  "vcycle_cluster_kernel<float>")
-        dom_bytes = vcycle_bytes(split)
-        dom_ms = vs_ms / vs_n
         dom = {"kernel": f"{kname} (V(2,2) sub-cycle of levels {split}..1, one launch)",
-               "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms,
+               "algorithmic_bytes_per_launch": vcycle_bytes(split), "avg_launch_ms": vs_ms / vs_n,
                "launches": vs_n,
-               "traffic": NCU_TRAFFIC.get(f"{kname}@split{split}")}
+               "traffic": NCU_TRAFFIC.get(build_id, {}).get(f"{kname}@split{split}")}
     else:
         dom = {"kernel": f"vanka_pass_tiled_kernel<float> (level {L}, one colour pass)",
                "algorithmic_bytes_per_launch": bytes_per_pass, "avg_launch_ms": avg_pass_ms,
@@ -572,7 +873,6 @@ def run_ours(args, rank, world):
     achieved = dom["algorithmic_bytes_per_launch"] / (dom["avg_launch_ms"] * 1e-3) / 1e9
     f_fwd, f_train = net_flops()
     mean = lambda v: sum(v) / len(v)
-    summary = summarize_series(series, "mg_L+1")
     comparison = {
         name: {"ms_per_step": times[name] / K,
                "newton_its": mean([s["newton_its"] for s in stats[name]]),
@@ -591,13 +891,27 @@ def run_ours(args, rank, world):
         "config": {"workload": WORKLOAD, "level_solve": L, "level_net": L + 1, "dofs_L": ndof(L),
                    "dofs_L+1": ndof(L + 1), "patches": P, "obstacle_block": list(ob),
                    "nu": NU, "dt": DT, "l2": "flushed (256 MB write) before every step",
+                   "start": f"developed flow: {SPIN_STEPS} level-{L} steps of {SPIN_DT} s from "
+                            f"rest (t = 1 s), P to level {L + 1}, then {max(1, args.warmup)} "
+                            f"untimed steps of every method",
                    "parallelism": f"independent replicas x{world}",
-                   "network_training": f"{TRAIN_ITERS} Adam steps, B={TRAIN_B}, T={TRAIN_T}, "
-                                       f"corpus {len(NU_TRAIN)} fine trajectories x "
-                                       f"{CORPUS_STEPS} steps (nu {NU_TRAIN})"},
+                   "network_training": f"{TRAIN_ITERS} Adam steps, B={TRAIN_B}, T={TRAIN_T} "
+                                       f"windows, device corpus of {len(CORPUS_SEEDS)} "
+                                       f"trajectories x {CORPUS_T} fine steps"},
         "comparison": comparison,
-        "vcycle": {"split_level_dnnmg": net_ctx.vcycle_split(), "split_level_fine": ref_ctx.vcycle_split(),
-                   "plan_dnnmg": net_ctx.vcycle_plan(), "plan_fine": ref_ctx.vcycle_plan(),
+        "equal_error": eq,
+        "corpus": {"trajectories": len(CORPUS_SEEDS), "steps_per_trajectory": CORPUS_T,
+                   "seeds": [CORPUS_SEEDS[0], CORPUS_SEEDS[-1]], "nu_range": list(NU_RANGE),
+                   "rows": len(CORPUS_SEEDS) * CORPUS_T * P,
+                   "spinup": f"{SPIN_STEPS} level-{L} steps of {SPIN_DT} s, {RELAX_STEPS} "
+                             f"relaxation steps on level {L + 1}",
+                   "seconds": corpus_s},
+        "heldout": heldout,
+        "plain_fp64_small": small,
+        "plain_mixed_fine": plain_fine,
+        "vcycle": {"split_level_dnnmg": plan_dnnmg["split_level"],
+                   "split_level_fine": plan_fine["split_level"],
+                   "plan_dnnmg": plan_dnnmg, "plan_fine": plan_fine,
                    "level6_ms": vc6, "level6_dof_per_s": ndof(6) / (vc6 * 1e-3),
                    "level6_gbs": vcycle_bytes(6) / (vc6 * 1e-3) / 1e9,
                    "level5_ms": vc5, "level5_dof_per_s": ndof(5) / (vc5 * 1e-3),
@@ -605,7 +919,7 @@ def run_ours(args, rank, world):
         "stages_ms_dnnmg": stage,
         "roofline": {"kernel": dom["kernel"], "bound": "hbm", "achieved": achieved, "peak": hbm,
                      "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,
-                     "traffic": dom["traffic"],
+                     "traffic": dom["traffic"], "build": build_id,
                      "algorithmic_bytes_per_launch": dom["algorithmic_bytes_per_launch"],
                      "avg_launch_ms": dom["avg_launch_ms"], "launches": dom["launches"],
                      "timing": "CUDA events around each launch in a repeat of the timed steps",
@@ -636,11 +950,13 @@ def run_ours(args, rank, world):
         "network_sizes": {"sizes": sizes,
                           "setup": f"each trained {TRAIN_ITERS} Adam steps on the corpus of "
                                    f"the default network; {args.steps} DNN-MG steps vs plain MG "
-                                   f"on level {L + 1} after {max(1, args.warmup)} warm-up steps"},
+                                   f"on level {L + 1} from the developed flow after "
+                                   f"{max(1, args.warmup)} warm-up steps"},
         "clocks": clk.summary(),
         "e2e": {"value": 1.0 / t_e2e, "unit": "time steps/s",
                 "h2d_bytes_per_step": 8 * ndof(L), "d2h_bytes_per_step": 8 * ndof(L)},
         "gpu_launches": int(launches),
+        "_small_states": small_states,
     }
 
 
@@ -989,24 +1305,33 @@ def summarize_launches(path):
         print(f"{k[:44]:44s} {n:8d} {t:10.1f} {100 * t / tot:5.1f}%")
 
 
+REF_BUDGET_S = 150.0  # the reference arm's timed oracle steps stop after this long
+
+
 def run_reference(args, rank, world):
+    """The FP64 oracle on the benchmarked workload: consecutive DNN-MG steps
+    (solve on level 5, network on level 6) from the impulsive start on the
+    host cores, single-threaded.  The oracle keeps no caches, so the warm-up
+    is one untimed step at most; the timed steps stop after REF_BUDGET_S
+    seconds (at least one step), so that the run ends within a few minutes."""
     if rank != 0:
         return None
     t = time.perf_counter()
-    per = [oracle_dnnmg_seconds(ORACLE_L - 1, steps=1, warm=0) * ndof(L) / ndof(ORACLE_L - 1)
-           for _ in range(args.steps)]
+    per = oracle_dnnmg_steps(L, steps=args.steps, warm=min(args.warmup, 1), threads=1,
+                             budget=REF_BUDGET_S)
     mean = sum(per) / len(per)
     v = 1.0 / mean
+    sample = (f"{len(per)} consecutive DNN-MG time steps (of the {args.steps} requested) of the "
+              f"FP64 oracle on the benchmarked workload (solve on 512x128, level {L}; network "
+              f"on 1024x256), after {min(args.warmup, 1)} untimed step(s) from the impulsive "
+              f"start; single-threaded; stopped after {REF_BUDGET_S:.0f} s of timed steps")
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "time steps/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "n_gpus": world, "steps": len(per), "warmup": min(args.warmup, 1),
             "ms_per_step": mean * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "level_solve": L, "dofs_L": ndof(L)},
             "cpu_baseline": {"value": v, "unit": "time steps/s", "cores": 1, "kind": "oracle",
-                             "sample": f"each step: the first DNN-MG time step of the FP64 oracle "
-                                       f"with the solve on the 128x32 channel (level "
-                                       f"{ORACLE_L - 1}) from the impulsive start, scaled by the "
-                                       f"level-L DOF ratio to level {L}; single-threaded"},
+                             "sample": sample},
             "e2e": {"value": v, "unit": "time steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
             "wall_s": time.perf_counter() - t}
@@ -1058,8 +1383,11 @@ def main():
             torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
             torch.distributed.init_process_group("nccl")
         out = run_ours(args, rank, world)
+        small_states = out.pop("_small_states") if out is not None else None
         if out is not None and world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline()
+            out["plain_fp64_small"]["oracle"] = oracle_plain_small(out["plain_fp64_small"],
+                                                                   small_states)
         if world > 1:
             import torch
             torch.distributed.destroy_process_group()

@@ -106,6 +106,10 @@ typedef struct dnnmg_config {
                               mode (-1)^i free: the Jacobian is singular and the solver
                               does not converge with it (operator, residual and
                               functionals only, for comparisons) */
+  int32_t stream_pass;     /* FP32 colour passes of the levels outside the persistent
+                              launch: 0 = the streaming kernel (inverses copied by TMA
+                              one tile ahead) where the autotuner finds it faster
+                              (default), 1 = always where it can run, -1 = never */
 } dnnmg_config;
 
 /* Per-step statistics returned by dnnmg_step(). */
@@ -338,6 +342,26 @@ int dnnmg_reset_optimizer(dnnmg_ctx* ctx);
 int dnnmg_make_sample(dnnmg_ctx* ctx, const double* xf_prev, const double* xf_next, float* X,
                       float* Y, dnnmg_step_stats* stats);
 
+/* The whole corpus of Sec. 3.1 on the device: n_traj plain trajectories of
+ * the context's channel (its obstacle), trajectory k with viscosity nu[k]
+ * (host array).  Each starts from rest: spinup_steps plain steps of the
+ * level-L solver with time step spinup_dt, the state prolongated (P, once
+ * per replaced level) to the fine level F = L + replaced_levels, then
+ * relax_steps plain fine-level steps with the configured dt, then T more
+ * fine steps; after fine step n the pair (x^F_{n-1}, x^F_n) gives one
+ * dnnmg_make_sample into slot s = k * T + n.
+ *   X: device [n_traj][T][P][C_in] float (raw inputs, row = s * P + patch),
+ *   Y: device [n_traj][T][P][C_out] float (targets); the layout
+ *      dnnmg_gather_batch reads with stride = P.
+ * The first call creates (allocates) a plain solver on level F inside the
+ * context; later calls reuse it.  On return the context's nu and dt are the
+ * configured ones again and its state is the impulsive start (network
+ * state cleared).  Errors: DNNMG_ERR_ARG (counts < 1, negative steps,
+ * non-positive nu or spinup_dt), DNNMG_ERR_STATE (no DNN-MG network), and
+ * the errors of the steps; a step that stops at its Newton cap is kept. */
+int dnnmg_make_corpus(dnnmg_ctx* ctx, int n_traj, const double* nu, int spinup_steps,
+                      double spinup_dt, int relax_steps, int T, float* X, float* Y);
+
 /* Per-feature mean and standard deviation (population, FP64 sums in fixed
  * order) of `rows` raw input rows (device [rows][C_in] float); they become the
  * context's standardisation (features with zero spread get std 1).  mean /
@@ -412,8 +436,8 @@ int dnnmg_vcycle_split(const dnnmg_ctx* ctx);
  * the split level as above; the kind of persistent launch below it (0: one
  * cooperative grid with grid-wide barriers, 1: one thread-block cluster of
  * up to 16 blocks with cluster barriers); and the tile of colour cells per
- * block of the colour pass on `level` (0: 16x4, 1: 8x4, 2: 8x8; -1 if the
- * level is not in the hierarchy). */
+ * block of the colour pass on `level` (0: 16x4, 1: 8x4, 2: 8x8, 3: the
+ * streaming pass of 16x4 tiles; -1 if the level is not in the hierarchy). */
 int dnnmg_vcycle_plan(const dnnmg_ctx* ctx, int level, int* split_level, int* split_mode,
                       int* pass_shape);
 

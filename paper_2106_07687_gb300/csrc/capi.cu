@@ -210,6 +210,7 @@ int dnnmg_default_config(dnnmg_config* c) {
   c->persistent_vcycle = -1;
   c->precond_lag = 1;
   c->persistent_mode = -1;
+  c->stream_pass = 0;
   return DNNMG_OK;
 }
 
@@ -422,6 +423,12 @@ int dnnmg_make_sample(dnnmg_ctx* ctx, const double* xf_prev, const double* xf_ne
                       float* Y, dnnmg_step_stats* stats) {
   if (!ctx || !xf_prev || !xf_next || !X || !Y) return DNNMG_ERR_ARG;
   return ctx->make_sample(xf_prev, xf_next, X, Y, stats);
+}
+
+int dnnmg_make_corpus(dnnmg_ctx* ctx, int n_traj, const double* nu, int spinup_steps,
+                      double spinup_dt, int relax_steps, int T, float* X, float* Y) {
+  if (!ctx || !nu || !X || !Y) return DNNMG_ERR_ARG;
+  return ctx->make_corpus(n_traj, nu, spinup_steps, spinup_dt, relax_steps, T, X, Y);
 }
 
 int dnnmg_feature_stats(dnnmg_ctx* ctx, const float* X, int64_t rows, float* mean, float* stdv) {

@@ -62,11 +62,30 @@ void launch_vanka_setup(const Grid& g, const Sten<T>& s, const T* vb, T* inv, in
 // one colour pass: xout = xin + omega A_c^{-1} (b - A xin)_c on the colour's cells;
 // `shape` picks the tile of colour cells a block owns: 0 = 16x4, 1 = 8x4, 2 = 8x8
 constexpr int kPassShapes = 3;
+constexpr int kPassStream = 3;  // plan code of the streaming pass (vanka_stream.cu)
 template <typename T>
 void launch_vanka_pass(const Grid& g, const Sten<T>& s, int colour, const T* b, const T* xin,
                        const T* vb, const T* inv, T omega, T* xout, cudaStream_t st,
                        int shape = 0);
-__host__ __device__ inline int vanka_slots(const Grid& g) { return (g.nx / 2 + 1) * (g.ny / 2 + 1); }
+// Slots of a colour's cells: slot (ti, tj) = cell (2 ti - cx, 2 tj - cy) of
+// colour (cx, cy), for ti < nx/2 + 1, tj < ny/2 + 1.  A row of slots is padded
+// to a multiple of 4 (16 bytes of FP32), so that a row of the inverse array
+// inv[colour][entry][tj][ti] starts on a 16-byte boundary (tensor-memory-
+// access copies need that); padding slots are never written or used.
+__host__ __device__ inline int vanka_pitch(const Grid& g) { return ((g.nx / 2 + 1) + 3) & ~3; }
+__host__ __device__ inline int vanka_slots(const Grid& g) { return vanka_pitch(g) * (g.ny / 2 + 1); }
+// Streaming FP32 colour pass for large levels (vanka_stream.cu): the same
+// result as launch_vanka_pass, with the tile's inverses copied by TMA one
+// tile ahead.  map: a tensor map of the level's inverse array made by
+// make_vanka_tensor_map (false if the driver cannot make one);
+// vanka_stream_grid is 0 when the kernel cannot be resident.  A copy that
+// does not arrive within the poll limit sets bit 8 of *status.
+constexpr int kTensorMapBytes = 128;
+bool make_vanka_tensor_map(void* map, const float* inv, const Grid& g);
+int vanka_stream_grid(const Grid& g);
+void launch_vanka_pass_stream(const void* map, const Grid& g, const Sten<float>& s, int colour,
+                              const float* b, const float* xin, const float* vb, float omega,
+                              float* xout, int* status, cudaStream_t st);
 // Vanka setup kernels: 16 lanes per cell, kSetupCells cells per block
 constexpr int kSetupThreads = 128;
 constexpr int kSetupCells = kSetupThreads / 16;

@@ -45,6 +45,12 @@ class Solver final : public SolverBase {
       l.vb64 = c_->mem.alloc<double>(n2);
       if (k > 0) l.inv = c_->mem.alloc<T>((size_t)4 * 144 * vanka_slots(l.g));
     }
+    // streaming colour passes (FP32): a tensor map of every level's inverses
+    if constexpr (sizeof(T) == 4) {
+      for (int k = 1; k <= K_; ++k)
+        lv_[k].stream_ok = lv_[k].inv && vanka_stream_grid(lv_[k].g) > 0 &&
+                           make_vanka_tensor_map(lv_[k].tmap, (const float*)lv_[k].inv, lv_[k].g);
+    }
     const Grid& g0 = lv_[0].g;
     if (!coarse_supported(g0)) return c_->fail(DNNMG_ERR_ARG, "coarse level too large");
     coarse_work_ = c_->mem.alloc<double>(coarse_work_doubles(g0));
@@ -255,6 +261,9 @@ class Solver final : public SolverBase {
     Sten<double> s64{};
     T *x = nullptr, *x2 = nullptr, *b = nullptr, *d = nullptr, *vb = nullptr, *inv = nullptr;
     double* vb64 = nullptr;
+    alignas(64) unsigned char tmap[kTensorMapBytes] = {};  // TMA map of inv (FP32)
+    bool stream_ok = false;  // the streaming colour pass can run on this level
+    bool stream = false;     // and the autotuner chose it
   };
 
   int read_scalar(const double* dev, double* out) {
@@ -273,8 +282,17 @@ class Solver final : public SolverBase {
     for (int s = 0; s < sweeps; ++s)
       for (int colour = 0; colour < 4; ++colour) {
         const int p = c_->prof.begin(DNNMG_STAGE_VANKA_PASS, l.level, st_);
-        launch_vanka_pass<T>(l.g, l.s, colour, b, cur, l.vb, l.inv, (T)c_->cfg.omega, nxt, st_,
-                             shape_[k]);
+        if constexpr (sizeof(T) == 4) {
+          if (l.stream)
+            launch_vanka_pass_stream(l.tmap, l.g, l.s, colour, b, cur, l.vb, (T)c_->cfg.omega,
+                                     nxt, status_ + 2, st_);
+          else
+            launch_vanka_pass<T>(l.g, l.s, colour, b, cur, l.vb, l.inv, (T)c_->cfg.omega, nxt,
+                                 st_, shape_[k]);
+        } else {
+          launch_vanka_pass<T>(l.g, l.s, colour, b, cur, l.vb, l.inv, (T)c_->cfg.omega, nxt, st_,
+                               shape_[k]);
+        }
         c_->prof.end(p, st_);
         T* t = cur;
         cur = nxt;
@@ -282,11 +300,35 @@ class Solver final : public SolverBase {
       }
   }
 
+  void set_physics() override {
+    const dnnmg_config& cfg = c_->cfg;
+    for (Lev& l : lv_) {
+      l.s = make_sten<T>(l.g.h, cfg);
+      l.s64 = make_sten<double>(l.g.h, cfg);
+    }
+    if (dlv_) {
+      std::vector<VLevel<T>> hv(K_ + 1);
+      for (int k = 0; k <= K_; ++k)
+        hv[k] = VLevel<T>{lv_[k].g, lv_[k].s, lv_[k].x, lv_[k].x2, lv_[k].b, lv_[k].d,
+                          lv_[k].vb, lv_[k].inv};
+      cudaMemcpyAsync(dlv_, hv.data(), sizeof(VLevel<T>) * hv.size(), cudaMemcpyHostToDevice, st_);
+      cudaStreamSynchronize(st_);
+    }
+    coarse_done_ = false;
+    linearized_ = linearized_j_ = false;
+  }
+
   int split_level() const override { return split_ > 0 ? split_ : 0; }
   int split_mode() const override { return split_mode_; }
   int pass_shape(int level) const override {
     const int k = level - lv_[0].level;
-    return k >= 0 && k <= K_ ? shape_[k] : -1;
+    return k >= 0 && k <= K_ ? (lv_[k].stream ? kPassStream : shape_[k]) : -1;
+  }
+  int device_status() override {
+    int st[4] = {0, 0, 0, 0};
+    cudaMemcpyAsync(st, status_, sizeof(st), cudaMemcpyDeviceToHost, st_);
+    if (cudaStreamSynchronize(st_) != cudaSuccess) return -1;
+    return st[2];
   }
 
   // Autotuner, run once at the first linearisation: (1) the tile shape of
@@ -314,12 +356,18 @@ class Solver final : public SolverBase {
     for (int k = 1; k <= K_; ++k) {
       float best = 1e30f;
       int best_s = 0;
+      lv_[k].stream = false;
       for (int sh = 0; sh < kPassShapes; ++sh) {
         shape_[k] = sh;
         const float ms = time_ms([&] { smooth(k, lv_[k].d, lv_[k].x, 1); }, 3);
         if (ms < best) best = ms, best_s = sh;
       }
       shape_[k] = best_s;
+      if (lv_[k].stream_ok && c_->cfg.stream_pass >= 0) {
+        lv_[k].stream = true;
+        const float ms = time_ms([&] { smooth(k, lv_[k].d, lv_[k].x, 1); }, 3);
+        lv_[k].stream = c_->cfg.stream_pass == 1 || ms < best;
+      }
     }
     const int top = K_;
     if (split_ == -1) {
@@ -840,6 +888,88 @@ int dnnmg_ctx::make_sample(const double* xf_prev, const double* xf_next, float* 
   return check("make_sample");
 }
 
+void dnnmg_ctx::set_physics(double nu, double dt) {
+  cfg.nu = nu;
+  cfg.dt = dt;
+  const Grid gL = grid(L());
+  s64L = make_sten<double>(gL.h, cfg);
+  sxL = make_explicit_sten(gL.h, cfg);
+  if (cfg.replaced_levels > 0) {
+    sxF = make_explicit_sten(grid(fine_level()).h, cfg);
+    s64F = make_sten<double>(grid(fine_level()).h, cfg);
+  }
+  solver->set_physics();
+  steps_taken = 0;
+}
+
+// Corpus of Sec. 3.1 from plain trajectories: per trajectory a viscosity,
+// a spin-up of the level-L solver from the impulsive start (larger time
+// step), the prolongated state relaxed by plain fine-level steps, then T
+// fine steps with one make_sample per step.
+int dnnmg_ctx::make_corpus(int n_traj, const double* nus, int spinup_steps, double spinup_dt,
+                           int relax_steps, int T, float* Xraw, float* Y) {
+  if (!X) return fail(DNNMG_ERR_STATE, "DNN-MG needs replaced_levels 1 or 2 and the default network");
+  if (n_traj < 1 || T < 1 || spinup_steps < 0 || relax_steps < 0 || !(spinup_dt > 0))
+    return fail(DNNMG_ERR_ARG, "make_corpus: bad trajectory counts or spin-up time step");
+  for (int k = 0; k < n_traj; ++k)
+    if (!(nus[k] > 0)) return fail(DNNMG_ERR_ARG, "make_corpus: viscosities must be positive");
+  if (!corpus_fine) {
+    auto f = std::make_unique<dnnmg_ctx>();
+    f->cfg = cfg;
+    f->cfg.level_solve = fine_level();
+    f->cfg.replaced_levels = 0;
+    f->cfg.train_batch = 0;
+    f->cfg.train_seq = 0;
+    f->st = st;
+    if (int rc = f->init()) return fail(rc, "make_corpus: fine-level solver: " + f->err);
+    corpus_fine = std::move(f);
+  }
+  dnnmg_ctx& fine = *corpus_fine;
+  const double nu0 = cfg.nu, dt0 = cfg.dt;
+  const Grid gL = grid(L()), gF = grid(fine_level());
+  const std::vector<double> x0 = initial_state(gL);
+  const size_t rows = (size_t)P;
+  int rc = DNNMG_OK;
+  auto ok = [](int r) { return r == DNNMG_OK || r == DNNMG_ERR_NOT_CONVERGED; };
+  for (int k = 0; k < n_traj && rc == DNNMG_OK; ++k) {
+    set_physics(nus[k], spinup_dt);
+    cudaMemcpyAsync(x64, x0.data(), x0.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+    cudaStreamSynchronize(st);
+    have_net_rhs = have_vcorr = false;
+    for (int s = 0; s < spinup_steps; ++s) {
+      const int r = step(DNNMG_PLAIN, nullptr);
+      if (!ok(r)) return r;
+    }
+    set_physics(nus[k], dt0);
+    fine.set_physics(nus[k], dt0);
+    prolong_up(x64, fine.x64, 3);
+    if (int r = fine.set_state(fine.x64)) return fail(r, "make_corpus: " + fine.err);
+    for (int s = 0; s < relax_steps; ++s) {
+      const int r = fine.step(DNNMG_PLAIN, nullptr);
+      if (!ok(r)) return fail(r, "make_corpus: " + fine.err);
+    }
+    for (int n = 0; n < T; ++n) {
+      // the fine step leaves its previous state in xold64
+      const int r = fine.step(DNNMG_PLAIN, nullptr);
+      if (!ok(r)) return fail(r, "make_corpus: " + fine.err);
+      const size_t slot = (size_t)k * T + n;
+      const int r2 = make_sample(fine.xold64, fine.x64, Xraw + slot * rows * nd.c_in,
+                                 Y + slot * rows * nd.c_out, nullptr);
+      if (!ok(r2)) return r2;
+    }
+  }
+  (void)gF;
+  // back to the configured physics and the impulsive start
+  set_physics(nu0, dt0);
+  fine.set_physics(nu0, dt0);
+  cudaMemcpyAsync(x64, x0.data(), x0.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+  cudaStreamSynchronize(st);
+  have_net_rhs = have_vcorr = false;
+  if (hid) cudaMemsetAsync(hid, 0, sizeof(float) * nd.layers * P * nd.hidden, st);
+  cudaStreamSynchronize(st);
+  return check("make_corpus");
+}
+
 int dnnmg_ctx::feature_stats(const float* Xraw, long long rows, float* mean_h, float* std_h) {
   if (!feat_mean) return fail(DNNMG_ERR_STATE, "no DNN-MG network in this context");
   if (rows <= 0) return fail(DNNMG_ERR_ARG, "no rows");
@@ -1055,6 +1185,8 @@ int dnnmg_ctx::newton(const double* f, dnnmg_step_stats* s) {
   s->newton_its = it;
   s->gmres_its = gits;
   s->res_final = nrm;
+  if (const int ds = solver->device_status())
+    return ds < 0 ? check("newton") : fail(DNNMG_ERR_TIMEOUT, "a colour pass's inverse copy timed out");
   if (!std::isfinite(nrm)) return fail(DNNMG_ERR_NUMERICAL, "non-finite Newton residual");
   if (nrm > cfg.newton_tol) return DNNMG_ERR_NOT_CONVERGED;
   return check("newton");

@@ -131,6 +131,11 @@ class SolverBase {
   virtual int split_level() const = 0;
   virtual int split_mode() const = 0;
   virtual int pass_shape(int level) const = 0;
+  // recompute every level's stencil constants from the context's nu and dt
+  // (after a change of either); the next linearisation refactors the coarse level
+  virtual void set_physics() = 0;
+  // device-side error bits of the smoother kernels (0: none; -1: CUDA error)
+  virtual int device_status() = 0;
 };
 
 std::unique_ptr<SolverBase> make_solver(struct ::dnnmg_ctx* ctx);
@@ -238,4 +243,10 @@ struct dnnmg_ctx {
   int gather_batch(const float* Xraw, const float* Yc, const int* idx, int B, int T,
                    long long stride, uint16_t* Xb, float* Yb);
   int newton(const double* f, dnnmg_step_stats* st);
+  // nu and dt of every stencil of this context (and of its corpus solver)
+  void set_physics(double nu, double dt);
+  // plain solver on the fine level, made by the first make_corpus call
+  std::unique_ptr<dnnmg_ctx> corpus_fine;
+  int make_corpus(int n_traj, const double* nu, int spinup_steps, double spinup_dt,
+                  int relax_steps, int T, float* Xraw, float* Y);
 };

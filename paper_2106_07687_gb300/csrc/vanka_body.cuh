@@ -41,10 +41,10 @@ __device__ __forceinline__ void vanka_setup_cell(const Grid& g, const Sten<T>& s
                                                  const T* __restrict__ vb, T* __restrict__ inv,
                                                  int* status, int colour, int slot) {
   const int cx = colour & 1, cy = colour >> 1;
-  const int sx = g.nx / 2 + 1;
-  const int nslots = sx * (g.ny / 2 + 1);
-  if (slot >= nslots) return;
-  const int ci = 2 * (slot % sx) - cx, cj = 2 * (slot / sx) - cy;
+  const int sx = g.nx / 2 + 1, pitch = vanka_pitch(g);
+  const int nslots = vanka_slots(g);
+  if (slot >= nslots || slot % pitch >= sx) return;
+  const int ci = 2 * (slot % pitch) - cx, cj = 2 * (slot / pitch) - cy;
   if (ci < 0 || cj < 0 || ci >= g.nx || cj >= g.ny || g.solid[cj * g.nx + ci]) return;
   const int lane = threadIdx.x & 15;
   const unsigned mask = 0xFFFFu << (threadIdx.x & 16);  // this half-warp
@@ -169,63 +169,22 @@ struct PassSmem {
   int8_t pvalid[(kTCY + 2) * (kTCX + 2)];
 };
 
-// Tile (bx, by) of the colour pass, computed by a group of NTT consecutive
-// threads of the block (a block may hold several such groups, each with its
-// own S; every thread of the block must call this together because of the
-// block barriers).  The first 4 kTCX kTCY threads own one node of a colour
-// cell each; with NTT larger, the other threads help stage the tile and
-// compute the cell and patch rows, so that those take one round instead of
-// two.  A group with active = false takes part in the barriers only and
-// writes nothing.
-template <typename T, int kTCX, int kTCY, int NTT = 4 * kTCX * kTCY>
-__device__ __forceinline__ void vanka_pass_tile(const Grid& g, const Sten<T>& s, int colour,
-                                                const T* __restrict__ b, const T* __restrict__ xin,
-                                                const T* __restrict__ vb, const T* __restrict__ inv,
-                                                T omega, T* __restrict__ xout, int bx, int by,
-                                                PassSmem<T, kTCX, kTCY>& S, bool active = true) {
-  if (!active) bx = by = 0;
-  constexpr int kTileThreads = 4 * kTCX * kTCY;
-  static_assert(NTT >= kTileThreads && NTT % 32 == 0 && kTileThreads % 32 == 0, "tile group");
+// Stage the tile whose first node is (i0, j0) -- nodes [i0-2, i0-2+kSX) x
+// [j0-2, j0-2+kSY) with the masked iterate, vbar, flags and the solid flag
+// of the cell whose lower-left node each one is -- then compute the 12 rows
+// of every cell touching the tile and the 9 LPS rows of every patch touching
+// it, once each.  Thread t of NTT; ends with the rows visible to all
+// threads of the group (two block barriers).
+template <typename T, int kTCX, int kTCY, int NTT>
+__device__ __forceinline__ void pass_stage_rows(const Grid& g, const Sten<T>& s,
+                                                const T* __restrict__ xin,
+                                                const T* __restrict__ vb, int i0, int j0, int t,
+                                                PassSmem<T, kTCX, kTCY>& S) {
   constexpr int kSX = 2 * kTCX + 4;
   constexpr int kCX = 2 * kTCX + 1, kCY = 2 * kTCY + 1;
   constexpr int kPX = kTCX + 2, kPY = kTCY + 2;
   constexpr int kSY = 2 * kTCY + 4;
-  const int cx = colour & 1, cy = colour >> 1;
-  const int sx = g.nx / 2 + 1, sy = g.ny / 2 + 1;
-  const int nslots = sx * sy;
   const int nn = g.nn;
-  const int tx0 = bx * kTCX, ty0 = by * kTCY;
-  const int i0 = 2 * tx0 - cx, j0 = 2 * ty0 - cy;  // first node of the tile
-  const int t = threadIdx.x % NTT;
-  const bool owner = t < kTileThreads;  // owns a node of a colour cell
-  // ---- this thread's node (quad q, local node a) and its loads that do not
-  // depend on the defect: b, x_in and its three rows of the cell's inverse,
-  // issued first so that their latency overlaps the stencil work below
-  const int q = t >> 2, a = t & 3;
-  const int ti = tx0 + (q % kTCX), tj = ty0 + (q / kTCX);
-  const bool slot_ok = owner && ti < sx && tj < sy;
-  const int slot = tj * sx + ti;
-  const int ci = 2 * ti - cx, cj = 2 * tj - cy;
-  const int i = ci + (a & 1), j = cj + (a >> 1);
-  const bool node_ok = slot_ok && i >= 0 && j >= 0 && i <= g.nx && j <= g.ny;
-  const int n = node_ok ? j * g.nnx + i : 0;
-  // every global load of the tile is issued before the first barrier, none
-  // depends on another: the thread's b, x_in and three inverse rows (read
-  // even for a solid cell, whose rows are then not used), and the staged
-  // nodes' flags, iterate, vbar and cell solid flags
-  T xu = 0, xv = 0, xp = 0, bu0 = 0, bv0 = 0, bp0 = 0;
-  T iv[36];
-  if (node_ok) {
-    xu = xin[n], xv = xin[nn + n], xp = xin[2 * nn + n];
-    bu0 = b[n], bv0 = b[nn + n], bp0 = b[2 * nn + n];
-    const T* row0 = inv + (size_t)colour * 144 * nslots + slot;
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int k = 0; k < 12; ++k) iv[c * 12 + k] = row0[(size_t)((c * 4 + a) * 12 + k) * nslots];
-  }
-  // ---- stage nodes [i0-2, i0-2+kSX) x [j0-2, j0-2+kSY), and the solid flag
-  // of the cell whose lower-left node each one is
   for (int e = t; e < kSX * kSY; e += NTT) {
     const int li = e % kSX, lj = e / kSX;
     const int i = i0 - 2 + li, j = j0 - 2 + lj;
@@ -250,9 +209,6 @@ __device__ __forceinline__ void vanka_pass_tile(const Grid& g, const Sten<T>& s,
     S.sol[lj][li] = so;
   }
   __syncthreads();
-  // own cell (ci, cj) sits at staged index (ci - i0 + 2, cj - j0 + 2)
-  const bool cell_ok = slot_ok && ci >= 0 && cj >= 0 && ci < g.nx && cj < g.ny &&
-                       !S.sol[cj - j0 + 2][ci - i0 + 2];
   // ---- cells [i0-1, i0-1+kCX) x [j0-1, j0-1+kCY): 12 rows each, then the
   // patches touching the tile: 9 LPS rows each; these are the patches from
   // ceil((i0 - 2) / 2) (also for negative i0) to floor((i0 + 2 kTCX - 1) / 2),
@@ -304,40 +260,110 @@ __device__ __forceinline__ void vanka_pass_tile(const Grid& g, const Sten<T>& s,
     }
   }
   __syncthreads();
+}
+
+// Defect b - A x at node (i, j) of the staged tile with first node (i0, j0)
+// from the staged rows (constrained rows: b - x), for a node of a fluid
+// colour cell; xu.. and bu0.. are the node's unmasked iterate and
+// right-hand side.
+template <typename T, int kTCX, int kTCY>
+__device__ __forceinline__ void pass_node_defect(int i, int j, int i0, int j0, T xu, T xv, T xp,
+                                                 T bu0, T bv0, T bp0,
+                                                 const PassSmem<T, kTCX, kTCY>& S, T& du, T& dv,
+                                                 T& dp) {
+  constexpr int kCX = 2 * kTCX + 1, kPX = kTCX + 2;
+  const int PI0 = (i0 - 1) >> 1, PJ0 = (j0 - 1) >> 1;
+  T ru = 0, rv = 0, rp = 0;
+#pragma unroll
+  for (int dyy = 0; dyy < 2; ++dyy)
+#pragma unroll
+    for (int dxx = 0; dxx < 2; ++dxx) {
+      const int lc = i - 1 + dxx - (i0 - 1), lr = j - 1 + dyy - (j0 - 1);
+      const int e = lr * kCX + lc;
+      if (!S.cvalid[e]) continue;
+      const int al = (1 - dxx) + 2 * (1 - dyy);
+      ru += S.cres[e][al];
+      rv += S.cres[e][4 + al];
+      rp += S.cres[e][8 + al];
+    }
+#pragma unroll
+  for (int dJ = 0; dJ < 2; ++dJ) {
+    const int PJ = (j >> 1) - dJ;
+    if (j - 2 * PJ > 2) continue;
+#pragma unroll
+    for (int dI = 0; dI < 2; ++dI) {
+      const int PI = (i >> 1) - dI;
+      if (i - 2 * PI > 2) continue;
+      const int e = (PJ - PJ0) * kPX + (PI - PI0);
+      if (!S.pvalid[e]) continue;
+      rp += S.pres[e][(i - 2 * PI) + 3 * (j - 2 * PJ)];
+    }
+  }
+  const uint8_t f = S.fl[j - (j0 - 2)][i - (i0 - 2)];
+  du = bu0 - ((f & kVDir) ? xu : ru);
+  dv = bv0 - ((f & kVDir) ? xv : rv);
+  dp = bp0 - ((f & kPFix) ? xp : rp);
+}
+
+// Tile (bx, by) of the colour pass, computed by a group of NTT consecutive
+// threads of the block (a block may hold several such groups, each with its
+// own S; every thread of the block must call this together because of the
+// block barriers).  The first 4 kTCX kTCY threads own one node of a colour
+// cell each; with NTT larger, the other threads help stage the tile and
+// compute the cell and patch rows, so that those take one round instead of
+// two.  A group with active = false takes part in the barriers only and
+// writes nothing.
+template <typename T, int kTCX, int kTCY, int NTT = 4 * kTCX * kTCY>
+__device__ __forceinline__ void vanka_pass_tile(const Grid& g, const Sten<T>& s, int colour,
+                                                const T* __restrict__ b, const T* __restrict__ xin,
+                                                const T* __restrict__ vb, const T* __restrict__ inv,
+                                                T omega, T* __restrict__ xout, int bx, int by,
+                                                PassSmem<T, kTCX, kTCY>& S, bool active = true) {
+  if (!active) bx = by = 0;
+  constexpr int kTileThreads = 4 * kTCX * kTCY;
+  static_assert(NTT >= kTileThreads && NTT % 32 == 0 && kTileThreads % 32 == 0, "tile group");
+  const int cx = colour & 1, cy = colour >> 1;
+  const int sx = g.nx / 2 + 1, sy = g.ny / 2 + 1;
+  const int pitch = vanka_pitch(g), nslots = vanka_slots(g);
+  const int nn = g.nn;
+  const int tx0 = bx * kTCX, ty0 = by * kTCY;
+  const int i0 = 2 * tx0 - cx, j0 = 2 * ty0 - cy;  // first node of the tile
+  const int t = threadIdx.x % NTT;
+  const bool owner = t < kTileThreads;  // owns a node of a colour cell
+  // ---- this thread's node (quad q, local node a) and its loads that do not
+  // depend on the defect: b, x_in and its three rows of the cell's inverse,
+  // issued first so that their latency overlaps the stencil work below
+  const int q = t >> 2, a = t & 3;
+  const int ti = tx0 + (q % kTCX), tj = ty0 + (q / kTCX);
+  const bool slot_ok = owner && ti < sx && tj < sy;
+  const int slot = tj * pitch + ti;
+  const int ci = 2 * ti - cx, cj = 2 * tj - cy;
+  const int i = ci + (a & 1), j = cj + (a >> 1);
+  const bool node_ok = slot_ok && i >= 0 && j >= 0 && i <= g.nx && j <= g.ny;
+  const int n = node_ok ? j * g.nnx + i : 0;
+  // every global load of the tile is issued before the first barrier, none
+  // depends on another: the thread's b, x_in and three inverse rows (read
+  // even for a solid cell, whose rows are then not used), and the staged
+  // nodes' flags, iterate, vbar and cell solid flags
+  T xu = 0, xv = 0, xp = 0, bu0 = 0, bv0 = 0, bp0 = 0;
+  T iv[36];
+  if (node_ok) {
+    xu = xin[n], xv = xin[nn + n], xp = xin[2 * nn + n];
+    bu0 = b[n], bv0 = b[nn + n], bp0 = b[2 * nn + n];
+    const T* row0 = inv + (size_t)colour * 144 * nslots + slot;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int k = 0; k < 12; ++k) iv[c * 12 + k] = row0[(size_t)((c * 4 + a) * 12 + k) * nslots];
+  }
+  pass_stage_rows<T, kTCX, kTCY, NTT>(g, s, xin, vb, i0, j0, t, S);
+  // own cell (ci, cj) sits at staged index (ci - i0 + 2, cj - j0 + 2)
+  const bool cell_ok = slot_ok && ci >= 0 && cj >= 0 && ci < g.nx && cj < g.ny &&
+                       !S.sol[cj - j0 + 2][ci - i0 + 2];
   if (!owner) return;  // helpers are whole warps past the owners
   T du = 0, dv = 0, dp = 0;
-  if (node_ok && cell_ok) {
-    T ru = 0, rv = 0, rp = 0;
-#pragma unroll
-    for (int dyy = 0; dyy < 2; ++dyy)
-#pragma unroll
-      for (int dxx = 0; dxx < 2; ++dxx) {
-        const int lc = i - 1 + dxx - (i0 - 1), lr = j - 1 + dyy - (j0 - 1);
-        const int e = lr * kCX + lc;
-        if (!S.cvalid[e]) continue;
-        const int al = (1 - dxx) + 2 * (1 - dyy);
-        ru += S.cres[e][al];
-        rv += S.cres[e][4 + al];
-        rp += S.cres[e][8 + al];
-      }
-#pragma unroll
-    for (int dJ = 0; dJ < 2; ++dJ) {
-      const int PJ = (j >> 1) - dJ;
-      if (j - 2 * PJ > 2) continue;
-#pragma unroll
-      for (int dI = 0; dI < 2; ++dI) {
-        const int PI = (i >> 1) - dI;
-        if (i - 2 * PI > 2) continue;
-        const int e = (PJ - PJ0) * kPX + (PI - PI0);
-        if (!S.pvalid[e]) continue;
-        rp += S.pres[e][(i - 2 * PI) + 3 * (j - 2 * PJ)];
-      }
-    }
-    const uint8_t f = S.fl[j - (j0 - 2)][i - (i0 - 2)];
-    du = bu0 - ((f & kVDir) ? xu : ru);
-    dv = bv0 - ((f & kVDir) ? xv : rv);
-    dp = bp0 - ((f & kPFix) ? xp : rp);
-  }
+  if (node_ok && cell_ok)
+    pass_node_defect<T, kTCX, kTCY>(i, j, i0, j0, xu, xv, xp, bu0, bv0, bp0, S, du, dv, dp);
   const int lane = t & 31, base = lane & ~3;
   T d[12];
 #pragma unroll
@@ -380,12 +406,12 @@ __device__ __forceinline__ void vanka_pass_zero_node(const Grid& g, int colour,
                                                      const T* __restrict__ inv, T omega,
                                                      T* __restrict__ xout, int e, bool valid) {
   const int cx = colour & 1, cy = colour >> 1;
-  const int sx = g.nx / 2 + 1, sy = g.ny / 2 + 1;
-  const int nslots = sx * sy;
+  const int sx = g.nx / 2 + 1, pitch = vanka_pitch(g);
+  const int nslots = vanka_slots(g);
   const int nn = g.nn;
   const int slot = e >> 2, a = e & 3;
-  const bool slot_ok = valid && slot < nslots;
-  const int ci = 2 * (slot % sx) - cx, cj = 2 * (slot / sx) - cy;
+  const bool slot_ok = valid && slot < nslots && slot % pitch < sx;
+  const int ci = 2 * (slot % pitch) - cx, cj = 2 * (slot / pitch) - cy;
   const int i = ci + (a & 1), j = cj + (a >> 1);
   const bool node_ok = slot_ok && i >= 0 && j >= 0 && i <= g.nx && j <= g.ny;
   const bool cell_ok = slot_ok && ci >= 0 && cj >= 0 && ci < g.nx && cj < g.ny &&

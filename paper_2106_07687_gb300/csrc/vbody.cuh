@@ -16,11 +16,11 @@ __device__ __forceinline__ void vanka_pass_thread(const Grid& g, const Sten<T>& 
                                                   const T* __restrict__ inv, T omega,
                                                   T* __restrict__ xout, int tid) {
   const int cx = colour & 1, cy = colour >> 1;
-  const int sx = g.nx / 2 + 1;
-  const int nslots = sx * (g.ny / 2 + 1);
+  const int sx = g.nx / 2 + 1, pitch = vanka_pitch(g);
+  const int nslots = vanka_slots(g);
   const int slot = tid >> 2, a = tid & 3;
-  const bool slot_ok = slot < nslots;
-  const int ci = 2 * (slot % sx) - cx, cj = 2 * (slot / sx) - cy;
+  const bool slot_ok = slot < nslots && slot % pitch < sx;
+  const int ci = 2 * (slot % pitch) - cx, cj = 2 * (slot / pitch) - cy;
   const int i = ci + (a & 1), j = cj + (a >> 1);
   const bool node_ok = slot_ok && i >= 0 && j >= 0 && i <= g.nx && j <= g.ny;
   const bool cell_ok = slot_ok && ci >= 0 && cj >= 0 && ci < g.nx && cj < g.ny &&

@@ -32,7 +32,7 @@ class Config(ctypes.Structure):
                 ("gru_layers", c_int32), ("mlp_width", c_int32), ("fallback_newton_its", c_int32),
                 ("train_batch", c_int32), ("train_seq", c_int32), ("coarse_refresh", c_int32),
                 ("persistent_vcycle", c_int32), ("precond_lag", c_int32),
-                ("persistent_mode", c_int32), ("lps_mode", c_int32)]
+                ("persistent_mode", c_int32), ("lps_mode", c_int32), ("stream_pass", c_int32)]
 
 
 class StepStats(ctypes.Structure):
@@ -83,6 +83,8 @@ def _declare(lib):
         "dnnmg_reset_optimizer": ([P], ctypes.c_int),
         "dnnmg_make_sample": ([P, P, P, P, P, P], ctypes.c_int),
         "dnnmg_feature_stats": ([P, P, ctypes.c_int64, P, P], ctypes.c_int),
+        "dnnmg_make_corpus": ([P, ctypes.c_int, P, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                               ctypes.c_int, P, P], ctypes.c_int),
         "dnnmg_step_io": ([P, ctypes.c_int, P, P, P], ctypes.c_int),
         "dnnmg_prolongate": ([P, ctypes.c_int, P, P], ctypes.c_int),
         "dnnmg_functionals": ([P, ctypes.c_int, P, P, P], ctypes.c_int),
@@ -289,6 +291,20 @@ class Context:
         st = StepStats()
         self._check(self.lib.dnnmg_make_sample(self.h, _ptr(xf_prev), _ptr(xf_next), _ptr(X),
                                                _ptr(Y), ctypes.byref(st)), allow=(ERR_NOT_CONVERGED,))
+        return X, Y
+
+    def make_corpus(self, nus, spinup_steps, spinup_dt, relax_steps, T, X=None, Y=None):
+        """Raw inputs [n_traj, T, P, C_in] and targets [n_traj, T, P, C_out]
+        (cuda float) of plain trajectories with viscosities nus."""
+        ci, co = self.net_dims()
+        P, n = self.num_patches(), len(nus)
+        X = torch.empty(n, T, P, ci, dtype=torch.float32, device="cuda") if X is None else X
+        Y = torch.empty(n, T, P, co, dtype=torch.float32, device="cuda") if Y is None else Y
+        if X.numel() != n * T * P * ci or Y.numel() != n * T * P * co:
+            raise ValueError("X, Y must hold n_traj x T x P x C_in / C_out floats")
+        nu = (ctypes.c_double * n)(*[float(v) for v in nus])
+        self._check(self.lib.dnnmg_make_corpus(self.h, n, nu, spinup_steps, spinup_dt,
+                                               relax_steps, T, _ptr(X), _ptr(Y)))
         return X, Y
 
     def feature_stats(self, X, rows=None):

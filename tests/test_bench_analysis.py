@@ -31,3 +31,36 @@ def test_first_max_and_phase_shift():
     assert bench.first_max(a) == 10          # sin peaks at t = period / 4 = 10 steps
     assert bench.first_max(b) - bench.first_max(a) == 7
     assert bench.first_max([1.0, 0.5, 0.2]) is None
+
+
+def _summary(errs):
+    return {k: {"vel_l2_err_mean": v} for k, v in errs.items()}
+
+
+def test_equal_error_interpolates_between_bracketing_points():
+    """MG(L+1)'s time at DNN-MG's error: log(time) linear in log(error)
+    between the two sweep points around the target error (Sec. 3.3's
+    comparison of time per step at equal accuracy)."""
+    K = 10
+    errs = {"dnnmg": 1e-4, "a": 1e-8, "b": 1e-5, "c": 1e-3}
+    times = {"dnnmg": 50.0, "a": 200.0, "b": 100.0, "c": 40.0}   # summed over K steps
+    eq = bench.equal_error(times, _summary(errs), K, ["a", "b", "c"])
+    assert eq["bracketed"] and eq["between"] == ["b", "c"]
+    # 1e-4 is halfway between 1e-5 and 1e-3 in log scale: sqrt(10 * 4) ms
+    assert abs(eq["mg_fine_ms_at_equal_error"] - math.sqrt(10.0 * 4.0)) < 1e-12
+    assert abs(eq["speedup_vs_mg_fine"] - math.sqrt(40.0) / 5.0) < 1e-12
+    assert [p["run"] for p in eq["sweep"]] == ["a", "b", "c"]
+
+
+def test_equal_error_unbracketed_gives_an_upper_bound():
+    K = 4
+    errs = {"dnnmg": 1e-2, "a": 1e-8, "b": 1e-5}
+    times = {"dnnmg": 20.0, "a": 80.0, "b": 24.0}
+    eq = bench.equal_error(times, _summary(errs), K, ["a", "b"])
+    assert not eq["bracketed"] and eq["between"] == ["b", None]
+    assert eq["mg_fine_ms_at_equal_error"] == 6.0 and eq["speedup_vs_mg_fine"] == 6.0 / 5.0
+
+
+def test_source_hash_is_stable_and_covers_the_sources():
+    h = bench.source_hash()
+    assert len(h) == 16 and h == bench.source_hash()
