@@ -85,7 +85,8 @@ typedef struct dnnmg_config {
   int32_t hidden;          /* GRU hidden size m: 32 or 64 (default 64) */
   int32_t gru_layers;      /* stacked GRU cells n: 1, 2 or 3 (default 2); m x n are
                               the sizes of Table 1 */
-  int32_t mlp_width;       /* width of the hidden dense layer (128, the only value) */
+  int32_t mlp_width;       /* width of the hidden dense layer: 128 (default), or 0 for a
+                              single dense layer m -> C_out after the GRUs (Table 1) */
   int32_t fallback_newton_its; /* DNN-MG step redone without the network if Newton needs more */
   int32_t train_batch;     /* largest training batch B (sequences) of dnnmg_train_*, 0 = none */
   int32_t train_seq;       /* largest training sequence length T */
@@ -110,6 +111,13 @@ typedef struct dnnmg_config {
                               launch: 0 = the streaming kernel (inverses copied by TMA
                               one tile ahead) where the autotuner finds it faster
                               (default), 1 = always where it can run, -1 = never */
+  int32_t net_bias;        /* 1: the GRUs and dense layers have biases (default); 0: none,
+                              as the networks of Table 1 */
+  int32_t net_inputs;      /* inputs C_in of the network: 0 = the patch features of
+                              Sec. 2.2 (4 K^2 + 4 for K x K patch nodes, default); any
+                              other value (1..127) makes a network for dnnmg_patch_infer
+                              and training only (DNN-MG steps and samples need the
+                              patch features); Table 1's networks have 51 */
 } dnnmg_config;
 
 /* Per-step statistics returned by dnnmg_step(). */

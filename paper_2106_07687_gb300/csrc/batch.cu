@@ -239,9 +239,10 @@ int Batch<T>::init() {
         c.gmres_rtol != c0_.gmres_rtol || c.coarse_refresh != c0_.coarse_refresh ||
         c.precond_lag != c0_.precond_lag || c.fallback_newton_its != c0_.fallback_newton_its ||
         c.hidden != c0_.hidden || c.gru_layers != c0_.gru_layers ||
-        c.mlp_width != c0_.mlp_width)
+        c.mlp_width != c0_.mlp_width || c.net_bias != c0_.net_bias || c.net_inputs != 0)
       return fail(DNNMG_ERR_ARG, "problems of a batch may differ only in nu, dt, theta, alpha0, "
-                                 "obstacle and level_solve");
+                                 "obstacle and level_solve (and take the patch features as "
+                                 "network inputs)");
   }
   if (c0_.replaced_levels > 1) return fail(DNNMG_ERR_ARG, "batched DNN-MG supports replaced_levels <= 1");
   R_ = c0_.replaced_levels;
@@ -398,6 +399,7 @@ int Batch<T>::init() {
     nd_.hidden = c0_.hidden;
     nd_.layers = c0_.gru_layers;
     nd_.mlp = c0_.mlp_width;
+    nd_.bias = c0_.net_bias;
     net_ok_ = net_supported(nd_);
     if (net_ok_) {
       std::vector<int> pi, pc, cp;

@@ -211,6 +211,8 @@ int dnnmg_default_config(dnnmg_config* c) {
   c->precond_lag = 1;
   c->persistent_mode = -1;
   c->stream_pass = 0;
+  c->net_bias = 1;
+  c->net_inputs = 0;
   return DNNMG_OK;
 }
 

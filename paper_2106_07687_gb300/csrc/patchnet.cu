@@ -50,27 +50,29 @@ __global__ void pack_block_kernel(const float* __restrict__ src, int ld, int row
   }
 }
 
+// fused biases; a network without biases gets zeros
 __global__ void pack_bias_kernel(const float* __restrict__ w, NetDims d, float* __restrict__ bias) {
   const int H = d.hidden;
-  size_t off = 0;
+  const NetOffsets o = d.offsets();
   for (int l = 0; l < d.layers; ++l) {
-    const int c = l == 0 ? d.c_in : H;
-    const float* bih = w + off + (size_t)3 * H * c + (size_t)3 * H * H;
-    const float* bhh = bih + 3 * H;
     for (int j = threadIdx.x; j < H; j += blockDim.x) {
       float* b = bias + (size_t)l * 4 * H;
-      b[j] = bih[j] + bhh[j];
-      b[H + j] = bih[H + j] + bhh[H + j];
-      b[2 * H + j] = bih[2 * H + j];
-      b[3 * H + j] = bhh[2 * H + j];
+      if (d.bias) {
+        const float* bih = w + o.bih[l];
+        const float* bhh = w + o.bhh[l];
+        b[j] = bih[j] + bhh[j];
+        b[H + j] = bih[H + j] + bhh[H + j];
+        b[2 * H + j] = bih[2 * H + j];
+        b[3 * H + j] = bhh[2 * H + j];
+      } else {
+        b[j] = b[H + j] = b[2 * H + j] = b[3 * H + j] = 0.0f;
+      }
     }
-    off += (size_t)3 * H * c + (size_t)3 * H * H + 6 * H;
   }
-  const float* b1 = w + off + (size_t)d.mlp * H;
-  const float* b2 = b1 + d.mlp + (size_t)d.c_out * d.mlp;
   float* ob = bias + (size_t)d.layers * 4 * H;
-  for (int j = threadIdx.x; j < d.mlp; j += blockDim.x) ob[j] = b1[j];
-  for (int j = threadIdx.x; j < d.nout(); j += blockDim.x) ob[d.mlp + j] = j < d.c_out ? b2[j] : 0.f;
+  for (int j = threadIdx.x; j < d.mlp; j += blockDim.x) ob[j] = d.bias ? w[o.b1 + j] : 0.0f;
+  for (int j = threadIdx.x; j < d.nout(); j += blockDim.x)
+    ob[d.mlp + j] = d.bias && j < d.c_out ? w[o.b2 + j] : 0.0f;
 }
 
 // -- shared-memory plan of the forward kernel ---------------------------------
@@ -264,17 +266,25 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
       // first layer's previous state (BF16 operand, this thread's units)
       {
         const int nq = kx0 / 8;
+        const bool vec = d.c_in % 8 == 0;  // input rows start on 16-byte boundaries
         for (int e = t; e < kTile * nq; e += kFwdThreads) {
           const int r = e / nq, q = e % nq;
           const int pr = tile * kTile + r;
           uint4 v = make_uint4(0, 0, 0, 0);
           const bool in = pr < P && q * 8 < d.c_in;
-          if (in) v = reinterpret_cast<const uint4*>(a.x + ((size_t)pr * T + step) * d.c_in)[q];
+          const uint16_t* src = a.x + ((size_t)pr * T + step) * d.c_in;
+          if (in && vec) {
+            v = reinterpret_cast<const uint4*>(src)[q];
+          } else if (in) {  // element by element, zeros past C_in
+            uint16_t* ev = reinterpret_cast<uint16_t*>(&v);
+            for (int i = 0; i < 8; ++i) ev[i] = q * 8 + i < d.c_in ? src[q * 8 + i] : 0;
+          }
           *reinterpret_cast<uint4*>(sm + S.a + kmajor_offset(r, q * 8, kx0)) = v;
           if (TRAIN && in) {
             const uint16_t* ev = reinterpret_cast<const uint16_t*>(&v);
             const size_t cr = (size_t)step * P + pr;
-            for (int i = 0; i < 8; ++i) a.xT[(size_t)(q * 8 + i) * ld + cr] = ev[i];
+            for (int i = 0; i < 8 && q * 8 + i < d.c_in; ++i)
+              a.xT[(size_t)(q * 8 + i) * ld + cr] = ev[i];
           }
         }
       }
@@ -316,7 +326,10 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         }
       }
       if (failed) break;
-      // ---- dense head: relu(h W1^T + b1) W2^T + b2 on the top layer's state
+      // ---- dense head: relu(h W1^T + b1) W2^T + b2 on the top layer's state,
+      // or h W2^T + b2 without the hidden dense layer
+      const float* b1 = bias + NL * 4 * H;
+      if (d.mlp) {
       fence_async_smem();
       fence_before_sync();
       __syncthreads();
@@ -332,7 +345,6 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         break;
       }
       fence_after_sync();
-      const float* b1 = bias + NL * 4 * H;
 #pragma unroll 1
       for (int c = 2 * cq; c < 2 * cq + 2; ++c) {  // 32 of the 128 units
         float v[16];
@@ -350,13 +362,17 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
 #pragma unroll
           for (int i = 0; i < 16; ++i) a.y1T[(size_t)(c * 16 + i) * ld + col] = f2bf(v[i]);
       }
+      }
       fence_async_smem();
       fence_before_sync();
       __syncthreads();
       const int n2 = d.nout();
       if (t == 0) {
         fence_after_sync();
-        mma_run(tbase + 128, sbase + S.m, 128, sbase + S.w + 2 * L.w2, 128, n2, 128, false);
+        if (d.mlp)
+          mma_run(tbase + 128, sbase + S.m, 128, sbase + S.w + 2 * L.w2, 128, n2, 128, false);
+        else  // the single dense layer reads the top state in region a
+          mma_run(tbase + 128, sbase + S.a, H, sbase + S.w + 2 * L.w2, H, n2, H, false);
         mma_commit(bar);
       }
       if (!mbar_wait(bar, phase, kWaitPolls)) failed = true;
@@ -494,8 +510,11 @@ size_t patchnet_forward_smem(const NetDims& d) {
 }
 
 bool net_supported(const NetDims& d) {
+  // (the input stream of the first layer's weight gradient, C_in + 1 rows
+  // with the ones row, must fit the 144-row operand of that GEMM)
   if ((d.hidden != 32 && d.hidden != 64) || d.layers < 1 || d.layers > kMaxLayers ||
-      d.mlp != 128 || d.c_in % 8 != 0 || d.c_out > 64 || d.nout() > 16 * kFwdWG)
+      (d.mlp != 128 && d.mlp != 0) || d.c_in < 1 || d.c_in > 127 || d.c_out < 1 ||
+      d.c_out > 64 || d.nout() > 16 * kFwdWG || (d.bias != 0 && d.bias != 1))
     return false;
   constexpr size_t kSmemMax = 227 * 1024;
   return patchnet_forward_smem(d) <= kSmemMax && patchnet_backward_smem(d) <= kSmemMax;
@@ -503,12 +522,12 @@ bool net_supported(const NetDims& d) {
 
 void launch_pack_weights(const NetDims& d, const float* w, PackedNet& pk, cudaStream_t st) {
   const PackLayout L = PackLayout::of(d);
+  const NetOffsets o = d.offsets();
   const int H = d.hidden;
-  size_t off = 0;
   for (int l = 0; l < d.layers; ++l) {
     const int c = l == 0 ? d.c_in : H;
-    const float* Wih = w + off;
-    const float* Whh = Wih + (size_t)3 * H * c;
+    const float* Wih = w + o.wih[l];
+    const float* Whh = w + o.whh[l];
     const int kx = L.kx[l];
     note_launch();
     pack_block_kernel<<<64, 256, 0, st>>>(Wih, c, 0, 2 * H, c, 2 * H, kx, pk.w + L.rz[l]);
@@ -518,14 +537,14 @@ void launch_pack_weights(const NetDims& d, const float* w, PackedNet& pk, cudaSt
     pack_block_kernel<<<64, 256, 0, st>>>(Whh, H, 0, 2 * H, H, 2 * H, H, pk.w + L.hrz[l]);
     note_launch();
     pack_block_kernel<<<64, 256, 0, st>>>(Whh, H, 2 * H, H, H, H, H, pk.w + L.hn[l]);
-    off += (size_t)3 * H * c + (size_t)3 * H * H + 6 * H;
   }
-  const float* W1 = w + off;
-  const float* W2 = W1 + (size_t)d.mlp * H + d.mlp;
+  if (d.mlp) {
+    note_launch();
+    pack_block_kernel<<<64, 256, 0, st>>>(w + o.w1, H, 0, 128, H, 128, H, pk.w + L.w1);
+  }
+  const int k2 = d.k2();
   note_launch();
-  pack_block_kernel<<<64, 256, 0, st>>>(W1, H, 0, 128, H, 128, H, pk.w + L.w1);
-  note_launch();
-  pack_block_kernel<<<64, 256, 0, st>>>(W2, d.mlp, 0, d.c_out, d.mlp, d.nout(), 128, pk.w + L.w2);
+  pack_block_kernel<<<64, 256, 0, st>>>(w + o.w2, k2, 0, d.c_out, k2, d.nout(), k2, pk.w + L.w2);
   note_launch();
   pack_bias_kernel<<<1, 128, 0, st>>>(w, d, pk.bias);
 }

@@ -1,12 +1,17 @@
 // Patch network of DNN-MG (Sec. 2.2, Sec. 3.1): n stacked GRU cells with
 // hidden size m (m x n in {32, 64} x {1, 2, 3}, the sizes of Table 1) and a
-// dense head Linear(m -> 128) + ReLU + Linear(128 -> C_out), evaluated for
-// every patch with tcgen05 tensor-core GEMMs.
+// dense head, either Linear(m -> 128) + ReLU + Linear(128 -> C_out) (mlp =
+// 128) or the single dense layer Linear(m -> C_out) of Table 1's networks
+// (mlp = 0), with or without biases, evaluated for every patch with tcgen05
+// tensor-core GEMMs.
 //
 // Flat FP32 parameter order (PyTorch's GRU order, gate rows r, z, n):
-//   per layer l: W_ih (3m x C_l), W_hh (3m x m), b_ih (3m), b_hh (3m)
-//   then W1 (128 x m), b1 (128), W2 (C_out x 128), b2 (C_out)
-// with C_0 = C_in (40 for one replaced level) and C_l = m above.
+//   per layer l: W_ih (3m x C_l), W_hh (3m x m), [b_ih (3m), b_hh (3m)]
+//   then [W1 (128 x m), [b1 (128)]], W2 (C_out x K2), [b2 (C_out)]
+// with C_0 = C_in (40 for one replaced level), C_l = m above, K2 = 128 with
+// the hidden dense layer and m without it; the bracketed biases exist only
+// with bias = 1.  Table 1's networks (bias-free, one dense layer, 51 inputs,
+// 18 outputs) have 171 m + 3 m^2 + 6 m^2 (n - 1) parameters.
 #pragma once
 #include <cstddef>
 #include <cstdint>
@@ -17,20 +22,40 @@ namespace dnnmg {
 
 constexpr int kMaxLayers = 3;
 
+constexpr size_t kNoParam = ~(size_t)0;  // offset of a parameter block that does not exist
+
+// Offsets of the parameter blocks in the flat vector (kNoParam if absent).
+struct NetOffsets {
+  size_t wih[kMaxLayers], whh[kMaxLayers], bih[kMaxLayers], bhh[kMaxLayers], w1, b1, w2, b2, total;
+};
+
 struct NetDims {
-  int c_in = 40, hidden = 64, layers = 2, mlp = 128, c_out = 18;
+  int c_in = 40, hidden = 64, layers = 2, mlp = 128, c_out = 18, bias = 1;
   __host__ __device__ int kx0() const { return (c_in + 15) / 16 * 16; }  // padded K of layer 0
   __host__ __device__ int nout() const {
     return (c_out + 15) / 16 * 16 < 32 ? 32 : (c_out + 15) / 16 * 16;
   }
-  __host__ __device__ size_t num_params() const {
+  // K of the output layer: the hidden dense layer's width, or m without it
+  __host__ __device__ int k2() const { return mlp ? mlp : hidden; }
+  __host__ __device__ NetOffsets offsets() const {
+    NetOffsets o{};
     size_t n = 0;
+    const size_t H = hidden;
     for (int l = 0; l < layers; ++l) {
-      const int c = l == 0 ? c_in : hidden;
-      n += (size_t)3 * hidden * c + (size_t)3 * hidden * hidden + 6 * hidden;
+      const size_t c = l == 0 ? c_in : hidden;
+      o.wih[l] = n;  n += 3 * H * c;
+      o.whh[l] = n;  n += 3 * H * H;
+      o.bih[l] = bias ? n : kNoParam;  n += bias ? 3 * H : 0;
+      o.bhh[l] = bias ? n : kNoParam;  n += bias ? 3 * H : 0;
     }
-    return n + (size_t)mlp * hidden + mlp + (size_t)c_out * mlp + c_out;
+    o.w1 = mlp ? n : kNoParam;          n += mlp ? (size_t)mlp * H : 0;
+    o.b1 = mlp && bias ? n : kNoParam;  n += mlp && bias ? mlp : 0;
+    o.w2 = n;                           n += (size_t)c_out * k2();
+    o.b2 = bias ? n : kNoParam;         n += bias ? c_out : 0;
+    o.total = n;
+    return o;
   }
+  __host__ __device__ size_t num_params() const { return offsets().total; }
 };
 
 // Packed BF16 operand image of the weights (the shared-memory layout of the
@@ -44,7 +69,8 @@ struct PackedNet {
 
 // element offsets of the packed operand blocks: per layer the gate rows r, z
 // of W_ih (2m x kx) and W_hh (2m x m), the n rows of W_ih (m x kx) and W_hh
-// (m x m); then W1 (128 x m) and W2 (nout x 128)
+// (m x m); then W1 (128 x m, only with the hidden dense layer) and W2
+// (nout x K2)
 struct PackLayout {
   size_t rz[kMaxLayers], in[kMaxLayers], hrz[kMaxLayers], hn[kMaxLayers], w1, w2, total;
   int kx[kMaxLayers];
@@ -59,8 +85,8 @@ struct PackLayout {
       p.hrz[l] = o; o += 2 * H * H;
       p.hn[l] = o;  o += H * H;
     }
-    p.w1 = o; o += (size_t)128 * H;
-    p.w2 = o; o += (size_t)d.nout() * 128;
+    p.w1 = o; o += d.mlp ? (size_t)128 * H : 0;
+    p.w2 = o; o += (size_t)d.nout() * d.k2();
     p.total = o;
     return p;
   }

@@ -101,6 +101,11 @@ class Solver final : public SolverBase {
       split_mode_ = cfg.persistent_mode >= 0 ? cfg.persistent_mode : (vgrid_ > 0 ? 0 : 1);
     }
     shape_.assign(K_ + 1, 0);
+    {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms_, cudaDevAttrMultiProcessorCount, dev);
+    }
     // side streams and events of the concurrent Vanka setups (levels 1..K-1)
     if (K_ > 1) {
       if (cudaEventCreateWithFlags(&fork_ev_, cudaEventDisableTiming) != cudaSuccess)
@@ -376,7 +381,7 @@ class Solver final : public SolverBase {
       T* x = wsol_;
       launch_fill<T>(b, T(0), 3 * (size_t)lv_[top].g.nn, st_);
       float best = 1e30f;
-      int best_s = 0, best_m = 0;
+      int best_s = 0, best_m = 0, best_cap = 0;
       for (int cand = lv_[top].level; cand >= 0; --cand) {
         if (cand > 0 && cand < lv_[0].level + 1) continue;
         for (int mode = 0; mode < 2; ++mode) {
@@ -385,16 +390,23 @@ class Solver final : public SolverBase {
           if (cand > 0 && ((mode == 0 && vgrid_ <= 0) || (mode == 1 && cluster_ <= 0))) continue;
           split_ = cand;
           split_mode_ = mode;
-          persistent_failed_ = false;
-          float ms = time_ms([&] { cycle(top, b, x); }, 5);
-          if (persistent_failed_) ms = 1e30f;
-          // candidates come from the highest split down: a lower split (more
-          // launches) must be faster by more than the timing noise
-          if (ms < 0.98f * best) best = ms, best_s = cand, best_m = mode;
+          // cooperative grids: also fewer blocks than tiles (cheaper grid
+          // barriers, more tiles per block); 0 = one block per tile
+          for (int cap : {0, 2, 1}) {
+            if (cap > 0 && (mode != 0 || cand == 0)) continue;
+            coop_cap_ = cap * sms_;
+            persistent_failed_ = false;
+            float ms = time_ms([&] { cycle(top, b, x); }, 5);
+            if (persistent_failed_) ms = 1e30f;
+            // candidates come from the highest split down: a lower split (more
+            // launches) or a capped grid must be faster by more than the timing noise
+            if (ms < 0.98f * best) best = ms, best_s = cand, best_m = mode, best_cap = coop_cap_;
+          }
         }
       }
       split_ = best_s;
       split_mode_ = best_m;
+      coop_cap_ = best_cap;
       persistent_failed_ = false;
     }
     if (prof_on) c_->prof.enable(true);
@@ -422,6 +434,7 @@ class Solver final : public SolverBase {
         // one block per colour-pass tile of the sub-cycle's top level
         int blocks = vcycle_coop_tiles(lv_[k].g);
         blocks = blocks < 64 ? 64 : blocks;
+        if (coop_cap_ > 0 && blocks > coop_cap_) blocks = coop_cap_;
         blocks = blocks > vgrid_ ? vgrid_ : blocks;
         rc = launch_vcycle_persistent<T>(dlv_, dph_ + ph_off_[k], ph_n_[k], k, b, x, ainv_,
                                          (T)c_->cfg.omega, blocks, coarse_nd_, st_);
@@ -484,6 +497,8 @@ class Solver final : public SolverBase {
   int vgrid_ = 0, coarse_nd_ = 0, cluster_ = 0;
   int split_ = 0;  // levels <= split_ (> 0) run as one persistent launch; -1: not tuned yet
   int split_mode_ = 0;        // 0: cooperative grid, 1: single cluster
+  int coop_cap_ = 0;          // most blocks of the cooperative grid (0: one per tile)
+  int sms_ = 0;               // multiprocessors of the device
   std::vector<int> shape_;    // colour-pass tile shape per level
   bool tuned_ = false;
   bool persistent_failed_ = false;
@@ -702,25 +717,27 @@ int dnnmg_ctx::train_grad_impl(const uint16_t* Xd, const float* Yd, int B, int T
   // against the layer's previous state (the unshifted view)
   WGradJob jobs[kMaxWGradJobs];
   int njobs = 0;
-  size_t off = 0;
+  const NetOffsets o = nd.offsets();
+  auto gb = [&](size_t off) { return off == kNoParam ? nullptr : grad + off; };  // bias gradient
   for (int l = 0; l < NL; ++l) {
-    const int c = l == 0 ? nd.c_in : H;
-    const size_t oWih = off, oWhh = oWih + (size_t)3 * H * c, obih = oWhh + (size_t)3 * H * H,
-                 obhh = obih + 3 * H;
-    off = obhh + 3 * H;
     if (l == 0)
       jobs[njobs++] = {giT[0], tb.xT, K, K, MG, (nd.c_in + 1 + 15) / 16 * 16, 3 * H, nd.c_in,
-                       nd.c_in, grad + oWih, grad + obih};
+                       nd.c_in, grad + o.wih[0], gb(o.bih[0])};
     else
-      jobs[njobs++] = {giT[l], tb.hT[l - 1] + B, K, Kh, MG, H + 16, 3 * H, H, H, grad + oWih,
-                       grad + obih};
-    jobs[njobs++] = {ghT[l], tb.hT[l], K, Kh, MG, H + 16, 3 * H, H, H, grad + oWhh, grad + obhh};
+      jobs[njobs++] = {giT[l], tb.hT[l - 1] + B, K, Kh, MG, H + 16, 3 * H, H, H,
+                       grad + o.wih[l], gb(o.bih[l])};
+    jobs[njobs++] = {ghT[l], tb.hT[l], K, Kh, MG, H + 16, 3 * H, H, H, grad + o.whh[l],
+                     gb(o.bhh[l])};
   }
-  const size_t oW1 = off, ob1 = oW1 + (size_t)nd.mlp * H, oW2 = ob1 + nd.mlp,
-               ob2 = oW2 + (size_t)nd.c_out * nd.mlp;
-  jobs[njobs++] = {da1T, tb.hT[NL - 1] + B, K, Kh, 128, H + 16, nd.mlp, H, H, grad + oW1,
-                   grad + ob1};
-  jobs[njobs++] = {dyT, tb.y1T, K, K, 128, 144, nd.c_out, nd.mlp, nd.mlp, grad + oW2, grad + ob2};
+  if (nd.mlp) {
+    jobs[njobs++] = {da1T, tb.hT[NL - 1] + B, K, Kh, 128, H + 16, nd.mlp, H, H, grad + o.w1,
+                     gb(o.b1)};
+    jobs[njobs++] = {dyT, tb.y1T, K, K, 128, 144, nd.c_out, nd.mlp, nd.mlp, grad + o.w2,
+                     gb(o.b2)};
+  } else {  // a single dense layer: W2 against the top layer's new state
+    jobs[njobs++] = {dyT, tb.hT[NL - 1] + B, K, Kh, 128, H + 16, nd.c_out, H, H, grad + o.w2,
+                     gb(o.b2)};
+  }
   // about two blocks per SM, at least four K chunks of 64 per block
   int tiles = 0;
   for (int q = 0; q < njobs; ++q) tiles += jobs[q].M / 128;
@@ -754,7 +771,8 @@ int dnnmg_ctx::train_step(const uint16_t* X, const float* Y, int B, int T, float
 
 // Patch lists and level L+1 buffers of the DNN-MG correction.
 int dnnmg_ctx::init_dnnmg() {
-  if (cfg.replaced_levels < 1 || !net_ok) return DNNMG_OK;  // NET steps report it
+  // NET steps, samples and corpora report the missing parts
+  if (cfg.replaced_levels < 1 || !net_ok || cfg.net_inputs > 0) return DNNMG_OK;
   const HostLevel& hl = lv[L()];
   std::vector<int> pc, cp(hl.solid.size(), -1);
   for (size_t c = 0; c < hl.solid.size(); ++c)
@@ -855,7 +873,9 @@ int dnnmg_ctx::dnnmg_correction() {
 // then the network inputs at P(v^L_n) and the targets v^{L+1}_n - P(v^L_n).
 int dnnmg_ctx::make_sample(const double* xf_prev, const double* xf_next, float* Xraw, float* Y,
                            dnnmg_step_stats* s) {
-  if (!X) return fail(DNNMG_ERR_STATE, "DNN-MG needs replaced_levels 1 or 2 and the default network");
+  if (!X)
+    return fail(DNNMG_ERR_STATE,
+                "DNN-MG needs replaced_levels 1 or 2 and a network on the patch features");
   const Grid gL = grid(L()), gF = grid(fine_level());
   const size_t n3L = 3 * (size_t)gL.nn;
   const int K = (1 << cfg.replaced_levels) + 1;
@@ -908,7 +928,9 @@ void dnnmg_ctx::set_physics(double nu, double dt) {
 // fine steps with one make_sample per step.
 int dnnmg_ctx::make_corpus(int n_traj, const double* nus, int spinup_steps, double spinup_dt,
                            int relax_steps, int T, float* Xraw, float* Y) {
-  if (!X) return fail(DNNMG_ERR_STATE, "DNN-MG needs replaced_levels 1 or 2 and the default network");
+  if (!X)
+    return fail(DNNMG_ERR_STATE,
+                "DNN-MG needs replaced_levels 1 or 2 and a network on the patch features");
   if (n_traj < 1 || T < 1 || spinup_steps < 0 || relax_steps < 0 || !(spinup_dt > 0))
     return fail(DNNMG_ERR_ARG, "make_corpus: bad trajectory counts or spin-up time step");
   for (int k = 0; k < n_traj; ++k)
@@ -1047,11 +1069,12 @@ int dnnmg_ctx::get_patch_inputs(uint16_t* x) {
 int dnnmg_ctx::init_net() {
   const int r = cfg.replaced_levels > 0 ? cfg.replaced_levels : 1;
   const int k = (1 << r) + 1;
-  nd.c_in = 4 * k * k + 4;
+  nd.c_in = cfg.net_inputs > 0 ? cfg.net_inputs : 4 * k * k + 4;
   nd.c_out = 2 * k * k;
   nd.hidden = cfg.hidden;
   nd.layers = cfg.gru_layers;
   nd.mlp = cfg.mlp_width;
+  nd.bias = cfg.net_bias;
   net_ok = net_supported(nd);
   if (!net_ok) return DNNMG_OK;  // network calls report the unsupported shape
   const PackLayout L = PackLayout::of(nd);
@@ -1197,7 +1220,8 @@ int dnnmg_ctx::step(int mode, dnnmg_step_stats* stats) {
   const Grid gL = grid(L());
   const size_t n3 = 3 * (size_t)gL.nn;
   if (mode == DNNMG_NET && (cfg.replaced_levels < 1 || !net_ok || !X))
-    return fail(DNNMG_ERR_ARG, "DNN-MG steps need replaced_levels 1 or 2 and the default network");
+    return fail(DNNMG_ERR_ARG,
+                "DNN-MG steps need replaced_levels 1 or 2 and a network on the patch features");
   cudaEventRecord(ev0, st);
   cudaMemcpyAsync(xold64, x64, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
   const bool use_net_rhs = mode == DNNMG_NET && have_net_rhs;

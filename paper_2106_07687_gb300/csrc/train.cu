@@ -228,8 +228,12 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
         }
         store_row<16>(R, row, 16 * cq, NO, dy);
       }
-      sync_mma([&] { mma_run(tbase + 0, sb + S.r, NO, sw + 2 * W.w2t, NO, 128, NO, false); });
+      sync_mma([&] { mma_run(tbase + 0, sb + S.r, NO, sw + 2 * W.w2t, NO, d.k2(), NO, false); });
       if (failed) break;
+      float dtop[U];  // gradient of the current layer's new state from above
+      if (!d.mlp) {   // a single dense layer: dY W2 is the top state's gradient
+        tmem_ld<U>(tm + u0, dtop);
+      } else {
       // ---- dense head: da1 = (dY W2) * [a1 > 0], 32 of the 128 units
 #pragma unroll
       for (int c = 2 * cq; c < 2 * cq + 2; ++c) {
@@ -245,8 +249,8 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
       }
       sync_mma([&] { mma_run(tbase + 128, sb + S.r, 128, sw + 2 * W.w1t, 128, H, 128, false); });
       if (failed) break;
-      float dtop[U];  // gradient of the current layer's new state from above
       tmem_ld<U>(tm + 128 + u0, dtop);
+      }
       // ---- GRU layers, top to bottom (the first layer's input gradient is
       // not needed)
 #pragma unroll
@@ -435,7 +439,7 @@ __global__ void wgrad_reduce_kernel(WGradArgs a, const float* __restrict__ Cpart
     for (int sp = 0; sp < a.splits; ++sp) acc += Cp[((size_t)sp * J.M + m) * J.N + cn];
     if (n < J.n_valid)
       J.gw[(size_t)m * J.n_valid + n] = (float)acc;
-    else
+    else if (J.gb)  // no bias: the ones column's sums are not a parameter
       J.gb[m] = (float)acc;
   }
 }
@@ -473,22 +477,20 @@ __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g,
 
 void launch_pack_backward(const NetDims& d, const float* w, uint16_t* wT, cudaStream_t st) {
   const BwdPack W = BwdPack::of(d);
-  const int H = d.hidden;
+  const NetOffsets o = d.offsets();
+  const int H = d.hidden, k2 = d.k2();
   const float* Wih[kMaxLayers] = {};
   const float* Whh[kMaxLayers] = {};
-  size_t off = 0;
   for (int l = 0; l < d.layers; ++l) {
-    const int c = l == 0 ? d.c_in : H;
-    Wih[l] = w + off;
-    Whh[l] = Wih[l] + (size_t)3 * H * c;
-    off += (size_t)3 * H * c + (size_t)3 * H * H + 6 * H;
+    Wih[l] = w + o.wih[l];
+    Whh[l] = w + o.whh[l];
   }
-  const float* W1 = w + off;
-  const float* W2 = W1 + (size_t)d.mlp * H + d.mlp;
   note_launch();
-  pack_transpose_kernel<<<64, 256, 0, st>>>(W2, d.mlp, 128, d.nout(), d.c_out, wT + W.w2t);
-  note_launch();
-  pack_transpose_kernel<<<64, 256, 0, st>>>(W1, H, H, 128, 128, wT + W.w1t);
+  pack_transpose_kernel<<<64, 256, 0, st>>>(w + o.w2, k2, k2, d.nout(), d.c_out, wT + W.w2t);
+  if (d.mlp) {
+    note_launch();
+    pack_transpose_kernel<<<64, 256, 0, st>>>(w + o.w1, H, H, 128, 128, wT + W.w1t);
+  }
   for (int l = 0; l < d.layers; ++l) {
     note_launch();
     pack_transpose_kernel<<<64, 256, 0, st>>>(Whh[l], H, H, 3 * H, 3 * H, wT + W.whh[l]);

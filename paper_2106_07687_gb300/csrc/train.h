@@ -8,16 +8,17 @@
 namespace dnnmg {
 
 // Element offsets of the transposed BF16 weight operands used by the
-// backward pass (B operands of dY W2, dA1 W1, dG_h W_hh of every layer and
-// dG_i W_ih of the layers above the first; m = hidden size).
+// backward pass (B operands of dY W2, dA1 W1 (with the hidden dense layer),
+// dG_h W_hh of every layer and dG_i W_ih of the layers above the first; m =
+// hidden size).
 struct BwdPack {
   size_t w2t, w1t, whh[kMaxLayers], wih[kMaxLayers], total;
   __host__ __device__ static BwdPack of(const NetDims& d) {
     BwdPack p{};
     const size_t H = d.hidden;
     size_t o = 0;
-    p.w2t = o; o += (size_t)128 * d.nout();  // [128][nout]  W2^T
-    p.w1t = o; o += H * 128;                 // [m][128]     W1^T
+    p.w2t = o; o += (size_t)d.k2() * d.nout();      // [K2][nout]   W2^T
+    p.w1t = o; o += d.mlp ? H * 128 : 0;             // [m][128]     W1^T (hidden dense layer)
     for (int l = 0; l < d.layers; ++l) {     // [m][3m]      W_hh^T
       p.whh[l] = o;
       o += H * 3 * H;

@@ -1,11 +1,13 @@
 // Streaming colour pass of the Vanka smoother for the large levels (FP32).
 //
-// One persistent block per pair of SM slots walks the colour's tiles of
-// 16 x 4 colour cells.  The 12 x 12 inverses of a tile (144 entries x 64
-// cells, 36 KB, the bulk of a pass's memory traffic) arrive in shared memory
-// by one tensor-memory-access (TMA) copy per tile, issued one tile ahead into
-// a second buffer, so that the copy of the next tile overlaps the staging,
-// operator rows and defects of the current one.  The arithmetic of a tile is
+// Persistent blocks (three per SM) walk the colour's tiles of 16 x 4 colour
+// cells.  The 12 x 12 inverses of a tile (144 entries x 64 cells, 36 KB, the
+// bulk of a pass's memory traffic) arrive in shared memory by one
+// tensor-memory-access (TMA) copy per tile, issued as soon as the previous
+// tile's products have read the buffer, so that the copy overlaps the
+// staging, operator rows and defects of the tile.  The pass is bound by the
+// latency of those dependent steps, not by bandwidth: one buffer and three
+// resident blocks (24 warps per SM) beat two buffers and two blocks.  The arithmetic of a tile is
 // that of vanka_pass_tile (the same staging, rows, defect sums and 12 x 12
 // products in the same order), so the result is bitwise the tiled pass's.
 //
@@ -34,8 +36,10 @@ constexpr int kStreamThreads = 4 * kQ;
 constexpr uint32_t kBoxBytes = 144u * kQ * sizeof(float);
 constexpr uint32_t kStreamPolls = 1u << 24;
 
+constexpr int kBufs = 1;
+
 struct StreamSmem {
-  float inv[2][144][kQ];  // inverse rows of two tiles, [entry][qy * 16 + qx]
+  float inv[kBufs][144][kQ];  // inverse rows of the tile, [entry][qy * 16 + qx]
   PassSmem<float, kQX, kQY> p;
   float d[kQ][13];        // the 12 defects of each colour cell (padded row)
   uint64_t bar[2];
@@ -57,7 +61,7 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-__global__ void __launch_bounds__(kStreamThreads, 2)
+__global__ void __launch_bounds__(kStreamThreads, kBufs == 1 ? 3 : 2)
     vanka_pass_stream_kernel(const __grid_constant__ CUtensorMap tmap, Grid g, Sten<float> s,
                              int colour, const float* __restrict__ b,
                              const float* __restrict__ xin, const float* __restrict__ vb,
@@ -86,9 +90,9 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
   bool failed = false;
   int it = 0;
   for (int tile = blockIdx.x; tile < nt && !failed; tile += gridDim.x, ++it) {
-    const int buf = it & 1;
+    const int buf = kBufs == 1 ? 0 : (it & 1);
     const int next = tile + gridDim.x;
-    if (next < nt) {  // the other buffer was released by the previous tile's last barrier
+    if (kBufs == 2 && next < nt) {  // the other buffer was released by the last barrier
       if (t == 0) issue(next, buf ^ 1);
       pending[buf ^ 1] = true;
     }
@@ -140,11 +144,15 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
       }
     }
     __syncthreads();  // the staged tile, the defects and this buffer are reused
+    if (kBufs == 1 && !failed && next < nt) {  // the buffer is free again: the next tile
+      if (t == 0) issue(next, 0);
+      pending[0] = true;
+    }
   }
   if (failed) {
     if (t == 0) atomicOr(status, 8);
     // copies still in flight land before the block's shared memory is released
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < kBufs; ++k)
       if (pending[k]) mbar_wait(&S.bar[k], parity[k], kStreamPolls);
   }
 }

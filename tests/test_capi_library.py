@@ -35,11 +35,11 @@ def test_default_config_and_argument_errors(lib):
     from paper_2106_07687_gb300 import dnnmg
     dnnmg.load()
     cfg = dnnmg.default_config()
-    assert ctypes.sizeof(cfg) == 160
+    assert ctypes.sizeof(cfg) == 168
     assert (cfg.nu, cfg.level_solve, cfg.level_coarse, cfg.gmres_m) == (0.01, 3, 1, 20)
     # fields late in the struct, written by the library: the ctypes layout matches the header
     assert (cfg.hidden, cfg.gru_layers, cfg.mlp_width, cfg.lps_mode) == (64, 2, 128, 0)
-    assert cfg.stream_pass == 0
+    assert (cfg.stream_pass, cfg.net_bias, cfg.net_inputs) == (0, 1, 0)
     assert (cfg.obstacle_i0, cfg.obstacle_j0) == (2, 1)
     L = dnnmg.load()
     assert L.dnnmg_default_config(None) == dnnmg.ERR_ARG
