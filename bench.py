@@ -41,7 +41,8 @@ NU_RANGE = (0.004, 0.01)                 # viscosities of the corpus and held-ou
 CORPUS_SEEDS = tuple(range(2000, 2032))  # 32 plain fine trajectories
 HELDOUT_SEEDS = tuple(range(2032, 2036))
 SPIN_STEPS, SPIN_DT, RELAX_STEPS = 50, 0.02, 4  # level-L spin-up to t = 1 s, fine relaxation
-CORPUS_T, TRAIN_ITERS, TRAIN_B, TRAIN_T = 16, 400, 16384, 10
+# training batch: 152 tiles of 128 sequences, one per SM of the GB300
+CORPUS_T, TRAIN_ITERS, TRAIN_B, TRAIN_T = 16, 400, 19456, 10
 LARGE_CORPUS_STEPS, LARGE_TRAIN_ITERS = 16, 100  # two replaced levels
 # plain MG(L+1) tolerance sweep: (Newton tolerance, FGMRES relative tolerance,
 # Newton cap, FGMRES cap); the last point is one Newton step with one V-cycle
@@ -1247,6 +1248,35 @@ def run_periodic(args):
     print(json.dumps(out))
 
 
+def run_dnnmg_steps(args):
+    """DNN-MG steps only (seeded weights, no corpus): --warmup untimed and
+    --steps timed steps of the default workload from the developed flow,
+    each inside an NVTX range "dnnmg_step" that kernel profilers select; a
+    short command for launch lists of the step."""
+    import numpy as np
+    import torch
+    from paper_2106_07687_gb300 import build, dnnmg as dn
+    import synthetic
+    build.build()
+    ob = synthetic.obstacle_block(1000)
+    ctx = dn.Context(level_solve=L, replaced_levels=1, precision=dn.MIXED, nu=NU, dt=DT,
+                     obstacle_i0=ob[0], obstacle_j0=ob[1])
+    ctx.set_weights(synthetic.random_weights(77, ctx.num_params(), 0.02).astype(np.float32))
+    x5, _ = spun_up_state(dn, NU, ob, dn.MIXED)
+    ctx.set_state(x5)
+    for _ in range(args.warmup):
+        ctx.step(dn.NET)
+    torch.cuda.synchronize()
+    stats = []
+    for _ in range(args.steps):
+        torch.cuda.nvtx.range_push("dnnmg_step")
+        stats.append(ctx.step(dn.NET))
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+    print(json.dumps({"mode": "dnnmg", "steps": args.steps,
+                      "ms": [round(s["ms"], 3) for s in stats], "plan": ctx.vcycle_plan()}))
+
+
 def run_coarse(args):
     """Coarse level only: --warmup + --steps refactorisations of the level-1
     Jacobian (assembly, cluster band LU, explicit inverse) through
@@ -1351,12 +1381,12 @@ def main():
                     help="with --split: 0 cooperative grid, 1 single cluster, -1 autotuned")
     ap.add_argument("--summarize-launches", metavar="CSV", default=None,
                     help="print the per-kernel table of an ncu launch list and exit")
-    ap.add_argument("--mode", choices=["step", "vcycle", "net", "coarse", "periodic"],
+    ap.add_argument("--mode", choices=["step", "vcycle", "net", "coarse", "periodic", "dnnmg"],
                     default="step",
                     help="vcycle: only V-cycles on --level; net: only the patch network; "
-                         "coarse: only coarse-level factorisations (short runs for kernel "
-                         "profilers); periodic: the long run to t = 10 s with the "
-                         "functionals over the last second")
+                         "coarse: only coarse-level factorisations; dnnmg: only DNN-MG steps "
+                         "(short runs for kernel profilers); periodic: the long run to "
+                         "t = 10 s with the functionals over the last second")
     args = ap.parse_args()
     if args.summarize_launches:
         summarize_launches(args.summarize_launches)
@@ -1371,6 +1401,9 @@ def main():
         return
     if args.mode == "coarse":
         run_coarse(args)
+        return
+    if args.mode == "dnnmg":
+        run_dnnmg_steps(args)
         return
     if args.mode == "periodic":
         run_periodic(args)

@@ -268,7 +268,10 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         const int nq = kx0 / 8;
         const bool vec = d.c_in % 8 == 0;  // input rows start on 16-byte boundaries
         for (int e = t; e < kTile * nq; e += kFwdThreads) {
-          const int r = e / nq, q = e % nq;
+          // inference: a thread's neighbours take the next chunks of the
+          // same row (coalesced loads); training: the same chunk of the next
+          // rows, so that the transposed copy is written coalesced
+          const int r = TRAIN ? e % kTile : e / nq, q = TRAIN ? e / kTile : e % nq;
           const int pr = tile * kTile + r;
           uint4 v = make_uint4(0, 0, 0, 0);
           const bool in = pr < P && q * 8 < d.c_in;

@@ -738,10 +738,11 @@ int dnnmg_ctx::train_grad_impl(const uint16_t* Xd, const float* Yd, int B, int T
     jobs[njobs++] = {dyT, tb.hT[NL - 1] + B, K, Kh, 128, H + 16, nd.c_out, H, H, grad + o.w2,
                      gb(o.b2)};
   }
-  // about two blocks per SM, at least four K chunks of 64 per block
+  // one wave: a block per SM at most (a block's 4-stage ring fills most of
+  // an SM's shared memory), at least four K chunks of 64 per block
   int tiles = 0;
   for (int q = 0; q < njobs; ++q) tiles += jobs[q].M / 128;
-  int splits = std::max(1, std::min((2 * tr_blocks_max + tiles - 1) / tiles, (int)(K / 256)));
+  int splits = std::max(1, std::min(tr_blocks_max / tiles, (int)(K / 256)));
   while (splits > 1 && wgrad_partials(jobs, njobs, (int)K, splits) > cpart_floats) --splits;
   if (launch_wgrad(jobs, njobs, (int)K, splits, cpart, net_status, st))
     return fail(DNNMG_ERR_ARG, "weight-gradient GEMM shape");
