@@ -496,6 +496,13 @@ int dnnmg_batch_linearize(dnnmg_batch* b);
  * x = 0: rhs, x are concatenated device vectors of `length` elements in the
  * batch precision (double for DNNMG_FP64, float for DNNMG_MIXED) */
 int dnnmg_batch_vcycle(dnnmg_batch* b, const void* rhs, void* x);
+/* One V(nu1, nu2) cycle (Sec. 2.2) of problem `inst` alone on its finest
+ * solved level, from x = 0, at the batch's current linearisation: rhs, x are
+ * that problem's own device vectors ([3][nn] of its level, batch precision),
+ * not the concatenated ones.  The instance form of dnnmg_vcycle.
+ * Errors: DNNMG_ERR_ARG (inst out of range), DNNMG_ERR_STATE (not
+ * linearised). */
+int dnnmg_batch_vcycle_inst(dnnmg_batch* b, int inst, const void* rhs, void* x);
 /* One time step of every problem; stats[0..n) (nullable) receive each
  * problem's counts and status (ms: the batch's step time).  Returns
  * DNNMG_OK or the first non-OK problem status. */

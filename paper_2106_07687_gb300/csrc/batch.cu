@@ -69,6 +69,7 @@ class Batch final : public BatchBase {
   long long offset_of(int p) const { return off_[p]; }
   int get_state(int p, double* x);
   int set_state(int p, const double* x);
+  int vcycle_one(int p, const void* b, void* x);
   int set_weights(const float* w);
   int set_feature_stats(const float* mean, const float* stdv);
   int get_fine_velocity(int p, double* v);
@@ -855,6 +856,28 @@ int Batch<T>::step(int mode, dnnmg_step_stats* stats) {
   return worst;
 }
 
+// One V-cycle of problem p alone: its right-hand side is placed at its
+// offset in the first FGMRES basis vector, the cycle runs with only p active
+// (the other problems' work is masked out) into the first search vector,
+// and p's part is copied out.  Both vectors are free between steps.
+template <typename T>
+int Batch<T>::vcycle_one(int p, const void* b, void* x) {
+  if (!linearized_) return fail(DNNMG_ERR_STATE, "vcycle before linearize");
+  sync_in();
+  const size_t n3 = 3 * (size_t)hl_[p][L_[p]].g.nn;
+  std::vector<int> one(n_, 0);
+  one[p] = 1;
+  const int* act = upload_mask(one, sel_);
+  T* bb = V_;
+  T* xx = Z_;
+  launch_fill<T>(xx, T(0), N_, st_);
+  cudaMemcpyAsync(bb + off_[p], b, sizeof(T) * n3, cudaMemcpyDeviceToDevice, st_);
+  vcycle_all(bb, xx, act);
+  cudaMemcpyAsync(x, xx + off_[p], sizeof(T) * n3, cudaMemcpyDeviceToDevice, st_);
+  cudaStreamSynchronize(st_);
+  return check("vcycle_one");
+}
+
 template <typename T>
 int Batch<T>::get_state(int p, double* x) {
   sync_in();
@@ -1010,6 +1033,11 @@ int dnnmg_batch_linearize(dnnmg_batch* b) {
 int dnnmg_batch_vcycle(dnnmg_batch* b, const void* rhs, void* x) {
   if (!b || !rhs || !x) return DNNMG_ERR_ARG;
   return b->eng->vcycle(rhs, x);
+}
+
+int dnnmg_batch_vcycle_inst(dnnmg_batch* b, int inst, const void* rhs, void* x) {
+  if (!b || !rhs || !x || inst < 0 || inst >= (int)b->cfg.size()) return DNNMG_ERR_ARG;
+  return with_engine(b, [&](auto& e) { return e.vcycle_one(inst, rhs, x); });
 }
 
 int dnnmg_batch_step(dnnmg_batch* b, int mode, dnnmg_step_stats* stats) {

@@ -106,6 +106,7 @@ def _declare(lib):
         "dnnmg_batch_set_state": ([P, ctypes.c_int, P], ctypes.c_int),
         "dnnmg_batch_linearize": ([P], ctypes.c_int),
         "dnnmg_batch_vcycle": ([P, P, P], ctypes.c_int),
+        "dnnmg_batch_vcycle_inst": ([P, ctypes.c_int, P, P], ctypes.c_int),
         "dnnmg_batch_step": ([P, ctypes.c_int, P], ctypes.c_int),
         "dnnmg_batch_set_weights": ([P, P], ctypes.c_int),
         "dnnmg_batch_set_feature_stats": ([P, P, P], ctypes.c_int),
@@ -464,6 +465,12 @@ class Batch:
         """b, x: concatenated cuda vectors of `length` elements (batch precision)."""
         x = torch.empty_like(b) if x is None else x
         self._check(self.lib.dnnmg_batch_vcycle(self.h, _ptr(b), _ptr(x)))
+        return x
+
+    def vcycle_inst(self, inst, b, x=None):
+        """One V-cycle of problem inst alone (b, x: its own cuda vectors)."""
+        x = torch.empty_like(b) if x is None else x
+        self._check(self.lib.dnnmg_batch_vcycle_inst(self.h, inst, _ptr(b), _ptr(x)))
         return x
 
     def step(self, mode=PLAIN):

@@ -62,6 +62,13 @@ def test_batched_vcycle_matches_single_contexts(precision, tol):
     for i, (ctx, L, b) in enumerate(singles):
         xs = ctx.vcycle(L, b)
         assert rel(_slice(xb, B, i).cpu().numpy(), xs.cpu().numpy()) < tol, i
+    # one problem alone (the instance form of the V-cycle) gives that
+    # problem's part of the batch cycle
+    for i, (ctx, L, b) in enumerate(singles):
+        xi = B.vcycle_inst(i, b.contiguous())
+        assert rel(xi.cpu().numpy(), _slice(xb, B, i).cpu().numpy()) < tol, i
+    with pytest.raises(dn.DnnmgError):
+        B.vcycle_inst(B.n, singles[0][2].contiguous())
     # the padding between problems stays zero
     mask = torch.ones(B.length, dtype=torch.bool, device="cuda")
     for i in range(B.n):
