@@ -56,6 +56,7 @@ class Solver final : public SolverBase {
     coarse_work_ = c_->mem.alloc<double>(coarse_work_doubles(g0));
     ainv_ = c_->mem.alloc<double>((size_t)9 * g0.nn * g0.nn);
     status_ = c_->mem.alloc<int>(4);
+    if (status_) cudaMemsetAsync(status_, 0, 4 * sizeof(int), st_);  // fresh memory is not zero
     m_ = cfg.gmres_m;
     n_ = 3 * (size_t)lv_[K_].g.nn;
     V_ = c_->mem.alloc<T>((m_ + 1) * n_);
@@ -333,6 +334,7 @@ class Solver final : public SolverBase {
     int st[4] = {0, 0, 0, 0};
     cudaMemcpyAsync(st, status_, sizeof(st), cudaMemcpyDeviceToHost, st_);
     if (cudaStreamSynchronize(st_) != cudaSuccess) return -1;
+    if (st[2]) cudaMemsetAsync(status_ + 2, 0, sizeof(int), st_);  // reported once
     return st[2];
   }
 

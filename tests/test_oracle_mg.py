@@ -22,6 +22,61 @@ def test_prolongation_reproduces_bilinears_and_restriction_is_adjoint():
     assert abs((P.T @ r) @ x - r @ (P @ x)) < 1e-12 * np.linalg.norm(r) * np.linalg.norm(x)
 
 
+def test_injection_samples_coinciding_nodes():
+    """Nodal injection (the linearisation point of the coarse levels) takes
+    the fine value at the coinciding node: a field sampled on the fine nodes
+    injects to the same field sampled on the coarse nodes, for any field,
+    component by component; after a bilinear prolongation it gives the
+    coarse vector back."""
+    coarse, fine = mesh.Level(2, obstacle=(2, 1)), mesh.Level(3, obstacle=(2, 1))
+    f = lambda X, Y: np.sin(3.1 * X + 0.7) * np.cos(2.3 * Y) + X * X * Y
+    g = lambda X, Y: np.exp(-X) + 5.0 * Y ** 3
+    Xf, Yf = fine.coords()
+    Xc, Yc = coarse.coords()
+    xf = np.concatenate([f(Xf, Yf).ravel(), g(Xf, Yf).ravel()])
+    xc = mg.inject(xf, coarse, fine, 2)
+    np.testing.assert_array_equal(xc, np.concatenate([f(Xc, Yc).ravel(), g(Xc, Yc).ravel()]))
+    rng = np.random.default_rng(9)
+    v = rng.standard_normal(coarse.nn)
+    Pn = mg.prolongation_nodes(coarse, fine)
+    np.testing.assert_allclose(mg.inject(Pn @ v, coarse, fine, 1), v, rtol=0, atol=1e-15)
+
+
+def test_vanka_update_of_a_lone_cell_scales_its_defect_by_one_minus_omega():
+    """A colour pass restricted to one cell changes x only on that cell's 12
+    DOFs, by omega A_c^-1 d_c, so the new defect on those DOFs is exactly
+    (1 - omega) d_c: pins the relaxation factor and that A_c is the block of
+    the global matrix on the cell's DOFs (a wrong omega, a transposed or
+    misindexed block would leave a different defect)."""
+    from oracle import fem
+    levels = mesh.hierarchy(2, obstacle=(2, 1))
+    prm = fem.Params(nu=0.01, dt=0.01)
+    rng = np.random.default_rng(12)
+    lev = levels[-1]
+    x0 = rng.standard_normal(lev.ndof) * 0.3
+    x0[lev.cons] = lev.dirichlet_values[lev.cons]
+    H = mg.Hierarchy(levels, x0, prm)
+    op = H.ops[-1]
+    b = rng.standard_normal(lev.ndof)
+    x = rng.standard_normal(lev.ndof)
+    cell = int(op.colour_cells[1][7])
+    saved = op.colour_cells
+    op.colour_cells = [np.array([cell])]
+    try:
+        dofs = lev.cell_dofs[cell]
+        free = lev.free[dofs]
+        d_old = (b - op.A @ x)[dofs]
+        for omega in (0.8, 0.5):
+            x1 = mg.vanka_sweep(op, b, x.copy(), omega)
+            d_new = (b - op.A @ x1)[dofs]
+            changed = np.flatnonzero(x1 != x)
+            assert set(changed) <= set(dofs.tolist())
+            np.testing.assert_allclose(d_new[free], (1 - omega) * d_old[free], rtol=1e-9,
+                                       atol=1e-12)
+    finally:
+        op.colour_cells = saved
+
+
 def test_vanka_colours_are_node_disjoint_and_cover_all_fluid_cells():
     lev = mesh.Level(2)
     op = mg.LevelOp(lev, np.zeros(lev.ndof), fem.Params(), coarsest=False)
