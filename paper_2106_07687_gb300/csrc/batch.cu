@@ -174,14 +174,14 @@ class Batch final : public BatchBase {
   dnnmg_config c0_{};
   std::vector<int> L_;
   std::vector<std::vector<HostLevel>> hl_;
-  std::vector<long long> off_, offF_;
-  long long N_ = 0, NF_ = 0;
+  std::vector<long long> off_, offF_, offM_;  // top, fine (L + R) and, for R = 2, L + 1
+  long long N_ = 0, NF_ = 0, NM_ = 0;
   DevMem mem_;
   std::vector<BLev<T>> hlev_;
   BView<T> v_{};
   // work lists
   std::map<int, Table> node0_, node1_, tiles_, setup_;
-  Table top_, fine_;
+  Table top_, fine_, mid_;
   int shape_ = 0;
   VecTab vt_{};
   // concatenated top-level vectors
@@ -218,7 +218,7 @@ class Batch final : public BatchBase {
   int P_ = 0;
   int *pinst_ = nullptr, *pcell_ = nullptr, *cell_patch_ = nullptr;
   double *xtF_ = nullptr, *ximpF_ = nullptr, *fF_ = nullptr, *rF_ = nullptr, *vcorr_ = nullptr,
-         *bF_ = nullptr, *bL_ = nullptr;
+         *bF_ = nullptr, *bL_ = nullptr, *midF_ = nullptr;  // midF_: level L + 1 (R = 2)
   uint16_t* X_ = nullptr;
   float *net_out_ = nullptr, *hid_ = nullptr, *feat_mean_ = nullptr, *feat_std_ = nullptr;
   bool have_vcorr_ = false, have_net_rhs_ = false;
@@ -245,7 +245,7 @@ int Batch<T>::init() {
                                  "obstacle and level_solve (and take the patch features as "
                                  "network inputs)");
   }
-  if (c0_.replaced_levels > 1) return fail(DNNMG_ERR_ARG, "batched DNN-MG supports replaced_levels <= 1");
+
   R_ = c0_.replaced_levels;
   m_ = c0_.gmres_m;
   L_.resize(n_);
@@ -253,7 +253,7 @@ int Batch<T>::init() {
     L_[p] = cf[p].level_solve;
     Lmax_ = std::max(Lmax_, L_[p]);
   }
-  nL_ = Lmax_ + 2;
+  nL_ = Lmax_ + std::max(2, R_ + 1);
   if (cudaStreamCreateWithFlags(&st_, cudaStreamNonBlocking) != cudaSuccess)
     return fail(DNNMG_ERR_CUDA, "stream creation failed");
   if (cudaMallocHost(&h_pin_, (size_t)n_ * (2 * m_ + 4) * sizeof(double) + 4096) != cudaSuccess ||
@@ -280,12 +280,17 @@ int Batch<T>::init() {
   // ---- offsets of the concatenated vectors
   off_.resize(n_);
   offF_.assign(n_, 0);
+  offM_.assign(n_, 0);
   for (int p = 0; p < n_; ++p) {
     off_[p] = N_;
     N_ += pad_to(3LL * hl_[p][L_[p]].g.nn, kVB);
     if (R_) {
       offF_[p] = NF_;
-      NF_ += pad_to(3LL * hl_[p][L_[p] + 1].g.nn, kVB);
+      NF_ += pad_to(3LL * hl_[p][L_[p] + R_].g.nn, kVB);
+    }
+    if (R_ == 2) {
+      offM_[p] = NM_;
+      NM_ += pad_to(3LL * hl_[p][L_[p] + 1].g.nn, kVB);
     }
   }
   // ---- per-level records and constants
@@ -302,8 +307,8 @@ int Batch<T>::init() {
       hsT[(size_t)p * nL_ + k] = make_sten<T>(g.h, c);
       hs64[(size_t)p * nL_ + k] = make_sten<double>(g.h, c);
       hsx[(size_t)p * nL_ + k] = make_explicit_sten(g.h, c);
-      if (k > L_[p]) {  // DNN-MG fine level: geometry and offset only
-        l.off = offF_[p];
+      if (k > L_[p]) {  // DNN-MG levels: geometry and offset only
+        l.off = k == L_[p] + R_ ? offF_[p] : offM_[p];
         continue;
       }
       const size_t n3 = 3 * (size_t)g.nn, n2 = 2 * (size_t)g.nn;
@@ -393,10 +398,12 @@ int Batch<T>::init() {
   }
   top_ = own_table(0);
   // ---- DNN-MG state
-  if (R_ == 1) {
-    fine_ = own_table(1);
-    nd_.c_in = 40;
-    nd_.c_out = 18;
+  if (R_ >= 1) {
+    fine_ = own_table(R_);
+    if (R_ == 2) mid_ = own_table(1);
+    const int K = (1 << R_) + 1;
+    nd_.c_in = 4 * K * K + 4;
+    nd_.c_out = 2 * K * K;
     nd_.hidden = c0_.hidden;
     nd_.layers = c0_.gru_layers;
     nd_.mlp = c0_.mlp_width;
@@ -427,6 +434,7 @@ int Batch<T>::init() {
       rF_ = mem_.alloc<double>(NF_);
       vcorr_ = mem_.alloc<double>(NF_);
       bF_ = mem_.alloc<double>(NF_);
+      if (R_ == 2) midF_ = mem_.alloc<double>(NM_);
       bL_ = mem_.alloc<double>(N_);
       X_ = mem_.alloc<uint16_t>((size_t)P_ * nd_.c_in);
       net_out_ = mem_.alloc<float>((size_t)P_ * nd_.c_out);
@@ -473,7 +481,7 @@ int Batch<T>::init() {
   cudaMemsetAsync(Z_, 0, sizeof(T) * (size_t)m_ * N_, st_);
   for (T* a : {wsol_, rT_, rcur_, vbJ_}) cudaMemsetAsync(a, 0, sizeof(T) * N_, st_);
   for (double* a : {xold64_, f64_, r64_}) cudaMemsetAsync(a, 0, sizeof(double) * N_, st_);
-  if (R_ == 1 && net_ok_)
+  if (R_ >= 1 && net_ok_)
     for (double* a : {xtF_, ximpF_, fF_, rF_, vcorr_, bF_}) cudaMemsetAsync(a, 0, sizeof(double) * NF_, st_);
   for (int p = 0; p < n_; ++p) {
     const std::vector<double> x0 = initial_state(hl_[p][L_[p]].g);
@@ -775,26 +783,42 @@ int Batch<T>::newton(const std::vector<int>& mask, std::vector<dnnmg_step_stats>
 template <typename T>
 void Batch<T>::correction() {
   const Work wf = fine_.w();
+  const int K = (1 << R_) + 1;
   const int pr = prof_.begin(DNNMG_STAGE_NETWORK, Lmax_, st_);
-  if (!have_vcorr_) bk_prolong_state<T>(v_, xold64_, vcorr_, 2, 1, wf, nullptr, st_);
-  bk_prolong_state<T>(v_, x64_, xtF_, 3, 0, wf, nullptr, st_);       // P
-  bk_old_rhs<T>(v_, 1, vcorr_, fF_, wf, nullptr, st_);
-  bk_copy_impose<T>(v_, 1, xtF_, ximpF_, wf, nullptr, st_);
-  bk_residual64<T>(v_, 1, ximpF_, fF_, rF_, wf, nullptr, st_);       // input: fine residual
-  bk_gather<T>(v_, P_, pinst_, pcell_, xtF_, rF_, feat_mean_, feat_std_, X_, st_);
+  // P once per replaced level (through level L + 1 when two are replaced)
+  auto prolong_up = [&](const double* xc, double* xf, int ncomp, int zero_p) {
+    if (R_ == 2) {
+      bk_prolong_state<T>(v_, xc, midF_, ncomp, 0, 1, mid_.w(), nullptr, st_);
+      bk_prolong_state<T>(v_, midF_, xf, ncomp, zero_p, 2, wf, nullptr, st_);
+    } else {
+      bk_prolong_state<T>(v_, xc, xf, ncomp, zero_p, 1, wf, nullptr, st_);
+    }
+  };
+  if (!have_vcorr_) prolong_up(xold64_, vcorr_, 2, 1);
+  prolong_up(x64_, xtF_, 3, 0);                                        // P
+  bk_old_rhs<T>(v_, R_, vcorr_, fF_, wf, nullptr, st_);
+  bk_copy_impose<T>(v_, R_, xtF_, ximpF_, wf, nullptr, st_);
+  bk_residual64<T>(v_, R_, ximpF_, fF_, rF_, wf, nullptr, st_);      // input: fine residual
+  bk_gather<T>(v_, K, P_, pinst_, pcell_, xtF_, rF_, feat_mean_, feat_std_, X_, st_);
   launch_patchnet_forward(nd_, pk_, X_, hid_, hid_, net_out_, P_, net_status_, st_);  // network
-  bk_scatter<T>(v_, cell_patch_, net_out_, nd_.c_out, xtF_, vcorr_, wf, nullptr, st_);
-  bk_old_rhs<T>(v_, 1, vcorr_, bF_, wf, nullptr, st_);                // Rhs
+  bk_scatter<T>(v_, K, cell_patch_, net_out_, nd_.c_out, xtF_, vcorr_, wf, nullptr, st_);
+  bk_old_rhs<T>(v_, R_, vcorr_, bF_, wf, nullptr, st_);               // Rhs
   cudaMemsetAsync(bL_, 0, sizeof(double) * N_, st_);
-  bk_restrict_full<T>(v_, bF_, bL_, 2, top_.w(), nullptr, st_);      // R
+  if (R_ == 2) {                                                       // R, twice
+    cudaMemsetAsync(midF_, 0, sizeof(double) * NM_, st_);
+    bk_restrict_full<T>(v_, bF_, midF_, 2, 2, mid_.w(), nullptr, st_);
+    bk_restrict_full<T>(v_, midF_, bL_, 2, 1, top_.w(), nullptr, st_);
+  } else {
+    bk_restrict_full<T>(v_, bF_, bL_, 2, 1, top_.w(), nullptr, st_);  // R
+  }
   prof_.end(pr, st_);
   have_vcorr_ = have_net_rhs_ = true;
 }
 
 template <typename T>
 int Batch<T>::step(int mode, dnnmg_step_stats* stats) {
-  if (mode == DNNMG_NET && (R_ != 1 || !net_ok_))
-    return fail(DNNMG_ERR_ARG, "DNN-MG steps need replaced_levels = 1 and the default network");
+  if (mode == DNNMG_NET && (R_ < 1 || !net_ok_))
+    return fail(DNNMG_ERR_ARG, "DNN-MG steps need replaced_levels 1 or 2 and the default network");
   sync_in();
   std::vector<dnnmg_step_stats> s(n_);
   for (auto& x : s) x = dnnmg_step_stats{};
@@ -926,7 +950,7 @@ template <typename T>
 int Batch<T>::get_fine_velocity(int p, double* v) {
   if (!have_vcorr_) return fail(DNNMG_ERR_STATE, "no DNN-MG step taken yet");
   sync_in();
-  cudaMemcpyAsync(v, vcorr_ + offF_[p], sizeof(double) * 2 * hl_[p][L_[p] + 1].g.nn,
+  cudaMemcpyAsync(v, vcorr_ + offF_[p], sizeof(double) * 2 * hl_[p][L_[p] + R_].g.nn,
                   cudaMemcpyDeviceToDevice, st_);
   cudaStreamSynchronize(st_);
   return check("get_fine_velocity");

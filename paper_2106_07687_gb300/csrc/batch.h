@@ -146,18 +146,21 @@ void bk_givens(int nprob, int m, double* H, double* cs, double* sn, double* gv,
                int* its, int maxit, int* gact, cudaStream_t st);
 void bk_backsolve(int nprob, int m, const double* H, const double* gv, const int* kcnt, double* y,
                   const int* act, cudaStream_t st);
+// P from level L + dlf - 1 to level L + dlf (work: node blocks of L + dlf)
 template <typename T>
 void bk_prolong_state(const BView<T>& v, const double* xc, double* xf, int ncomp, int zero_p,
+                      int dlf, Work wk, const int* act, cudaStream_t st);
+// R = P^T from level L + dlf to level L + dlf - 1 (work: node blocks of L + dlf - 1)
+template <typename T>
+void bk_restrict_full(const BView<T>& v, const double* bf, double* bc, int ncomp, int dlf,
                       Work wk, const int* act, cudaStream_t st);
+// patch inputs of K x K-node patches (K = 3 or 5) on level L + (K == 3 ? 1 : 2)
 template <typename T>
-void bk_restrict_full(const BView<T>& v, const double* bf, double* bc, int ncomp, Work wk,
-                      const int* act, cudaStream_t st);
+void bk_gather(const BView<T>& v, int K, int P, const int* pinst, const int* pcell,
+               const double* xt, const double* r, const float* mean, const float* stdv,
+               uint16_t* X, cudaStream_t st);
 template <typename T>
-void bk_gather(const BView<T>& v, int P, const int* pinst, const int* pcell, const double* xt,
-               const double* r, const float* mean, const float* stdv, uint16_t* X,
-               cudaStream_t st);
-template <typename T>
-void bk_scatter(const BView<T>& v, const int* cell_patch, const float* out, int c_out,
+void bk_scatter(const BView<T>& v, int K, const int* cell_patch, const float* out, int c_out,
                 const double* xt, double* vcorr, Work wk, const int* act, cudaStream_t st);
 // tile shape (cells per block) of pass shape s
 void pass_shape_dims(int s, int* tcx, int* tcy);

@@ -460,63 +460,69 @@ __global__ void bbacksolve_kernel(int nprob, int m, const double* __restrict__ H
 
 // ---------------------------------------------------------------- DNN-MG
 
-// work: fine-level node blocks; xc in the top layout, xf in the fine layout
+// work: node blocks of level L + dlf; xc in the layout of level L + dlf - 1
+// (the top layout for dlf = 1), xf in the layout of level L + dlf
 template <typename T>
 __global__ void __launch_bounds__(kNB)
     bprolong_state_kernel(BView<T> v, const double* __restrict__ xc, double* __restrict__ xf,
-                          int ncomp, int zero_p, const int2* __restrict__ work,
+                          int ncomp, int zero_p, int dlf, const int2* __restrict__ work,
                           const int* __restrict__ act) {
   const int2 wk = work[blockIdx.x];
   if (masked(act, wk.x)) return;
-  const BLev<T> F = own_level(v, wk.x, 1), C = own_level(v, wk.x, 0);
+  const BLev<T> F = own_level(v, wk.x, dlf), C = own_level(v, wk.x, dlf - 1);
   const int n = wk.y * kNB + threadIdx.x;
   if (n >= F.g.nn) return;
   prolong_state_node(F.g, C.g, xc + C.off, xf + F.off, ncomp, n % F.g.nnx, n / F.g.nnx);
   if (zero_p) xf[F.off + 2 * F.g.nn + n] = 0.0;
 }
 
-// work: top-level node blocks; bf in the fine layout, bc in the top layout
+// work: node blocks of level L + dlf - 1; bf in the layout of level L + dlf,
+// bc in the layout of level L + dlf - 1
 template <typename T>
 __global__ void __launch_bounds__(kNB)
     brestrict_full_kernel(BView<T> v, const double* __restrict__ bf, double* __restrict__ bc,
-                          int ncomp, const int2* __restrict__ work, const int* __restrict__ act) {
+                          int ncomp, int dlf, const int2* __restrict__ work,
+                          const int* __restrict__ act) {
   const int2 wk = work[blockIdx.x];
   if (masked(act, wk.x)) return;
-  const BLev<T> F = own_level(v, wk.x, 1), C = own_level(v, wk.x, 0);
+  const BLev<T> F = own_level(v, wk.x, dlf), C = own_level(v, wk.x, dlf - 1);
   const int n = wk.y * kNB + threadIdx.x;
   if (n >= C.g.nn) return;
   restrict_node<double, false>(F.g, C.g, bf + F.off, bc + C.off, ncomp, n % C.g.nnx,
                                n / C.g.nnx);
 }
 
-template <typename T>
+// patches of K x K fine nodes: K = 3 with one replaced level, 5 with two
+template <typename T, int K>
 __global__ void bgather_kernel(BView<T> v, int P, const int* __restrict__ pinst,
                                const int* __restrict__ pcell, const double* __restrict__ xt,
                                const double* __restrict__ r, const float* __restrict__ mean,
                                const float* __restrict__ stdv, uint16_t* __restrict__ X) {
+  constexpr int kR = K == 3 ? 1 : 2, kCin = 4 * K * K + 4;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= P) return;
   const int p = pinst[q];
   const BPar pr = v.par[p];
   const BLev<T>& L = lev_of(v, p, pr.L);
-  const BLev<T>& F = lev_of(v, p, pr.L + 1);
-  gather_patch<false, 3>(L.g, F.g, pcell[q], xt + F.off, r + F.off, mean, stdv, pr.nu, pr.dt,
-                      X + (size_t)q * 40, nullptr);
+  const BLev<T>& F = lev_of(v, p, pr.L + kR);
+  gather_patch<false, K>(L.g, F.g, pcell[q], xt + F.off, r + F.off, mean, stdv, pr.nu, pr.dt,
+                         X + (size_t)q * kCin, nullptr);
 }
 
-template <typename T>
+template <typename T, int K>
 __global__ void __launch_bounds__(kNB)
     bscatter_kernel(BView<T> v, const int* __restrict__ cell_patch, const float* __restrict__ out,
                     int c_out, const double* __restrict__ xt, double* __restrict__ vcorr,
                     const int2* __restrict__ work, const int* __restrict__ act) {
+  constexpr int kR = K == 3 ? 1 : 2;
   const int2 wk = work[blockIdx.x];
   if (masked(act, wk.x)) return;
   const BPar pr = v.par[wk.x];
-  const BLev<T> F = lev_of(v, wk.x, pr.L + 1), L = lev_of(v, wk.x, pr.L);
+  const BLev<T> F = lev_of(v, wk.x, pr.L + kR), L = lev_of(v, wk.x, pr.L);
   const int n = wk.y * kNB + threadIdx.x;
   if (n >= F.g.nn) return;
-  scatter_node<3>(L.g, F.g, cell_patch + pr.coff, out, c_out, xt + F.off, vcorr + F.off,
-               n % F.g.nnx, n / F.g.nnx);
+  scatter_node<K>(L.g, F.g, cell_patch + pr.coff, out, c_out, xt + F.off, vcorr + F.off,
+                  n % F.g.nnx, n / F.g.nnx);
 }
 
 template <typename T, int TCX, int TCY>
@@ -730,29 +736,36 @@ void bk_backsolve(int nprob, int m, const double* H, const double* gv, const int
 
 template <typename T>
 void bk_prolong_state(const BView<T>& v, const double* xc, double* xf, int ncomp, int zero_p,
+                      int dlf, Work w, const int* act, cudaStream_t st) {
+  NODE_LAUNCH(bprolong_state_kernel<T>, v, xc, xf, ncomp, zero_p, dlf);
+}
+
+template <typename T>
+void bk_restrict_full(const BView<T>& v, const double* bf, double* bc, int ncomp, int dlf,
                       Work w, const int* act, cudaStream_t st) {
-  NODE_LAUNCH(bprolong_state_kernel<T>, v, xc, xf, ncomp, zero_p);
+  NODE_LAUNCH(brestrict_full_kernel<T>, v, bf, bc, ncomp, dlf);
 }
 
 template <typename T>
-void bk_restrict_full(const BView<T>& v, const double* bf, double* bc, int ncomp, Work w,
-                      const int* act, cudaStream_t st) {
-  NODE_LAUNCH(brestrict_full_kernel<T>, v, bf, bc, ncomp);
-}
-
-template <typename T>
-void bk_gather(const BView<T>& v, int P, const int* pinst, const int* pcell, const double* xt,
-               const double* r, const float* mean, const float* stdv, uint16_t* X,
-               cudaStream_t st) {
+void bk_gather(const BView<T>& v, int K, int P, const int* pinst, const int* pcell,
+               const double* xt, const double* r, const float* mean, const float* stdv,
+               uint16_t* X, cudaStream_t st) {
   if (P <= 0) return;
   note_launch();
-  bgather_kernel<T><<<cdiv(P, 128), 128, 0, st>>>(v, P, pinst, pcell, xt, r, mean, stdv, X);
+  if (K == 5)
+    bgather_kernel<T, 5><<<cdiv(P, 128), 128, 0, st>>>(v, P, pinst, pcell, xt, r, mean, stdv, X);
+  else
+    bgather_kernel<T, 3><<<cdiv(P, 128), 128, 0, st>>>(v, P, pinst, pcell, xt, r, mean, stdv, X);
 }
 
 template <typename T>
-void bk_scatter(const BView<T>& v, const int* cell_patch, const float* out, int c_out,
+void bk_scatter(const BView<T>& v, int K, const int* cell_patch, const float* out, int c_out,
                 const double* xt, double* vcorr, Work w, const int* act, cudaStream_t st) {
-  NODE_LAUNCH(bscatter_kernel<T>, v, cell_patch, out, c_out, xt, vcorr);
+  if (K == 5) {
+    NODE_LAUNCH((bscatter_kernel<T, 5>), v, cell_patch, out, c_out, xt, vcorr);
+  } else {
+    NODE_LAUNCH((bscatter_kernel<T, 3>), v, cell_patch, out, c_out, xt, vcorr);
+  }
 }
 
 #undef NODE_LAUNCH
@@ -792,15 +805,15 @@ void bk_scatter(const BView<T>& v, const int* cell_patch, const float* out, int 
                             const int*, cudaStream_t);                                          \
   template void bk_combine<T, T>(const T*, size_t, const int*, const double*, int, double, T*,  \
                                  const VecTab&, const int*, cudaStream_t);                      \
-  template void bk_prolong_state<T>(const BView<T>&, const double*, double*, int, int, Work,    \
+  template void bk_prolong_state<T>(const BView<T>&, const double*, double*, int, int, int,    \
+                                    Work, const int*, cudaStream_t);                            \
+  template void bk_restrict_full<T>(const BView<T>&, const double*, double*, int, int, Work,    \
                                     const int*, cudaStream_t);                                  \
-  template void bk_restrict_full<T>(const BView<T>&, const double*, double*, int, Work,         \
-                                    const int*, cudaStream_t);                                  \
-  template void bk_gather<T>(const BView<T>&, int, const int*, const int*, const double*,       \
+  template void bk_gather<T>(const BView<T>&, int, int, const int*, const int*, const double*,  \
                              const double*, const float*, const float*, uint16_t*,              \
                              cudaStream_t);                                                     \
-  template void bk_scatter<T>(const BView<T>&, const int*, const float*, int, const double*,    \
-                              double*, Work, const int*, cudaStream_t);
+  template void bk_scatter<T>(const BView<T>&, int, const int*, const float*, int,              \
+                              const double*, double*, Work, const int*, cudaStream_t);
 BK_INST(float)
 BK_INST(double)
 #undef BK_INST

@@ -104,19 +104,24 @@ def test_batched_plain_steps_match_single_contexts_and_oracle(precision):
         assert rel(B.get_state(0).cpu().numpy(), x0) < tol, n
 
 
-def test_batched_dnnmg_steps_match_single_contexts():
+@pytest.mark.parametrize("replaced", [1, 2])
+def test_batched_dnnmg_steps_match_single_contexts(replaced):
     """DNN-MG steps with a random network (shared weights and feature
     statistics): the corrected fine velocities and the level-L states of all
-    problems equal those of single contexts."""
+    problems equal those of single contexts; with one replaced level (3x3-node
+    patches, 40 inputs) and with two (5x5-node patches, 104 inputs, P and R
+    applied twice)."""
     dn = lib()
-    cfgs = _cfgs(dn, 0)
+    cfgs = _cfgs(dn, 0, replaced_levels=replaced)
     B = dn.Batch(cfgs)
     ctxs = [dn.Context(cfg=c) for c in cfgs]
     npar = ctxs[0].num_params()
+    c_in = ctxs[0].net_dims()[0]
+    assert c_in == (40 if replaced == 1 else 104)
     w = synthetic.random_weights(11, npar, 0.05).astype(np.float32)
     rng = np.random.default_rng(5)
-    mean = rng.normal(0, 0.1, 40).astype(np.float32)
-    std = rng.uniform(0.5, 2.0, 40).astype(np.float32)
+    mean = rng.normal(0, 0.1, c_in).astype(np.float32)
+    std = rng.uniform(0.5, 2.0, c_in).astype(np.float32)
     B.set_weights(w)
     B.set_feature_stats(mean, std)
     for ctx in ctxs:
