@@ -24,7 +24,6 @@ workload) on the host cores.
 """
 import argparse
 import hashlib
-import glob
 import json
 import os
 import subprocess
@@ -52,20 +51,32 @@ WORKLOAD = ("DNN-MG time step: multigrid on the 512x128 channel (level 5, 198,53
             "network on 1024x256 (level 6, 61,440 patches, GRU 2x64 + MLP 128, BF16), nu=0.0065, "
             "dt=0.005, mixed FP32/FP64, developed flow (t ~ 1 s)")
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
-# capture, keyed by the hash of the library sources it was taken on; after
-# any source change the figure no longer describes the kernel and is not
-# reported (traffic = null) until a new capture is entered here.
-NCU_TRAFFIC = {}
+# capture, keyed by the hash of the kernel's sources (source_hash) at the
+# capture; after a change of those sources the figure no longer describes
+# the kernel and is not reported (traffic = null) until a new capture is
+# entered here.
+NCU_TRAFFIC = {"fb5c2716fa946855": {"vcycle_kernel<float>@split5": 60208384 + 1144576}}
 L2_BYTES = 129 * 2 ** 20
 
 
-def source_hash():
-    """First 16 hex digits of the SHA-256 of the library's CUDA/C++ sources
-    and headers (sorted by name): the build a traffic capture belongs to."""
+def source_hash(unit="vcycle.cu"):
+    """First 16 hex digits of the SHA-256 of one translation unit of the
+    library and every header it includes from the project (recursively,
+    sorted by name): the sources a kernel's traffic capture belongs to."""
+    csrc = os.path.join(ROOT, "paper_2106_07687_gb300", "csrc")
+    found, todo = set(), [os.path.join(csrc, unit)]
+    while todo:
+        f = os.path.normpath(todo.pop())
+        if f in found or not os.path.exists(f):
+            continue
+        found.add(f)
+        with open(f) as fh:
+            for line in fh:
+                line = line.strip()
+                if line.startswith("#include \""):
+                    todo.append(os.path.join(os.path.dirname(f), line.split('"')[1]))
     h = hashlib.sha256()
-    pats = ("paper_2106_07687_gb300/csrc/*.cu", "paper_2106_07687_gb300/csrc/*.cuh",
-            "paper_2106_07687_gb300/csrc/*.h", "include/*.h")
-    for f in sorted(x for pat in pats for x in glob.glob(os.path.join(ROOT, pat))):
+    for f in sorted(found):
         h.update(os.path.relpath(f, ROOT).encode())
         with open(f, "rb") as fh:
             h.update(fh.read())
@@ -1085,7 +1096,7 @@ def run_vcycles(args):
     kw = {} if args.split < 0 else dict(persistent_vcycle=args.split,
                                         persistent_mode=args.split_mode)
     ctx = dn.Context(level_solve=lev, precision=dn.MIXED, nu=0.005, dt=DT, obstacle_i0=ob[0],
-                     obstacle_j0=ob[1], **kw)
+                     obstacle_j0=ob[1], stream_pass=args.stream_pass, **kw)
     x = ctx.get_state()
     ctx.linearize(x)
     b = torch.from_numpy(synthetic.random_vector(7, ndof(lev))).float().cuda()
@@ -1402,6 +1413,9 @@ def main():
     ap.add_argument("--level", type=int, default=6, help="--mode vcycle: level")
     ap.add_argument("--split", type=int, default=-1,
                     help="fixed persistent V-cycle split level (-1: autotuned; 0: none)")
+    ap.add_argument("--stream-pass", type=int, default=0, choices=[-1, 0, 1],
+                    help="--mode vcycle: streaming colour pass never (-1), autotuned (0), "
+                         "always (1)")
     ap.add_argument("--split-mode", type=int, default=-1,
                     help="with --split: 0 cooperative grid, 1 single cluster, -1 autotuned")
     ap.add_argument("--summarize-launches", metavar="CSV", default=None,

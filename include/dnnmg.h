@@ -511,8 +511,8 @@ int dnnmg_batch_step(dnnmg_batch* b, int mode, dnnmg_step_stats* stats);
  * feature standardisation (host, C_in floats each) */
 int dnnmg_batch_set_weights(dnnmg_batch* b, const float* w);
 int dnnmg_batch_set_feature_stats(dnnmg_batch* b, const float* mean, const float* std);
-/* corrected level L+1 velocity of problem `inst` after a DNN-MG step
- * ([2][..] of level L+1, device) */
+/* corrected fine velocity of problem `inst` after a DNN-MG step ([2][..] of
+ * level L + replaced_levels, device) */
 int dnnmg_batch_get_fine_velocity(dnnmg_batch* b, int inst, double* v);
 /* on != 0 (default): replay FGMRES iterations as CUDA graphs */
 int dnnmg_batch_graphs(dnnmg_batch* b, int on);

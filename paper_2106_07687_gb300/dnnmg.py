@@ -491,7 +491,8 @@ class Batch:
 
     def get_fine_velocity(self, inst):
         lev, _ = self.layout(inst)
-        v = torch.empty(2 * level_nodes(lev + 1), dtype=torch.float64, device="cuda")
+        v = torch.empty(2 * level_nodes(lev + self.cfgs[0].replaced_levels), dtype=torch.float64,
+                        device="cuda")
         self._check(self.lib.dnnmg_batch_get_fine_velocity(self.h, inst, _ptr(v)))
         return v
 
