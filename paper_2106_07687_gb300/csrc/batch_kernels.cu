@@ -261,8 +261,9 @@ __global__ void __launch_bounds__(kSetupThreads)
   const BLev<T> L = lev_of(v, wk.x, k);
   load_const(ss, v.sT[(size_t)wk.x * v.nL + k]);
   const int nsb = cdiv(vanka_slots(L.g), kSetupCells);
+  __shared__ SetupSmem<T> W[kSetupCells];
   vanka_setup_cell<T>(L.g, ss, L.vb, L.inv, status + wk.x, wk.y / nsb,
-                      (wk.y % nsb) * kSetupCells + threadIdx.x / 16);
+                      (wk.y % nsb) * kSetupCells + threadIdx.x / 16, W[threadIdx.x / 16]);
 }
 
 template <typename T>

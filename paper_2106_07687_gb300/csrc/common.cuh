@@ -58,6 +58,19 @@ __device__ __forceinline__ void shape_at(int q, T phi[4], T dx[4], T dy[4]) {
   }
 }
 
+// The same values for one local node b (a runtime index: selects, not an
+// indexed local array).
+template <typename T>
+__device__ __forceinline__ void shape_one(int q, int b, T& phi, T& dx, T& dy) {
+  const T gx = (q & 1) ? T(kG1) : T(kG0);
+  const T gy = (q >> 1) ? T(kG1) : T(kG0);
+  const T fx = (b & 1) ? gx : T(1) - gx;
+  const T fy = (b >> 1) ? gy : T(1) - gy;
+  phi = fx * fy;
+  dx = ((b & 1) ? T(1) : T(-1)) * fy;
+  dy = fx * ((b >> 1) ? T(1) : T(-1));
+}
+
 // Rows of local node a of one fluid cell, added to (ru, rv, rp).
 //   NONLIN = true : A(x) with x = (wu, wv, wp) (Eqs. 4-5), convection N(w)w.
 //   NONLIN = false: A'(vbar) w (Eq. 6), convection N(vbar)w + (w.grad)vbar.
@@ -218,10 +231,11 @@ __device__ __forceinline__ void elem_pair(const Sten<T>& s, const GaussData<T>& 
   T N = 0, Cuu = 0, Cuv = 0, Cvu = 0, Cvv = 0;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    T phi[4], dx[4], dy[4];
-    shape_at<T>(q, phi, dx, dy);
-    const T pa = phi[al], pab = phi[al] * phi[be];
-    N += pa * (gd.Bu[q] * dx[be] + gd.Bv[q] * dy[be]);
+    T pa, dxa, dya, pb, dxb, dyb;
+    shape_one<T>(q, al, pa, dxa, dya);
+    shape_one<T>(q, be, pb, dxb, dyb);
+    const T pab = pa * pb;
+    N += pa * (gd.Bu[q] * dxb + gd.Bv[q] * dyb);
     Cuu += pab * gd.Bux[q];
     Cuv += pab * gd.Buy[q];
     Cvu += pab * gd.Bvx[q];

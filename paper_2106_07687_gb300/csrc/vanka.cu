@@ -14,8 +14,9 @@ template <typename T>
 __global__ void __launch_bounds__(kSetupThreads)
     vanka_setup_kernel(Grid g, Sten<T> s, const T* __restrict__ vb, T* __restrict__ inv,
                        int* status) {
+  __shared__ SetupSmem<T> W[kSetupCells];
   vanka_setup_cell<T>(g, s, vb, inv, status, blockIdx.y,
-                      blockIdx.x * kSetupCells + threadIdx.x / 16);
+                      blockIdx.x * kSetupCells + threadIdx.x / 16, W[threadIdx.x / 16]);
 }
 
 template <typename T, int TCX, int TCY>

@@ -26,20 +26,36 @@ __device__ __forceinline__ T vk_abs(T v) {
   return v < T(0) ? -v : v;
 }
 
+// Shared memory of one cell's setup (one half-warp): the Gauss-point data of
+// the 9 cells around it and the 3x3 element blocks of its 36 (element, a, b)
+// triples.
+template <typename T>
+struct SetupSmem {
+  T gd[9][24];  // Bu, Bv, Bux, Buy, Bvx, Bvy at the 4 Gauss points
+  T J[36][9];   // J[c][c2] of triple a * 9 + m (see vanka_setup_cell)
+  int ok[9];    // the element is a fluid cell of the level
+};
+
 // Inverse of the local 12x12 block of the cell of `slot` in `colour`,
 // computed by a group of 16 consecutive lanes (a half-warp; every lane of it
-// calls this with the same cell).  Lane r < 12 assembles row r = (c, a) of
-// the block (component c of local node a) from the cells around node a and
-// keeps row r of [A | I] in registers; Gauss-Jordan elimination with partial
-// pivoting then runs across the lanes: at step k the unused lane with the
-// largest |A[.][k]| (lowest lane on ties) is the pivot row, its normalised
-// row is broadcast by shuffles and every other lane eliminates column k.
-// Rows are never swapped; the lane that pivoted on column k ends with row k
-// of the inverse in its right half.
+// calls this with the same cell and its own W).  The block's entry between
+// local nodes a and b sums the element Jacobians of the cells that hold both
+// nodes: the 4 cells around a (b = a), the 2 cells on the edge a-b, or the
+// cell itself (a, b diagonal) -- 36 (element, a, b) triples over the 9 cells
+// around the cell.  Lanes 0..8 form the Gauss-point data of one of those 9
+// cells each, the 16 lanes then form the triples' 3x3 element blocks, and
+// lane r < 12 sums row r = (c, a) of the block (component c of local node a)
+// in the order of the cells around node a (rows first) and keeps it in
+// registers.  Gauss-Jordan elimination with partial pivoting then runs
+// across the lanes: at step k the unused lane with the largest |A[.][k]|
+// (lowest lane on ties) is the pivot row, its normalised row is broadcast by
+// shuffles and every other lane eliminates column k.  Rows are never
+// swapped; the lane that pivoted on column k ends with row k of the inverse.
 template <typename T>
 __device__ __forceinline__ void vanka_setup_cell(const Grid& g, const Sten<T>& s,
                                                  const T* __restrict__ vb, T* __restrict__ inv,
-                                                 int* status, int colour, int slot) {
+                                                 int* status, int colour, int slot,
+                                                 SetupSmem<T>& W) {
   const int cx = colour & 1, cy = colour >> 1;
   const int sx = g.nx / 2 + 1, pitch = vanka_pitch(g);
   const int nslots = vanka_slots(g);
@@ -52,34 +68,90 @@ __device__ __forceinline__ void vanka_setup_cell(const Grid& g, const Sten<T>& s
   const int c = r >> 2, a = r & 3;
   const int ai = ci + (a & 1), aj = cj + (a >> 1);       // node a
 
-  T A[24];
-#pragma unroll
-  for (int k = 0; k < 24; ++k) A[k] = T(0);
-  // element contributions of the (up to) 4 cells around node a, in the
-  // order of the cells around the block's cell (rows first)
-#pragma unroll
-  for (int ty = 0; ty < 2; ++ty)
-#pragma unroll
-    for (int tx = 0; tx < 2; ++tx) {
-      const int Tx = ai - 1 + tx, Ty = aj - 1 + ty;
-      if (Tx < 0 || Ty < 0 || Tx >= g.nx || Ty >= g.ny || g.solid[Ty * g.nx + Tx]) continue;
+  // ---- Gauss-point data of cell e = ex + 3 ey at (ci - 1 + ex, cj - 1 + ey)
+  if (lane < 9) {
+    const int Tx = ci - 1 + lane % 3, Ty = cj - 1 + lane / 3;
+    const bool ev = Tx >= 0 && Ty >= 0 && Tx < g.nx && Ty < g.ny && !g.solid[Ty * g.nx + Tx];
+    W.ok[lane] = ev;
+    if (ev) {
       T bu[4], bv[4];
       load_cell<T, false>(g, vb, Tx, Ty, 0, bu);
       load_cell<T, false>(g, vb + g.nn, Tx, Ty, 0, bv);
       GaussData<T> gd;
       gauss_data<T>(bu, bv, gd);
-      const int al = (ai - Tx) + 2 * (aj - Ty);
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int bex = ci + (b & 1) - Tx, bey = cj + (b >> 1) - Ty;
-        if (bex < 0 || bex > 1 || bey < 0 || bey > 1) continue;
-        T J[3][3];
-        elem_pair<T>(s, gd, al, bex + 2 * bey, J);
-#pragma unroll
-        for (int c2 = 0; c2 < 3; ++c2)  // row c of J, selected without indexing
-          A[c2 * 4 + b] += c == 0 ? J[0][c2] : (c == 1 ? J[1][c2] : J[2][c2]);
+      for (int q = 0; q < 4; ++q) {
+        W.gd[lane][q] = gd.Bu[q];
+        W.gd[lane][4 + q] = gd.Bv[q];
+        W.gd[lane][8 + q] = gd.Bux[q];
+        W.gd[lane][12 + q] = gd.Buy[q];
+        W.gd[lane][16 + q] = gd.Bvx[q];
+        W.gd[lane][20 + q] = gd.Bvy[q];
       }
     }
+  }
+  __syncwarp(mask);
+  // ---- element blocks of triple t = a * 9 + m: node b = a ^ d and the cell
+  // (ex, ey) holding both, with m < 4: d = 0, the 4 cells around a (rows
+  // first); m = 4, 5: d = 1, the 2 cells on the x edge (bottom first);
+  // m = 6, 7: d = 2, the 2 cells on the y edge (left first); m = 8: d = 3,
+  // the cell itself
+  for (int t = lane; t < 36; t += 16) {
+    const int ta = t / 9, m = t % 9;
+    const int tax = ta & 1, tay = ta >> 1;
+    int d, ex, ey;
+    if (m < 4) {
+      d = 0, ex = tax + (m & 1), ey = tay + (m >> 1);
+    } else if (m < 6) {
+      d = 1, ex = 1, ey = tay + (m - 4);
+    } else if (m < 8) {
+      d = 2, ex = tax + (m - 6), ey = 1;
+    } else {
+      d = 3, ex = 1, ey = 1;
+    }
+    const int tb = ta ^ d, tbx = tb & 1, tby = tb >> 1;
+    const int e = ex + 3 * ey;
+    T J[3][3];
+    if (W.ok[e]) {
+      GaussData<T> gd;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        gd.Bu[q] = W.gd[e][q];
+        gd.Bv[q] = W.gd[e][4 + q];
+        gd.Bux[q] = W.gd[e][8 + q];
+        gd.Buy[q] = W.gd[e][12 + q];
+        gd.Bvx[q] = W.gd[e][16 + q];
+        gd.Bvy[q] = W.gd[e][20 + q];
+      }
+      elem_pair<T>(s, gd, (tax + 1 - ex) + 2 * (tay + 1 - ey), (tbx + 1 - ex) + 2 * (tby + 1 - ey),
+                   J);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) W.J[t][k] = J[k / 3][k % 3];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) W.J[t][k] = T(0);
+    }
+  }
+  __syncwarp(mask);
+  // ---- row r: column block b sums the triples of (a, b), d = a ^ b: the
+  // 4, 2, 2 or 1 consecutive ones from a * 9 + 0, 4, 6 or 8
+  T A[24];
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const int d = a ^ b;
+    const int t0 = a * 9 + (d == 0 ? 0 : (d == 1 ? 4 : (d == 2 ? 6 : 8)));
+    const int cnt = d == 0 ? 4 : (d == 3 ? 1 : 2);
+#pragma unroll
+    for (int c2 = 0; c2 < 3; ++c2) A[c2 * 4 + b] = T(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k < cnt) {
+#pragma unroll
+        for (int c2 = 0; c2 < 3; ++c2) A[c2 * 4 + b] += W.J[t0 + k][c * 3 + c2];
+      }
+  }
+#pragma unroll
+  for (int k = 12; k < 24; ++k) A[k] = T(0);
   // local projection stabilisation (pressure rows) of the patches
   // containing node pairs
   if (c == 2) {
@@ -113,9 +185,16 @@ __device__ __forceinline__ void vanka_setup_cell(const Grid& g, const Sten<T>& s
 #pragma unroll
   for (int k = 0; k < 12; ++k) A[12 + k] = k == r ? T(1) : T(0);
 
-  // Gauss-Jordan elimination with partial pivoting across the lanes
+  // Gauss-Jordan elimination with partial pivoting across the lanes, in
+  // place: the right half of [A | I] is kept in the columns already
+  // eliminated.  Before step k, the identity column of an unused row p is
+  // still e_p, so after the step it holds 1 / A[p][k] in row p and
+  // -A[i][k] / A[p][k] elsewhere, which column k receives; columns j < k hold
+  // the identity column of the row that pivoted on column j (pcol[j]).  The
+  // arithmetic is that of the explicit form, entry by entry.
   bool used = lane >= 12, ok = true;
   int my_col = 0;
+  int pcol[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
     T best = used ? T(-1) : vk_abs(A[k]);
@@ -126,17 +205,19 @@ __device__ __forceinline__ void vanka_setup_cell(const Grid& g, const Sten<T>& s
       const int op = __shfl_xor_sync(mask, p, o, 16);
       if (ob > best || (ob == best && op < p)) best = ob, p = op;
     }
+    pcol[k] = p;
     ok = ok && best > T(0);  // the same in every lane of the group
     if (ok) {
       const T ip = T(1) / __shfl_sync(mask, A[k], p, 16);
       const T f = A[k];
       const bool piv = lane == p;
-      // columns before k are zero in the pivot row (eliminated earlier)
 #pragma unroll
-      for (int cc = k; cc < 24; ++cc) {
+      for (int cc = 0; cc < 12; ++cc) {
+        if (cc == k) continue;
         const T pn = __shfl_sync(mask, A[cc], p, 16) * ip;  // normalised pivot row
         A[cc] = piv ? pn : A[cc] - f * pn;
       }
+      A[k] = piv ? ip : T(0) - f * ip;
       if (piv) used = true, my_col = k;
     }
   }
@@ -144,10 +225,11 @@ __device__ __forceinline__ void vanka_setup_cell(const Grid& g, const Sten<T>& s
     if (lane == 0) atomicOr(status, 1);
   }
   if (lane >= 12) return;
+  // row my_col of the inverse; entry j is its column pcol[j]
   T* out = inv + (size_t)colour * 144 * nslots + slot;
 #pragma unroll
-  for (int cc = 0; cc < 12; ++cc)
-    out[(size_t)(my_col * 12 + cc) * nslots] = ok ? A[12 + cc] : T(0);
+  for (int j = 0; j < 12; ++j)
+    out[(size_t)(my_col * 12 + pcol[j]) * nslots] = ok ? A[j] : T(0);
 }
 
 // Resident blocks per SM the pass kernels ask the compiler for: FP32 passes
