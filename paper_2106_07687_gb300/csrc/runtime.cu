@@ -130,7 +130,7 @@ class Solver final : public SolverBase {
 
   // Linearise every level at the velocity of x64 (level L): nodal injection
   // down the hierarchy, Vanka inverses, coarse LU and inverse.
-  int linearize(const double* x64, bool coarse, bool precond) override {
+  int linearize(const double* x64, bool coarse, bool precond, bool report) override {
     // the Jacobian of the FGMRES matvec always follows the current iterate
     launch_cast<double, T>(x64, vbJ_, 2 * (size_t)lv_[K_].g.nn, st_);
     linearized_j_ = true;
@@ -139,7 +139,7 @@ class Solver final : public SolverBase {
                     cudaMemcpyDeviceToDevice, st_);
     for (int k = K_; k > 0; --k)
       launch_inject<double>(lv_[k].g, lv_[k - 1].g, lv_[k].vb64, lv_[k - 1].vb64, 2, st_);
-    cudaMemsetAsync(status_, 0, sizeof(int), st_);
+    if (report || !tuned_) cudaMemsetAsync(status_, 0, sizeof(int), st_);
     for (int k = 0; k <= K_; ++k)
       launch_cast<double, T>(lv_[k].vb64, lv_[k].vb, 2 * (size_t)lv_[k].g.nn, st_);
     // the levels' setups are independent and each leaves most of the GPU
@@ -165,6 +165,10 @@ class Solver final : public SolverBase {
       launch_coarse_factor(lv_[0].g, lv_[0].s64, lv_[0].vb64, coarse_work_, ainv_, status_, st_);
       c_->prof.end(p, st_);
       coarse_done_ = true;
+    }
+    if (!report && tuned_) {
+      linearized_ = true;
+      return c_->check("linearize");
     }
     int status = 0;
     cudaMemcpyAsync(c_->h_scalars, status_, sizeof(int), cudaMemcpyDeviceToHost, st_);
@@ -207,14 +211,12 @@ class Solver final : public SolverBase {
     bool done = false;
     while (!done) {
       launch_multidot<T>(rcur_, n_, 1, rcur_, n_, partials_, hcol_, st_);
+      // |r|^2 of the first cycle travels to the host beside the first
+      // iteration's residual estimate (one synchronisation for both)
+      bool first = target < 0;
+      if (first)
+        cudaMemcpyAsync(c_->h_scalars + 1, hcol_, sizeof(double), cudaMemcpyDeviceToHost, st_);
       launch_gmres_start<T>(rcur_, hcol_, V_, gv_, n_, st_);
-      if (target < 0) {
-        double b2 = 0;
-        if (int rc = read_scalar(hcol_, &b2)) return rc;
-        target = cfg.gmres_rtol * std::sqrt(b2);
-        if (!(b2 > 0)) break;
-        if (!std::isfinite(b2)) return c_->fail(DNNMG_ERR_NUMERICAL, "non-finite residual");
-      }
       int k = 0;
       for (int j = 0; j < m_; ++j) {
         T* vj = V_ + (size_t)j * n_;
@@ -241,12 +243,26 @@ class Solver final : public SolverBase {
         k = j + 1;
         double res = 0;
         if (int rc = read_scalar(y_ + m_, &res)) return rc;
+        if (first) {
+          first = false;
+          double b2 = 0;
+          std::memcpy(&b2, c_->h_scalars + 1, sizeof(double));
+          if (!(b2 > 0)) {  // zero right-hand side: no update (the iteration is discarded)
+            its = 0;
+            k = 0;
+            done = true;
+            break;
+          }
+          if (!std::isfinite(b2)) return c_->fail(DNNMG_ERR_NUMERICAL, "non-finite residual");
+          target = cfg.gmres_rtol * std::sqrt(b2);
+        }
         if (!std::isfinite(res)) return c_->fail(DNNMG_ERR_NUMERICAL, "non-finite GMRES residual");
         if (res <= target || its >= cfg.gmres_maxit) {
           done = true;
           break;
         }
       }
+      if (k == 0) break;
       launch_backsolve(H_, m_ + 1, gv_, k, y_, st_);
       launch_combine<T, T>(Z_, n_, k, y_, 1.0, wsol_, n_, st_);
       if (!done) {
@@ -330,13 +346,15 @@ class Solver final : public SolverBase {
     const int k = level - lv_[0].level;
     return k >= 0 && k <= K_ ? (lv_[k].stream ? kPassStream : shape_[k]) : -1;
   }
-  int device_status() override {
+  int device_status(int* setup) override {
     int st[4] = {0, 0, 0, 0};
     cudaMemcpyAsync(st, status_, sizeof(st), cudaMemcpyDeviceToHost, st_);
     if (cudaStreamSynchronize(st_) != cudaSuccess) return -1;
     if (st[2]) cudaMemsetAsync(status_ + 2, 0, sizeof(int), st_);  // reported once
+    if (setup) *setup = st[0];
     return st[2];
   }
+  void clear_setup_status() override { cudaMemsetAsync(status_, 0, sizeof(int), st_); }
 
   // Autotuner, run once at the first linearisation: (1) the tile shape of
   // the colour pass on every level, by timing four passes per shape; (2) the
@@ -1190,6 +1208,8 @@ int dnnmg_ctx::newton(const double* f, dnnmg_step_stats* s) {
   double nrm = norm64(r64, n3);
   s->res0 = nrm;
   int it = 0, gits = 0;
+  // the linearisations' singularity flags are read once, after the loop
+  solver->clear_setup_status();
   while (nrm > cfg.newton_tol && it < cfg.newton_max) {
     if (!std::isfinite(nrm)) return fail(DNNMG_ERR_NUMERICAL, "non-finite Newton residual");
     // the coarse-level factorisation is refreshed at the first Newton step of
@@ -1198,7 +1218,7 @@ int dnnmg_ctx::newton(const double* f, dnnmg_step_stats* s) {
     // with precond_lag the multigrid preconditioner keeps the linearisation
     // of the step's first Newton iteration; the matvec always uses the current one
     const bool precond = it == 0 || !cfg.precond_lag;
-    if (int rc = solver->linearize(x64, refresh, precond)) return rc;
+    if (int rc = solver->linearize(x64, refresh, precond, false)) return rc;
     int its = 0;
     if (int rc = solver->solve(r64, x64, cfg.eps_damp, &its)) return rc;
     gits += its;
@@ -1211,8 +1231,11 @@ int dnnmg_ctx::newton(const double* f, dnnmg_step_stats* s) {
   s->newton_its = it;
   s->gmres_its = gits;
   s->res_final = nrm;
-  if (const int ds = solver->device_status())
+  int setup = 0;
+  if (const int ds = solver->device_status(&setup))
     return ds < 0 ? check("newton") : fail(DNNMG_ERR_TIMEOUT, "a colour pass's inverse copy timed out");
+  if (setup & 1) return fail(DNNMG_ERR_NUMERICAL, "singular local Vanka matrix");
+  if (setup & 2) return fail(DNNMG_ERR_NUMERICAL, "singular coarse-level matrix");
   if (!std::isfinite(nrm)) return fail(DNNMG_ERR_NUMERICAL, "non-finite Newton residual");
   if (nrm > cfg.newton_tol) return DNNMG_ERR_NOT_CONVERGED;
   return check("newton");

@@ -118,8 +118,10 @@ class SolverBase {
  public:
   virtual ~SolverBase() = default;
   // coarse = false keeps the coarse-level factorisation of the previous call;
-  // precond = false only updates the Jacobian of the FGMRES matvec
-  virtual int linearize(const double* x64, bool coarse, bool precond) = 0;
+  // precond = false only updates the Jacobian of the FGMRES matvec.  With
+  // report = false the setups' singularity flags are not read back (no host
+  // synchronisation); they accumulate on the device until device_status.
+  virtual int linearize(const double* x64, bool coarse, bool precond, bool report = true) = 0;
   virtual int apply(int k, const void* w, void* y) = 0;
   virtual int vcycle(int k, const void* b, void* x) = 0;
   // FGMRES on the finest level: w64 += eps * A'^{-1} r64 (approximately)
@@ -134,8 +136,11 @@ class SolverBase {
   // recompute every level's stencil constants from the context's nu and dt
   // (after a change of either); the next linearisation refactors the coarse level
   virtual void set_physics() = 0;
-  // device-side error bits of the smoother kernels (0: none; -1: CUDA error)
-  virtual int device_status() = 0;
+  // device-side error bits of the smoother kernels (0: none; -1: CUDA error);
+  // *setup receives the setups' singularity bits accumulated since
+  // clear_setup_status (1: a local Vanka matrix, 2: the coarse matrix)
+  virtual int device_status(int* setup = nullptr) = 0;
+  virtual void clear_setup_status() = 0;
 };
 
 std::unique_ptr<SolverBase> make_solver(struct ::dnnmg_ctx* ctx);
