@@ -73,7 +73,8 @@ typedef struct dnnmg_config {
   double gmres_rtol;  /* relative residual reduction of FGMRES per Newton step */
   double omega;       /* damping of the Vanka update */
   double eps_damp;    /* Newton damping epsilon (the damped update of Algorithm 1) */
-  int32_t obstacle_i0, obstacle_j0; /* lower-left level-0 cell of the 2x2 solid block, -1 = none */
+  int32_t obstacle_i0, obstacle_j0; /* lower-left cell, on level obstacle_level, of the
+                                       solid square of 2x2 level-0 cells; -1 = none */
   int32_t level_solve;     /* finest level L solved by multigrid */
   int32_t level_coarse;    /* coarsest multigrid level (direct solve), >= 1 */
   int32_t replaced_levels; /* levels above L replaced by the network (1 or 2; 0 = none) */
@@ -118,6 +119,20 @@ typedef struct dnnmg_config {
                               other value (1..127) makes a network for dnnmg_patch_infer
                               and training only (DNN-MG steps and samples need the
                               patch features); Table 1's networks have 51 */
+  int32_t obstacle_level;  /* level whose cells place the obstacle square (Sec. 2.1 gives no
+                              geometry): 0 = level-0 cells, 1 <= i0 <= 13, j0 = 1 (default);
+                              1 = snapped to level-1 cells (the square is 4x4 of them),
+                              2 <= i0 <= 27, 1 <= j0 <= 3, and j0 = 2 or i0 odd (the other
+                              positions leave a one-cell fluid strip along the inflow or
+                              a wall with no free velocity node on level 1, and the
+                              coarse problem is singular there).  At odd level-1 offsets the 2h
+                              stabilisation patches of level 1 along the square are partly
+                              solid (their term integrates over the fluid cells only); the
+                              coarse direct solve assembles them, and dnnmg_apply refuses
+                              level 1 there; level 0 keeps only its fully covered cells.
+                              Levels >= 2 see the square exactly, as whole patches.  Single
+                              contexts only (not the batched engine nor the allocation-free
+                              call). */
 } dnnmg_config;
 
 /* Per-step statistics returned by dnnmg_step(). */

@@ -13,9 +13,10 @@ Readings:
   * pi is bilinear interpolation on the patch mesh of width 2h (2x2 blocks
     of cells, i.e. the cells of the parent level), so kappa = id - pi
     vanishes on bilinear p.  The integral runs over the fluid cells of each
-    patch; on level >= 1 a patch is all fluid or all solid because the
-    obstacle is made of level-0 cells, and on level 0 (only used inside the
-    preconditioner) a patch may be partly solid;
+    patch; on level >= 1 a patch is all fluid or all solid when the
+    obstacle is made of level-0 cells, and on level 0 a patch may be partly
+    solid; with an obstacle of level-1 cells at odd level-1 offsets the
+    patches of level 1 (the coarse level of the cycle) are partly solid too;
   * all integrals use 2x2 Gauss quadrature per cell, exact here for mass,
     stiffness, divergence and the Q1 convection term on square cells;
   * constrained DOFs (velocity Dirichlet nodes, fixed pressures) get identity

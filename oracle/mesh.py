@@ -8,7 +8,10 @@ Readings (the paper gives no geometry for this channel):
   * domain [0,4]x[0,1], level l has (16*2^l) x (4*2^l) square cells of
     width h_l = 0.25 * 2^-l;
   * the obstacle is a 2x2 block of level-0 cells, so it is resolved exactly
-    on every level;
+    on every level; or (obstacle = (i0, j0, 1)) the same square snapped to
+    level-1 cells (4x4 of them from cell (i0, j0)), resolved exactly on
+    levels >= 1, where a level-0 cell is solid only when all four of its
+    level-1 children are (the coarser level sees a smaller obstacle);
   * velocity Dirichlet nodes: the inflow x=0 (u = 6y(1-y), v = 0), the walls
     y=0 and y=1 and every node of a solid cell (no slip, also the obstacle
     interior); the outflow x=4 is do-nothing (natural);
@@ -39,14 +42,25 @@ class Level:
         self.ndof = 3 * self.nn
         self.obstacle = obstacle
 
-        ci = np.arange(self.nx) >> ell
-        cj = np.arange(self.ny) >> ell
         if obstacle is None:
             solid = np.zeros((self.ny, self.nx), dtype=bool)
         else:
-            i0, j0 = obstacle
-            solid = ((ci[None, :] >= i0) & (ci[None, :] < i0 + 2)
-                     & (cj[:, None] >= j0) & (cj[:, None] < j0 + 2))
+            i0, j0 = obstacle[0], obstacle[1]
+            olev = obstacle[2] if len(obstacle) > 2 else 0
+            B = 2 << olev                     # the square's width in level-olev cells
+            if ell >= olev:
+                # the level-olev cell containing each cell of this level
+                ci = np.arange(self.nx) >> (ell - olev)
+                cj = np.arange(self.ny) >> (ell - olev)
+                solid = ((ci[None, :] >= i0) & (ci[None, :] < i0 + B)
+                         & (cj[:, None] >= j0) & (cj[:, None] < j0 + B))
+            else:
+                # the descendants [s i, s (i + 1)) on level olev all in the square
+                sc = 1 << (olev - ell)
+                ci = np.arange(self.nx)
+                cj = np.arange(self.ny)
+                solid = ((sc * ci[None, :] >= i0) & (sc * (ci[None, :] + 1) <= i0 + B)
+                         & (sc * cj[:, None] >= j0) & (sc * (cj[:, None] + 1) <= j0 + B))
         self.cell_solid = solid
 
         # A node touches the (up to four) cells around it.

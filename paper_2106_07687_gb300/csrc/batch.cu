@@ -232,6 +232,8 @@ int Batch<T>::init() {
   for (int p = 0; p < n_; ++p) {
     std::string e;
     if (int rc = check_config(cf[p], e)) return fail(rc, "problem " + std::to_string(p) + ": " + e);
+    if (cf[p].obstacle_level != 0)
+      return fail(DNNMG_ERR_ARG, "problem " + std::to_string(p) + ": only level-0 obstacle blocks");
     const dnnmg_config& c = cf[p];
     if (c.precision != c0_.precision || c.replaced_levels != c0_.replaced_levels ||
         c.gmres_m != c0_.gmres_m || c.gmres_maxit != c0_.gmres_maxit ||
@@ -266,7 +268,7 @@ int Batch<T>::init() {
   for (int p = 0; p < n_; ++p) {
     const int top = L_[p] + R_;
     for (int l = 0; l <= top; ++l) {
-      hl_[p].push_back(make_level(l, cf[p].obstacle_i0, cf[p].obstacle_j0));
+      hl_[p].push_back(make_level(l, cf[p].obstacle_i0, cf[p].obstacle_j0, 0));
       Grid& g = hl_[p].back().g;
       uint8_t* s = mem_.alloc<uint8_t>((size_t)g.nx * g.ny);
       uint8_t* f = mem_.alloc<uint8_t>(g.nn);

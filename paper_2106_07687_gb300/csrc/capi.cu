@@ -12,6 +12,7 @@
 #include "../../include/dnnmg.h"
 #include "kernels.h"
 #include "dnnmg_step.h"
+#include "coarse_body.cuh"
 #include "runtime.h"
 
 using namespace dnnmg;
@@ -20,9 +21,12 @@ namespace dnnmg {
 
 // ---------------------------------------------------------------------------
 // Geometry of one level (host side), Sec. 2.1 / Eq. 2 with the channel
-// reading: obstacle = 2x2 block of level-0 cells, no-slip on walls and on
-// every node of a solid cell, parabolic inflow at x = 0, do-nothing at x = 4.
-HostLevel make_level(int ell, int oi0, int oj0) {
+// reading: obstacle = square of 2x2 level-0 cells whose lower-left corner
+// is the corner of cell (oi0, oj0) of level olev (0 or 1; on level 1 it is
+// 4x4 cells), no-slip on walls and on every node of a solid cell, parabolic
+// inflow at x = 0, do-nothing at x = 4.  A cell of a level coarser than olev
+// is solid when all its descendants on level olev are.
+HostLevel make_level(int ell, int oi0, int oj0, int olev) {
   HostLevel L;
   L.ell = ell;
   Grid& g = L.g;
@@ -36,8 +40,16 @@ HostLevel make_level(int ell, int oi0, int oj0) {
   if (oi0 >= 0)
     for (int j = 0; j < g.ny; ++j)
       for (int i = 0; i < g.nx; ++i) {
-        const int I = i >> ell, J = j >> ell;
-        if (I >= oi0 && I < oi0 + 2 && J >= oj0 && J < oj0 + 2) L.solid[(size_t)j * g.nx + i] = 1;
+        const int B = 2 << olev;  // the block's width in level-olev cells
+        bool in;
+        if (ell >= olev) {
+          const int I = i >> (ell - olev), J = j >> (ell - olev);
+          in = I >= oi0 && I < oi0 + B && J >= oj0 && J < oj0 + B;
+        } else {  // the cell's descendants on level olev: [i s, (i + 1) s)
+          const int sc = 1 << (olev - ell);
+          in = i * sc >= oi0 && (i + 1) * sc <= oi0 + B && j * sc >= oj0 && (j + 1) * sc <= oj0 + B;
+        }
+        if (in) L.solid[(size_t)j * g.nx + i] = 1;
       }
   L.flags.assign(g.nn, 0);
   for (int j = 0; j <= g.ny; ++j)
@@ -143,6 +155,70 @@ Sten<T> make_sten(double h, const dnnmg_config& c) {
   return s;
 }
 
+// The stabilisation of each cell of a 2h patch on the patch's 3x3 nodes
+// (the summands of S9 above, cell c = cx + 2 cy): a part-solid patch sums the
+// pieces of its fluid cells (its integral runs over those cells only).
+PatchPieces make_patch_pieces(double h, const dnnmg_config& c) {
+  const double m1[2][2] = {{h / 3, h / 6}, {h / 6, h / 3}};
+  const double k1[2][2] = {{1 / h, -1 / h}, {-1 / h, 1 / h}};
+  double K[4][4];
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) {
+      const int ax = a & 1, ay = a >> 1, bx = b & 1, by = b >> 1;
+      K[a][b] = k1[ax][bx] * m1[ay][by] + m1[ax][bx] * k1[ay][by];
+    }
+  double kap[9][9] = {};
+  for (int m = 0; m < 9; ++m) {
+    const int sx = m % 3, sy = m / 3;
+    kap[m][m] += 1.0;
+    for (int cy = 0; cy <= 2; cy += 2)
+      for (int cx = 0; cx <= 2; cx += 2)
+        kap[m][cx + 3 * cy] -= (1.0 - std::abs(sx - cx) / 2.0) * (1.0 - std::abs(sy - cy) / 2.0);
+  }
+  const double alpha = c.alpha0 * h * h / c.nu;
+  PatchPieces pp{};
+  for (int cc = 0; cc < 4; ++cc) {
+    const int cx = cc & 1, cy = cc >> 1;
+    double Kc[9][9] = {}, Mc[9][9] = {};
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) {
+        const int ma = (cx + (a & 1)) + 3 * (cy + (a >> 1));
+        const int mb = (cx + (b & 1)) + 3 * (cy + (b >> 1));
+        Kc[ma][mb] += K[a][b];
+        const double ca = ((a & 1) == (a >> 1)) ? 1.0 : -1.0;
+        const double cb = ((b & 1) == (b >> 1)) ? 1.0 : -1.0;
+        Mc[ma][mb] += alpha / 6.0 * ca * cb;
+      }
+    for (int m = 0; m < 9; ++m)
+      for (int n = 0; n < 9; ++n) {
+        double v;
+        if (c.lps_mode == 1) {
+          v = alpha * Kc[m][n];
+        } else if (c.lps_mode == 2) {
+          v = Mc[m][n];
+        } else {
+          double acc = 0;
+          for (int p = 0; p < 9; ++p)
+            for (int q = 0; q < 9; ++q) acc += kap[p][m] * Kc[p][q] * kap[q][n];
+          v = alpha * acc;
+        }
+        pp.S[cc][m * 9 + n] = v;
+      }
+  }
+  return pp;
+}
+
+bool part_solid_patches(const HostLevel& L) {
+  const Grid& g = L.g;
+  for (int J = 0; J < g.ny / 2; ++J)
+    for (int I = 0; I < g.nx / 2; ++I) {
+      const size_t c = (size_t)(2 * J) * g.nx + 2 * I;
+      const int n = L.solid[c] + L.solid[c + 1] + L.solid[c + g.nx] + L.solid[c + g.nx + 1];
+      if (n != 0 && n != 4) return true;
+    }
+  return false;
+}
+
 // Constants of the explicit old-time bracket nu (grad v, grad phi) + (v.grad v, phi)
 // of the theta-scheme: E = nu K, no mass, no pressure, no LPS, Gauss weight h^2/4.
 Sten<double> make_explicit_sten(double h, const dnnmg_config& c) {
@@ -213,6 +289,7 @@ int dnnmg_default_config(dnnmg_config* c) {
   c->stream_pass = 0;
   c->net_bias = 1;
   c->net_inputs = 0;
+  c->obstacle_level = 0;
   return DNNMG_OK;
 }
 

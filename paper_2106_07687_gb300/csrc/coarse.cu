@@ -12,8 +12,17 @@ namespace {
 
 // One thread per row of the coarse Jacobian.
 __global__ void assemble_kernel(Grid g, Sten<double> s, const double* __restrict__ vb,
-                                double* __restrict__ ab) {
-  assemble_row(g, s, vb, ab, blockIdx.x * blockDim.x + threadIdx.x);
+                                double* __restrict__ ab, const __grid_constant__ PatchPieces pp,
+                                int use_pieces) {
+  assemble_row(g, s, vb, ab, blockIdx.x * blockDim.x + threadIdx.x, use_pieces ? &pp : nullptr);
+}
+
+void launch_assemble(const Grid& g, const Sten<double>& s, const double* vb, double* ab,
+                     const PatchPieces* pp, cudaStream_t st) {
+  static const PatchPieces none{};
+  note_launch();
+  assemble_kernel<<<cdiv(band_of(g).n, 128), 128, 0, st>>>(g, s, vb, ab, pp ? *pp : none,
+                                                            pp ? 1 : 0);
 }
 
 __global__ void __launch_bounds__(kLUThreads)
@@ -317,9 +326,7 @@ size_t coarse_band_doubles(const Grid& g) {
 
 void launch_coarse_lu(const Grid& g, const Sten<double>& s, const double* vb, double* band,
                       int* piv, int* status, cudaStream_t st) {
-  const Band bd = band_of(g);
-  note_launch();
-  assemble_kernel<<<cdiv(bd.n, 128), 128, 0, st>>>(g, s, vb, band);
+  launch_assemble(g, s, vb, band, nullptr, st);
   launch_band_lu(g, band, piv, status, st);
 }
 
@@ -344,12 +351,11 @@ size_t coarse_work_doubles(const Grid& g) {
 }
 
 void launch_coarse_factor(const Grid& g, const Sten<double>& s, const double* vb, double* work,
-                          double* Ainv, int* status, cudaStream_t st) {
+                          double* Ainv, int* status, cudaStream_t st, const PatchPieces* pp) {
   const Band bd = band_of(g);
   double* ab = work;
   int* piv = reinterpret_cast<int*>(work + (size_t)bd.n * bd.W);
-  note_launch();
-  assemble_kernel<<<cdiv(bd.n, 128), 128, 0, st>>>(g, s, vb, ab);
+  launch_assemble(g, s, vb, ab, pp, st);
   launch_band_lu(g, ab, piv, status, st);
   double* rd = work + (size_t)bd.n * bd.W + bd.n;
   note_launch();

@@ -35,15 +35,26 @@ __host__ __device__ inline int lidx(const Grid& g, int p) {
   return c * g.nn + j * g.nnx + i;
 }
 
+// Stabilisation pieces of the four cells of a 2h patch: S[c][m * 9 + n] =
+// alpha kappa^T K_c kappa with K_c the Q1 stiffness of cell c = cx + 2 cy of
+// the patch on its 3x3 nodes (the cellwise forms: their own cell blocks).  A
+// patch whose cells are partly solid integrates over its fluid cells only,
+// so its matrix is the sum of those cells' pieces; whole patches use S9.
+struct PatchPieces {
+  double S[4][81];
+};
+
 // entry (r, col) of the band matrix
 __device__ __forceinline__ double& AB(double* ab, const Band& b, int r, int col) {
   return ab[(size_t)r * b.W + (col - r + b.kl)];
 }
 
-// Row `row` of the banded coarse Jacobian (one thread per row).
+// Row `row` of the banded coarse Jacobian (one thread per row); pp (may be
+// null when every patch is whole) gives the pieces of part-solid patches.
 __device__ __forceinline__ void assemble_row(const Grid& g, const Sten<double>& s,
                                              const double* __restrict__ vb,
-                                             double* __restrict__ ab, int row) {
+                                             double* __restrict__ ab, int row,
+                                             const PatchPieces* pp = nullptr) {
   const Band bd = band_of(g);
   if (row >= bd.n) return;
   for (int k = 0; k < bd.W; ++k) ab[(size_t)row * bd.W + k] = 0.0;
@@ -84,12 +95,24 @@ __device__ __forceinline__ void assemble_row(const Grid& g, const Sten<double>& 
       for (int dI = 0; dI < 2; ++dI) {
         const int PI = (i >> 1) - dI;
         if (PI < 0 || PI >= g.nx / 2 || i - 2 * PI > 2) continue;
-        if (g.solid[(2 * PJ) * g.nx + 2 * PI]) continue;
+        const int c00 = (2 * PJ) * g.nx + 2 * PI;
+        const int fm = (g.solid[c00] ? 0 : 1) | (g.solid[c00 + 1] ? 0 : 2) |
+                       (g.solid[c00 + g.nx] ? 0 : 4) | (g.solid[c00 + g.nx + 1] ? 0 : 8);
+        const bool whole = fm == 15 || !pp;  // whole patch (or no pieces: lower-left cell decides)
+        if (whole && g.solid[c00]) continue;
+        if (fm == 0) continue;
         const int mn = (i - 2 * PI) + 3 * (j - 2 * PJ);
         for (int m = 0; m < 9; ++m) {
           const int ni = 2 * PI + m % 3, nj = 2 * PJ + m / 3;
           if (g.flags[nj * g.nnx + ni] & kPFix) continue;
-          AB(ab, bd, row, bidx(g, 2, ni, nj)) += s.S9[mn * 9 + m];
+          double v = 0.0;
+          if (whole) {
+            v = s.S9[mn * 9 + m];
+          } else {
+            for (int c = 0; c < 4; ++c)
+              if (fm & (1 << c)) v += pp->S[c][mn * 9 + m];
+          }
+          AB(ab, bd, row, bidx(g, 2, ni, nj)) += v;
         }
       }
     }

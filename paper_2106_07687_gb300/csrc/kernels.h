@@ -103,8 +103,11 @@ void launch_coarse_lu(const Grid& g, const Sten<double>& s, const double* vb, do
                       int* piv, int* status, cudaStream_t st);
 void launch_coarse_lu_solve(const Grid& g, const double* band, const int* piv, const double* b,
                             double* x, cudaStream_t st);
+struct PatchPieces;  // coarse_body.cuh
+// pp: stabilisation pieces of part-solid patches (null: every patch is whole)
 void launch_coarse_factor(const Grid& g, const Sten<double>& s, const double* vb, double* work,
-                          double* Ainv, int* status, cudaStream_t st);
+                          double* Ainv, int* status, cudaStream_t st,
+                          const PatchPieces* pp = nullptr);
 // x = Ainv b, b and x in the [3][nn] layout of the level
 template <typename T>
 void launch_coarse_solve(const Grid& g, const double* Ainv, const T* b, T* x, cudaStream_t st);

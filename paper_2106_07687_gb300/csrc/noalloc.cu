@@ -73,6 +73,10 @@ extern "C" int dnnmg_coarse_solve_noalloc(const dnnmg_config* cfg, const double*
     set_thread_error("dnnmg_coarse_solve_noalloc: nu, dt, alpha0 or theta out of range");
     return DNNMG_ERR_ARG;
   }
+  if (cfg->obstacle_level != 0) {
+    set_thread_error("dnnmg_coarse_solve_noalloc: only level-0 obstacle blocks");
+    return DNNMG_ERR_ARG;
+  }
   if (cfg->obstacle_i0 >= 0 &&
       (cfg->obstacle_i0 < 1 || cfg->obstacle_i0 > 13 || cfg->obstacle_j0 != 1)) {
     set_thread_error("dnnmg_coarse_solve_noalloc: obstacle must be a 2x2 level-0 block, j0 = 1");

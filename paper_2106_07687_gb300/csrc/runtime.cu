@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cstring>
 
+#include "coarse_body.cuh"
 #include "dnnmg_step.h"
 #include "runtime.h"
 #include "vcycle.h"
@@ -53,6 +54,9 @@ class Solver final : public SolverBase {
     }
     const Grid& g0 = lv_[0].g;
     if (!coarse_supported(g0)) return c_->fail(DNNMG_ERR_ARG, "coarse level too large");
+    // a level-1 obstacle at odd offsets leaves part-solid patches on the coarse level
+    part_solid_ = part_solid_patches(c_->lv[lv_[0].level]);
+    if (part_solid_) pieces_ = make_patch_pieces(g0.h, cfg);
     coarse_work_ = c_->mem.alloc<double>(coarse_work_doubles(g0));
     ainv_ = c_->mem.alloc<double>((size_t)9 * g0.nn * g0.nn);
     status_ = c_->mem.alloc<int>(4);
@@ -162,7 +166,8 @@ class Solver final : public SolverBase {
     c_->prof.end(p, st_);
     if (coarse || !coarse_done_) {
       const int p = c_->prof.begin(DNNMG_STAGE_COARSE_FACTOR, lv_[0].level, st_);
-      launch_coarse_factor(lv_[0].g, lv_[0].s64, lv_[0].vb64, coarse_work_, ainv_, status_, st_);
+      launch_coarse_factor(lv_[0].g, lv_[0].s64, lv_[0].vb64, coarse_work_, ainv_, status_, st_,
+                           part_solid_ ? &pieces_ : nullptr);
       c_->prof.end(p, st_);
       coarse_done_ = true;
     }
@@ -328,6 +333,7 @@ class Solver final : public SolverBase {
       l.s = make_sten<T>(l.g.h, cfg);
       l.s64 = make_sten<double>(l.g.h, cfg);
     }
+    if (part_solid_) pieces_ = make_patch_pieces(lv_[0].g.h, cfg);
     if (dlv_) {
       std::vector<VLevel<T>> hv(K_ + 1);
       for (int k = 0; k <= K_; ++k)
@@ -497,6 +503,8 @@ class Solver final : public SolverBase {
   size_t n_ = 0;
   std::vector<Lev> lv_;
   double *coarse_work_ = nullptr, *ainv_ = nullptr;
+  bool part_solid_ = false;  // the coarse level has part-solid stabilisation patches
+  PatchPieces pieces_{};
   int* status_ = nullptr;
   T *V_ = nullptr, *Z_ = nullptr, *wsol_ = nullptr, *rT_ = nullptr, *rcur_ = nullptr;
   double *H_ = nullptr, *cs_ = nullptr, *sn_ = nullptr, *gv_ = nullptr, *hcol_ = nullptr,
@@ -573,9 +581,23 @@ int check_config(const dnnmg_config& c, std::string& err) {
   if (c.level_coarse != 1) return fail_msg(err, DNNMG_ERR_ARG, "the coarse direct solve supports level 1");
   if (c.replaced_levels < 0 || c.replaced_levels > 2 || c.level_solve + c.replaced_levels > 10)
     return fail_msg(err, DNNMG_ERR_ARG, "replaced_levels must be 0, 1 or 2");
-  if (c.obstacle_i0 >= 0 && (c.obstacle_i0 < 1 || c.obstacle_i0 > 13 || c.obstacle_j0 < 1 ||
-                             c.obstacle_j0 > 1))
+  if (c.obstacle_level != 0 && c.obstacle_level != 1)
+    return fail_msg(err, DNNMG_ERR_ARG, "obstacle_level must be 0 or 1");
+  if (c.obstacle_level == 0 && c.obstacle_i0 >= 0 &&
+      (c.obstacle_i0 < 1 || c.obstacle_i0 > 13 || c.obstacle_j0 < 1 || c.obstacle_j0 > 1))
     return fail_msg(err, DNNMG_ERR_ARG, "obstacle must be a 2x2 level-0 block with 1 <= i0 <= 13, j0 = 1");
+  // a one-cell strip between the square and the inflow, or between the
+  // square and a wall with the square at an even level-1 offset along it,
+  // has no free velocity node on level 1 and leaves the coarse problem
+  // singular: those positions are refused
+  if (c.obstacle_level == 1 && c.obstacle_i0 >= 0 &&
+      (c.obstacle_i0 < 2 || c.obstacle_i0 > 27 || c.obstacle_j0 < 1 || c.obstacle_j0 > 3 ||
+       (c.obstacle_j0 != 2 && c.obstacle_i0 % 2 == 0)))
+    return fail_msg(err, DNNMG_ERR_ARG,
+                    "an obstacle snapped to level 1 needs 2 <= i0 <= 27, 1 <= j0 <= 3 and j0 = 2 or "
+                    "i0 odd (level-1 cells; other positions make the level-1 problem singular)");
+  if (c.obstacle_level == 1 && c.level_solve < 2)
+    return fail_msg(err, DNNMG_ERR_ARG, "a level-1 obstacle needs level_solve >= 2");
   if (c.precision != DNNMG_FP64 && c.precision != DNNMG_MIXED)
     return fail_msg(err, DNNMG_ERR_ARG, "unknown precision");
   if (c.gmres_m < 1 || c.gmres_m > 40 || c.gmres_maxit < 1 || c.newton_max < 1 || c.nu1 < 0 ||
@@ -601,7 +623,8 @@ int dnnmg_ctx::init() {
   const dnnmg_config& c = cfg;
   if (int rc = check_config(c, err)) return rc;
   const int nlev = c.level_solve + c.replaced_levels + 1;
-  for (int l = 0; l < nlev; ++l) lv.push_back(make_level(l, c.obstacle_i0, c.obstacle_j0));
+  for (int l = 0; l < nlev; ++l)
+    lv.push_back(make_level(l, c.obstacle_i0, c.obstacle_j0, c.obstacle_level));
   for (int l = 0; l < nlev; ++l) {
     Grid& g = lv[l].g;
     uint8_t* s = mem.alloc<uint8_t>((size_t)g.nx * g.ny);
@@ -1184,6 +1207,8 @@ int dnnmg_ctx::linearize_api(const double* x) { return solver->linearize(x, true
 
 int dnnmg_ctx::apply_api(int level, const void* w, void* y, int precision) {
   if (level < lc() || level > L()) return fail(DNNMG_ERR_ARG, "level out of range");
+  if (part_solid_patches(lv[level]))
+    return fail(DNNMG_ERR_ARG, "the operator kernels need whole stabilisation patches on this level");
   if (precision != solver->precision()) return fail(DNNMG_ERR_ARG, "precision mismatch");
   return solver->apply(level - lc(), w, y);
 }

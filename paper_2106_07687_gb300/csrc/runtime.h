@@ -18,7 +18,11 @@ struct HostLevel {
   std::vector<uint8_t> solid, flags;
 };
 
-HostLevel make_level(int ell, int oi0, int oj0);
+HostLevel make_level(int ell, int oi0, int oj0, int olev);
+// whether some 2h stabilisation patch of the level is part solid
+bool part_solid_patches(const HostLevel& L);
+struct PatchPieces;
+PatchPieces make_patch_pieces(double h, const dnnmg_config& c);
 // DNNMG_OK, or an error code with the reason in err
 int check_config(const dnnmg_config& c, std::string& err);
 // impulsive start on a level: zero state with the inflow profile on x = 0

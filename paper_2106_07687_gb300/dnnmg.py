@@ -33,7 +33,7 @@ class Config(ctypes.Structure):
                 ("train_batch", c_int32), ("train_seq", c_int32), ("coarse_refresh", c_int32),
                 ("persistent_vcycle", c_int32), ("precond_lag", c_int32),
                 ("persistent_mode", c_int32), ("lps_mode", c_int32), ("stream_pass", c_int32),
-                ("net_bias", c_int32), ("net_inputs", c_int32)]
+                ("net_bias", c_int32), ("net_inputs", c_int32), ("obstacle_level", c_int32)]
 
 
 class StepStats(ctypes.Structure):

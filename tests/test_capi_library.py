@@ -40,7 +40,7 @@ def test_default_config_and_argument_errors(lib):
     # fields late in the struct, written by the library: the ctypes layout matches the header
     assert (cfg.hidden, cfg.gru_layers, cfg.mlp_width, cfg.lps_mode) == (64, 2, 128, 0)
     assert (cfg.stream_pass, cfg.net_bias, cfg.net_inputs) == (0, 1, 0)
-    assert (cfg.obstacle_i0, cfg.obstacle_j0) == (2, 1)
+    assert (cfg.obstacle_i0, cfg.obstacle_j0, cfg.obstacle_level) == (2, 1, 0)
     L = dnnmg.load()
     assert L.dnnmg_default_config(None) == dnnmg.ERR_ARG
     out = ctypes.c_void_p(1)
@@ -48,7 +48,11 @@ def test_default_config_and_argument_errors(lib):
     assert out.value is None
     for bad in (dict(level_coarse=0), dict(level_solve=12), dict(nu=-1.0), dict(gmres_m=0),
                 dict(precision=7), dict(replaced_levels=5), dict(obstacle_i0=20),
-                dict(coarse_refresh=0), dict(persistent_mode=3), dict(lps_mode=3), dict(lps_mode=-1)):
+                dict(coarse_refresh=0), dict(persistent_mode=3), dict(lps_mode=3), dict(lps_mode=-1),
+                dict(obstacle_level=2), dict(obstacle_level=1, obstacle_i0=30),
+                dict(obstacle_level=1, obstacle_j0=6), dict(obstacle_level=1, level_solve=1),
+                dict(obstacle_level=1, obstacle_i0=1, obstacle_j0=2),
+                dict(obstacle_level=1, obstacle_i0=6, obstacle_j0=1)):
         c = dnnmg.default_config(**bad)
         assert L.dnnmg_setup(ctypes.byref(c), None, ctypes.byref(out)) == dnnmg.ERR_ARG, bad
         assert out.value is None
@@ -74,6 +78,12 @@ def test_batch_argument_errors(lib):
     c = dnnmg.default_config(gmres_m=10, level_solve=4)
     arr = (dnnmg.Config * 2)(a, c)
     assert L.dnnmg_batch_setup(arr, 2, None, ctypes.byref(out)) == dnnmg.ERR_ARG
+    assert out.value is None
+    # the obstacle snapped to level-1 cells is for single contexts only
+    d = dnnmg.default_config(obstacle_level=1, obstacle_i0=5, obstacle_j0=3)
+    arr = (dnnmg.Config * 2)(a, d)
+    assert L.dnnmg_batch_setup(arr, 2, None, ctypes.byref(out)) == dnnmg.ERR_ARG
+    assert b"level-0 obstacle" in L.dnnmg_batch_last_error(None)
     assert out.value is None
     assert L.dnnmg_batch_destroy(None) == dnnmg.OK
     assert L.dnnmg_batch_step(None, 0, None) == dnnmg.ERR_ARG
