@@ -6,16 +6,18 @@ the device heap, or a real-time loop forbids allocation), so they cannot
 create a context; this entry point keeps its working memory in a static
 device array instead.  The test calls it through the C ABI twice in a row
 (the array keeps the previous call's contents) and compares each result with
+the oracle's direct solve of the same linearised operator and with
 dnnmg_vcycle on the coarsest level, which applies the context's inverse of
-the same operator.  This file is collected last so that a failure here does
-not hide the other GPU tests."""
+that operator.  This file is collected last so that a failure here does not
+hide the other GPU tests."""
 import ctypes
 
 import numpy as np
 import pytest
+import scipy.sparse.linalg as spla
 
 import synthetic
-from oracle import mesh
+from oracle import fem, mesh
 from tests.gpu_util import lib, rel, seeded_state
 
 pytestmark = pytest.mark.gpu
@@ -30,7 +32,7 @@ def _entry(dn):
 
 
 @pytest.mark.parametrize("with_obstacle", [True, False])
-def test_noalloc_coarse_solve_matches_context_vcycle(with_obstacle):
+def test_noalloc_coarse_solve_matches_oracle_and_context_vcycle(with_obstacle):
     dn = lib()
     f = _entry(dn)
     # without an obstacle the device-side masks take their other branch
@@ -56,6 +58,10 @@ def test_noalloc_coarse_solve_matches_context_vcycle(with_obstacle):
         got = out.cpu().numpy()
         assert np.isfinite(got).all()
         assert rel(got, ref) < 1e-10, (call, rel(got, ref))
+        # the oracle: A'(vbar)^-1 b with the FP64 Jacobian of the same level
+        A = fem.jacobian(lev, x.cpu().numpy(), fem.Params(nu=0.006, dt=0.01))
+        xo = spla.spsolve(A.tocsc(), bh)
+        assert rel(got, xo) < 1e-10, (call, rel(got, xo))
     ctx.close()
 
 
