@@ -19,6 +19,7 @@
 #include <map>
 
 #include "batch.h"
+#include "dnnmg_body.cuh"
 #include "coarse_body.cuh"
 #include "runtime.h"
 
@@ -333,6 +334,12 @@ int Batch<T>::init() {
     pr.dt = c.dt;
     pr.L = L_[p];
     pr.explicit_on = c.theta != 1.0;
+    {
+      const FeatConsts fc = feat_consts(hl_[p][L_[p]].g.h, c.nu, c.dt, (1 << (R_ > 0 ? R_ : 1)) + 1);
+      pr.feat_h = fc.h_rel;
+      pr.feat_k = fc.k_rel;
+      pr.feat_pe = fc.pe;
+    }
   }
   if (!mem_.ok()) return fail(DNNMG_ERR_CUDA, "device allocation failed");
   const Grid& g1 = hl_[0][1].g;

@@ -48,6 +48,8 @@ struct BPar {
   long long coff;  // offset of the problem's level-L cells in the cell -> patch table
   int L;           // finest solved level
   int explicit_on;
+  float feat_h, feat_k;  // patch features h_L / 0.25 and k / h_L
+  double feat_pe;        // h_L / (K^2 nu), the Peclet number's factor
 };
 
 // Device-side view of all problems (arrays indexed [problem * nL + level]).

@@ -182,10 +182,11 @@ __global__ void __launch_bounds__(kNB)
   const int k = pr.L + dl;
   const BLev<T> L = lev_of(v, wk.x, k);
   if (pr.explicit_on) load_const(ss, v.sx[(size_t)wk.x * v.nL + k]);
+  const double m = block_scalar([&] { return L.g.h * L.g.h / 36.0 * pr.inv_k; });
   const int n = wk.y * kNB + threadIdx.x;
   if (n >= L.g.nn) return;
   const int i = n % L.g.nnx, j = n / L.g.nnx;
-  old_rhs64_node(L.g, pr.inv_k, xo + L.off, f + L.off, i, j);
+  old_rhs64_node(L.g, m, xo + L.off, f + L.off, i, j);
   if (pr.explicit_on) explicit_sub64_node(L.g, ss, pr.ecoef, xo + L.off, f + L.off, i, j);
 }
 
@@ -377,9 +378,12 @@ __global__ void __launch_bounds__(kVT)
                   T* __restrict__ y, const int* __restrict__ vinst, const int* __restrict__ act) {
   const int p = vinst[blockIdx.x];
   if (masked(act, p)) return;
-  double s = a[(size_t)p * astride];
-  if (mode == 2) s = sqrt(fmax(s, 0.0));
-  if (mode >= 1) s = s != 0.0 ? 1.0 / s : 0.0;
+  const double s = block_scalar([&] {
+    double v = a[(size_t)p * astride];
+    if (mode == 2) v = sqrt(fmax(v, 0.0));
+    if (mode >= 1) v = v != 0.0 ? 1.0 / v : 0.0;
+    return v;
+  });
   const size_t base = (size_t)blockIdx.x * kVB + threadIdx.x;
 #pragma unroll
   for (int r = 0; r < kVE; ++r) y[base + r * kVT] = (T)(s * (double)x[base + r * kVT]);
@@ -393,8 +397,8 @@ __global__ void __launch_bounds__(kVT)
                   const int* __restrict__ act) {
   const int p = vinst[blockIdx.x];
   if (masked(act, p)) return;
-  const double beta = sqrt(fmax(nrm2[(size_t)p * nstride], 0.0));
-  const double s = beta > 0 ? 1.0 / beta : 0.0;
+  const double beta = block_scalar([&] { return sqrt(fmax(nrm2[(size_t)p * nstride], 0.0)); });
+  const double s = block_scalar([&] { return beta > 0 ? 1.0 / beta : 0.0; });
   if (blockIdx.x == (unsigned)first[p] && threadIdx.x == 0) gv[(size_t)p * gstride] = beta;
   const size_t base = (size_t)blockIdx.x * kVB + threadIdx.x;
 #pragma unroll
@@ -506,7 +510,8 @@ __global__ void bgather_kernel(BView<T> v, int P, const int* __restrict__ pinst,
   const BPar pr = v.par[p];
   const BLev<T>& L = lev_of(v, p, pr.L);
   const BLev<T>& F = lev_of(v, p, pr.L + kR);
-  gather_patch<false, K>(L.g, F.g, pcell[q], xt + F.off, r + F.off, mean, stdv, pr.nu, pr.dt,
+  const FeatConsts fc{pr.feat_h, pr.feat_k, pr.feat_pe};
+  gather_patch<false, K>(L.g, F.g, pcell[q], xt + F.off, r + F.off, mean, stdv, fc,
                          X + (size_t)q * kCin, nullptr);
 }
 

@@ -41,6 +41,17 @@ struct Sten {
 
 __host__ __device__ inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 
+// A scalar derived once per block by its first thread and shared with the
+// block (an FP64 square root or division in every thread would make a
+// vector kernel FP64-bound on this GPU).  All threads of the block call it.
+template <class F>
+__device__ __forceinline__ double block_scalar(F f) {
+  __shared__ double v;
+  if (threadIdx.x == 0) v = f();
+  __syncthreads();
+  return v;
+}
+
 // Values of the four bilinear shape functions and their derivatives (times
 // h) at Gauss point q = qx + 2 qy.
 template <typename T>

@@ -31,6 +31,17 @@ __device__ __forceinline__ void impose_dirichlet_node(const Grid& g, double* __r
   if (f & kPFix) x[2 * g.nn + n] = 0.0;
 }
 
+// Per-launch constants of the patch features: h_L / 0.25, k / h_L and the
+// factor h_L / (K^2 nu) of the Peclet number |sum of the patch's velocities|
+// h_L / (K^2 nu) (formed once on the host: no FP64 division per patch).
+struct FeatConsts {
+  float h_rel, k_rel;
+  double pe;
+};
+inline FeatConsts feat_consts(double hL, double nu, double dt, int K) {
+  return FeatConsts{(float)(hL / 0.25), (float)(dt / hL), hL / ((double)(K * K) * nu)};
+}
+
 // The network inputs of the patch on level-L cell `cell` whose K x K nodes
 // (K = 2^r + 1 for r replaced levels: 3 or 5) lie on level L + r, in the
 // order [u at the K^2 nodes, v, residual u, residual v, h_L / 0.25,
@@ -41,7 +52,7 @@ __device__ __forceinline__ void gather_patch(const Grid& gL, const Grid& gF, int
                                              const double* __restrict__ xt,
                                              const double* __restrict__ r,
                                              const float* __restrict__ mean,
-                                             const float* __restrict__ stdv, double nu, double dt,
+                                             const float* __restrict__ stdv, const FeatConsts& fc,
                                              uint16_t* __restrict__ X, float* __restrict__ Xraw) {
   constexpr int K2 = K * K, C = 4 * K2 + 4, S = K - 1;
   const int I = cell % gL.nx, J = cell / gL.nx;
@@ -58,11 +69,10 @@ __device__ __forceinline__ void gather_patch(const Grid& gL, const Grid& gF, int
     f[2 * K2 + m] = (float)r[n];
     f[3 * K2 + m] = (float)r[gF.nn + n];
   }
-  const double hL = gL.h;
-  f[4 * K2] = (float)(hL / 0.25);
+  f[4 * K2] = fc.h_rel;
   f[4 * K2 + 1] = 1.0f;
-  f[4 * K2 + 2] = (float)(sqrt(su * su + sv * sv) / K2 * hL / nu);
-  f[4 * K2 + 3] = (float)(dt / hL);
+  f[4 * K2 + 2] = (float)(sqrt(su * su + sv * sv) * fc.pe);
+  f[4 * K2 + 3] = fc.k_rel;
   if (RAW) {
 #pragma unroll
     for (int k = 0; k < C; ++k) Xraw[k] = f[k];
@@ -100,8 +110,16 @@ __device__ __forceinline__ void scatter_node(const Grid& gL, const Grid& gF,
       ++cnt;
     }
   }
-  if (cnt == 0 || (gF.flags[n] & kVDir)) du = dv = 0.0;
-  else du /= cnt, dv /= cnt;
+  // the mean; counts 1, 2 and 4 scale by exact powers of two (the same
+  // result as the division, without an FP64 division per node)
+  if (cnt == 0 || (gF.flags[n] & kVDir)) {
+    du = dv = 0.0;
+  } else if (cnt == 3) {
+    du /= 3.0, dv /= 3.0;
+  } else {
+    const double sc = cnt == 4 ? 0.25 : (cnt == 2 ? 0.5 : 1.0);
+    du *= sc, dv *= sc;
+  }
   vcorr[n] = xt[n] + du;
   vcorr[gF.nn + n] = xt[gF.nn + n] + dv;
   vcorr[2 * gF.nn + n] = 0.0;

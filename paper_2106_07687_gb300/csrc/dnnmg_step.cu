@@ -31,12 +31,12 @@ template <bool RAW, int K>
 __global__ void gather_kernel(Grid gL, Grid gF, const int* __restrict__ patch_cell, int P,
                               const double* __restrict__ xt, const double* __restrict__ r,
                               const float* __restrict__ mean, const float* __restrict__ stdv,
-                              double nu, double dt, uint16_t* __restrict__ X,
+                              FeatConsts fc, uint16_t* __restrict__ X,
                               float* __restrict__ Xraw) {
   constexpr int C = 4 * K * K + 4;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
-  gather_patch<RAW, K>(gL, gF, patch_cell[p], xt, r, mean, stdv, nu, dt,
+  gather_patch<RAW, K>(gL, gF, patch_cell[p], xt, r, mean, stdv, fc,
                        RAW ? nullptr : X + (size_t)p * C, RAW ? Xraw + (size_t)p * C : nullptr);
 }
 
@@ -134,12 +134,13 @@ void launch_gather(const Grid& gL, const Grid& gF, int K, const int* patch_cell,
                    double nu, double dt, uint16_t* X, cudaStream_t st) {
   if (P <= 0) return;
   note_launch();
+  const FeatConsts fc = feat_consts(gL.h, nu, dt, K);
   if (K == 5)
     gather_kernel<false, 5><<<cdiv(P, 128), 128, 0, st>>>(gL, gF, patch_cell, P, xt, r, mean,
-                                                          stdv, nu, dt, X, nullptr);
+                                                          stdv, fc, X, nullptr);
   else
     gather_kernel<false, 3><<<cdiv(P, 128), 128, 0, st>>>(gL, gF, patch_cell, P, xt, r, mean,
-                                                          stdv, nu, dt, X, nullptr);
+                                                          stdv, fc, X, nullptr);
 }
 
 void launch_gather_raw(const Grid& gL, const Grid& gF, int K, const int* patch_cell, int P,
@@ -147,12 +148,13 @@ void launch_gather_raw(const Grid& gL, const Grid& gF, int K, const int* patch_c
                        cudaStream_t st) {
   if (P <= 0) return;
   note_launch();
+  const FeatConsts fc = feat_consts(gL.h, nu, dt, K);
   if (K == 5)
     gather_kernel<true, 5><<<cdiv(P, 128), 128, 0, st>>>(gL, gF, patch_cell, P, xt, r, nullptr,
-                                                         nullptr, nu, dt, nullptr, Xraw);
+                                                         nullptr, fc, nullptr, Xraw);
   else
     gather_kernel<true, 3><<<cdiv(P, 128), 128, 0, st>>>(gL, gF, patch_cell, P, xt, r, nullptr,
-                                                         nullptr, nu, dt, nullptr, Xraw);
+                                                         nullptr, fc, nullptr, Xraw);
 }
 
 void launch_targets(const Grid& gL, const Grid& gF, int K, const int* patch_cell, int P,

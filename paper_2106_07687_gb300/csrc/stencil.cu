@@ -17,10 +17,10 @@ namespace {
 constexpr int kBX = 32, kBY = 4;
 
 __global__ void __launch_bounds__(kBX* kBY)
-    old_rhs64_kernel(Grid g, double inv_k, const double* __restrict__ x, double* __restrict__ f) {
+    old_rhs64_kernel(Grid g, double m, const double* __restrict__ x, double* __restrict__ f) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   if (i >= g.nnx || j >= g.nny) return;
-  old_rhs64_node(g, inv_k, x, f, i, j);
+  old_rhs64_node(g, m, x, f, i, j);
 }
 
 __global__ void __launch_bounds__(kBX* kBY)
@@ -168,7 +168,8 @@ void launch_residual64(const Grid& g, const Sten<double>& s, const double* x, co
 void launch_old_time_rhs64(const Grid& g, double inv_k, const double* x_old, double* f,
                            cudaStream_t st) {
   note_launch();
-  old_rhs64_kernel<<<node_grid(g), dim3(kBX, kBY), 0, st>>>(g, inv_k, x_old, f);
+  old_rhs64_kernel<<<node_grid(g), dim3(kBX, kBY), 0, st>>>(g, g.h * g.h / 36.0 * inv_k, x_old,
+                                                              f);
 }
 
 void launch_explicit_sub64(const Grid& g, const Sten<double>& sx, double coef, const double* x,

@@ -233,12 +233,12 @@ __device__ __forceinline__ void residual64_node(const Grid& g, const Sten<double
 }
 
 // f = (1/k) (v_old, phi) at node (i, j) with the Q1 mass matrix
-// (h^2/36) [4 2 2 1] pattern; pressure rows 0.
-__device__ __forceinline__ void old_rhs64_node(const Grid& g, double inv_k,
+// (h^2/36) [4 2 2 1] pattern; pressure rows 0.  m = h^2 / 36 / k, formed by
+// the caller once (an FP64 division per node is slow on this GPU).
+__device__ __forceinline__ void old_rhs64_node(const Grid& g, double m,
                                                const double* __restrict__ x,
                                                double* __restrict__ f, int i, int j) {
   const int n = j * g.nnx + i, nn = g.nn;
-  const double m = g.h * g.h / 36.0 * inv_k;
   double fu = 0, fv = 0;
   for (int cy = 0; cy < 2; ++cy)
     for (int cx = 0; cx < 2; ++cx) {

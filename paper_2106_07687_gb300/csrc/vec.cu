@@ -71,9 +71,12 @@ __global__ void multiaxpy_kernel(const T* __restrict__ V, size_t ld, int k,
 template <typename T>
 __global__ void scale_dev_kernel(const T* __restrict__ x, const double* a, int mode,
                                  T* __restrict__ y, size_t n) {
-  double s = *a;
-  if (mode == 2) s = sqrt(fmax(s, 0.0));
-  if (mode >= 1) s = s != 0.0 ? 1.0 / s : 0.0;
+  const double s = block_scalar([&] {
+    double v = *a;
+    if (mode == 2) v = sqrt(fmax(v, 0.0));
+    if (mode >= 1) v = v != 0.0 ? 1.0 / v : 0.0;
+    return v;
+  });
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
        e += (size_t)gridDim.x * blockDim.x)
     y[e] = (T)(s * (double)x[e]);
@@ -108,8 +111,8 @@ __global__ void backsolve_kernel(const double* H, int ldh, const double* g, int 
 template <typename T>
 __global__ void gmres_start_kernel(const T* __restrict__ r, const double* nrm2, T* __restrict__ v0,
                                    double* g, size_t n) {
-  const double beta = sqrt(fmax(*nrm2, 0.0));
-  const double s = beta > 0 ? 1.0 / beta : 0.0;
+  const double beta = block_scalar([&] { return sqrt(fmax(*nrm2, 0.0)); });
+  const double s = block_scalar([&] { return beta > 0 ? 1.0 / beta : 0.0; });
   if (blockIdx.x == 0 && threadIdx.x == 0) g[0] = beta;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
        e += (size_t)gridDim.x * blockDim.x)
@@ -212,8 +215,10 @@ __global__ void __launch_bounds__(kThreads)
   dots(nullptr, 1, p3);
   grid.sync();
   finish(p3, 1, &nrm2);
-  double s = sqrt(fmax(nrm2, 0.0));
-  s = s != 0.0 ? 1.0 / s : 0.0;
+  const double s = block_scalar([&] {
+    const double v = sqrt(fmax(nrm2, 0.0));
+    return v != 0.0 ? 1.0 / v : 0.0;
+  });
   const T sT = (T)s;
   for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) w[e] *= sT;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
