@@ -4,6 +4,11 @@
 // columns of dG^T x, computed as split-K tcgen05 GEMMs on the transposed
 // BF16 streams written by the forward and backward passes; a ones row in
 // every input stream makes the bias gradient the last output column.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "kernels.h"
 #include "patchnet.cuh"
 #include "train.h"
@@ -423,6 +428,184 @@ __global__ void __launch_bounds__(kTile, 1)
   }
 }
 
+// The same partial sums with the operands copied by the tensor memory
+// accelerator (TMA): one thread of the block issues, per 64-column chunk, one
+// 3-D tile copy of A (128 rows) and one of B (N rows) into a ring of
+// kTStages stages, waits for a stage's bytes on its mbarrier, issues the
+// chunk's MMAs and commits them to the stage's release barrier; the copy of
+// chunk c + kTStages waits for that release.  The tensor maps view an operand
+// [rows][ld] as (8 columns, rows, column groups of 8), so a copied box lands
+// as 8 x 8 core matrices, 128 bytes each, row groups 128 bytes apart and
+// column groups (box rows x 16) bytes apart: the K-major operand layout of the
+// MMA with those two strides.
+constexpr int kTStages = 6;
+constexpr size_t kTStageA = (size_t)kTile * kKC * 2;                 // 16 KB
+constexpr size_t kTStage = (kTStageA + (size_t)kWNmax * kKC * 2 + 1023) / 1024 * 1024;
+constexpr size_t kTSmem = kTStages * kTStage + 1024 + 256;
+constexpr uint32_t kTPolls = 1u << 24;
+
+struct WGradMaps {
+  CUtensorMap a[kMaxWGradJobs], b[kMaxWGradJobs];
+};
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(mbar))
+      : "memory");
+}
+
+__global__ void __launch_bounds__(kTile, 1)
+    wgrad_tma_kernel(WGradArgs a, const __grid_constant__ WGradMaps maps,
+                     float* __restrict__ Cpart, int* status) {
+  extern __shared__ __align__(1024) uint8_t smraw[];
+  // stages on a 1024-byte boundary (the copies need 128)
+  uint8_t* sm = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + kTStages * kTStage);
+  uint64_t* empty = full + kTStages;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(empty + kTStages);
+  __shared__ int s_failed;
+  int jb = 0;
+  while (jb + 1 < a.njobs && (int)blockIdx.x >= a.first[jb + 1]) ++jb;
+  const WGradJob& J = a.job[jb];
+  const int nmt = J.M / kTile;
+  const int b = blockIdx.x - a.first[jb];
+  const int mt = b % nmt, split = b / nmt;
+  const int row0 = mt * kTile;
+  const int kbeg = split * a.Ks, kend = min(a.K, kbeg + a.Ks);
+  const int nch = kend > kbeg ? (kend - kbeg + kKC - 1) / kKC : 0;
+  uint32_t ncols = 32;
+  while (ncols < (uint32_t)J.N) ncols <<= 1;
+  const int t = threadIdx.x, warp = t >> 5;
+  if (warp == 0) tmem_alloc(tslot, ncols);
+  if (t == 0) {
+    for (int q = 0; q < kTStages; ++q) {
+      mbar_init(full + q, 1);
+      mbar_init(empty + q, 1);
+    }
+    s_failed = 0;
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tbase = *tslot;
+  const uint32_t bytes = (uint32_t)(kTStageA + (size_t)J.N * kKC * 2);
+  const uint32_t lboA = kTile * 16, lboB = (uint32_t)J.N * 16;
+  int last = -1;  // last chunk whose MMAs were committed
+  if (t == 0) {
+    const CUtensorMap* ma = &maps.a[jb];
+    const CUtensorMap* mb = &maps.b[jb];
+    auto issue = [&](int c) {
+      uint8_t* sa = sm + (size_t)(c % kTStages) * kTStage;
+      const int kg = (kbeg + c * kKC) >> 3;
+      mbar_expect_tx(full + c % kTStages, bytes);
+      tma_load_3d(sa, ma, 0, row0, kg, full + c % kTStages);
+      tma_load_3d(sa + kTStageA, mb, 0, 0, kg, full + c % kTStages);
+    };
+    const uint32_t id = idesc_bf16(kTile, J.N);
+    bool failed = false;
+    int issued = 0;
+    for (; issued < nch && issued < kTStages; ++issued) issue(issued);
+    for (int c = 0; c < nch && !failed; ++c) {
+      const int sidx = c % kTStages;
+      const uint32_t par = (uint32_t)(c / kTStages) & 1u;
+      if (!mbar_wait(full + sidx, par, kTPolls)) {
+        failed = true;
+        break;
+      }
+      fence_after_sync();
+      const uint32_t sa = smem_u32(sm + (size_t)sidx * kTStage);
+      const uint32_t sb = sa + (uint32_t)kTStageA;
+      const int kc = min(kKC, kend - (kbeg + c * kKC));
+      for (int ks = 0; ks < kc / 16; ++ks) {
+        const uint64_t da = smem_desc(sa + ks * 2 * lboA, lboA, 128);
+        const uint64_t db = smem_desc(sb + ks * 2 * lboB, lboB, 128);
+        mma_bf16(tbase, da, db, id, (c > 0 || ks > 0) ? 1u : 0u);
+      }
+      mma_commit(empty + sidx);
+      last = c;
+      if (issued < nch) {  // the stage is free once these MMAs are done
+        if (!mbar_wait(empty + sidx, par, kTPolls)) {
+          failed = true;
+          break;
+        }
+        issue(issued++);
+      }
+    }
+    if (!failed && last >= 0 &&
+        !mbar_wait(empty + last % kTStages, (uint32_t)(last / kTStages) & 1u, kTPolls))
+      failed = true;
+    if (failed) {
+      // copies and MMAs still in flight finish before the block's memory is
+      // released: every issued stage's bytes, then the last commit (bounded)
+      for (int c = last + 1; c < issued; ++c)
+        mbar_wait(full + c % kTStages, (uint32_t)(c / kTStages) & 1u, kTPolls);
+      if (last >= 0) mbar_wait(empty + last % kTStages, (uint32_t)(last / kTStages) & 1u, kTPolls);
+      s_failed = 1;
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const bool failed = s_failed != 0;
+  float* Cp = Cpart + a.coff[jb] + (size_t)split * J.M * J.N;
+  const int r = row0 + t;
+  if (!failed) {
+    for (int c = 0; c < J.N / 16; ++c) {
+      float v[16];
+      if (nch > 0) tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + c * 16, v);
+      for (int i = 0; i < 16; ++i) Cp[(size_t)r * J.N + c * 16 + i] = nch > 0 ? v[i] : 0.0f;
+    }
+  } else if (t == 0) {
+    atomicOr(status, 4);
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after_sync();
+    tmem_dealloc(tbase, ncols);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+// Tensor map of a BF16 operand [rows][ld] viewed as (8 columns, rows, K / 8
+// column groups) with boxes of (8, box_rows, kKC / 8); false when it cannot
+// be made (alignment, sizes, no driver entry point).
+bool wgrad_map(CUtensorMap* m, const uint16_t* p, int rows, size_t ld, int K, int box_rows) {
+  const PFN_cuTensorMapEncodeTiled_v12000 fn = tmap_encode_fn();
+  if (!fn || !p || (reinterpret_cast<uintptr_t>(p) & 15) || ld % 8 || K % 8 || box_rows > 256)
+    return false;
+  const cuuint64_t dims[3] = {8, (cuuint64_t)rows, (cuuint64_t)(K / 8)};
+  const cuuint64_t strides[2] = {(cuuint64_t)ld * 2, 16};
+  const cuuint32_t box[3] = {8, (cuuint32_t)box_rows, (cuuint32_t)(kKC / 8)};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(p), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // grad_w[m * n_valid + n] = sum_s Cpart[job][s][m][n] (fixed order, FP64),
 // grad_b[m] = sum_s Cpart[job][s][m][bias_col], all jobs in one launch
 __global__ void wgrad_reduce_kernel(WGradArgs a, const float* __restrict__ Cpart) {
@@ -557,6 +740,25 @@ int launch_wgrad(const WGradJob* jobs, int njobs, int K, int splits, float* Cpar
   }
   a.first[njobs] = blocks;
   a.eoff[njobs] = elems;
+  // the TMA-fed kernel where every operand has a tensor map
+  WGradMaps maps;
+  bool tma = true;
+  for (int q = 0; q < njobs && tma; ++q) {
+    const WGradJob& J = jobs[q];
+    tma = wgrad_map(&maps.a[q], J.A, J.M, J.lda, K, kTile) &&
+          wgrad_map(&maps.b[q], J.B, J.N, J.ldb, K, J.N);
+  }
+  static const bool tattr =
+      cudaFuncSetAttribute(wgrad_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kTSmem) == cudaSuccess;
+  if (tma && tattr) {
+    note_launch();
+    wgrad_tma_kernel<<<blocks, kTile, kTSmem, st>>>(a, maps, Cpart, status);
+    note_launch();
+    wgrad_reduce_kernel<<<cdiv(elems, 256), 256, 0, st>>>(a, Cpart);
+    return 0;
+  }
+  cudaGetLastError();
   static const bool attr =
       cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)kWSmem) == cudaSuccess;
