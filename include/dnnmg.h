@@ -150,7 +150,7 @@ typedef struct dnnmg_step_stats {
  * newton_tol = 1e-10, gmres_rtol = 1e-4, omega = 0.8, eps_damp = 1,
  * obstacle at level-0 cell (2, 1), L = 3, coarse level 1, replaced_levels = 1,
  * FP64, newton_max = 20, gmres_m = 20, gmres_maxit = 200, V(2,2), GRU 2 x 64,
- * dense width 128, fallback_newton_its = 8, coarse_refresh = 8,
+ * dense width 128, fallback_newton_its = 8, coarse_refresh = 32,
  * persistent_vcycle = -1, precond_lag = 1.  Returns DNNMG_ERR_ARG if cfg is
  * NULL. */
 int dnnmg_default_config(dnnmg_config* cfg);

@@ -282,7 +282,7 @@ int dnnmg_default_config(dnnmg_config* c) {
   c->gru_layers = 2;
   c->mlp_width = 128;
   c->fallback_newton_its = 8;
-  c->coarse_refresh = 8;
+  c->coarse_refresh = 32;
   c->persistent_vcycle = -1;
   c->precond_lag = 1;
   c->persistent_mode = -1;
