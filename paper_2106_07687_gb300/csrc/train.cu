@@ -430,14 +430,12 @@ __global__ void __launch_bounds__(kTile, 1)
 
 // The same partial sums with the operands copied by the tensor memory
 // accelerator (TMA): one thread of the block issues, per 64-column chunk, one
-// 3-D tile copy of A (128 rows) and one of B (N rows) into a ring of
+// 2-D tile copy of A (128 rows) and one of B (N rows) into a ring of
 // kTStages stages, waits for a stage's bytes on its mbarrier, issues the
 // chunk's MMAs and commits them to the stage's release barrier; the copy of
-// chunk c + kTStages waits for that release.  The tensor maps view an operand
-// [rows][ld] as (8 columns, rows, column groups of 8), so a copied box lands
-// as 8 x 8 core matrices, 128 bytes each, row groups 128 bytes apart and
-// column groups (box rows x 16) bytes apart: the K-major operand layout of the
-// MMA with those two strides.
+// chunk c + kTStages waits for that release.  A box row is 64 columns (128
+// bytes) copied with the 128-byte swizzle, which is the MMA's swizzled
+// K-major operand layout (smem_desc_sw128): one copy request per row.
 constexpr int kTStages = 6;
 constexpr size_t kTStageA = (size_t)kTile * kKC * 2;                 // 16 KB
 constexpr size_t kTStage = (kTStageA + (size_t)kWNmax * kKC * 2 + 1023) / 1024 * 1024;
@@ -453,12 +451,12 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
                "r"(bytes)
                : "memory");
 }
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
                                             uint64_t* mbar) {
   asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-      "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(mbar))
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(mbar))
       : "memory");
 }
 
@@ -498,17 +496,16 @@ __global__ void __launch_bounds__(kTile, 1)
   fence_after_sync();
   const uint32_t tbase = *tslot;
   const uint32_t bytes = (uint32_t)(kTStageA + (size_t)J.N * kKC * 2);
-  const uint32_t lboA = kTile * 16, lboB = (uint32_t)J.N * 16;
   int last = -1;  // last chunk whose MMAs were committed
   if (t == 0) {
     const CUtensorMap* ma = &maps.a[jb];
     const CUtensorMap* mb = &maps.b[jb];
     auto issue = [&](int c) {
       uint8_t* sa = sm + (size_t)(c % kTStages) * kTStage;
-      const int kg = (kbeg + c * kKC) >> 3;
+      const int k0 = kbeg + c * kKC;
       mbar_expect_tx(full + c % kTStages, bytes);
-      tma_load_3d(sa, ma, 0, row0, kg, full + c % kTStages);
-      tma_load_3d(sa + kTStageA, mb, 0, 0, kg, full + c % kTStages);
+      tma_load_2d(sa, ma, k0, row0, full + c % kTStages);
+      tma_load_2d(sa + kTStageA, mb, k0, 0, full + c % kTStages);
     };
     const uint32_t id = idesc_bf16(kTile, J.N);
     bool failed = false;
@@ -526,8 +523,8 @@ __global__ void __launch_bounds__(kTile, 1)
       const uint32_t sb = sa + (uint32_t)kTStageA;
       const int kc = min(kKC, kend - (kbeg + c * kKC));
       for (int ks = 0; ks < kc / 16; ++ks) {
-        const uint64_t da = smem_desc(sa + ks * 2 * lboA, lboA, 128);
-        const uint64_t db = smem_desc(sb + ks * 2 * lboB, lboB, 128);
+        const uint64_t da = smem_desc_sw128(sa + ks * 32);
+        const uint64_t db = smem_desc_sw128(sb + ks * 32);
         mma_bf16(tbase, da, db, id, (c > 0 || ks > 0) ? 1u : 0u);
       }
       mma_commit(empty + sidx);
@@ -590,19 +587,19 @@ PFN_cuTensorMapEncodeTiled_v12000 tmap_encode_fn() {
   return fn;
 }
 
-// Tensor map of a BF16 operand [rows][ld] viewed as (8 columns, rows, K / 8
-// column groups) with boxes of (8, box_rows, kKC / 8); false when it cannot
-// be made (alignment, sizes, no driver entry point).
+// Tensor map of a BF16 operand [rows][ld] (columns K) with boxes of kKC
+// columns x box_rows rows in the 128-byte swizzle; false when it cannot be
+// made (alignment, sizes, no driver entry point).
 bool wgrad_map(CUtensorMap* m, const uint16_t* p, int rows, size_t ld, int K, int box_rows) {
   const PFN_cuTensorMapEncodeTiled_v12000 fn = tmap_encode_fn();
   if (!fn || !p || (reinterpret_cast<uintptr_t>(p) & 15) || ld % 8 || K % 8 || box_rows > 256)
     return false;
-  const cuuint64_t dims[3] = {8, (cuuint64_t)rows, (cuuint64_t)(K / 8)};
-  const cuuint64_t strides[2] = {(cuuint64_t)ld * 2, 16};
-  const cuuint32_t box[3] = {8, (cuuint32_t)box_rows, (cuuint32_t)(kKC / 8)};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(p), dims, strides, box,
-            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)kKC, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t*>(p), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

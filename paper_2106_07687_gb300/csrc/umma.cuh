@@ -35,6 +35,22 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
   return d;                // base offset 0, layout type 0 (no swizzle)
 }
 
+// Descriptor of a K-major operand in the 128-byte swizzled layout that a
+// TMA copy with CU_TENSOR_MAP_SWIZZLE_128B writes: rows of 64 BF16 (128 B)
+// whose 16-byte chunks are permuted by (row % 8), 8-row groups 1024 B apart
+// (stride byte offset; the leading offset is unused in this layout).  The
+// operand must start on a 1024-byte boundary; a K = 16 slice k of it starts
+// k * 32 bytes in.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;                   // leading byte offset (unused): 16 B
+  d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                   // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;                   // layout type: 128-byte swizzle
+  return d;
+}
+
 // Instruction descriptor: kind::f16, A = B = BF16, D = FP32, both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4)                       // D format F32
