@@ -26,6 +26,11 @@ void launch_defect(const Grid& g, const Sten<T>& s, const T* b, const T* x, cons
 // significant bits, FP32 units) and only f - A(x) in FP64.
 void launch_residual64(const Grid& g, const Sten<double>& s, const double* x, const double* f,
                        double* r, cudaStream_t st, bool dfloat_ops = false);
+// The fine-level residual f - A(x) whose only use is the network's input
+// features (rounded to BF16): the operator in FP32 when fp32_ops (mixed
+// precision contexts), else launch_residual64 in FP64.
+void launch_residual_features(const Grid& g, const Sten<double>& s, const double* x,
+                              const double* f, double* r, cudaStream_t st, bool fp32_ops);
 // f = (1/k) M v_old on the velocity rows, 0 on the pressure rows.
 void launch_old_time_rhs64(const Grid& g, double inv_k, const double* x_old, double* f,
                            cudaStream_t st);

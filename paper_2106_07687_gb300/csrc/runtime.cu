@@ -900,7 +900,7 @@ int dnnmg_ctx::dnnmg_correction() {
   old_rhs(fine_level(), vcorr, fF);
   cudaMemcpyAsync(ximpF, xtF, n3F * sizeof(double), cudaMemcpyDeviceToDevice, st);
   launch_impose_dirichlet64(gF, ximpF, st);
-  launch_residual64(gF, s64F, ximpF, fF, rF, st, mixed());                     // input: fine residual
+  launch_residual_features(gF, s64F, ximpF, fF, rF, st, mixed());  // input: fine residual
   launch_gather(gL, gF, K, patch_cell, P, xtF, rF, feat_mean, feat_std, cfg.nu, cfg.dt, X, st);
   launch_patchnet_forward(nd, pk, X, hid, hid, net_out, P, net_status, st);  // network
   launch_scatter(gL, gF, K, cell_patch, net_out, nd.c_out, xtF, vcorr, st);
@@ -943,7 +943,7 @@ int dnnmg_ctx::make_sample(const double* xf_prev, const double* xf_next, float* 
   prolong_up(x64, xtF, 3);
   cudaMemcpyAsync(ximpF, xtF, 3 * sizeof(double) * gF.nn, cudaMemcpyDeviceToDevice, st);
   launch_impose_dirichlet64(gF, ximpF, st);
-  launch_residual64(gF, s64F, ximpF, fF, rF, st, mixed());
+  launch_residual_features(gF, s64F, ximpF, fF, rF, st, mixed());
   launch_gather_raw(gL, gF, K, patch_cell, P, xtF, rF, cfg.nu, cfg.dt, Xraw, st);
   launch_targets(gL, gF, K, patch_cell, P, xf_next, xtF, Y, st);
   have_net_rhs = have_vcorr = false;

@@ -94,6 +94,26 @@ __global__ void __launch_bounds__(kTX* kTY)
   r[2 * nn + n] = (fl & kPFix) ? 0.0 : f[2 * nn + n] - rp;
 }
 
+// The same residual with the operator evaluated in FP32 (the state rounded
+// to FP32, the subtraction from f in FP64): the fine-level residual whose
+// only use is the network's input features, which are rounded to BF16.
+__global__ void __launch_bounds__(kTX* kTY)
+    residual32_tiled_kernel(Grid g, Sten<float> s, const double* __restrict__ x,
+                            const double* __restrict__ f, double* __restrict__ r) {
+  extern __shared__ __align__(16) uint8_t smraw[];
+  auto& S = *reinterpret_cast<OpSmem<float, kTX, kTY>*>(smraw);
+  float ru, rv, rp;
+  int n;
+  op_tile_rows<float, true, false, kTX, kTY, kTX * kTY, double>(g, s, x, nullptr, blockIdx.x,
+                                                               blockIdx.y, S, ru, rv, rp, n);
+  if (n < 0) return;
+  const uint8_t fl = op_tile_flags<float, kTX, kTY>(S);
+  const int nn = g.nn;
+  r[n] = (fl & kVDir) ? 0.0 : f[n] - (double)ru;
+  r[nn + n] = (fl & kVDir) ? 0.0 : f[nn + n] - (double)rv;
+  r[2 * nn + n] = (fl & kPFix) ? 0.0 : f[2 * nn + n] - (double)rp;
+}
+
 // The same residual with the operator evaluated in double-float arithmetic
 // (about 48 significant bits; the subtraction from f in FP64), for
 // mixed-precision contexts.
@@ -163,6 +183,26 @@ void launch_residual64(const Grid& g, const Sten<double>& s, const double* x, co
   note_launch();
   static const size_t sm = smem_attr(residual64_tiled_kernel, sizeof(OpSmem<double, kTX, kTY>));
   residual64_tiled_kernel<<<tile_grid(g), kTX * kTY, sm, st>>>(g, s, x, f, r);
+}
+
+void launch_residual_features(const Grid& g, const Sten<double>& s, const double* x,
+                              const double* f, double* r, cudaStream_t st, bool fp32_ops) {
+  if (!fp32_ops) {
+    launch_residual64(g, s, x, f, r, st, false);
+    return;
+  }
+  Sten<float> sf;
+  for (int e = 0; e < 16; ++e) {
+    sf.E[e] = (float)s.E[e];
+    sf.Dx[e] = (float)s.Dx[e];
+    sf.Dy[e] = (float)s.Dy[e];
+  }
+  for (int e = 0; e < 81; ++e) sf.S9[e] = (float)s.S9[e];
+  sf.wq = (float)s.wq;
+  sf.ih = (float)s.ih;
+  note_launch();
+  static const size_t sm = smem_attr(residual32_tiled_kernel, sizeof(OpSmem<float, kTX, kTY>));
+  residual32_tiled_kernel<<<tile_grid(g), kTX * kTY, sm, st>>>(g, sf, x, f, r);
 }
 
 void launch_old_time_rhs64(const Grid& g, double inv_k, const double* x_old, double* f,
