@@ -122,7 +122,9 @@ __global__ void gmres_start_kernel(const T* __restrict__ r, const double* nrm2, 
 // One Arnoldi step of FGMRES for the new vector w against V[0..j] (CGS with
 // one re-orthogonalisation, then normalisation and the Givens update of
 // Hessenberg column j) in one cooperative launch of kDotBlocks blocks with
-// three grid barriers.  Block b owns the chunk of elements that multidot
+// two grid barriers: the second pass's products include <w, w>, and the
+// norm of the re-orthogonalised vector follows from it as ||w||^2 - |h2|^2
+// (the columns of V are orthonormal).  Block b owns the chunk of elements that multidot
 // assigns to it: it updates only that chunk, so the second pass's and the
 // norm's partial sums follow its own updates without a barrier, and every
 // block finishes the sums over all partials itself in one fixed order (one
@@ -143,18 +145,17 @@ __global__ void __launch_bounds__(kThreads)
   const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const size_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
   double* p1 = partials;                           // [k][kDotBlocks]
-  double* p2 = partials + (size_t)k * kDotBlocks;  // [k][kDotBlocks]
-  double* p3 = partials + (size_t)2 * k * kDotBlocks;
+  double* p2 = partials + (size_t)k * kDotBlocks;  // [k + 1][kDotBlocks]
   __shared__ T hT[64];
   constexpr int kG = 8;                // dot products reduced together
   constexpr int kW = kThreads / 32;
   __shared__ double sg[kW][kG];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // the k partial dot products <V[i], w> (or <w, w> if V is null) of this
-  // block's chunk, kG at a time in one pass over the elements: products and
-  // per-thread sums in T, then per value a shuffle tree in each warp and a
-  // second one over the warps' sums (the order of block_sum)
-  auto dots = [&](const T* Vb, int nk, double* part) {
+  // the nk partial dot products <V[i], w> for i < nv and <w, w> for i >= nv
+  // of this block's chunk, kG at a time in one pass over the elements:
+  // products and per-thread sums in T, then per value a shuffle tree in each
+  // warp and a second one over the warps' sums (the order of block_sum)
+  auto dots = [&](const T* Vb, int nv, int nk, double* part) {
     for (int i0 = 0; i0 < nk; i0 += kG) {
       const int gk = min(kG, nk - i0);
       T acc[kG];
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(kThreads)
         const T we = w[e];
 #pragma unroll
         for (int u = 0; u < kG; ++u)
-          if (u < gk) acc[u] += (Vb ? Vb[(size_t)(i0 + u) * ld + e] : we) * we;
+          if (u < gk) acc[u] += (i0 + u < nv ? Vb[(size_t)(i0 + u) * ld + e] : we) * we;
       }
 #pragma unroll
       for (int u = 0; u < kG; ++u) {
@@ -204,17 +205,20 @@ __global__ void __launch_bounds__(kThreads)
     }
     __syncthreads();  // hT is rewritten by the next pass
   };
-  dots(V, k, p1);
+  dots(V, k, k, p1);
   grid.sync();
   finish(p1, k, h[0]);
   axpy(h[0]);
-  dots(V, k, p2);
+  dots(V, k, k + 1, p2);
   grid.sync();
-  finish(p2, k, h[1]);
+  finish(p2, k + 1, h[1]);  // h[1][k] = <w, w> before the second update
   axpy(h[1]);
-  dots(nullptr, 1, p3);
-  grid.sync();
-  finish(p3, 1, &nrm2);
+  if (threadIdx.x == 0) {
+    double q = h[1][k];
+    for (int i = 0; i < k; ++i) q -= h[1][i] * h[1][i];
+    nrm2 = q;
+  }
+  __syncthreads();
   const double s = block_scalar([&] {
     const double v = sqrt(fmax(nrm2, 0.0));
     return v != 0.0 ? 1.0 / v : 0.0;
@@ -289,7 +293,7 @@ template <typename T>
 int launch_arnoldi_step(const T* V, size_t ld, int j, T* w, size_t n, double* partials,
                         double* hcol, double* H, int ldh, double* cs, double* sn, double* gvec,
                         double* resid, cudaStream_t st) {
-  if (j + 1 > 64) return 1;
+  if (j + 2 > 64) return 1;  // the second pass holds k + 1 values
   static const bool fits = [] {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
