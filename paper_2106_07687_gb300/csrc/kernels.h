@@ -51,6 +51,21 @@ void launch_prolong_add(const Grid& fine, const Grid& coarse, const T* xc, T* x,
 template <typename T>
 void launch_inject(const Grid& fine, const Grid& coarse, const T* xf, T* xc, int ncomp,
                    cudaStream_t st);
+// Every level's linearisation point from the finest velocity at once: level
+// k of nlev (the last the finest) takes the fine node (2^m I, 2^m J), m =
+// nlev-1-k, which is the nodal injection applied m times.  Writes vb64 (FP64)
+// and vb (T) of each level, vbJ (T) of the finest, and clears *status when
+// status is not null.  One launch; results equal inject + cast bit for bit.
+template <typename T>
+struct LinLevels {
+  int nlev;
+  int nnx[kMaxLevels], nn[kMaxLevels], off[kMaxLevels + 1];  // off: prefix of nn
+  double* vb64[kMaxLevels];
+  T* vb[kMaxLevels];
+};
+template <typename T>
+void launch_linearize_levels(const LinLevels<T>& L, const double* x64, T* vbJ, int* status,
+                             cudaStream_t st);
 // Unmasked bilinear prolongation of ncomp fields (DNN-MG state transfer).
 void launch_prolong_state64(const Grid& fine, const Grid& coarse, const double* xc, double* xf,
                             int ncomp, cudaStream_t st);
@@ -118,15 +133,32 @@ template <typename T>
 void launch_coarse_solve(const Grid& g, const double* Ainv, const T* b, T* x, cudaStream_t st);
 
 // Vectors (vec.cu) ----------------------------------------------------------
+// A scalar mailbox in mapped pinned host memory.  A kernel stores the values
+// the host needs (v, iv), then, after a system-scope fence, the sequence
+// number of the post; the host polls seq instead of copying the values back
+// and synchronising the stream, which shortens each host round trip of the
+// Newton and FGMRES loops.  Posts on one stream carry increasing numbers, so
+// seq >= t means that post t and every earlier one have landed.
+struct HostMail {
+  volatile double v[8];
+  volatile int iv[8];
+  volatile unsigned long long seq;
+};
+// Post n doubles from src (device) into v[slot..] and ni ints from isrc into
+// iv[islot..] as post number seq (one thread; src/isrc may be null).
+void launch_post(HostMail* mail, unsigned long long seq, const double* src, int slot, int n,
+                 const int* isrc, int islot, int ni, cudaStream_t st);
 template <typename Ts, typename Td>
 void launch_cast(const Ts* a, Td* b, size_t n, cudaStream_t st);
 template <typename T>
 void launch_fill(T* a, T v, size_t n, cudaStream_t st);
 // partial dot products of w against k vectors V[i] (stride ld); out[k] after
 // launch_dots_finish.  partials needs dots_partials(n, k) doubles.
+// With mail (k = 1 only), out[0] is also posted into mail->v[0] as post seq.
 template <typename T>
 void launch_multidot(const T* V, size_t ld, int k, const T* w, size_t n, double* partials,
-                     double* out, cudaStream_t st);
+                     double* out, cudaStream_t st, HostMail* mail = nullptr,
+                     unsigned long long seq = 0);
 // w -= sum_i h[i] V[i]
 template <typename T>
 void launch_multiaxpy(const T* V, size_t ld, int k, const double* h, T* w, size_t n,
@@ -143,11 +175,13 @@ size_t dots_partials(size_t n, int k);
 // column j, resid = |g[j+1]|) in one cooperative launch; products in the
 // vectors' precision, sums over threads and blocks in FP64.  Returns nonzero
 // (nothing launched) when the cooperative grid cannot be resident.  partials needs (2 j + 3) x
-// dots_partials(n, 1) doubles, hcol 2 j + 3.
+// dots_partials(n, 1) doubles, hcol 2 j + 3.  With mail, resid is also
+// posted into mail->v[0] as post seq.
 template <typename T>
 int launch_arnoldi_step(const T* V, size_t ld, int j, T* w, size_t n, double* partials,
                         double* hcol, double* H, int ldh, double* cs, double* sn, double* gvec,
-                        double* resid, cudaStream_t st);
+                        double* resid, cudaStream_t st, HostMail* mail = nullptr,
+                        unsigned long long seq = 0);
 // FGMRES small-matrix kernels: Hessenberg column j (from h[0..j+1]) is
 // rotated, the new Givens rotation stored and g updated; resid = |g[j+1]|.
 void launch_givens(double* H, int ldh, double* cs, double* sn, double* gvec, const double* hcol,
@@ -155,10 +189,28 @@ void launch_givens(double* H, int ldh, double* cs, double* sn, double* gvec, con
 // y = H[0:k,0:k]^{-1} g[0:k] (back substitution)
 void launch_backsolve(const double* H, int ldh, const double* gvec, int k, double* y,
                       cudaStream_t st);
-// set V0 = r / ||r|| with norm from nrm2[0]; g[0] = ||r||
+// The start of an FGMRES cycle (one cooperative launch; nonzero return:
+// nothing launched, the grid cannot be resident): with init, rT = (T) r64,
+// rcur = rT, wsol = 0; then hcol[0] = |rcur|^2, V0 = rcur / |rcur|,
+// gvec[0] = |rcur|, and with mail |rcur|^2 posted into mail->v[1].  Equal bit
+// for bit to cast, fill, copy, launch_multidot and launch_gmres_start.
+// partials needs dots_partials(n, 1) doubles.
+template <typename T>
+int launch_fgmres_begin(const double* r64, T* rT, T* wsol, T* rcur, T* v0, size_t n,
+                        double* partials, double* hcol, double* gvec, bool init, HostMail* mail,
+                        unsigned long long seq, cudaStream_t st);
+// The end of a converged FGMRES cycle: y = H[0:k,0:k]^{-1} g[0:k], then
+// x64 += eps * (T)(wsol + sum_i y[i] Z[i]); equal bit for bit to
+// launch_backsolve, launch_combine into wsol and launch_combine into x64.
+template <typename T>
+void launch_fgmres_finish(const double* H, int ldh, const double* gvec, int k, const T* Z,
+                          size_t ld, const T* wsol, double eps, double* x64, size_t n,
+                          cudaStream_t st);
+// set V0 = r / ||r|| with norm from nrm2[0]; g[0] = ||r||.  With mail,
+// nrm2[0] is also posted into mail->v[1] as post seq.
 template <typename T>
 void launch_gmres_start(const T* r, const double* nrm2, T* v0, double* gvec, size_t n,
-                        cudaStream_t st);
+                        cudaStream_t st, HostMail* mail = nullptr, unsigned long long seq = 0);
 
 // ---- functionals of Sec. 3.4 (functionals.cu) --------------------------------
 // Backward-Euler constants of a level (theta = 1) and its mass matrix over k.

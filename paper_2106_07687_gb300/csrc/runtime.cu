@@ -52,6 +52,15 @@ class Solver final : public SolverBase {
         lv_[k].stream_ok = lv_[k].inv && vanka_stream_grid(lv_[k].g) > 0 &&
                            make_vanka_tensor_map(lv_[k].tmap, (const float*)lv_[k].inv, lv_[k].g);
     }
+    lin_.nlev = K_ + 1;
+    lin_.off[0] = 0;
+    for (int k = 0; k <= K_; ++k) {
+      lin_.nnx[k] = lv_[k].g.nnx;
+      lin_.nn[k] = lv_[k].g.nn;
+      lin_.off[k + 1] = lin_.off[k] + lv_[k].g.nn;
+      lin_.vb64[k] = lv_[k].vb64;
+      lin_.vb[k] = lv_[k].vb;
+    }
     const Grid& g0 = lv_[0].g;
     if (!coarse_supported(g0)) return c_->fail(DNNMG_ERR_ARG, "coarse level too large");
     // a level-1 obstacle at odd offsets leaves part-solid patches on the coarse level
@@ -74,7 +83,6 @@ class Solver final : public SolverBase {
     gv_ = c_->mem.alloc<double>(m_ + 2);
     hcol_ = c_->mem.alloc<double>(2 * m_ + 4);
     y_ = c_->mem.alloc<double>(m_ + 1);
-    one_ = c_->mem.alloc<double>(1);
     vbJ_ = c_->mem.alloc<T>(2 * (size_t)lv_[K_].g.nn);
     partials_ = c_->mem.alloc<double>(dots_partials(n_, 2 * m_ + 4));
     if (!c_->mem.ok()) return c_->fail(DNNMG_ERR_CUDA, "device allocation failed");
@@ -125,8 +133,6 @@ class Solver final : public SolverBase {
         side_ev_.push_back(e);
       }
     }
-    const double one = 1.0;
-    cudaMemcpyAsync(one_, &one, sizeof(double), cudaMemcpyHostToDevice, st_);
     return c_->check("solver init");
   }
 
@@ -136,16 +142,14 @@ class Solver final : public SolverBase {
   // down the hierarchy, Vanka inverses, coarse LU and inverse.
   int linearize(const double* x64, bool coarse, bool precond, bool report) override {
     // the Jacobian of the FGMRES matvec always follows the current iterate
-    launch_cast<double, T>(x64, vbJ_, 2 * (size_t)lv_[K_].g.nn, st_);
     linearized_j_ = true;
-    if (!precond && linearized_) return c_->check("linearize");
-    cudaMemcpyAsync(lv_[K_].vb64, x64, 2 * sizeof(double) * lv_[K_].g.nn,
-                    cudaMemcpyDeviceToDevice, st_);
-    for (int k = K_; k > 0; --k)
-      launch_inject<double>(lv_[k].g, lv_[k - 1].g, lv_[k].vb64, lv_[k - 1].vb64, 2, st_);
-    if (report || !tuned_) cudaMemsetAsync(status_, 0, sizeof(int), st_);
-    for (int k = 0; k <= K_; ++k)
-      launch_cast<double, T>(lv_[k].vb64, lv_[k].vb, 2 * (size_t)lv_[k].g.nn, st_);
+    if (!precond && linearized_) {
+      launch_cast<double, T>(x64, vbJ_, 2 * (size_t)lv_[K_].g.nn, st_);
+      return c_->check("linearize");
+    }
+    // every level's point (injection down the hierarchy, FP64 and T copies)
+    // and the matvec's, in one launch
+    launch_linearize_levels<T>(lin_, x64, vbJ_, report || !tuned_ ? status_ : nullptr, st_);
     // the levels' setups are independent and each leaves most of the GPU
     // idle: levels below the top run on side streams beside it
     const int p = c_->prof.begin(DNNMG_STAGE_VANKA_SETUP, lv_[K_].level, st_);
@@ -208,20 +212,27 @@ class Solver final : public SolverBase {
   // re-orthogonalisation; x64 += eps * w at the end.
   int solve(const double* r64, double* x64, double eps, int* its_out) override {
     const dnnmg_config& cfg = c_->cfg;
-    launch_cast<double, T>(r64, rT_, n_, st_);
-    launch_fill<T>(wsol_, T(0), n_, st_);
-    cudaMemcpyAsync(rcur_, rT_, n_ * sizeof(T), cudaMemcpyDeviceToDevice, st_);
     int its = 0;
     double target = -1.0;
     bool done = false;
     while (!done) {
-      launch_multidot<T>(rcur_, n_, 1, rcur_, n_, partials_, hcol_, st_);
       // |r|^2 of the first cycle travels to the host beside the first
-      // iteration's residual estimate (one synchronisation for both)
+      // iteration's residual estimate (one wait for both)
       bool first = target < 0;
-      if (first)
-        cudaMemcpyAsync(c_->h_scalars + 1, hcol_, sizeof(double), cudaMemcpyDeviceToHost, st_);
-      launch_gmres_start<T>(rcur_, hcol_, V_, gv_, n_, st_);
+      HostMail* mail = first ? c_->mail_d : nullptr;
+      const unsigned long long t0 = first ? c_->mail_ticket() : 0;
+      // rounding of r, zero correction, |r|, V0 in one launch where the
+      // cooperative grid fits, else the separate steps
+      if (launch_fgmres_begin<T>(r64, rT_, wsol_, rcur_, V_, n_, partials_, hcol_, gv_, first,
+                                 mail, t0, st_) != 0) {
+        if (first) {
+          launch_cast<double, T>(r64, rT_, n_, st_);
+          launch_fill<T>(wsol_, T(0), n_, st_);
+          cudaMemcpyAsync(rcur_, rT_, n_ * sizeof(T), cudaMemcpyDeviceToDevice, st_);
+        }
+        launch_multidot<T>(rcur_, n_, 1, rcur_, n_, partials_, hcol_, st_);
+        launch_gmres_start<T>(rcur_, hcol_, V_, gv_, n_, st_, mail, t0);
+      }
       int k = 0;
       for (int j = 0; j < m_; ++j) {
         T* vj = V_ + (size_t)j * n_;
@@ -233,8 +244,9 @@ class Solver final : public SolverBase {
         launch_apply<T>(lv_[K_].g, lv_[K_].s, zj, vbJ_, w, st_);
         c_->prof.end(p, st_);
         p = c_->prof.begin(DNNMG_STAGE_KRYLOV, lv_[K_].level, st_);
+        const unsigned long long ticket = c_->mail_ticket();
         if (launch_arnoldi_step<T>(V_, n_, j, w, n_, partials_, hcol_, H_, m_ + 1, cs_, sn_, gv_,
-                                   y_ + m_, st_) != 0) {
+                                   y_ + m_, st_, c_->mail_d, ticket) != 0) {
           launch_multidot<T>(V_, n_, j + 1, w, n_, partials_, hcol_, st_);
           launch_multiaxpy<T>(V_, n_, j + 1, hcol_, w, n_, st_);
           launch_multidot<T>(V_, n_, j + 1, w, n_, partials_, hcol_ + j + 1, st_);
@@ -242,16 +254,18 @@ class Solver final : public SolverBase {
           launch_multidot<T>(w, n_, 1, w, n_, partials_, hcol_ + 2 * j + 2, st_);
           launch_givens(H_, m_ + 1, cs_, sn_, gv_, hcol_, j, y_ + m_, st_);
           launch_scale_dev<T>(w, hcol_ + 2 * j + 2, 2, w, n_, st_);
+          launch_post(c_->mail_d, ticket, y_ + m_, 0, 1, nullptr, 0, 0, st_);
         }
         c_->prof.end(p, st_);
         ++its;
         k = j + 1;
-        double res = 0;
-        if (int rc = read_scalar(y_ + m_, &res)) return rc;
+        // the residual estimate (and, in the first cycle, |r|^2 posted
+        // by gmres_start) from the host mailbox
+        if (int rc = c_->mail_wait(ticket, "fgmres")) return rc;
+        const double res = c_->mail_h->v[0];
         if (first) {
           first = false;
-          double b2 = 0;
-          std::memcpy(&b2, c_->h_scalars + 1, sizeof(double));
+          const double b2 = c_->mail_h->v[1];
           if (!(b2 > 0)) {  // zero right-hand side: no update (the iteration is discarded)
             its = 0;
             k = 0;
@@ -268,14 +282,16 @@ class Solver final : public SolverBase {
         }
       }
       if (k == 0) break;
+      if (done) {
+        // y = H^-1 g and x64 += eps (wsol + Z y) in one launch
+        launch_fgmres_finish<T>(H_, m_ + 1, gv_, k, Z_, n_, wsol_, eps, x64, n_, st_);
+        break;
+      }
       launch_backsolve(H_, m_ + 1, gv_, k, y_, st_);
       launch_combine<T, T>(Z_, n_, k, y_, 1.0, wsol_, n_, st_);
-      if (!done) {
-        // restart from the true residual of the current iterate
-        launch_defect<T>(lv_[K_].g, lv_[K_].s, rT_, wsol_, vbJ_, rcur_, false, st_);
-      }
+      // restart from the true residual of the current iterate
+      launch_defect<T>(lv_[K_].g, lv_[K_].s, rT_, wsol_, vbJ_, rcur_, false, st_);
     }
-    launch_combine<T, double>(wsol_, n_, 1, one_, eps, x64, n_, st_);
     if (its_out) *its_out = its;
     return c_->check("fgmres");
   }
@@ -292,13 +308,6 @@ class Solver final : public SolverBase {
     bool stream_ok = false;  // the streaming colour pass can run on this level
     bool stream = false;     // and the autotuner chose it
   };
-
-  int read_scalar(const double* dev, double* out) {
-    cudaMemcpyAsync(c_->h_scalars, dev, sizeof(double), cudaMemcpyDeviceToHost, st_);
-    if (cudaStreamSynchronize(st_) != cudaSuccess) return c_->check("sync");
-    std::memcpy(out, c_->h_scalars, sizeof(double));
-    return DNNMG_OK;
-  }
 
   // nu sweeps of four colour passes, ping-ponging between x and the level's
   // second buffer; an even number of passes leaves the result in x.
@@ -354,8 +363,10 @@ class Solver final : public SolverBase {
   }
   int device_status(int* setup) override {
     int st[4] = {0, 0, 0, 0};
-    cudaMemcpyAsync(st, status_, sizeof(st), cudaMemcpyDeviceToHost, st_);
-    if (cudaStreamSynchronize(st_) != cudaSuccess) return -1;
+    const unsigned long long t = c_->mail_ticket();
+    launch_post(c_->mail_d, t, nullptr, 0, 0, status_, 0, 4, st_);
+    if (c_->mail_wait(t, "status") != DNNMG_OK) return -1;
+    for (int i = 0; i < 4; ++i) st[i] = c_->mail_h->iv[i];
     if (st[2]) cudaMemsetAsync(status_ + 2, 0, sizeof(int), st_);  // reported once
     if (setup) *setup = st[0];
     return st[2];
@@ -508,10 +519,11 @@ class Solver final : public SolverBase {
   int* status_ = nullptr;
   T *V_ = nullptr, *Z_ = nullptr, *wsol_ = nullptr, *rT_ = nullptr, *rcur_ = nullptr;
   double *H_ = nullptr, *cs_ = nullptr, *sn_ = nullptr, *gv_ = nullptr, *hcol_ = nullptr,
-         *y_ = nullptr, *one_ = nullptr, *partials_ = nullptr;
+         *y_ = nullptr, *partials_ = nullptr;
   bool linearized_ = false, linearized_j_ = false;
   bool coarse_done_ = false;
   T* vbJ_ = nullptr;  // top-level linearisation of the FGMRES matvec
+  LinLevels<T> lin_ = {};  // every level's linearisation buffers
   VLevel<T>* dlv_ = nullptr;
   std::vector<cudaStream_t> side_;   // side_[k - 1]: setup of level k < K
   std::vector<cudaEvent_t> side_ev_;
@@ -554,6 +566,7 @@ dnnmg_ctx::~dnnmg_ctx() {
   if (st) cudaStreamSynchronize(st);
   solver.reset();
   if (h_scalars) cudaFreeHost(h_scalars);
+  if (mail_h) cudaFreeHost(mail_h);
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
 }
@@ -637,6 +650,10 @@ int dnnmg_ctx::init() {
   }
   if (cudaMallocHost(&h_scalars, 64 * sizeof(double)) != cudaSuccess)
     return fail(DNNMG_ERR_CUDA, "pinned allocation failed");
+  if (cudaHostAlloc(&mail_h, sizeof(HostMail), cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer(&mail_d, mail_h, 0) != cudaSuccess)
+    return fail(DNNMG_ERR_CUDA, "mapped pinned allocation failed");
+  mail_h->seq = 0;
   cudaEventCreate(&ev0);
   cudaEventCreate(&ev1);
   const Grid gL = grid(L());
@@ -1135,12 +1152,28 @@ int dnnmg_ctx::init_net() {
   return check("network setup");
 }
 
+int dnnmg_ctx::mail_wait(unsigned long long t, const char* what) {
+  if (int rc = check(what)) return rc;  // a failed launch never posts
+  for (unsigned polls = 1;; ++polls) {
+    if (__atomic_load_n(&mail_h->seq, __ATOMIC_ACQUIRE) >= t) return DNNMG_OK;
+    if (polls % 1024 == 0) {
+      // every kernel before the post has ended (or failed) once the stream
+      // is idle: the post is then either visible or never comes
+      const cudaError_t e = cudaStreamQuery(st);
+      if (e == cudaErrorNotReady) continue;
+      if (__atomic_load_n(&mail_h->seq, __ATOMIC_ACQUIRE) >= t) return DNNMG_OK;
+      if (e != cudaSuccess) return check(what);
+      return fail(DNNMG_ERR_CUDA, std::string(what) + ": the device posted no value");
+    }
+  }
+}
+
 int dnnmg_ctx::net_check(const char* what) {
   if (int rc = check(what)) return rc;
-  int s = 0;
-  cudaMemcpyAsync(h_scalars, net_status, sizeof(int), cudaMemcpyDeviceToHost, st);
-  if (cudaStreamSynchronize(st) != cudaSuccess) return check(what);
-  std::memcpy(&s, h_scalars, sizeof(int));
+  const unsigned long long t = mail_ticket();
+  launch_post(mail_d, t, nullptr, 0, 0, net_status, 0, 1, st);
+  if (int rc = mail_wait(t, what)) return rc;
+  const int s = mail_h->iv[0];
   if (s & 4) {
     cudaMemsetAsync(net_status, 0, sizeof(int), st);
     return fail(DNNMG_ERR_TIMEOUT, std::string(what) + ": tensor-core wait timed out");
@@ -1180,11 +1213,12 @@ void dnnmg_ctx::old_rhs(int level, const double* x_old, double* f) {
     launch_explicit_sub64(g, level == L() ? sxL : sxF, 1.0 - cfg.theta, x_old, f, st);
 }
 
-double dnnmg_ctx::norm64(const double* v, size_t n) {
-  launch_multidot<double>(v, n, 1, v, n, partials, dots, st);
-  cudaMemcpyAsync(h_scalars, dots, sizeof(double), cudaMemcpyDeviceToHost, st);
-  cudaStreamSynchronize(st);
-  return std::sqrt(h_scalars[0]);
+int dnnmg_ctx::norm64(const double* v, size_t n, double* out) {
+  const unsigned long long t = mail_ticket();
+  launch_multidot<double>(v, n, 1, v, n, partials, dots, st, mail_d, t);
+  if (int rc = mail_wait(t, "norm")) return rc;
+  *out = std::sqrt(mail_h->v[0]);
+  return DNNMG_OK;
 }
 
 int dnnmg_ctx::get_state(double* x) {
@@ -1230,7 +1264,8 @@ int dnnmg_ctx::newton(const double* f, dnnmg_step_stats* s) {
   int p = prof.begin(DNNMG_STAGE_RESIDUAL, L(), st);
   launch_residual64(gL, s64L, x64, f, r64, st, mixed());
   prof.end(p, st);
-  double nrm = norm64(r64, n3);
+  double nrm = 0;
+  if (int rc = norm64(r64, n3, &nrm)) return rc;
   s->res0 = nrm;
   int it = 0, gits = 0;
   // the linearisations' singularity flags are read once, after the loop
@@ -1250,7 +1285,7 @@ int dnnmg_ctx::newton(const double* f, dnnmg_step_stats* s) {
     p = prof.begin(DNNMG_STAGE_RESIDUAL, L(), st);
     launch_residual64(gL, s64L, x64, f, r64, st, mixed());
     prof.end(p, st);
-    nrm = norm64(r64, n3);
+    if (int rc = norm64(r64, n3, &nrm)) return rc;
     ++it;
   }
   s->newton_its = it;

@@ -169,6 +169,9 @@ struct dnnmg_ctx {
   double* dots = nullptr;      // small device scratch for reductions
   double* partials = nullptr;  // reduction partials
   double* h_scalars = nullptr; // pinned host scalars
+  dnnmg::HostMail* mail_h = nullptr;  // mapped pinned mailbox: host view
+  dnnmg::HostMail* mail_d = nullptr;  // and device view
+  unsigned long long mail_seq = 0;  // number of the last post issued on st
   double *fpart = nullptr, *fout = nullptr;  // functionals: partial sums, results
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   dnnmg::Prof prof;
@@ -209,6 +212,10 @@ struct dnnmg_ctx {
     return code;
   }
   int check(const char* what);
+  // the number of the next post on st
+  unsigned long long mail_ticket() { return ++mail_seq; }
+  // wait (host poll, bounded by the stream's progress) until post t landed
+  int mail_wait(unsigned long long t, const char* what);
   dnnmg::Grid grid(int level) const { return lv[level].g; }
   int L() const { return cfg.level_solve; }
   // the level the network corrects: L + replaced_levels
@@ -216,7 +223,7 @@ struct dnnmg_ctx {
   int lc() const { return cfg.level_coarse; }
   // mixed precision: the FP64 residuals evaluate the operator in double-float
   bool mixed() const { return cfg.precision == DNNMG_MIXED; }
-  double norm64(const double* v, size_t n);  // synchronous
+  int norm64(const double* v, size_t n, double* out);  // waits for the value
 
   int get_state(double* x);
   int set_state(const double* x);

@@ -41,6 +41,25 @@ __global__ void inject_kernel(Grid f, Grid c, const T* __restrict__ xf, T* __res
   inject_node<T>(f, c, xf, xc, ncomp, I, J);
 }
 
+template <typename T>
+__global__ void linearize_levels_kernel(const __grid_constant__ LinLevels<T> L,
+                                        const double* x64, T* vbJ, int* status) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0 && status) *status = 0;
+  if (t >= L.off[L.nlev]) return;
+  int k = 0;
+  while (t >= L.off[k + 1]) ++k;
+  const int top = L.nlev - 1, m = top - k;
+  const int n = t - L.off[k], J = n / L.nnx[k], I = n - J * L.nnx[k];
+  const int f = ((J << m) * L.nnx[top]) + (I << m);
+  for (int comp = 0; comp < 2; ++comp) {
+    const double v = x64[comp * L.nn[top] + f];
+    L.vb64[k][comp * L.nn[k] + n] = v;
+    L.vb[k][comp * L.nn[k] + n] = static_cast<T>(v);
+    if (k == top) vbJ[comp * L.nn[k] + n] = static_cast<T>(v);
+  }
+}
+
 inline dim3 grid_of(const Grid& g) { return dim3(cdiv(g.nnx, kBX), cdiv(g.nny, kBY)); }
 
 }  // namespace
@@ -64,6 +83,14 @@ void launch_inject(const Grid& fine, const Grid& coarse, const T* xf, T* xc, int
   inject_kernel<T><<<grid_of(coarse), dim3(kBX, kBY), 0, st>>>(fine, coarse, xf, xc, ncomp);
 }
 
+template <typename T>
+void launch_linearize_levels(const LinLevels<T>& L, const double* x64, T* vbJ, int* status,
+                             cudaStream_t st) {
+  note_launch();
+  const int n = L.off[L.nlev] > 0 ? L.off[L.nlev] : 1;
+  linearize_levels_kernel<T><<<cdiv(n, 256), 256, 0, st>>>(L, x64, vbJ, status);
+}
+
 void launch_prolong_state64(const Grid& fine, const Grid& coarse, const double* xc, double* xf,
                             int ncomp, cudaStream_t st) {
   note_launch();
@@ -80,7 +107,9 @@ void launch_restrict_full64(const Grid& fine, const Grid& coarse, const double* 
 #define DNNMG_INST(T)                                                                         \
   template void launch_restrict<T>(const Grid&, const Grid&, const T*, T*, cudaStream_t);     \
   template void launch_prolong_add<T>(const Grid&, const Grid&, const T*, T*, cudaStream_t);  \
-  template void launch_inject<T>(const Grid&, const Grid&, const T*, T*, int, cudaStream_t);
+  template void launch_inject<T>(const Grid&, const Grid&, const T*, T*, int, cudaStream_t);     \
+  template void launch_linearize_levels<T>(const LinLevels<T>&, const double*, T*, int*,        \
+                                           cudaStream_t);
 DNNMG_INST(float)
 DNNMG_INST(double)
 #undef DNNMG_INST

@@ -46,12 +46,34 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-__global__ void dots_finish_kernel(const double* __restrict__ partials, int nb, double* out) {
+// the values of a post are stored before the sequence number, with a
+// system-scope fence between them (the host reads seq first)
+__device__ __forceinline__ void mail_post(HostMail* m, unsigned long long seq) {
+  __threadfence_system();
+  m->seq = seq;
+}
+
+__global__ void post_kernel(HostMail* m, unsigned long long seq, const double* src, int slot,
+                            int n, const int* isrc, int islot, int ni) {
+  if (threadIdx.x != 0) return;
+  for (int i = 0; i < n; ++i) m->v[slot + i] = src[i];
+  for (int i = 0; i < ni; ++i) m->iv[islot + i] = isrc[i];
+  mail_post(m, seq);
+}
+
+__global__ void dots_finish_kernel(const double* __restrict__ partials, int nb, double* out,
+                                   HostMail* mail, unsigned long long seq) {
   __shared__ double sh[32];
   double acc = 0.0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += partials[(size_t)blockIdx.x * nb + b];
   const double t = block_sum(acc, sh);
-  if (threadIdx.x == 0) out[blockIdx.x] = t;
+  if (threadIdx.x == 0) {
+    out[blockIdx.x] = t;
+    if (mail) {  // a single block (k = 1)
+      mail->v[0] = t;
+      mail_post(mail, seq);
+    }
+  }
 }
 
 template <typename T>
@@ -110,10 +132,16 @@ __global__ void backsolve_kernel(const double* H, int ldh, const double* g, int 
 
 template <typename T>
 __global__ void gmres_start_kernel(const T* __restrict__ r, const double* nrm2, T* __restrict__ v0,
-                                   double* g, size_t n) {
+                                   double* g, size_t n, HostMail* mail, unsigned long long seq) {
   const double beta = block_scalar([&] { return sqrt(fmax(*nrm2, 0.0)); });
   const double s = block_scalar([&] { return beta > 0 ? 1.0 / beta : 0.0; });
-  if (blockIdx.x == 0 && threadIdx.x == 0) g[0] = beta;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    g[0] = beta;
+    if (mail) {
+      mail->v[1] = *nrm2;
+      mail_post(mail, seq);
+    }
+  }
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
        e += (size_t)gridDim.x * blockDim.x)
     v0[e] = (T)(s * (double)r[e]);
@@ -136,7 +164,8 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
     arnoldi_kernel(const T* __restrict__ V, size_t ld, int j, T* __restrict__ w, size_t n,
                    double* __restrict__ partials, double* __restrict__ hcol, double* H, int ldh,
-                   double* cs, double* sn, double* g, double* resid) {
+                   double* cs, double* sn, double* g, double* resid, HostMail* mail,
+                   unsigned long long seq) {
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
   __shared__ double h[2][64];
@@ -228,7 +257,91 @@ __global__ void __launch_bounds__(kThreads)
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     for (int i = 0; i < k; ++i) hcol[i] = h[0][i], hcol[k + i] = h[1][i];
     hcol[2 * k] = nrm2;
-    *resid = givens_column(H, ldh, cs, sn, g, hcol, j);
+    const double res = givens_column(H, ldh, cs, sn, g, hcol, j);
+    *resid = res;
+    if (mail) {
+      mail->v[0] = res;
+      mail_post(mail, seq);
+    }
+  }
+}
+
+// The start of an FGMRES cycle in one cooperative launch of kDotBlocks
+// blocks: with init, the right-hand side r64 is rounded to T (rT, and the
+// first residual rcur = rT) and the correction wsol cleared; then |rcur|^2
+// (the chunks, per-thread sums and block sums of multidot_kernel, the sum
+// over the blocks' partials in the order of dots_finish_kernel, repeated by
+// every block), V0 = rcur / |rcur| and g[0] = |rcur| as gmres_start_kernel
+// computes them.  hcol[0] = |rcur|^2; with mail it is also posted into
+// mail->v[1].  Same results, bit for bit, as the separate launches.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    fgmres_begin_kernel(const double* __restrict__ r64, T* __restrict__ rT, T* __restrict__ wsol,
+                        T* __restrict__ rcur, T* __restrict__ v0, size_t n,
+                        double* __restrict__ partials, double* hcol, double* g, int init,
+                        HostMail* mail, unsigned long long seq) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double sh[32];
+  __shared__ double nrm2s;
+  const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const size_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+  double acc = 0.0;
+  for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+    T t;
+    if (init) {
+      t = (T)r64[e];
+      rT[e] = t;
+      rcur[e] = t;
+      wsol[e] = T(0);
+    } else {
+      t = rcur[e];
+    }
+    acc += (double)t * (double)t;
+  }
+  const double bsum = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = bsum;
+  grid.sync();
+  acc = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) acc += partials[b];
+  const double tot = block_sum(acc, sh);
+  if (threadIdx.x == 0) nrm2s = tot;
+  __syncthreads();
+  const double nrm2 = nrm2s;
+  const double beta = block_scalar([&] { return sqrt(fmax(nrm2, 0.0)); });
+  const double sc = block_scalar([&] { return beta > 0 ? 1.0 / beta : 0.0; });
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    hcol[0] = nrm2;
+    g[0] = beta;
+    if (mail) {
+      mail->v[1] = nrm2;
+      mail_post(mail, seq);
+    }
+  }
+  // the thread's own elements of rcur (written above by this thread)
+  for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) v0[e] = (T)(sc * (double)rcur[e]);
+}
+
+// The end of a converged FGMRES cycle in one launch: y = H^-1 g (the
+// k x k back substitution, repeated by every block), then
+// x64 += eps * (T)(wsol + sum_i y_i Z_i), the arithmetic of combine_kernel
+// into wsol followed by combine_kernel into x64.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    fgmres_finish_kernel(const double* __restrict__ H, int ldh, const double* __restrict__ g,
+                         int k, const T* __restrict__ Z, size_t ld,
+                         const T* __restrict__ wsol, double eps, double* __restrict__ x64,
+                         size_t n) {
+  __shared__ double y[64];
+  if (threadIdx.x == 0) backsolve_small(H, ldh, g, k, y);
+  __syncthreads();
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < k; ++i) acc += y[i] * (double)Z[(size_t)i * ld + e];
+    const T ws = (T)((double)wsol[e] + 1.0 * acc);
+    const double a1 = 1.0 * (double)ws;
+    x64[e] = (double)(x64[e] + eps * a1);
   }
 }
 
@@ -262,11 +375,18 @@ void launch_fill(T* a, T v, size_t n, cudaStream_t st) {
 
 template <typename T>
 void launch_multidot(const T* V, size_t ld, int k, const T* w, size_t n, double* partials,
-                     double* out, cudaStream_t st) {
+                     double* out, cudaStream_t st, HostMail* mail, unsigned long long seq) {
   note_launch();
   multidot_kernel<T><<<kDotBlocks, kThreads, 0, st>>>(V, ld, k, w, n, partials);
   note_launch();
-  dots_finish_kernel<<<k, kThreads, 0, st>>>(partials, kDotBlocks, out);
+  dots_finish_kernel<<<k, kThreads, 0, st>>>(partials, kDotBlocks, out, k == 1 ? mail : nullptr,
+                                             seq);
+}
+
+void launch_post(HostMail* mail, unsigned long long seq, const double* src, int slot, int n,
+                 const int* isrc, int islot, int ni, cudaStream_t st) {
+  note_launch();
+  post_kernel<<<1, 32, 0, st>>>(mail, seq, src, slot, n, isrc, islot, ni);
 }
 
 template <typename T>
@@ -292,7 +412,7 @@ void launch_combine(const T* Z, size_t ld, int k, const double* y, double eps, T
 template <typename T>
 int launch_arnoldi_step(const T* V, size_t ld, int j, T* w, size_t n, double* partials,
                         double* hcol, double* H, int ldh, double* cs, double* sn, double* gvec,
-                        double* resid, cudaStream_t st) {
+                        double* resid, cudaStream_t st, HostMail* mail, unsigned long long seq) {
   if (j + 2 > 64) return 1;  // the second pass holds k + 1 values
   static const bool fits = [] {
     int dev = 0, sms = 0, per = 0;
@@ -307,7 +427,7 @@ int launch_arnoldi_step(const T* V, size_t ld, int j, T* w, size_t n, double* pa
   if (!fits) return 1;
   void* args[] = {(void*)&V, (void*)&ld, (void*)&j, (void*)&w, (void*)&n, (void*)&partials,
                   (void*)&hcol, (void*)&H, (void*)&ldh, (void*)&cs, (void*)&sn, (void*)&gvec,
-                  (void*)&resid};
+                  (void*)&resid, (void*)&mail, (void*)&seq};
   if (cudaLaunchCooperativeKernel((void*)arnoldi_kernel<T>, dim3(kDotBlocks), dim3(kThreads),
                                   args, 0, st) != cudaSuccess) {
     cudaGetLastError();
@@ -330,26 +450,69 @@ void launch_backsolve(const double* H, int ldh, const double* gvec, int k, doubl
 }
 
 template <typename T>
-void launch_gmres_start(const T* r, const double* nrm2, T* v0, double* gvec, size_t n,
-                        cudaStream_t st) {
+int launch_fgmres_begin(const double* r64, T* rT, T* wsol, T* rcur, T* v0, size_t n,
+                        double* partials, double* hcol, double* gvec, bool init, HostMail* mail,
+                        unsigned long long seq, cudaStream_t st) {
+  static const bool fits = [] {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const bool ok = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fgmres_begin_kernel<T>,
+                                                                  kThreads, 0) == cudaSuccess &&
+                    per * sms >= kDotBlocks;
+    cudaGetLastError();
+    return ok;
+  }();
+  if (!fits) return 1;
+  int in = init ? 1 : 0;
+  void* args[] = {(void*)&r64,  (void*)&rT,       (void*)&wsol, (void*)&rcur,
+                  (void*)&v0,   (void*)&n,        (void*)&partials, (void*)&hcol,
+                  (void*)&gvec, (void*)&in,       (void*)&mail, (void*)&seq};
+  if (cudaLaunchCooperativeKernel((void*)fgmres_begin_kernel<T>, dim3(kDotBlocks), dim3(kThreads),
+                                  args, 0, st) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
   note_launch();
-  gmres_start_kernel<T><<<blocks_for(n), kThreads, 0, st>>>(r, nrm2, v0, gvec, n);
+  return 0;
+}
+
+template <typename T>
+void launch_fgmres_finish(const double* H, int ldh, const double* gvec, int k, const T* Z,
+                          size_t ld, const T* wsol, double eps, double* x64, size_t n,
+                          cudaStream_t st) {
+  note_launch();
+  const int nb = std::min(blocks_for(n), kDotBlocks);
+  fgmres_finish_kernel<T><<<nb, kThreads, 0, st>>>(H, ldh, gvec, k, Z, ld, wsol, eps, x64, n);
+}
+
+template <typename T>
+void launch_gmres_start(const T* r, const double* nrm2, T* v0, double* gvec, size_t n,
+                        cudaStream_t st, HostMail* mail, unsigned long long seq) {
+  note_launch();
+  gmres_start_kernel<T><<<blocks_for(n), kThreads, 0, st>>>(r, nrm2, v0, gvec, n, mail, seq);
 }
 
 #define DNNMG_INST(T)                                                                          \
   template void launch_fill<T>(T*, T, size_t, cudaStream_t);                                   \
   template void launch_multidot<T>(const T*, size_t, int, const T*, size_t, double*, double*,  \
-                                   cudaStream_t);                                              \
+                                   cudaStream_t, HostMail*, unsigned long long);               \
   template void launch_multiaxpy<T>(const T*, size_t, int, const double*, T*, size_t,          \
                                     cudaStream_t);                                             \
   template void launch_scale_dev<T>(const T*, const double*, int, T*, size_t, cudaStream_t);  \
   template void launch_gmres_start<T>(const T*, const double*, T*, double*, size_t,            \
-                                      cudaStream_t);                                           \
+                                      cudaStream_t, HostMail*, unsigned long long);            \
   template void launch_combine<T, T>(const T*, size_t, int, const double*, double, T*, size_t, \
                                      cudaStream_t);                                            \
   template int launch_arnoldi_step<T>(const T*, size_t, int, T*, size_t, double*, double*,     \
                                       double*, int, double*, double*, double*, double*,        \
-                                      cudaStream_t);
+                                      cudaStream_t, HostMail*, unsigned long long);            \
+  template int launch_fgmres_begin<T>(const double*, T*, T*, T*, T*, size_t, double*, double*, \
+                                      double*, bool, HostMail*, unsigned long long,            \
+                                      cudaStream_t);                                           \
+  template void launch_fgmres_finish<T>(const double*, int, const double*, int, const T*,      \
+                                        size_t, const T*, double, double*, size_t,             \
+                                        cudaStream_t);
 DNNMG_INST(float)
 DNNMG_INST(double)
 #undef DNNMG_INST
