@@ -191,17 +191,15 @@ void launch_backsolve(const double* H, int ldh, const double* gvec, int k, doubl
                       cudaStream_t st);
 // The start of an FGMRES cycle (one cooperative launch; nonzero return:
 // nothing launched, the grid cannot be resident): with init, rT = (T) r64,
-// rcur = rT, wsol = 0; then hcol[0] = |rcur|^2, V0 = rcur / |rcur|,
-// gvec[0] = |rcur|, and with mail |rcur|^2 posted into mail->v[1].  Equal bit
-// for bit to cast, fill, copy, launch_multidot and launch_gmres_start.
-// partials needs dots_partials(n, 1) doubles.
+// rcur = rT, wsol = 0; then hcol[0] = |rcur|^2 (products in T, sums in
+// FP64), V0 = rcur / |rcur|, gvec[0] = |rcur|, and with mail |rcur|^2 posted
+// into mail->v[1].  partials needs dots_partials(n, 1) doubles.
 template <typename T>
 int launch_fgmres_begin(const double* r64, T* rT, T* wsol, T* rcur, T* v0, size_t n,
                         double* partials, double* hcol, double* gvec, bool init, HostMail* mail,
                         unsigned long long seq, cudaStream_t st);
-// The end of a converged FGMRES cycle: y = H[0:k,0:k]^{-1} g[0:k], then
-// x64 += eps * (T)(wsol + sum_i y[i] Z[i]); equal bit for bit to
-// launch_backsolve, launch_combine into wsol and launch_combine into x64.
+// The end of a converged FGMRES cycle: y = H[0:k,0:k]^{-1} g[0:k] (FP64),
+// then x64 += eps * (wsol + sum_i y[i] Z[i]), the combination in T.
 template <typename T>
 void launch_fgmres_finish(const double* H, int ldh, const double* gvec, int k, const T* Z,
                           size_t ld, const T* wsol, double eps, double* x64, size_t n,

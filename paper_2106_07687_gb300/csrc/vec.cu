@@ -269,11 +269,11 @@ __global__ void __launch_bounds__(kThreads)
 // The start of an FGMRES cycle in one cooperative launch of kDotBlocks
 // blocks: with init, the right-hand side r64 is rounded to T (rT, and the
 // first residual rcur = rT) and the correction wsol cleared; then |rcur|^2
-// (the chunks, per-thread sums and block sums of multidot_kernel, the sum
-// over the blocks' partials in the order of dots_finish_kernel, repeated by
-// every block), V0 = rcur / |rcur| and g[0] = |rcur| as gmres_start_kernel
-// computes them.  hcol[0] = |rcur|^2; with mail it is also posted into
-// mail->v[1].  Same results, bit for bit, as the separate launches.
+// (the chunks of multidot_kernel; products and per-thread sums in T, the
+// sums over threads and over the blocks' partials in FP64, the latter in one
+// fixed order repeated by every block), V0 = rcur / |rcur| (scaled in T)
+// and g[0] = |rcur|.  hcol[0] = |rcur|^2; with mail it is also posted into
+// mail->v[1].  Per element only the rounding of r64 is an FP64 operation.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     fgmres_begin_kernel(const double* __restrict__ r64, T* __restrict__ rT, T* __restrict__ wsol,
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(kThreads)
   __shared__ double nrm2s;
   const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const size_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
-  double acc = 0.0;
+  T acc = T(0);
   for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
     T t;
     if (init) {
@@ -297,14 +297,14 @@ __global__ void __launch_bounds__(kThreads)
     } else {
       t = rcur[e];
     }
-    acc += (double)t * (double)t;
+    acc += t * t;
   }
-  const double bsum = block_sum(acc, sh);
+  const double bsum = block_sum((double)acc, sh);
   if (threadIdx.x == 0) partials[blockIdx.x] = bsum;
   grid.sync();
-  acc = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) acc += partials[b];
-  const double tot = block_sum(acc, sh);
+  double a2 = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) a2 += partials[b];
+  const double tot = block_sum(a2, sh);
   if (threadIdx.x == 0) nrm2s = tot;
   __syncthreads();
   const double nrm2 = nrm2s;
@@ -319,13 +319,14 @@ __global__ void __launch_bounds__(kThreads)
     }
   }
   // the thread's own elements of rcur (written above by this thread)
-  for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) v0[e] = (T)(sc * (double)rcur[e]);
+  const T sT = (T)sc;
+  for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) v0[e] = sT * rcur[e];
 }
 
 // The end of a converged FGMRES cycle in one launch: y = H^-1 g (the
-// k x k back substitution, repeated by every block), then
-// x64 += eps * (T)(wsol + sum_i y_i Z_i), the arithmetic of combine_kernel
-// into wsol followed by combine_kernel into x64.
+// k x k back substitution in FP64, repeated by every block), then
+// x64 += eps * (wsol + sum_i y_i Z_i) with the combination taken in T (the
+// precision of the Krylov vectors) and only the update of x64 in FP64.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     fgmres_finish_kernel(const double* __restrict__ H, int ldh, const double* __restrict__ g,
@@ -333,15 +334,17 @@ __global__ void __launch_bounds__(kThreads)
                          const T* __restrict__ wsol, double eps, double* __restrict__ x64,
                          size_t n) {
   __shared__ double y[64];
-  if (threadIdx.x == 0) backsolve_small(H, ldh, g, k, y);
+  __shared__ T yT[64];
+  if (threadIdx.x == 0) {
+    backsolve_small(H, ldh, g, k, y);
+    for (int i = 0; i < k; ++i) yT[i] = (T)y[i];
+  }
   __syncthreads();
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
        e += (size_t)gridDim.x * blockDim.x) {
-    double acc = 0.0;
-    for (int i = 0; i < k; ++i) acc += y[i] * (double)Z[(size_t)i * ld + e];
-    const T ws = (T)((double)wsol[e] + 1.0 * acc);
-    const double a1 = 1.0 * (double)ws;
-    x64[e] = (double)(x64[e] + eps * a1);
+    T acc = wsol[e];
+    for (int i = 0; i < k; ++i) acc += yT[i] * Z[(size_t)i * ld + e];
+    x64[e] += eps * (double)acc;
   }
 }
 
