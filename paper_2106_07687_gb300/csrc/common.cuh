@@ -52,6 +52,18 @@ __device__ __forceinline__ double block_scalar(F f) {
   return v;
 }
 
+// A scalar mailbox in mapped pinned host memory.  A kernel stores the values
+// the host needs (v, iv), then, after a system-scope fence, the sequence
+// number of the post; the host polls seq instead of copying the values back
+// and synchronising the stream, which shortens each host round trip of the
+// Newton and FGMRES loops.  Posts on one stream carry increasing numbers, so
+// seq >= t means that post t and every earlier one have landed.
+struct HostMail {
+  volatile double v[8];
+  volatile int iv[8];
+  volatile unsigned long long seq;
+};
+
 // Values of the four bilinear shape functions and their derivatives (times
 // h) at Gauss point q = qx + 2 qy.
 template <typename T>

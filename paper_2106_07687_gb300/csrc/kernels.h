@@ -133,17 +133,6 @@ template <typename T>
 void launch_coarse_solve(const Grid& g, const double* Ainv, const T* b, T* x, cudaStream_t st);
 
 // Vectors (vec.cu) ----------------------------------------------------------
-// A scalar mailbox in mapped pinned host memory.  A kernel stores the values
-// the host needs (v, iv), then, after a system-scope fence, the sequence
-// number of the post; the host polls seq instead of copying the values back
-// and synchronising the stream, which shortens each host round trip of the
-// Newton and FGMRES loops.  Posts on one stream carry increasing numbers, so
-// seq >= t means that post t and every earlier one have landed.
-struct HostMail {
-  volatile double v[8];
-  volatile int iv[8];
-  volatile unsigned long long seq;
-};
 // Post n doubles from src (device) into v[slot..] and ni ints from isrc into
 // iv[islot..] as post number seq (one thread; src/isrc may be null).
 void launch_post(HostMail* mail, unsigned long long seq, const double* src, int slot, int n,

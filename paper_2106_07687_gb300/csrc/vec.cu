@@ -46,13 +46,6 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-// the values of a post are stored before the sequence number, with a
-// system-scope fence between them (the host reads seq first)
-__device__ __forceinline__ void mail_post(HostMail* m, unsigned long long seq) {
-  __threadfence_system();
-  m->seq = seq;
-}
-
 __global__ void post_kernel(HostMail* m, unsigned long long seq, const double* src, int slot,
                             int n, const int* isrc, int islot, int ni) {
   if (threadIdx.x != 0) return;
@@ -147,123 +140,14 @@ __global__ void gmres_start_kernel(const T* __restrict__ r, const double* nrm2, 
     v0[e] = (T)(s * (double)r[e]);
 }
 
-// One Arnoldi step of FGMRES for the new vector w against V[0..j] (CGS with
-// one re-orthogonalisation, then normalisation and the Givens update of
-// Hessenberg column j) in one cooperative launch of kDotBlocks blocks with
-// two grid barriers: the second pass's products include <w, w>, and the
-// norm of the re-orthogonalised vector follows from it as ||w||^2 - |h2|^2
-// (the columns of V are orthonormal).  Block b owns the chunk of elements that multidot
-// assigns to it: it updates only that chunk, so the second pass's and the
-// norm's partial sums follow its own updates without a barrier, and every
-// block finishes the sums over all partials itself in one fixed order (one
-// warp per coefficient), so all blocks hold the same coefficients.  Products
-// and updates are taken in the vectors' precision T (a thread sums its few
-// products in T), the sums over threads and blocks in FP64: on this GPU an
-// FP64 operation per element would make the step FP64-bound.
+// One Arnoldi step (arnoldi_body) in one cooperative launch of kDotBlocks
+// blocks.
+constexpr int kArnThreads = 512;
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
-    arnoldi_kernel(const T* __restrict__ V, size_t ld, int j, T* __restrict__ w, size_t n,
-                   double* __restrict__ partials, double* __restrict__ hcol, double* H, int ldh,
-                   double* cs, double* sn, double* g, double* resid, HostMail* mail,
-                   unsigned long long seq) {
+__global__ void __launch_bounds__(kArnThreads) arnoldi_kernel(const ArnoldiArgs<T> a) {
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
-  __shared__ double h[2][64];
-  __shared__ double nrm2;
-  const int k = j + 1;
-  const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
-  const size_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
-  double* p1 = partials;                           // [k][kDotBlocks]
-  double* p2 = partials + (size_t)k * kDotBlocks;  // [k + 1][kDotBlocks]
-  __shared__ T hT[64];
-  constexpr int kG = 8;                // dot products reduced together
-  constexpr int kW = kThreads / 32;
-  __shared__ double sg[kW][kG];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // the nk partial dot products <V[i], w> for i < nv and <w, w> for i >= nv
-  // of this block's chunk, kG at a time in one pass over the elements:
-  // products and per-thread sums in T, then per value a shuffle tree in each
-  // warp and a second one over the warps' sums (the order of block_sum)
-  auto dots = [&](const T* Vb, int nv, int nk, double* part) {
-    for (int i0 = 0; i0 < nk; i0 += kG) {
-      const int gk = min(kG, nk - i0);
-      T acc[kG];
-#pragma unroll
-      for (int u = 0; u < kG; ++u) acc[u] = T(0);
-      for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
-        const T we = w[e];
-#pragma unroll
-        for (int u = 0; u < kG; ++u)
-          if (u < gk) acc[u] += (i0 + u < nv ? Vb[(size_t)(i0 + u) * ld + e] : we) * we;
-      }
-#pragma unroll
-      for (int u = 0; u < kG; ++u) {
-        if (u >= gk) break;
-        double v = (double)acc[u];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) sg[warp][u] = v;
-      }
-      __syncthreads();
-      if (warp < gk) {  // warp u finishes value u
-        double t = lane < kW ? sg[lane][warp] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) part[(size_t)(i0 + warp) * gridDim.x + blockIdx.x] = t;
-      }
-      __syncthreads();  // sg is rewritten by the next group
-    }
-  };
-  // out[i] = sum over the blocks' partials of row i, i < nk: one warp per
-  // row, lane l adding partials l, l + 32, ... in order, then a shuffle
-  // tree; the same fixed order in every block
-  auto finish = [&](const double* part, int nk, double* out) {
-    for (int i = warp; i < nk; i += kW) {
-      double t = 0.0;
-      for (int bb = lane; bb < kDotBlocks; bb += 32) t += part[(size_t)i * kDotBlocks + bb];
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (lane == 0) out[i] = t;
-    }
-    __syncthreads();
-  };
-  auto axpy = [&](const double* hh) {
-    if (threadIdx.x < k) hT[threadIdx.x] = (T)hh[threadIdx.x];
-    __syncthreads();
-    for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
-      T acc = w[e];
-      for (int i = 0; i < k; ++i) acc -= hT[i] * V[(size_t)i * ld + e];
-      w[e] = acc;
-    }
-    __syncthreads();  // hT is rewritten by the next pass
-  };
-  dots(V, k, k, p1);
-  grid.sync();
-  finish(p1, k, h[0]);
-  axpy(h[0]);
-  dots(V, k, k + 1, p2);
-  grid.sync();
-  finish(p2, k + 1, h[1]);  // h[1][k] = <w, w> before the second update
-  axpy(h[1]);
-  if (threadIdx.x == 0) {
-    double q = h[1][k];
-    for (int i = 0; i < k; ++i) q -= h[1][i] * h[1][i];
-    nrm2 = q;
-  }
-  __syncthreads();
-  const double s = block_scalar([&] {
-    const double v = sqrt(fmax(nrm2, 0.0));
-    return v != 0.0 ? 1.0 / v : 0.0;
-  });
-  const T sT = (T)s;
-  for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) w[e] *= sT;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    for (int i = 0; i < k; ++i) hcol[i] = h[0][i], hcol[k + i] = h[1][i];
-    hcol[2 * k] = nrm2;
-    const double res = givens_column(H, ldh, cs, sn, g, hcol, j);
-    *resid = res;
-    if (mail) {
-      mail->v[0] = res;
-      mail_post(mail, seq);
-    }
-  }
+  arnoldi_body<T, kArnThreads>(a, [&] { grid.sync(); });
 }
 
 // The start of an FGMRES cycle in one cooperative launch of kDotBlocks
@@ -417,22 +301,21 @@ int launch_arnoldi_step(const T* V, size_t ld, int j, T* w, size_t n, double* pa
                         double* hcol, double* H, int ldh, double* cs, double* sn, double* gvec,
                         double* resid, cudaStream_t st, HostMail* mail, unsigned long long seq) {
   if (j + 2 > 64) return 1;  // the second pass holds k + 1 values
-  static const bool fits = [] {
+  static const int nblk = [] {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const bool ok = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, arnoldi_kernel<T>,
-                                                                  kThreads, 0) == cudaSuccess &&
-                    per * sms >= kDotBlocks;
+                                                                  kArnThreads, 0) == cudaSuccess &&
+                    per >= 1 && sms <= kDotBlocks;
     cudaGetLastError();
-    return ok;
+    return ok ? sms : 0;
   }();
-  if (!fits) return 1;
-  void* args[] = {(void*)&V, (void*)&ld, (void*)&j, (void*)&w, (void*)&n, (void*)&partials,
-                  (void*)&hcol, (void*)&H, (void*)&ldh, (void*)&cs, (void*)&sn, (void*)&gvec,
-                  (void*)&resid, (void*)&mail, (void*)&seq};
-  if (cudaLaunchCooperativeKernel((void*)arnoldi_kernel<T>, dim3(kDotBlocks), dim3(kThreads),
-                                  args, 0, st) != cudaSuccess) {
+  if (nblk == 0) return 1;
+  const ArnoldiArgs<T> a{V, ld, j, w, n, partials, hcol, H, ldh, cs, sn, gvec, resid, mail, seq};
+  void* args[] = {(void*)&a};
+  if (cudaLaunchCooperativeKernel((void*)arnoldi_kernel<T>, dim3(nblk), dim3(kArnThreads), args,
+                                  0, st) != cudaSuccess) {
     cudaGetLastError();
     return 1;
   }
