@@ -24,8 +24,22 @@ void launch_defect(const Grid& g, const Sten<T>& s, const T* b, const T* x, cons
 // r = f - A(x) on free DOFs, 0 on constrained DOFs (FP64 nonlinear residual).
 // With dfloat_ops, A(x) is evaluated in double-float arithmetic (about 48
 // significant bits, FP32 units) and only f - A(x) in FP64.
+// With no.partials set, the launch also forms |r|^2: every block's sum in a
+// fixed order, then the last block to finish adds the blocks' sums in block
+// order, stores the total in *no.out, posts it into no.mail->v[0] (as post
+// no.seq, when mail is set) and resets *no.counter (zero between launches).
+// no.partials holds residual_blocks(g) doubles.
+struct NormOut {
+  double* partials = nullptr;
+  unsigned* counter = nullptr;
+  double* out = nullptr;
+  HostMail* mail = nullptr;
+  unsigned long long seq = 0;
+};
+int residual_blocks(const Grid& g);
 void launch_residual64(const Grid& g, const Sten<double>& s, const double* x, const double* f,
-                       double* r, cudaStream_t st, bool dfloat_ops = false);
+                       double* r, cudaStream_t st, bool dfloat_ops = false,
+                       const NormOut& no = NormOut{});
 // The fine-level residual f - A(x) whose only use is the network's input
 // features (rounded to BF16): the operator in FP32 when fp32_ops (mixed
 // precision contexts), else launch_residual64 in FP64.
@@ -67,8 +81,9 @@ template <typename T>
 void launch_linearize_levels(const LinLevels<T>& L, const double* x64, T* vbJ, int* status,
                              cudaStream_t st);
 // Unmasked bilinear prolongation of ncomp fields (DNN-MG state transfer).
+// With ximp (ncomp = 3), also ximp = xf with the Dirichlet values imposed.
 void launch_prolong_state64(const Grid& fine, const Grid& coarse, const double* xc, double* xf,
-                            int ncomp, cudaStream_t st);
+                            int ncomp, cudaStream_t st, double* ximp = nullptr);
 // Unmasked R = P^T of ncomp fields (DNN-MG right-hand side restriction).
 void launch_restrict_full64(const Grid& fine, const Grid& coarse, const double* bf, double* bc,
                             int ncomp, cudaStream_t st);
@@ -141,6 +156,9 @@ template <typename Ts, typename Td>
 void launch_cast(const Ts* a, Td* b, size_t n, cudaStream_t st);
 template <typename T>
 void launch_fill(T* a, T v, size_t n, cudaStream_t st);
+// b = a and d = c, n doubles each, in one launch
+void launch_copy2(const double* a, double* b, const double* c, double* d, size_t n,
+                  cudaStream_t st);
 // partial dot products of w against k vectors V[i] (stride ld); out[k] after
 // launch_dots_finish.  partials needs dots_partials(n, k) doubles.
 // With mail (k = 1 only), out[0] is also posted into mail->v[0] as post seq.

@@ -666,7 +666,10 @@ int dnnmg_ctx::init() {
   partials = mem.alloc<double>(dots_partials(n3, 4));
   fpart = mem.alloc<double>(4 * kFnBlocks);
   fout = mem.alloc<double>(4);
+  norm_partials = mem.alloc<double>(residual_blocks(gL));
+  norm_counter = mem.alloc<unsigned>(1);
   if (!mem.ok()) return fail(DNNMG_ERR_CUDA, "device allocation failed");
+  cudaMemsetAsync(norm_counter, 0, sizeof(unsigned), st);
   s64L = make_sten<double>(gL.h, cfg);
   sxL = make_explicit_sten(gL.h, cfg);
   if (cfg.replaced_levels > 0) sxF = make_explicit_sten(grid(fine_level()).h, cfg);
@@ -877,14 +880,14 @@ int dnnmg_ctx::init_dnnmg() {
 
 // P applied once per replaced level: xc on level L -> xf on the fine level
 // (ncomp fields; midF holds the level L+1 values when two levels are replaced)
-void dnnmg_ctx::prolong_up(const double* xc, double* xf, int ncomp) {
+void dnnmg_ctx::prolong_up(const double* xc, double* xf, int ncomp, double* ximp) {
   const Grid gL = grid(L()), gF = grid(fine_level());
   if (cfg.replaced_levels == 2) {
     const Grid gM = grid(L() + 1);
     launch_prolong_state64(gM, gL, xc, midF, ncomp, st);
-    launch_prolong_state64(gF, gM, midF, xf, ncomp, st);
+    launch_prolong_state64(gF, gM, midF, xf, ncomp, st, ximp);
   } else {
-    launch_prolong_state64(gF, gL, xc, xf, ncomp, st);
+    launch_prolong_state64(gF, gL, xc, xf, ncomp, st, ximp);
   }
 }
 
@@ -906,17 +909,14 @@ void dnnmg_ctx::restrict_down(const double* bf, double* bc) {
 // the network correction of Algorithm 1 after the level-L solve of this step (x64 = v^L_n).
 int dnnmg_ctx::dnnmg_correction() {
   const Grid gL = grid(L()), gF = grid(fine_level());
-  const size_t n3F = 3 * (size_t)gF.nn;
   const int K = (1 << cfg.replaced_levels) + 1;
   const int pr = prof.begin(DNNMG_STAGE_NETWORK, L(), st);
   if (!have_vcorr) {  // first correction: the previous fine velocity is P(v^L_{n-1})
     prolong_up(xold64, vcorr, 2);
     cudaMemsetAsync(vcorr + 2 * gF.nn, 0, sizeof(double) * gF.nn, st);
   }
-  prolong_up(x64, xtF, 3);                                            // P
+  prolong_up(x64, xtF, 3, ximpF);  // P, and the same with the Dirichlet values imposed
   old_rhs(fine_level(), vcorr, fF);
-  cudaMemcpyAsync(ximpF, xtF, n3F * sizeof(double), cudaMemcpyDeviceToDevice, st);
-  launch_impose_dirichlet64(gF, ximpF, st);
   launch_residual_features(gF, s64F, ximpF, fF, rF, st, mixed());  // input: fine residual
   launch_gather(gL, gF, K, patch_cell, P, xtF, rF, feat_mean, feat_std, cfg.nu, cfg.dt, X, st);
   launch_patchnet_forward(nd, pk, X, hid, hid, net_out, P, net_status, st);  // network
@@ -1258,14 +1258,27 @@ int dnnmg_ctx::residual_api(const double* x, const double* f, double* r) {
   return check("residual");
 }
 
-int dnnmg_ctx::newton(const double* f, dnnmg_step_stats* s) {
+// r64 = f - A(x64) and its norm (formed by the residual launch and read
+// through the host mailbox)
+int dnnmg_ctx::residual_norm(const double* f, double* nrm) {
   const Grid gL = grid(L());
-  const size_t n3 = 3 * (size_t)gL.nn;
-  int p = prof.begin(DNNMG_STAGE_RESIDUAL, L(), st);
-  launch_residual64(gL, s64L, x64, f, r64, st, mixed());
+  NormOut no;
+  no.partials = norm_partials;
+  no.counter = norm_counter;
+  no.out = dots;
+  no.mail = mail_d;
+  no.seq = mail_ticket();
+  const int p = prof.begin(DNNMG_STAGE_RESIDUAL, L(), st);
+  launch_residual64(gL, s64L, x64, f, r64, st, mixed(), no);
   prof.end(p, st);
+  if (int rc = mail_wait(no.seq, "residual norm")) return rc;
+  *nrm = std::sqrt(mail_h->v[0]);
+  return DNNMG_OK;
+}
+
+int dnnmg_ctx::newton(const double* f, dnnmg_step_stats* s) {
   double nrm = 0;
-  if (int rc = norm64(r64, n3, &nrm)) return rc;
+  if (int rc = residual_norm(f, &nrm)) return rc;
   s->res0 = nrm;
   int it = 0, gits = 0;
   // the linearisations' singularity flags are read once, after the loop
@@ -1282,10 +1295,7 @@ int dnnmg_ctx::newton(const double* f, dnnmg_step_stats* s) {
     int its = 0;
     if (int rc = solver->solve(r64, x64, cfg.eps_damp, &its)) return rc;
     gits += its;
-    p = prof.begin(DNNMG_STAGE_RESIDUAL, L(), st);
-    launch_residual64(gL, s64L, x64, f, r64, st, mixed());
-    prof.end(p, st);
-    if (int rc = norm64(r64, n3, &nrm)) return rc;
+    if (int rc = residual_norm(f, &nrm)) return rc;
     ++it;
   }
   s->newton_its = it;
@@ -1309,12 +1319,13 @@ int dnnmg_ctx::step(int mode, dnnmg_step_stats* stats) {
     return fail(DNNMG_ERR_ARG,
                 "DNN-MG steps need replaced_levels 1 or 2 and a network on the patch features");
   cudaEventRecord(ev0, st);
-  cudaMemcpyAsync(xold64, x64, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
   const bool use_net_rhs = mode == DNNMG_NET && have_net_rhs;
-  if (use_net_rhs)
-    cudaMemcpyAsync(f64, bL, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
-  else
+  if (use_net_rhs) {
+    launch_copy2(x64, xold64, bL, f64, n3, st);  // both copies in one launch
+  } else {
+    cudaMemcpyAsync(xold64, x64, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
     old_rhs(L(), xold64, f64);
+  }
   int rc = newton(f64, &s);
   if (use_net_rhs && (rc != DNNMG_OK || s.newton_its > cfg.fallback_newton_its)) {
     // the corrected right-hand side slowed Newton down: redo the step without it

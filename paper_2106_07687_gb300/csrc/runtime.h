@@ -224,6 +224,9 @@ struct dnnmg_ctx {
   // mixed precision: the FP64 residuals evaluate the operator in double-float
   bool mixed() const { return cfg.precision == DNNMG_MIXED; }
   int norm64(const double* v, size_t n, double* out);  // waits for the value
+  int residual_norm(const double* f, double* nrm);     // r64 = f - A(x64), waits for |r64|
+  double* norm_partials = nullptr;  // per-block sums of the residual launch
+  unsigned* norm_counter = nullptr; // blocks done (zero between launches)
 
   int get_state(double* x);
   int set_state(const double* x);
@@ -241,7 +244,9 @@ struct dnnmg_ctx {
   // f = old-time right-hand side of Eq. 5 from x_old on level `level`
   void old_rhs(int level, const double* x_old, double* f);
   int dnnmg_correction();
-  void prolong_up(const double* xc, double* xf, int ncomp);
+  // xf = P xc (each replaced level once); with ximp, also ximp = xf with the
+  // Dirichlet values imposed
+  void prolong_up(const double* xc, double* xf, int ncomp, double* ximp = nullptr);
   void restrict_down(const double* bf, double* bc);
   int set_feature_stats(const float* mean, const float* stdv);
   int get_fine_velocity(double* v);

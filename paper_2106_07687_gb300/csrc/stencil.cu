@@ -7,6 +7,7 @@
 // warp reads contiguous rows of the SoA fields.
 #include "kernels.h"
 #include "dfloat.cuh"
+#include "krylov_body.cuh"
 #include "optile_body.cuh"
 #include "vbody.cuh"
 
@@ -77,21 +78,55 @@ __global__ void __launch_bounds__(kTX* kTY)
     d[2 * nn + n] = b[2 * nn + n] - rp;
 }
 
+// |r|^2 over all blocks of the launch (see NormOut); every thread of the
+// block calls it with the squares of its node's residual (0 for none)
+__device__ __forceinline__ void norm_reduce(double sq, const NormOut& no) {
+  __shared__ double sh[32];
+  __shared__ bool last;
+  const double bs = block_sum(sq, sh);  // valid in thread 0
+  const int nb = gridDim.x * gridDim.y, b = blockIdx.y * gridDim.x + blockIdx.x;
+  if (threadIdx.x == 0) {
+    no.partials[b] = bs;
+    __threadfence();
+    last = atomicAdd(no.counter, 1u) == (unsigned)(nb - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double acc = 0.0;
+  for (int q = threadIdx.x; q < nb; q += blockDim.x) acc += __ldcg(no.partials + q);
+  const double tot = block_sum(acc, sh);
+  if (threadIdx.x == 0) {
+    *no.out = tot;
+    *no.counter = 0u;
+    if (no.mail) {
+      no.mail->v[0] = tot;
+      mail_post(no.mail, no.seq);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kTX* kTY)
     residual64_tiled_kernel(Grid g, Sten<double> s, const double* __restrict__ x,
-                            const double* __restrict__ f, double* __restrict__ r) {
+                            const double* __restrict__ f, double* __restrict__ r,
+                            const NormOut no) {
   extern __shared__ __align__(16) uint8_t smraw[];
   auto& S = *reinterpret_cast<OpSmem<double, kTX, kTY>*>(smraw);
   double ru, rv, rp;
   int n;
   op_tile_rows<double, true, false, kTX, kTY>(g, s, x, nullptr, blockIdx.x, blockIdx.y, S, ru, rv,
                                               rp, n);
-  if (n < 0) return;
-  const uint8_t fl = op_tile_flags<double, kTX, kTY>(S);
-  const int nn = g.nn;
-  r[n] = (fl & kVDir) ? 0.0 : f[n] - ru;
-  r[nn + n] = (fl & kVDir) ? 0.0 : f[nn + n] - rv;
-  r[2 * nn + n] = (fl & kPFix) ? 0.0 : f[2 * nn + n] - rp;
+  double sq = 0.0;
+  if (n >= 0) {
+    const uint8_t fl = op_tile_flags<double, kTX, kTY>(S);
+    const int nn = g.nn;
+    const double r0 = (fl & kVDir) ? 0.0 : f[n] - ru;
+    const double r1 = (fl & kVDir) ? 0.0 : f[nn + n] - rv;
+    const double r2 = (fl & kPFix) ? 0.0 : f[2 * nn + n] - rp;
+    r[n] = r0, r[nn + n] = r1, r[2 * nn + n] = r2;
+    sq = r0 * r0 + r1 * r1 + r2 * r2;
+  }
+  if (no.partials) norm_reduce(sq, no);
 }
 
 // The same residual with the operator evaluated in FP32 (the state rounded
@@ -119,19 +154,25 @@ __global__ void __launch_bounds__(kTX* kTY)
 // mixed-precision contexts.
 __global__ void __launch_bounds__(kTX* kTY)
     residual_df_tiled_kernel(Grid g, Sten<dfloat> s, const double* __restrict__ x,
-                             const double* __restrict__ f, double* __restrict__ r) {
+                             const double* __restrict__ f, double* __restrict__ r,
+                             const NormOut no) {
   extern __shared__ __align__(16) uint8_t smraw[];
   auto& S = *reinterpret_cast<OpSmem<dfloat, kTX, kTY>*>(smraw);
   dfloat ru, rv, rp;
   int n;
   op_tile_rows<dfloat, true, false, kTX, kTY, kTX * kTY, double>(
       g, s, x, nullptr, blockIdx.x, blockIdx.y, S, ru, rv, rp, n);
-  if (n < 0) return;
-  const uint8_t fl = op_tile_flags<dfloat, kTX, kTY>(S);
-  const int nn = g.nn;
-  r[n] = (fl & kVDir) ? 0.0 : f[n] - (double)ru;
-  r[nn + n] = (fl & kVDir) ? 0.0 : f[nn + n] - (double)rv;
-  r[2 * nn + n] = (fl & kPFix) ? 0.0 : f[2 * nn + n] - (double)rp;
+  double sq = 0.0;
+  if (n >= 0) {
+    const uint8_t fl = op_tile_flags<dfloat, kTX, kTY>(S);
+    const int nn = g.nn;
+    const double r0 = (fl & kVDir) ? 0.0 : f[n] - (double)ru;
+    const double r1 = (fl & kVDir) ? 0.0 : f[nn + n] - (double)rv;
+    const double r2 = (fl & kPFix) ? 0.0 : f[2 * nn + n] - (double)rp;
+    r[n] = r0, r[nn + n] = r1, r[2 * nn + n] = r2;
+    sq = r0 * r0 + r1 * r1 + r2 * r2;
+  }
+  if (no.partials) norm_reduce(sq, no);
 }
 
 inline dim3 tile_grid(const Grid& g) { return dim3(cdiv(g.nnx, kTX), cdiv(g.nny, kTY)); }
@@ -162,8 +203,10 @@ void launch_defect(const Grid& g, const Sten<T>& s, const T* b, const T* x, cons
   defect_tiled_kernel<T><<<tile_grid(g), kTX * kTY, sm, st>>>(g, s, b, x, vb, d, masked);
 }
 
+int residual_blocks(const Grid& g) { return cdiv(g.nnx, kTX) * cdiv(g.nny, kTY); }
+
 void launch_residual64(const Grid& g, const Sten<double>& s, const double* x, const double* f,
-                       double* r, cudaStream_t st, bool dfloat_ops) {
+                       double* r, cudaStream_t st, bool dfloat_ops, const NormOut& no) {
   if (dfloat_ops) {
     Sten<dfloat> sd;
     for (int e = 0; e < 16; ++e) {
@@ -177,12 +220,12 @@ void launch_residual64(const Grid& g, const Sten<double>& s, const double* x, co
     note_launch();
     static const size_t smd =
         smem_attr(residual_df_tiled_kernel, sizeof(OpSmem<dfloat, kTX, kTY>));
-    residual_df_tiled_kernel<<<tile_grid(g), kTX * kTY, smd, st>>>(g, sd, x, f, r);
+    residual_df_tiled_kernel<<<tile_grid(g), kTX * kTY, smd, st>>>(g, sd, x, f, r, no);
     return;
   }
   note_launch();
   static const size_t sm = smem_attr(residual64_tiled_kernel, sizeof(OpSmem<double, kTX, kTY>));
-  residual64_tiled_kernel<<<tile_grid(g), kTX * kTY, sm, st>>>(g, s, x, f, r);
+  residual64_tiled_kernel<<<tile_grid(g), kTX * kTY, sm, st>>>(g, s, x, f, r, no);
 }
 
 void launch_residual_features(const Grid& g, const Sten<double>& s, const double* x,

@@ -2,6 +2,7 @@
 // transpose R = P^T, and nodal injection (Sec. 2.2, the prolongation and restriction of Algorithm 1).
 // Inside the V-cycle both P and R act on free DOFs only; the DNN-MG state and
 // right-hand-side transfers use the unmasked operators.
+#include "dnnmg_body.cuh"
 #include "kernels.h"
 #include "vbody.cuh"
 
@@ -27,10 +28,16 @@ __global__ void prolong_add_kernel(Grid f, Grid c, const T* __restrict__ xc, T* 
 }
 
 __global__ void prolong_state_kernel(Grid f, Grid c, const double* __restrict__ xc,
-                                     double* __restrict__ xf, int ncomp) {
+                                     double* __restrict__ xf, int ncomp,
+                                     double* __restrict__ ximp) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   if (i >= f.nnx || j >= f.nny) return;
   prolong_state_node(f, c, xc, xf, ncomp, i, j);
+  if (ximp) {  // the same field with the Dirichlet values imposed
+    const int n = j * f.nnx + i;
+    for (int comp = 0; comp < 3; ++comp) ximp[comp * f.nn + n] = xf[comp * f.nn + n];
+    impose_dirichlet_node(f, ximp, i, j);
+  }
 }
 
 template <typename T>
@@ -92,9 +99,10 @@ void launch_linearize_levels(const LinLevels<T>& L, const double* x64, T* vbJ, i
 }
 
 void launch_prolong_state64(const Grid& fine, const Grid& coarse, const double* xc, double* xf,
-                            int ncomp, cudaStream_t st) {
+                            int ncomp, cudaStream_t st, double* ximp) {
   note_launch();
-  prolong_state_kernel<<<grid_of(fine), dim3(kBX, kBY), 0, st>>>(fine, coarse, xc, xf, ncomp);
+  prolong_state_kernel<<<grid_of(fine), dim3(kBX, kBY), 0, st>>>(fine, coarse, xc, xf, ncomp,
+                                                                 ncomp == 3 ? ximp : nullptr);
 }
 
 void launch_restrict_full64(const Grid& fine, const Grid& coarse, const double* bf, double* bc,

@@ -153,23 +153,29 @@ __device__ __forceinline__ void vanka_setup_cell(const Grid& g, const Sten<T>& s
 #pragma unroll
   for (int k = 12; k < 24; ++k) A[k] = T(0);
   // local projection stabilisation (pressure rows) of the patches
-  // containing node pairs
-  if (c == 2) {
-    const int PI0 = ci >> 1, PJ0 = cj >> 1;
-    for (int dJ = -1; dJ <= 1; ++dJ)
-      for (int dI = -1; dI <= 1; ++dI) {
-        const int PI = PI0 + dI, PJ = PJ0 + dJ;
+  // containing node pairs: lane l forms the entry of the pressure row of
+  // node l / 4 and the pressure column of node l % 4 (the sum over the
+  // patches that hold both nodes, rows of patches first), and the lanes of
+  // the pressure rows collect their four entries (the pressure-pressure
+  // element blocks are zero, so A[8 + b] is 0 before)
+  {
+    const int la = lane >> 2, lb = lane & 3;
+    const int pai = ci + (la & 1), paj = cj + (la >> 1);  // node la
+    const int pbi = ci + (lb & 1), pbj = cj + (lb >> 1);  // node lb
+    T lps = T(0);
+    for (int PJ = (paj - 1) >> 1; PJ <= (paj >> 1); ++PJ)  // patches holding node la
+      for (int PI = (pai - 1) >> 1; PI <= (pai >> 1); ++PI) {
         if (PI < 0 || PJ < 0 || PI >= g.nx / 2 || PJ >= g.ny / 2) continue;
         if (g.solid[(2 * PJ) * g.nx + 2 * PI]) continue;
-        const int sa = ai - 2 * PI, ta = aj - 2 * PJ;
-        if (sa < 0 || sa > 2 || ta < 0 || ta > 2) continue;
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const int sb = ci + (b & 1) - 2 * PI, tb = cj + (b >> 1) - 2 * PJ;
-          if (sb < 0 || sb > 2 || tb < 0 || tb > 2) continue;
-          A[8 + b] += s.S9[(sa + 3 * ta) * 9 + sb + 3 * tb];
-        }
+        const int sb = pbi - 2 * PI, tb = pbj - 2 * PJ;
+        if (sb < 0 || sb > 2 || tb < 0 || tb > 2) continue;
+        lps += s.S9[((pai - 2 * PI) + 3 * (paj - 2 * PJ)) * 9 + sb + 3 * tb];
       }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const T v = __shfl_sync(mask, lps, a * 4 + b, 16);
+      if (c == 2) A[8 + b] += v;
+    }
   }
   // identity rows and zero columns on constrained DOFs
   uint8_t fl[4];
@@ -197,13 +203,25 @@ __device__ __forceinline__ void vanka_setup_cell(const Grid& g, const Sten<T>& s
   int pcol[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
-    T best = used ? T(-1) : vk_abs(A[k]);
-    int p = lane;
+    // pivot: the largest |A[k]| among the unused rows, the lowest lane on a tie
+    T best;
+    int p;
+    if constexpr (sizeof(T) == 4) {
+      // the bit patterns of non-negative floats order like the floats: one
+      // maximum over the half-warp, then the lowest lane that holds it
+      const unsigned key = used ? 0u : __float_as_uint(vk_abs(A[k]));
+      const unsigned mx = __reduce_max_sync(mask, key);
+      p = (__ffs(__ballot_sync(mask, key == mx) & mask) - 1) & 15;
+      best = __uint_as_float(mx);
+    } else {
+      best = used ? T(-1) : vk_abs(A[k]);
+      p = lane;
 #pragma unroll
-    for (int o = 8; o > 0; o >>= 1) {
-      const T ob = __shfl_xor_sync(mask, best, o, 16);
-      const int op = __shfl_xor_sync(mask, p, o, 16);
-      if (ob > best || (ob == best && op < p)) best = ob, p = op;
+      for (int o = 8; o > 0; o >>= 1) {
+        const T ob = __shfl_xor_sync(mask, best, o, 16);
+        const int op = __shfl_xor_sync(mask, p, o, 16);
+        if (ob > best || (ob == best && op < p)) best = ob, p = op;
+      }
     }
     pcol[k] = p;
     ok = ok && best > T(0);  // the same in every lane of the group

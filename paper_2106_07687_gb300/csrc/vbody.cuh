@@ -239,6 +239,22 @@ __device__ __forceinline__ void old_rhs64_node(const Grid& g, double m,
                                                const double* __restrict__ x,
                                                double* __restrict__ f, int i, int j) {
   const int n = j * g.nnx + i, nn = g.nn;
+  // interior node with four fluid cells: the assembled row, 16 on the node,
+  // 4 on its edge neighbours and 1 on its corner neighbours (fewer FP64
+  // operations than the sum over the cells; FP64 runs at 1/64 of FP32 here)
+  if (i >= 1 && j >= 1 && i < g.nx && j < g.ny && !g.solid[(j - 1) * g.nx + i - 1] &&
+      !g.solid[(j - 1) * g.nx + i] && !g.solid[j * g.nx + i - 1] && !g.solid[j * g.nx + i]) {
+    const int w = n - 1, e = n + 1, s = n - g.nnx, no = n + g.nnx;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const double* xc = x + c * nn;
+      const double edges = (xc[w] + xc[e]) + (xc[s] + xc[no]);
+      const double corners = (xc[s - 1] + xc[s + 1]) + (xc[no - 1] + xc[no + 1]);
+      f[c * nn + n] = m * (16.0 * xc[n] + 4.0 * edges + corners);
+    }
+    f[2 * nn + n] = 0.0;
+    return;
+  }
   double fu = 0, fv = 0;
   for (int cy = 0; cy < 2; ++cy)
     for (int cx = 0; cx < 2; ++cx) {

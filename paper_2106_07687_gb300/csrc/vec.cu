@@ -22,6 +22,15 @@ __global__ void cast_kernel(const Ts* __restrict__ a, Td* __restrict__ b, size_t
     b[i] = (Td)a[i];
 }
 
+__global__ void copy2_kernel(const double2* __restrict__ a, double2* __restrict__ b,
+                             const double2* __restrict__ c, double2* __restrict__ d, size_t n2) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2;
+       i += (size_t)gridDim.x * blockDim.x) {
+    b[i] = a[i];
+    d[i] = c[i];
+  }
+}
+
 template <typename T>
 __global__ void fill_kernel(T* a, T v, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
@@ -252,6 +261,21 @@ template <typename Ts, typename Td>
 void launch_cast(const Ts* a, Td* b, size_t n, cudaStream_t st) {
   note_launch();
   cast_kernel<Ts, Td><<<blocks_for(n), kThreads, 0, st>>>(a, b, n);
+}
+
+void launch_copy2(const double* a, double* b, const double* c, double* d, size_t n,
+                  cudaStream_t st) {
+  const bool vec = n % 2 == 0 && ((uintptr_t)a | (uintptr_t)b | (uintptr_t)c | (uintptr_t)d) % 16 == 0;
+  if (!vec) {
+    cudaMemcpyAsync(b, a, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(d, c, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    return;
+  }
+  note_launch();
+  copy2_kernel<<<blocks_for(n / 2), kThreads, 0, st>>>(reinterpret_cast<const double2*>(a),
+                                                      reinterpret_cast<double2*>(b),
+                                                      reinterpret_cast<const double2*>(c),
+                                                      reinterpret_cast<double2*>(d), n / 2);
 }
 
 template <typename T>
