@@ -211,3 +211,25 @@ def test_streaming_colour_pass_matches_tiled_pass_and_oracle(L, obstacle):
         c.set_state(x)
         c.step(dn.PLAIN)
     assert rel(ctxs[0].get_state().cpu().numpy(), ctxs[1].get_state().cpu().numpy()) < 1e-9
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-9)])
+def test_step_residual_norm_matches_oracle(precision, tol):
+    """The Newton loop's residual norm is formed inside the residual launch
+    (each block's sum, then the last block to finish adds them in block
+    order) and read through the host mailbox: a plain step's res0 is
+    |f - A(x)| of the oracle at the step's start state, f the old-time
+    right-hand side (Eq. 5); on the 256x64 channel the launch has 81
+    blocks.  The mixed build forms A(x) in double-float arithmetic."""
+    dn = lib()
+    ob = synthetic.obstacle_block(1000)
+    prm = fem.Params(nu=0.01, dt=0.01)
+    L = 4
+    ctx = dn.Context(level_solve=L, precision=precision, obstacle_i0=ob[0],
+                     obstacle_j0=ob[1], nu=prm.nu, dt=prm.dt)
+    lev = mesh.hierarchy(L, obstacle=ob)[-1]
+    x = seeded_state(lev, 23)
+    ctx.set_state(torch.from_numpy(x).cuda())
+    st = ctx.step(dn.PLAIN)
+    ref = np.linalg.norm(fem.residual(lev, x, fem.old_time_rhs(lev, x, prm), prm))
+    assert abs(st["res0"] - ref) <= tol * ref, (st["res0"], ref)
