@@ -49,7 +49,7 @@ struct BPar {
   int L;           // finest solved level
   int explicit_on;
   float feat_h, feat_k;  // patch features h_L / 0.25 and k / h_L
-  double feat_pe;        // h_L / (K^2 nu), the Peclet number's factor
+  float feat_pe;         // h_L / (K^2 nu), the Peclet number's factor
 };
 
 // Device-side view of all problems (arrays indexed [problem * nL + level]).

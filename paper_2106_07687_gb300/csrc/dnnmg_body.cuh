@@ -35,11 +35,10 @@ __device__ __forceinline__ void impose_dirichlet_node(const Grid& g, double* __r
 // factor h_L / (K^2 nu) of the Peclet number |sum of the patch's velocities|
 // h_L / (K^2 nu) (formed once on the host: no FP64 division per patch).
 struct FeatConsts {
-  float h_rel, k_rel;
-  double pe;
+  float h_rel, k_rel, pe;
 };
 inline FeatConsts feat_consts(double hL, double nu, double dt, int K) {
-  return FeatConsts{(float)(hL / 0.25), (float)(dt / hL), hL / ((double)(K * K) * nu)};
+  return FeatConsts{(float)(hL / 0.25), (float)(dt / hL), (float)(hL / ((double)(K * K) * nu))};
 }
 
 // The network inputs of the patch on level-L cell `cell` whose K x K nodes
@@ -57,30 +56,44 @@ __device__ __forceinline__ void gather_patch(const Grid& gL, const Grid& gF, int
   constexpr int K2 = K * K, C = 4 * K2 + 4, S = K - 1;
   const int I = cell % gL.nx, J = cell / gL.nx;
   float f[C];
-  double su = 0, sv = 0;
+  // the Peclet feature from the FP32 velocities (the features are rounded to
+  // BF16; FP64 sums and square roots per patch would cost far more here)
+  float su = 0.0f, sv = 0.0f;
 #pragma unroll
   for (int m = 0; m < K2; ++m) {
     const int n = (S * J + m / K) * gF.nnx + S * I + m % K;
-    const double u = xt[n], v = xt[gF.nn + n];
+    const float u = (float)xt[n], v = (float)xt[gF.nn + n];
     su += u;
     sv += v;
-    f[m] = (float)u;
-    f[K2 + m] = (float)v;
+    f[m] = u;
+    f[K2 + m] = v;
     f[2 * K2 + m] = (float)r[n];
     f[3 * K2 + m] = (float)r[gF.nn + n];
   }
   f[4 * K2] = fc.h_rel;
   f[4 * K2 + 1] = 1.0f;
-  f[4 * K2 + 2] = (float)(sqrt(su * su + sv * sv) * fc.pe);
+  f[4 * K2 + 2] = sqrtf(su * su + sv * sv) * fc.pe;
   f[4 * K2 + 3] = fc.k_rel;
   if (RAW) {
 #pragma unroll
     for (int k = 0; k < C; ++k) Xraw[k] = f[k];
     return;
   }
+  // C = 40 or 104 BF16 values, a multiple of 8: 16-byte stores
+  static_assert(C % 8 == 0, "patch row of whole 16-byte chunks");
 #pragma unroll
-  for (int k = 0; k < C; ++k)
-    X[k] = __bfloat16_as_ushort(__float2bfloat16_rn((f[k] - mean[k]) / stdv[k]));
+  for (int q = 0; q < C / 8; ++q) {
+    uint32_t wv[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const int k = 8 * q + 2 * h;
+      const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn((f[k] - mean[k]) / stdv[k]));
+      const uint32_t hi =
+          __bfloat16_as_ushort(__float2bfloat16_rn((f[k + 1] - mean[k + 1]) / stdv[k + 1]));
+      wv[h] = lo | (hi << 16);
+    }
+    reinterpret_cast<uint4*>(X)[q] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+  }
 }
 
 // v_corr = xt + d at fine node (i, j), d = mean of the predictions of the
@@ -94,7 +107,9 @@ __device__ __forceinline__ void scatter_node(const Grid& gL, const Grid& gF,
                                              double* __restrict__ vcorr, int i, int j) {
   constexpr int S = K - 1, K2 = K * K;
   const int n = j * gF.nnx + i;
-  double du = 0, dv = 0;
+  // the mean of the (FP32) predictions in FP32; only the sum with the
+  // prolongated state in FP64 (FP64 work per node is costly on this GPU)
+  float du = 0.0f, dv = 0.0f;
   int cnt = 0;
   for (int dJ = 0; dJ < 2; ++dJ) {
     const int J = j / S - dJ;
@@ -111,17 +126,17 @@ __device__ __forceinline__ void scatter_node(const Grid& gL, const Grid& gF,
     }
   }
   // the mean; counts 1, 2 and 4 scale by exact powers of two (the same
-  // result as the division, without an FP64 division per node)
+  // result as the division)
   if (cnt == 0 || (gF.flags[n] & kVDir)) {
-    du = dv = 0.0;
+    du = dv = 0.0f;
   } else if (cnt == 3) {
-    du /= 3.0, dv /= 3.0;
+    du /= 3.0f, dv /= 3.0f;
   } else {
-    const double sc = cnt == 4 ? 0.25 : (cnt == 2 ? 0.5 : 1.0);
+    const float sc = cnt == 4 ? 0.25f : (cnt == 2 ? 0.5f : 1.0f);
     du *= sc, dv *= sc;
   }
-  vcorr[n] = xt[n] + du;
-  vcorr[gF.nn + n] = xt[gF.nn + n] + dv;
+  vcorr[n] = xt[n] + (double)du;
+  vcorr[gF.nn + n] = xt[gF.nn + n] + (double)dv;
   vcorr[2 * gF.nn + n] = 0.0;
 }
 
