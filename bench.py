@@ -40,6 +40,11 @@ NU_RANGE = (0.004, 0.01)                 # viscosities of the corpus and held-ou
 CORPUS_SEEDS = tuple(range(2000, 2032))  # 32 plain fine trajectories
 HELDOUT_SEEDS = tuple(range(2032, 2036))
 SPIN_STEPS, SPIN_DT, RELAX_STEPS = 50, 0.02, 4  # level-L spin-up to t = 1 s, fine relaxation
+# untimed steps of every method before the timed ones, at least: the
+# network's GRU memory is zero after the state is set, and DNN-MG's third
+# and fourth steps from there take a third Newton iteration (11 FGMRES
+# iterations) while it fills; from the fifth on the step is steady
+NET_WARMUP = 5
 # training batch: 152 tiles of 128 sequences, one per SM of the GB300
 CORPUS_T, TRAIN_ITERS, TRAIN_B, TRAIN_T = 16, 400, 19456, 10
 LARGE_CORPUS_STEPS, LARGE_TRAIN_ITERS = 16, 100  # two replaced levels
@@ -518,7 +523,7 @@ def run_sizes(dn, torch, stream, flush, args, common, corpus, start):
         ref.set_state(x6)
         runs = {"dnnmg": (ctx, dn.NET), "mg_L+1": (ref, dn.PLAIN)}
         for c, mode in runs.values():
-            for _ in range(max(1, args.warmup)):
+            for _ in range(max(NET_WARMUP, args.warmup)):
                 c.step(mode)
         K = args.steps
         times, series, stats, _ = compare_runs(runs, "mg_L+1", ref, L, 1, stream, flush, torch,
@@ -799,7 +804,8 @@ def run_ours(args, rank, world):
     runs = {"dnnmg": (net_ctx, dn.NET), "mg_L": (coarse_ctx, dn.PLAIN),
             "mg_L+1_fp64": (ref_ctx, dn.PLAIN), **{k: (c, dn.PLAIN) for k, c in sweep.items()}}
     fine_names = ("mg_L+1_fp64",) + tuple(sweep)
-    start_runs(runs, x5, x6, fine_names, max(1, args.warmup))
+    warm = max(NET_WARMUP, args.warmup)
+    start_runs(runs, x5, x6, fine_names, warm)
     barrier()
 
     def nvtx(name, begin):  # kernel profilers select the DNN-MG launches by this range
@@ -924,8 +930,10 @@ def run_ours(args, rank, world):
                    "dofs_L+1": ndof(L + 1), "patches": P, "obstacle_block": list(ob),
                    "nu": NU, "dt": DT, "l2": "flushed (256 MB write) before every step",
                    "start": f"developed flow: {SPIN_STEPS} level-{L} steps of {SPIN_DT} s from "
-                            f"rest (t = 1 s), P to level {L + 1}, then {max(1, args.warmup)} "
-                            f"untimed steps of every method",
+                            f"rest (t = 1 s), P to level {L + 1}, then {warm} untimed steps "
+                            f"of every method (at least {NET_WARMUP}: the network's GRU memory "
+                            f"starts at zero; DNN-MG's third and fourth steps take a third "
+                            f"Newton iteration while it fills)",
                    "parallelism": f"independent replicas x{world}",
                    "network_training": f"{TRAIN_ITERS} Adam steps, B={TRAIN_B}, T={TRAIN_T} "
                                        f"windows, device corpus of {len(CORPUS_SEEDS)} "
@@ -988,7 +996,7 @@ def run_ours(args, rank, world):
                           "setup": f"each trained {TRAIN_ITERS} Adam steps on the corpus of "
                                    f"the default network; {args.steps} DNN-MG steps vs plain MG "
                                    f"on level {L + 1} from the developed flow after "
-                                   f"{max(1, args.warmup)} warm-up steps"},
+                                   f"{max(NET_WARMUP, args.warmup)} warm-up steps"},
         "clocks": clk.summary(),
         "e2e": {"value": 1.0 / t_e2e, "unit": "time steps/s",
                 "h2d_bytes_per_step": 8 * ndof(L), "d2h_bytes_per_step": 8 * ndof(L)},
