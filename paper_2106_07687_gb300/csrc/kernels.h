@@ -13,9 +13,11 @@ void note_launches(unsigned long long n);  // kernels of a replayed graph
 unsigned long long launches();
 
 // Operator rows (stencil.cu) ---------------------------------------------
-// y = A'(vbar) w on free DOFs, y = w on constrained DOFs (Eq. 6).
+// y = A'(vbar) w on free DOFs, y = w on constrained DOFs (Eq. 6); nothing
+// when skip is set and *skip != 0 at the launch's start.
 template <typename T>
-void launch_apply(const Grid& g, const Sten<T>& s, const T* w, const T* vb, T* y, cudaStream_t st);
+void launch_apply(const Grid& g, const Sten<T>& s, const T* w, const T* vb, T* y, cudaStream_t st,
+                  const int* skip = nullptr);
 // d = b - A'(vbar) x with the same constrained handling; if `masked`,
 // d is zeroed on constrained DOFs (input of the restriction).
 template <typename T>
@@ -46,8 +48,9 @@ void launch_residual64(const Grid& g, const Sten<double>& s, const double* x, co
 void launch_residual_features(const Grid& g, const Sten<double>& s, const double* x,
                               const double* f, double* r, cudaStream_t st, bool fp32_ops);
 // f = (1/k) M v_old on the velocity rows, 0 on the pressure rows.
+// With copy, also copy = x_old (all three fields) in the same launch.
 void launch_old_time_rhs64(const Grid& g, double inv_k, const double* x_old, double* f,
-                           cudaStream_t st);
+                           cudaStream_t st, double* copy = nullptr);
 
 // f -= coef * (explicit transport + diffusion of x) on the velocity rows
 // (theta-scheme old-time terms); sx from make_explicit_sten
@@ -188,7 +191,11 @@ template <typename T>
 int launch_arnoldi_step(const T* V, size_t ld, int j, T* w, size_t n, double* partials,
                         double* hcol, double* H, int ldh, double* cs, double* sn, double* gvec,
                         double* resid, cudaStream_t st, HostMail* mail = nullptr,
-                        unsigned long long seq = 0);
+                        unsigned long long seq = 0, int slot = 0, int* skip = nullptr,
+                        const double* target = nullptr, int its = 0, int maxit = 0);
+// whether launch_arnoldi_step can launch (its cooperative grid is resident)
+template <typename T>
+bool arnoldi_available();
 // FGMRES small-matrix kernels: Hessenberg column j (from h[0..j+1]) is
 // rotated, the new Givens rotation stored and g updated; resid = |g[j+1]|.
 void launch_givens(double* H, int ldh, double* cs, double* sn, double* gvec, const double* hcol,
@@ -200,11 +207,14 @@ void launch_backsolve(const double* H, int ldh, const double* gvec, int k, doubl
 // nothing launched, the grid cannot be resident): with init, rT = (T) r64,
 // rcur = rT, wsol = 0; then hcol[0] = |rcur|^2 (products in T, sums in
 // FP64), V0 = rcur / |rcur|, gvec[0] = |rcur|, and with mail |rcur|^2 posted
-// into mail->v[1].  partials needs dots_partials(n, 1) doubles.
+// into mail->v[1].  With skip, *skip = 0 (the cycle's iterations run) and,
+// with init, *target = rtol |rcur| (see launch_arnoldi_step).  partials
+// needs dots_partials(n, 1) doubles.
 template <typename T>
 int launch_fgmres_begin(const double* r64, T* rT, T* wsol, T* rcur, T* v0, size_t n,
                         double* partials, double* hcol, double* gvec, bool init, HostMail* mail,
-                        unsigned long long seq, cudaStream_t st);
+                        unsigned long long seq, cudaStream_t st, int* skip = nullptr,
+                        double* target = nullptr, double rtol = 0.0);
 // The end of a converged FGMRES cycle: y = H[0:k,0:k]^{-1} g[0:k] (FP64),
 // then x64 += eps * (wsol + sum_i y[i] Z[i]), the combination in T.
 template <typename T>

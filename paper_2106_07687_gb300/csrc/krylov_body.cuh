@@ -83,6 +83,15 @@ struct ArnoldiArgs {
   double *cs, *sn, *g, *resid;
   HostMail* mail;  // may be null
   unsigned long long seq;
+  int slot;        // resid goes to mail->v[slot]
+  // Device-side stop flag of a speculatively enqueued iteration (may be
+  // null): the step does nothing if *skip is set when it starts, and sets
+  // *skip itself when the cycle stops here, that is when resid <= *target,
+  // its >= maxit (its counts this iteration) or resid is not finite: the
+  // test the host applies to the posted value.
+  int* skip;
+  const double* target;
+  int its, maxit;
 };
 
 // The step over all blocks of a cooperative grid with two grid barriers
@@ -107,6 +116,7 @@ __device__ __forceinline__ void arnoldi_body(const ArnoldiArgs<T>& a, Sync sync)
   constexpr int kG = 8;  // dot products reduced together
   constexpr int kW = NT / 32;
   __shared__ double sg[kW][kG];
+  if (a.skip && *reinterpret_cast<volatile int*>(a.skip)) return;  // the same in every block
   const T* __restrict__ V = a.V;
   T* __restrict__ w = a.w;
   const size_t ld = a.ld;
@@ -206,8 +216,11 @@ __device__ __forceinline__ void arnoldi_body(const ArnoldiArgs<T>& a, Sync sync)
     a.hcol[2 * k] = nrm2;
     const double res = givens_column(a.H, a.ldh, a.cs, a.sn, a.g, a.hcol, j);
     *a.resid = res;
+    // every block read *skip before the first grid barrier: setting it now
+    // only affects the launches after this one
+    if (a.skip) *a.skip = (res <= *a.target || a.its >= a.maxit || !isfinite(res)) ? 1 : 0;
     if (a.mail) {
-      a.mail->v[0] = res;
+      a.mail->v[a.slot] = res;
       mail_post(a.mail, a.seq);
     }
   }

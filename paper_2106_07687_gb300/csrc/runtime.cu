@@ -85,6 +85,8 @@ class Solver final : public SolverBase {
     y_ = c_->mem.alloc<double>(m_ + 1);
     vbJ_ = c_->mem.alloc<T>(2 * (size_t)lv_[K_].g.nn);
     partials_ = c_->mem.alloc<double>(dots_partials(n_, 2 * m_ + 4));
+    skip_ = c_->mem.alloc<int>(1);
+    target_dev_ = c_->mem.alloc<double>(1);
     if (!c_->mem.ok()) return c_->fail(DNNMG_ERR_CUDA, "device allocation failed");
     // persistent sub-cycles: level table and one phase list per possible top level
     if (cfg.persistent_vcycle != 0) {
@@ -222,9 +224,13 @@ class Solver final : public SolverBase {
       HostMail* mail = first ? c_->mail_d : nullptr;
       const unsigned long long t0 = first ? c_->mail_ticket() : 0;
       // rounding of r, zero correction, |r|, V0 in one launch where the
-      // cooperative grid fits, else the separate steps
+      // cooperative grid fits, else the separate steps.  The fused start also
+      // resets the device-side stop flag and sets the stopping target, which
+      // lets the iterations run one ahead of the host (spec).
+      bool spec = arnoldi_available<T>();
       if (launch_fgmres_begin<T>(r64, rT_, wsol_, rcur_, V_, n_, partials_, hcol_, gv_, first,
-                                 mail, t0, st_) != 0) {
+                                 mail, t0, st_, skip_, target_dev_, cfg.gmres_rtol) != 0) {
+        spec = false;
         if (first) {
           launch_cast<double, T>(r64, rT_, n_, st_);
           launch_fill<T>(wsol_, T(0), n_, st_);
@@ -233,36 +239,57 @@ class Solver final : public SolverBase {
         launch_multidot<T>(rcur_, n_, 1, rcur_, n_, partials_, hcol_, st_);
         launch_gmres_start<T>(rcur_, hcol_, V_, gv_, n_, st_, mail, t0);
       }
-      int k = 0;
-      for (int j = 0; j < m_; ++j) {
-        T* vj = V_ + (size_t)j * n_;
-        T* zj = Z_ + (size_t)j * n_;
-        T* w = V_ + (size_t)(j + 1) * n_;
+      // one iteration: preconditioner, matvec and Arnoldi step, whose
+      // residual estimate goes to mailbox slot 2 + (jj & 1); with spec each
+      // launch does nothing once an earlier iteration stopped the cycle on
+      // the device (the same test as the host's below)
+      auto enqueue = [&](int jj, int its_after) -> unsigned long long {
+        T* vj = V_ + (size_t)jj * n_;
+        T* zj = Z_ + (size_t)jj * n_;
+        T* w = V_ + (size_t)(jj + 1) * n_;
+        int* sk = spec ? skip_ : nullptr;
         if (!cycle_ignores_x(K_)) launch_fill<T>(zj, T(0), n_, st_);
-        cycle(K_, vj, zj);
+        cycle(K_, vj, zj, sk);
         int p = c_->prof.begin(DNNMG_STAGE_APPLY, lv_[K_].level, st_);
-        launch_apply<T>(lv_[K_].g, lv_[K_].s, zj, vbJ_, w, st_);
+        launch_apply<T>(lv_[K_].g, lv_[K_].s, zj, vbJ_, w, st_, sk);
         c_->prof.end(p, st_);
         p = c_->prof.begin(DNNMG_STAGE_KRYLOV, lv_[K_].level, st_);
         const unsigned long long ticket = c_->mail_ticket();
-        if (launch_arnoldi_step<T>(V_, n_, j, w, n_, partials_, hcol_, H_, m_ + 1, cs_, sn_, gv_,
-                                   y_ + m_, st_, c_->mail_d, ticket) != 0) {
-          launch_multidot<T>(V_, n_, j + 1, w, n_, partials_, hcol_, st_);
-          launch_multiaxpy<T>(V_, n_, j + 1, hcol_, w, n_, st_);
-          launch_multidot<T>(V_, n_, j + 1, w, n_, partials_, hcol_ + j + 1, st_);
-          launch_multiaxpy<T>(V_, n_, j + 1, hcol_ + j + 1, w, n_, st_);
-          launch_multidot<T>(w, n_, 1, w, n_, partials_, hcol_ + 2 * j + 2, st_);
-          launch_givens(H_, m_ + 1, cs_, sn_, gv_, hcol_, j, y_ + m_, st_);
-          launch_scale_dev<T>(w, hcol_ + 2 * j + 2, 2, w, n_, st_);
-          launch_post(c_->mail_d, ticket, y_ + m_, 0, 1, nullptr, 0, 0, st_);
+        const int slot = 2 + (jj & 1);
+        if (launch_arnoldi_step<T>(V_, n_, jj, w, n_, partials_, hcol_, H_, m_ + 1, cs_, sn_, gv_,
+                                   y_ + m_, st_, c_->mail_d, ticket, slot, sk, target_dev_,
+                                   its_after, cfg.gmres_maxit) != 0) {
+          launch_multidot<T>(V_, n_, jj + 1, w, n_, partials_, hcol_, st_);
+          launch_multiaxpy<T>(V_, n_, jj + 1, hcol_, w, n_, st_);
+          launch_multidot<T>(V_, n_, jj + 1, w, n_, partials_, hcol_ + jj + 1, st_);
+          launch_multiaxpy<T>(V_, n_, jj + 1, hcol_ + jj + 1, w, n_, st_);
+          launch_multidot<T>(w, n_, 1, w, n_, partials_, hcol_ + 2 * jj + 2, st_);
+          launch_givens(H_, m_ + 1, cs_, sn_, gv_, hcol_, jj, y_ + m_, st_);
+          launch_scale_dev<T>(w, hcol_ + 2 * jj + 2, 2, w, n_, st_);
+          launch_post(c_->mail_d, ticket, y_ + m_, slot, 1, nullptr, 0, 0, st_);
         }
         c_->prof.end(p, st_);
+        return ticket;
+      };
+      int k = 0;
+      const int its0 = its;
+      unsigned long long tcur = enqueue(0, its0 + 1);
+      for (int j = 0; j < m_; ++j) {
+        // is there an iteration after this one unless it converges?
+        const bool ahead = j + 1 < m_ && its0 + j + 1 < cfg.gmres_maxit;
+        unsigned long long tnext = 0;
+        size_t rec0 = 0, rec1 = 0;  // its stage-timer records
+        if (spec && ahead) {  // before the host's wait
+          rec0 = c_->prof.mark();
+          tnext = enqueue(j + 1, its0 + j + 2);
+          rec1 = c_->prof.mark();
+        }
         ++its;
         k = j + 1;
         // the residual estimate (and, in the first cycle, |r|^2 posted
-        // by gmres_start) from the host mailbox
-        if (int rc = c_->mail_wait(ticket, "fgmres")) return rc;
-        const double res = c_->mail_h->v[0];
+        // by the cycle's start) from the host mailbox
+        if (int rc = c_->mail_wait(tcur, "fgmres")) return rc;
+        const double res = c_->mail_h->v[2 + (j & 1)];
         if (first) {
           first = false;
           const double b2 = c_->mail_h->v[1];
@@ -270,6 +297,7 @@ class Solver final : public SolverBase {
             its = 0;
             k = 0;
             done = true;
+            c_->prof.drop(rec0, rec1);
             break;
           }
           if (!std::isfinite(b2)) return c_->fail(DNNMG_ERR_NUMERICAL, "non-finite residual");
@@ -278,8 +306,11 @@ class Solver final : public SolverBase {
         if (!std::isfinite(res)) return c_->fail(DNNMG_ERR_NUMERICAL, "non-finite GMRES residual");
         if (res <= target || its >= cfg.gmres_maxit) {
           done = true;
+          c_->prof.drop(rec0, rec1);  // the iteration ahead did nothing
           break;
         }
+        if (!spec && ahead) tnext = enqueue(j + 1, its0 + j + 2);
+        tcur = tnext;
       }
       if (k == 0) break;
       if (done) {
@@ -462,7 +493,9 @@ class Solver final : public SolverBase {
   // One V(nu1, nu2) cycle on level k for A x = b with x = 0 on entry (or any
   // x when cycle_ignores_x(k)).  Levels at or below split_ run their whole
   // sub-cycle as one cooperative launch.
-  void cycle(int k, const T* b, T* x) {
+  // one V-cycle on level k; with skip, the persistent launch does nothing
+  // when *skip is set at its start (a speculative FGMRES iteration)
+  void cycle(int k, const T* b, T* x, const int* skip = nullptr) {
     if (split_ > 0 && lv_[k].level <= split_ && !persistent_failed_ &&
         (split_mode_ == 0 ? vgrid_ > 0 : cluster_ > 0)) {
       const int p = c_->prof.begin(DNNMG_STAGE_VCYCLE, lv_[k].level, st_);
@@ -474,7 +507,7 @@ class Solver final : public SolverBase {
         if (coop_cap_ > 0 && blocks > coop_cap_) blocks = coop_cap_;
         blocks = blocks > vgrid_ ? vgrid_ : blocks;
         rc = launch_vcycle_persistent<T>(dlv_, dph_ + ph_off_[k], ph_n_[k], k, b, x, ainv_,
-                                         (T)c_->cfg.omega, blocks, coarse_nd_, st_);
+                                         (T)c_->cfg.omega, blocks, coarse_nd_, st_, skip);
       } else {
         rc = launch_vcycle_cluster<T>(dlv_, dph_ + ph_off_[k], ph_n_[k], k, b, x, ainv_,
                                       (T)c_->cfg.omega, cluster_, coarse_nd_, st_);
@@ -520,6 +553,8 @@ class Solver final : public SolverBase {
   T *V_ = nullptr, *Z_ = nullptr, *wsol_ = nullptr, *rT_ = nullptr, *rcur_ = nullptr;
   double *H_ = nullptr, *cs_ = nullptr, *sn_ = nullptr, *gv_ = nullptr, *hcol_ = nullptr,
          *y_ = nullptr, *partials_ = nullptr;
+  int* skip_ = nullptr;            // device-side stop flag of an FGMRES cycle
+  double* target_dev_ = nullptr;   // its stopping target rtol |r0|
   bool linearized_ = false, linearized_j_ = false;
   bool coarse_done_ = false;
   T* vbJ_ = nullptr;  // top-level linearisation of the FGMRES matvec
@@ -1206,9 +1241,9 @@ int dnnmg_ctx::patch_infer(const uint16_t* x, float* h, float* out, int P) {
   return net_check("patch_infer");
 }
 
-void dnnmg_ctx::old_rhs(int level, const double* x_old, double* f) {
+void dnnmg_ctx::old_rhs(int level, const double* x_old, double* f, double* copy) {
   const Grid g = grid(level);
-  launch_old_time_rhs64(g, 1.0 / cfg.dt, x_old, f, st);
+  launch_old_time_rhs64(g, 1.0 / cfg.dt, x_old, f, st, copy);
   if (cfg.theta != 1.0)
     launch_explicit_sub64(g, level == L() ? sxL : sxF, 1.0 - cfg.theta, x_old, f, st);
 }
@@ -1259,8 +1294,8 @@ int dnnmg_ctx::residual_api(const double* x, const double* f, double* r) {
 }
 
 // r64 = f - A(x64) and its norm (formed by the residual launch and read
-// through the host mailbox)
-int dnnmg_ctx::residual_norm(const double* f, double* nrm) {
+// through the host mailbox): enqueue, returning the post's number, and wait
+unsigned long long dnnmg_ctx::residual_norm_begin(const double* f) {
   const Grid gL = grid(L());
   NormOut no;
   no.partials = norm_partials;
@@ -1271,18 +1306,31 @@ int dnnmg_ctx::residual_norm(const double* f, double* nrm) {
   const int p = prof.begin(DNNMG_STAGE_RESIDUAL, L(), st);
   launch_residual64(gL, s64L, x64, f, r64, st, mixed(), no);
   prof.end(p, st);
-  if (int rc = mail_wait(no.seq, "residual norm")) return rc;
+  return no.seq;
+}
+
+int dnnmg_ctx::residual_norm_end(unsigned long long t, double* nrm) {
+  if (int rc = mail_wait(t, "residual norm")) return rc;
   *nrm = std::sqrt(mail_h->v[0]);
   return DNNMG_OK;
 }
 
 int dnnmg_ctx::newton(const double* f, dnnmg_step_stats* s) {
-  double nrm = 0;
-  if (int rc = residual_norm(f, &nrm)) return rc;
-  s->res0 = nrm;
-  int it = 0, gits = 0;
+  const unsigned long long t0 = residual_norm_begin(f);
   // the linearisations' singularity flags are read once, after the loop
   solver->clear_setup_status();
+  // the first Newton iteration's linearisation does not depend on the
+  // residual: it is enqueued before the host waits for the norm, so that
+  // the setups run during that round trip (it is wasted only when the state
+  // already meets the tolerance)
+  const bool lin0 = cfg.newton_max > 0;
+  if (lin0)
+    if (int rc = solver->linearize(x64, steps_taken % cfg.coarse_refresh == 0, true, false))
+      return rc;
+  double nrm = 0;
+  if (int rc = residual_norm_end(t0, &nrm)) return rc;
+  s->res0 = nrm;
+  int it = 0, gits = 0;
   while (nrm > cfg.newton_tol && it < cfg.newton_max) {
     if (!std::isfinite(nrm)) return fail(DNNMG_ERR_NUMERICAL, "non-finite Newton residual");
     // the coarse-level factorisation is refreshed at the first Newton step of
@@ -1291,11 +1339,12 @@ int dnnmg_ctx::newton(const double* f, dnnmg_step_stats* s) {
     // with precond_lag the multigrid preconditioner keeps the linearisation
     // of the step's first Newton iteration; the matvec always uses the current one
     const bool precond = it == 0 || !cfg.precond_lag;
-    if (int rc = solver->linearize(x64, refresh, precond, false)) return rc;
+    if (!(it == 0 && lin0))
+      if (int rc = solver->linearize(x64, refresh, precond, false)) return rc;
     int its = 0;
     if (int rc = solver->solve(r64, x64, cfg.eps_damp, &its)) return rc;
     gits += its;
-    if (int rc = residual_norm(f, &nrm)) return rc;
+    if (int rc = residual_norm_end(residual_norm_begin(f), &nrm)) return rc;
     ++it;
   }
   s->newton_its = it;
@@ -1323,8 +1372,7 @@ int dnnmg_ctx::step(int mode, dnnmg_step_stats* stats) {
   if (use_net_rhs) {
     launch_copy2(x64, xold64, bL, f64, n3, st);  // both copies in one launch
   } else {
-    cudaMemcpyAsync(xold64, x64, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
-    old_rhs(L(), xold64, f64);
+    old_rhs(L(), x64, f64, xold64);  // and xold64 = x64 in the same launch
   }
   int rc = newton(f64, &s);
   if (use_net_rhs && (rc != DNNMG_OK || s.newton_its > cfg.fallback_newton_its)) {

@@ -89,6 +89,12 @@ class Prof {
   void end(int e0, cudaStream_t st) {
     if (e0 >= 0) cudaEventRecord(ev_[e0 + 1], st);
   }
+  // records [from, to) of launches that turned out to do nothing (a
+  // speculative FGMRES iteration after the cycle stopped) are not counted
+  size_t mark() const { return recs_.size(); }
+  void drop(size_t from, size_t to) {
+    if (from < to && to <= recs_.size()) recs_.erase(recs_.begin() + from, recs_.begin() + to);
+  }
   void collect(cudaStream_t st) {
     if (recs_.empty()) return;
     cudaStreamSynchronize(st);
@@ -224,7 +230,10 @@ struct dnnmg_ctx {
   // mixed precision: the FP64 residuals evaluate the operator in double-float
   bool mixed() const { return cfg.precision == DNNMG_MIXED; }
   int norm64(const double* v, size_t n, double* out);  // waits for the value
-  int residual_norm(const double* f, double* nrm);     // r64 = f - A(x64), waits for |r64|
+  // r64 = f - A(x64) with |r64| posted to the mailbox (returns the post's
+  // number), and the wait for it
+  unsigned long long residual_norm_begin(const double* f);
+  int residual_norm_end(unsigned long long t, double* nrm);
   double* norm_partials = nullptr;  // per-block sums of the residual launch
   unsigned* norm_counter = nullptr; // blocks done (zero between launches)
 
@@ -242,7 +251,7 @@ struct dnnmg_ctx {
   int net_check(const char* what);
   int init_dnnmg();
   // f = old-time right-hand side of Eq. 5 from x_old on level `level`
-  void old_rhs(int level, const double* x_old, double* f);
+  void old_rhs(int level, const double* x_old, double* f, double* copy = nullptr);
   int dnnmg_correction();
   // xf = P xc (each replaced level once); with ximp, also ximp = xf with the
   // Dirichlet values imposed

@@ -18,10 +18,15 @@ namespace {
 constexpr int kBX = 32, kBY = 4;
 
 __global__ void __launch_bounds__(kBX* kBY)
-    old_rhs64_kernel(Grid g, double m, const double* __restrict__ x, double* __restrict__ f) {
+    old_rhs64_kernel(Grid g, double m, const double* __restrict__ x, double* __restrict__ f,
+                     double* __restrict__ copy) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y;
   if (i >= g.nnx || j >= g.nny) return;
   old_rhs64_node(g, m, x, f, i, j);
+  if (copy) {  // the state itself, saved beside the right-hand side
+    const int n = j * g.nnx + i;
+    for (int c = 0; c < 3; ++c) copy[c * g.nn + n] = x[c * g.nn + n];
+  }
 }
 
 __global__ void __launch_bounds__(kBX* kBY)
@@ -40,7 +45,8 @@ constexpr int kTX = 32, kTY = 8;
 template <typename T>
 __global__ void __launch_bounds__(kTX* kTY)
     apply_tiled_kernel(Grid g, Sten<T> s, const T* __restrict__ w, const T* __restrict__ vb,
-                       T* __restrict__ y) {
+                       T* __restrict__ y, const int* skip) {
+  if (skip && *skip) return;  // a speculative FGMRES iteration after the cycle stopped
   extern __shared__ __align__(16) uint8_t smraw[];
   auto& S = *reinterpret_cast<OpSmem<T, kTX, kTY>*>(smraw);
   T ru, rv, rp;
@@ -189,10 +195,11 @@ size_t smem_attr(K kernel, size_t bytes) {
 }  // namespace
 
 template <typename T>
-void launch_apply(const Grid& g, const Sten<T>& s, const T* w, const T* vb, T* y, cudaStream_t st) {
+void launch_apply(const Grid& g, const Sten<T>& s, const T* w, const T* vb, T* y, cudaStream_t st,
+                  const int* skip) {
   note_launch();
   static const size_t sm = smem_attr(apply_tiled_kernel<T>, sizeof(OpSmem<T, kTX, kTY>));
-  apply_tiled_kernel<T><<<tile_grid(g), kTX * kTY, sm, st>>>(g, s, w, vb, y);
+  apply_tiled_kernel<T><<<tile_grid(g), kTX * kTY, sm, st>>>(g, s, w, vb, y, skip);
 }
 
 template <typename T>
@@ -249,10 +256,10 @@ void launch_residual_features(const Grid& g, const Sten<double>& s, const double
 }
 
 void launch_old_time_rhs64(const Grid& g, double inv_k, const double* x_old, double* f,
-                           cudaStream_t st) {
+                           cudaStream_t st, double* copy) {
   note_launch();
   old_rhs64_kernel<<<node_grid(g), dim3(kBX, kBY), 0, st>>>(g, g.h * g.h / 36.0 * inv_k, x_old,
-                                                              f);
+                                                              f, copy);
 }
 
 void launch_explicit_sub64(const Grid& g, const Sten<double>& sx, double coef, const double* x,
@@ -262,9 +269,9 @@ void launch_explicit_sub64(const Grid& g, const Sten<double>& sx, double coef, c
 }
 
 template void launch_apply<float>(const Grid&, const Sten<float>&, const float*, const float*,
-                                  float*, cudaStream_t);
+                                  float*, cudaStream_t, const int*);
 template void launch_apply<double>(const Grid&, const Sten<double>&, const double*, const double*,
-                                   double*, cudaStream_t);
+                                   double*, cudaStream_t, const int*);
 template void launch_defect<float>(const Grid&, const Sten<float>&, const float*, const float*,
                                    const float*, float*, bool, cudaStream_t);
 template void launch_defect<double>(const Grid&, const Sten<double>&, const double*,

@@ -223,7 +223,10 @@ template <typename T>
 __global__ void __launch_bounds__(kCoopThreads)
     vcycle_kernel(const VLevel<T>* __restrict__ lv, const Phase* __restrict__ ph, int nph, int top,
                   const T* __restrict__ topb, T* __restrict__ topx, const double* __restrict__ Ainv,
-                  T omega) {
+                  T omega, const int* skip) {
+  // a speculative FGMRES iteration after the cycle stopped: every block
+  // reads the same flag (set before this launch) and returns before any barrier
+  if (skip && *skip) return;
   extern __shared__ __align__(16) uint8_t dyn[];  // coarse vector or pass tiles
   __shared__ WalkSmem<T> S;
   cg::grid_group grid = cg::this_grid();
@@ -323,9 +326,9 @@ int vcycle_grid(int coarse_nd) {
 template <typename T>
 int launch_vcycle_persistent(const VLevel<T>* lv, const Phase* ph, int nph, int top, const T* topb,
                              T* topx, const double* Ainv, T omega, int grid, int coarse_nd,
-                             cudaStream_t st) {
-  void* args[] = {(void*)&lv, (void*)&ph, (void*)&nph, (void*)&top, (void*)&topb,
-                  (void*)&topx, (void*)&Ainv, (void*)&omega};
+                             cudaStream_t st, const int* skip) {
+  void* args[] = {(void*)&lv,   (void*)&ph,   (void*)&nph,   (void*)&top, (void*)&topb,
+                  (void*)&topx, (void*)&Ainv, (void*)&omega, (void*)&skip};
   note_launch();
   const cudaError_t e =
       cudaLaunchCooperativeKernel((void*)vcycle_kernel<T>, dim3(grid), dim3(kCoopThreads), args,
@@ -394,10 +397,10 @@ template int vcycle_grid<float>(int);
 template int vcycle_grid<double>(int);
 template int launch_vcycle_persistent<float>(const VLevel<float>*, const Phase*, int, int,
                                              const float*, float*, const double*, float, int, int,
-                                             cudaStream_t);
+                                             cudaStream_t, const int*);
 template int launch_vcycle_persistent<double>(const VLevel<double>*, const Phase*, int, int,
                                               const double*, double*, const double*, double, int,
-                                              int, cudaStream_t);
+                                              int, cudaStream_t, const int*);
 template int vcycle_cluster_size<float>(int);
 template int vcycle_cluster_size<double>(int);
 template int launch_vcycle_cluster<float>(const VLevel<float>*, const Phase*, int, int,

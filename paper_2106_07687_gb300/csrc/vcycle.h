@@ -51,10 +51,11 @@ template <typename T>
 int launch_vcycle_cluster(const VLevel<T>* lv, const Phase* ph, int nph, int top, const T* topb,
                           T* topx, const double* Ainv, T omega, int cluster, int coarse_nd,
                           cudaStream_t st);
-// returns 0 on success
+// returns 0 on success; with skip, nothing runs when *skip != 0 at the
+// launch's start
 template <typename T>
 int launch_vcycle_persistent(const VLevel<T>* lv, const Phase* ph, int nph, int top, const T* topb,
                              T* topx, const double* Ainv, T omega, int grid, int coarse_nd,
-                             cudaStream_t st);
+                             cudaStream_t st, const int* skip = nullptr);
 
 }  // namespace dnnmg

@@ -22,12 +22,23 @@ __global__ void cast_kernel(const Ts* __restrict__ a, Td* __restrict__ b, size_t
     b[i] = (Td)a[i];
 }
 
-__global__ void copy2_kernel(const double2* __restrict__ a, double2* __restrict__ b,
-                             const double2* __restrict__ c, double2* __restrict__ d, size_t n2) {
+// b = a, d = c over n doubles: pairs as 16-byte accesses, the odd last
+// element (n odd) by the first thread
+__global__ void copy2_kernel(const double* __restrict__ a, double* __restrict__ b,
+                             const double* __restrict__ c, double* __restrict__ d, size_t n) {
+  const size_t n2 = n / 2;
+  const double2* a2 = reinterpret_cast<const double2*>(a);
+  const double2* c2 = reinterpret_cast<const double2*>(c);
+  double2* b2 = reinterpret_cast<double2*>(b);
+  double2* d2 = reinterpret_cast<double2*>(d);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2;
        i += (size_t)gridDim.x * blockDim.x) {
-    b[i] = a[i];
-    d[i] = c[i];
+    b2[i] = a2[i];
+    d2[i] = c2[i];
+  }
+  if (n % 2 && blockIdx.x == 0 && threadIdx.x == 0) {
+    b[n - 1] = a[n - 1];
+    d[n - 1] = c[n - 1];
   }
 }
 
@@ -172,7 +183,8 @@ __global__ void __launch_bounds__(kThreads)
     fgmres_begin_kernel(const double* __restrict__ r64, T* __restrict__ rT, T* __restrict__ wsol,
                         T* __restrict__ rcur, T* __restrict__ v0, size_t n,
                         double* __restrict__ partials, double* hcol, double* g, int init,
-                        HostMail* mail, unsigned long long seq) {
+                        HostMail* mail, unsigned long long seq, int* skip, double* target,
+                        double rtol) {
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
   __shared__ double sh[32];
@@ -206,6 +218,10 @@ __global__ void __launch_bounds__(kThreads)
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     hcol[0] = nrm2;
     g[0] = beta;
+    if (skip) {  // a new cycle runs; the first cycle's |r| sets the stopping target
+      *skip = 0;
+      if (init) *target = rtol * beta;
+    }
     if (mail) {
       mail->v[1] = nrm2;
       mail_post(mail, seq);
@@ -265,17 +281,14 @@ void launch_cast(const Ts* a, Td* b, size_t n, cudaStream_t st) {
 
 void launch_copy2(const double* a, double* b, const double* c, double* d, size_t n,
                   cudaStream_t st) {
-  const bool vec = n % 2 == 0 && ((uintptr_t)a | (uintptr_t)b | (uintptr_t)c | (uintptr_t)d) % 16 == 0;
+  const bool vec = ((uintptr_t)a | (uintptr_t)b | (uintptr_t)c | (uintptr_t)d) % 16 == 0;
   if (!vec) {
     cudaMemcpyAsync(b, a, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
     cudaMemcpyAsync(d, c, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
     return;
   }
   note_launch();
-  copy2_kernel<<<blocks_for(n / 2), kThreads, 0, st>>>(reinterpret_cast<const double2*>(a),
-                                                      reinterpret_cast<double2*>(b),
-                                                      reinterpret_cast<const double2*>(c),
-                                                      reinterpret_cast<double2*>(d), n / 2);
+  copy2_kernel<<<blocks_for(n / 2 + 1), kThreads, 0, st>>>(a, b, c, d, n);
 }
 
 template <typename T>
@@ -320,11 +333,9 @@ void launch_combine(const T* Z, size_t ld, int k, const double* y, double eps, T
   combine_kernel<T, Tx><<<blocks_for(n), kThreads, 0, st>>>(Z, ld, k, y, eps, x, n);
 }
 
+// blocks of the cooperative Arnoldi launch (one per SM), 0 if it cannot run
 template <typename T>
-int launch_arnoldi_step(const T* V, size_t ld, int j, T* w, size_t n, double* partials,
-                        double* hcol, double* H, int ldh, double* cs, double* sn, double* gvec,
-                        double* resid, cudaStream_t st, HostMail* mail, unsigned long long seq) {
-  if (j + 2 > 64) return 1;  // the second pass holds k + 1 values
+int arnoldi_blocks() {
   static const int nblk = [] {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
@@ -335,8 +346,24 @@ int launch_arnoldi_step(const T* V, size_t ld, int j, T* w, size_t n, double* pa
     cudaGetLastError();
     return ok ? sms : 0;
   }();
+  return nblk;
+}
+
+template <typename T>
+bool arnoldi_available() {
+  return arnoldi_blocks<T>() > 0;
+}
+
+template <typename T>
+int launch_arnoldi_step(const T* V, size_t ld, int j, T* w, size_t n, double* partials,
+                        double* hcol, double* H, int ldh, double* cs, double* sn, double* gvec,
+                        double* resid, cudaStream_t st, HostMail* mail, unsigned long long seq,
+                        int slot, int* skip, const double* target, int its, int maxit) {
+  if (j + 2 > 64) return 1;  // the second pass holds k + 1 values
+  const int nblk = arnoldi_blocks<T>();
   if (nblk == 0) return 1;
-  const ArnoldiArgs<T> a{V, ld, j, w, n, partials, hcol, H, ldh, cs, sn, gvec, resid, mail, seq};
+  const ArnoldiArgs<T> a{V,  ld, j,    w,    n,    partials, hcol,   H,  ldh,  cs,
+                         sn, gvec, resid, mail, seq, slot,     skip,  target, its, maxit};
   void* args[] = {(void*)&a};
   if (cudaLaunchCooperativeKernel((void*)arnoldi_kernel<T>, dim3(nblk), dim3(kArnThreads), args,
                                   0, st) != cudaSuccess) {
@@ -362,7 +389,8 @@ void launch_backsolve(const double* H, int ldh, const double* gvec, int k, doubl
 template <typename T>
 int launch_fgmres_begin(const double* r64, T* rT, T* wsol, T* rcur, T* v0, size_t n,
                         double* partials, double* hcol, double* gvec, bool init, HostMail* mail,
-                        unsigned long long seq, cudaStream_t st) {
+                        unsigned long long seq, cudaStream_t st, int* skip, double* target,
+                        double rtol) {
   static const bool fits = [] {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
@@ -377,7 +405,8 @@ int launch_fgmres_begin(const double* r64, T* rT, T* wsol, T* rcur, T* v0, size_
   int in = init ? 1 : 0;
   void* args[] = {(void*)&r64,  (void*)&rT,       (void*)&wsol, (void*)&rcur,
                   (void*)&v0,   (void*)&n,        (void*)&partials, (void*)&hcol,
-                  (void*)&gvec, (void*)&in,       (void*)&mail, (void*)&seq};
+                  (void*)&gvec, (void*)&in,       (void*)&mail, (void*)&seq,
+                  (void*)&skip, (void*)&target,   (void*)&rtol};
   if (cudaLaunchCooperativeKernel((void*)fgmres_begin_kernel<T>, dim3(kDotBlocks), dim3(kThreads),
                                   args, 0, st) != cudaSuccess) {
     cudaGetLastError();
@@ -416,10 +445,12 @@ void launch_gmres_start(const T* r, const double* nrm2, T* v0, double* gvec, siz
                                      cudaStream_t);                                            \
   template int launch_arnoldi_step<T>(const T*, size_t, int, T*, size_t, double*, double*,     \
                                       double*, int, double*, double*, double*, double*,        \
-                                      cudaStream_t, HostMail*, unsigned long long);            \
+                                      cudaStream_t, HostMail*, unsigned long long, int, int*,  \
+                                      const double*, int, int);                                \
+  template bool arnoldi_available<T>();                                                       \
   template int launch_fgmres_begin<T>(const double*, T*, T*, T*, T*, size_t, double*, double*, \
                                       double*, bool, HostMail*, unsigned long long,            \
-                                      cudaStream_t);                                           \
+                                      cudaStream_t, int*, double*, double);                    \
   template void launch_fgmres_finish<T>(const double*, int, const double*, int, const T*,      \
                                         size_t, const T*, double, double*, size_t,             \
                                         cudaStream_t);
