@@ -227,7 +227,9 @@ class Solver final : public SolverBase {
       // cooperative grid fits, else the separate steps.  The fused start also
       // resets the device-side stop flag and sets the stopping target, which
       // lets the iterations run one ahead of the host (spec).
-      bool spec = arnoldi_available<T>();
+      // (only where every launch of an iteration can skip itself: the whole
+      // cycle one cooperative launch, the cooperative Arnoldi step)
+      bool spec = arnoldi_available<T>() && cycle_one_coop_launch(K_);
       if (launch_fgmres_begin<T>(r64, rT_, wsol_, rcur_, V_, n_, partials_, hcol_, gv_, first,
                                  mail, t0, st_, skip_, target_dev_, cfg.gmres_rtol) != 0) {
         spec = false;
@@ -490,11 +492,18 @@ class Solver final : public SolverBase {
            (split_mode_ == 0 ? vgrid_ > 0 : cluster_ > 0) && c_->cfg.nu1 > 0 && k > 0;
   }
 
+  // Whether the whole cycle on level k is one cooperative launch (which
+  // can skip itself on the device; the per-stage launches of the levels
+  // above a split cannot).
+  bool cycle_one_coop_launch(int k) const {
+    return split_ > 0 && lv_[k].level <= split_ && !persistent_failed_ && split_mode_ == 0 &&
+           vgrid_ > 0;
+  }
+
   // One V(nu1, nu2) cycle on level k for A x = b with x = 0 on entry (or any
   // x when cycle_ignores_x(k)).  Levels at or below split_ run their whole
-  // sub-cycle as one cooperative launch.
-  // one V-cycle on level k; with skip, the persistent launch does nothing
-  // when *skip is set at its start (a speculative FGMRES iteration)
+  // sub-cycle as one cooperative launch; with skip, that launch does nothing
+  // when *skip is set at its start (a speculative FGMRES iteration).
   void cycle(int k, const T* b, T* x, const int* skip = nullptr) {
     if (split_ > 0 && lv_[k].level <= split_ && !persistent_failed_ &&
         (split_mode_ == 0 ? vgrid_ > 0 : cluster_ > 0)) {
@@ -1321,9 +1330,9 @@ int dnnmg_ctx::newton(const double* f, dnnmg_step_stats* s) {
   solver->clear_setup_status();
   // the first Newton iteration's linearisation does not depend on the
   // residual: it is enqueued before the host waits for the norm, so that
-  // the setups run during that round trip (it is wasted only when the state
-  // already meets the tolerance)
-  const bool lin0 = cfg.newton_max > 0;
+  // the setups run during that round trip (it is wasted when the state
+  // already meets the tolerance, so not after a step that needed no iteration)
+  const bool lin0 = cfg.newton_max > 0 && last_newton_its > 0;
   if (lin0)
     if (int rc = solver->linearize(x64, steps_taken % cfg.coarse_refresh == 0, true, false))
       return rc;
@@ -1349,6 +1358,7 @@ int dnnmg_ctx::newton(const double* f, dnnmg_step_stats* s) {
   }
   s->newton_its = it;
   s->gmres_its = gits;
+  last_newton_its = it;
   s->res_final = nrm;
   int setup = 0;
   if (const int ds = solver->device_status(&setup))

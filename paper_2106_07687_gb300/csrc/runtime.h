@@ -182,6 +182,7 @@ struct dnnmg_ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   dnnmg::Prof prof;
   long long steps_taken = 0;   // time steps since setup (coarse refresh schedule)
+  int last_newton_its = 1;     // Newton iterations of the last Newton solve
   // patch network
   dnnmg::NetDims nd{};
   bool net_ok = false;
