@@ -572,8 +572,8 @@ def equal_error(times, summary, K, names, target="dnnmg"):
     the sweep points (mean velocity error, ms per step) sorted by error, and
     log(time) interpolated linearly in log(error) between the two points
     that bracket the target's error.  When every point is more accurate
-    than the target, the loosest point's time is an upper bound of MG(L+1)'s
-    time at equal error (bracketed = false)."""
+    than the target, the fastest of them bounds MG(L+1)'s time at equal
+    error from above (bracketed = false)."""
     import math
     e_t = summary[target]["vel_l2_err_mean"]
     pts = sorted((summary[n]["vel_l2_err_mean"], times[n] / K, n) for n in names)
@@ -588,9 +588,9 @@ def equal_error(times, summary, K, names, target="dnnmg"):
         t_eq = math.exp(math.log(t0) + w * (math.log(t1) - math.log(t0)))
         out.update(bracketed=True, between=[n0, n1], mg_fine_ms_at_equal_error=t_eq)
     elif lo:
-        e0, t0, n0 = lo[-1]
+        e0, t0, n0 = min(lo, key=lambda p: p[1])
         out.update(bracketed=False, between=[n0, None], mg_fine_ms_at_equal_error=t0,
-                   note="every MG(L+1) point is more accurate than the target; the loosest "
+                   note="every MG(L+1) point is more accurate than the target; the fastest "
                         "point's time bounds MG(L+1)'s time at equal error from above")
     else:
         out.update(bracketed=False, between=[None, pts[0][2]], mg_fine_ms_at_equal_error=None,

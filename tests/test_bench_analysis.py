@@ -61,6 +61,19 @@ def test_equal_error_unbracketed_gives_an_upper_bound():
     assert eq["mg_fine_ms_at_equal_error"] == 6.0 and eq["speedup_vs_mg_fine"] == 6.0 / 5.0
 
 
+def test_equal_error_unbracketed_takes_the_fastest_accurate_point():
+    """When every sweep point is more accurate than the target, the bound is
+    the fastest of them, not necessarily the loosest (the loosest can be the
+    slower one, e.g. a one-Newton-step, one-V-cycle point)."""
+    K = 2
+    errs = {"dnnmg": 1e-3, "a": 1e-9, "b": 1e-5, "c": 3e-5}
+    times = {"dnnmg": 6.0, "a": 18.0, "b": 3.4, "c": 4.8}
+    eq = bench.equal_error(times, _summary(errs), K, ["a", "b", "c"])
+    assert not eq["bracketed"] and eq["between"] == ["b", None]
+    assert eq["mg_fine_ms_at_equal_error"] == 1.7
+    assert abs(eq["speedup_vs_mg_fine"] - 1.7 / 3.0) < 1e-15
+
+
 def test_source_hash_is_stable_and_covers_the_sources():
     h = bench.source_hash()
     assert len(h) == 16 and h == bench.source_hash()
