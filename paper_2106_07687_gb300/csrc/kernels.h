@@ -37,6 +37,7 @@ struct NormOut {
   double* out = nullptr;
   HostMail* mail = nullptr;
   unsigned long long seq = 0;
+  const int* status = nullptr;  // when set, status[0..3] is posted too (mail->iv[0..3])
 };
 int residual_blocks(const Grid& g);
 void launch_residual64(const Grid& g, const Sten<double>& s, const double* x, const double* f,

@@ -400,6 +400,10 @@ class Solver final : public SolverBase {
     launch_post(c_->mail_d, t, nullptr, 0, 0, status_, 0, 4, st_);
     if (c_->mail_wait(t, "status") != DNNMG_OK) return -1;
     for (int i = 0; i < 4; ++i) st[i] = c_->mail_h->iv[i];
+    return status_from(st, setup);
+  }
+  const int* status_words() const override { return status_; }
+  int status_from(const int st[4], int* setup) override {
     if (st[2]) cudaMemsetAsync(status_ + 2, 0, sizeof(int), st_);  // reported once
     if (setup) *setup = st[0];
     return st[2];
@@ -969,7 +973,12 @@ int dnnmg_ctx::dnnmg_correction() {
   restrict_down(bF, bL);                                              // R
   prof.end(pr, st);
   have_vcorr = have_net_rhs = true;
-  return net_check("dnnmg correction");
+  // the network's status goes to the mailbox and is read once the step's
+  // work is complete (step() synchronises at its end anyway)
+  if (int rc = check("dnnmg correction")) return rc;
+  launch_post(mail_d, mail_ticket(), nullptr, 0, 0, net_status, 4, 1, st);
+  net_status_posted = true;
+  return DNNMG_OK;
 }
 
 // One training sample per patch (corpus generation): the level-L step from
@@ -1304,7 +1313,7 @@ int dnnmg_ctx::residual_api(const double* x, const double* f, double* r) {
 
 // r64 = f - A(x64) and its norm (formed by the residual launch and read
 // through the host mailbox): enqueue, returning the post's number, and wait
-unsigned long long dnnmg_ctx::residual_norm_begin(const double* f) {
+unsigned long long dnnmg_ctx::residual_norm_begin(const double* f, bool with_status) {
   const Grid gL = grid(L());
   NormOut no;
   no.partials = norm_partials;
@@ -1312,6 +1321,7 @@ unsigned long long dnnmg_ctx::residual_norm_begin(const double* f) {
   no.out = dots;
   no.mail = mail_d;
   no.seq = mail_ticket();
+  if (with_status) no.status = solver->status_words();
   const int p = prof.begin(DNNMG_STAGE_RESIDUAL, L(), st);
   launch_residual64(gL, s64L, x64, f, r64, st, mixed(), no);
   prof.end(p, st);
@@ -1353,7 +1363,8 @@ int dnnmg_ctx::newton(const double* f, dnnmg_step_stats* s) {
     int its = 0;
     if (int rc = solver->solve(r64, x64, cfg.eps_damp, &its)) return rc;
     gits += its;
-    if (int rc = residual_norm_end(residual_norm_begin(f), &nrm)) return rc;
+    // the smoothers' and setups' status words travel with this norm
+    if (int rc = residual_norm_end(residual_norm_begin(f, true), &nrm)) return rc;
     ++it;
   }
   s->newton_its = it;
@@ -1361,7 +1372,10 @@ int dnnmg_ctx::newton(const double* f, dnnmg_step_stats* s) {
   last_newton_its = it;
   s->res_final = nrm;
   int setup = 0;
-  if (const int ds = solver->device_status(&setup))
+  int words[4];
+  for (int i = 0; i < 4; ++i) words[i] = mail_h->iv[i];
+  // after an iteration the status words came with the last norm; else read them now
+  if (const int ds = it > 0 ? solver->status_from(words, &setup) : solver->device_status(&setup))
     return ds < 0 ? check("newton") : fail(DNNMG_ERR_TIMEOUT, "a colour pass's inverse copy timed out");
   if (setup & 1) return fail(DNNMG_ERR_NUMERICAL, "singular local Vanka matrix");
   if (setup & 2) return fail(DNNMG_ERR_NUMERICAL, "singular coarse-level matrix");
@@ -1401,7 +1415,19 @@ int dnnmg_ctx::step(int mode, dnnmg_step_stats* stats) {
   }
   ++steps_taken;
   cudaEventRecord(ev1, st);
-  cudaEventSynchronize(ev1);
+  if (cudaEventSynchronize(ev1) != cudaSuccess) {  // a fault in the step's kernels
+    net_status_posted = false;
+    const int rc3 = check("step");
+    return rc3 ? rc3 : fail(DNNMG_ERR_CUDA, "step: stream synchronisation failed");
+  }
+  if (net_status_posted) {  // the correction's status, complete with the step
+    net_status_posted = false;
+    if (mail_h->iv[4] & 4) {
+      cudaMemsetAsync(net_status, 0, sizeof(int), st);
+      if (rc == DNNMG_OK || rc == DNNMG_ERR_NOT_CONVERGED)
+        rc = fail(DNNMG_ERR_TIMEOUT, "dnnmg correction: tensor-core wait timed out");
+    }
+  }
   float ms = 0;
   cudaEventElapsedTime(&ms, ev0, ev1);
   s.ms = ms;

@@ -151,6 +151,10 @@ class SolverBase {
   // clear_setup_status (1: a local Vanka matrix, 2: the coarse matrix)
   virtual int device_status(int* setup = nullptr) = 0;
   virtual void clear_setup_status() = 0;
+  // the device status words (4 ints) and the same answer as device_status
+  // from their values already read (posted with a later residual norm)
+  virtual const int* status_words() const = 0;
+  virtual int status_from(const int st[4], int* setup) = 0;
 };
 
 std::unique_ptr<SolverBase> make_solver(struct ::dnnmg_ctx* ctx);
@@ -200,6 +204,7 @@ struct dnnmg_ctx {
   uint16_t* X = nullptr;
   float *net_out = nullptr, *hid = nullptr, *feat_mean = nullptr, *feat_std = nullptr;
   bool have_net_rhs = false, have_vcorr = false;
+  bool net_status_posted = false;  // the correction's status waits in mailbox iv[4]
   double* stat_partial = nullptr;  // [128][C_in][2] feature-statistics partials
   // training workspace (capacity cfg.train_batch x cfg.train_seq)
   dnnmg::TrainBufs tb{};
@@ -233,7 +238,7 @@ struct dnnmg_ctx {
   int norm64(const double* v, size_t n, double* out);  // waits for the value
   // r64 = f - A(x64) with |r64| posted to the mailbox (returns the post's
   // number), and the wait for it
-  unsigned long long residual_norm_begin(const double* f);
+  unsigned long long residual_norm_begin(const double* f, bool with_status = false);
   int residual_norm_end(unsigned long long t, double* nrm);
   double* norm_partials = nullptr;  // per-block sums of the residual launch
   unsigned* norm_counter = nullptr; // blocks done (zero between launches)

@@ -107,6 +107,8 @@ __device__ __forceinline__ void norm_reduce(double sq, const NormOut& no) {
     *no.counter = 0u;
     if (no.mail) {
       no.mail->v[0] = tot;
+      if (no.status)
+        for (int i = 0; i < 4; ++i) no.mail->iv[i] = no.status[i];
       mail_post(no.mail, no.seq);
     }
   }
