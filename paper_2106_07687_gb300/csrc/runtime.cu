@@ -226,9 +226,9 @@ class Solver final : public SolverBase {
       // rounding of r, zero correction, |r|, V0 in one launch where the
       // cooperative grid fits, else the separate steps.  The fused start also
       // resets the device-side stop flag and sets the stopping target, which
-      // lets the iterations run one ahead of the host (spec).
-      // (only where every launch of an iteration can skip itself: the whole
-      // cycle one cooperative launch, the cooperative Arnoldi step)
+      // lets the iterations run one ahead of the host (spec) where every
+      // launch of an iteration can skip itself: the whole cycle one
+      // cooperative launch and the cooperative Arnoldi step.
       bool spec = arnoldi_available<T>() && cycle_one_coop_launch(K_);
       if (launch_fgmres_begin<T>(r64, rT_, wsol_, rcur_, V_, n_, partials_, hcol_, gv_, first,
                                  mail, t0, st_, skip_, target_dev_, cfg.gmres_rtol) != 0) {
