@@ -233,3 +233,31 @@ def test_step_residual_norm_matches_oracle(precision, tol):
     st = ctx.step(dn.PLAIN)
     ref = np.linalg.norm(fem.residual(lev, x, fem.old_time_rhs(lev, x, prm), prm))
     assert abs(st["res0"] - ref) <= tol * ref, (st["res0"], ref)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-5)])
+def test_speculative_fgmres_takes_the_same_steps_as_the_staged_path(precision, tol):
+    """With the whole V-cycle in one cooperative launch, each FGMRES iteration
+    is enqueued before the host has read the previous one's residual
+    estimate and skips itself on the device once the cycle has stopped; with
+    the per-stage launches (persistent_vcycle = 0) nothing runs ahead.  Both
+    must take the same Newton and FGMRES iterations and reach the same
+    states (same stopping tests; the two cycle implementations agree to
+    rounding)."""
+    dn = lib()
+    ob = synthetic.obstacle_block(1000)
+    L = 4
+    kw = dict(level_solve=L, precision=precision, obstacle_i0=ob[0], obstacle_j0=ob[1],
+              nu=0.01, dt=0.01)
+    spec = dn.Context(persistent_vcycle=L, persistent_mode=0, **kw)
+    staged = dn.Context(persistent_vcycle=0, **kw)
+    x0 = torch.from_numpy(seeded_state(mesh.hierarchy(L, obstacle=ob)[-1], 29)).cuda()
+    for c in (spec, staged):
+        c.set_state(x0)
+    for n in range(3):
+        sa, sb = spec.step(dn.PLAIN), staged.step(dn.PLAIN)
+        assert (sa["newton_its"], sa["gmres_its"]) == (sb["newton_its"], sb["gmres_its"]), n
+        assert rel(spec.get_state().cpu().numpy(), staged.get_state().cpu().numpy()) < tol, n
+    plan = spec.vcycle_plan()
+    assert plan["split_level"] == L and plan["split_mode"] == 0, plan
+    assert staged.vcycle_plan()["split_level"] == 0
