@@ -126,11 +126,29 @@ __device__ __forceinline__ void arnoldi_body(const ArnoldiArgs<T>& a, Sync sync)
   double* p1 = a.partials;                    // [k][nb]
   double* p2 = a.partials + (size_t)k * nb;   // [k + 1][nb]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // per value of a group of gk <= kG dot products (this thread's sums in
+  // acc): a shuffle tree in each warp in T, then a second tree over the
+  // warps' sums in FP64 (the order of block_sum); the block's partial of
+  // value i0 + u goes to part[(i0 + u) nb + block]
+  auto reduce_group = [&](const T* acc, int gk, int i0, double* part) {
+#pragma unroll
+    for (int u = 0; u < kG; ++u) {
+      if (u >= gk) break;
+      T v = acc[u];  // the warp's sum in T, then FP64 from the block level on
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) sg[warp][u] = (double)v;
+    }
+    __syncthreads();
+    if (warp < gk) {  // warp u finishes value u
+      double t = lane < kW ? sg[lane][warp] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) part[(size_t)(i0 + warp) * nb + blockIdx.x] = t;
+    }
+    __syncthreads();  // sg is rewritten by the next group
+  };
   // the nk partial dot products <V[i], w> for i < nv and <w, w> for i >= nv
-  // of this block's chunk, kG at a time in one pass over the elements:
-  // products, per-thread sums and a shuffle tree in each warp in T, then
-  // per value a second tree over the warps' sums in FP64 (the order of
-  // block_sum)
+  // of this block's chunk, kG at a time in one pass over the elements
+  // (products and per-thread sums in T)
   auto dots = [&](int nv, int nk, double* part) {
     for (int i0 = 0; i0 < nk; i0 += kG) {
       const int gk = min(kG, nk - i0);
@@ -143,20 +161,7 @@ __device__ __forceinline__ void arnoldi_body(const ArnoldiArgs<T>& a, Sync sync)
         for (int u = 0; u < kG; ++u)
           if (u < gk) acc[u] += (i0 + u < nv ? V[(size_t)(i0 + u) * ld + e] : we) * we;
       }
-#pragma unroll
-      for (int u = 0; u < kG; ++u) {
-        if (u >= gk) break;
-        T v = acc[u];  // the warp's sum in T, then FP64 from the block level on
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) sg[warp][u] = (double)v;
-      }
-      __syncthreads();
-      if (warp < gk) {  // warp u finishes value u
-        double t = lane < kW ? sg[lane][warp] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) part[(size_t)(i0 + warp) * nb + blockIdx.x] = t;
-      }
-      __syncthreads();  // sg is rewritten by the next group
+      reduce_group(acc, gk, i0, part);
     }
   };
   // out[i] = sum over the blocks' partials of row i, i < nk: one warp per
@@ -191,26 +196,87 @@ __device__ __forceinline__ void arnoldi_body(const ArnoldiArgs<T>& a, Sync sync)
     }
     __syncthreads();  // hT is rewritten by the next pass
   };
-  dots(k, k, p1);
-  sync();
-  finish(p1, k, h[0]);
-  axpy(h[0]);
-  dots(k, k + 1, p2);
-  sync();
-  finish(p2, k + 1, h[1]);  // h[1][k] = <w, w> before the second update
-  axpy(h[1]);
-  if (threadIdx.x == 0) {
-    double q = h[1][k];
-    for (int i = 0; i < k; ++i) q -= h[1][i] * h[1][i];
-    nrm2 = q;
+  auto norm_scale = [&]() -> T {
+    if (threadIdx.x == 0) {
+      double q = h[1][k];
+      for (int i = 0; i < k; ++i) q -= h[1][i] * h[1][i];
+      nrm2 = q;
+    }
+    __syncthreads();
+    const double s = block_scalar([&] {
+      const double v = sqrt(fmax(nrm2, 0.0));
+      return v != 0.0 ? 1.0 / v : 0.0;
+    });
+    return (T)s;
+  };
+  // With few basis vectors, the thread's elements of w and of V[0..j] stay
+  // in registers through both passes (one load of each, one store of w):
+  // the same operations in the same order as the general path below, which
+  // reloads them from L2 for every pass.
+  // (the second pass's k + 1 products form one group of at most kG)
+  constexpr int kRK = sizeof(T) == 4 ? kG - 1 : 4;  // basis vectors held in registers
+  constexpr int kRE = 4;                       // elements per thread
+  if (k <= kRK && hi - lo <= (size_t)kRE * NT) {
+    T wr[kRE], vr[kRK][kRE];
+    bool in[kRE];
+#pragma unroll
+    for (int q = 0; q < kRE; ++q) {
+      const size_t e = lo + threadIdx.x + (size_t)q * NT;
+      in[q] = e < hi;
+      wr[q] = in[q] ? w[e] : T(0);
+#pragma unroll
+      for (int i = 0; i < kRK; ++i) vr[i][q] = (in[q] && i < k) ? V[(size_t)i * ld + e] : T(0);
+    }
+    auto rdots = [&](int nk, double* part) {  // <V[i], w> for i < k, then <w, w>
+      T acc[kG];
+#pragma unroll
+      for (int u = 0; u < kG; ++u) acc[u] = T(0);
+#pragma unroll
+      for (int q = 0; q < kRE; ++q) {
+        if (!in[q]) continue;
+#pragma unroll
+        for (int u = 0; u < kG; ++u)
+          if (u < nk) acc[u] += (u < k && u < kRK ? vr[u < kRK ? u : 0][q] : wr[q]) * wr[q];
+      }
+      reduce_group(acc, nk, 0, part);
+    };
+    auto raxpy = [&](const double* hh) {
+      if (threadIdx.x < k) hT[threadIdx.x] = (T)hh[threadIdx.x];
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < kRE; ++q) {
+        T acc = wr[q];
+#pragma unroll
+        for (int i = 0; i < kRK; ++i)
+          if (i < k) acc -= hT[i] * vr[i][q];
+        wr[q] = acc;
+      }
+      __syncthreads();  // hT is rewritten by the next pass
+    };
+    rdots(k, p1);
+    sync();
+    finish(p1, k, h[0]);
+    raxpy(h[0]);
+    rdots(k + 1, p2);
+    sync();
+    finish(p2, k + 1, h[1]);  // h[1][k] = <w, w> before the second update
+    raxpy(h[1]);
+    const T sT = norm_scale();
+#pragma unroll
+    for (int q = 0; q < kRE; ++q)
+      if (in[q]) w[lo + threadIdx.x + (size_t)q * NT] = wr[q] * sT;
+  } else {
+    dots(k, k, p1);
+    sync();
+    finish(p1, k, h[0]);
+    axpy(h[0]);
+    dots(k, k + 1, p2);
+    sync();
+    finish(p2, k + 1, h[1]);  // h[1][k] = <w, w> before the second update
+    axpy(h[1]);
+    const T sT = norm_scale();
+    for (size_t e = lo + threadIdx.x; e < hi; e += NT) w[e] *= sT;
   }
-  __syncthreads();
-  const double s = block_scalar([&] {
-    const double v = sqrt(fmax(nrm2, 0.0));
-    return v != 0.0 ? 1.0 / v : 0.0;
-  });
-  const T sT = (T)s;
-  for (size_t e = lo + threadIdx.x; e < hi; e += NT) w[e] *= sT;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     for (int i = 0; i < k; ++i) a.hcol[i] = h[0][i], a.hcol[k + i] = h[1][i];
     a.hcol[2 * k] = nrm2;
