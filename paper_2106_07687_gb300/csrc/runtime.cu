@@ -1266,14 +1266,6 @@ void dnnmg_ctx::old_rhs(int level, const double* x_old, double* f, double* copy)
     launch_explicit_sub64(g, level == L() ? sxL : sxF, 1.0 - cfg.theta, x_old, f, st);
 }
 
-int dnnmg_ctx::norm64(const double* v, size_t n, double* out) {
-  const unsigned long long t = mail_ticket();
-  launch_multidot<double>(v, n, 1, v, n, partials, dots, st, mail_d, t);
-  if (int rc = mail_wait(t, "norm")) return rc;
-  *out = std::sqrt(mail_h->v[0]);
-  return DNNMG_OK;
-}
-
 int dnnmg_ctx::get_state(double* x) {
   cudaMemcpyAsync(x, x64, 3 * sizeof(double) * grid(L()).nn, cudaMemcpyDeviceToDevice, st);
   cudaStreamSynchronize(st);

@@ -235,7 +235,6 @@ struct dnnmg_ctx {
   int lc() const { return cfg.level_coarse; }
   // mixed precision: the FP64 residuals evaluate the operator in double-float
   bool mixed() const { return cfg.precision == DNNMG_MIXED; }
-  int norm64(const double* v, size_t n, double* out);  // waits for the value
   // r64 = f - A(x64) with |r64| posted to the mailbox (returns the post's
   // number), and the wait for it
   unsigned long long residual_norm_begin(const double* f, bool with_status = false);
