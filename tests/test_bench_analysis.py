@@ -77,3 +77,54 @@ def test_equal_error_unbracketed_takes_the_fastest_accurate_point():
 def test_source_hash_is_stable_and_covers_the_sources():
     h = bench.source_hash()
     assert len(h) == 16 and h == bench.source_hash()
+
+
+def test_vcycle_bytes_closed_form():
+    """The algorithmic bytes of one V(2,2) cycle, against the count written
+    out by hand for a two-level cycle (top level 2 over the coarse level 1):
+    16 colour passes of 576 B per fluid cell / 4 and 44 B per node, one
+    defect of 44 B per node, the transfers (36 B per fine node, 36 B per
+    coarse node), zeroing the top iterate (12 B per node), and the 891 x 891
+    FP64 coarse inverse with its vector read once."""
+    n2 = (16 * 4 + 1) * (4 * 4 + 1)       # 1105 nodes on level 2
+    n1 = (16 * 2 + 1) * (4 * 2 + 1)       # 297 nodes on level 1
+    cells2 = 64 * 16 - 4 * 16             # 960 fluid cells (the 2 x 2-cell block per level-0 cell)
+    passes = 16 * (cells2 / 4 * 576 + 44 * n2)
+    expect = 12 * n2 + passes + 44 * n2 + 36 * n2 + 36 * n1 + 8 * 891 * 891 + 8 * 891
+    assert bench.vcycle_bytes(2) == expect
+    assert bench.nnodes(2) == n2 and bench.fluid_cells(2) == cells2
+    # the benchmark's figure (top level 5), quoted in the design notes
+    assert bench.vcycle_bytes(5) == 265147100
+
+
+def test_job_throughput_counts_every_rank():
+    assert bench.job_throughput(1000.0, 10, 1) == 10.0
+    assert bench.job_throughput(500.0, 10, 4) == 80.0
+
+
+def test_summarize_launches_aggregates_an_ncu_launch_list(tmp_path, capsys):
+    """Launches and total time per kernel (template arguments kept, the
+    namespace and the parameter list dropped), units converted to us, shares
+    of the total, largest first."""
+    head = ["ID", "Process ID", "Kernel Name", "Metric Name", "Metric Unit", "Metric Value"]
+    rows = [
+        ["0", "1", "void dnnmg::(anonymous namespace)::vcycle_kernel<float>(const int *)",
+         "gpu__time_duration.sum", "usecond", "300"],
+        ["1", "1", "void dnnmg::(anonymous namespace)::vcycle_kernel<float>(const int *)",
+         "gpu__time_duration.sum", "nsecond", "100,000"],
+        ["2", "1", "dnnmg::(anonymous namespace)::post_kernel(dnnmg::HostMail *)",
+         "gpu__time_duration.sum", "usecond", "100"],
+        ["3", "1", "dnnmg::(anonymous namespace)::post_kernel(dnnmg::HostMail *)",
+         "dram__bytes_read.sum", "byte", "64"],
+    ]
+    p = tmp_path / "launches.csv"
+    with open(p, "w", newline="") as fh:
+        import csv
+        w = csv.writer(fh)
+        w.writerow(["==PROF== a line before the table"])
+        w.writerow(head)
+        w.writerows(rows)
+    bench.summarize_launches(str(p))
+    out = capsys.readouterr().out.splitlines()
+    assert out[1].split() == ["vcycle_kernel<float>", "2", "400.0", "80.0%"]
+    assert out[2].split() == ["post_kernel", "1", "100.0", "20.0%"]
